@@ -1,0 +1,188 @@
+"""FP64 CPU oracle for the direct polygon / polyhedron Fourier transform.
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow reference the CUDA
+library is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import it; the library never does, and it
+shares no code with the CUDA path.
+
+The arithmetic lives in ``pft_oracle.c`` (plain C99, FP64, OpenMP over Q or
+faces); this module compiles it with gcc on first use and wraps it with ctypes.
+Sign convention: FT(Q) = integral of exp(+i Q.r) over the region (Sec. 2, Eq. 9).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pft_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64 = ctypes.c_int64
+
+
+def build(force: bool = False) -> str:
+    """Compile pft_oracle.c to a shared library (gcc -O2 -fopenmp, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                               "-fno-fast-math", "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.orc_ft2d.argtypes = [_dp, _i64p, _i64, _dp, _i64, _dp, ctypes.c_int]
+            lib.orc_seg_terms2d.argtypes = [_dp, _i64p, _i64, ctypes.c_double, ctypes.c_double, _dp]
+            lib.orc_ft2d_batched.argtypes = [_dp, _i64p, _i64, _dp, _i64p, _i64, _dp, ctypes.c_int]
+            lib.orc_ft3d.argtypes = [_dp, _i64, _i32p, _i64, _dp, _i64, _dp, ctypes.c_int]
+            lib.orc_face_terms3d.argtypes = [_dp, _i64, _i32p, _i64, _dp, _dp]
+            lib.orc_grad2d.argtypes = [_dp, _i64p, _i64, _dp, _i64, _dp, _dp, ctypes.c_int]
+            lib.orc_grad3d.argtypes = [_dp, _i64, _i32p, _i64, _dp, _i64, _dp, _i64p, _i64, _dp,
+                                       ctypes.c_int]
+            lib.orc_max_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _f64(a, cols=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if cols is not None:
+        a = a.reshape(-1, cols)
+    return a
+
+
+def _ptr(a, typ):
+    return a.ctypes.data_as(typ)
+
+
+def _threads(n):
+    return int(n) if n else max(1, _load().orc_max_threads())
+
+
+def _complex(out):
+    return out[:, 0] + 1j * out[:, 1]
+
+
+def _loops(verts, loop_off):
+    v = _f64(verts, 2)
+    off = np.ascontiguousarray(np.asarray(loop_off if loop_off is not None else [0, v.shape[0]],
+                                          dtype=np.int64))
+    return v, off
+
+
+def ft2d(verts, q, loop_off=None, threads=None) -> np.ndarray:
+    """FT_A(Q) of the region bounded by CCW loops (Eq. 7 summed over segments)."""
+    v, off = _loops(verts, loop_off)
+    q = _f64(q, 2)
+    out = np.empty((q.shape[0], 2))
+    _load().orc_ft2d(_ptr(v, _dp), _ptr(off, _i64p), off.size - 1, _ptr(q, _dp), q.shape[0],
+                     _ptr(out, _dp), _threads(threads))
+    return _complex(out)
+
+
+def seg_terms2d(verts, qxy, loop_off=None) -> np.ndarray:
+    """The individual segment terms of Eq. 5/7 at one Q (their sum is FT_A)."""
+    v, off = _loops(verts, loop_off)
+    out = np.empty((v.shape[0], 2))
+    _load().orc_seg_terms2d(_ptr(v, _dp), _ptr(off, _i64p), off.size - 1, float(qxy[0]),
+                            float(qxy[1]), _ptr(out, _dp))
+    return _complex(out)
+
+
+def ft2d_batched(verts, poly_off, q, q_off=None, threads=None) -> np.ndarray:
+    """One FT_A per polygon; shared Q (q_off None, result [n_polys, n_q]) or per-polygon Q (CSR)."""
+    v = _f64(verts, 2)
+    off = np.ascontiguousarray(np.asarray(poly_off, dtype=np.int64))
+    q = _f64(q, 2)
+    npoly = off.size - 1
+    if q_off is None:
+        out = np.empty((npoly * q.shape[0], 2))
+        qo = None
+    else:
+        qo = np.ascontiguousarray(np.asarray(q_off, dtype=np.int64))
+        out = np.empty((q.shape[0], 2))
+    _load().orc_ft2d_batched(_ptr(v, _dp), _ptr(off, _i64p), npoly, _ptr(q, _dp),
+                             None if qo is None else _ptr(qo, _i64p), q.shape[0], _ptr(out, _dp),
+                             _threads(threads))
+    r = _complex(out)
+    return r.reshape(npoly, -1) if q_off is None else r
+
+
+def _mesh(verts, faces):
+    v = _f64(verts, 3)
+    f = np.ascontiguousarray(np.asarray(faces, dtype=np.int32).reshape(-1, 3))
+    return v, f
+
+
+def ft3d(verts, faces, q, threads=None) -> np.ndarray:
+    """FT_V(Q) of a closed outward-oriented triangle surface (sign-corrected Eq. 17)."""
+    v, f = _mesh(verts, faces)
+    q = _f64(q, 3)
+    out = np.empty((q.shape[0], 2))
+    rc = _load().orc_ft3d(_ptr(v, _dp), v.shape[0], _ptr(f, _i32p), f.shape[0], _ptr(q, _dp),
+                          q.shape[0], _ptr(out, _dp), _threads(threads))
+    if rc:
+        raise ValueError("face index out of range")
+    return _complex(out)
+
+
+def face_terms3d(verts, faces, Q) -> np.ndarray:
+    """The per-face terms I_m of Eq. 17 (sign-corrected) at one Q != 0."""
+    v, f = _mesh(verts, faces)
+    Q = _f64(Q).reshape(3)
+    out = np.empty((f.shape[0], 2))
+    rc = _load().orc_face_terms3d(_ptr(v, _dp), v.shape[0], _ptr(f, _i32p), f.shape[0],
+                                  _ptr(Q, _dp), _ptr(out, _dp))
+    if rc:
+        raise ValueError("face index out of range")
+    return _complex(out)
+
+
+def grad2d(verts, q, g, loop_off=None, threads=None) -> np.ndarray:
+    """dL/dverts [n_v, 2] for g_Q = dL/dRe F + i dL/dIm F (shape derivative)."""
+    v, off = _loops(verts, loop_off)
+    q = _f64(q, 2)
+    g = np.ascontiguousarray(np.stack([np.real(g), np.imag(g)], axis=1).astype(np.float64))
+    out = np.empty((v.shape[0], 2))
+    _load().orc_grad2d(_ptr(v, _dp), _ptr(off, _i64p), off.size - 1, _ptr(q, _dp), q.shape[0],
+                       _ptr(g, _dp), _ptr(out, _dp), _threads(threads))
+    return out
+
+
+def grad3d(verts, faces, q, g, vsel=None, threads=None) -> np.ndarray:
+    """dL/dverts [n_v, 3] (or [len(vsel), 3]) for g_Q = dL/dRe F + i dL/dIm F (shape derivative)."""
+    v, f = _mesh(verts, faces)
+    q = _f64(q, 3)
+    g = np.ascontiguousarray(np.stack([np.real(g), np.imag(g)], axis=1).astype(np.float64))
+    if vsel is not None:
+        sel = np.ascontiguousarray(np.asarray(vsel, dtype=np.int64))
+        out = np.empty((sel.size, 3))
+        selp, nsel = _ptr(sel, _i64p), sel.size
+    else:
+        out = np.empty((v.shape[0], 3))
+        selp, nsel = None, 0
+    rc = _load().orc_grad3d(_ptr(v, _dp), v.shape[0], _ptr(f, _i32p), f.shape[0], _ptr(q, _dp),
+                            q.shape[0], _ptr(g, _dp), selp, nsel, _ptr(out, _dp), _threads(threads))
+    if rc:
+        raise ValueError("oracle grad3d failed (bad index or out of memory)")
+    return out
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
