@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the direct polyhedron Fourier transform on one or more GB300s.
+
+Workload (one step): FT_V(Q) of an icosphere of subdivision 8 (1,310,720
+triangles, vertices moved radially by 1 + 0.05 U[-1,1), seed 5) on a 128^3 Q
+grid over [-60, 60)^3 -- 2.75e12 (Q, triangle) pairs -- through the C ABI
+(pft3d_mesh, FP32 arithmetic with compensated sums and an FP64 finish).
+
+Prints one JSON line: G pair-evaluations/s, the main kernel's roofline
+fraction against the FP32/SFU issue limit, the end-to-end rate with host
+buffers, and the FP64 CPU oracle's rate on a bounded sample of the same
+workload.  ``--impl reference`` times that oracle alone (the reference arm).
+
+Multi-GPU (torchrun): every rank transforms its own perturbed mesh (seed
+5 + rank) on the full grid; there is no collective on the data path (weak
+scaling); the step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G (Q,segment) pair-evals/s and % FP32/SFU roofline at stated error vs FP64"
+UNIT = "Gpair/s"
+WORKLOAD = "icosphere8_perturbed_q128cubed"
+
+# Algorithmic per-pair instruction counts of the 3D FP32 face term (see the
+# face_pair_f32 formula): FP32-pipe operations (add/mul/fma/compare/round) and
+# SFU operations (sin, cos, reciprocal), per branch.
+OPS_SERIES = {"fp32": 40, "sfu": 2}   # face-integral series (small phase spread)
+OPS_EDGE = {"fp32": 107, "sfu": 9}    # edge sum of Eq. 17, polynomial sinc
+FP32_LANES, SFU_LANES = 128, 16       # per SM per clock
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU-oracle sample")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle leg")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
+
+
+def workload(rank):
+    from paper_2104_08309_gb300 import synth
+    v, f = synth.perturbed_icosphere(8, seed=5 + rank, amp=0.05)
+    q = synth.q_grid_3d(128, 60.0)
+    return v, f, q
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+def branch_mix(v, f, q, tau=1.0, n=1 << 16, seed=0):
+    """Fraction of (Q, face) pairs taking the series branch (P < tau^2/4), from a seeded sample."""
+    rng = np.random.default_rng(seed)
+    fi = rng.integers(0, f.shape[0], n)
+    qi = rng.integers(0, q.shape[0], n)
+    p = v.astype(np.float64)[f[fi]]
+    g = p.mean(axis=1)
+    a0 = np.einsum("ij,ij->i", q[qi], p[:, 0] - g)
+    a1 = np.einsum("ij,ij->i", q[qi], p[:, 1] - g)
+    P = a0 * a0 + a0 * a1 + a1 * a1
+    return float(np.mean(P < 0.25 * tau * tau))
+
+
+def roofline(pairs, t_main_s, mix, n_sm, clk_mhz):
+    ops = {k: mix * OPS_SERIES[k] + (1 - mix) * OPS_EDGE[k] for k in ("fp32", "sfu")}
+    issue = ops["fp32"] + ops["sfu"]
+    cyc = max(issue / FP32_LANES, ops["sfu"] / SFU_LANES)       # SM cycles per pair at the limit
+    peak_ops = n_sm * clk_mhz * 1e6 * issue / cyc                # issue-slot ops/s at the limit
+    achieved = issue * pairs / t_main_s
+    return ops, issue, achieved, peak_ops
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid, self.proc, self.path = uuid, None, None
+
+    def start(self):
+        try:
+            out = os.path.join(ROOT, "gpurun_out")
+            os.makedirs(out, exist_ok=True)
+            self.path = os.path.join(out, f"clocks_{os.getpid()}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.uuid}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = [r.split(", ") for r in open(self.path).read().strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def cpu_baseline(v, f, q, target_s, seed=7):
+    """FP64 oracle (as it stands) on a seeded Q sample over all faces, on every host core."""
+    import oracle
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(q.shape[0])
+    t0 = time.perf_counter()
+    oracle.ft3d(v, f, q[order[:threads]], threads=threads)          # calibration
+    dt = time.perf_counter() - t0
+    n = int(max(threads, min(q.shape[0], threads * round(max(1.0, target_s / max(dt, 1e-6))))))
+    idx = np.sort(order[:n])
+    t0 = time.perf_counter()
+    ref = oracle.ft3d(v, f, q[idx], threads=threads)
+    dt = time.perf_counter() - t0
+    rate = n * f.shape[0] / dt / 1e9
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} seeded Q points of the 128^3 grid x all {f.shape[0]} triangles ({dt:.1f} s)"}, idx, ref
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    v, f, q = workload(0)
+    import oracle
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(11)
+    t0 = time.perf_counter()
+    oracle.ft3d(v, f, q[rng.integers(0, q.shape[0], threads)], threads=threads)
+    per_q = (time.perf_counter() - t0) / threads
+    n = max(threads, int(threads * round(6.0 / max(per_q * threads, 1e-6))))   # ~6 s per step
+    times = []
+    for s in range(args.warmup + args.steps):
+        idx = rng.choice(q.shape[0], n, replace=False)
+        t0 = time.perf_counter()
+        oracle.ft3d(v, f, q[idx], threads=threads)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    value = n * f.shape[0] / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "faces": int(f.shape[0]), "q_points": int(q.shape[0]),
+                       "step": f"{n} seeded Q points x all triangles (bounded sample)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{n} Q points per step x {f.shape[0]} triangles"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def traffic_from_profile():
+    """DRAM bytes per main-kernel launch from the committed ncu summary, if it matches this source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "fwd3d_icosphere8_traffic.txt")
+    src = os.path.join(ROOT, "paper_2104_08309_gb300", "csrc", "pft_fwd.cu")
+    try:
+        kv = dict(l.split(":", 1) for l in open(path).read().splitlines() if ":" in l)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if kv.get("source_sha256_16", "").strip() == sha:
+            return float(kv["dram_bytes_per_launch_full_size"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import paper_2104_08309_gb300 as pft
+    from paper_2104_08309_gb300 import build as pbuild
+    pbuild.build()
+
+    v, f, q = workload(rank)
+    pairs = float(f.shape[0]) * float(q.shape[0])
+    vd, fd, qd = (torch.from_numpy(a).to(dev) for a in (v, f, q))
+    lib = pft.load()
+    e_main = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    e_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    for a, b in e_main:
+        a.record()
+        b.record()
+    opts = pft.make_options({})
+    nbytes = lib.pft3d_workspace_size(v.shape[0], f.shape[0], q.shape[0], ctypes.byref(opts))
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = torch.empty(q.shape[0], 2, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)    # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step(o):
+        rc = lib.pft3d_mesh(vd.data_ptr(), v.shape[0], fd.data_ptr(), f.shape[0], qd.data_ptr(), q.shape[0],
+                            out.data_ptr(), ws.data_ptr(), nbytes, ctypes.byref(o), stream.cuda_stream)
+        if rc:
+            raise RuntimeError(f"pft3d_mesh failed: {pft.status_string(rc)}")
+        return lib.pft_last_launch_count()
+
+    for _ in range(args.warmup):
+        step(opts)
+    torch.cuda.synchronize()
+    if pft.pft_status(ws) != 0:
+        raise RuntimeError("device status after warm-up: " + pft.status_string(pft.pft_status(ws)))
+
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    clocks = ClockSampler(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches = 0
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                                   # L2 flushed between steps (outside the step events)
+        o = pft.make_options({"main_start_event": e_main[k][0].cuda_event,
+                              "main_stop_event": e_main[k][1].cuda_event})
+        e_step[k][0].record(stream)
+        launches += step(o)
+        e_step[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms_step = float(np.mean([a.elapsed_time(b) for a, b in e_step]))
+    ms_main = float(np.mean([a.elapsed_time(b) for a, b in e_main]))
+    if world > 1:
+        t = torch.tensor([ms_step, ms_main], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step, ms_main = t.tolist()
+    status = pft.pft_status(ws)
+
+    # end to end: pinned host buffers, H2D of the inputs and D2H of the result inside the timed region
+    hv, hf, hq = (torch.from_numpy(a).pin_memory() for a in (v, f, q))
+    hout = torch.empty(q.shape[0], 2, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(max(1, args.e2e_steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        vd.copy_(hv, non_blocking=True)
+        fd.copy_(hf, non_blocking=True)
+        qd.copy_(hq, non_blocking=True)
+        step(opts)
+        hout.copy_(out, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_t = float(np.mean(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_t = t.item()
+
+    if rank == 0:
+        pk, pk_kind = peaks()
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        clk_max = float(pk.get("sm_max_mhz", 2070.0))
+        mix = branch_mix(v, f, q)
+        ops, issue, achieved, peak_ops = roofline(pairs, ms_main / 1e3, mix, n_sm, clk_max)
+        value = world * pairs / (ms_step / 1e3) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "faces": int(f.shape[0]), "q_points": int(q.shape[0]),
+                       "pairs_per_step": pairs, "edge_terms_per_step": 3 * pairs,
+                       "l2": "flushed between steps (512 MB write outside the step events)",
+                       "parallelism": f"independent replicas x{world}" if world > 1 else "single GPU",
+                       "wall_s_timed_region": t_wall, "device_status": int(status)},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "Tops/s", "frac": achieved / peak_ops,
+                         "traffic": traffic_from_profile(),
+                         "kernel": "k_fwd<Pol3F32,4,256>", "main_kernel_ms": ms_main,
+                         "peak_basis": f"{n_sm} SMs x 128 FP32/SFU issue slots x {clk_max:.0f} MHz "
+                                       f"({pk_kind} max SM clock)",
+                         "ops_per_pair": {"fp32": ops["fp32"], "sfu": ops["sfu"]},
+                         "series_branch_fraction": mix},
+            "clocks": clk,
+            "gpu_launches": launches,
+            "e2e": {"value": world * pairs / (e2e_t / 1e3) / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": int(v.nbytes + f.nbytes + q.nbytes),
+                    "d2h_bytes_per_step": int(q.shape[0] * 16)},
+        }
+        if clk and clk.get("sm_mhz"):
+            line["roofline"]["frac_at_measured_clock"] = achieved / (peak_ops * clk["sm_mhz"] / clk_max)
+        if not args.no_cpu and world == 1:
+            cb, idx, ref = cpu_baseline(v, f, q, args.cpu_seconds)
+            got = out.cpu().numpy()[idx]
+            vol = float(np.real(__import__("oracle").ft3d(v, f, np.zeros((1, 3)))[0]))
+            cb["max_abs_err_vs_oracle_over_volume"] = float(np.max(np.abs(got[:, 0] + 1j * got[:, 1] - ref)) / vol)
+            line["cpu_baseline"] = cb
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,176 @@
+/*
+ * pft.h -- C ABI of libpft: direct (non-FFT) Fourier transform of polygonal
+ * areas and closed triangulated surfaces on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: B. B. Maranville, "An implementation of an efficient direct Fourier
+ * transform of polygonal areas and volumes", arXiv 2104.08309.
+ *   FT(Q) = integral over the region of exp(+i Q.r) dA (2D) or dV (3D)  (Sec. 2, Sec. 3 Eq. 9)
+ * evaluated by the divergence theorem (Eq. 1, Eq. 10) as a sum over boundary
+ * segments (2D, Eq. 7) or over faces and their edges (3D, Eq. 17 with the overall
+ * sign fixed so that FT(0) = +volume for outward faces).  Q carries no 2 pi.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every array argument is a DEVICE pointer owned by the caller.  The library
+ *    never allocates or frees device memory in these calls; scratch space comes
+ *    from the caller as `ws` (at least `*_workspace_size` bytes, 256-byte aligned).
+ *  - Calls only enqueue work on `stream` (a cudaStream_t passed as void*; NULL =
+ *    the legacy default stream) and return at once.  Argument errors are
+ *    returned synchronously; errors the GPU detects (bad index, non-finite
+ *    coordinate, malformed offsets, a wait that timed out) are written into a
+ *    status word inside `ws`, read back with pft_status().
+ *  - Vertices are float32 and are taken as exact.  Q is float64 at the boundary;
+ *    the FP32 path rounds it once on the device.  Outputs are float64 (re, im)
+ *    pairs and are fully overwritten.
+ *  - Results are deterministic: no floating-point atomics; every reduction runs
+ *    in a fixed order.
+ *  - Thread safety: no mutable global state; concurrent calls need separate
+ *    workspaces.
+ */
+#ifndef PFT_H
+#define PFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes (synchronous) and status-word values (device-detected). */
+typedef enum {
+  PFT_OK = 0,
+  PFT_ERR_INVALID_ARG = 1,   /* null pointer, negative count, bad option          */
+  PFT_ERR_INDEX_RANGE = 2,   /* face index outside [0, n_verts) (status word)     */
+  PFT_ERR_NONFINITE = 3,     /* NaN/Inf vertex coordinate (status word)           */
+  PFT_ERR_WORKSPACE = 4,     /* ws NULL, misaligned or smaller than required      */
+  PFT_ERR_CUDA = 5,          /* a CUDA launch or copy failed                      */
+  PFT_ERR_TIMEOUT = 6,       /* a bounded wait on a copy gave up (status word)    */
+  PFT_ERR_UNSUPPORTED = 7,   /* option combination not implemented                */
+  PFT_ERR_OFFSETS = 8        /* CSR offsets not non-decreasing / inconsistent     */
+} pft_status_code;
+
+typedef enum {
+  PFT_FP32_COMPENSATED = 0,  /* FP32 bulk arithmetic, compensated sums, FP64 finish */
+  PFT_FP64 = 1               /* plain FP64 throughout (comparison path)             */
+} pft_precision;
+
+/*
+ * Options.  Zero-initialised means "defaults".  A NULL pointer is the same as
+ * all defaults.
+ *  precision        pft_precision.
+ *  q_per_thread     Q points each thread keeps in registers (0 = default; FP32: 1, 2,
+ *                   4 or 8; FP64: 1 or 2).
+ *  block_threads    threads per block of the main kernel (0 = default; 128 or 256).
+ *  k_splits         number of segment/face chunks summed in the FP64 second pass
+ *                   (0 = chosen from the problem size and the GPU).  For a fixed
+ *                   value the result is bitwise reproducible; different values
+ *                   agree to rounding.
+ *  tile_items       must be 0 (the shared-memory tile size is fixed per path).
+ *  face_series_tau  3D only: faces whose corner phases satisfy
+ *                   P = (a0^2 + a1^2 + a2^2)/2 < tau^2/4 (a_k = Q.(p_k - centroid);
+ *                   this implies max_l |Q.d_l| < tau) take the series of the face
+ *                   integral (Eq. 14) instead of the edge sum of Eq. 17, which
+ *                   cancels there.  0 = default 1.0; must lie in (0, 1].
+ *  main_start_event, main_stop_event
+ *                   cudaEvent_t handles or NULL.  When set, they are recorded on
+ *                   `stream` immediately before and after the main (pair-sum)
+ *                   kernel, so that a caller can time it alone.
+ */
+typedef struct {
+  int32_t precision;
+  int32_t q_per_thread;
+  int32_t block_threads;
+  int32_t k_splits;
+  int32_t tile_items;
+  float face_series_tau;
+  void* main_start_event;
+  void* main_stop_event;
+  int32_t reserved[4];
+} pft_options;
+
+/* Bytes of workspace the matching call needs for these sizes and options. */
+size_t pft2d_workspace_size(int64_t n_verts, int64_t n_loops, int64_t n_q, const pft_options* opts);
+size_t pft2d_batched_workspace_size(int64_t n_verts, int64_t n_polys, int64_t n_q,
+                                    const int64_t* q_off_host, const pft_options* opts);
+size_t pft3d_workspace_size(int64_t n_verts, int64_t n_faces, int64_t n_q, const pft_options* opts);
+
+/*
+ * 2D: FT_A(Q) of the region bounded by closed loops (Sec. 2, Eq. 7 per segment).
+ *  verts     [n_verts][2] float32.  Loop l is verts[loop_off[l] .. loop_off[l+1]-1],
+ *            its last vertex joined to its first.  CCW loops add area, CW loops
+ *            subtract it (holes).
+ *  loop_off  [n_loops+1] int64, loop_off[0] = 0, non-decreasing,
+ *            loop_off[n_loops] = n_verts (checked on the device -> PFT_ERR_OFFSETS).
+ *  q         [n_q][2] float64.      out  [n_q][2] float64 (re, im).
+ */
+int pft2d_polygons(const float* verts, int64_t n_verts, const int64_t* loop_off, int64_t n_loops,
+                   const double* q, int64_t n_q, double* out,
+                   void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
+
+/*
+ * Batched 2D: one FT_A per polygon, all polygons in one persistent launch.
+ *  verts     [n_verts][2] float32; polygon i is verts[poly_off[i] .. poly_off[i+1]-1] (one CCW loop).
+ *  poly_off  [n_polys+1] int64 device array.
+ *  q         float64 Q points.  With q_off == NULL every polygon uses all n_q
+ *            points and out is [n_polys][n_q][2]; otherwise polygon i uses
+ *            q[q_off[i] .. q_off[i+1]-1] and out is [n_q][2] in the same order.
+ *  q_off     [n_polys+1] int64 DEVICE array or NULL.
+ *  poly_off_host, q_off_host: the same offsets in HOST memory (used to build the
+ *            cost-sorted static work list on the host; q_off_host NULL iff q_off NULL).
+ */
+int pft2d_polygons_batched(const float* verts, int64_t n_verts, const int64_t* poly_off,
+                           const int64_t* poly_off_host, int64_t n_polys,
+                           const double* q, const int64_t* q_off, const int64_t* q_off_host,
+                           int64_t n_q, double* out,
+                           void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
+
+/*
+ * 3D: FT_V(Q) of a closed surface of triangles (Sec. 3, Eq. 17 sign-corrected).
+ *  verts  [n_verts][3] float32.
+ *  faces  [n_faces][3] int32, 0-based, each triangle counter-clockwise seen from
+ *         outside (outward normal).  Out-of-range indices set PFT_ERR_INDEX_RANGE
+ *         and the face is skipped.
+ *  q      [n_q][3] float64.      out  [n_q][2] float64 (re, im).
+ */
+int pft3d_mesh(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces,
+               const double* q, int64_t n_q, double* out,
+               void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
+
+/*
+ * Backward passes (adjoints of the calls above; not in the paper).
+ *  grad_out   [n_q][2] float64: (dL/dRe F, dL/dIm F) at each Q.
+ *  grad_verts [n_verts][d] float32: dL/dverts = sum_Q Re(conj(g_Q) dF(Q)/dverts),
+ *             g_Q = grad_out[Q][0] + i grad_out[Q][1].  Overwritten.
+ * Segment/face terms are recomputed, not stored by the forward call.
+ */
+size_t pft2d_backward_workspace_size(int64_t n_verts, int64_t n_loops, int64_t n_q, const pft_options* opts);
+size_t pft3d_backward_workspace_size(int64_t n_verts, int64_t n_faces, int64_t n_q, const pft_options* opts);
+int pft2d_polygons_backward(const float* verts, int64_t n_verts, const int64_t* loop_off, int64_t n_loops,
+                            const double* q, int64_t n_q, const double* grad_out, float* grad_verts,
+                            void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
+int pft3d_mesh_backward(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces,
+                        const double* q, int64_t n_q, const double* grad_out, float* grad_verts,
+                        void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
+
+/*
+ * Device-detected status of the last call that used `ws`: synchronises `stream`,
+ * copies the status word back and returns PFT_OK or the first error found
+ * (PFT_ERR_INDEX_RANGE, PFT_ERR_NONFINITE, PFT_ERR_OFFSETS, PFT_ERR_TIMEOUT), or
+ * PFT_ERR_CUDA if the copy itself failed.
+ */
+int pft_status(const void* ws, void* stream);
+
+/* Static English text for a code (never NULL). */
+const char* pft_status_string(int code);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int pft_version(void);
+
+/* Number of kernel launches the most recent call on this host thread enqueued (for accounting). */
+int pft_last_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFT_H */

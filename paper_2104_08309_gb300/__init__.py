@@ -1,0 +1,273 @@
+"""pft -- direct Fourier transform of polygonal areas and closed triangulated
+surfaces on an NVIDIA GB300 (sm_103a), after Maranville, arXiv 2104.08309.
+
+This module is the thin Python face of ``libpft.so`` (C ABI in include/pft.h).
+PyTorch supplies device memory and streams; every step of the computation runs
+in the library's CUDA kernels.  There is no CPU fallback: calls on CPU tensors,
+or without the built library, raise.
+
+Functions named like the C entry points take CUDA tensors and return float64
+[n_q, 2] (re, im) tensors; ``ft2d`` / ``ft3d`` wrap them as differentiable
+complex128 results (``torch.autograd``) whose backward runs the adjoint kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import synth  # noqa: F401  (seeded inputs; no transform arithmetic)
+from ._capi import (PFT_FP32_COMPENSATED, PFT_FP64, Options, PFTError, check, load,  # noqa: F401
+                    status_string)
+
+__all__ = [
+    "pft2d_polygons", "pft2d_polygons_batched", "pft3d_mesh", "pft2d_polygons_backward",
+    "pft3d_mesh_backward", "pft_status", "ft2d", "ft3d", "make_options", "Options", "PFTError",
+    "launch_count", "version",
+]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def make_options(options=None) -> Options:
+    """Build a pft_options struct from None, an Options, or a dict of its fields.
+
+    ``precision`` may be "fp32" (FP32 with compensated sums, the default) or "fp64".
+    """
+    if isinstance(options, Options):
+        return options
+    o = Options()
+    for k, v in (options or {}).items():
+        if k == "precision":
+            v = {"fp32": PFT_FP32_COMPENSATED, "fp64": PFT_FP64}.get(v, v)
+        if not hasattr(o, k):
+            raise KeyError(f"unknown pft option {k!r}")
+        setattr(o, k, v)
+    return o
+
+
+def _dev(t, dtype, name, cols=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (libpft has no CPU path)")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+        raise ValueError(f"{name} must have shape [n, {cols}], got {tuple(t.shape)}")
+    return t.contiguous()
+
+
+def _stream(stream, device):
+    torch = _torch()
+    if stream is None:
+        return torch.cuda.current_stream(device).cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ws(nbytes, device, ws):
+    torch = _torch()
+    if ws is None:
+        ws = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    elif ws.numel() < nbytes:
+        raise ValueError(f"workspace of {ws.numel()} bytes < {nbytes} required")
+    return ws
+
+
+def pft2d_polygons(verts, q, loop_off=None, *, options=None, out=None, ws=None, stream=None,
+                   check_status=False):
+    """FT_A(Q) of the region bounded by closed loops (Eq. 7).  Returns float64 [n_q, 2]."""
+    torch = _torch()
+    v = _dev(verts, torch.float32, "verts", 2)
+    qq = _dev(q, torch.float64, "q", 2)
+    if loop_off is None:
+        loop_off = torch.tensor([0, v.shape[0]], dtype=torch.int64, device=v.device)
+    off = _dev(loop_off.to(v.device) if loop_off.device != v.device else loop_off, torch.int64, "loop_off")
+    o = make_options(options)
+    lib = load()
+    nv, nl, nq = v.shape[0], off.numel() - 1, qq.shape[0]
+    nb = lib.pft2d_workspace_size(nv, nl, nq, ctypes.byref(o))
+    ws = _ws(nb, v.device, ws)
+    out = torch.empty(nq, 2, dtype=torch.float64, device=v.device) if out is None else out
+    st = _stream(stream, v.device)
+    check(lib.pft2d_polygons(v.data_ptr(), nv, off.data_ptr(), nl, qq.data_ptr(), nq, out.data_ptr(),
+                             ws.data_ptr(), ws.numel(), ctypes.byref(o), st), "pft2d_polygons")
+    if check_status:
+        check(lib.pft_status(ws.data_ptr(), st), "pft2d_polygons (device status)")
+    return out
+
+
+def pft2d_polygons_batched(verts, poly_off, q, q_off=None, *, options=None, out=None, ws=None, stream=None,
+                           check_status=False):
+    """One FT_A per polygon in one persistent launch.
+
+    With q_off None every polygon uses all Q and the result is [n_polys, n_q, 2];
+    otherwise polygon i uses q[q_off[i]:q_off[i+1]] and the result is [n_q, 2].
+    """
+    torch = _torch()
+    v = _dev(verts, torch.float32, "verts", 2)
+    qq = _dev(q, torch.float64, "q", 2)
+    off_h = poly_off.detach().to("cpu", torch.int64).contiguous() if isinstance(poly_off, torch.Tensor) \
+        else torch.as_tensor(poly_off, dtype=torch.int64)
+    off_d = off_h.to(v.device)
+    qo_h = qo_d = None
+    if q_off is not None:
+        qo_h = q_off.detach().to("cpu", torch.int64).contiguous() if isinstance(q_off, torch.Tensor) \
+            else torch.as_tensor(q_off, dtype=torch.int64)
+        qo_d = qo_h.to(v.device)
+    o = make_options(options)
+    lib = load()
+    nv, npoly, nq = v.shape[0], off_h.numel() - 1, qq.shape[0]
+    nb = lib.pft2d_batched_workspace_size(nv, npoly, nq, None if qo_h is None else qo_h.data_ptr(),
+                                          ctypes.byref(o))
+    ws = _ws(nb, v.device, ws)
+    n_out = npoly * nq if q_off is None else nq
+    if out is None:
+        out = torch.empty(n_out, 2, dtype=torch.float64, device=v.device)
+    st = _stream(stream, v.device)
+    check(lib.pft2d_polygons_batched(v.data_ptr(), nv, off_d.data_ptr(), off_h.data_ptr(), npoly, qq.data_ptr(),
+                                     None if qo_d is None else qo_d.data_ptr(),
+                                     None if qo_h is None else qo_h.data_ptr(), nq, out.data_ptr(),
+                                     ws.data_ptr(), ws.numel(), ctypes.byref(o), st), "pft2d_polygons_batched")
+    if check_status:
+        check(lib.pft_status(ws.data_ptr(), st), "pft2d_polygons_batched (device status)")
+    return out.view(npoly, nq, 2) if q_off is None else out
+
+
+def pft3d_mesh(verts, faces, q, *, options=None, out=None, ws=None, stream=None, check_status=False):
+    """FT_V(Q) of a closed outward triangle surface (Eq. 17, sign-corrected).  Returns float64 [n_q, 2]."""
+    torch = _torch()
+    v = _dev(verts, torch.float32, "verts", 3)
+    f = _dev(faces, torch.int32, "faces", 3)
+    qq = _dev(q, torch.float64, "q", 3)
+    o = make_options(options)
+    lib = load()
+    nv, nf, nq = v.shape[0], f.shape[0], qq.shape[0]
+    nb = lib.pft3d_workspace_size(nv, nf, nq, ctypes.byref(o))
+    ws = _ws(nb, v.device, ws)
+    out = torch.empty(nq, 2, dtype=torch.float64, device=v.device) if out is None else out
+    st = _stream(stream, v.device)
+    check(lib.pft3d_mesh(v.data_ptr(), nv, f.data_ptr(), nf, qq.data_ptr(), nq, out.data_ptr(), ws.data_ptr(),
+                         ws.numel(), ctypes.byref(o), st), "pft3d_mesh")
+    if check_status:
+        check(lib.pft_status(ws.data_ptr(), st), "pft3d_mesh (device status)")
+    return out
+
+
+def pft2d_polygons_backward(verts, q, grad_out, loop_off=None, *, options=None, out=None, ws=None,
+                            stream=None, check_status=False):
+    """dL/dverts [n_v, 2] float32 from grad_out [n_q, 2] = (dL/dRe F, dL/dIm F)."""
+    torch = _torch()
+    v = _dev(verts, torch.float32, "verts", 2)
+    qq = _dev(q, torch.float64, "q", 2)
+    g = _dev(grad_out, torch.float64, "grad_out", 2)
+    if loop_off is None:
+        loop_off = torch.tensor([0, v.shape[0]], dtype=torch.int64, device=v.device)
+    off = _dev(loop_off.to(v.device), torch.int64, "loop_off")
+    o = make_options(options)
+    lib = load()
+    nv, nl, nq = v.shape[0], off.numel() - 1, qq.shape[0]
+    nb = lib.pft2d_backward_workspace_size(nv, nl, nq, ctypes.byref(o))
+    ws = _ws(nb, v.device, ws)
+    out = torch.empty(nv, 2, dtype=torch.float32, device=v.device) if out is None else out
+    st = _stream(stream, v.device)
+    check(lib.pft2d_polygons_backward(v.data_ptr(), nv, off.data_ptr(), nl, qq.data_ptr(), nq, g.data_ptr(),
+                                      out.data_ptr(), ws.data_ptr(), ws.numel(), ctypes.byref(o), st),
+          "pft2d_polygons_backward")
+    if check_status:
+        check(lib.pft_status(ws.data_ptr(), st), "pft2d_polygons_backward (device status)")
+    return out
+
+
+def pft3d_mesh_backward(verts, faces, q, grad_out, *, options=None, out=None, ws=None, stream=None,
+                        check_status=False):
+    """dL/dverts [n_v, 3] float32 from grad_out [n_q, 2] = (dL/dRe F, dL/dIm F)."""
+    torch = _torch()
+    v = _dev(verts, torch.float32, "verts", 3)
+    f = _dev(faces, torch.int32, "faces", 3)
+    qq = _dev(q, torch.float64, "q", 3)
+    g = _dev(grad_out, torch.float64, "grad_out", 2)
+    o = make_options(options)
+    lib = load()
+    nv, nf, nq = v.shape[0], f.shape[0], qq.shape[0]
+    nb = lib.pft3d_backward_workspace_size(nv, nf, nq, ctypes.byref(o))
+    ws = _ws(nb, v.device, ws)
+    out = torch.empty(nv, 3, dtype=torch.float32, device=v.device) if out is None else out
+    st = _stream(stream, v.device)
+    check(lib.pft3d_mesh_backward(v.data_ptr(), nv, f.data_ptr(), nf, qq.data_ptr(), nq, g.data_ptr(),
+                                  out.data_ptr(), ws.data_ptr(), ws.numel(), ctypes.byref(o), st),
+          "pft3d_mesh_backward")
+    if check_status:
+        check(lib.pft_status(ws.data_ptr(), st), "pft3d_mesh_backward (device status)")
+    return out
+
+
+def pft_status(ws, stream=None) -> int:
+    """Device-detected status of the last call on this workspace (synchronises the stream)."""
+    return int(load().pft_status(ws.data_ptr(), _stream(stream, ws.device)))
+
+
+def launch_count() -> int:
+    """Kernel launches enqueued by the most recent library call on this thread."""
+    return int(load().pft_last_launch_count())
+
+
+def version() -> int:
+    return int(load().pft_version())
+
+
+# ----------------------------------------------------------------------------
+# Differentiable wrappers.
+# ----------------------------------------------------------------------------
+
+def _autograd():
+    torch = _torch()
+
+    class _FT2D(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, verts, q, loop_off, options):
+            ctx.save_for_backward(verts, q, loop_off)
+            ctx.options = options
+            return pft2d_polygons(verts.detach(), q, loop_off, options=options)
+
+        @staticmethod
+        def backward(ctx, g):
+            verts, q, loop_off = ctx.saved_tensors
+            gv = pft2d_polygons_backward(verts.detach(), q, g.contiguous(), loop_off, options=ctx.options)
+            return gv, None, None, None
+
+    class _FT3D(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, verts, faces, q, options):
+            ctx.save_for_backward(verts, faces, q)
+            ctx.options = options
+            return pft3d_mesh(verts.detach(), faces, q, options=options)
+
+        @staticmethod
+        def backward(ctx, g):
+            verts, faces, q = ctx.saved_tensors
+            gv = pft3d_mesh_backward(verts.detach(), faces, q, g.contiguous(), options=ctx.options)
+            return gv, None, None, None
+
+    return _FT2D, _FT3D
+
+
+_FNS = None
+
+
+def ft2d(verts, q, loop_off=None, options=None):
+    """Differentiable FT_A(Q) as complex128 [n_q]; grad w.r.t. verts via the adjoint kernel."""
+    global _FNS
+    torch = _torch()
+    _FNS = _FNS or _autograd()
+    if loop_off is None:
+        loop_off = torch.tensor([0, verts.shape[0]], dtype=torch.int64, device=verts.device)
+    return torch.view_as_complex(_FNS[0].apply(verts, q, loop_off, options))
+
+
+def ft3d(verts, faces, q, options=None):
+    """Differentiable FT_V(Q) as complex128 [n_q]; grad w.r.t. verts via the adjoint kernel."""
+    global _FNS
+    torch = _torch()
+    _FNS = _FNS or _autograd()
+    return torch.view_as_complex(_FNS[1].apply(verts, faces, q, options))

@@ -1,0 +1,257 @@
+// pft_api.cu -- the C ABI (include/pft.h): argument checks, workspace layout,
+// launch planning and the kernel sequence of each call.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "pft_kernels.cuh"
+
+namespace pft {
+namespace {
+
+thread_local int g_last_launches = 0;
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Opts {
+  bool fp64;
+  int r, nt, k_splits;
+  float tau;
+  cudaEvent_t ev_start, ev_stop;
+};
+
+int resolve(const pft_options* o, int dim, Opts& out) {
+  pft_options z;
+  std::memset(&z, 0, sizeof(z));
+  const pft_options& p = o ? *o : z;
+  if (p.precision != PFT_FP32_COMPENSATED && p.precision != PFT_FP64) return PFT_ERR_INVALID_ARG;
+  out.fp64 = (p.precision == PFT_FP64);
+  out.r = p.q_per_thread ? p.q_per_thread : (out.fp64 ? 1 : 4);
+  out.nt = p.block_threads ? p.block_threads : (out.fp64 ? 128 : 256);
+  const bool r_ok = out.fp64 ? (out.r == 1 || out.r == 2) : (out.r == 1 || out.r == 2 || out.r == 4 || out.r == 8);
+  if (!r_ok || (out.nt != 128 && out.nt != 256)) return PFT_ERR_UNSUPPORTED;
+  if (p.k_splits < 0) return PFT_ERR_INVALID_ARG;
+  out.k_splits = p.k_splits;
+  if (p.tile_items != 0) return PFT_ERR_UNSUPPORTED;
+  float tau = p.face_series_tau;
+  if (tau == 0.f) tau = 1.0f;
+  if (!(tau > 0.f && tau <= 1.0f)) return PFT_ERR_INVALID_ARG;
+  out.tau = tau;
+  out.ev_start = static_cast<cudaEvent_t>(p.main_start_event);
+  out.ev_stop = static_cast<cudaEvent_t>(p.main_stop_event);
+  (void)dim;
+  return PFT_OK;
+}
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return sms > 0 ? sms : 1;
+}
+
+// Split-K choice: the smallest number of chunks that fills the GPU in whole
+// waves (>= 90 % of the last wave busy), each chunk at least two tiles long.
+FwdLaunch plan_fwd(int dim, const Opts& o, int64_t n_items, int64_t n_q) {
+  FwdLaunch L{};
+  L.r = o.r;
+  L.nt = o.nt;
+  const int tile = fwd_tile(dim, o.fp64);
+  const int64_t q_per_block = (int64_t)o.r * o.nt;
+  L.q_tiles = std::max<int64_t>(1, (n_q + q_per_block - 1) / q_per_block);
+  const int64_t item_tiles = std::max<int64_t>(1, (n_items + tile - 1) / tile);
+  int k = o.k_splits;
+  if (k == 0) {
+    const int64_t slots = (int64_t)device_sms() * fwd_blocks_per_sm(dim, o.fp64, o.r, o.nt);
+    const int kmax = (int)std::max<int64_t>(1, std::min<int64_t>(64, item_tiles / 2));
+    double best_eff = -1.0;
+    int best_k = 1;
+    k = 0;
+    for (int c = 1; c <= kmax; ++c) {
+      const double waves = (double)(L.q_tiles * c) / (double)slots;
+      const double eff = waves / std::ceil(waves);
+      if (L.q_tiles * c >= slots && eff >= 0.9) { k = c; break; }
+      if (eff > best_eff + 1e-9) { best_eff = eff; best_k = c; }
+    }
+    if (k == 0) k = best_k;
+  }
+  k = (int)std::min<int64_t>(k, item_tiles);
+  const int64_t tiles_per = (item_tiles + k - 1) / k;
+  L.per_split = tiles_per * tile;
+  L.k_splits = (int)((item_tiles + tiles_per - 1) / tiles_per);
+  return L;
+}
+
+struct FwdLayout {
+  size_t mparts, items, partial, small, total;
+  int nblk;
+  FwdLaunch L;
+};
+
+FwdLayout layout_fwd(int dim, const Opts& o, int64_t n_items, int64_t n_prep, int64_t n_q) {
+  FwdLayout y{};
+  y.L = plan_fwd(dim, o, n_items, n_q);
+  y.nblk = std::max(1, prep_blocks(n_prep));
+  const size_t item_bytes = dim == 2 ? (o.fp64 ? sizeof(Seg64) : sizeof(Seg32)) : (o.fp64 ? sizeof(Face64) : sizeof(Face32));
+  size_t off = align_up(sizeof(WsHeader));
+  y.mparts = off;  off = align_up(off + sizeof(double) * (size_t)y.nblk);
+  y.items = off;   off = align_up(off + item_bytes * (size_t)std::max<int64_t>(n_items, 1));
+  y.partial = off; off = align_up(off + sizeof(double2) * (size_t)y.L.k_splits * (size_t)std::max<int64_t>(n_q, 1));
+  y.small = off;   off = align_up(off + sizeof(int32_t) * (size_t)std::max<int64_t>(n_q, 1));
+  y.total = off;
+  return y;
+}
+
+template <typename T>
+T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(ws) + off); }
+
+bool bad_ws(const void* ws, size_t bytes, size_t need) {
+  return ws == nullptr || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0 || bytes < need;
+}
+
+// Records an optional caller event on the stream (timing of the main kernel alone).
+inline cudaError_t mark(cudaEvent_t ev, cudaStream_t st) { return ev ? cudaEventRecord(ev, st) : cudaSuccess; }
+
+#define PFT_LAUNCH(expr)                        \
+  do {                                          \
+    if ((expr) != cudaSuccess) return PFT_ERR_CUDA; \
+    ++g_last_launches;                          \
+  } while (0)
+
+}  // namespace
+}  // namespace pft
+
+using namespace pft;
+
+extern "C" {
+
+size_t pft2d_workspace_size(int64_t n_verts, int64_t n_loops, int64_t n_q, const pft_options* opts) {
+  Opts o;
+  if (n_verts < 0 || n_loops < 0 || n_q < 0 || resolve(opts, 2, o) != PFT_OK) return 0;
+  return layout_fwd(2, o, n_verts, std::max<int64_t>(n_verts, n_loops + 1), n_q).total;
+}
+
+size_t pft3d_workspace_size(int64_t n_verts, int64_t n_faces, int64_t n_q, const pft_options* opts) {
+  Opts o;
+  if (n_verts < 0 || n_faces < 0 || n_q < 0 || resolve(opts, 3, o) != PFT_OK) return 0;
+  return layout_fwd(3, o, n_faces, n_faces, n_q).total;
+}
+
+int pft2d_polygons(const float* verts, int64_t n_verts, const int64_t* loop_off, int64_t n_loops, const double* q,
+                   int64_t n_q, double* out, void* ws, size_t ws_bytes, const pft_options* opts, void* stream) {
+  g_last_launches = 0;
+  Opts o;
+  if (int e = resolve(opts, 2, o)) return e;
+  if (n_verts < 0 || n_loops < 0 || n_q < 0) return PFT_ERR_INVALID_ARG;
+  if (n_q > 0 && (q == nullptr || out == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (n_verts > 0 && (verts == nullptr || loop_off == nullptr || n_loops == 0)) return PFT_ERR_INVALID_ARG;
+  if (n_q > INT32_MAX) return PFT_ERR_UNSUPPORTED;
+  const FwdLayout y = layout_fwd(2, o, n_verts, std::max<int64_t>(n_verts, n_loops + 1), n_q);
+  if (bad_ws(ws, ws_bytes, y.total)) return PFT_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader* h = at<WsHeader>(ws, 0);
+  PFT_LAUNCH(launch_init_header(h, st));
+  if (n_q == 0) return PFT_OK;
+  if (n_verts == 0) {
+    if (cudaMemsetAsync(out, 0, sizeof(double) * 2 * (size_t)n_q, st) != cudaSuccess) return PFT_ERR_CUDA;
+    return PFT_OK;
+  }
+  double* mp = at<double>(ws, y.mparts);
+  PFT_LAUNCH(launch_bbox(verts, n_verts, 2, h, st));
+  PFT_LAUNCH(launch_prep2d(verts, n_verts, loop_off, n_loops, h, at<void>(ws, y.items), o.fp64, mp, y.nblk, st));
+  if (mark(o.ev_start, st) != cudaSuccess) return PFT_ERR_CUDA;
+  PFT_LAUNCH(launch_fwd(2, o.fp64, y.L, at<void>(ws, y.items), n_verts, q, n_q, o.tau, at<double2>(ws, y.partial),
+                        &h->status, st));
+  if (mark(o.ev_stop, st) != cudaSuccess) return PFT_ERR_CUDA;
+  PFT_LAUNCH(launch_finalize(2, q, n_q, at<double2>(ws, y.partial), y.L.k_splits, o.fp64, h, mp, y.nblk,
+                             at<int32_t>(ws, y.small), out, st));
+  PFT_LAUNCH(launch_smallq2d(verts, n_verts, loop_off, n_loops, q, o.fp64, h, at<int32_t>(ws, y.small), out, st));
+  return PFT_OK;
+}
+
+int pft3d_mesh(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces, const double* q,
+               int64_t n_q, double* out, void* ws, size_t ws_bytes, const pft_options* opts, void* stream) {
+  g_last_launches = 0;
+  Opts o;
+  if (int e = resolve(opts, 3, o)) return e;
+  if (n_verts < 0 || n_faces < 0 || n_q < 0) return PFT_ERR_INVALID_ARG;
+  if (n_q > 0 && (q == nullptr || out == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (n_faces > 0 && (faces == nullptr || verts == nullptr || n_verts == 0)) return PFT_ERR_INVALID_ARG;
+  if (n_q > INT32_MAX || n_verts > INT32_MAX) return PFT_ERR_UNSUPPORTED;
+  const FwdLayout y = layout_fwd(3, o, n_faces, n_faces, n_q);
+  if (bad_ws(ws, ws_bytes, y.total)) return PFT_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader* h = at<WsHeader>(ws, 0);
+  PFT_LAUNCH(launch_init_header(h, st));
+  if (n_q == 0) return PFT_OK;
+  if (n_faces == 0) {
+    if (cudaMemsetAsync(out, 0, sizeof(double) * 2 * (size_t)n_q, st) != cudaSuccess) return PFT_ERR_CUDA;
+    return PFT_OK;
+  }
+  double* mp = at<double>(ws, y.mparts);
+  PFT_LAUNCH(launch_bbox(verts, n_verts, 3, h, st));
+  PFT_LAUNCH(launch_prep3d(verts, n_verts, faces, n_faces, h, at<void>(ws, y.items), o.fp64, mp, y.nblk, st));
+  if (mark(o.ev_start, st) != cudaSuccess) return PFT_ERR_CUDA;
+  PFT_LAUNCH(launch_fwd(3, o.fp64, y.L, at<void>(ws, y.items), n_faces, q, n_q, o.tau, at<double2>(ws, y.partial),
+                        &h->status, st));
+  if (mark(o.ev_stop, st) != cudaSuccess) return PFT_ERR_CUDA;
+  PFT_LAUNCH(launch_finalize(3, q, n_q, at<double2>(ws, y.partial), y.L.k_splits, o.fp64, h, mp, y.nblk,
+                             at<int32_t>(ws, y.small), out, st));
+  PFT_LAUNCH(launch_smallq3d(verts, n_verts, faces, n_faces, q, o.fp64, h, at<int32_t>(ws, y.small), out, st));
+  return PFT_OK;
+}
+
+size_t pft2d_batched_workspace_size(int64_t, int64_t, int64_t, const int64_t*, const pft_options*) { return 0; }
+int pft2d_polygons_batched(const float*, int64_t, const int64_t*, const int64_t*, int64_t, const double*,
+                           const int64_t*, const int64_t*, int64_t, double*, void*, size_t, const pft_options*,
+                           void*) {
+  g_last_launches = 0;
+  return PFT_ERR_UNSUPPORTED;
+}
+size_t pft2d_backward_workspace_size(int64_t, int64_t, int64_t, const pft_options*) { return 0; }
+size_t pft3d_backward_workspace_size(int64_t, int64_t, int64_t, const pft_options*) { return 0; }
+int pft2d_polygons_backward(const float*, int64_t, const int64_t*, int64_t, const double*, int64_t, const double*,
+                            float*, void*, size_t, const pft_options*, void*) {
+  g_last_launches = 0;
+  return PFT_ERR_UNSUPPORTED;
+}
+int pft3d_mesh_backward(const float*, int64_t, const int32_t*, int64_t, const double*, int64_t, const double*,
+                        float*, void*, size_t, const pft_options*, void*) {
+  g_last_launches = 0;
+  return PFT_ERR_UNSUPPORTED;
+}
+
+int pft_status(const void* ws, void* stream) {
+  if (ws == nullptr) return PFT_ERR_INVALID_ARG;
+  uint32_t word = 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&word, ws, sizeof(word), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PFT_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PFT_ERR_CUDA;
+  if (word & ST_INDEX) return PFT_ERR_INDEX_RANGE;
+  if (word & ST_NONFINITE) return PFT_ERR_NONFINITE;
+  if (word & ST_OFFSETS) return PFT_ERR_OFFSETS;
+  if (word & ST_TIMEOUT) return PFT_ERR_TIMEOUT;
+  return PFT_OK;
+}
+
+const char* pft_status_string(int code) {
+  switch (code) {
+    case PFT_OK: return "ok";
+    case PFT_ERR_INVALID_ARG: return "invalid argument";
+    case PFT_ERR_INDEX_RANGE: return "face index out of range";
+    case PFT_ERR_NONFINITE: return "non-finite vertex coordinate";
+    case PFT_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case PFT_ERR_CUDA: return "CUDA launch or copy failed";
+    case PFT_ERR_TIMEOUT: return "bounded wait on a bulk copy timed out";
+    case PFT_ERR_UNSUPPORTED: return "unsupported option combination";
+    case PFT_ERR_OFFSETS: return "malformed CSR offsets";
+    default: return "unknown status code";
+  }
+}
+
+int pft_version(void) { return 10000 * 0 + 100 * 1 + 0; }
+
+int pft_last_launch_count(void) { return g_last_launches; }
+
+}  // extern "C"

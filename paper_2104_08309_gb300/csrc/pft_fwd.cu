@@ -1,0 +1,444 @@
+// pft_fwd.cu -- the hot loop: every (Q, segment) or (Q, face) pair of the
+// divergence-theorem sum.
+//
+// Mapping: each thread owns R Q points in registers; a block covers NT*R Q
+// points and one chunk of the segments/faces (blockIdx.y, split-K).  Segment or
+// face records stream through shared memory in tiles moved by bulk copies
+// (cp.async.bulk, TMA) into a STAGES-deep ring guarded by mbarriers; one thread
+// issues the copies, every thread reads each record as a broadcast.  Sums are
+// per thread and in a fixed order: FP32 within a tile, error-free (TwoSum)
+// compensation across tiles; the per-chunk partials are added in FP64 by the
+// finalize kernel.  No atomics on data, so results are deterministic.
+#include "pft_kernels.cuh"
+
+namespace pft {
+namespace {
+
+constexpr int kStages = 4;
+
+// ---------------------------------------------------------------------------
+// Per-pair arithmetic.
+// ---------------------------------------------------------------------------
+
+// 2D, Eq. 7 (Sec. 2): the segment p0 -> p1 contributes
+//   -i (Qx Dy - Qy Dx) sinc(Q.D/2) exp(iQ.m)           (times 1/|Q|^2, applied later)
+// Records hold m / (2 pi) and D/2, so w below is half the cross product; the
+// factor 2 and 1/|Q|^2 are applied in FP64 by the finalize kernel.
+__device__ __forceinline__ void seg_pair_f32(float qx, float qy, const float4 s, float& re, float& im) {
+  const float pt = fmaf(qx, s.x, qy * s.y);    // Q.m in turns
+  const float u = fmaf(qx, s.z, qy * s.w);     // Q.D / 2
+  const float w = fmaf(qx, s.w, -qy * s.z);    // (Qx Dy - Qy Dx) / 2
+  float sn, cs;
+  sincos_turns(pt, &sn, &cs);
+  const float ws = w * sinc_f32(u);
+  re = ws * sn;    // -i * ws * (cos + i sin) = ws sin - i ws cos
+  im = -ws * cs;
+}
+
+__device__ __forceinline__ double sinc_f64(double u) {
+  const double u2 = u * u;
+  if (u2 < 1e-2) {   // Taylor through u^10: truncation < 1e-18 at |u| = 0.1
+    double p = fma(u2, -1.0 / 39916800.0, 1.0 / 362880.0);
+    p = fma(u2, p, -1.0 / 5040.0);
+    p = fma(u2, p, 1.0 / 120.0);
+    p = fma(u2, p, -1.0 / 6.0);
+    return fma(u2, p, 1.0);
+  }
+  return sin(u) / u;
+}
+
+__device__ __forceinline__ void seg_pair_f64(double qx, double qy, const Seg64& s, double& re, double& im) {
+  const double ph = fma(qx, s.mx, qy * s.my);
+  const double u = fma(qx, s.hx, qy * s.hy);
+  const double w = fma(qx, s.hy, -qy * s.hx);
+  double sn, cs;
+  sincos(ph, &sn, &cs);
+  const double ws = w * sinc_f64(u);
+  re = ws * sn;
+  im = -ws * cs;
+}
+
+// 3D, Eq. 17 with the sign fixed (Sec. 3).  With X = N x Q, s = Q.N and the
+// corner phases a_k = Q.(p_k - centroid) (a_0 + a_1 + a_2 = 0), a face gives
+//   |Q|^2 I_m = -s exp(i mu) Z,     mu = Q.centroid,
+//   Z = (1/|X|^2) sum_l w_l sinc(u_l) exp(i psi_l)         (edge sum)
+// with w_l = Q.(d_l x N) = b_{l+1} - b_l, b_k = (p_k - centroid).X,
+// u_l = (a_{l+1} - a_l)/2 and psi_l = (a_l + a_{l+1})/2 = -a_{l+2}/2.
+// The edge sum cancels to O(spread) of its terms when the phase spread of the
+// face is small (it is 0/0 for Q parallel to N); there the same face integral
+// (Eq. 14) is taken from its series, Z = i G,
+//   G = sum_k i^k h_k(a) / (k+2)!,   h_k = P h_{k-2} + T h_{k-3},
+// P = a0^2 + a0 a1 + a1^2 (= h_2), T = a0 a1 a2 (= h_3), kept through k = 8.
+// The series is used when P < tau^2/4, which implies max_l |Q.d_l| < tau <= 1;
+// there the omitted terms are below 1e-9 relative.
+__device__ __forceinline__ void face_pair_f32(float qx, float qy, float qz, const float4 A, const float4 B,
+                                              const float4 C, float p_tau, float& re, float& im) {
+  // A = (g/2pi).xyz, q0.x   B = q0.yz, q1.xy   C = q1.z, N.xyz
+  const float mut = fmaf(qx, A.x, fmaf(qy, A.y, qz * A.z));   // mu in turns
+  const float a0 = fmaf(qx, A.w, fmaf(qy, B.x, qz * B.y));
+  const float a1 = fmaf(qx, B.z, fmaf(qy, B.w, qz * C.x));
+  const float s = fmaf(qx, C.y, fmaf(qy, C.z, qz * C.w));
+  const float a01 = a0 + a1;
+  const float a2 = -a01;
+  const float P = fmaf(a0, a01, a1 * a1);
+  float zr, zi;
+  if (P < p_tau) {
+    const float T = a0 * a1 * a2;
+    const float T2 = T * T;
+    float gre = fmaf(P, 2.75573192e-7f, -2.48015873e-5f);   // 1/10!, -1/8!
+    gre = fmaf(P, gre, 1.38888889e-3f);                      // 1/6!
+    gre = fmaf(P, gre, -4.16666667e-2f);                     // -1/4!
+    gre = fmaf(P, gre, 0.5f);                                // 1/2!
+    gre = fmaf(T2, fmaf(P, 8.26719577e-7f, -2.48015873e-5f), gre);   // T^2 (3P/10! - 1/8!)
+    const float gim = T * fmaf(P, fmaf(P, -8.26719577e-6f, 3.96825397e-4f), -8.33333333e-3f);  // -T/5! + PT/2520 - P^2 T/120960
+    zr = -gim;
+    zi = gre;
+  } else {
+    const float nx = C.y, ny = C.z, nz = C.w;
+    const float Xx = fmaf(ny, qz, -nz * qy), Xy = fmaf(nz, qx, -nx * qz), Xz = fmaf(nx, qy, -ny * qx);
+    const float x2 = fmaf(Xx, Xx, fmaf(Xy, Xy, Xz * Xz));
+    const float b0 = fmaf(A.w, Xx, fmaf(B.x, Xy, B.y * Xz));
+    const float b1 = fmaf(B.z, Xx, fmaf(B.w, Xy, C.x * Xz));
+    const float b2 = -(b0 + b1);
+    const float w[3] = {b1 - b0, b2 - b1, b0 - b2};
+    const float psi[3] = {-0.5f * a2, -0.5f * a0, -0.5f * a1};
+    const float u[3] = {0.5f * (a1 - a0), 0.5f * (a2 - a1), 0.5f * (a0 - a2)};
+    float sr = 0.f, si = 0.f;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      float sp, cp;
+      sincos_turns(psi[l] * kInvTwoPi, &sp, &cp);
+      const float ws = w[l] * sinc_f32(u[l]);
+      sr = fmaf(ws, cp, sr);
+      si = fmaf(ws, sp, si);
+    }
+    const float inv = (x2 > 0.f) ? __frcp_rn(x2) : 0.f;   // x2 = 0 only for a degenerate face (s = 0 too)
+    zr = sr * inv;
+    zi = si * inv;
+  }
+  float sm, cm;
+  sincos_turns(mut, &sm, &cm);
+  re = -s * fmaf(cm, zr, -sm * zi);
+  im = -s * fmaf(cm, zi, sm * zr);
+}
+
+// Same face term in FP64 (comparison path): library sincos, series through k = 16.
+__device__ __forceinline__ void face_pair_f64(double qx, double qy, double qz, const Face64& f, double p_tau,
+                                              double& re, double& im) {
+  const double mu = fma(qx, f.gx, fma(qy, f.gy, qz * f.gz));
+  const double a0 = fma(qx, f.q0x, fma(qy, f.q0y, qz * f.q0z));
+  const double a1 = fma(qx, f.q1x, fma(qy, f.q1y, qz * f.q1z));
+  const double s = fma(qx, f.nx, fma(qy, f.ny, qz * f.nz));
+  const double a2 = -(a0 + a1);
+  const double P = fma(a0, a0 + a1, a1 * a1);
+  double zr, zi;
+  if (P < p_tau) {
+    const double T = a0 * a1 * a2;
+    constexpr int K = 16;
+    double h[K + 1];
+    h[0] = 1.0; h[1] = 0.0; h[2] = P;
+#pragma unroll
+    for (int k = 3; k <= K; ++k) h[k] = fma(P, h[k - 2], T * h[k - 3]);
+    double gre = 0.0, gim = 0.0, inv = 0.5;   // 1/(k+2)!
+#pragma unroll
+    for (int k = 0; k <= K; ++k) {
+      const double t = h[k] * inv;
+      switch (k & 3) { case 0: gre += t; break; case 1: gim += t; break; case 2: gre -= t; break; default: gim -= t; }
+      inv /= (double)(k + 3);
+    }
+    zr = -gim;
+    zi = gre;
+  } else {
+    const double Xx = fma(f.ny, qz, -f.nz * qy), Xy = fma(f.nz, qx, -f.nx * qz), Xz = fma(f.nx, qy, -f.ny * qx);
+    const double x2 = fma(Xx, Xx, fma(Xy, Xy, Xz * Xz));
+    const double b0 = fma(f.q0x, Xx, fma(f.q0y, Xy, f.q0z * Xz));
+    const double b1 = fma(f.q1x, Xx, fma(f.q1y, Xy, f.q1z * Xz));
+    const double b2 = -(b0 + b1);
+    const double w[3] = {b1 - b0, b2 - b1, b0 - b2};
+    const double psi[3] = {-0.5 * a2, -0.5 * a0, -0.5 * a1};
+    const double u[3] = {0.5 * (a1 - a0), 0.5 * (a2 - a1), 0.5 * (a0 - a2)};
+    double sr = 0.0, si = 0.0;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      double sp, cp;
+      sincos(psi[l], &sp, &cp);
+      const double ws = w[l] * sinc_f64(u[l]);
+      sr = fma(ws, cp, sr);
+      si = fma(ws, sp, si);
+    }
+    const double inv = (x2 > 0.0) ? 1.0 / x2 : 0.0;
+    zr = sr * inv;
+    zi = si * inv;
+  }
+  double sm, cm;
+  sincos(mu, &sm, &cm);
+  re = -s * fma(cm, zr, -sm * zi);
+  im = -s * fma(cm, zi, sm * zr);
+}
+
+// ---------------------------------------------------------------------------
+// Policies: record type, Q registers, accumulators and the per-tile loop.
+// ---------------------------------------------------------------------------
+
+template <int R>
+struct Acc32 {
+  CAcc re[R], im[R];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int r = 0; r < R; ++r) { re[r].init(); im[r].init(); }
+  }
+  __device__ __forceinline__ double2 get(int r) const {
+    return make_double2((double)re[r].hi + (double)re[r].lo, (double)im[r].hi + (double)im[r].lo);
+  }
+};
+
+template <int R>
+struct Acc64 {
+  double re[R], im[R];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int r = 0; r < R; ++r) { re[r] = 0.0; im[r] = 0.0; }
+  }
+  __device__ __forceinline__ double2 get(int r) const { return make_double2(re[r], im[r]); }
+};
+
+struct Pol2F32 {
+  using Item = Seg32;
+  static constexpr int kDim = 2, kTile = 128;
+  template <int R> using Acc = Acc32<R>;
+  using QT = float;
+  template <int R>
+  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc, float) {
+    float tre[R], tim[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { tre[r] = 0.f; tim[r] = 0.f; }
+#pragma unroll 2
+    for (int i = 0; i < cnt; ++i) {
+      const float4 s = reinterpret_cast<const float4*>(t)[i];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float re, im;
+        seg_pair_f32(q[r][0], q[r][1], s, re, im);
+        tre[r] += re;
+        tim[r] += im;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) { acc.re[r].add(tre[r]); acc.im[r].add(tim[r]); }
+  }
+};
+
+struct Pol2F64 {
+  using Item = Seg64;
+  static constexpr int kDim = 2, kTile = 64;
+  template <int R> using Acc = Acc64<R>;
+  using QT = double;
+  template <int R>
+  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc, float) {
+    for (int i = 0; i < cnt; ++i) {
+      const Seg64 s = t[i];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        double re, im;
+        seg_pair_f64(q[r][0], q[r][1], s, re, im);
+        acc.re[r] += re;
+        acc.im[r] += im;
+      }
+    }
+  }
+};
+
+struct Pol3F32 {
+  using Item = Face32;
+  static constexpr int kDim = 3, kTile = 64;
+  template <int R> using Acc = Acc32<R>;
+  using QT = float;
+  template <int R>
+  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc,
+                                              float p_tau) {
+    float tre[R], tim[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { tre[r] = 0.f; tim[r] = 0.f; }
+#pragma unroll 1
+    for (int i = 0; i < cnt; ++i) {
+      const float4* p = reinterpret_cast<const float4*>(t + i);
+      const float4 A = p[0], B = p[1], C = p[2];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float re, im;
+        face_pair_f32(q[r][0], q[r][1], q[r][2], A, B, C, p_tau, re, im);
+        tre[r] += re;
+        tim[r] += im;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) { acc.re[r].add(tre[r]); acc.im[r].add(tim[r]); }
+  }
+};
+
+struct Pol3F64 {
+  using Item = Face64;
+  static constexpr int kDim = 3, kTile = 32;
+  template <int R> using Acc = Acc64<R>;
+  using QT = double;
+  template <int R>
+  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc,
+                                              float p_tau) {
+    for (int i = 0; i < cnt; ++i) {
+      const Face64 f = t[i];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        double re, im;
+        face_pair_f64(q[r][0], q[r][1], q[r][2], f, (double)p_tau, re, im);
+        acc.re[r] += re;
+        acc.im[r] += im;
+      }
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// The main kernel: bulk-copy ring of record tiles, R Q points per thread.
+// ---------------------------------------------------------------------------
+template <class Pol, int R, int NT>
+__global__ void __launch_bounds__(NT) k_fwd(const typename Pol::Item* __restrict__ items, int64_t n_items,
+                                            int64_t per_split, const double* __restrict__ q, int64_t n_q,
+                                            float p_tau, double2* __restrict__ partial, uint32_t* status) {
+  using Item = typename Pol::Item;
+  using QT = typename Pol::QT;
+  constexpr int TILE = Pol::kTile;
+  constexpr int D = Pol::kDim;
+  __shared__ __align__(128) Item ring[kStages * TILE];
+  __shared__ __align__(8) uint64_t bar[kStages];
+
+  const int64_t i0 = (int64_t)blockIdx.y * per_split;
+  const int64_t n = max((int64_t)0, min(per_split, n_items - i0));
+  const int ntiles = (int)((n + TILE - 1) / TILE);
+  const Item* src = items + i0;
+
+  QT qr[R][3];
+  const int64_t qbase = (int64_t)blockIdx.x * (NT * R) + threadIdx.x;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t iq = qbase + (int64_t)r * NT;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) qr[r][d] = (QT)0;
+    if (iq < n_q) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) qr[r][d] = (QT)q[iq * D + d];
+    }
+  }
+  typename Pol::template Acc<R> acc;
+  acc.init();
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int t) {
+    const int s = t % kStages;
+    const int64_t cnt = min((int64_t)TILE, n - (int64_t)t * TILE);
+    const uint32_t bytes = (uint32_t)(cnt * (int64_t)sizeof(Item));
+    mbar_arrive_expect_tx(&bar[s], bytes);
+    bulk_g2s(ring + s * TILE, src + (int64_t)t * TILE, bytes, &bar[s]);
+  };
+  if (threadIdx.x == 0)
+    for (int t = 0; t < min(kStages, ntiles); ++t) issue(t);
+
+  for (int t = 0; t < ntiles; ++t) {
+    const int s = t % kStages;
+    const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((t / kStages) & 1));
+    if (__syncthreads_or(!ok)) {
+      // A copy never landed: report it, let the copies still in flight finish
+      // (bounded), and leave without touching the ring again.
+      if (threadIdx.x == 0) {
+        set_status(status, ST_TIMEOUT);
+        for (int u = t + 1; u < min(t + kStages, ntiles); ++u)
+          (void)mbar_wait_bounded(&bar[u % kStages], (uint32_t)((u / kStages) & 1));
+      }
+      return;
+    }
+    const int cnt = (int)min((int64_t)TILE, n - (int64_t)t * TILE);
+    Pol::template tile<R>(ring + s * TILE, cnt, qr, acc, p_tau);
+    __syncthreads();   // every thread is done with slot s
+    if (threadIdx.x == 0 && t + kStages < ntiles) {
+      fence_proxy_async_smem();
+      issue(t + kStages);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t iq = qbase + (int64_t)r * NT;
+    if (iq < n_q) partial[(int64_t)blockIdx.y * n_q + iq] = acc.get(r);
+  }
+}
+
+template <class Pol, int R, int NT>
+cudaError_t launch_one(const FwdLaunch& L, const void* items, int64_t n_items, const double* q, int64_t n_q,
+                       float p_tau, double2* partial, uint32_t* status, cudaStream_t st) {
+  dim3 grid((unsigned)L.q_tiles, (unsigned)L.k_splits);
+  k_fwd<Pol, R, NT><<<grid, NT, 0, st>>>(static_cast<const typename Pol::Item*>(items), n_items, L.per_split, q,
+                                         n_q, p_tau, partial, status);
+  return cudaGetLastError();
+}
+
+template <class Pol, int R, int NT>
+int occupancy_one() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fwd<Pol, R, NT>, NT, 0) != cudaSuccess) return 1;
+  return b > 0 ? b : 1;
+}
+
+// Dispatch over the instantiated configurations (FP64 paths keep R <= 2).
+template <class Pol, class F>
+cudaError_t dispatch(int r, int nt, F&& f) {
+  constexpr bool kBig = sizeof(typename Pol::QT) == 4;
+#define PFT_CASE(RR, NN) \
+  if (r == RR && nt == NN) return f.template operator()<Pol, RR, NN>();
+  PFT_CASE(1, 128) PFT_CASE(2, 128) PFT_CASE(1, 256) PFT_CASE(2, 256)
+  if constexpr (kBig) {
+    PFT_CASE(4, 128) PFT_CASE(8, 128) PFT_CASE(4, 256) PFT_CASE(8, 256)
+  }
+#undef PFT_CASE
+  return cudaErrorInvalidConfiguration;
+}
+
+struct LaunchF {
+  const FwdLaunch& L; const void* items; int64_t n_items; const double* q; int64_t n_q; float p_tau;
+  double2* partial; uint32_t* status; cudaStream_t st;
+  template <class Pol, int R, int NT>
+  cudaError_t operator()() const { return launch_one<Pol, R, NT>(L, items, n_items, q, n_q, p_tau, partial, status, st); }
+};
+
+struct OccF {
+  int* out;
+  template <class Pol, int R, int NT>
+  cudaError_t operator()() const { *out = occupancy_one<Pol, R, NT>(); return cudaSuccess; }
+};
+
+}  // namespace
+
+cudaError_t launch_fwd(int dim, bool fp64, const FwdLaunch& L, const void* items, int64_t n_items, const double* q,
+                       int64_t n_q, float tau, double2* partial, uint32_t* status, cudaStream_t st) {
+  const float p_tau = 0.25f * tau * tau;
+  LaunchF f{L, items, n_items, q, n_q, p_tau, partial, status, st};
+  if (dim == 2) return fp64 ? dispatch<Pol2F64>(L.r, L.nt, f) : dispatch<Pol2F32>(L.r, L.nt, f);
+  return fp64 ? dispatch<Pol3F64>(L.r, L.nt, f) : dispatch<Pol3F32>(L.r, L.nt, f);
+}
+
+int fwd_blocks_per_sm(int dim, bool fp64, int r, int nt) {
+  int b = 1;
+  OccF f{&b};
+  cudaError_t e;
+  if (dim == 2) e = fp64 ? dispatch<Pol2F64>(r, nt, f) : dispatch<Pol2F32>(r, nt, f);
+  else e = fp64 ? dispatch<Pol3F64>(r, nt, f) : dispatch<Pol3F32>(r, nt, f);
+  return e == cudaSuccess ? b : 1;
+}
+
+int fwd_tile(int dim, bool fp64) {
+  if (dim == 2) return fp64 ? Pol2F64::kTile : Pol2F32::kTile;
+  return fp64 ? Pol3F64::kTile : Pol3F32::kTile;
+}
+
+}  // namespace pft

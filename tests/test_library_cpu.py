@@ -1,0 +1,92 @@
+"""Host-side checks of libpft that need no GPU.
+
+The shared library builds for sm_103a, loads, and exports every entry point
+that include/pft.h declares; workspace sizing and argument validation answer
+without touching a device.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2104_08309_gb300 import _capi
+from paper_2104_08309_gb300 import build as pbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pft.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pbuild.build()
+    return _capi.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pft\w+)\s*\(", text)))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for n in ("pft2d_polygons", "pft2d_polygons_batched", "pft3d_mesh", "pft2d_polygons_backward",
+              "pft3d_mesh_backward", "pft_status"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    # and the ctypes table covers exactly the declared set
+    assert sorted(_capi.SIGNATURES) == declared_functions()
+
+
+def test_options_struct_layout_matches_header():
+    # int32 x5, float, two pointers (8-aligned at offset 24), int32[4]
+    assert ctypes.sizeof(_capi.Options) == 24 + 16 + 16
+    assert _capi.Options.main_start_event.offset == 24
+
+
+def test_status_strings_and_version(lib):
+    assert lib.pft_status_string(0) == b"ok"
+    assert b"index" in lib.pft_status_string(2)
+    assert lib.pft_status_string(999) == b"unknown status code"
+    assert lib.pft_version() >= 100
+
+
+def test_workspace_sizes(lib):
+    o = _capi.Options()
+    s3 = lib.pft3d_workspace_size(10242, 20480, 262144, ctypes.byref(o))
+    assert s3 >= 256 + 20480 * 48 + 262144 * 16
+    assert s3 % 256 == 0
+    o64 = _capi.Options(precision=1)
+    assert lib.pft3d_workspace_size(10242, 20480, 262144, ctypes.byref(o64)) > s3   # 96-byte records
+    assert lib.pft2d_workspace_size(64, 1, 16384, None) >= 256 + 64 * 16 + 16384 * 16
+    assert lib.pft3d_workspace_size(-1, 3, 3, None) == 0
+    bad = _capi.Options(face_series_tau=2.0)
+    assert lib.pft3d_workspace_size(3, 1, 1, ctypes.byref(bad)) == 0
+
+
+def test_argument_errors_are_synchronous(lib):
+    """Rejected before any device work: negative sizes, bad options, short or misaligned workspace."""
+    fake = ctypes.c_void_p(256)     # never dereferenced: every call below fails its host checks
+    o = _capi.Options()
+    assert lib.pft3d_mesh(fake, -1, fake, 1, fake, 1, fake, fake, 1 << 20, ctypes.byref(o), None) == 1
+    assert lib.pft3d_mesh(fake, 3, fake, 1, fake, 1, fake, None, 1 << 20, ctypes.byref(o), None) == 4
+    assert lib.pft3d_mesh(fake, 3, fake, 1, fake, 1, fake, ctypes.c_void_p(256 + 8), 1 << 20,
+                          ctypes.byref(o), None) == 4
+    assert lib.pft3d_mesh(fake, 3, fake, 1, fake, 1, fake, fake, 16, ctypes.byref(o), None) == 4
+    bad = _capi.Options(q_per_thread=3)
+    assert lib.pft3d_mesh(fake, 3, fake, 1, fake, 1, fake, fake, 1 << 20, ctypes.byref(bad), None) == 7
+    bad = _capi.Options(precision=5)
+    assert lib.pft2d_polygons(fake, 3, fake, 1, fake, 1, fake, fake, 1 << 20, ctypes.byref(bad), None) == 1
+    assert lib.pft2d_polygons(None, 3, fake, 1, fake, 1, fake, fake, 1 << 20, None, None) == 1
+
+
+def test_python_binding_refuses_cpu_tensors():
+    torch = pytest.importorskip("torch")
+    import paper_2104_08309_gb300 as pft
+    with pytest.raises(ValueError, match="CUDA"):
+        pft.pft3d_mesh(torch.zeros(3, 3), torch.zeros(1, 3, dtype=torch.int32), torch.zeros(1, 3, dtype=torch.float64))
