@@ -37,8 +37,8 @@ WORKLOAD = "icosphere8_perturbed_q128cubed"
 # Algorithmic per-pair instruction counts of the 3D FP32 face term (see the
 # face_pair_f32 formula): FP32-pipe operations (add/mul/fma/compare/round) and
 # SFU operations (sin, cos, reciprocal), per branch.
-OPS_SERIES = {"fp32": 40, "sfu": 2}   # face-integral series (small phase spread)
-OPS_EDGE = {"fp32": 107, "sfu": 9}    # edge sum of Eq. 17, polynomial sinc
+OPS_SERIES = {"fp32": 38, "sfu": 2}   # face-integral series (small phase spread)
+OPS_EDGE = {"fp32": 97, "sfu": 9}     # edge sum of Eq. 17, polynomial sinc
 FP32_LANES, SFU_LANES = 128, 16       # per SM per clock
 
 
@@ -51,6 +51,12 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU-oracle sample")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle leg")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="c5",
+                   help="c5: the benchmark workload; c5small: same mesh family at subdivision 6 on 64^3 Q "
+                        "(for profiling captures)")
+    p.add_argument("--q-per-thread", type=int, default=0)
+    p.add_argument("--block-threads", type=int, default=0)
+    p.add_argument("--tau", type=float, default=0.0, help="face_series_tau (0 = library default)")
     return p.parse_args()
 
 
@@ -59,10 +65,21 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
 
 
-def workload(rank):
+WORKLOADS = {
+    "c5": (WORKLOAD, 1),
+    # the same mesh on every 4th (qx, qy) column of the same grid (1/16 of the Q
+    # points, same spacing along qz): for profiler captures of the main kernel
+    "c5small": ("icosphere8_perturbed_q128cubed_every16th_column", 4),
+}
+
+
+def workload(rank, name="c5"):
     from paper_2104_08309_gb300 import synth
+    _, stride = WORKLOADS[name]
     v, f = synth.perturbed_icosphere(8, seed=5 + rank, amp=0.05)
     q = synth.q_grid_3d(128, 60.0)
+    if stride > 1:
+        q = np.ascontiguousarray(q.reshape(128, 128, 128, 3)[::stride, ::stride].reshape(-1, 3))
     return v, f, q
 
 
@@ -74,17 +91,25 @@ def peaks():
         return {"sm_max_mhz": 2070.0}, "fallback"
 
 
-def branch_mix(v, f, q, tau=1.0, n=1 << 16, seed=0):
-    """Fraction of (Q, face) pairs taking the series branch (P < tau^2/4), from a seeded sample."""
+def branch_mix(v, f, q, tau=1.0, tau_lo=0.05, n_warps=4096, seed=0):
+    """Fraction of (Q, face) pairs the kernel evaluates with the series branch.
+
+    Mirrors the kernel's rule on a seeded sample: a warp covers 32 consecutive Q
+    indices against one face; a lane takes the series if all 32 lanes have
+    P < tau^2/4, or if its own P < tau_lo^2/4.
+    """
     rng = np.random.default_rng(seed)
-    fi = rng.integers(0, f.shape[0], n)
-    qi = rng.integers(0, q.shape[0], n)
-    p = v.astype(np.float64)[f[fi]]
+    fi = rng.integers(0, f.shape[0], n_warps)
+    q0 = 32 * rng.integers(0, q.shape[0] // 32, n_warps)
+    p = v.astype(np.float64)[f[fi]]                      # [w, 3, 3]
     g = p.mean(axis=1)
-    a0 = np.einsum("ij,ij->i", q[qi], p[:, 0] - g)
-    a1 = np.einsum("ij,ij->i", q[qi], p[:, 1] - g)
+    qq = q[q0[:, None] + np.arange(32)[None, :]]         # [w, 32, 3]
+    a0 = np.einsum("wlj,wj->wl", qq, p[:, 0] - g)
+    a1 = np.einsum("wlj,wj->wl", qq, p[:, 1] - g)
     P = a0 * a0 + a0 * a1 + a1 * a1
-    return float(np.mean(P < 0.25 * tau * tau))
+    tl = min(tau, tau_lo)
+    series = np.all(P < 0.25 * tau * tau, axis=1, keepdims=True) | (P < 0.25 * tl * tl)
+    return float(np.mean(series))
 
 
 def roofline(pairs, t_main_s, mix, n_sm, clk_mhz):
@@ -219,7 +244,7 @@ def main():
     from paper_2104_08309_gb300 import build as pbuild
     pbuild.build()
 
-    v, f, q = workload(rank)
+    v, f, q = workload(rank, args.workload)
     pairs = float(f.shape[0]) * float(q.shape[0])
     vd, fd, qd = (torch.from_numpy(a).to(dev) for a in (v, f, q))
     lib = pft.load()
@@ -230,7 +255,9 @@ def main():
     for a, b in e_main:
         a.record()
         b.record()
-    opts = pft.make_options({})
+    tune = {"q_per_thread": args.q_per_thread, "block_threads": args.block_threads,
+            "face_series_tau": args.tau}
+    opts = pft.make_options(tune)
     nbytes = lib.pft3d_workspace_size(v.shape[0], f.shape[0], q.shape[0], ctypes.byref(opts))
     ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     out = torch.empty(q.shape[0], 2, dtype=torch.float64, device=dev)
@@ -260,7 +287,7 @@ def main():
     t_wall = time.perf_counter()
     for k in range(args.steps):
         flush.zero_()                                   # L2 flushed between steps (outside the step events)
-        o = pft.make_options({"main_start_event": e_main[k][0].cuda_event,
+        o = pft.make_options({**tune, "main_start_event": e_main[k][0].cuda_event,
                               "main_stop_event": e_main[k][1].cuda_event})
         e_step[k][0].record(stream)
         launches += step(o)
@@ -305,22 +332,25 @@ def main():
         pk, pk_kind = peaks()
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         clk_max = float(pk.get("sm_max_mhz", 2070.0))
-        mix = branch_mix(v, f, q)
+        mix = branch_mix(v, f, q, tau=args.tau or 1.0)
         ops, issue, achieved, peak_ops = roofline(pairs, ms_main / 1e3, mix, n_sm, clk_max)
         value = world * pairs / (ms_step / 1e3) / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "faces": int(f.shape[0]), "q_points": int(q.shape[0]),
-                       "pairs_per_step": pairs, "edge_terms_per_step": 3 * pairs,
+            "config": {"workload": WORKLOADS[args.workload][0], "faces": int(f.shape[0]),
+                       "q_points": int(q.shape[0]), "pairs_per_step": pairs,
+                       "launch": {"q_per_thread": opts.q_per_thread or 4, "block_threads": opts.block_threads or 256,
+                                  "face_series_tau": opts.face_series_tau or 1.0}, "edge_terms_per_step": 3 * pairs,
                        "l2": "flushed between steps (512 MB write outside the step events)",
                        "parallelism": f"independent replicas x{world}" if world > 1 else "single GPU",
                        "wall_s_timed_region": t_wall, "device_status": int(status)},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Tops/s", "frac": achieved / peak_ops,
                          "traffic": traffic_from_profile(),
-                         "kernel": "k_fwd<Pol3F32,4,256>", "main_kernel_ms": ms_main,
+                         "kernel": f"k_fwd<Pol3F32,{opts.q_per_thread or 4},{opts.block_threads or 256}>",
+                         "main_kernel_ms": ms_main,
                          "peak_basis": f"{n_sm} SMs x 128 FP32/SFU issue slots x {clk_max:.0f} MHz "
                                        f"({pk_kind} max SM clock)",
                          "ops_per_pair": {"fp32": ops["fp32"], "sfu": ops["sfu"]},

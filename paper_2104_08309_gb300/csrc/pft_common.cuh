@@ -57,6 +57,13 @@ __device__ __forceinline__ float ord2f(uint32_t u) {
 constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kInvTwoPi = 0.15915494309189533577f;
 
+// 1/x on the SFU (rcp.approx: about 1 ulp; x is never a denormal here).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // exp(2 pi i t) for a phase t given in turns.  t - rint(t) is exact in FP32, so
 // the reduction adds no error; sin/cos then run on the SFU over [-pi, pi].
 __device__ __forceinline__ void sincos_turns(float t, float* s, float* c) {
@@ -64,20 +71,32 @@ __device__ __forceinline__ void sincos_turns(float t, float* s, float* c) {
   __sincosf(kTwoPi * r, s, c);
 }
 
-// sinc(u) = sin(u)/u for |u| <= 1 by its Taylor series through u^10 (truncation
-// below 2.6e-8 relative at |u| = 1); the SFU (after reduction) beyond.
+// sinc(u) = sin(u)/u from u2 = u^2 <= pi^2: Taylor series through u^16, whose
+// truncation is below 7.3e-9 at |u| = pi (coefficients (-1)^k / (2k+1)!).
+__device__ __forceinline__ float sinc_poly(float u2) {
+  float p = fmaf(u2, 2.81145725e-15f, -7.64716373e-13f);   // 1/17!, -1/15!
+  p = fmaf(u2, p, 1.60590438e-10f);                        // 1/13!
+  p = fmaf(u2, p, -2.50521084e-8f);                        // -1/11!
+  p = fmaf(u2, p, 2.75573192e-6f);                         // 1/9!
+  p = fmaf(u2, p, -1.98412698e-4f);                        // -1/7!
+  p = fmaf(u2, p, 8.33333333e-3f);                         // 1/5!
+  p = fmaf(u2, p, -1.66666667e-1f);                        // -1/3!
+  return fmaf(u2, p, 1.0f);
+}
+
+constexpr float kPi2 = 9.86960440108935861883f;   // pi^2
+
+// sinc(u) for any u: the polynomial on |u| <= pi, otherwise sin of the
+// turn-reduced argument on the SFU times 1/u (relative error ~1e-7 there).
 __device__ __forceinline__ float sinc_f32(float u) {
-  float u2 = u * u;
-  if (u2 <= 1.0f) {
-    float p = fmaf(u2, -2.50521084e-8f, 2.75573192e-6f);   // -1/11!, 1/9!
-    p = fmaf(u2, p, -1.98412698e-4f);                       // -1/7!
-    p = fmaf(u2, p, 8.33333333e-3f);                        // 1/5!
-    p = fmaf(u2, p, -1.66666667e-1f);                       // -1/3!
-    return fmaf(u2, p, 1.0f);
+  const float u2 = u * u;
+  float r = sinc_poly(u2);
+  if (u2 > kPi2) {
+    float s, c;
+    sincos_turns(u * kInvTwoPi, &s, &c);
+    r = s * rcp_approx(u);
   }
-  float s, c;
-  sincos_turns(u * kInvTwoPi, &s, &c);
-  return s * __frcp_rn(u);
+  return r;
 }
 
 // Error-free sum a + b = s + e (Knuth TwoSum).

@@ -16,20 +16,26 @@ namespace {
 
 constexpr int kStages = 4;
 
+// Thresholds on P (see face_pair_f32): p_hi = tau^2/4, p_lo = tau_lo^2/4.
+struct Thr {
+  float hi, lo;
+};
+constexpr float kTauLo = 0.05f;
+
 // ---------------------------------------------------------------------------
 // Per-pair arithmetic.
 // ---------------------------------------------------------------------------
 
 // 2D, Eq. 7 (Sec. 2): the segment p0 -> p1 contributes
 //   -i (Qx Dy - Qy Dx) sinc(Q.D/2) exp(iQ.m)           (times 1/|Q|^2, applied later)
-// Records hold m / (2 pi) and D/2, so w below is half the cross product; the
-// factor 2 and 1/|Q|^2 are applied in FP64 by the finalize kernel.
+// Records hold m and D/2, so w below is half the cross product; the factor 2
+// and 1/|Q|^2 are applied in FP64 by the finalize kernel.
 __device__ __forceinline__ void seg_pair_f32(float qx, float qy, const float4 s, float& re, float& im) {
-  const float pt = fmaf(qx, s.x, qy * s.y);    // Q.m in turns
+  const float ph = fmaf(qx, s.x, qy * s.y);    // Q.m
   const float u = fmaf(qx, s.z, qy * s.w);     // Q.D / 2
   const float w = fmaf(qx, s.w, -qy * s.z);    // (Qx Dy - Qy Dx) / 2
   float sn, cs;
-  sincos_turns(pt, &sn, &cs);
+  __sincosf(ph, &sn, &cs);
   const float ws = w * sinc_f32(u);
   re = ws * sn;    // -i * ws * (cos + i sin) = ws sin - i ws cos
   im = -ws * cs;
@@ -68,13 +74,18 @@ __device__ __forceinline__ void seg_pair_f64(double qx, double qy, const Seg64& 
 // face is small (it is 0/0 for Q parallel to N); there the same face integral
 // (Eq. 14) is taken from its series, Z = i G,
 //   G = sum_k i^k h_k(a) / (k+2)!,   h_k = P h_{k-2} + T h_{k-3},
-// P = a0^2 + a0 a1 + a1^2 (= h_2), T = a0 a1 a2 (= h_3), kept through k = 8.
-// The series is used when P < tau^2/4, which implies max_l |Q.d_l| < tau <= 1;
-// there the omitted terms are below 1e-9 relative.
+// P = a0^2 + a0 a1 + a1^2 (= h_2), T = a0 a1 a2 (= h_3), kept through k = 8;
+// P < tau^2/4 implies max_l |Q.d_l| < tau <= 1, where the omitted terms are
+// below 1e-9 relative.
+// Branch choice (warp-uniform where possible): a lane takes the series when
+// every lane of its warp has P < p_hi = tau^2/4, or when its own P < p_lo =
+// tau_lo^2/4 (tau_lo = min(tau, 0.05): below it the edge sum would lose more
+// than ~4 bits to cancellation).  Otherwise it takes the edge sum.  Both
+// evaluate the same face integral, so the choice only moves rounding.
 __device__ __forceinline__ void face_pair_f32(float qx, float qy, float qz, const float4 A, const float4 B,
-                                              const float4 C, float p_tau, float& re, float& im) {
-  // A = (g/2pi).xyz, q0.x   B = q0.yz, q1.xy   C = q1.z, N.xyz
-  const float mut = fmaf(qx, A.x, fmaf(qy, A.y, qz * A.z));   // mu in turns
+                                              const float4 C, float p_hi, float p_lo, float& re, float& im) {
+  // A = g.xyz, q0.x   B = q0.yz, q1.xy   C = q1.z, N.xyz
+  const float mu = fmaf(qx, A.x, fmaf(qy, A.y, qz * A.z));
   const float a0 = fmaf(qx, A.w, fmaf(qy, B.x, qz * B.y));
   const float a1 = fmaf(qx, B.z, fmaf(qy, B.w, qz * C.x));
   const float s = fmaf(qx, C.y, fmaf(qy, C.z, qz * C.w));
@@ -82,7 +93,8 @@ __device__ __forceinline__ void face_pair_f32(float qx, float qy, float qz, cons
   const float a2 = -a01;
   const float P = fmaf(a0, a01, a1 * a1);
   float zr, zi;
-  if (P < p_tau) {
+  const bool series = __all_sync(0xffffffffu, P < p_hi) || (P < p_lo);
+  if (series) {
     const float T = a0 * a1 * a2;
     const float T2 = T * T;
     float gre = fmaf(P, 2.75573192e-7f, -2.48015873e-5f);   // 1/10!, -1/8!
@@ -101,29 +113,30 @@ __device__ __forceinline__ void face_pair_f32(float qx, float qy, float qz, cons
     const float b1 = fmaf(B.z, Xx, fmaf(B.w, Xy, C.x * Xz));
     const float b2 = -(b0 + b1);
     const float w[3] = {b1 - b0, b2 - b1, b0 - b2};
-    const float psi[3] = {-0.5f * a2, -0.5f * a0, -0.5f * a1};
-    const float u[3] = {0.5f * (a1 - a0), 0.5f * (a2 - a1), 0.5f * (a0 - a2)};
+    const float h0 = 0.5f * a0, h1 = 0.5f * a1;
+    const float psi[3] = {h0 + h1, -h0, -h1};                               // -a_{l+2}/2
+    const float u[3] = {h1 - h0, fmaf(-2.0f, h1, -h0), fmaf(2.0f, h0, h1)};  // (a_{l+1} - a_l)/2
     float sr = 0.f, si = 0.f;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
       float sp, cp;
-      sincos_turns(psi[l] * kInvTwoPi, &sp, &cp);
+      __sincosf(psi[l], &sp, &cp);
       const float ws = w[l] * sinc_f32(u[l]);
       sr = fmaf(ws, cp, sr);
       si = fmaf(ws, sp, si);
     }
-    const float inv = (x2 > 0.f) ? __frcp_rn(x2) : 0.f;   // x2 = 0 only for a degenerate face (s = 0 too)
+    const float inv = (x2 > 0.f) ? rcp_approx(x2) : 0.f;   // x2 = 0 only for a degenerate face (s = 0 too)
     zr = sr * inv;
     zi = si * inv;
   }
   float sm, cm;
-  sincos_turns(mut, &sm, &cm);
+  __sincosf(mu, &sm, &cm);
   re = -s * fmaf(cm, zr, -sm * zi);
   im = -s * fmaf(cm, zi, sm * zr);
 }
 
 // Same face term in FP64 (comparison path): library sincos, series through k = 16.
-__device__ __forceinline__ void face_pair_f64(double qx, double qy, double qz, const Face64& f, double p_tau,
+__device__ __forceinline__ void face_pair_f64(double qx, double qy, double qz, const Face64& f, double p_hi, double p_lo,
                                               double& re, double& im) {
   const double mu = fma(qx, f.gx, fma(qy, f.gy, qz * f.gz));
   const double a0 = fma(qx, f.q0x, fma(qy, f.q0y, qz * f.q0z));
@@ -132,7 +145,8 @@ __device__ __forceinline__ void face_pair_f64(double qx, double qy, double qz, c
   const double a2 = -(a0 + a1);
   const double P = fma(a0, a0 + a1, a1 * a1);
   double zr, zi;
-  if (P < p_tau) {
+  const bool series = __all_sync(0xffffffffu, P < p_hi) || (P < p_lo);
+  if (series) {
     const double T = a0 * a1 * a2;
     constexpr int K = 16;
     double h[K + 1];
@@ -208,7 +222,7 @@ struct Pol2F32 {
   template <int R> using Acc = Acc32<R>;
   using QT = float;
   template <int R>
-  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc, float) {
+  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc, Thr) {
     float tre[R], tim[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { tre[r] = 0.f; tim[r] = 0.f; }
@@ -234,7 +248,7 @@ struct Pol2F64 {
   template <int R> using Acc = Acc64<R>;
   using QT = double;
   template <int R>
-  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc, float) {
+  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc, Thr) {
     for (int i = 0; i < cnt; ++i) {
       const Seg64 s = t[i];
 #pragma unroll
@@ -255,7 +269,7 @@ struct Pol3F32 {
   using QT = float;
   template <int R>
   __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc,
-                                              float p_tau) {
+                                              Thr th) {
     float tre[R], tim[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { tre[r] = 0.f; tim[r] = 0.f; }
@@ -266,7 +280,7 @@ struct Pol3F32 {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         float re, im;
-        face_pair_f32(q[r][0], q[r][1], q[r][2], A, B, C, p_tau, re, im);
+        face_pair_f32(q[r][0], q[r][1], q[r][2], A, B, C, th.hi, th.lo, re, im);
         tre[r] += re;
         tim[r] += im;
       }
@@ -283,13 +297,13 @@ struct Pol3F64 {
   using QT = double;
   template <int R>
   __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc,
-                                              float p_tau) {
+                                              Thr th) {
     for (int i = 0; i < cnt; ++i) {
       const Face64 f = t[i];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         double re, im;
-        face_pair_f64(q[r][0], q[r][1], q[r][2], f, (double)p_tau, re, im);
+        face_pair_f64(q[r][0], q[r][1], q[r][2], f, (double)th.hi, (double)th.lo, re, im);
         acc.re[r] += re;
         acc.im[r] += im;
       }
@@ -303,7 +317,7 @@ struct Pol3F64 {
 template <class Pol, int R, int NT>
 __global__ void __launch_bounds__(NT) k_fwd(const typename Pol::Item* __restrict__ items, int64_t n_items,
                                             int64_t per_split, const double* __restrict__ q, int64_t n_q,
-                                            float p_tau, double2* __restrict__ partial, uint32_t* status) {
+                                            Thr th, double2* __restrict__ partial, uint32_t* status) {
   using Item = typename Pol::Item;
   using QT = typename Pol::QT;
   constexpr int TILE = Pol::kTile;
@@ -360,7 +374,7 @@ __global__ void __launch_bounds__(NT) k_fwd(const typename Pol::Item* __restrict
       return;
     }
     const int cnt = (int)min((int64_t)TILE, n - (int64_t)t * TILE);
-    Pol::template tile<R>(ring + s * TILE, cnt, qr, acc, p_tau);
+    Pol::template tile<R>(ring + s * TILE, cnt, qr, acc, th);
     __syncthreads();   // every thread is done with slot s
     if (threadIdx.x == 0 && t + kStages < ntiles) {
       fence_proxy_async_smem();
@@ -376,10 +390,10 @@ __global__ void __launch_bounds__(NT) k_fwd(const typename Pol::Item* __restrict
 
 template <class Pol, int R, int NT>
 cudaError_t launch_one(const FwdLaunch& L, const void* items, int64_t n_items, const double* q, int64_t n_q,
-                       float p_tau, double2* partial, uint32_t* status, cudaStream_t st) {
+                       Thr th, double2* partial, uint32_t* status, cudaStream_t st) {
   dim3 grid((unsigned)L.q_tiles, (unsigned)L.k_splits);
   k_fwd<Pol, R, NT><<<grid, NT, 0, st>>>(static_cast<const typename Pol::Item*>(items), n_items, L.per_split, q,
-                                         n_q, p_tau, partial, status);
+                                         n_q, th, partial, status);
   return cudaGetLastError();
 }
 
@@ -405,10 +419,10 @@ cudaError_t dispatch(int r, int nt, F&& f) {
 }
 
 struct LaunchF {
-  const FwdLaunch& L; const void* items; int64_t n_items; const double* q; int64_t n_q; float p_tau;
+  const FwdLaunch& L; const void* items; int64_t n_items; const double* q; int64_t n_q; Thr th;
   double2* partial; uint32_t* status; cudaStream_t st;
   template <class Pol, int R, int NT>
-  cudaError_t operator()() const { return launch_one<Pol, R, NT>(L, items, n_items, q, n_q, p_tau, partial, status, st); }
+  cudaError_t operator()() const { return launch_one<Pol, R, NT>(L, items, n_items, q, n_q, th, partial, status, st); }
 };
 
 struct OccF {
@@ -421,8 +435,9 @@ struct OccF {
 
 cudaError_t launch_fwd(int dim, bool fp64, const FwdLaunch& L, const void* items, int64_t n_items, const double* q,
                        int64_t n_q, float tau, double2* partial, uint32_t* status, cudaStream_t st) {
-  const float p_tau = 0.25f * tau * tau;
-  LaunchF f{L, items, n_items, q, n_q, p_tau, partial, status, st};
+  const float tau_lo = fminf(tau, kTauLo);
+  const Thr th{0.25f * tau * tau, 0.25f * tau_lo * tau_lo};
+  LaunchF f{L, items, n_items, q, n_q, th, partial, status, st};
   if (dim == 2) return fp64 ? dispatch<Pol2F64>(L.r, L.nt, f) : dispatch<Pol2F32>(L.r, L.nt, f);
   return fp64 ? dispatch<Pol3F64>(L.r, L.nt, f) : dispatch<Pol3F32>(L.r, L.nt, f);
 }

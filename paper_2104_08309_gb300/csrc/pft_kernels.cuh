@@ -12,18 +12,18 @@ namespace pft {
 // applied once per Q in the finalize kernel.
 // ---------------------------------------------------------------------------
 
-// 2D segment, FP32: midpoint / (2 pi) (phase in turns) and half the edge vector.
+// 2D segment, FP32: midpoint and half the edge vector.
 struct __align__(16) Seg32 {
-  float mxt, myt, hx, hy;
+  float mx, my, hx, hy;
 };
 // 2D segment, FP64: midpoint and half the edge vector.
 struct __align__(16) Seg64 {
   double mx, my, hx, hy;
 };
-// 3D triangle, FP32: centroid / (2 pi), the first two corners relative to the
-// centroid (the third is -(q0 + q1)), and N = (p1 - p0) x (p2 - p0).
+// 3D triangle, FP32: centroid, the first two corners relative to the centroid
+// (the third is -(q0 + q1)), and N = (p1 - p0) x (p2 - p0).
 struct __align__(16) Face32 {
-  float gtx, gty, gtz, q0x, q0y, q0z, q1x, q1y, q1z, nx, ny, nz;
+  float gx, gy, gz, q0x, q0y, q0z, q1x, q1y, q1z, nx, ny, nz;
 };
 // 3D triangle, FP64: centroid, corners 0 and 1 relative to it, N.
 struct __align__(16) Face64 {

@@ -7,7 +7,6 @@ namespace pft {
 
 namespace {
 
-constexpr double kTwoPiD = 6.283185307179586476925286766559;
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T x) {
@@ -122,7 +121,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep2d(const float* __restrict
       reinterpret_cast<Seg64*>(items)[j] = Seg64{mx, my, hx, hy};
     } else {
       reinterpret_cast<Seg32*>(items)[j] =
-          Seg32{(float)(mx / kTwoPiD), (float)(my / kTwoPiD), (float)hx, (float)hy};
+          Seg32{(float)mx, (float)my, (float)hx, (float)hy};
     }
   }
   double s = block_sum<kPrepThreads>(area, sh);
@@ -174,7 +173,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep3d(const float* __restrict
                                                    N[0], N[1], N[2]};
     } else {
       reinterpret_cast<Face32*>(items)[m] =
-          Face32{(float)(g[0] / kTwoPiD), (float)(g[1] / kTwoPiD), (float)(g[2] / kTwoPiD),
+          Face32{(float)g[0], (float)g[1], (float)g[2],
                  (float)q0[0], (float)q0[1], (float)q0[2], (float)q1[0], (float)q1[1], (float)q1[2],
                  (float)N[0], (float)N[1], (float)N[2]};
     }
