@@ -70,6 +70,7 @@ WORKLOADS = {
     # the same mesh on every 4th (qx, qy) column of the same grid (1/16 of the Q
     # points, same spacing along qz): for profiler captures of the main kernel
     "c5small": ("icosphere8_perturbed_q128cubed_every16th_column", 4),
+    "c5tiny": ("icosphere8_perturbed_q128cubed_every64th_column", 8),
 }
 
 

@@ -114,16 +114,20 @@ __device__ __forceinline__ void face_pair_f32(float qx, float qy, float qz, cons
     const float b2 = -(b0 + b1);
     const float w[3] = {b1 - b0, b2 - b1, b0 - b2};
     const float h0 = 0.5f * a0, h1 = 0.5f * a1;
-    const float psi[3] = {h0 + h1, -h0, -h1};                               // -a_{l+2}/2
     const float u[3] = {h1 - h0, fmaf(-2.0f, h1, -h0), fmaf(2.0f, h0, h1)};  // (a_{l+1} - a_l)/2
+    // exp(i psi_l), psi_l = -a_{l+2}/2: psi_1 = -h0 and psi_2 = -h1 on the SFU,
+    // psi_0 = h0 + h1 as the conjugate of their product.
+    float sp[3], cp[3];
+    __sincosf(-h0, &sp[1], &cp[1]);
+    __sincosf(-h1, &sp[2], &cp[2]);
+    cp[0] = fmaf(cp[1], cp[2], -sp[1] * sp[2]);
+    sp[0] = -fmaf(sp[1], cp[2], cp[1] * sp[2]);
     float sr = 0.f, si = 0.f;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-      float sp, cp;
-      __sincosf(psi[l], &sp, &cp);
       const float ws = w[l] * sinc_f32(u[l]);
-      sr = fmaf(ws, cp, sr);
-      si = fmaf(ws, sp, si);
+      sr = fmaf(ws, cp[l], sr);
+      si = fmaf(ws, sp[l], si);
     }
     const float inv = (x2 > 0.f) ? rcp_approx(x2) : 0.f;   // x2 = 0 only for a degenerate face (s = 0 too)
     zr = sr * inv;
@@ -313,6 +317,15 @@ struct Pol3F64 {
 
 // ---------------------------------------------------------------------------
 // The main kernel: bulk-copy ring of record tiles, R Q points per thread.
+//
+// Ring protocol (no block-wide barrier inside the loop): full[s] completes when
+// the bulk copy of the tile in slot s has landed (expect_tx by the issuing
+// thread); empty[s] completes when every warp has finished reading slot s (one
+// arrive per warp).  Thread 0 issues tile t+2 after finishing tile t, once all
+// warps are done with tile t-2 (the tile that last used that slot), so warps
+// may drift up to two tiles apart without waiting for each other.  Every wait
+// is bounded; a wait that gives up sets ST_TIMEOUT and the block stops early
+// after letting its copies in flight land (also bounded).
 // ---------------------------------------------------------------------------
 template <class Pol, int R, int NT>
 __global__ void __launch_bounds__(NT) k_fwd(const typename Pol::Item* __restrict__ items, int64_t n_items,
@@ -322,8 +335,11 @@ __global__ void __launch_bounds__(NT) k_fwd(const typename Pol::Item* __restrict
   using QT = typename Pol::QT;
   constexpr int TILE = Pol::kTile;
   constexpr int D = Pol::kDim;
+  constexpr int kLag = 2;   // tiles between the consumption of a slot and its refill
+  static_assert(kStages > kLag, "ring must hold the lagging slots");
   __shared__ __align__(128) Item ring[kStages * TILE];
-  __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ __align__(8) uint64_t empty[kStages];
 
   const int64_t i0 = (int64_t)blockIdx.y * per_split;
   const int64_t n = max((int64_t)0, min(per_split, n_items - i0));
@@ -346,7 +362,10 @@ __global__ void __launch_bounds__(NT) k_fwd(const typename Pol::Item* __restrict
   acc.init();
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NT / 32);
+    }
     fence_mbar_init();
   }
   __syncthreads();
@@ -354,33 +373,34 @@ __global__ void __launch_bounds__(NT) k_fwd(const typename Pol::Item* __restrict
     const int s = t % kStages;
     const int64_t cnt = min((int64_t)TILE, n - (int64_t)t * TILE);
     const uint32_t bytes = (uint32_t)(cnt * (int64_t)sizeof(Item));
-    mbar_arrive_expect_tx(&bar[s], bytes);
-    bulk_g2s(ring + s * TILE, src + (int64_t)t * TILE, bytes, &bar[s]);
+    mbar_arrive_expect_tx(&full[s], bytes);
+    bulk_g2s(ring + s * TILE, src + (int64_t)t * TILE, bytes, &full[s]);
   };
+  int issued = min(kStages, ntiles);
   if (threadIdx.x == 0)
-    for (int t = 0; t < min(kStages, ntiles); ++t) issue(t);
+    for (int t = 0; t < issued; ++t) issue(t);
 
+  bool ok = true;
   for (int t = 0; t < ntiles; ++t) {
     const int s = t % kStages;
-    const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((t / kStages) & 1));
-    if (__syncthreads_or(!ok)) {
-      // A copy never landed: report it, let the copies still in flight finish
-      // (bounded), and leave without touching the ring again.
-      if (threadIdx.x == 0) {
-        set_status(status, ST_TIMEOUT);
-        for (int u = t + 1; u < min(t + kStages, ntiles); ++u)
-          (void)mbar_wait_bounded(&bar[u % kStages], (uint32_t)((u / kStages) & 1));
-      }
-      return;
-    }
+    if (!mbar_wait_bounded(&full[s], (uint32_t)((t / kStages) & 1))) { ok = false; break; }
     const int cnt = (int)min((int64_t)TILE, n - (int64_t)t * TILE);
     Pol::template tile<R>(ring + s * TILE, cnt, qr, acc, th);
-    __syncthreads();   // every thread is done with slot s
-    if (threadIdx.x == 0 && t + kStages < ntiles) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);
+    if (threadIdx.x == 0 && t + kLag < ntiles && t + kLag >= kStages) {
+      const int u = t + kLag - kStages;   // the tile that last used slot (t + kLag) % kStages
+      if (!mbar_wait_bounded(&empty[u % kStages], (uint32_t)((u / kStages) & 1))) { ok = false; break; }
       fence_proxy_async_smem();
-      issue(t + kStages);
+      issue(t + kLag);
+      issued = t + kLag + 1;
     }
   }
+  if (!ok) set_status(status, ST_TIMEOUT);
+  if (threadIdx.x == 0)   // no copy may still be writing into the ring when the block exits
+    for (int u = max(0, issued - kStages); u < issued; ++u)
+      (void)mbar_wait_bounded(&full[u % kStages], (uint32_t)((u / kStages) & 1));
+  if (!ok) return;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int64_t iq = qbase + (int64_t)r * NT;
