@@ -38,7 +38,7 @@ WORKLOAD = "icosphere8_perturbed_q128cubed"
 # face_pair_f32 formula): FP32-pipe operations (add/mul/fma/compare/round) and
 # SFU operations (sin, cos, reciprocal), per branch.
 OPS_SERIES = {"fp32": 38, "sfu": 2}   # face-integral series (small phase spread)
-OPS_EDGE = {"fp32": 97, "sfu": 9}     # edge sum of Eq. 17, polynomial sinc
+OPS_EDGE = {"fp32": 99, "sfu": 7}     # edge sum of Eq. 17, polynomial sinc
 FP32_LANES, SFU_LANES = 128, 16       # per SM per clock
 
 

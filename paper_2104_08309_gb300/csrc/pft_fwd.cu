@@ -16,11 +16,17 @@ namespace {
 
 constexpr int kStages = 4;
 
-// Thresholds on P (see face_pair_f32): p_hi = tau^2/4, p_lo = tau_lo^2/4.
+// Thresholds on P (see the 3D face term below): p_hi = tau^2/4, p_lo = tau_lo^2/4.
 struct Thr {
   float hi, lo;
 };
 constexpr float kTauLo = 0.05f;
+
+// Resident blocks per SM the register budget is sized for: 16-24 warps of
+// 256 threads, fewer registers per thread for fewer Q points per thread.
+// (FP64 paths: one block, so that the double-precision temporaries never spill.)
+template <class Pol, int R, int NT>
+constexpr int kMinBlocks = sizeof(typename Pol::QT) == 8 ? 1 : (NT == 256 ? 1 : 2) * (R >= 8 ? 1 : (R == 4 ? 2 : 3));
 
 // ---------------------------------------------------------------------------
 // Per-pair arithmetic.
@@ -77,62 +83,82 @@ __device__ __forceinline__ void seg_pair_f64(double qx, double qy, const Seg64& 
 // P = a0^2 + a0 a1 + a1^2 (= h_2), T = a0 a1 a2 (= h_3), kept through k = 8;
 // P < tau^2/4 implies max_l |Q.d_l| < tau <= 1, where the omitted terms are
 // below 1e-9 relative.
-// Branch choice (warp-uniform where possible): a lane takes the series when
-// every lane of its warp has P < p_hi = tau^2/4, or when its own P < p_lo =
-// tau_lo^2/4 (tau_lo = min(tau, 0.05): below it the edge sum would lose more
-// than ~4 bits to cancellation).  Otherwise it takes the edge sum.  Both
-// evaluate the same face integral, so the choice only moves rounding.
-__device__ __forceinline__ void face_pair_f32(float qx, float qy, float qz, const float4 A, const float4 B,
-                                              const float4 C, float p_hi, float p_lo, float& re, float& im) {
-  // A = g.xyz, q0.x   B = q0.yz, q1.xy   C = q1.z, N.xyz
-  const float mu = fmaf(qx, A.x, fmaf(qy, A.y, qz * A.z));
-  const float a0 = fmaf(qx, A.w, fmaf(qy, B.x, qz * B.y));
-  const float a1 = fmaf(qx, B.z, fmaf(qy, B.w, qz * C.x));
-  const float s = fmaf(qx, C.y, fmaf(qy, C.z, qz * C.w));
-  const float a01 = a0 + a1;
-  const float a2 = -a01;
-  const float P = fmaf(a0, a01, a1 * a1);
-  float zr, zi;
-  const bool series = __all_sync(0xffffffffu, P < p_hi) || (P < p_lo);
-  if (series) {
-    const float T = a0 * a1 * a2;
-    const float T2 = T * T;
-    float gre = fmaf(P, 2.75573192e-7f, -2.48015873e-5f);   // 1/10!, -1/8!
-    gre = fmaf(P, gre, 1.38888889e-3f);                      // 1/6!
-    gre = fmaf(P, gre, -4.16666667e-2f);                     // -1/4!
-    gre = fmaf(P, gre, 0.5f);                                // 1/2!
-    gre = fmaf(T2, fmaf(P, 8.26719577e-7f, -2.48015873e-5f), gre);   // T^2 (3P/10! - 1/8!)
-    const float gim = T * fmaf(P, fmaf(P, -8.26719577e-6f, 3.96825397e-4f), -8.33333333e-3f);  // -T/5! + PT/2520 - P^2 T/120960
-    zr = -gim;
-    zi = gre;
-  } else {
-    const float nx = C.y, ny = C.z, nz = C.w;
-    const float Xx = fmaf(ny, qz, -nz * qy), Xy = fmaf(nz, qx, -nx * qz), Xz = fmaf(nx, qy, -ny * qx);
-    const float x2 = fmaf(Xx, Xx, fmaf(Xy, Xy, Xz * Xz));
-    const float b0 = fmaf(A.w, Xx, fmaf(B.x, Xy, B.y * Xz));
-    const float b1 = fmaf(B.z, Xx, fmaf(B.w, Xy, C.x * Xz));
-    const float b2 = -(b0 + b1);
-    const float w[3] = {b1 - b0, b2 - b1, b0 - b2};
-    const float h0 = 0.5f * a0, h1 = 0.5f * a1;
-    const float u[3] = {h1 - h0, fmaf(-2.0f, h1, -h0), fmaf(2.0f, h0, h1)};  // (a_{l+1} - a_l)/2
-    // exp(i psi_l), psi_l = -a_{l+2}/2: psi_1 = -h0 and psi_2 = -h1 on the SFU,
-    // psi_0 = h0 + h1 as the conjugate of their product.
-    float sp[3], cp[3];
-    __sincosf(-h0, &sp[1], &cp[1]);
-    __sincosf(-h1, &sp[2], &cp[2]);
-    cp[0] = fmaf(cp[1], cp[2], -sp[1] * sp[2]);
-    sp[0] = -fmaf(sp[1], cp[2], cp[1] * sp[2]);
-    float sr = 0.f, si = 0.f;
+//
+// Branch choice, per face and warp: the series is taken for all of a thread's
+// Q points when every Q point of every lane of the warp has P < p_hi = tau^2/4;
+// otherwise the edge sum, except for Q points with P < p_lo = tau_lo^2/4
+// (tau_lo = min(tau, 0.05): below it the edge sum would lose more than ~4 bits
+// to cancellation), which are redone with the series.  Both evaluate the same
+// face integral, so the choice only moves rounding; the R Q points of a thread
+// share the branch, so their arithmetic interleaves.
+
+// Projections shared by both branches.  A = g.xyz, q0.x  B = q0.yz, q1.xy  C = q1.z, N.xyz
+__device__ __forceinline__ void face_common(float qx, float qy, float qz, const float4 A, const float4 B,
+                                            const float4 C, float& mu, float& a0, float& a1, float& s, float& P) {
+  mu = fmaf(qx, A.x, fmaf(qy, A.y, qz * A.z));
+  a0 = fmaf(qx, A.w, fmaf(qy, B.x, qz * B.y));
+  a1 = fmaf(qx, B.z, fmaf(qy, B.w, qz * C.x));
+  s = fmaf(qx, C.y, fmaf(qy, C.z, qz * C.w));
+  P = fmaf(a0, a0 + a1, a1 * a1);
+}
+
+// Z = i G from the face-integral series.
+__device__ __forceinline__ void face_series(float a0, float a1, float P, float& zr, float& zi) {
+  const float T = -(a0 * a1) * (a0 + a1);
+  const float T2 = T * T;
+  float gre = fmaf(P, 2.75573192e-7f, -2.48015873e-5f);   // 1/10!, -1/8!
+  gre = fmaf(P, gre, 1.38888889e-3f);                      // 1/6!
+  gre = fmaf(P, gre, -4.16666667e-2f);                     // -1/4!
+  gre = fmaf(P, gre, 0.5f);                                // 1/2!
+  gre = fmaf(T2, fmaf(P, 8.26719577e-7f, -2.48015873e-5f), gre);   // T^2 (3P/10! - 1/8!)
+  const float gim = T * fmaf(P, fmaf(P, -8.26719577e-6f, 3.96825397e-4f), -8.33333333e-3f);  // -T/5! + PT/2520 - P^2 T/120960
+  zr = -gim;
+  zi = gre;
+}
+
+// Z from the edge sum of Eq. 17.
+__device__ __forceinline__ void face_edge(float qx, float qy, float qz, const float4 A, const float4 B,
+                                          const float4 C, float a0, float a1, float& zr, float& zi) {
+  const float nx = C.y, ny = C.z, nz = C.w;
+  const float Xx = fmaf(ny, qz, -nz * qy), Xy = fmaf(nz, qx, -nx * qz), Xz = fmaf(nx, qy, -ny * qx);
+  const float x2 = fmaf(Xx, Xx, fmaf(Xy, Xy, Xz * Xz));
+  const float b0 = fmaf(A.w, Xx, fmaf(B.x, Xy, B.y * Xz));
+  const float b1 = fmaf(B.z, Xx, fmaf(B.w, Xy, C.x * Xz));
+  const float b2 = -(b0 + b1);
+  const float w[3] = {b1 - b0, b2 - b1, b0 - b2};
+  const float h0 = 0.5f * a0, h1 = 0.5f * a1;
+  const float u[3] = {h1 - h0, fmaf(-2.0f, h1, -h0), fmaf(2.0f, h0, h1)};  // (a_{l+1} - a_l)/2
+  // exp(i psi_l), psi_l = -a_{l+2}/2: psi_1 = -h0 and psi_2 = -h1 on the SFU,
+  // psi_0 = h0 + h1 as the conjugate of their product.
+  float sp[3], cp[3];
+  __sincosf(-h0, &sp[1], &cp[1]);
+  __sincosf(-h1, &sp[2], &cp[2]);
+  cp[0] = fmaf(cp[1], cp[2], -sp[1] * sp[2]);
+  sp[0] = -fmaf(sp[1], cp[2], cp[1] * sp[2]);
+  float u2[3], S[3];
 #pragma unroll
-    for (int l = 0; l < 3; ++l) {
-      const float ws = w[l] * sinc_f32(u[l]);
-      sr = fmaf(ws, cp[l], sr);
-      si = fmaf(ws, sp[l], si);
-    }
-    const float inv = (x2 > 0.f) ? rcp_approx(x2) : 0.f;   // x2 = 0 only for a degenerate face (s = 0 too)
-    zr = sr * inv;
-    zi = si * inv;
+  for (int l = 0; l < 3; ++l) {
+    u2[l] = u[l] * u[l];
+    S[l] = sinc_poly(u2[l]);
   }
+  if (fmaxf(u2[0], fmaxf(u2[1], u2[2])) > kPi2) {   // rare: an edge with |Q.d_l| > 2 pi
+#pragma unroll
+    for (int l = 0; l < 3; ++l) S[l] = sinc_f32(u[l]);
+  }
+  float sr = 0.f, si = 0.f;
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const float ws = w[l] * S[l];
+    sr = fmaf(ws, cp[l], sr);
+    si = fmaf(ws, sp[l], si);
+  }
+  const float inv = (x2 > 0.f) ? rcp_approx(x2) : 0.f;   // x2 = 0 only for Q parallel to N (series then)
+  zr = sr * inv;
+  zi = si * inv;
+}
+
+// |Q|^2 I_m = -s exp(i mu) Z.
+__device__ __forceinline__ void face_finish(float mu, float s, float zr, float zi, float& re, float& im) {
   float sm, cm;
   __sincosf(mu, &sm, &cm);
   re = -s * fmaf(cm, zr, -sm * zi);
@@ -281,10 +307,30 @@ struct Pol3F32 {
     for (int i = 0; i < cnt; ++i) {
       const float4* p = reinterpret_cast<const float4*>(t + i);
       const float4 A = p[0], B = p[1], C = p[2];
+      float mu[R], a0[R], a1[R], s[R], P[R], zr[R], zi[R];
+      bool all_hi = true, any_lo = false;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        face_common(q[r][0], q[r][1], q[r][2], A, B, C, mu[r], a0[r], a1[r], s[r], P[r]);
+        all_hi = all_hi && (P[r] < th.hi);
+        any_lo = any_lo || (P[r] < th.lo);
+      }
+      if (__all_sync(0xffffffffu, all_hi)) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) face_series(a0[r], a1[r], P[r], zr[r], zi[r]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) face_edge(q[r][0], q[r][1], q[r][2], A, B, C, a0[r], a1[r], zr[r], zi[r]);
+        if (any_lo) {
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            if (P[r] < th.lo) face_series(a0[r], a1[r], P[r], zr[r], zi[r]);
+        }
+      }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         float re, im;
-        face_pair_f32(q[r][0], q[r][1], q[r][2], A, B, C, th.hi, th.lo, re, im);
+        face_finish(mu[r], s[r], zr[r], zi[r], re, im);
         tre[r] += re;
         tim[r] += im;
       }
@@ -328,7 +374,7 @@ struct Pol3F64 {
 // after letting its copies in flight land (also bounded).
 // ---------------------------------------------------------------------------
 template <class Pol, int R, int NT>
-__global__ void __launch_bounds__(NT) k_fwd(const typename Pol::Item* __restrict__ items, int64_t n_items,
+__global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_fwd(const typename Pol::Item* __restrict__ items, int64_t n_items,
                                             int64_t per_split, const double* __restrict__ q, int64_t n_q,
                                             Thr th, double2* __restrict__ partial, uint32_t* status) {
   using Item = typename Pol::Item;
