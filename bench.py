@@ -34,11 +34,12 @@ METRIC = "G (Q,segment) pair-evals/s and % FP32/SFU roofline at stated error vs 
 UNIT = "Gpair/s"
 WORKLOAD = "icosphere8_perturbed_q128cubed"
 
-# Algorithmic per-pair instruction counts of the 3D FP32 face term (see the
-# face_pair_f32 formula): FP32-pipe operations (add/mul/fma/compare/round) and
-# SFU operations (sin, cos, reciprocal), per branch.
+# Algorithmic per-pair instruction counts of the 3D FP32 face term (face_common,
+# face_series / face_edge, face_finish in pft_fwd.cu): FP32-pipe operations
+# (add/mul/fma/compare/select, the SFU argument scaling) and SFU operations
+# (sin, cos, reciprocal), per branch.
 OPS_SERIES = {"fp32": 38, "sfu": 2}   # face-integral series (small phase spread)
-OPS_EDGE = {"fp32": 99, "sfu": 7}     # edge sum of Eq. 17, polynomial sinc
+OPS_EDGE = {"fp32": 93, "sfu": 7}     # edge sum of Eq. 17, polynomial sinc
 FP32_LANES, SFU_LANES = 128, 16       # per SM per clock
 
 
@@ -54,8 +55,8 @@ def parse():
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="c5",
                    help="c5: the benchmark workload; c5small: same mesh family at subdivision 6 on 64^3 Q "
                         "(for profiling captures)")
-    p.add_argument("--q-per-thread", type=int, default=0)
-    p.add_argument("--block-threads", type=int, default=0)
+    p.add_argument("--q-per-thread", type=int, default=2)
+    p.add_argument("--block-threads", type=int, default=256)
     p.add_argument("--tau", type=float, default=0.0, help="face_series_tau (0 = library default)")
     return p.parse_args()
 
@@ -92,19 +93,24 @@ def peaks():
         return {"sm_max_mhz": 2070.0}, "fallback"
 
 
-def branch_mix(v, f, q, tau=1.0, tau_lo=0.05, n_warps=4096, seed=0):
+def branch_mix(v, f, q, tau=1.0, r=2, nt=256, tau_lo=0.05, n_warps=4096, seed=0):
     """Fraction of (Q, face) pairs the kernel evaluates with the series branch.
 
-    Mirrors the kernel's rule on a seeded sample: a warp covers 32 consecutive Q
-    indices against one face; a lane takes the series if all 32 lanes have
-    P < tau^2/4, or if its own P < tau_lo^2/4.
+    Mirrors the kernel's rule on a seeded sample: for one face, a warp holds the
+    Q indices base + k*nt + 32*w + lane (k < r, lane < 32); all of them take the
+    series if every one has P < tau^2/4, otherwise only those with P < tau_lo^2/4.
     """
     rng = np.random.default_rng(seed)
     fi = rng.integers(0, f.shape[0], n_warps)
-    q0 = 32 * rng.integers(0, q.shape[0] // 32, n_warps)
+    per_block = r * nt
+    base = per_block * rng.integers(0, max(1, q.shape[0] // per_block), n_warps)
+    w = rng.integers(0, nt // 32, n_warps)
+    idx = (base[:, None, None] + np.arange(r)[None, :, None] * nt + 32 * w[:, None, None]
+           + np.arange(32)[None, None, :]).reshape(n_warps, -1)
+    idx = np.minimum(idx, q.shape[0] - 1)
     p = v.astype(np.float64)[f[fi]]                      # [w, 3, 3]
     g = p.mean(axis=1)
-    qq = q[q0[:, None] + np.arange(32)[None, :]]         # [w, 32, 3]
+    qq = q[idx]                                          # [w, r*32, 3]
     a0 = np.einsum("wlj,wj->wl", qq, p[:, 0] - g)
     a1 = np.einsum("wlj,wj->wl", qq, p[:, 1] - g)
     P = a0 * a0 + a0 * a1 + a1 * a1
@@ -333,7 +339,7 @@ def main():
         pk, pk_kind = peaks()
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         clk_max = float(pk.get("sm_max_mhz", 2070.0))
-        mix = branch_mix(v, f, q, tau=args.tau or 1.0)
+        mix = branch_mix(v, f, q, tau=args.tau or 1.0, r=args.q_per_thread, nt=args.block_threads)
         ops, issue, achieved, peak_ops = roofline(pairs, ms_main / 1e3, mix, n_sm, clk_max)
         value = world * pairs / (ms_step / 1e3) / 1e9
         line = {
@@ -342,7 +348,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload][0], "faces": int(f.shape[0]),
                        "q_points": int(q.shape[0]), "pairs_per_step": pairs,
-                       "launch": {"q_per_thread": opts.q_per_thread or 4, "block_threads": opts.block_threads or 256,
+                       "launch": {"q_per_thread": args.q_per_thread, "block_threads": args.block_threads,
                                   "face_series_tau": opts.face_series_tau or 1.0}, "edge_terms_per_step": 3 * pairs,
                        "l2": "flushed between steps (512 MB write outside the step events)",
                        "parallelism": f"independent replicas x{world}" if world > 1 else "single GPU",
@@ -350,7 +356,7 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Tops/s", "frac": achieved / peak_ops,
                          "traffic": traffic_from_profile(),
-                         "kernel": f"k_fwd<Pol3F32,{opts.q_per_thread or 4},{opts.block_threads or 256}>",
+                         "kernel": f"k_fwd<Pol3F32,{args.q_per_thread},{args.block_threads}>",
                          "main_kernel_ms": ms_main,
                          "peak_basis": f"{n_sm} SMs x 128 FP32/SFU issue slots x {clk_max:.0f} MHz "
                                        f"({pk_kind} max SM clock)",
