@@ -39,7 +39,7 @@ WORKLOAD = "icosphere8_perturbed_q128cubed"
 # (add/mul/fma/compare/select, the SFU argument scaling) and SFU operations
 # (sin, cos, reciprocal), per branch.
 OPS_SERIES = {"fp32": 38, "sfu": 2}   # face-integral series (small phase spread)
-OPS_EDGE = {"fp32": 93, "sfu": 7}     # edge sum of Eq. 17, polynomial sinc
+OPS_EDGE = {"fp32": 93, "sfu": 7}     # edge sum of Eq. 14, polynomial sinc
 FP32_LANES, SFU_LANES = 128, 16       # per SM per clock
 
 

@@ -4,9 +4,9 @@
  *
  * Method: B. B. Maranville, "An implementation of an efficient direct Fourier
  * transform of polygonal areas and volumes", arXiv 2104.08309.
- *   FT(Q) = integral over the region of exp(+i Q.r) dA (2D) or dV (3D)  (Sec. 2, Sec. 3 Eq. 9)
- * evaluated by the divergence theorem (Eq. 1, Eq. 10) as a sum over boundary
- * segments (2D, Eq. 7) or over faces and their edges (3D, Eq. 17 with the overall
+ *   FT(Q) = integral over the region of exp(+i Q.r) dA (2D) or dV (3D)  (Sec. 2, Sec. 3 Eq. 7)
+ * evaluated by the divergence theorem (Eq. 1, Eq. 8) as a sum over boundary
+ * segments (2D, Eq. 6) or over faces and their edges (3D, Eq. 14 with the overall
  * sign fixed so that FT(0) = +volume for outward faces).  Q carries no 2 pi.
  *
  * Conventions shared by every call
@@ -70,7 +70,7 @@ typedef enum {
  *  face_series_tau  3D only: faces whose corner phases satisfy
  *                   P = (a0^2 + a1^2 + a2^2)/2 < tau^2/4 (a_k = Q.(p_k - centroid);
  *                   this implies max_l |Q.d_l| < tau) take the series of the face
- *                   integral (Eq. 14) instead of the edge sum of Eq. 17, which
+ *                   integral (Eq. 13) instead of the edge sum of Eq. 14, which
  *                   cancels there.  0 = default 1.0; must lie in (0, 1].
  *  main_start_event, main_stop_event
  *                   cudaEvent_t handles or NULL.  When set, they are recorded on
@@ -96,7 +96,7 @@ size_t pft2d_batched_workspace_size(int64_t n_verts, int64_t n_polys, int64_t n_
 size_t pft3d_workspace_size(int64_t n_verts, int64_t n_faces, int64_t n_q, const pft_options* opts);
 
 /*
- * 2D: FT_A(Q) of the region bounded by closed loops (Sec. 2, Eq. 7 per segment).
+ * 2D: FT_A(Q) of the region bounded by closed loops (Sec. 2, Eq. 6 per segment).
  *  verts     [n_verts][2] float32.  Loop l is verts[loop_off[l] .. loop_off[l+1]-1],
  *            its last vertex joined to its first.  CCW loops add area, CW loops
  *            subtract it (holes).
@@ -126,7 +126,7 @@ int pft2d_polygons_batched(const float* verts, int64_t n_verts, const int64_t* p
                            void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
 
 /*
- * 3D: FT_V(Q) of a closed surface of triangles (Sec. 3, Eq. 17 sign-corrected).
+ * 3D: FT_V(Q) of a closed surface of triangles (Sec. 3, Eq. 14 sign-corrected).
  *  verts  [n_verts][3] float32.
  *  faces  [n_faces][3] int32, 0-based, each triangle counter-clockwise seen from
  *         outside (outward normal).  Out-of-range indices set PFT_ERR_INDEX_RANGE

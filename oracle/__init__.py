@@ -7,7 +7,7 @@ shares no code with the CUDA path.
 
 The arithmetic lives in ``pft_oracle.c`` (plain C99, FP64, OpenMP over Q or
 faces); this module compiles it with gcc on first use and wraps it with ctypes.
-Sign convention: FT(Q) = integral of exp(+i Q.r) over the region (Sec. 2, Eq. 9).
+Sign convention: FT(Q) = integral of exp(+i Q.r) over the region (Sec. 2, Eq. 7).
 """
 from __future__ import annotations
 
@@ -87,7 +87,7 @@ def _loops(verts, loop_off):
 
 
 def ft2d(verts, q, loop_off=None, threads=None) -> np.ndarray:
-    """FT_A(Q) of the region bounded by CCW loops (Eq. 7 summed over segments)."""
+    """FT_A(Q) of the region bounded by CCW loops (Eq. 6 summed over segments)."""
     v, off = _loops(verts, loop_off)
     q = _f64(q, 2)
     out = np.empty((q.shape[0], 2))
@@ -97,7 +97,7 @@ def ft2d(verts, q, loop_off=None, threads=None) -> np.ndarray:
 
 
 def seg_terms2d(verts, qxy, loop_off=None) -> np.ndarray:
-    """The individual segment terms of Eq. 5/7 at one Q (their sum is FT_A)."""
+    """The individual segment terms of Eq. 4/6 at one Q (their sum is FT_A)."""
     v, off = _loops(verts, loop_off)
     out = np.empty((v.shape[0], 2))
     _load().orc_seg_terms2d(_ptr(v, _dp), _ptr(off, _i64p), off.size - 1, float(qxy[0]),
@@ -131,7 +131,7 @@ def _mesh(verts, faces):
 
 
 def ft3d(verts, faces, q, threads=None) -> np.ndarray:
-    """FT_V(Q) of a closed outward-oriented triangle surface (sign-corrected Eq. 17)."""
+    """FT_V(Q) of a closed outward-oriented triangle surface (sign-corrected Eq. 14)."""
     v, f = _mesh(verts, faces)
     q = _f64(q, 3)
     out = np.empty((q.shape[0], 2))
@@ -143,7 +143,7 @@ def ft3d(verts, faces, q, threads=None) -> np.ndarray:
 
 
 def face_terms3d(verts, faces, Q) -> np.ndarray:
-    """The per-face terms I_m of Eq. 17 (sign-corrected) at one Q != 0."""
+    """The per-face terms I_m of Eq. 14 (sign-corrected) at one Q != 0."""
     v, f = _mesh(verts, faces)
     Q = _f64(Q).reshape(3)
     out = np.empty((f.shape[0], 2))

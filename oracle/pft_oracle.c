@@ -7,7 +7,7 @@
  * check and the benchmark's CPU-baseline leg load it; the library itself never
  * does, and the two share no code.
  *
- * Convention (Sec. 2, Eq. 9): FT(Q) = integral over the region of exp(+i Q.r),
+ * Convention (Sec. 2, Eq. 7): FT(Q) = integral over the region of exp(+i Q.r),
  * with no 2 pi in the exponent.  Loops are counter-clockwise for positive area;
  * triangles are counter-clockwise seen from outside (outward normal).
  *
@@ -59,7 +59,7 @@ static void init_tables(void) {
   inv_fact_ready = 1;
 }
 
-/* sinc(u) = sin(u)/u, unnormalised, as in the midpoint form of Eq. 7 (Sec. 2). */
+/* sinc(u) = sin(u)/u, unnormalised, as in the midpoint form of Eq. 6 (Sec. 2). */
 static double sinc(double u) {
   if (fabs(u) < TAU_SINC) { double u2 = u * u; return 1.0 - u2 / 6.0 * (1.0 - u2 / 20.0 * (1.0 - u2 / 42.0)); }
   return sin(u) / u;
@@ -108,9 +108,9 @@ static double area2d(const double* v, const int64_t* off, int64_t nl) {
 }
 
 /*
- * Segment term of Eq. 7 (Sec. 2): for p0 -> p1, Delta = p1 - p0,
+ * Segment term of Eq. 6 (Sec. 2): for p0 -> p1, Delta = p1 - p0,
  *   T = -i (Qx Dy - Qy Dx) exp(iQ.(p0+p1)/2) sinc(Q.Delta/2)      (times 1/|Q|^2)
- * which equals the exponential-difference form of Eq. 5 segment by segment.
+ * which equals the exponential-difference form of Eq. 4 segment by segment.
  * Returned without the 1/|Q|^2 factor.
  */
 static double complex seg_term(double qx, double qy, double x0, double y0, double x1, double y1) {
@@ -166,7 +166,7 @@ int orc_ft2d(const double* verts, const int64_t* loop_off, int64_t n_loops,
   return 0;
 }
 
-/* Per-segment terms of Eq. 5/7 (with the 1/|Q|^2 factor) at one Q; out[n_seg][2]. */
+/* Per-segment terms of Eq. 4/6 (with the 1/|Q|^2 factor) at one Q; out[n_seg][2]. */
 int orc_seg_terms2d(const double* verts, const int64_t* loop_off, int64_t n_loops,
                     double qx, double qy, double* out) {
   double q2 = qx * qx + qy * qy;
@@ -212,18 +212,18 @@ static void cross3(const double* a, const double* b, double* c) {
 static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
 /*
- * One face's term I_m of Eq. 17 with the sign fixed (Sec. 3, Eqs. 12-17).
+ * One face's term I_m of Eq. 14 with the sign fixed (Sec. 3, Eqs. 11-14).
  * With N = (p1-p0) x (p2-p0) (|N| = 2 area, along the outward normal),
  * s = Q.N, X = N x Q (|X| = |N| |Q_perp|), d_l = p_{l+1} - p_l (wrapping):
  *   I_m = -s / (|Q|^2 |X|^2) * sum_l Q.(d_l x N) exp(iQ.(p_l+p_{l+1})/2) sinc(Q.d_l/2)
- * which is Eq. 14 (face factor -i Q_par/Q^2 exp(i Q_par r_par) times the in-plane
- * 2D transform) with the in-plane transform taken from Eq. 7.  As printed, Eq. 17
+ * which is Eq. 13 (face factor -i Q_par/Q^2 exp(i Q_par r_par) times the in-plane
+ * 2D transform) with the in-plane transform taken from Eq. 6.  As printed, Eq. 14
  * has the opposite overall sign; this sign reproduces the prism face values of
  * Sec. 4.2 and gives FT(0) = +volume for outward faces.
  *
  * When the face's phase spread max_l |Q.d_l| is below TAU_FACE the edge sum
  * cancels (it is O(|Q_perp| L) relative to its terms) and is undefined for
- * Q parallel to N; there Eq. 14 is evaluated directly, the in-face integral of
+ * Q parallel to N; there Eq. 13 is evaluated directly, the in-face integral of
  * exp(iQ.r) coming from the simplex series:  I_m = -i s exp(i mu) G(a) / |Q|^2,
  * mu = mean_k Q.p_k, a_k = Q.p_k - mu, G = sum_k i^k h_k(a)/(k+2)!.
  * Returned without the 1/|Q|^2 factor.

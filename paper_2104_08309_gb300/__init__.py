@@ -76,7 +76,7 @@ def _ws(nbytes, device, ws):
 
 def pft2d_polygons(verts, q, loop_off=None, *, options=None, out=None, ws=None, stream=None,
                    check_status=False):
-    """FT_A(Q) of the region bounded by closed loops (Eq. 7).  Returns float64 [n_q, 2]."""
+    """FT_A(Q) of the region bounded by closed loops (Eq. 6).  Returns float64 [n_q, 2]."""
     torch = _torch()
     v = _dev(verts, torch.float32, "verts", 2)
     qq = _dev(q, torch.float64, "q", 2)
@@ -135,7 +135,7 @@ def pft2d_polygons_batched(verts, poly_off, q, q_off=None, *, options=None, out=
 
 
 def pft3d_mesh(verts, faces, q, *, options=None, out=None, ws=None, stream=None, check_status=False):
-    """FT_V(Q) of a closed outward triangle surface (Eq. 17, sign-corrected).  Returns float64 [n_q, 2]."""
+    """FT_V(Q) of a closed outward triangle surface (Eq. 14, sign-corrected).  Returns float64 [n_q, 2]."""
     torch = _torch()
     v = _dev(verts, torch.float32, "verts", 3)
     f = _dev(faces, torch.int32, "faces", 3)

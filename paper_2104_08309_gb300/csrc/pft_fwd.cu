@@ -32,7 +32,7 @@ constexpr int kMinBlocks = sizeof(typename Pol::QT) == 8 ? 1 : (NT == 256 ? 1 : 
 // Per-pair arithmetic.
 // ---------------------------------------------------------------------------
 
-// 2D, Eq. 7 (Sec. 2): the segment p0 -> p1 contributes
+// 2D, Eq. 6 (Sec. 2): the segment p0 -> p1 contributes
 //   -i (Qx Dy - Qy Dx) sinc(Q.D/2) exp(iQ.m)           (times 1/|Q|^2, applied later)
 // Records hold m and D/2, so w below is half the cross product; the factor 2
 // and 1/|Q|^2 are applied in FP64 by the finalize kernel.
@@ -70,7 +70,7 @@ __device__ __forceinline__ void seg_pair_f64(double qx, double qy, const Seg64& 
   im = -ws * cs;
 }
 
-// 3D, Eq. 17 with the sign fixed (Sec. 3).  With X = N x Q, s = Q.N and the
+// 3D, Eq. 14 with the sign fixed (Sec. 3).  With X = N x Q, s = Q.N and the
 // corner phases a_k = Q.(p_k - centroid) (a_0 + a_1 + a_2 = 0), a face gives
 //   |Q|^2 I_m = -s exp(i mu) Z,     mu = Q.centroid,
 //   Z = (1/|X|^2) sum_l w_l sinc(u_l) exp(i psi_l)         (edge sum)
@@ -78,7 +78,7 @@ __device__ __forceinline__ void seg_pair_f64(double qx, double qy, const Seg64& 
 // u_l = (a_{l+1} - a_l)/2 and psi_l = (a_l + a_{l+1})/2 = -a_{l+2}/2.
 // The edge sum cancels to O(spread) of its terms when the phase spread of the
 // face is small (it is 0/0 for Q parallel to N); there the same face integral
-// (Eq. 14) is taken from its series, Z = i G,
+// (Eq. 13) is taken from its series, Z = i G,
 //   G = sum_k i^k h_k(a) / (k+2)!,   h_k = P h_{k-2} + T h_{k-3},
 // P = a0^2 + a0 a1 + a1^2 (= h_2), T = a0 a1 a2 (= h_3), kept through k = 8;
 // P < tau^2/4 implies max_l |Q.d_l| < tau <= 1, where the omitted terms are
@@ -116,7 +116,7 @@ __device__ __forceinline__ void face_series(float a0, float a1, float P, float& 
   zi = gre;
 }
 
-// Z from the edge sum of Eq. 17.
+// Z from the edge sum of Eq. 14.
 __device__ __forceinline__ void face_edge(float qx, float qy, float qz, const float4 A, const float4 B,
                                           const float4 C, float a0, float a1, float& zr, float& zi) {
   const float nx = C.y, ny = C.z, nz = C.w;

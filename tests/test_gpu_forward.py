@@ -86,7 +86,7 @@ def test_3d_box_normals_and_limits(torch_dev, prec):
 
 @pytest.mark.parametrize("tau", [1e-3, 0.25, 1.0])
 def test_3d_face_branch_threshold(torch_dev, tau, rng):
-    """Both per-face branches (edge sum of Eq. 17, series of Eq. 14) agree with the oracle."""
+    """Both per-face branches (edge sum of Eq. 14, series of Eq. 13) agree with the oracle."""
     v, f = synth.perturbed_icosphere(3, seed=5, amp=0.05)
     q = _q3_mix(rng, 1500, 40.0)
     ref = oracle.ft3d(v, f, q)

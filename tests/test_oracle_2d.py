@@ -1,6 +1,6 @@
 """Pins of the 2D oracle against what the paper and the mathematics fix.
 
-Each test checks oracle.ft2d (Eq. 7 summed over CCW segments, Sec. 2) against
+Each test checks oracle.ft2d (Eq. 6 summed over CCW segments, Sec. 2) against
 something it does not compute itself: the paper's rectangle worked example
 (Sec. 4.1), brute-force quadrature, the disc limit, exact invariances and the
 Q -> 0 limit.
@@ -35,7 +35,7 @@ def test_rectangle_closed_form(rng):
 
 
 def test_rectangle_edge_terms_match_paper():
-    """The four segment terms printed in Sec. 4.1 (exponential-difference form, Eq. 5)."""
+    """The four segment terms printed in Sec. 4.1 (exponential-difference form, Eq. 4)."""
     a, b = A, B
     for qx, qy in [(0.7, -1.3), (3.0, 2.0), (-5.5, 0.25)]:
         q2 = qx * qx + qy * qy

@@ -1,6 +1,6 @@
 """Pins of the 3D oracle against what the paper and the mathematics fix.
 
-oracle.ft3d sums the sign-corrected Eq. 17 (Sec. 3) over the faces of a closed
+oracle.ft3d sums the sign-corrected Eq. 14 (Sec. 3) over the faces of a closed
 outward triangle mesh.  It is checked against the prism closed form and the
 prism face values of Sec. 4.2, the sphere closed form of Sec. 4.3 (convergence
 under refinement), brute-force tetrahedral quadrature (including the paper's own
@@ -188,7 +188,7 @@ def test_branches_agree_at_the_same_q():
         for eps in (0.9e-2, 1.1e-2, 0.5e-2, 2e-2):
             Q = np.array([eps, 0.0, qz])
             term = oracle.face_terms3d(p, tri, Q)[0]
-            # direct quadrature of the face integral of Eq. 14 with -i Q_par/|Q|^2
+            # direct quadrature of the face integral of Eq. 13 with -i Q_par/|Q|^2
             l1, l2, w = quad.tri_rule(20)
             pts = l1[:, None] * p[1] + l2[:, None] * p[2]
             integral = np.sum(w * np.exp(1j * pts @ Q))     # area 1/2 * 2 = weights sum 1/2
