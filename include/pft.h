@@ -47,7 +47,8 @@ typedef enum {
   PFT_ERR_CUDA = 5,          /* a CUDA launch or copy failed                      */
   PFT_ERR_TIMEOUT = 6,       /* a bounded wait on a copy gave up (status word)    */
   PFT_ERR_UNSUPPORTED = 7,   /* option combination not implemented                */
-  PFT_ERR_OFFSETS = 8        /* CSR offsets not non-decreasing / inconsistent     */
+  PFT_ERR_OFFSETS = 8,       /* CSR offsets not non-decreasing / inconsistent     */
+  PFT_ERR_SCRATCH_LIMIT = 9  /* problem too large for pft3d_mesh_noalloc's scratch */
 } pft_status_code;
 
 typedef enum {
@@ -152,6 +153,29 @@ int pft2d_polygons_backward(const float* verts, int64_t n_verts, const int64_t* 
 int pft3d_mesh_backward(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces,
                         const double* q, int64_t n_q, const double* grad_out, float* grad_verts,
                         void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
+
+/*
+ * pft3d_mesh without a workspace argument, for callers that cannot allocate
+ * device memory when they need a transform: code running while a stream is
+ * captured into a CUDA graph, plug-ins whose host application owns all device
+ * allocations, loops that forbid allocation after start-up.  (The paper has no
+ * counterpart; this is a calling convenience.)
+ *  - Same arguments, result and options as pft3d_mesh, minus ws / ws_bytes.
+ *    It allocates nothing and calls no allocating routine.
+ *  - Scratch is a file-scope device array of 32 MiB, which every GPU that loads
+ *    the library keeps until the process exits.  Problems whose
+ *    pft3d_workspace_size() exceeds 32 MiB return PFT_ERR_SCRATCH_LIMIT at once.
+ *  - All calls on a device share that array and it keeps the last call's
+ *    contents; calls whose GPU work overlaps (several streams or host threads)
+ *    race on it, so serialise them.
+ *  - The first call on each device looks up the array's address (with that
+ *    device current); make it before any stream capture begins.
+ *  - Device-detected input errors are recorded in the shared scratch, which
+ *    callers cannot read: validate indices and coordinates beforehand, or use
+ *    pft3d_mesh and pft_status() where that matters.
+ */
+int pft3d_mesh_noalloc(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces,
+                       const double* q, int64_t n_q, double* out, const pft_options* opts, void* stream);
 
 /*
  * Device-detected status of the last call that used `ws`: synchronises `stream`,

@@ -20,7 +20,8 @@ from ._capi import (PFT_FP32_COMPENSATED, PFT_FP64, Options, PFTError, check, lo
 
 __all__ = [
     "pft2d_polygons", "pft2d_polygons_batched", "pft3d_mesh", "pft2d_polygons_backward",
-    "pft3d_mesh_backward", "pft_status", "ft2d", "ft3d", "make_options", "Options", "PFTError",
+    "pft3d_mesh_backward", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft3d", "make_options", "Options",
+    "PFTError",
     "launch_count", "version",
 ]
 
@@ -151,6 +152,29 @@ def pft3d_mesh(verts, faces, q, *, options=None, out=None, ws=None, stream=None,
                          ws.numel(), ctypes.byref(o), st), "pft3d_mesh")
     if check_status:
         check(lib.pft_status(ws.data_ptr(), st), "pft3d_mesh (device status)")
+    return out
+
+
+def pft3d_mesh_noalloc(verts, faces, q, out, *, options=None, stream=None):
+    """pft3d_mesh with the library's fixed 32 MiB device scratch instead of a workspace.
+
+    For callers that must not allocate at call time (stream capture, host
+    applications that own all device memory): ``out`` ([n_q, 2] float64, CUDA)
+    is required and nothing is allocated here or in the library.  Calls whose
+    GPU work overlaps share the scratch and race; the first call on a device
+    must come before any stream capture.
+    """
+    torch = _torch()
+    v = _dev(verts, torch.float32, "verts", 3)
+    f = _dev(faces, torch.int32, "faces", 3)
+    qq = _dev(q, torch.float64, "q", 3)
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64
+            and out.is_contiguous() and out.shape == (qq.shape[0], 2)):
+        raise ValueError("out must be a contiguous CUDA float64 tensor of shape [n_q, 2]")
+    o = make_options(options)
+    check(load().pft3d_mesh_noalloc(v.data_ptr(), v.shape[0], f.data_ptr(), f.shape[0], qq.data_ptr(),
+                                    qq.shape[0], out.data_ptr(), ctypes.byref(o), _stream(stream, v.device)),
+          "pft3d_mesh_noalloc")
     return out
 
 

@@ -50,6 +50,7 @@ SIGNATURES = {
     "pft3d_backward_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_vp]),
     "pft2d_polygons_backward": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp, c_size,
                                                c_vp, c_vp]),
+    "pft3d_mesh_noalloc": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp]),
     "pft3d_mesh_backward": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp, c_size,
                                            c_vp, c_vp]),
     "pft_status": (ctypes.c_int, [c_vp, c_vp]),

@@ -245,6 +245,7 @@ const char* pft_status_string(int code) {
     case PFT_ERR_TIMEOUT: return "bounded wait on a bulk copy timed out";
     case PFT_ERR_UNSUPPORTED: return "unsupported option combination";
     case PFT_ERR_OFFSETS: return "malformed CSR offsets";
+    case PFT_ERR_SCRATCH_LIMIT: return "problem exceeds the 32 MiB static scratch of pft3d_mesh_noalloc";
     default: return "unknown status code";
   }
 }
