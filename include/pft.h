@@ -92,8 +92,6 @@ typedef struct {
 
 /* Bytes of workspace the matching call needs for these sizes and options. */
 size_t pft2d_workspace_size(int64_t n_verts, int64_t n_loops, int64_t n_q, const pft_options* opts);
-size_t pft2d_batched_workspace_size(int64_t n_verts, int64_t n_polys, int64_t n_q,
-                                    const int64_t* q_off_host, const pft_options* opts);
 size_t pft3d_workspace_size(int64_t n_verts, int64_t n_faces, int64_t n_q, const pft_options* opts);
 
 /*
@@ -110,21 +108,44 @@ int pft2d_polygons(const float* verts, int64_t n_verts, const int64_t* loop_off,
                    void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
 
 /*
- * Batched 2D: one FT_A per polygon, all polygons in one persistent launch.
- *  verts     [n_verts][2] float32; polygon i is verts[poly_off[i] .. poly_off[i+1]-1] (one CCW loop).
- *  poly_off  [n_polys+1] int64 device array.
- *  q         float64 Q points.  With q_off == NULL every polygon uses all n_q
- *            points and out is [n_polys][n_q][2]; otherwise polygon i uses
- *            q[q_off[i] .. q_off[i+1]-1] and out is [n_q][2] in the same order.
- *  q_off     [n_polys+1] int64 DEVICE array or NULL.
- *  poly_off_host, q_off_host: the same offsets in HOST memory (used to build the
- *            cost-sorted static work list on the host; q_off_host NULL iff q_off NULL).
+ * Batched 2D: one FT_A per polygon (Sec. 2, Eq. 6 per segment), thousands of
+ * polygons of uneven sizes in one persistent launch.  Two steps:
+ *
+ * 1. pft2d_batched_prepare (host work + copies; synchronises `stream`; not for
+ *    use inside stream capture): cuts every polygon into work items (polygon,
+ *    segment chunk of <= 4096, Q tile), sorts them by cost and deals them to the
+ *    persistent blocks longest-first onto the least-loaded block, then copies that
+ *    static schedule into `ws` and fills `plan` (a small host struct the caller
+ *    keeps).  Redo it whenever the offsets, n_q or the options change.
+ * 2. pft2d_polygons_batched (kernel launches only, so a CUDA graph can capture
+ *    and replay it): runs the prepared schedule on the current vertices and Q.
+ *
+ *  verts        [n_verts][2] float32; polygon i is one CCW loop
+ *               verts[poly_off[i] .. poly_off[i+1]-1].
+ *  poly_off     [n_polys+1] int64: HOST copy for prepare, DEVICE copy for the call
+ *               (the device checks that it matches the plan -> PFT_ERR_OFFSETS).
+ *  q, q_off     float64 Q points.  With q_off == NULL every polygon uses all n_q
+ *               points and out is [n_polys][n_q][2]; otherwise polygon i uses
+ *               q[q_off[i] .. q_off[i+1]-1] and out is [n_q][2] in the same order
+ *               (q_off: HOST copy for prepare, DEVICE copy for the call).
+ *  opts         precision, q_per_thread, block_threads (k_splits, tile_items 0).
+ * Workspace size from pft2d_batched_workspace_size (same host arguments).
  */
-int pft2d_polygons_batched(const float* verts, int64_t n_verts, const int64_t* poly_off,
-                           const int64_t* poly_off_host, int64_t n_polys,
-                           const double* q, const int64_t* q_off, const int64_t* q_off_host,
-                           int64_t n_q, double* out,
-                           void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
+typedef struct {
+  int64_t opaque[24];
+} pft_batched_plan;
+
+size_t pft2d_batched_workspace_size(int64_t n_verts, const int64_t* poly_off_host, int64_t n_polys,
+                                    const int64_t* q_off_host, int64_t n_q, const pft_options* opts);
+int pft2d_batched_prepare(const int64_t* poly_off_host, int64_t n_polys, const int64_t* q_off_host, int64_t n_q,
+                          void* ws, size_t ws_bytes, const pft_options* opts, pft_batched_plan* plan,
+                          void* stream);
+int pft2d_polygons_batched(const float* verts, int64_t n_verts, const int64_t* poly_off, int64_t n_polys,
+                           const double* q, const int64_t* q_off, int64_t n_q, double* out,
+                           void* ws, size_t ws_bytes, const pft_batched_plan* plan, void* stream);
+
+/* Kernel launches enqueued by the most recent pft2d_polygons_batched on this host thread. */
+int pft_batched_last_launch_count(void);
 
 /*
  * 3D: FT_V(Q) of a closed surface of triangles (Sec. 3, Eq. 14 sign-corrected).

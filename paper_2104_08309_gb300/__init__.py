@@ -15,11 +15,11 @@ from __future__ import annotations
 import ctypes
 
 from . import synth  # noqa: F401  (seeded inputs; no transform arithmetic)
-from ._capi import (PFT_FP32_COMPENSATED, PFT_FP64, Options, PFTError, check, load,  # noqa: F401
+from ._capi import (PFT_FP32_COMPENSATED, PFT_FP64, BatchedPlan, Options, PFTError, check, load,  # noqa: F401
                     status_string)
 
 __all__ = [
-    "pft2d_polygons", "pft2d_polygons_batched", "pft3d_mesh", "pft2d_polygons_backward",
+    "pft2d_polygons", "pft2d_batched_prepare", "pft2d_polygons_batched", "BatchedPrepared", "pft3d_mesh", "pft2d_polygons_backward",
     "pft3d_mesh_backward", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft3d", "make_options", "Options",
     "PFTError",
     "launch_count", "version",
@@ -98,40 +98,81 @@ def pft2d_polygons(verts, q, loop_off=None, *, options=None, out=None, ws=None, 
     return out
 
 
-def pft2d_polygons_batched(verts, poly_off, q, q_off=None, *, options=None, out=None, ws=None, stream=None,
+class BatchedPrepared:
+    """Workspace and schedule from pft2d_batched_prepare, reusable while the offsets stay the same."""
+
+    def __init__(self, ws, plan, n_verts, n_polys, n_q, shared):
+        self.ws, self.plan = ws, plan
+        self.n_verts, self.n_polys, self.n_q, self.shared = n_verts, n_polys, n_q, shared
+
+
+def _host_i64(x):
+    torch = _torch()
+    if isinstance(x, torch.Tensor):
+        return x.detach().to("cpu", torch.int64).contiguous()
+    return torch.as_tensor(x, dtype=torch.int64).contiguous()
+
+
+def pft2d_batched_prepare(poly_off, n_q, q_off=None, *, options=None, device=None, stream=None):
+    """Build the cost-sorted static schedule for a batch of polygons (host) and copy it to a new workspace.
+
+    Synchronises the stream; call it outside CUDA-graph capture.  The returned object is
+    passed to pft2d_polygons_batched as ``prepared``.
+    """
+    torch = _torch()
+    off_h = _host_i64(poly_off)
+    qo_h = None if q_off is None else _host_i64(q_off)
+    device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    o = make_options(options)
+    lib = load()
+    n_polys = off_h.numel() - 1
+    n_verts = int(off_h[-1]) if n_polys > 0 else 0
+    qo_ptr = None if qo_h is None else qo_h.data_ptr()
+    nb = lib.pft2d_batched_workspace_size(n_verts, off_h.data_ptr(), n_polys, qo_ptr, int(n_q), ctypes.byref(o))
+    if nb == 0:
+        raise ValueError("pft2d_batched_workspace_size rejected the offsets, sizes or options")
+    ws = torch.empty(int(nb), dtype=torch.uint8, device=device)
+    plan = BatchedPlan()
+    check(lib.pft2d_batched_prepare(off_h.data_ptr(), n_polys, qo_ptr, int(n_q), ws.data_ptr(), ws.numel(),
+                                    ctypes.byref(o), ctypes.byref(plan), _stream(stream, device)),
+          "pft2d_batched_prepare")
+    return BatchedPrepared(ws, plan, n_verts, n_polys, int(n_q), q_off is None)
+
+
+def pft2d_polygons_batched(verts, poly_off, q, q_off=None, *, prepared=None, options=None, out=None, stream=None,
                            check_status=False):
-    """One FT_A per polygon in one persistent launch.
+    """One FT_A per polygon (Eq. 6 per segment) in one persistent launch.
 
     With q_off None every polygon uses all Q and the result is [n_polys, n_q, 2];
     otherwise polygon i uses q[q_off[i]:q_off[i+1]] and the result is [n_q, 2].
+    Pass ``prepared`` (from pft2d_batched_prepare) to reuse a schedule; this call
+    then only launches kernels and can be captured into a CUDA graph.
     """
     torch = _torch()
     v = _dev(verts, torch.float32, "verts", 2)
     qq = _dev(q, torch.float64, "q", 2)
-    off_h = poly_off.detach().to("cpu", torch.int64).contiguous() if isinstance(poly_off, torch.Tensor) \
-        else torch.as_tensor(poly_off, dtype=torch.int64)
-    off_d = off_h.to(v.device)
-    qo_h = qo_d = None
+    if prepared is None:
+        prepared = pft2d_batched_prepare(poly_off, qq.shape[0], q_off, options=options, device=v.device,
+                                         stream=stream)
+    off_d = poly_off if (isinstance(poly_off, torch.Tensor) and poly_off.is_cuda) else \
+        _host_i64(poly_off).to(v.device)
+    off_d = _dev(off_d, torch.int64, "poly_off")
+    qo_d = None
     if q_off is not None:
-        qo_h = q_off.detach().to("cpu", torch.int64).contiguous() if isinstance(q_off, torch.Tensor) \
-            else torch.as_tensor(q_off, dtype=torch.int64)
-        qo_d = qo_h.to(v.device)
-    o = make_options(options)
-    lib = load()
-    nv, npoly, nq = v.shape[0], off_h.numel() - 1, qq.shape[0]
-    nb = lib.pft2d_batched_workspace_size(nv, npoly, nq, None if qo_h is None else qo_h.data_ptr(),
-                                          ctypes.byref(o))
-    ws = _ws(nb, v.device, ws)
+        qo_d = q_off if (isinstance(q_off, torch.Tensor) and q_off.is_cuda) else _host_i64(q_off).to(v.device)
+        qo_d = _dev(qo_d, torch.int64, "q_off")
+    npoly, nq = off_d.numel() - 1, qq.shape[0]
     n_out = npoly * nq if q_off is None else nq
     if out is None:
         out = torch.empty(n_out, 2, dtype=torch.float64, device=v.device)
     st = _stream(stream, v.device)
-    check(lib.pft2d_polygons_batched(v.data_ptr(), nv, off_d.data_ptr(), off_h.data_ptr(), npoly, qq.data_ptr(),
-                                     None if qo_d is None else qo_d.data_ptr(),
-                                     None if qo_h is None else qo_h.data_ptr(), nq, out.data_ptr(),
-                                     ws.data_ptr(), ws.numel(), ctypes.byref(o), st), "pft2d_polygons_batched")
+    lib = load()
+    check(lib.pft2d_polygons_batched(v.data_ptr(), v.shape[0], off_d.data_ptr(), npoly, qq.data_ptr(),
+                                     None if qo_d is None else qo_d.data_ptr(), nq, out.data_ptr(),
+                                     prepared.ws.data_ptr(), prepared.ws.numel(), ctypes.byref(prepared.plan), st),
+          "pft2d_polygons_batched")
     if check_status:
-        check(lib.pft_status(ws.data_ptr(), st), "pft2d_polygons_batched (device status)")
+        check(lib.pft_status(prepared.ws.data_ptr(), st), "pft2d_polygons_batched (device status)")
     return out.view(npoly, nq, 2) if q_off is None else out
 
 

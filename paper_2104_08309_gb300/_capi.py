@@ -40,11 +40,13 @@ class Options(ctypes.Structure):
 # name -> (restype, argtypes); exactly the entry points include/pft.h declares.
 SIGNATURES = {
     "pft2d_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_vp]),
-    "pft2d_batched_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_vp, c_vp]),
+    "pft2d_batched_workspace_size": (c_size, [c_i64, c_vp, c_i64, c_vp, c_i64, c_vp]),
+    "pft2d_batched_prepare": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_size, c_vp, c_vp, c_vp]),
+    "pft_batched_last_launch_count": (ctypes.c_int, []),
     "pft3d_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_vp]),
     "pft2d_polygons": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_size, c_vp, c_vp]),
-    "pft2d_polygons_batched": (ctypes.c_int, [c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, c_i64, c_vp,
-                                              c_vp, c_size, c_vp, c_vp]),
+    "pft2d_polygons_batched": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_size,
+                                              c_vp, c_vp]),
     "pft3d_mesh": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_size, c_vp, c_vp]),
     "pft2d_backward_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_vp]),
     "pft3d_backward_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_vp]),
@@ -61,6 +63,11 @@ SIGNATURES = {
 
 _lock = threading.Lock()
 _lib = None
+
+
+class BatchedPlan(ctypes.Structure):
+    """pft_batched_plan: opaque host-side handle filled by pft2d_batched_prepare."""
+    _fields_ = [("opaque", ctypes.c_int64 * 24)]
 
 
 class PFTError(RuntimeError):

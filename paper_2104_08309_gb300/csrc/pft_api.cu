@@ -201,13 +201,6 @@ int pft3d_mesh(const float* verts, int64_t n_verts, const int32_t* faces, int64_
   return PFT_OK;
 }
 
-size_t pft2d_batched_workspace_size(int64_t, int64_t, int64_t, const int64_t*, const pft_options*) { return 0; }
-int pft2d_polygons_batched(const float*, int64_t, const int64_t*, const int64_t*, int64_t, const double*,
-                           const int64_t*, const int64_t*, int64_t, double*, void*, size_t, const pft_options*,
-                           void*) {
-  g_last_launches = 0;
-  return PFT_ERR_UNSUPPORTED;
-}
 size_t pft2d_backward_workspace_size(int64_t, int64_t, int64_t, const pft_options*) { return 0; }
 size_t pft3d_backward_workspace_size(int64_t, int64_t, int64_t, const pft_options*) { return 0; }
 int pft2d_polygons_backward(const float*, int64_t, const int64_t*, int64_t, const double*, int64_t, const double*,

@@ -1,0 +1,667 @@
+// pft_batched.cu -- many polygons in one persistent launch (batched 2D).
+//
+// Host (pft2d_batched_prepare): every polygon i is cut into work items
+// (polygon, segment chunk, Q tile) whose cost is segments x Q points (+ a fixed
+// per-item charge for the finalize arithmetic).  Items are sorted by cost and
+// dealt to the G = SMs x resident-blocks persistent blocks, each to the least
+// loaded one so far (longest-processing-time first); every block gets a fixed
+// list, so the schedule, and with it every floating-point sum, is the same on
+// every call.  The plan is copied once into the workspace.
+//
+// Device (pft2d_polygons_batched, kernels only, so a CUDA graph can capture and
+// replay it): k_bprep builds per-polygon centres, areas and segment records;
+// k_batched walks each block's item list with the same bulk-copy ring as the
+// single-shape kernel (the tile stream runs across item boundaries) and
+// finishes single-chunk polygons in place; k_bfinal adds the chunk partials of
+// the rare multi-chunk polygons; k_bsmall redoes points with |Q| R < 0.25 in
+// FP64.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <queue>
+#include <vector>
+
+#include "pft_pairs.cuh"
+
+namespace pft {
+namespace {
+
+constexpr uint64_t kPlanMagic = 0x706674626174636bULL;   // "pftbatck"
+constexpr int64_t kChunk = 4096;                          // segments per item at most
+constexpr int kBThreads = 256;                            // prep / finalize block size
+
+struct BPlanHeader {
+  uint64_t magic;
+  int64_t n_polys, n_verts, n_q, n_items, n_cta, n_mc, part_rows, n_out;
+  int32_t r, nt, shared_q, fp64;
+  uint8_t pad[256 - 8 * 9 - 4 * 4];
+};
+static_assert(sizeof(BPlanHeader) == 256, "plan header is 256 bytes");
+
+struct PolyPlan {       // per polygon
+  int64_t seg_begin, q_begin, out_base, part_base;
+  int32_t n_seg, n_q, n_chunks, pad;
+};
+struct BItem {          // per work item
+  int32_t poly, chunk, qtile, pad;
+};
+struct PolyInfo {       // written by k_bprep
+  double cx, cy, area;
+  float rmax;
+  uint32_t pad;
+};
+
+struct BLayout {
+  size_t plan_hdr, cta_off, items, pplan, mc, info, segs, partial, small, total;
+};
+
+inline size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+BLayout layout(int64_t n_polys, int64_t n_verts, int64_t n_items, int64_t n_cta, int64_t n_mc, int64_t part_rows,
+               int64_t n_out, bool fp64) {
+  BLayout y{};
+  size_t o = al(sizeof(WsHeader));
+  y.plan_hdr = o; o = al(o + sizeof(BPlanHeader));
+  y.cta_off = o;  o = al(o + sizeof(int32_t) * (size_t)(n_cta + 1));
+  y.items = o;    o = al(o + sizeof(BItem) * (size_t)std::max<int64_t>(n_items, 1));
+  y.pplan = o;    o = al(o + sizeof(PolyPlan) * (size_t)std::max<int64_t>(n_polys, 1));
+  y.mc = o;       o = al(o + sizeof(int32_t) * (size_t)std::max<int64_t>(n_mc, 1));
+  y.info = o;     o = al(o + sizeof(PolyInfo) * (size_t)std::max<int64_t>(n_polys, 1));
+  y.segs = o;     o = al(o + (fp64 ? sizeof(Seg64) : sizeof(Seg32)) * (size_t)std::max<int64_t>(n_verts, 1));
+  y.partial = o;  o = al(o + sizeof(double2) * (size_t)std::max<int64_t>(part_rows, 1));
+  y.small = o;    o = al(o + sizeof(uint32_t) * (size_t)std::max<int64_t>(n_out, 1));
+  y.total = o;
+  return y;
+}
+
+template <typename T>
+T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(ws) + off); }
+
+// ---------------------------------------------------------------------------
+// Host plan.
+// ---------------------------------------------------------------------------
+struct HostPlan {
+  BPlanHeader h{};
+  std::vector<int32_t> cta_off;
+  std::vector<BItem> items;
+  std::vector<PolyPlan> pplan;
+  std::vector<int32_t> mc;
+};
+
+int resolve_batched(const pft_options* o, bool& fp64, int& r, int& nt) {
+  pft_options z;
+  std::memset(&z, 0, sizeof(z));
+  const pft_options& p = o ? *o : z;
+  if (p.precision != PFT_FP32_COMPENSATED && p.precision != PFT_FP64) return PFT_ERR_INVALID_ARG;
+  fp64 = p.precision == PFT_FP64;
+  r = p.q_per_thread ? p.q_per_thread : (fp64 ? 1 : 4);
+  nt = p.block_threads ? p.block_threads : 128;
+  const bool ok = fp64 ? (r == 1 || r == 2) : (r == 1 || r == 2 || r == 4 || r == 8);
+  if (!ok || (nt != 128 && nt != 256) || p.tile_items != 0 || p.k_splits != 0) return PFT_ERR_UNSUPPORTED;
+  return PFT_OK;
+}
+
+int batched_blocks_per_sm(bool fp64, int r, int nt);
+
+int build_plan(const int64_t* poly_off, int64_t n_polys, const int64_t* q_off, int64_t n_q,
+               const pft_options* opts, HostPlan& P) {
+  bool fp64;
+  int r, nt;
+  if (int e = resolve_batched(opts, fp64, r, nt)) return e;
+  if (n_polys < 0 || n_q < 0 || (n_polys > 0 && poly_off == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (n_polys > 0 && poly_off[0] != 0) return PFT_ERR_OFFSETS;
+  for (int64_t i = 0; i < n_polys; ++i)
+    if (poly_off[i + 1] < poly_off[i] || poly_off[i + 1] - poly_off[i] > INT32_MAX) return PFT_ERR_OFFSETS;
+  if (q_off) {
+    if (n_polys > 0 && (q_off[0] != 0 || q_off[n_polys] != n_q)) return PFT_ERR_OFFSETS;
+    for (int64_t i = 0; i < n_polys; ++i)
+      if (q_off[i + 1] < q_off[i] || q_off[i + 1] - q_off[i] > INT32_MAX) return PFT_ERR_OFFSETS;
+  } else if (n_q > INT32_MAX) {
+    return PFT_ERR_UNSUPPORTED;
+  }
+  const int64_t n_out = q_off ? n_q : n_polys * n_q;
+  if (n_out > (int64_t)UINT32_MAX) return PFT_ERR_UNSUPPORTED;
+  const int64_t qt = (int64_t)r * nt;
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t G = std::max(1, sms) * (int64_t)batched_blocks_per_sm(fp64, r, nt);
+
+  P.pplan.resize((size_t)n_polys);
+  std::vector<int64_t> cost;
+  int64_t part_rows = 0;
+  for (int64_t i = 0; i < n_polys; ++i) {
+    PolyPlan& pp = P.pplan[(size_t)i];
+    pp.seg_begin = poly_off[i];
+    pp.n_seg = (int32_t)(poly_off[i + 1] - poly_off[i]);
+    pp.q_begin = q_off ? q_off[i] : 0;
+    pp.n_q = (int32_t)(q_off ? q_off[i + 1] - q_off[i] : n_q);
+    pp.out_base = q_off ? q_off[i] : i * n_q;
+    pp.n_chunks = pp.n_seg > 0 ? (int32_t)((pp.n_seg + kChunk - 1) / kChunk) : 1;
+    pp.part_base = 0;
+    pp.pad = 0;
+    if (pp.n_chunks > 1) {
+      pp.part_base = part_rows;
+      part_rows += (int64_t)pp.n_chunks * pp.n_q;
+      P.mc.push_back((int32_t)i);
+    }
+    const int64_t n_qt = (pp.n_q + qt - 1) / qt;
+    for (int32_t c = 0; c < pp.n_chunks; ++c) {
+      const int64_t segs = std::min<int64_t>(kChunk, std::max<int64_t>(0, pp.n_seg - (int64_t)c * kChunk));
+      for (int64_t t = 0; t < n_qt; ++t) {
+        const int64_t nq = std::min<int64_t>(qt, pp.n_q - t * qt);
+        P.items.push_back(BItem{(int32_t)i, c, (int32_t)t, 0});
+        cost.push_back(nq * (segs + 64));   // pairs plus the per-Q finalize charge
+      }
+    }
+  }
+  // longest processing time first onto the least loaded block (ties: lowest index)
+  const int64_t n_items = (int64_t)P.items.size();
+  std::vector<int64_t> order((size_t)n_items);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+  using Slot = std::pair<int64_t, int64_t>;   // (load, block)
+  std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+  for (int64_t b = 0; b < G; ++b) heap.push({0, b});
+  std::vector<std::vector<int64_t>> lists((size_t)G);
+  for (int64_t k : order) {
+    Slot s = heap.top();
+    heap.pop();
+    lists[(size_t)s.second].push_back(k);
+    heap.push({s.first + cost[k], s.second});
+  }
+  std::vector<BItem> sorted;
+  sorted.reserve((size_t)n_items);
+  P.cta_off.assign((size_t)G + 1, 0);
+  for (int64_t b = 0; b < G; ++b) {
+    for (int64_t k : lists[(size_t)b]) sorted.push_back(P.items[(size_t)k]);
+    P.cta_off[(size_t)b + 1] = (int32_t)sorted.size();
+  }
+  P.items.swap(sorted);
+  std::memset(&P.h, 0, sizeof(P.h));
+  P.h.magic = kPlanMagic;
+  P.h.n_polys = n_polys;
+  P.h.n_verts = n_polys > 0 ? poly_off[n_polys] : 0;
+  P.h.n_q = n_q;
+  P.h.n_items = n_items;
+  P.h.n_cta = G;
+  P.h.n_mc = (int64_t)P.mc.size();
+  P.h.part_rows = part_rows;
+  P.h.n_out = n_out;
+  P.h.r = r;
+  P.h.nt = nt;
+  P.h.shared_q = q_off ? 0 : 1;
+  P.h.fp64 = fp64 ? 1 : 0;
+  return PFT_OK;
+}
+
+BLayout layout_of(const BPlanHeader& h) {
+  return layout(h.n_polys, h.n_verts, h.n_items, h.n_cta, h.n_mc, h.part_rows, h.n_out, h.fp64 != 0);
+}
+
+// ---------------------------------------------------------------------------
+// Device kernels.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double bsum(double x, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = x;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ float bminmax(float x, bool is_max, float* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = is_max ? fmaxf(x, y) : fminf(x, y);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = x;
+  __syncthreads();
+  float r = sh[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = is_max ? fmaxf(r, sh[w]) : fminf(r, sh[w]);
+  __syncthreads();
+  return r;
+}
+
+// One block per polygon: plan check, bounding-box centre, records, FP64 area, max radius.
+template <bool FP64>
+__global__ void __launch_bounds__(kBThreads) k_bprep(const float* __restrict__ v, const int64_t* __restrict__ poly_off,
+                                                     const BPlanHeader* ph, const PolyPlan* __restrict__ pplan,
+                                                     PolyInfo* info, void* segs, WsHeader* h) {
+  __shared__ double shd[kBThreads / 32];
+  __shared__ float shf[kBThreads / 32];
+  const int64_t i = blockIdx.x;
+  const PolyPlan pp = pplan[i];
+  const int64_t s0 = poly_off[i], s1 = poly_off[i + 1];
+  if (threadIdx.x == 0 && (s0 != pp.seg_begin || s1 - s0 != pp.n_seg || ph->magic != kPlanMagic))
+    set_status(&h->status, ST_OFFSETS);   // offsets differ from the prepared plan
+  const int64_t n = min((int64_t)pp.n_seg, max((int64_t)0, s1 - s0));
+  float mn[2] = {3.4e38f, 3.4e38f}, mx[2] = {-3.4e38f, -3.4e38f};
+  bool bad = false;
+  for (int64_t j = threadIdx.x; j < n; j += kBThreads)
+    for (int d = 0; d < 2; ++d) {
+      const float x = v[2 * (pp.seg_begin + j) + d];
+      if (!isfinite(x)) { bad = true; continue; }
+      mn[d] = fminf(mn[d], x);
+      mx[d] = fmaxf(mx[d], x);
+    }
+  if (bad) set_status(&h->status, ST_NONFINITE);
+  double c[2];
+  for (int d = 0; d < 2; ++d) {
+    const float lo = bminmax(mn[d], false, shf), hi = bminmax(mx[d], true, shf);
+    c[d] = (n > 0 && lo <= hi) ? 0.5 * ((double)lo + (double)hi) : 0.0;
+  }
+  double area = 0.0;
+  float rm = 0.f;
+  for (int64_t j = threadIdx.x; j < n; j += kBThreads) {
+    const int64_t a = pp.seg_begin + j, b = pp.seg_begin + (j + 1 < n ? j + 1 : 0);
+    const double x0 = (double)v[2 * a] - c[0], y0 = (double)v[2 * a + 1] - c[1];
+    const double x1 = (double)v[2 * b] - c[0], y1 = (double)v[2 * b + 1] - c[1];
+    const double mxd = 0.5 * (x0 + x1), myd = 0.5 * (y0 + y1), hx = 0.5 * (x1 - x0), hy = 0.5 * (y1 - y0);
+    area += 0.5 * (x0 * y1 - x1 * y0);
+    rm = fmaxf(rm, __double2float_ru(sqrt(x0 * x0 + y0 * y0)));
+    if (FP64) reinterpret_cast<Seg64*>(segs)[a] = Seg64{mxd, myd, hx, hy};
+    else reinterpret_cast<Seg32*>(segs)[a] = Seg32{(float)mxd, (float)myd, (float)hx, (float)hy};
+  }
+  area = bsum(area, shd);
+  rm = bminmax(rm, true, shf);
+  if (threadIdx.x == 0) info[i] = PolyInfo{c[0], c[1], area, rm, 0u};
+}
+
+// Shared finish of one output: 2/|Q|^2 * exp(iQ.c) * sum, Q = 0 -> area, small |Q| -> FP64 list.
+__device__ __forceinline__ void finish_out(double qx, double qy, double re, double im, const PolyInfo& pi,
+                                           int64_t row, double* out, uint32_t* small, WsHeader* h) {
+  const double q2 = qx * qx + qy * qy;
+  if (q2 == 0.0) {
+    out[2 * row] = pi.area;
+    out[2 * row + 1] = 0.0;
+    return;
+  }
+  if (sqrt(q2) * (double)pi.rmax < kTauSmallQ) {
+    small[atomicAdd(&h->small_q_count, 1u)] = (uint32_t)row;
+    return;
+  }
+  const double k = 2.0 / q2;
+  double sp, cp;
+  sincos(qx * pi.cx + qy * pi.cy, &sp, &cp);
+  out[2 * row] = k * (re * cp - im * sp);
+  out[2 * row + 1] = k * (re * sp + im * cp);
+}
+
+// Persistent kernel: block b runs items [cta_off[b], cta_off[b+1]) in order.
+template <class Pol, int R, int NT>
+__global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_batched(
+    const BPlanHeader* __restrict__ ph, const int32_t* __restrict__ cta_off, const BItem* __restrict__ items,
+    const PolyPlan* __restrict__ pplan, const PolyInfo* __restrict__ info, const typename Pol::Item* __restrict__ segs,
+    const double* __restrict__ q, double2* __restrict__ partial, double* __restrict__ out, uint32_t* small,
+    WsHeader* h) {
+  using Item = typename Pol::Item;
+  using QT = typename Pol::QT;
+  constexpr int TILE = Pol::kTile;
+  constexpr int kLag = 2;
+  __shared__ __align__(128) Item ring[kStages * TILE];
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ __align__(8) uint64_t empty[kStages];
+
+  const int k0 = cta_off[blockIdx.x], k1 = cta_off[blockIdx.x + 1];
+  auto seg_range = [&](const BItem& it, int64_t& begin, int& count) {
+    const PolyPlan& pp = pplan[it.poly];
+    const int64_t off = (int64_t)it.chunk * kChunk;
+    begin = pp.seg_begin + off;
+    count = (int)max((int64_t)0, min((int64_t)kChunk, (int64_t)pp.n_seg - off));
+  };
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NT / 32);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // producer cursor (thread 0): next tile to issue, as (item, tile-in-item) and global index
+  int pk = k0, ptile = 0;
+  int64_t issued = 0, total = 0;
+  auto issue_next = [&]() {
+    for (;;) {
+      int64_t b;
+      int cnt;
+      seg_range(items[pk], b, cnt);
+      const int nt_item = (cnt + TILE - 1) / TILE;
+      if (ptile < nt_item) {
+        const int s = (int)(issued % kStages);
+        const int c = min(TILE, cnt - ptile * TILE);
+        const uint32_t bytes = (uint32_t)(c * (int)sizeof(Item));
+        mbar_arrive_expect_tx(&full[s], bytes);
+        bulk_g2s(ring + s * TILE, segs + b + (int64_t)ptile * TILE, bytes, &full[s]);
+        ++ptile;
+        ++issued;
+        return;
+      }
+      ++pk;
+      ptile = 0;
+    }
+  };
+  if (threadIdx.x == 0) {
+    for (int k = k0; k < k1; ++k) {
+      int64_t b;
+      int cnt;
+      seg_range(items[k], b, cnt);
+      total += (cnt + TILE - 1) / TILE;
+    }
+    for (int64_t t = 0; t < min((int64_t)kStages, total); ++t) issue_next();
+  }
+
+  bool ok = true;
+  int64_t g = 0;   // global tile counter of this block
+  for (int k = k0; k < k1 && ok; ++k) {
+    const BItem it = items[k];
+    const PolyPlan pp = pplan[it.poly];
+    int64_t sb;
+    int cnt;
+    seg_range(it, sb, cnt);
+    const int64_t q0 = pp.q_begin + (int64_t)it.qtile * (NT * R);
+    const int64_t qend = pp.q_begin + pp.n_q;
+    QT qr[R][3];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t iq = q0 + (int64_t)r * NT + threadIdx.x;
+      qr[r][0] = qr[r][1] = qr[r][2] = (QT)0;
+      if (iq < qend) {
+        qr[r][0] = (QT)q[2 * iq];
+        qr[r][1] = (QT)q[2 * iq + 1];
+      }
+    }
+    typename Pol::template Acc<R> acc;
+    acc.init();
+    const int ntk = (cnt + TILE - 1) / TILE;
+    for (int t = 0; t < ntk; ++t, ++g) {
+      const int s = (int)(g % kStages);
+      // stop decisions are warp-uniform (see k_fwd)
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], (uint32_t)((g / kStages) & 1)))) {
+        ok = false;
+        break;
+      }
+      Pol::template tile<R>(ring + s * TILE, min(TILE, cnt - t * TILE), qr, acc, Thr{0.f, 0.f});
+      __syncwarp();
+      if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);
+      if (threadIdx.x < 32) {
+        bool rok = true;
+        if (threadIdx.x == 0 && g + kLag < total && g + kLag >= kStages) {
+          const int64_t u = g + kLag - kStages;
+          rok = mbar_wait_bounded(&empty[u % kStages], (uint32_t)((u / kStages) & 1));
+          if (rok) {
+            fence_proxy_async_smem();
+            issue_next();
+          }
+        }
+        if (!__shfl_sync(0xffffffffu, rok, 0)) { ok = false; break; }
+      }
+    }
+    if (!ok) break;
+    const PolyInfo pi = info[it.poly];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t iq = q0 + (int64_t)r * NT + threadIdx.x;
+      if (iq >= qend) continue;
+      const double2 f = acc.get(r);
+      const int64_t local = iq - pp.q_begin;
+      if (pp.n_chunks > 1) {
+        partial[pp.part_base + (int64_t)it.chunk * pp.n_q + local] = f;
+      } else {
+        finish_out((double)qr[r][0], (double)qr[r][1], f.x, f.y, pi, pp.out_base + local, out, small, h);
+      }
+    }
+  }
+  if (!ok) set_status(&h->status, ST_TIMEOUT);
+  if (threadIdx.x == 0)
+    for (int64_t u = max((int64_t)0, issued - kStages); u < issued; ++u)
+      (void)mbar_wait_bounded(&full[u % kStages], (uint32_t)((u / kStages) & 1));
+}
+
+// Multi-chunk polygons: fixed-order FP64 sum of their chunk partials, then the finish.
+__global__ void __launch_bounds__(kBThreads) k_bfinal(const BPlanHeader* ph, const int32_t* __restrict__ mc,
+                                                      const PolyPlan* __restrict__ pplan,
+                                                      const PolyInfo* __restrict__ info, const double* __restrict__ q,
+                                                      const double2* __restrict__ partial, double* out,
+                                                      uint32_t* small, WsHeader* h) {
+  const int i = mc[blockIdx.x];
+  const PolyPlan pp = pplan[i];
+  const PolyInfo pi = info[i];
+  const bool fp64 = ph->fp64 != 0;
+  for (int64_t l = threadIdx.x; l < pp.n_q; l += kBThreads) {
+    double re = 0.0, im = 0.0;
+    for (int c = 0; c < pp.n_chunks; ++c) {
+      const double2 p = partial[pp.part_base + (int64_t)c * pp.n_q + l];
+      re += p.x;
+      im += p.y;
+    }
+    const int64_t iq = pp.q_begin + l;
+    const double qx = fp64 ? q[2 * iq] : (double)(float)q[2 * iq];
+    const double qy = fp64 ? q[2 * iq + 1] : (double)(float)q[2 * iq + 1];
+    finish_out(qx, qy, re, im, pi, pp.out_base + l, out, small, h);
+  }
+}
+
+// FP64 small-|Q| pass: fan of signed triangles (c, p_j, p_{j+1}) with the simplex series.
+__global__ void __launch_bounds__(kBThreads) k_bsmall(const float* __restrict__ v, const BPlanHeader* ph,
+                                                      const PolyPlan* __restrict__ pplan,
+                                                      const PolyInfo* __restrict__ info, const int64_t* q_off,
+                                                      const double* __restrict__ q, const uint32_t* small,
+                                                      double* out, const WsHeader* h) {
+  __shared__ double sh[kBThreads / 32];
+  const uint32_t count = h->small_q_count;
+  const int64_t n_q = ph->n_q, n_polys = ph->n_polys;
+  for (uint32_t e = blockIdx.x; e < count; e += gridDim.x) {
+    const int64_t row = small[e];
+    int64_t i, iq;
+    if (ph->shared_q) {
+      i = row / n_q;
+      iq = row % n_q;
+    } else {
+      int64_t lo = 0, hi = n_polys;   // last polygon whose Q range starts at or before row
+      while (lo + 1 < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (q_off[mid] <= row) lo = mid; else hi = mid;
+      }
+      i = lo;
+      iq = row;
+    }
+    const PolyPlan pp = pplan[i];
+    const PolyInfo pi = info[i];
+    const double qx = ph->fp64 ? q[2 * iq] : (double)(float)q[2 * iq];
+    const double qy = ph->fp64 ? q[2 * iq + 1] : (double)(float)q[2 * iq + 1];
+    double re = 0.0, im = 0.0;
+    for (int64_t j = threadIdx.x; j < pp.n_seg; j += kBThreads) {
+      const int64_t a = pp.seg_begin + j, b = pp.seg_begin + (j + 1 < pp.n_seg ? j + 1 : 0);
+      const double x0 = (double)v[2 * a] - pi.cx, y0 = (double)v[2 * a + 1] - pi.cy;
+      const double x1 = (double)v[2 * b] - pi.cx, y1 = (double)v[2 * b + 1] - pi.cy;
+      const double n0 = qx * x0 + qy * y0, n1 = qx * x1 + qy * y1;
+      // sum_k i^k h_k(n0, n1) / (k+2)!, 16 terms (|n| < 0.25)
+      double hk = 1.0, p1 = 1.0, inv = 0.5, sr = 0.0, si = 0.0;
+      for (int k = 0; k <= 16; ++k) {
+        if (k > 0) {
+          p1 *= n1;
+          hk = n0 * hk + p1;   // h_k(n0, n1) = n0 h_{k-1} + n1^k
+        }
+        const double t = hk * inv;
+        switch (k & 3) { case 0: sr += t; break; case 1: si += t; break; case 2: sr -= t; break; default: si -= t; }
+        inv /= (double)(k + 3);
+      }
+      const double det = x0 * y1 - x1 * y0;
+      re += det * sr;
+      im += det * si;
+    }
+    re = bsum(re, sh);
+    im = bsum(im, sh);
+    if (threadIdx.x == 0) {
+      double sp, cp;
+      sincos(qx * pi.cx + qy * pi.cy, &sp, &cp);
+      out[2 * row] = re * cp - im * sp;
+      out[2 * row + 1] = re * sp + im * cp;
+    }
+  }
+}
+
+template <class Pol, int R, int NT>
+int occ_batched() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batched<Pol, R, NT>, NT, 0) != cudaSuccess) return 1;
+  return b > 0 ? b : 1;
+}
+
+template <class Pol, int R, int NT>
+cudaError_t launch_batched_one(int grid, const BPlanHeader* ph, const int32_t* cta_off, const BItem* items,
+                               const PolyPlan* pplan, const PolyInfo* info, const void* segs, const double* q,
+                               double2* partial, double* out, uint32_t* small, WsHeader* h, cudaStream_t st) {
+  k_batched<Pol, R, NT><<<grid, NT, 0, st>>>(ph, cta_off, items, pplan, info,
+                                             static_cast<const typename Pol::Item*>(segs), q, partial, out, small, h);
+  return cudaGetLastError();
+}
+
+#define PFT_BATCHED_CASES(X)                                                                          \
+  X(Pol2F32, 1, 128) X(Pol2F32, 2, 128) X(Pol2F32, 4, 128) X(Pol2F32, 8, 128) X(Pol2F32, 1, 256)      \
+  X(Pol2F32, 2, 256) X(Pol2F32, 4, 256) X(Pol2F32, 8, 256) X(Pol2F64, 1, 128) X(Pol2F64, 2, 128)      \
+  X(Pol2F64, 1, 256) X(Pol2F64, 2, 256)
+
+int batched_blocks_per_sm(bool fp64, int r, int nt) {
+#define X(P, RR, NN) \
+  if ((sizeof(P::QT) == 8) == fp64 && r == RR && nt == NN) return occ_batched<P, RR, NN>();
+  PFT_BATCHED_CASES(X)
+#undef X
+  return 1;
+}
+
+cudaError_t launch_batched(bool fp64, int r, int nt, int grid, const BPlanHeader* ph, const int32_t* cta_off,
+                           const BItem* items, const PolyPlan* pplan, const PolyInfo* info, const void* segs,
+                           const double* q, double2* partial, double* out, uint32_t* small, WsHeader* h,
+                           cudaStream_t st) {
+#define X(P, RR, NN)                                                                                     \
+  if ((sizeof(P::QT) == 8) == fp64 && r == RR && nt == NN)                                              \
+    return launch_batched_one<P, RR, NN>(grid, ph, cta_off, items, pplan, info, segs, q, partial, out, small, h, \
+                                         st);
+  PFT_BATCHED_CASES(X)
+#undef X
+  return cudaErrorInvalidConfiguration;
+}
+
+thread_local int g_batched_launches = 0;
+
+// Host-side copy of what a batched call needs (kept in the caller's pft_batched_plan).
+struct PlanHandle {
+  int64_t magic, n_polys, n_verts, n_q, shared_q, fp64, r, nt, grid, n_mc;
+  int64_t plan_hdr, cta_off, items, pplan, mc, info, segs, partial, small, total;
+};
+static_assert(sizeof(PlanHandle) <= sizeof(pft_batched_plan), "plan handle fits the public struct");
+
+}  // namespace
+}  // namespace pft
+
+using namespace pft;
+
+extern "C" {
+
+size_t pft2d_batched_workspace_size(int64_t n_verts, const int64_t* poly_off_host, int64_t n_polys,
+                                    const int64_t* q_off_host, int64_t n_q, const pft_options* opts) {
+  HostPlan P;
+  if (n_verts < 0 || build_plan(poly_off_host, n_polys, q_off_host, n_q, opts, P) != PFT_OK) return 0;
+  if (P.h.n_verts != n_verts) return 0;
+  return layout_of(P.h).total;
+}
+
+int pft2d_batched_prepare(const int64_t* poly_off_host, int64_t n_polys, const int64_t* q_off_host, int64_t n_q,
+                          void* ws, size_t ws_bytes, const pft_options* opts, pft_batched_plan* plan,
+                          void* stream) {
+  if (plan == nullptr) return PFT_ERR_INVALID_ARG;
+  std::memset(plan, 0, sizeof(*plan));
+  HostPlan P;
+  if (int e = build_plan(poly_off_host, n_polys, q_off_host, n_q, opts, P)) return e;
+  const BLayout y = layout_of(P.h);
+  if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < y.total) return PFT_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  auto put = [&](size_t off, const void* src, size_t bytes) {
+    return bytes == 0 || cudaMemcpyAsync(at<char>(ws, off), src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  };
+  bool ok = put(y.plan_hdr, &P.h, sizeof(P.h)) &&
+            put(y.cta_off, P.cta_off.data(), sizeof(int32_t) * P.cta_off.size()) &&
+            put(y.items, P.items.data(), sizeof(BItem) * P.items.size()) &&
+            put(y.pplan, P.pplan.data(), sizeof(PolyPlan) * P.pplan.size()) &&
+            put(y.mc, P.mc.data(), sizeof(int32_t) * P.mc.size());
+  ok = ok && cudaStreamSynchronize(st) == cudaSuccess;   // the host vectors die on return
+  if (!ok) return PFT_ERR_CUDA;
+  PlanHandle ph{};
+  ph.magic = (int64_t)kPlanMagic;
+  ph.n_polys = n_polys;
+  ph.n_verts = P.h.n_verts;
+  ph.n_q = n_q;
+  ph.shared_q = P.h.shared_q;
+  ph.fp64 = P.h.fp64;
+  ph.r = P.h.r;
+  ph.nt = P.h.nt;
+  ph.grid = P.h.n_cta;
+  ph.n_mc = P.h.n_mc;
+  ph.plan_hdr = (int64_t)y.plan_hdr; ph.cta_off = (int64_t)y.cta_off; ph.items = (int64_t)y.items;
+  ph.pplan = (int64_t)y.pplan; ph.mc = (int64_t)y.mc; ph.info = (int64_t)y.info; ph.segs = (int64_t)y.segs;
+  ph.partial = (int64_t)y.partial; ph.small = (int64_t)y.small; ph.total = (int64_t)y.total;
+  std::memcpy(plan, &ph, sizeof(ph));
+  return PFT_OK;
+}
+
+int pft2d_polygons_batched(const float* verts, int64_t n_verts, const int64_t* poly_off, int64_t n_polys,
+                           const double* q, const int64_t* q_off, int64_t n_q, double* out, void* ws,
+                           size_t ws_bytes, const pft_batched_plan* plan, void* stream) {
+  g_batched_launches = 0;
+  if (plan == nullptr) return PFT_ERR_INVALID_ARG;
+  PlanHandle p;
+  std::memcpy(&p, plan, sizeof(p));
+  if (p.magic != (int64_t)kPlanMagic) return PFT_ERR_INVALID_ARG;
+  if (n_verts != p.n_verts || n_polys != p.n_polys || n_q != p.n_q || (q_off == nullptr) != (p.shared_q != 0))
+    return PFT_ERR_INVALID_ARG;   // not the shape the plan was prepared for
+  if (n_polys > 0 && (poly_off == nullptr || verts == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (n_q > 0 && (q == nullptr || out == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < (size_t)p.total)
+    return PFT_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader* h = at<WsHeader>(ws, 0);
+  if (launch_init_header(h, st) != cudaSuccess) return PFT_ERR_CUDA;
+  ++g_batched_launches;
+  if (n_polys == 0 || n_q == 0) return PFT_OK;
+  const BPlanHeader* phd = at<BPlanHeader>(ws, (size_t)p.plan_hdr);
+  const PolyPlan* pplan = at<PolyPlan>(ws, (size_t)p.pplan);
+  PolyInfo* info = at<PolyInfo>(ws, (size_t)p.info);
+  void* segs = at<void>(ws, (size_t)p.segs);
+  uint32_t* small = at<uint32_t>(ws, (size_t)p.small);
+  double2* partial = at<double2>(ws, (size_t)p.partial);
+  if (p.fp64) k_bprep<true><<<(unsigned)n_polys, kBThreads, 0, st>>>(verts, poly_off, phd, pplan, info, segs, h);
+  else k_bprep<false><<<(unsigned)n_polys, kBThreads, 0, st>>>(verts, poly_off, phd, pplan, info, segs, h);
+  if (cudaGetLastError() != cudaSuccess) return PFT_ERR_CUDA;
+  ++g_batched_launches;
+  if (launch_batched(p.fp64 != 0, (int)p.r, (int)p.nt, (int)p.grid, phd, at<int32_t>(ws, (size_t)p.cta_off),
+                     at<BItem>(ws, (size_t)p.items), pplan, info, segs, q, partial, out, small, h, st) != cudaSuccess)
+    return PFT_ERR_CUDA;
+  ++g_batched_launches;
+  if (p.n_mc > 0) {
+    k_bfinal<<<(unsigned)p.n_mc, kBThreads, 0, st>>>(phd, at<int32_t>(ws, (size_t)p.mc), pplan, info, q, partial,
+                                                      out, small, h);
+    if (cudaGetLastError() != cudaSuccess) return PFT_ERR_CUDA;
+    ++g_batched_launches;
+  }
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_bsmall<<<std::max(1, sms), kBThreads, 0, st>>>(verts, phd, pplan, info, q_off, q, small, out, h);
+  if (cudaGetLastError() != cudaSuccess) return PFT_ERR_CUDA;
+  ++g_batched_launches;
+  return PFT_OK;
+}
+
+int pft_batched_last_launch_count(void) { return g_batched_launches; }
+
+}  // extern "C"

@@ -9,357 +9,10 @@
 // per thread and in a fixed order: FP32 within a tile, error-free (TwoSum)
 // compensation across tiles; the per-chunk partials are added in FP64 by the
 // finalize kernel.  No atomics on data, so results are deterministic.
-#include "pft_kernels.cuh"
+#include "pft_pairs.cuh"
 
 namespace pft {
 namespace {
-
-constexpr int kStages = 4;
-
-// Thresholds on P (see the 3D face term below): p_hi = tau^2/4, p_lo = tau_lo^2/4.
-struct Thr {
-  float hi, lo;
-};
-constexpr float kTauLo = 0.05f;
-
-// Resident blocks per SM the register budget is sized for: 16-24 warps of
-// 256 threads, fewer registers per thread for fewer Q points per thread.
-// (FP64 paths: one block, so that the double-precision temporaries never spill.)
-template <class Pol, int R, int NT>
-constexpr int kMinBlocks = sizeof(typename Pol::QT) == 8 ? 1 : (NT == 256 ? 1 : 2) * (R >= 8 ? 1 : (R == 4 ? 2 : 3));
-
-// ---------------------------------------------------------------------------
-// Per-pair arithmetic.
-// ---------------------------------------------------------------------------
-
-// 2D, Eq. 6 (Sec. 2): the segment p0 -> p1 contributes
-//   -i (Qx Dy - Qy Dx) sinc(Q.D/2) exp(iQ.m)           (times 1/|Q|^2, applied later)
-// Records hold m and D/2, so w below is half the cross product; the factor 2
-// and 1/|Q|^2 are applied in FP64 by the finalize kernel.
-__device__ __forceinline__ void seg_pair_f32(float qx, float qy, const float4 s, float& re, float& im) {
-  const float ph = fmaf(qx, s.x, qy * s.y);    // Q.m
-  const float u = fmaf(qx, s.z, qy * s.w);     // Q.D / 2
-  const float w = fmaf(qx, s.w, -qy * s.z);    // (Qx Dy - Qy Dx) / 2
-  float sn, cs;
-  __sincosf(ph, &sn, &cs);
-  const float ws = w * sinc_f32(u);
-  re = ws * sn;    // -i * ws * (cos + i sin) = ws sin - i ws cos
-  im = -ws * cs;
-}
-
-__device__ __forceinline__ double sinc_f64(double u) {
-  const double u2 = u * u;
-  if (u2 < 1e-2) {   // Taylor through u^10: truncation < 1e-18 at |u| = 0.1
-    double p = fma(u2, -1.0 / 39916800.0, 1.0 / 362880.0);
-    p = fma(u2, p, -1.0 / 5040.0);
-    p = fma(u2, p, 1.0 / 120.0);
-    p = fma(u2, p, -1.0 / 6.0);
-    return fma(u2, p, 1.0);
-  }
-  return sin(u) / u;
-}
-
-__device__ __forceinline__ void seg_pair_f64(double qx, double qy, const Seg64& s, double& re, double& im) {
-  const double ph = fma(qx, s.mx, qy * s.my);
-  const double u = fma(qx, s.hx, qy * s.hy);
-  const double w = fma(qx, s.hy, -qy * s.hx);
-  double sn, cs;
-  sincos(ph, &sn, &cs);
-  const double ws = w * sinc_f64(u);
-  re = ws * sn;
-  im = -ws * cs;
-}
-
-// 3D, Eq. 14 with the sign fixed (Sec. 3).  With X = N x Q, s = Q.N and the
-// corner phases a_k = Q.(p_k - centroid) (a_0 + a_1 + a_2 = 0), a face gives
-//   |Q|^2 I_m = -s exp(i mu) Z,     mu = Q.centroid,
-//   Z = (1/|X|^2) sum_l w_l sinc(u_l) exp(i psi_l)         (edge sum)
-// with w_l = Q.(d_l x N) = b_{l+1} - b_l, b_k = (p_k - centroid).X,
-// u_l = (a_{l+1} - a_l)/2 and psi_l = (a_l + a_{l+1})/2 = -a_{l+2}/2.
-// The edge sum cancels to O(spread) of its terms when the phase spread of the
-// face is small (it is 0/0 for Q parallel to N); there the same face integral
-// (Eq. 13) is taken from its series, Z = i G,
-//   G = sum_k i^k h_k(a) / (k+2)!,   h_k = P h_{k-2} + T h_{k-3},
-// P = a0^2 + a0 a1 + a1^2 (= h_2), T = a0 a1 a2 (= h_3), kept through k = 8;
-// P < tau^2/4 implies max_l |Q.d_l| < tau <= 1, where the omitted terms are
-// below 1e-9 relative.
-//
-// Branch choice, per face and warp: the series is taken for all of a thread's
-// Q points when every Q point of every lane of the warp has P < p_hi = tau^2/4;
-// otherwise the edge sum, except for Q points with P < p_lo = tau_lo^2/4
-// (tau_lo = min(tau, 0.05): below it the edge sum would lose more than ~4 bits
-// to cancellation), which are redone with the series.  Both evaluate the same
-// face integral, so the choice only moves rounding; the R Q points of a thread
-// share the branch, so their arithmetic interleaves.
-
-// Projections shared by both branches.  A = g.xyz, q0.x  B = q0.yz, q1.xy  C = q1.z, N.xyz
-__device__ __forceinline__ void face_common(float qx, float qy, float qz, const float4 A, const float4 B,
-                                            const float4 C, float& mu, float& a0, float& a1, float& s, float& P) {
-  mu = fmaf(qx, A.x, fmaf(qy, A.y, qz * A.z));
-  a0 = fmaf(qx, A.w, fmaf(qy, B.x, qz * B.y));
-  a1 = fmaf(qx, B.z, fmaf(qy, B.w, qz * C.x));
-  s = fmaf(qx, C.y, fmaf(qy, C.z, qz * C.w));
-  P = fmaf(a0, a0 + a1, a1 * a1);
-}
-
-// Z = i G from the face-integral series.
-__device__ __forceinline__ void face_series(float a0, float a1, float P, float& zr, float& zi) {
-  const float T = -(a0 * a1) * (a0 + a1);
-  const float T2 = T * T;
-  float gre = fmaf(P, 2.75573192e-7f, -2.48015873e-5f);   // 1/10!, -1/8!
-  gre = fmaf(P, gre, 1.38888889e-3f);                      // 1/6!
-  gre = fmaf(P, gre, -4.16666667e-2f);                     // -1/4!
-  gre = fmaf(P, gre, 0.5f);                                // 1/2!
-  gre = fmaf(T2, fmaf(P, 8.26719577e-7f, -2.48015873e-5f), gre);   // T^2 (3P/10! - 1/8!)
-  const float gim = T * fmaf(P, fmaf(P, -8.26719577e-6f, 3.96825397e-4f), -8.33333333e-3f);  // -T/5! + PT/2520 - P^2 T/120960
-  zr = -gim;
-  zi = gre;
-}
-
-// Z from the edge sum of Eq. 14.
-__device__ __forceinline__ void face_edge(float qx, float qy, float qz, const float4 A, const float4 B,
-                                          const float4 C, float a0, float a1, float& zr, float& zi) {
-  const float nx = C.y, ny = C.z, nz = C.w;
-  const float Xx = fmaf(ny, qz, -nz * qy), Xy = fmaf(nz, qx, -nx * qz), Xz = fmaf(nx, qy, -ny * qx);
-  const float x2 = fmaf(Xx, Xx, fmaf(Xy, Xy, Xz * Xz));
-  const float b0 = fmaf(A.w, Xx, fmaf(B.x, Xy, B.y * Xz));
-  const float b1 = fmaf(B.z, Xx, fmaf(B.w, Xy, C.x * Xz));
-  const float b2 = -(b0 + b1);
-  const float w[3] = {b1 - b0, b2 - b1, b0 - b2};
-  const float h0 = 0.5f * a0, h1 = 0.5f * a1;
-  const float u[3] = {h1 - h0, fmaf(-2.0f, h1, -h0), fmaf(2.0f, h0, h1)};  // (a_{l+1} - a_l)/2
-  // exp(i psi_l), psi_l = -a_{l+2}/2: psi_1 = -h0 and psi_2 = -h1 on the SFU,
-  // psi_0 = h0 + h1 as the conjugate of their product.
-  float sp[3], cp[3];
-  __sincosf(-h0, &sp[1], &cp[1]);
-  __sincosf(-h1, &sp[2], &cp[2]);
-  cp[0] = fmaf(cp[1], cp[2], -sp[1] * sp[2]);
-  sp[0] = -fmaf(sp[1], cp[2], cp[1] * sp[2]);
-  float u2[3], S[3];
-#pragma unroll
-  for (int l = 0; l < 3; ++l) {
-    u2[l] = u[l] * u[l];
-    S[l] = sinc_poly(u2[l]);
-  }
-  if (fmaxf(u2[0], fmaxf(u2[1], u2[2])) > kPi2) {   // rare: an edge with |Q.d_l| > 2 pi
-#pragma unroll
-    for (int l = 0; l < 3; ++l) S[l] = sinc_f32(u[l]);
-  }
-  float sr = 0.f, si = 0.f;
-#pragma unroll
-  for (int l = 0; l < 3; ++l) {
-    const float ws = w[l] * S[l];
-    sr = fmaf(ws, cp[l], sr);
-    si = fmaf(ws, sp[l], si);
-  }
-  const float inv = (x2 > 0.f) ? rcp_approx(x2) : 0.f;   // x2 = 0 only for Q parallel to N (series then)
-  zr = sr * inv;
-  zi = si * inv;
-}
-
-// |Q|^2 I_m = -s exp(i mu) Z.
-__device__ __forceinline__ void face_finish(float mu, float s, float zr, float zi, float& re, float& im) {
-  float sm, cm;
-  __sincosf(mu, &sm, &cm);
-  re = -s * fmaf(cm, zr, -sm * zi);
-  im = -s * fmaf(cm, zi, sm * zr);
-}
-
-// Same face term in FP64 (comparison path): library sincos, series through k = 16.
-__device__ __forceinline__ void face_pair_f64(double qx, double qy, double qz, const Face64& f, double p_hi, double p_lo,
-                                              double& re, double& im) {
-  const double mu = fma(qx, f.gx, fma(qy, f.gy, qz * f.gz));
-  const double a0 = fma(qx, f.q0x, fma(qy, f.q0y, qz * f.q0z));
-  const double a1 = fma(qx, f.q1x, fma(qy, f.q1y, qz * f.q1z));
-  const double s = fma(qx, f.nx, fma(qy, f.ny, qz * f.nz));
-  const double a2 = -(a0 + a1);
-  const double P = fma(a0, a0 + a1, a1 * a1);
-  double zr, zi;
-  const bool series = __all_sync(0xffffffffu, P < p_hi) || (P < p_lo);
-  if (series) {
-    const double T = a0 * a1 * a2;
-    constexpr int K = 16;
-    double h[K + 1];
-    h[0] = 1.0; h[1] = 0.0; h[2] = P;
-#pragma unroll
-    for (int k = 3; k <= K; ++k) h[k] = fma(P, h[k - 2], T * h[k - 3]);
-    double gre = 0.0, gim = 0.0, inv = 0.5;   // 1/(k+2)!
-#pragma unroll
-    for (int k = 0; k <= K; ++k) {
-      const double t = h[k] * inv;
-      switch (k & 3) { case 0: gre += t; break; case 1: gim += t; break; case 2: gre -= t; break; default: gim -= t; }
-      inv /= (double)(k + 3);
-    }
-    zr = -gim;
-    zi = gre;
-  } else {
-    const double Xx = fma(f.ny, qz, -f.nz * qy), Xy = fma(f.nz, qx, -f.nx * qz), Xz = fma(f.nx, qy, -f.ny * qx);
-    const double x2 = fma(Xx, Xx, fma(Xy, Xy, Xz * Xz));
-    const double b0 = fma(f.q0x, Xx, fma(f.q0y, Xy, f.q0z * Xz));
-    const double b1 = fma(f.q1x, Xx, fma(f.q1y, Xy, f.q1z * Xz));
-    const double b2 = -(b0 + b1);
-    const double w[3] = {b1 - b0, b2 - b1, b0 - b2};
-    const double psi[3] = {-0.5 * a2, -0.5 * a0, -0.5 * a1};
-    const double u[3] = {0.5 * (a1 - a0), 0.5 * (a2 - a1), 0.5 * (a0 - a2)};
-    double sr = 0.0, si = 0.0;
-#pragma unroll
-    for (int l = 0; l < 3; ++l) {
-      double sp, cp;
-      sincos(psi[l], &sp, &cp);
-      const double ws = w[l] * sinc_f64(u[l]);
-      sr = fma(ws, cp, sr);
-      si = fma(ws, sp, si);
-    }
-    const double inv = (x2 > 0.0) ? 1.0 / x2 : 0.0;
-    zr = sr * inv;
-    zi = si * inv;
-  }
-  double sm, cm;
-  sincos(mu, &sm, &cm);
-  re = -s * fma(cm, zr, -sm * zi);
-  im = -s * fma(cm, zi, sm * zr);
-}
-
-// ---------------------------------------------------------------------------
-// Policies: record type, Q registers, accumulators and the per-tile loop.
-// ---------------------------------------------------------------------------
-
-template <int R>
-struct Acc32 {
-  CAcc re[R], im[R];
-  __device__ __forceinline__ void init() {
-#pragma unroll
-    for (int r = 0; r < R; ++r) { re[r].init(); im[r].init(); }
-  }
-  __device__ __forceinline__ double2 get(int r) const {
-    return make_double2((double)re[r].hi + (double)re[r].lo, (double)im[r].hi + (double)im[r].lo);
-  }
-};
-
-template <int R>
-struct Acc64 {
-  double re[R], im[R];
-  __device__ __forceinline__ void init() {
-#pragma unroll
-    for (int r = 0; r < R; ++r) { re[r] = 0.0; im[r] = 0.0; }
-  }
-  __device__ __forceinline__ double2 get(int r) const { return make_double2(re[r], im[r]); }
-};
-
-struct Pol2F32 {
-  using Item = Seg32;
-  static constexpr int kDim = 2, kTile = 128;
-  template <int R> using Acc = Acc32<R>;
-  using QT = float;
-  template <int R>
-  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc, Thr) {
-    float tre[R], tim[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) { tre[r] = 0.f; tim[r] = 0.f; }
-#pragma unroll 2
-    for (int i = 0; i < cnt; ++i) {
-      const float4 s = reinterpret_cast<const float4*>(t)[i];
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        float re, im;
-        seg_pair_f32(q[r][0], q[r][1], s, re, im);
-        tre[r] += re;
-        tim[r] += im;
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) { acc.re[r].add(tre[r]); acc.im[r].add(tim[r]); }
-  }
-};
-
-struct Pol2F64 {
-  using Item = Seg64;
-  static constexpr int kDim = 2, kTile = 64;
-  template <int R> using Acc = Acc64<R>;
-  using QT = double;
-  template <int R>
-  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc, Thr) {
-    for (int i = 0; i < cnt; ++i) {
-      const Seg64 s = t[i];
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        double re, im;
-        seg_pair_f64(q[r][0], q[r][1], s, re, im);
-        acc.re[r] += re;
-        acc.im[r] += im;
-      }
-    }
-  }
-};
-
-struct Pol3F32 {
-  using Item = Face32;
-  static constexpr int kDim = 3, kTile = 64;
-  template <int R> using Acc = Acc32<R>;
-  using QT = float;
-  template <int R>
-  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc,
-                                              Thr th) {
-    float tre[R], tim[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) { tre[r] = 0.f; tim[r] = 0.f; }
-#pragma unroll 1
-    for (int i = 0; i < cnt; ++i) {
-      const float4* p = reinterpret_cast<const float4*>(t + i);
-      const float4 A = p[0], B = p[1], C = p[2];
-      float mu[R], a0[R], a1[R], s[R], P[R], zr[R], zi[R];
-      bool all_hi = true, any_lo = false;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        face_common(q[r][0], q[r][1], q[r][2], A, B, C, mu[r], a0[r], a1[r], s[r], P[r]);
-        all_hi = all_hi && (P[r] < th.hi);
-        any_lo = any_lo || (P[r] < th.lo);
-      }
-      if (__all_sync(0xffffffffu, all_hi)) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) face_series(a0[r], a1[r], P[r], zr[r], zi[r]);
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) face_edge(q[r][0], q[r][1], q[r][2], A, B, C, a0[r], a1[r], zr[r], zi[r]);
-        if (any_lo) {
-#pragma unroll
-          for (int r = 0; r < R; ++r)
-            if (P[r] < th.lo) face_series(a0[r], a1[r], P[r], zr[r], zi[r]);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        float re, im;
-        face_finish(mu[r], s[r], zr[r], zi[r], re, im);
-        tre[r] += re;
-        tim[r] += im;
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) { acc.re[r].add(tre[r]); acc.im[r].add(tim[r]); }
-  }
-};
-
-struct Pol3F64 {
-  using Item = Face64;
-  static constexpr int kDim = 3, kTile = 32;
-  template <int R> using Acc = Acc64<R>;
-  using QT = double;
-  template <int R>
-  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc,
-                                              Thr th) {
-    for (int i = 0; i < cnt; ++i) {
-      const Face64 f = t[i];
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        double re, im;
-        face_pair_f64(q[r][0], q[r][1], q[r][2], f, (double)th.hi, (double)th.lo, re, im);
-        acc.re[r] += re;
-        acc.im[r] += im;
-      }
-    }
-  }
-};
 
 // ---------------------------------------------------------------------------
 // The main kernel: bulk-copy ring of record tiles, R Q points per thread.
@@ -429,17 +82,24 @@ __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_fwd(const typena
   bool ok = true;
   for (int t = 0; t < ntiles; ++t) {
     const int s = t % kStages;
-    if (!mbar_wait_bounded(&full[s], (uint32_t)((t / kStages) & 1))) { ok = false; break; }
+    // every decision to stop is made for a whole warp, so no lane is left behind at a warp sync
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], (uint32_t)((t / kStages) & 1)))) { ok = false; break; }
     const int cnt = (int)min((int64_t)TILE, n - (int64_t)t * TILE);
     Pol::template tile<R>(ring + s * TILE, cnt, qr, acc, th);
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);
-    if (threadIdx.x == 0 && t + kLag < ntiles && t + kLag >= kStages) {
-      const int u = t + kLag - kStages;   // the tile that last used slot (t + kLag) % kStages
-      if (!mbar_wait_bounded(&empty[u % kStages], (uint32_t)((u / kStages) & 1))) { ok = false; break; }
-      fence_proxy_async_smem();
-      issue(t + kLag);
-      issued = t + kLag + 1;
+    if (threadIdx.x < 32) {   // warp 0; its lane 0 refills the ring
+      bool rok = true;
+      if (threadIdx.x == 0 && t + kLag < ntiles && t + kLag >= kStages) {
+        const int u = t + kLag - kStages;   // the tile that last used slot (t + kLag) % kStages
+        rok = mbar_wait_bounded(&empty[u % kStages], (uint32_t)((u / kStages) & 1));
+        if (rok) {
+          fence_proxy_async_smem();
+          issue(t + kLag);
+          issued = t + kLag + 1;
+        }
+      }
+      if (!__shfl_sync(0xffffffffu, rok, 0)) { ok = false; break; }
     }
   }
   if (!ok) set_status(status, ST_TIMEOUT);

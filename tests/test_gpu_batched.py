@@ -1,0 +1,133 @@
+"""GPU parity of the batched 2D transform (one persistent launch over a CSR of polygons)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_08309_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "fp64": 1e-12}
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_08309_gb300 import build as pbuild
+    pbuild.build()
+    return torch, torch.device("cuda:0")
+
+
+def _mixed_batch():
+    """Polygons of 3..5000 vertices (one above the 4096-segment chunk), some far from the origin."""
+    rng = np.random.default_rng(17)
+    sizes = [3, 4, 8, 5000, 17, 300, 9, 1024, 4096, 4097, 64, 3]
+    parts = [synth.star_polygon(n, seed=100 + i, center=tuple(rng.uniform(-3, 3, 2)))
+             for i, n in enumerate(sizes)]
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    return np.concatenate(parts).astype(np.float32), off
+
+
+def _c(a):
+    a = a.detach().cpu().numpy()
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def _areas(v, off):
+    return np.array([abs(oracle.ft2d(v[off[i]:off[i + 1]], [[0.0, 0.0]])[0]) for i in range(off.size - 1)])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("r,nt", [(4, 128), (1, 256), (2, 128)])
+def test_shared_grid_vs_oracle(torch_dev, prec, r, nt):
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    if prec == "fp64" and r > 2:
+        pytest.skip("FP64 path keeps at most 2 Q per thread")
+    v, off = _mixed_batch()
+    rng = np.random.default_rng(3)
+    q = np.concatenate([[[0, 0], [1e-5, 0], [0, 0.02], [30.0, 0]], rng.uniform(-40, 40, (900, 2))])
+    out = pft.pft2d_polygons_batched(torch.from_numpy(v).to(dev), torch.from_numpy(off), torch.from_numpy(q).to(dev),
+                                     options={"precision": prec, "q_per_thread": r, "block_threads": nt},
+                                     check_status=True)
+    got = _c(out)
+    ref = oracle.ft2d_batched(v, off, q)
+    areas = _areas(v, off)
+    err = np.max(np.abs(got - ref), axis=1) / areas
+    assert np.all(err < TOL[prec]), err
+
+
+def test_per_polygon_q_sets(torch_dev):
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    v, off = _mixed_batch()
+    rng = np.random.default_rng(5)
+    counts = np.array([5, 0, 700, 3, 1, 64, 513, 2, 0, 40, 1000, 6])
+    q_off = np.zeros(counts.size + 1, dtype=np.int64)
+    q_off[1:] = np.cumsum(counts)
+    q = rng.uniform(-25, 25, (q_off[-1], 2))
+    q[q_off[2]] = 0.0
+    out = pft.pft2d_polygons_batched(torch.from_numpy(v).to(dev), torch.from_numpy(off), torch.from_numpy(q).to(dev),
+                                     q_off=torch.from_numpy(q_off), check_status=True)
+    got = _c(out)
+    ref = oracle.ft2d_batched(v, off, q, q_off=q_off)
+    areas = _areas(v, off)
+    for i in range(counts.size):
+        sl = slice(q_off[i], q_off[i + 1])
+        if counts[i]:
+            assert np.max(np.abs(got[sl] - ref[sl])) / areas[i] < TOL["fp32"], i
+
+
+def test_c3_full_batch_sampled_and_graph_replay(torch_dev):
+    """4,096 polygons (log-uniform 8..4096 vertices) on the shared 64x64 grid: one prepared schedule,
+    captured in a CUDA graph and replayed; 40 seeded polygons checked against the oracle on every Q."""
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    w = synth.workload_c3()
+    vd, qd = torch.from_numpy(w.verts).to(dev), torch.from_numpy(w.q).to(dev)
+    offd = torch.from_numpy(w.poly_off).to(dev)
+    prep = pft.pft2d_batched_prepare(w.poly_off, w.q.shape[0], device=dev)
+    direct = pft.pft2d_polygons_batched(vd, offd, qd, prepared=prep, check_status=True).clone()
+    out = torch.empty(w.poly_off.size - 1, w.q.shape[0], 2, dtype=torch.float64, device=dev)
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):          # warm the library on the capture stream
+        pft.pft2d_polygons_batched(vd, offd, qd, prepared=prep, out=out)
+    torch.cuda.current_stream(dev).wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        pft.pft2d_polygons_batched(vd, offd, qd, prepared=prep, out=out)
+    out.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert pft.pft_status(prep.ws) == 0
+    assert torch.equal(out, direct)                 # deterministic schedule: bitwise equal
+    rng = np.random.default_rng(33)
+    sel = np.sort(rng.choice(w.poly_off.size - 1, 40, replace=False))
+    got = _c(direct)[sel]
+    for k, i in enumerate(sel):
+        vi = w.verts[w.poly_off[i]:w.poly_off[i + 1]]
+        ref = oracle.ft2d(vi, w.q)
+        area = abs(oracle.ft2d(vi, [[0.0, 0.0]])[0])
+        assert np.max(np.abs(got[k] - ref)) / area < TOL["fp32"], i
+
+
+def test_plan_mismatch_is_rejected(torch_dev):
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    v, off = _mixed_batch()
+    q = torch.zeros(10, 2, dtype=torch.float64, device=dev)
+    prep = pft.pft2d_batched_prepare(off, 10, device=dev)
+    with pytest.raises(pft.PFTError):
+        pft.pft2d_polygons_batched(torch.from_numpy(v).to(dev), torch.from_numpy(off), q[:7], prepared=prep)
+    # device-side check: same sizes, different offsets
+    off2 = off.copy()
+    off2[1] += 1
+    with pytest.raises(pft.PFTError, match="offsets"):
+        pft.pft2d_polygons_batched(torch.from_numpy(v).to(dev), torch.from_numpy(off2).to(dev), q, prepared=prep,
+                                   check_status=True)

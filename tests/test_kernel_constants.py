@@ -41,7 +41,7 @@ def test_sinc_polynomial_accuracy():
 
 def test_face_series_coefficients_are_inverse_factorials():
     """G = sum_k i^k h_k/(k+2)!: the constants are +-1/(k+2)! and their combinations."""
-    c = _floats(_body("pft_fwd.cu", "void face_series("))
+    c = _floats(_body("pft_pairs.cuh", "void face_series("))
     f = math.factorial
     expected = [1 / f(10), -1 / f(8), 1 / f(6), -1 / f(4),           # Horner in P for the real part
                 3 / f(10), -1 / f(8),                                  # T^2 terms
