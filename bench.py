@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--q-per-thread", type=int, default=2)
     p.add_argument("--block-threads", type=int, default=256)
     p.add_argument("--tau", type=float, default=0.0, help="face_series_tau (0 = library default)")
+    p.add_argument("--no-extra", action="store_true", help="skip the secondary paths (batched 2D)")
     return p.parse_args()
 
 
@@ -221,6 +222,46 @@ def run_reference(args):
     return 0
 
 
+def bench_batched(dev, warmup, steps):
+    """Secondary path: 4,096 star polygons (8..4,096 vertices) on a shared 64^2 grid, one prepared
+    schedule replayed from a CUDA graph; each replay is one full batched transform."""
+    import torch
+    import paper_2104_08309_gb300 as pft
+    from paper_2104_08309_gb300 import synth
+    w = synth.workload_c3()
+    vd, qd = torch.from_numpy(w.verts).to(dev), torch.from_numpy(w.q).to(dev)
+    offd = torch.from_numpy(w.poly_off).to(dev)
+    prep = pft.pft2d_batched_prepare(w.poly_off, w.q.shape[0], device=dev)
+    out = torch.empty(w.poly_off.size - 1, w.q.shape[0], 2, dtype=torch.float64, device=dev)
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        pft.pft2d_polygons_batched(vd, offd, qd, prepared=prep, out=out)
+    torch.cuda.current_stream(dev).wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        pft.pft2d_polygons_batched(vd, offd, qd, prepared=prep, out=out)
+    launches = pft.load().pft_batched_last_launch_count()
+    for _ in range(max(3, warmup)):
+        g.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        g.replay()
+        b.record()
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    pairs = float(w.verts.shape[0]) * float(w.q.shape[0])
+    status = pft.pft_status(prep.ws)
+    return {"value": pairs / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "pairs_per_step": pairs,
+            "polygons": int(w.poly_off.size - 1), "segments": int(w.verts.shape[0]), "q_points": int(w.q.shape[0]),
+            "launches_per_step": int(launches), "cuda_graph": True, "device_status": int(status),
+            "l2": "flushed between steps"}
+
+
 def traffic_from_profile():
     """DRAM bytes per main-kernel launch from the committed ncu summary, if it matches this source."""
     import hashlib
@@ -376,6 +417,8 @@ def main():
             vol = float(np.real(__import__("oracle").ft3d(v, f, np.zeros((1, 3)))[0]))
             cb["max_abs_err_vs_oracle_over_volume"] = float(np.max(np.abs(got[:, 0] + 1j * got[:, 1] - ref)) / vol)
             line["cpu_baseline"] = cb
+        if not args.no_extra and world == 1:
+            line["other_paths"] = {"batched2d_4096stars_q64x64": bench_batched(dev, args.warmup, args.steps)}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -297,7 +297,9 @@ __device__ __forceinline__ void finish_out(double qx, double qy, double re, doub
   out[2 * row + 1] = k * (re * sp + im * cp);
 }
 
-// Persistent kernel: block b runs items [cta_off[b], cta_off[b+1]) in order.
+// Persistent kernel: block b runs items [cta_off[b], cta_off[b+1]) in order.  The
+// segment tiles of consecutive items form one stream through the ring; the last
+// warp to finish a slot issues the tile kStages further on (as in k_fwd).
 template <class Pol, int R, int NT>
 __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_batched(
     const BPlanHeader* __restrict__ ph, const int32_t* __restrict__ cta_off, const BItem* __restrict__ items,
@@ -307,67 +309,76 @@ __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_batched(
   using Item = typename Pol::Item;
   using QT = typename Pol::QT;
   constexpr int TILE = Pol::kTile;
-  constexpr int kLag = 2;
+  constexpr int NW = NT / 32;
   __shared__ __align__(128) Item ring[kStages * TILE];
   __shared__ __align__(8) uint64_t full[kStages];
-  __shared__ __align__(8) uint64_t empty[kStages];
+  __shared__ int done[kStages];
+  __shared__ int issued;
 
   const int k0 = cta_off[blockIdx.x], k1 = cta_off[blockIdx.x + 1];
-  auto seg_range = [&](const BItem& it, int64_t& begin, int& count) {
+  auto seg_range = [&](int k, int64_t& begin, int& count) {
+    const BItem it = items[k];
     const PolyPlan& pp = pplan[it.poly];
     const int64_t off = (int64_t)it.chunk * kChunk;
     begin = pp.seg_begin + off;
     count = (int)max((int64_t)0, min((int64_t)kChunk, (int64_t)pp.n_seg - off));
   };
+  auto n_tiles = [&](int k) {
+    int64_t b;
+    int c;
+    seg_range(k, b, c);
+    return (c + TILE - 1) / TILE;
+  };
+  // copy tile tt of item kk into slot s
+  auto issue = [&](int kk, int tt, int s) {
+    int64_t b;
+    int c;
+    seg_range(kk, b, c);
+    const int m = min(TILE, c - tt * TILE);
+    const uint32_t bytes = (uint32_t)(m * (int)sizeof(Item));
+    mbar_arrive_expect_tx(&full[s], bytes);
+    bulk_g2s(ring + s * TILE, segs + b + (int64_t)tt * TILE, bytes, &full[s]);
+    atomicAdd(&issued, 1);
+  };
+  // the position `steps` tiles after (kk, tt) in this block's stream; false past the end
+  auto advance = [&](int& kk, int& tt, int steps) {
+    while (steps-- > 0) {
+      if (tt + 1 < n_tiles(kk)) {
+        ++tt;
+        continue;
+      }
+      do { ++kk; } while (kk < k1 && n_tiles(kk) == 0);
+      if (kk >= k1) return false;
+      tt = 0;
+    }
+    return true;
+  };
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], NT / 32);
+      done[s] = 0;
     }
+    issued = 0;
     fence_mbar_init();
   }
   __syncthreads();
-  // producer cursor (thread 0): next tile to issue, as (item, tile-in-item) and global index
-  int pk = k0, ptile = 0;
-  int64_t issued = 0, total = 0;
-  auto issue_next = [&]() {
-    for (;;) {
-      int64_t b;
-      int cnt;
-      seg_range(items[pk], b, cnt);
-      const int nt_item = (cnt + TILE - 1) / TILE;
-      if (ptile < nt_item) {
-        const int s = (int)(issued % kStages);
-        const int c = min(TILE, cnt - ptile * TILE);
-        const uint32_t bytes = (uint32_t)(c * (int)sizeof(Item));
-        mbar_arrive_expect_tx(&full[s], bytes);
-        bulk_g2s(ring + s * TILE, segs + b + (int64_t)ptile * TILE, bytes, &full[s]);
-        ++ptile;
-        ++issued;
-        return;
-      }
-      ++pk;
-      ptile = 0;
+  if (threadIdx.x == 0) {   // the first kStages tiles of the stream
+    int kk = k0, tt = 0;
+    while (kk < k1 && n_tiles(kk) == 0) ++kk;
+    for (int s = 0; s < kStages && kk < k1; ++s) {
+      issue(kk, tt, s);
+      if (!advance(kk, tt, 1)) break;
     }
-  };
-  if (threadIdx.x == 0) {
-    for (int k = k0; k < k1; ++k) {
-      int64_t b;
-      int cnt;
-      seg_range(items[k], b, cnt);
-      total += (cnt + TILE - 1) / TILE;
-    }
-    for (int64_t t = 0; t < min((int64_t)kStages, total); ++t) issue_next();
   }
 
   bool ok = true;
-  int64_t g = 0;   // global tile counter of this block
+  int64_t g = 0;   // position of the current tile in this block's stream
   for (int k = k0; k < k1 && ok; ++k) {
     const BItem it = items[k];
     const PolyPlan pp = pplan[it.poly];
     int64_t sb;
     int cnt;
-    seg_range(it, sb, cnt);
+    seg_range(k, sb, cnt);
     const int64_t q0 = pp.q_begin + (int64_t)it.qtile * (NT * R);
     const int64_t qend = pp.q_begin + pp.n_q;
     QT qr[R][3];
@@ -392,18 +403,16 @@ __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_batched(
       }
       Pol::template tile<R>(ring + s * TILE, min(TILE, cnt - t * TILE), qr, acc, Thr{0.f, 0.f});
       __syncwarp();
-      if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);
-      if (threadIdx.x < 32) {
-        bool rok = true;
-        if (threadIdx.x == 0 && g + kLag < total && g + kLag >= kStages) {
-          const int64_t u = g + kLag - kStages;
-          rok = mbar_wait_bounded(&empty[u % kStages], (uint32_t)((u / kStages) & 1));
-          if (rok) {
+      if ((threadIdx.x & 31) == 0) {
+        __threadfence_block();
+        if (atomicAdd(&done[s], 1) == NW - 1) {   // last warp out of slot s refills it
+          atomicExch(&done[s], 0);
+          int kk = k, tt = t;
+          if (advance(kk, tt, kStages)) {
             fence_proxy_async_smem();
-            issue_next();
+            issue(kk, tt, s);
           }
         }
-        if (!__shfl_sync(0xffffffffu, rok, 0)) { ok = false; break; }
       }
     }
     if (!ok) break;
@@ -422,9 +431,12 @@ __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_batched(
     }
   }
   if (!ok) set_status(&h->status, ST_TIMEOUT);
-  if (threadIdx.x == 0)
-    for (int64_t u = max((int64_t)0, issued - kStages); u < issued; ++u)
+  __syncthreads();
+  if (threadIdx.x == 0) {   // no copy may still be writing into the ring when the block exits
+    const int m = issued;
+    for (int u = max(0, m - kStages); u < m; ++u)
       (void)mbar_wait_bounded(&full[u % kStages], (uint32_t)((u / kStages) & 1));
+  }
 }
 
 // Multi-chunk polygons: fixed-order FP64 sum of their chunk partials, then the finish.

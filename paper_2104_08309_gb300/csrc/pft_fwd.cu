@@ -19,12 +19,13 @@ namespace {
 //
 // Ring protocol (no block-wide barrier inside the loop): full[s] completes when
 // the bulk copy of the tile in slot s has landed (expect_tx by the issuing
-// thread); empty[s] completes when every warp has finished reading slot s (one
-// arrive per warp).  Thread 0 issues tile t+2 after finishing tile t, once all
-// warps are done with tile t-2 (the tile that last used that slot), so warps
-// may drift up to two tiles apart without waiting for each other.  Every wait
-// is bounded; a wait that gives up sets ST_TIMEOUT and the block stops early
-// after letting its copies in flight land (also bounded).
+// thread).  When a warp has finished reading slot s its lane 0 increments
+// done[s]; the warp that brings the count to the number of warps resets it and
+// issues the copy of the tile kStages further on into the same slot.  So no
+// warp ever waits for a particular other warp: the slowest warp gates a slot's
+// refill, and the others may run up to kStages - 1 tiles ahead.  Every wait is
+// bounded and every stop decision is warp-uniform; a wait that gives up sets
+// ST_TIMEOUT and the block stops early, after letting copies in flight land.
 // ---------------------------------------------------------------------------
 template <class Pol, int R, int NT>
 __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_fwd(const typename Pol::Item* __restrict__ items, int64_t n_items,
@@ -34,11 +35,11 @@ __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_fwd(const typena
   using QT = typename Pol::QT;
   constexpr int TILE = Pol::kTile;
   constexpr int D = Pol::kDim;
-  constexpr int kLag = 2;   // tiles between the consumption of a slot and its refill
-  static_assert(kStages > kLag, "ring must hold the lagging slots");
+  constexpr int NW = NT / 32;
   __shared__ __align__(128) Item ring[kStages * TILE];
   __shared__ __align__(8) uint64_t full[kStages];
-  __shared__ __align__(8) uint64_t empty[kStages];
+  __shared__ int done[kStages];
+  __shared__ int issued;
 
   const int64_t i0 = (int64_t)blockIdx.y * per_split;
   const int64_t n = max((int64_t)0, min(per_split, n_items - i0));
@@ -60,52 +61,51 @@ __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_fwd(const typena
   typename Pol::template Acc<R> acc;
   acc.init();
 
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], NT / 32);
-    }
-    fence_mbar_init();
-  }
-  __syncthreads();
   auto issue = [&](int t) {
     const int s = t % kStages;
     const int64_t cnt = min((int64_t)TILE, n - (int64_t)t * TILE);
     const uint32_t bytes = (uint32_t)(cnt * (int64_t)sizeof(Item));
     mbar_arrive_expect_tx(&full[s], bytes);
     bulk_g2s(ring + s * TILE, src + (int64_t)t * TILE, bytes, &full[s]);
+    atomicAdd(&issued, 1);
   };
-  int issued = min(kStages, ntiles);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      done[s] = 0;
+    }
+    issued = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
   if (threadIdx.x == 0)
-    for (int t = 0; t < issued; ++t) issue(t);
+    for (int t = 0; t < min(kStages, ntiles); ++t) issue(t);
 
   bool ok = true;
   for (int t = 0; t < ntiles; ++t) {
     const int s = t % kStages;
-    // every decision to stop is made for a whole warp, so no lane is left behind at a warp sync
     if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], (uint32_t)((t / kStages) & 1)))) { ok = false; break; }
     const int cnt = (int)min((int64_t)TILE, n - (int64_t)t * TILE);
     Pol::template tile<R>(ring + s * TILE, cnt, qr, acc, th);
     __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);
-    if (threadIdx.x < 32) {   // warp 0; its lane 0 refills the ring
-      bool rok = true;
-      if (threadIdx.x == 0 && t + kLag < ntiles && t + kLag >= kStages) {
-        const int u = t + kLag - kStages;   // the tile that last used slot (t + kLag) % kStages
-        rok = mbar_wait_bounded(&empty[u % kStages], (uint32_t)((u / kStages) & 1));
-        if (rok) {
+    if ((threadIdx.x & 31) == 0) {
+      __threadfence_block();                       // this warp's reads of slot s come first
+      if (atomicAdd(&done[s], 1) == NW - 1) {      // last warp out of slot s refills it
+        atomicExch(&done[s], 0);
+        if (t + kStages < ntiles) {
           fence_proxy_async_smem();
-          issue(t + kLag);
-          issued = t + kLag + 1;
+          issue(t + kStages);
         }
       }
-      if (!__shfl_sync(0xffffffffu, rok, 0)) { ok = false; break; }
     }
   }
   if (!ok) set_status(status, ST_TIMEOUT);
-  if (threadIdx.x == 0)   // no copy may still be writing into the ring when the block exits
-    for (int u = max(0, issued - kStages); u < issued; ++u)
+  __syncthreads();   // reached by every thread: stop decisions above are per warp, never inside a warp
+  if (threadIdx.x == 0) {   // no copy may still be writing into the ring when the block exits
+    const int m = issued;
+    for (int u = max(0, m - kStages); u < m; ++u)
       (void)mbar_wait_bounded(&full[u % kStages], (uint32_t)((u / kStages) & 1));
+  }
   if (!ok) return;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
