@@ -56,7 +56,7 @@ def parse():
                    help="c5: the benchmark workload; c5small: same mesh family at subdivision 6 on 64^3 Q "
                         "(for profiling captures)")
     p.add_argument("--q-per-thread", type=int, default=2)
-    p.add_argument("--block-threads", type=int, default=256)
+    p.add_argument("--block-threads", type=int, default=128)
     p.add_argument("--tau", type=float, default=0.0, help="face_series_tau (0 = library default)")
     p.add_argument("--no-extra", action="store_true", help="skip the secondary paths (batched 2D)")
     return p.parse_args()
@@ -231,7 +231,10 @@ def bench_batched(dev, warmup, steps):
     w = synth.workload_c3()
     vd, qd = torch.from_numpy(w.verts).to(dev), torch.from_numpy(w.q).to(dev)
     offd = torch.from_numpy(w.poly_off).to(dev)
-    prep = pft.pft2d_batched_prepare(w.poly_off, w.q.shape[0], device=dev)
+    from paper_2104_08309_gb300 import autotune
+    tuned = autotune.tune_batched2d(vd, w.poly_off, qd,
+                                    path=os.path.join(ROOT, "gpurun_out", "tune_cache.json"))
+    prep = pft.pft2d_batched_prepare(w.poly_off, w.q.shape[0], options=tuned, device=dev)
     out = torch.empty(w.poly_off.size - 1, w.q.shape[0], 2, dtype=torch.float64, device=dev)
     s = torch.cuda.Stream(dev)
     s.wait_stream(torch.cuda.current_stream(dev))
@@ -259,6 +262,8 @@ def bench_batched(dev, warmup, steps):
     return {"value": pairs / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "pairs_per_step": pairs,
             "polygons": int(w.poly_off.size - 1), "segments": int(w.verts.shape[0]), "q_points": int(w.q.shape[0]),
             "launches_per_step": int(launches), "cuda_graph": True, "device_status": int(status),
+            "launch": {"q_per_thread": tuned["q_per_thread"], "block_threads": tuned["block_threads"],
+                       "chosen_by": "autotune"},
             "l2": "flushed between steps"}
 
 

@@ -28,7 +28,7 @@ int resolve(const pft_options* o, int dim, Opts& out) {
   if (p.precision != PFT_FP32_COMPENSATED && p.precision != PFT_FP64) return PFT_ERR_INVALID_ARG;
   out.fp64 = (p.precision == PFT_FP64);
   out.r = p.q_per_thread ? p.q_per_thread : (out.fp64 ? 1 : (dim == 3 ? 2 : 4));
-  out.nt = p.block_threads ? p.block_threads : (out.fp64 ? 128 : 256);
+  out.nt = p.block_threads ? p.block_threads : ((out.fp64 || dim == 3) ? 128 : 256);
   const bool r_ok = out.fp64 ? (out.r == 1 || out.r == 2) : (out.r == 1 || out.r == 2 || out.r == 4 || out.r == 8);
   if (!r_ok || (out.nt != 128 && out.nt != 256)) return PFT_ERR_UNSUPPORTED;
   if (p.k_splits < 0) return PFT_ERR_INVALID_ARG;
