@@ -160,11 +160,19 @@ int pft3d_mesh(const float* verts, int64_t n_verts, const int32_t* faces, int64_
                void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
 
 /*
- * Backward passes (adjoints of the calls above; not in the paper).
+ * Backward passes: adjoints of pft2d_polygons / pft3d_mesh with respect to the
+ * vertices (the paper has no gradients; they differentiate its sums, Eq. 6 and
+ * Eq. 14, term by term).
  *  grad_out   [n_q][2] float64: (dL/dRe F, dL/dIm F) at each Q.
  *  grad_verts [n_verts][d] float32: dL/dverts = sum_Q Re(conj(g_Q) dF(Q)/dverts),
  *             g_Q = grad_out[Q][0] + i grad_out[Q][1].  Overwritten.
- * Segment/face terms are recomputed, not stored by the forward call.
+ * Segment/face terms are recomputed (not stored by the forward call) and
+ * differentiated in reverse mode exactly as the FP32 forward evaluates them, in
+ * FP32 with compensated sums; Q = 0 and |Q| max|r - c| < 0.25 use an FP64
+ * boundary-flux series instead.  Options: precision must be
+ * PFT_FP32_COMPENSATED; launch fields 0; face_series_tau as in the forward.
+ * Vertex sums run in a fixed order (3D: through a device-built, sorted
+ * vertex -> face-corner list), so results are reproducible.
  */
 size_t pft2d_backward_workspace_size(int64_t n_verts, int64_t n_loops, int64_t n_q, const pft_options* opts);
 size_t pft3d_backward_workspace_size(int64_t n_verts, int64_t n_faces, int64_t n_q, const pft_options* opts);
@@ -174,6 +182,9 @@ int pft2d_polygons_backward(const float* verts, int64_t n_verts, const int64_t* 
 int pft3d_mesh_backward(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces,
                         const double* q, int64_t n_q, const double* grad_out, float* grad_verts,
                         void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
+
+/* Kernel launches enqueued by the most recent backward call on this host thread. */
+int pft_backward_last_launch_count(void);
 
 /*
  * pft3d_mesh without a workspace argument, for callers that cannot allocate

@@ -59,6 +59,7 @@ SIGNATURES = {
     "pft_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pft_version": (ctypes.c_int, []),
     "pft_last_launch_count": (ctypes.c_int, []),
+    "pft_backward_last_launch_count": (ctypes.c_int, []),
 }
 
 _lock = threading.Lock()

@@ -201,19 +201,6 @@ int pft3d_mesh(const float* verts, int64_t n_verts, const int32_t* faces, int64_
   return PFT_OK;
 }
 
-size_t pft2d_backward_workspace_size(int64_t, int64_t, int64_t, const pft_options*) { return 0; }
-size_t pft3d_backward_workspace_size(int64_t, int64_t, int64_t, const pft_options*) { return 0; }
-int pft2d_polygons_backward(const float*, int64_t, const int64_t*, int64_t, const double*, int64_t, const double*,
-                            float*, void*, size_t, const pft_options*, void*) {
-  g_last_launches = 0;
-  return PFT_ERR_UNSUPPORTED;
-}
-int pft3d_mesh_backward(const float*, int64_t, const int32_t*, int64_t, const double*, int64_t, const double*,
-                        float*, void*, size_t, const pft_options*, void*) {
-  g_last_launches = 0;
-  return PFT_ERR_UNSUPPORTED;
-}
-
 int pft_status(const void* ws, void* stream) {
   if (ws == nullptr) return PFT_ERR_INVALID_ARG;
   uint32_t word = 0;

@@ -1,0 +1,769 @@
+// pft_bwd.cu -- adjoints of the forward transforms (vertex gradients of a loss on F).
+//
+// For g_Q = dL/dRe F(Q) + i dL/dIm F(Q) the calls return
+//   dL/dv = sum_Q Re(conj(g_Q) dF(Q)/dv).
+// The segment / face terms are recomputed, not stored by the forward call, and
+// differentiated in reverse mode exactly as the forward kernels evaluate them
+// (the same branches, phases and polynomials), in FP32 with compensated sums:
+//  * k_bq: per Q, the weight gt = g exp(-iQ.c) * scale / |Q|^2 that carries the
+//    finalize factors onto each pair (scale 2 in 2D for the half vectors), and
+//    the list of Q = 0 / small-|Q| points, which take an FP64 path instead;
+//  * k_bwd2d / k_bwd3d: thread <-> segment or face, Q records streamed through
+//    shared memory by the same bulk-copy ring as the forward kernels, adjoints
+//    of the record fields accumulated per thread, FP64 partials per Q chunk;
+//  * FP64 small-|Q| contributions from the boundary-flux (shape derivative)
+//    series, then a fixed-order gather to the vertices (3D through a vertex ->
+//    face-corner CSR built on the device and sorted, so sums are reproducible).
+#include <algorithm>
+#include <cstring>
+
+#include "pft_pairs.cuh"
+
+namespace pft {
+namespace {
+
+constexpr int kBwdNT = 128;        // threads per block of the pair kernels (one item each)
+constexpr int kQTile = 128;        // Q records per shared-memory tile
+constexpr int kAux = 256;          // threads per block of the auxiliary kernels
+
+struct __align__(16) QRec {
+  float qx, qy, qz, gr, gi, pad0, pad1, pad2;
+};
+static_assert(sizeof(QRec) == 32, "Q record is two float4");
+
+// ---------------------------------------------------------------------------
+// Generic bulk-copy ring over an array of records (same protocol as k_fwd: the
+// last warp out of a slot issues the tile kStages further on).
+// ---------------------------------------------------------------------------
+template <class Item, int TILE, int NT>
+struct Ring {
+  Item* slots;
+  uint64_t* full;
+  int* done;
+  int* issued;
+  const Item* src;
+  int64_t n;
+  int ntiles;
+
+  __device__ void issue(int t) {
+    const int s = t % kStages;
+    const int64_t c = min((int64_t)TILE, n - (int64_t)t * TILE);
+    const uint32_t bytes = (uint32_t)(c * (int64_t)sizeof(Item));
+    mbar_arrive_expect_tx(&full[s], bytes);
+    bulk_g2s(slots + s * TILE, src + (int64_t)t * TILE, bytes, &full[s]);
+    atomicAdd(issued, 1);
+  }
+  __device__ void start() {   // every thread; contains a block barrier
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < kStages; ++s) {
+        mbar_init(&full[s], 1);
+        done[s] = 0;
+      }
+      *issued = 0;
+      fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int t = 0; t < min(kStages, ntiles); ++t) issue(t);
+  }
+  // warp-uniform: true when tile t is in its slot
+  __device__ bool wait(int t) {
+    return __all_sync(0xffffffffu, mbar_wait_bounded(&full[t % kStages], (uint32_t)((t / kStages) & 1)));
+  }
+  __device__ const Item* tile(int t) const { return slots + (t % kStages) * TILE; }
+  __device__ int count(int t) const { return (int)min((int64_t)TILE, n - (int64_t)t * TILE); }
+  __device__ void release(int t) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+      __threadfence_block();
+      const int s = t % kStages;
+      if (atomicAdd(&done[s], 1) == NT / 32 - 1) {
+        atomicExch(&done[s], 0);
+        if (t + kStages < ntiles) {
+          fence_proxy_async_smem();
+          issue(t + kStages);
+        }
+      }
+    }
+  }
+  __device__ void finish() {   // every thread; contains a block barrier
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int m = *issued;
+      for (int u = max(0, m - kStages); u < m; ++u)
+        (void)mbar_wait_bounded(&full[u % kStages], (uint32_t)((u / kStages) & 1));
+    }
+  }
+};
+
+// sinc(u) and its derivative: the Chebyshev polynomial and its derivative on
+// |u| <= pi, sin and cos of the turn-reduced argument beyond.
+__device__ __forceinline__ void sinc_d(float u, float& S, float& dS) {
+  const float v = u * u;
+  float p = fmaf(v, 1.361159657e-10f, -2.472836691e-8f);
+  p = fmaf(v, p, 2.753580020e-6f);
+  p = fmaf(v, p, -1.984053088e-4f);
+  p = fmaf(v, p, 8.333321661e-3f);
+  p = fmaf(v, p, -1.666666567e-1f);
+  S = fmaf(v, p, 1.0f);
+  float d = fmaf(v, 6.0f * 1.361159657e-10f, 5.0f * -2.472836691e-8f);   // p'(v)
+  d = fmaf(v, d, 4.0f * 2.753580020e-6f);
+  d = fmaf(v, d, 3.0f * -1.984053088e-4f);
+  d = fmaf(v, d, 2.0f * 8.333321661e-3f);
+  d = fmaf(v, d, -1.666666567e-1f);
+  dS = 2.0f * u * d;
+  if (v > kPi2) {
+    float s, c;
+    sincos_turns(u * kInvTwoPi, &s, &c);
+    const float r = rcp_approx(u);
+    S = s * r;
+    dS = (c - S) * r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-pair adjoints.
+// ---------------------------------------------------------------------------
+
+// 2D: term -i w S(u) exp(i ph) of one (Q, segment) pair with weight gt; adds the
+// adjoints of the record fields (m.x, m.y, h.x, h.y).
+__device__ __forceinline__ void seg_adj(const QRec& Q, const float4 s, float (&a)[4]) {
+  const float ph = fmaf(Q.qx, s.x, Q.qy * s.y);
+  const float u = fmaf(Q.qx, s.z, Q.qy * s.w);
+  const float w = fmaf(Q.qx, s.w, -Q.qy * s.z);
+  float sn, cs;
+  __sincosf(ph, &sn, &cs);
+  float S, dS;
+  sinc_d(u, S, dS);
+  const float A = fmaf(Q.gr, sn, -Q.gi * cs);   // Re(conj(gt)(sin - i cos))
+  const float B = fmaf(Q.gr, cs, Q.gi * sn);    // dA/dph
+  const float wb = S * A, Sb = w * A, phb = w * S * B;
+  const float ub = Sb * dS;
+  a[0] = fmaf(phb, Q.qx, a[0]);
+  a[1] = fmaf(phb, Q.qy, a[1]);
+  a[2] = fmaf(ub, Q.qx, fmaf(-wb, Q.qy, a[2]));
+  a[3] = fmaf(ub, Q.qy, fmaf(wb, Q.qx, a[3]));
+}
+
+// 3D: face term J = -s exp(i mu) Z (series or edge branch, chosen as in the
+// forward kernel, warp-uniform over the lanes' faces) with weight gt; adds the
+// adjoints of the 12 record fields g, q0, q1, N (same order as Face32).
+__device__ __forceinline__ void face_adj(const QRec& Q, const float4 A, const float4 B, const float4 C, Thr th,
+                                         float (&a)[12]) {
+  const float qx = Q.qx, qy = Q.qy, qz = Q.qz;
+  float mu, a0, a1, s, P;
+  face_common(qx, qy, qz, A, B, C, mu, a0, a1, s, P);
+  const bool series = __all_sync(0xffffffffu, P < th.hi) || (P < th.lo);
+  float sm, cm;
+  __sincosf(mu, &sm, &cm);
+  float zr, zi;
+  // forward Z, then (after the common adjoints below) its reverse pass
+  float dGre_dP = 0.f, dGre_dT = 0.f, dGim_dP = 0.f, dGim_dT = 0.f, T = 0.f;
+  float Xx = 0.f, Xy = 0.f, Xz = 0.f, x2 = 0.f, inv = 0.f, w[3] = {0.f, 0.f, 0.f}, S[3], dS[3], sp[3], cp[3];
+  if (series) {
+    T = -(a0 * a1) * (a0 + a1);
+    const float T2 = T * T;
+    float gre = fmaf(P, 2.75573192e-7f, -2.48015873e-5f);
+    gre = fmaf(P, gre, 1.38888889e-3f);
+    gre = fmaf(P, gre, -4.16666667e-2f);
+    gre = fmaf(P, gre, 0.5f);
+    const float k2 = fmaf(P, 8.26719577e-7f, -2.48015873e-5f);
+    gre = fmaf(T2, k2, gre);
+    const float r = fmaf(P, fmaf(P, -8.26719577e-6f, 3.96825397e-4f), -8.33333333e-3f);
+    const float gim = T * r;
+    zr = -gim;
+    zi = gre;
+    float d = fmaf(P, 4.0f * 2.75573192e-7f, 3.0f * -2.48015873e-5f);
+    d = fmaf(P, d, 2.0f * 1.38888889e-3f);
+    dGre_dP = fmaf(P, d, -4.16666667e-2f) + T2 * 8.26719577e-7f;
+    dGre_dT = 2.0f * T * k2;
+    dGim_dP = T * fmaf(P, 2.0f * -8.26719577e-6f, 3.96825397e-4f);
+    dGim_dT = r;
+  } else {
+    const float nx = C.y, ny = C.z, nz = C.w;
+    Xx = fmaf(ny, qz, -nz * qy);
+    Xy = fmaf(nz, qx, -nx * qz);
+    Xz = fmaf(nx, qy, -ny * qx);
+    x2 = fmaf(Xx, Xx, fmaf(Xy, Xy, Xz * Xz));
+    const float b0 = fmaf(A.w, Xx, fmaf(B.x, Xy, B.y * Xz));
+    const float b1 = fmaf(B.z, Xx, fmaf(B.w, Xy, C.x * Xz));
+    w[0] = b1 - b0;
+    w[1] = fmaf(-2.0f, b1, -b0);
+    w[2] = fmaf(2.0f, b0, b1);
+    const float h0 = 0.5f * a0, h1 = 0.5f * a1;
+    const float u[3] = {h1 - h0, fmaf(-2.0f, h1, -h0), fmaf(2.0f, h0, h1)};
+    __sincosf(-h0, &sp[1], &cp[1]);
+    __sincosf(-h1, &sp[2], &cp[2]);
+    cp[0] = fmaf(cp[1], cp[2], -sp[1] * sp[2]);
+    sp[0] = -fmaf(sp[1], cp[2], cp[1] * sp[2]);
+    float sr = 0.f, si = 0.f;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      sinc_d(u[l], S[l], dS[l]);
+      const float ws = w[l] * S[l];
+      sr = fmaf(ws, cp[l], sr);
+      si = fmaf(ws, sp[l], si);
+    }
+    inv = (x2 > 0.f) ? rcp_approx(x2) : 0.f;
+    zr = sr * inv;
+    zi = si * inv;
+  }
+  // J = -s W, W = exp(i mu) Z
+  const float Wr = fmaf(cm, zr, -sm * zi), Wi = fmaf(cm, zi, sm * zr);
+  const float sb = -fmaf(Q.gr, Wr, Q.gi * Wi);       // dc/ds
+  const float mub = s * fmaf(Q.gr, Wi, -Q.gi * Wr);  // dc/dmu
+  const float ghr = -s * fmaf(Q.gr, cm, Q.gi * sm);  // ghat = -s gt exp(-i mu): dc = Re(conj(ghat) dZ)
+  const float ghi = -s * fmaf(Q.gi, cm, -Q.gr * sm);
+  float a0b, a1b;
+  if (series) {
+    const float Pb = fmaf(ghi, dGre_dP, -ghr * dGim_dP);
+    const float Tb = fmaf(ghi, dGre_dT, -ghr * dGim_dT);
+    const float e0 = fmaf(2.0f, a0, a1), e1 = fmaf(2.0f, a1, a0);
+    a0b = e0 * fmaf(-Tb, a1, Pb);
+    a1b = e1 * fmaf(-Tb, a0, Pb);
+  } else {
+    const float Sr = ghr * inv, Si = ghi * inv;        // adjoint of the edge sum
+    const float x2b = -fmaf(ghr, zr, ghi * zi) * inv;
+    float wb[3], psib[3], ub[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const float R = fmaf(Sr, cp[l], Si * sp[l]);
+      const float I = fmaf(Sr, sp[l], -Si * cp[l]);
+      wb[l] = S[l] * R;
+      psib[l] = -w[l] * S[l] * I;
+      ub[l] = w[l] * R * dS[l];
+    }
+    const float h0b = psib[0] - psib[1] - ub[0] - ub[1] + 2.0f * ub[2];
+    const float h1b = psib[0] - psib[2] + ub[0] - 2.0f * ub[1] + ub[2];
+    a0b = 0.5f * h0b;
+    a1b = 0.5f * h1b;
+    const float b0b = -wb[0] - wb[1] + 2.0f * wb[2];
+    const float b1b = wb[0] - 2.0f * wb[1] + wb[2];
+    const float Xbx = fmaf(b0b, A.w, fmaf(b1b, B.z, 2.0f * x2b * Xx));
+    const float Xby = fmaf(b0b, B.x, fmaf(b1b, B.w, 2.0f * x2b * Xy));
+    const float Xbz = fmaf(b0b, B.y, fmaf(b1b, C.x, 2.0f * x2b * Xz));
+    a[3] = fmaf(b0b, Xx, a[3]);
+    a[4] = fmaf(b0b, Xy, a[4]);
+    a[5] = fmaf(b0b, Xz, a[5]);
+    a[6] = fmaf(b1b, Xx, a[6]);
+    a[7] = fmaf(b1b, Xy, a[7]);
+    a[8] = fmaf(b1b, Xz, a[8]);
+    a[9] = fmaf(qy, Xbz, fmaf(-qz, Xby, a[9]));    // N += Q x Xbar
+    a[10] = fmaf(qz, Xbx, fmaf(-qx, Xbz, a[10]));
+    a[11] = fmaf(qx, Xby, fmaf(-qy, Xbx, a[11]));
+  }
+  a[0] = fmaf(mub, qx, a[0]);
+  a[1] = fmaf(mub, qy, a[1]);
+  a[2] = fmaf(mub, qz, a[2]);
+  a[3] = fmaf(a0b, qx, a[3]);
+  a[4] = fmaf(a0b, qy, a[4]);
+  a[5] = fmaf(a0b, qz, a[5]);
+  a[6] = fmaf(a1b, qx, a[6]);
+  a[7] = fmaf(a1b, qy, a[7]);
+  a[8] = fmaf(a1b, qz, a[8]);
+  a[9] = fmaf(sb, qx, a[9]);
+  a[10] = fmaf(sb, qy, a[10]);
+  a[11] = fmaf(sb, qz, a[11]);
+}
+
+// ---------------------------------------------------------------------------
+// Kernels.
+// ---------------------------------------------------------------------------
+
+// Q records: Q rounded to FP32 (as the forward uses it) and gt; Q = 0 and small
+// |Q| go to the FP64 list with a zero weight here.
+template <int D>
+__global__ void k_bq(const double* __restrict__ q, const double* __restrict__ g, int64_t n_q, WsHeader* h,
+                     double scale, QRec* rec, int32_t* small) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_q) return;
+  float qf[3] = {0.f, 0.f, 0.f};
+  for (int d = 0; d < D; ++d) qf[d] = (float)q[D * i + d];
+  const double Q[3] = {qf[0], qf[1], qf[2]};
+  const double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
+  QRec r{qf[0], qf[1], qf[2], 0.f, 0.f, 0.f, 0.f, 0.f};
+  const double rmax = (double)__uint_as_float(h->rmax_bits);
+  if (q2 == 0.0 || sqrt(q2) * rmax < kTauSmallQ) {
+    small[atomicAdd(&h->small_q_count, 1u)] = (int32_t)i;
+  } else {
+    double sp, cp;
+    sincos(-(Q[0] * h->center[0] + Q[1] * h->center[1] + Q[2] * h->center[2]), &sp, &cp);
+    const double gr = g[2 * i], gi = g[2 * i + 1], k = scale / q2;
+    r.gr = (float)(k * (gr * cp - gi * sp));
+    r.gi = (float)(k * (gr * sp + gi * cp));
+  }
+  rec[i] = r;
+}
+
+// Thread <-> item (segment or face); Q chunk blockIdx.y; FP64 partial per (chunk, item, field).
+template <int D, int NF>
+__global__ void __launch_bounds__(kBwdNT) k_bwd(const void* __restrict__ items, int64_t n_items,
+                                                const QRec* __restrict__ rec, int64_t n_q, int64_t per_split,
+                                                Thr th, double* __restrict__ partial, uint32_t* status) {
+  __shared__ __align__(128) QRec slots[kStages * kQTile];
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ int done[kStages];
+  __shared__ int issued;
+  const int64_t m = blockIdx.x * (int64_t)kBwdNT + threadIdx.x;
+  float4 F[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+  if (m < n_items) {
+    if constexpr (D == 2) F[0] = reinterpret_cast<const float4*>(items)[m];
+    else for (int k = 0; k < 3; ++k) F[k] = reinterpret_cast<const float4*>(items)[3 * m + k];
+  }
+  const int64_t q0 = (int64_t)blockIdx.y * per_split;
+  const int64_t nq = max((int64_t)0, min(per_split, n_q - q0));
+  Ring<QRec, kQTile, kBwdNT> ring{slots, full, done, &issued, rec + q0, nq, (int)((nq + kQTile - 1) / kQTile)};
+  ring.start();
+  CAcc acc[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) acc[f].init();
+  bool ok = true;
+  for (int t = 0; t < ring.ntiles; ++t) {
+    if (!ring.wait(t)) { ok = false; break; }
+    const QRec* tq = ring.tile(t);
+    const int cnt = ring.count(t);
+    float a[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) a[f] = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < cnt; ++j) {
+      const QRec Q = tq[j];
+      if constexpr (D == 2) seg_adj(Q, F[0], *reinterpret_cast<float(*)[4]>(a));
+      else face_adj(Q, F[0], F[1], F[2], th, *reinterpret_cast<float(*)[12]>(a));
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) acc[f].add(a[f]);
+    ring.release(t);
+  }
+  if (!ok) set_status(status, ST_TIMEOUT);
+  ring.finish();
+  if (!ok || m >= n_items) return;
+  double* dst = partial + ((int64_t)blockIdx.y * n_items + m) * NF;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) dst[f] = (double)acc[f].hi + (double)acc[f].lo;
+}
+
+// 2D vertex gradients: record adjoints of segment j (start) and of the segment
+// ending at j, summed over Q chunks in order, plus FP64 small-|Q| terms.
+// Small |Q|: dF/dp0 = nu e^{i a0} (J0 - J1), dF/dp1 = nu e^{i a0} J1 with
+// nu = (dy, -dx), J0 = int_0^1 e^{itd}, J1 = int_0^1 t e^{itd} (series, |d| small).
+__device__ __forceinline__ void seg_small(const double* p0, const double* p1, double qx, double qy, double gr,
+                                          double gi, double ph_c, double* g0, double* g1) {
+  const double a0 = qx * p0[0] + qy * p0[1], d = qx * (p1[0] - p0[0]) + qy * (p1[1] - p0[1]);
+  double j0r = 0, j0i = 0, j1r = 0, j1i = 0, tr = 1, ti = 0;   // term (i d)^n / n!
+  for (int n = 0; n < 24; ++n) {
+    j0r += tr / (n + 1); j0i += ti / (n + 1);
+    j1r += tr / (n + 2); j1i += ti / (n + 2);
+    const double nr = -ti * d / (n + 1), ni = tr * d / (n + 1);
+    tr = nr; ti = ni;
+  }
+  double se, ce;
+  sincos(a0 + ph_c, &se, &ce);   // exp(i(Q.c + Q.(p0 - c)))
+  // conj(g) * e * J  -> real part
+  const double er0 = ce * (j0r - j1r) - se * (j0i - j1i), ei0 = ce * (j0i - j1i) + se * (j0r - j1r);
+  const double er1 = ce * j1r - se * j1i, ei1 = ce * j1i + se * j1r;
+  const double c0 = gr * er0 + gi * ei0, c1 = gr * er1 + gi * ei1;
+  const double nu[2] = {p1[1] - p0[1], -(p1[0] - p0[0])};
+  g0[0] += c0 * nu[0]; g0[1] += c0 * nu[1];
+  g1[0] += c1 * nu[0]; g1[1] += c1 * nu[1];
+}
+
+__global__ void k_bvert2d(const float* __restrict__ v, int64_t nv, const int64_t* __restrict__ off, int64_t nl,
+                          const double* __restrict__ partial, int ks, const WsHeader* h,
+                          const int32_t* __restrict__ small, const double* __restrict__ q,
+                          const double* __restrict__ g, float* __restrict__ grad) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= nv) return;
+  int64_t lo = 0, hi = nl;
+  while (lo + 1 < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (off[mid] <= j) lo = mid; else hi = mid;
+  }
+  const int64_t s0 = off[lo], s1 = off[lo + 1];
+  int64_t jp = (j > s0) ? j - 1 : s1 - 1;   // segment ending at j
+  int64_t jn = (j + 1 < s1) ? j + 1 : s0;    // end of segment j
+  if (jp < 0 || jp >= nv) jp = j;
+  if (jn < 0 || jn >= nv) jn = j;
+  double mS[2] = {0, 0}, hS[2] = {0, 0}, mP[2] = {0, 0}, hP[2] = {0, 0};
+  for (int s = 0; s < ks; ++s) {
+    const double* a = partial + ((int64_t)s * nv + j) * 4;
+    const double* b = partial + ((int64_t)s * nv + jp) * 4;
+    mS[0] += a[0]; mS[1] += a[1]; hS[0] += a[2]; hS[1] += a[3];
+    mP[0] += b[0]; mP[1] += b[1]; hP[0] += b[2]; hP[1] += b[3];
+  }
+  // m = (p0+p1)/2, h = (p1-p0)/2: start of segment j gets mbar/2 - hbar/2, end of segment jp gets mbar/2 + hbar/2
+  double gx = 0.5 * (mS[0] - hS[0]) + 0.5 * (mP[0] + hP[0]);
+  double gy = 0.5 * (mS[1] - hS[1]) + 0.5 * (mP[1] + hP[1]);
+  const uint32_t ns = h->small_q_count;
+  if (ns) {
+    const double c[2] = {h->center[0], h->center[1]};
+    const double pj[2] = {(double)v[2 * j] - c[0], (double)v[2 * j + 1] - c[1]};
+    const double pn[2] = {(double)v[2 * jn] - c[0], (double)v[2 * jn + 1] - c[1]};
+    const double pp[2] = {(double)v[2 * jp] - c[0], (double)v[2 * jp + 1] - c[1]};
+    for (uint32_t e = 0; e < ns; ++e) {   // fixed order is not needed for a plain sum of a few terms, but kept
+      const int64_t iq = small[e];
+      const double qx = (double)(float)q[2 * iq], qy = (double)(float)q[2 * iq + 1];
+      const double phc = qx * c[0] + qy * c[1];
+      double d0[2] = {0, 0}, d1[2] = {0, 0}, e0[2] = {0, 0}, e1[2] = {0, 0};
+      seg_small(pj, pn, qx, qy, g[2 * iq], g[2 * iq + 1], phc, d0, d1);   // j is the start
+      seg_small(pp, pj, qx, qy, g[2 * iq], g[2 * iq + 1], phc, e0, e1);   // j is the end
+      gx += d0[0] + e1[0];
+      gy += d0[1] + e1[1];
+    }
+  }
+  grad[2 * j] = (float)gx;
+  grad[2 * j + 1] = (float)gy;
+}
+
+// 3D: per face, chunk sums of the record adjoints -> corner adjoints (FP64), plus
+// small-|Q| corner terms dF/dp_k = exp(iQ.c) N sum_j i^j h_j(a, a_k)/(j+3)!.
+__global__ void k_bcorner3d(const float* __restrict__ v, int64_t nv, const int32_t* __restrict__ f, int64_t nf,
+                            const double* __restrict__ partial, int ks, const WsHeader* h,
+                            const int32_t* __restrict__ small, const double* __restrict__ q,
+                            const double* __restrict__ g, double* __restrict__ corner) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= nf) return;
+  double* out = corner + 9 * m;
+  const int32_t id[3] = {f[3 * m], f[3 * m + 1], f[3 * m + 2]};
+  if (id[0] < 0 || id[1] < 0 || id[2] < 0 || id[0] >= nv || id[1] >= nv || id[2] >= nv) {
+    for (int k = 0; k < 9; ++k) out[k] = 0.0;
+    return;
+  }
+  double ab[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int s = 0; s < ks; ++s) {
+    const double* a = partial + ((int64_t)s * nf + m) * 12;
+    for (int k = 0; k < 12; ++k) ab[k] += a[k];
+  }
+  const double c[3] = {h->center[0], h->center[1], h->center[2]};
+  double P[3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int d = 0; d < 3; ++d) P[k][d] = (double)v[3 * (int64_t)id[k] + d] - c[d];
+  // records: g = (P0+P1+P2)/3, q0 = P0 - g, q1 = P1 - g, N = (P1-P0) x (P2-P0)
+  double pb[3][3];
+  for (int d = 0; d < 3; ++d) {
+    const double gt = ab[d] - ab[3 + d] - ab[6 + d];
+    pb[0][d] = ab[3 + d] + gt / 3.0;
+    pb[1][d] = ab[6 + d] + gt / 3.0;
+    pb[2][d] = gt / 3.0;
+  }
+  const double e1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+  const double e2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+  const double* Nb = ab + 9;
+  const double e1b[3] = {e2[1] * Nb[2] - e2[2] * Nb[1], e2[2] * Nb[0] - e2[0] * Nb[2], e2[0] * Nb[1] - e2[1] * Nb[0]};
+  const double e2b[3] = {Nb[1] * e1[2] - Nb[2] * e1[1], Nb[2] * e1[0] - Nb[0] * e1[2], Nb[0] * e1[1] - Nb[1] * e1[0]};
+  for (int d = 0; d < 3; ++d) {
+    pb[1][d] += e1b[d];
+    pb[2][d] += e2b[d];
+    pb[0][d] -= e1b[d] + e2b[d];
+  }
+  const uint32_t ns = h->small_q_count;
+  if (ns) {
+    const double N[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    for (uint32_t e = 0; e < ns; ++e) {
+      const int64_t iq = small[e];
+      const double Q[3] = {(double)(float)q[3 * iq], (double)(float)q[3 * iq + 1], (double)(float)q[3 * iq + 2]};
+      const double al[3] = {Q[0] * P[0][0] + Q[1] * P[0][1] + Q[2] * P[0][2],
+                            Q[0] * P[1][0] + Q[1] * P[1][1] + Q[2] * P[1][2],
+                            Q[0] * P[2][0] + Q[1] * P[2][1] + Q[2] * P[2][2]};
+      const double mu = (al[0] + al[1] + al[2]) / 3.0;
+      double se, ce;
+      sincos(mu + Q[0] * c[0] + Q[1] * c[1] + Q[2] * c[2], &se, &ce);
+      for (int k = 0; k < 3; ++k) {
+        // sum_j i^j h_j(x) / (j+3)!, x = (a0, a1, a2, a_k) centred at mu, 18 terms
+        const double x[4] = {al[0] - mu, al[1] - mu, al[2] - mu, al[k] - mu};
+        double hh[19];
+        hh[0] = 1.0;
+        for (int j = 1; j <= 18; ++j) hh[j] = 0.0;
+        for (int t = 0; t < 4; ++t)
+          for (int j = 1; j <= 18; ++j) hh[j] = fma(x[t], hh[j - 1], hh[j]);
+        double sr = 0.0, si = 0.0, inv = 1.0 / 6.0;
+        for (int j = 0; j <= 18; ++j) {
+          const double t = hh[j] * inv;
+          switch (j & 3) { case 0: sr += t; break; case 1: si += t; break; case 2: sr -= t; break; default: si -= t; }
+          inv /= (double)(j + 4);
+        }
+        const double hr = ce * sr - se * si, hi = ce * si + se * sr;
+        const double cf = g[2 * iq] * hr + g[2 * iq + 1] * hi;   // Re(conj(g) * H)
+        for (int d = 0; d < 3; ++d) pb[k][d] += cf * N[d];
+      }
+    }
+  }
+  for (int k = 0; k < 3; ++k)
+    for (int d = 0; d < 3; ++d) out[3 * k + d] = pb[k][d];
+}
+
+// Vertex -> face-corner CSR: degrees, exclusive scan, fill, per-vertex sort.
+__global__ void k_deg(const int32_t* __restrict__ f, int64_t nf, int64_t nv, int32_t* deg) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= 3 * nf) return;
+  const int32_t vtx = f[i];
+  if (vtx >= 0 && vtx < nv) atomicAdd(&deg[vtx], 1);
+}
+
+// Exclusive scan in three steps: per-block scan with block totals, scan of the
+// totals (one block, sequential over chunks), add back.
+__global__ void k_scan_block(const int32_t* __restrict__ in, int64_t n, int64_t* out, int64_t* block_tot) {
+  __shared__ int64_t sh[kAux];
+  const int64_t i = blockIdx.x * (int64_t)kAux + threadIdx.x;
+  int64_t x = (i < n) ? in[i] : 0;
+  sh[threadIdx.x] = x;
+  __syncthreads();
+  for (int o = 1; o < kAux; o <<= 1) {
+    const int64_t y = (threadIdx.x >= (unsigned)o) ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += y;
+    __syncthreads();
+  }
+  if (i < n) out[i] = sh[threadIdx.x] - x;
+  if (threadIdx.x == kAux - 1) block_tot[blockIdx.x] = sh[kAux - 1];
+}
+
+__global__ void k_scan_totals(int64_t* block_tot, int64_t nb) {
+  if (threadIdx.x != 0) return;
+  int64_t run = 0;
+  for (int64_t b = 0; b < nb; ++b) {
+    const int64_t t = block_tot[b];
+    block_tot[b] = run;
+    run += t;
+  }
+}
+
+__global__ void k_scan_add(int64_t* out, int64_t n, const int64_t* block_tot) {
+  const int64_t i = blockIdx.x * (int64_t)kAux + threadIdx.x;
+  if (i < n) out[i] += block_tot[blockIdx.x];
+}
+
+__global__ void k_fill(const int32_t* __restrict__ f, int64_t nf, int64_t nv, const int64_t* __restrict__ start,
+                       int32_t* cursor, int32_t* list) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= 3 * nf) return;
+  const int32_t vtx = f[i];
+  if (vtx < 0 || vtx >= nv) return;
+  list[start[vtx] + atomicAdd(&cursor[vtx], 1)] = (int32_t)i;   // corner id 3m + k
+}
+
+__global__ void k_gather3d(int64_t nv, const int64_t* __restrict__ start, const int32_t* __restrict__ deg,
+                           int32_t* list, const double* __restrict__ corner, float* __restrict__ grad) {
+  const int64_t vtx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (vtx >= nv) return;
+  int32_t* L = list + start[vtx];
+  const int n = deg[vtx];
+  for (int a = 1; a < n; ++a) {   // insertion sort: corner ids in increasing order
+    const int32_t key = L[a];
+    int b = a - 1;
+    while (b >= 0 && L[b] > key) { L[b + 1] = L[b]; --b; }
+    L[b + 1] = key;
+  }
+  double s[3] = {0, 0, 0};
+  for (int a = 0; a < n; ++a) {
+    const int64_t cid = L[a];
+    const int64_t mm = cid / 3, k = cid % 3;
+    for (int d = 0; d < 3; ++d) s[d] += corner[9 * mm + 3 * k + d];
+  }
+  for (int d = 0; d < 3; ++d) grad[3 * vtx + d] = (float)s[d];
+}
+
+__global__ void k_zero_i32(int32_t* p, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+thread_local int g_bwd_launches = 0;
+inline size_t al(size_t x) { return (x + 255) / 256 * 256; }
+template <typename T>
+T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(ws) + off); }
+inline unsigned blocks(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+int sm_count() {
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, sms);
+}
+
+// Q chunks so that the grid (item blocks x chunks) covers the GPU in whole waves.
+int q_splits(int64_t n_items, int64_t n_q) {
+  const int64_t item_blocks = std::max<int64_t>(1, (n_items + kBwdNT - 1) / kBwdNT);
+  const int64_t slots = (int64_t)sm_count() * 8;   // ~8 resident blocks of 128 threads per SM
+  const int64_t q_tiles = std::max<int64_t>(1, (n_q + kQTile - 1) / kQTile);
+  int64_t k = std::max<int64_t>(1, (4 * slots + item_blocks - 1) / item_blocks);
+  return (int)std::min<int64_t>({k, q_tiles, 256});
+}
+
+struct BwdLayout {
+  size_t mparts, items, qrec, small, partial, corner, deg, cursor, start, btot, list, total;
+  int nblk, ks;
+  int64_t per_split;
+};
+
+BwdLayout bwd_layout(int dim, int64_t n_verts, int64_t n_items, int64_t n_prep, int64_t n_q) {
+  BwdLayout y{};
+  y.ks = q_splits(n_items, n_q);
+  const int64_t q_tiles = std::max<int64_t>(1, (n_q + kQTile - 1) / kQTile);
+  y.per_split = ((q_tiles + y.ks - 1) / y.ks) * kQTile;
+  y.ks = (int)std::max<int64_t>(1, (n_q + y.per_split - 1) / y.per_split);
+  y.nblk = std::max(1, prep_blocks(n_prep));
+  const int nf = dim == 2 ? 4 : 12;
+  size_t o = al(sizeof(WsHeader));
+  y.mparts = o;  o = al(o + sizeof(double) * (size_t)y.nblk);
+  y.items = o;   o = al(o + (dim == 2 ? sizeof(Seg32) : sizeof(Face32)) * (size_t)std::max<int64_t>(n_items, 1));
+  y.qrec = o;    o = al(o + sizeof(QRec) * (size_t)std::max<int64_t>(n_q, 1));
+  y.small = o;   o = al(o + sizeof(int32_t) * (size_t)std::max<int64_t>(n_q, 1));
+  y.partial = o; o = al(o + sizeof(double) * nf * (size_t)y.ks * (size_t)std::max<int64_t>(n_items, 1));
+  if (dim == 3) {
+    y.corner = o; o = al(o + sizeof(double) * 9 * (size_t)std::max<int64_t>(n_items, 1));
+    y.deg = o;    o = al(o + sizeof(int32_t) * (size_t)std::max<int64_t>(n_verts, 1));
+    y.cursor = o; o = al(o + sizeof(int32_t) * (size_t)std::max<int64_t>(n_verts, 1));
+    y.start = o;  o = al(o + sizeof(int64_t) * (size_t)std::max<int64_t>(n_verts, 1));
+    y.btot = o;   o = al(o + sizeof(int64_t) * (size_t)blocks(n_verts, kAux));
+    y.list = o;   o = al(o + sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(n_items, 1));
+  }
+  y.total = o;
+  return y;
+}
+
+int check_opts(const pft_options* o, Thr& th) {
+  pft_options z;
+  std::memset(&z, 0, sizeof(z));
+  const pft_options& p = o ? *o : z;
+  if (p.precision != PFT_FP32_COMPENSATED) return PFT_ERR_UNSUPPORTED;   // the adjoint runs in FP32
+  if (p.q_per_thread != 0 || p.block_threads != 0 || p.k_splits != 0 || p.tile_items != 0)
+    return PFT_ERR_UNSUPPORTED;
+  float tau = p.face_series_tau == 0.f ? 1.0f : p.face_series_tau;
+  if (!(tau > 0.f && tau <= 1.f)) return PFT_ERR_INVALID_ARG;
+  const float lo = std::min(tau, 0.05f);
+  th = Thr{0.25f * tau * tau, 0.25f * lo * lo};
+  return PFT_OK;
+}
+
+#define PFT_BWD_LAUNCH()                                   \
+  do {                                                     \
+    if (cudaGetLastError() != cudaSuccess) return PFT_ERR_CUDA; \
+    ++g_bwd_launches;                                      \
+  } while (0)
+
+}  // namespace
+}  // namespace pft
+
+using namespace pft;
+
+extern "C" {
+
+size_t pft2d_backward_workspace_size(int64_t n_verts, int64_t n_loops, int64_t n_q, const pft_options* opts) {
+  Thr th;
+  if (n_verts < 0 || n_loops < 0 || n_q < 0 || check_opts(opts, th) != PFT_OK) return 0;
+  return bwd_layout(2, n_verts, n_verts, std::max<int64_t>(n_verts, n_loops + 1), n_q).total;
+}
+
+size_t pft3d_backward_workspace_size(int64_t n_verts, int64_t n_faces, int64_t n_q, const pft_options* opts) {
+  Thr th;
+  if (n_verts < 0 || n_faces < 0 || n_q < 0 || check_opts(opts, th) != PFT_OK) return 0;
+  return bwd_layout(3, n_verts, n_faces, n_faces, n_q).total;
+}
+
+int pft2d_polygons_backward(const float* verts, int64_t n_verts, const int64_t* loop_off, int64_t n_loops,
+                            const double* q, int64_t n_q, const double* grad_out, float* grad_verts, void* ws,
+                            size_t ws_bytes, const pft_options* opts, void* stream) {
+  g_bwd_launches = 0;
+  Thr th;
+  if (int e = check_opts(opts, th)) return e;
+  if (n_verts < 0 || n_loops < 0 || n_q < 0) return PFT_ERR_INVALID_ARG;
+  if (n_verts > 0 && (verts == nullptr || loop_off == nullptr || grad_verts == nullptr || n_loops == 0))
+    return PFT_ERR_INVALID_ARG;
+  if (n_q > 0 && (q == nullptr || grad_out == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (n_q > INT32_MAX) return PFT_ERR_UNSUPPORTED;
+  const BwdLayout y = bwd_layout(2, n_verts, n_verts, std::max<int64_t>(n_verts, n_loops + 1), n_q);
+  if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < y.total) return PFT_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader* h = at<WsHeader>(ws, 0);
+  if (launch_init_header(h, st) != cudaSuccess) return PFT_ERR_CUDA;
+  ++g_bwd_launches;
+  if (n_verts == 0) return PFT_OK;
+  if (n_q == 0) {
+    return cudaMemsetAsync(grad_verts, 0, sizeof(float) * 2 * (size_t)n_verts, st) == cudaSuccess ? PFT_OK
+                                                                                                  : PFT_ERR_CUDA;
+  }
+  if (launch_bbox(verts, n_verts, 2, h, st) != cudaSuccess) return PFT_ERR_CUDA;
+  if (launch_prep2d(verts, n_verts, loop_off, n_loops, h, at<void>(ws, y.items), false, at<double>(ws, y.mparts),
+                    y.nblk, st) != cudaSuccess)
+    return PFT_ERR_CUDA;
+  g_bwd_launches += 2;
+  k_bq<2><<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, h, 2.0, at<QRec>(ws, y.qrec), at<int32_t>(ws, y.small));
+  PFT_BWD_LAUNCH();
+  dim3 grid(blocks(n_verts, kBwdNT), (unsigned)y.ks);
+  k_bwd<2, 4><<<grid, kBwdNT, 0, st>>>(at<void>(ws, y.items), n_verts, at<QRec>(ws, y.qrec), n_q, y.per_split, th,
+                                       at<double>(ws, y.partial), &h->status);
+  PFT_BWD_LAUNCH();
+  k_bvert2d<<<blocks(n_verts, kAux), kAux, 0, st>>>(verts, n_verts, loop_off, n_loops, at<double>(ws, y.partial),
+                                                    y.ks, h, at<int32_t>(ws, y.small), q, grad_out, grad_verts);
+  PFT_BWD_LAUNCH();
+  return PFT_OK;
+}
+
+int pft3d_mesh_backward(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces, const double* q,
+                        int64_t n_q, const double* grad_out, float* grad_verts, void* ws, size_t ws_bytes,
+                        const pft_options* opts, void* stream) {
+  g_bwd_launches = 0;
+  Thr th;
+  if (int e = check_opts(opts, th)) return e;
+  if (n_verts < 0 || n_faces < 0 || n_q < 0) return PFT_ERR_INVALID_ARG;
+  if (n_verts > 0 && (verts == nullptr || grad_verts == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (n_faces > 0 && faces == nullptr) return PFT_ERR_INVALID_ARG;
+  if (n_q > 0 && (q == nullptr || grad_out == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (n_q > INT32_MAX || n_verts > INT32_MAX || 3 * n_faces > INT32_MAX) return PFT_ERR_UNSUPPORTED;
+  const BwdLayout y = bwd_layout(3, n_verts, n_faces, n_faces, n_q);
+  if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < y.total) return PFT_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader* h = at<WsHeader>(ws, 0);
+  if (launch_init_header(h, st) != cudaSuccess) return PFT_ERR_CUDA;
+  ++g_bwd_launches;
+  if (n_verts == 0) return PFT_OK;
+  if (n_faces == 0 || n_q == 0) {
+    return cudaMemsetAsync(grad_verts, 0, sizeof(float) * 3 * (size_t)n_verts, st) == cudaSuccess ? PFT_OK
+                                                                                                  : PFT_ERR_CUDA;
+  }
+  if (launch_bbox(verts, n_verts, 3, h, st) != cudaSuccess) return PFT_ERR_CUDA;
+  if (launch_prep3d(verts, n_verts, faces, n_faces, h, at<void>(ws, y.items), false, at<double>(ws, y.mparts),
+                    y.nblk, st) != cudaSuccess)
+    return PFT_ERR_CUDA;
+  g_bwd_launches += 2;
+  k_bq<3><<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, h, 1.0, at<QRec>(ws, y.qrec), at<int32_t>(ws, y.small));
+  PFT_BWD_LAUNCH();
+  dim3 grid(blocks(n_faces, kBwdNT), (unsigned)y.ks);
+  k_bwd<3, 12><<<grid, kBwdNT, 0, st>>>(at<void>(ws, y.items), n_faces, at<QRec>(ws, y.qrec), n_q, y.per_split, th,
+                                        at<double>(ws, y.partial), &h->status);
+  PFT_BWD_LAUNCH();
+  k_bcorner3d<<<blocks(n_faces, kAux), kAux, 0, st>>>(verts, n_verts, faces, n_faces, at<double>(ws, y.partial),
+                                                      y.ks, h, at<int32_t>(ws, y.small), q, grad_out,
+                                                      at<double>(ws, y.corner));
+  PFT_BWD_LAUNCH();
+  int32_t* deg = at<int32_t>(ws, y.deg);
+  int32_t* cursor = at<int32_t>(ws, y.cursor);
+  int64_t* start = at<int64_t>(ws, y.start);
+  int64_t* btot = at<int64_t>(ws, y.btot);
+  k_zero_i32<<<blocks(n_verts, kAux), kAux, 0, st>>>(deg, n_verts);
+  PFT_BWD_LAUNCH();
+  k_zero_i32<<<blocks(n_verts, kAux), kAux, 0, st>>>(cursor, n_verts);
+  PFT_BWD_LAUNCH();
+  k_deg<<<blocks(3 * n_faces, kAux), kAux, 0, st>>>(faces, n_faces, n_verts, deg);
+  PFT_BWD_LAUNCH();
+  const unsigned nb = blocks(n_verts, kAux);
+  k_scan_block<<<nb, kAux, 0, st>>>(deg, n_verts, start, btot);
+  PFT_BWD_LAUNCH();
+  k_scan_totals<<<1, 32, 0, st>>>(btot, nb);
+  PFT_BWD_LAUNCH();
+  k_scan_add<<<nb, kAux, 0, st>>>(start, n_verts, btot);
+  PFT_BWD_LAUNCH();
+  k_fill<<<blocks(3 * n_faces, kAux), kAux, 0, st>>>(faces, n_faces, n_verts, start, cursor, at<int32_t>(ws, y.list));
+  PFT_BWD_LAUNCH();
+  k_gather3d<<<blocks(n_verts, kAux), kAux, 0, st>>>(n_verts, start, deg, at<int32_t>(ws, y.list),
+                                                     at<double>(ws, y.corner), grad_verts);
+  PFT_BWD_LAUNCH();
+  return PFT_OK;
+}
+
+int pft_backward_last_launch_count(void) { return g_bwd_launches; }
+
+}  // extern "C"
