@@ -267,6 +267,50 @@ def bench_batched(dev, warmup, steps):
             "l2": "flushed between steps"}
 
 
+def bench_adjoint(dev, warmup, steps):
+    """Secondary path: vertex gradient of sum_Q (|F|^2 - I)^2 for 16 icospheres (81,920 triangles) on
+    a 32^3 grid; a step is one forward plus one adjoint call (the loss weights in between on torch)."""
+    import torch
+    import paper_2104_08309_gb300 as pft
+    from paper_2104_08309_gb300 import synth
+    w = synth.workload_c4()
+    vd, fd, qd = (torch.from_numpy(a).to(dev) for a in (w.verts, w.faces, w.q))
+    vt = torch.from_numpy(w.verts_target).to(dev)
+    Ft = pft.pft3d_mesh(vt, fd, qd)
+    target = (Ft[:, 0] ** 2 + Ft[:, 1] ** 2)
+
+    def step():
+        F = pft.pft3d_mesh(vd, fd, qd)
+        r = F[:, 0] ** 2 + F[:, 1] ** 2 - target
+        g = 4.0 * r[:, None] * F
+        return pft.pft3d_mesh_backward(vd, fd, qd, g)
+
+    for _ in range(max(3, warmup)):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    eb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for (a, b), (c, d) in zip(ev, eb):
+        flush.zero_()
+        a.record()
+        F = pft.pft3d_mesh(vd, fd, qd)
+        r = F[:, 0] ** 2 + F[:, 1] ** 2 - target
+        g = 4.0 * r[:, None] * F
+        c.record()
+        grad = pft.pft3d_mesh_backward(vd, fd, qd, g)
+        d.record()
+        b.record()
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    ms_b = float(np.mean([c.elapsed_time(d) for c, d in eb]))
+    pairs = float(w.faces.shape[0]) * float(w.q.shape[0])
+    return {"value": pairs / (ms_b / 1e3) / 1e9, "unit": UNIT + " (adjoint call)", "ms_adjoint": ms_b,
+            "ms_forward_plus_adjoint": ms, "pairs_per_call": pairs, "faces": int(w.faces.shape[0]),
+            "q_points": int(w.q.shape[0]), "finite": bool(torch.isfinite(grad).all().item()),
+            "launches_adjoint": int(pft.load().pft_backward_last_launch_count())}
+
+
 def traffic_from_profile():
     """DRAM bytes per main-kernel launch from the committed ncu summary, if it matches this source."""
     import hashlib
@@ -423,7 +467,9 @@ def main():
             cb["max_abs_err_vs_oracle_over_volume"] = float(np.max(np.abs(got[:, 0] + 1j * got[:, 1] - ref)) / vol)
             line["cpu_baseline"] = cb
         if not args.no_extra and world == 1:
-            line["other_paths"] = {"batched2d_4096stars_q64x64": bench_batched(dev, args.warmup, args.steps)}
+            line["other_paths"] = {"batched2d_4096stars_q64x64": bench_batched(dev, args.warmup, args.steps),
+                                   "adjoint3d_union16icospheres4_q32cubed": bench_adjoint(dev, args.warmup,
+                                                                                          args.steps)}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
