@@ -58,7 +58,9 @@ def parse():
     p.add_argument("--q-per-thread", type=int, default=2)
     p.add_argument("--block-threads", type=int, default=128)
     p.add_argument("--tau", type=float, default=0.0, help="face_series_tau (0 = library default)")
-    p.add_argument("--no-extra", action="store_true", help="skip the secondary paths (batched 2D)")
+    p.add_argument("--no-extra", action="store_true", help="skip the secondary paths (batched 2D, adjoint)")
+    p.add_argument("--only", choices=["batched", "adjoint"], default=None,
+                   help="run one secondary path alone and print its result (for profiler captures)")
     return p.parse_args()
 
 
@@ -330,6 +332,15 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        import torch
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        torch.cuda.set_device(dev)
+        from paper_2104_08309_gb300 import build as pbuild
+        pbuild.build()
+        fn = bench_batched if args.only == "batched" else bench_adjoint
+        print(json.dumps({"path": args.only, **fn(dev, args.warmup, args.steps)}))
+        return 0
     import torch
     rank, local, world = dist_env()
     torch.cuda.set_device(local)
