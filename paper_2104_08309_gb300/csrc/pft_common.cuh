@@ -8,7 +8,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/pft.h"
+#include "pft.h"
 
 namespace pft {
 
