@@ -12,6 +12,7 @@ constexpr int kStages = 4;
 // Thresholds on P (see the 3D face term below): p_hi = tau^2/4, p_lo = tau_lo^2/4.
 struct Thr {
   float hi, lo;
+  int longs;   // tau > 1: the face series needs its long form
 };
 constexpr float kTauLo = 0.05f;
 
@@ -73,9 +74,9 @@ __device__ __forceinline__ void seg_pair_f64(double qx, double qy, const Seg64& 
 // face is small (it is 0/0 for Q parallel to N); there the same face integral
 // (Eq. 13) is taken from its series, Z = i G,
 //   G = sum_k i^k h_k(a) / (k+2)!,   h_k = P h_{k-2} + T h_{k-3},
-// P = a0^2 + a0 a1 + a1^2 (= h_2), T = a0 a1 a2 (= h_3), kept through k = 8;
-// P < tau^2/4 implies max_l |Q.d_l| < tau <= 1, where the omitted terms are
-// below 1e-9 relative.
+// P = a0^2 + a0 a1 + a1^2 (= h_2), T = a0 a1 a2 (= h_3); P < tau^2/4 implies
+// max_l |Q.d_l| < tau.  For tau <= 1 the series is kept through k = 8, for
+// 1 < tau <= 3 through k = 12; the omitted terms are below 1e-9 relative.
 //
 // Branch choice, per face and warp: the series is taken for all of a thread's
 // Q points when every Q point of every lane of the warp has P < p_hi = tau^2/4;
@@ -96,6 +97,7 @@ __device__ __forceinline__ void face_common(float qx, float qy, float qz, const 
 }
 
 // Z = i G from the face-integral series.
+// Short form (P < 1/4, i.e. tau <= 1): h_k through k = 8; omitted terms < 1e-9.
 __device__ __forceinline__ void face_series(float a0, float a1, float P, float& zr, float& zi) {
   const float T = -(a0 * a1) * (a0 + a1);
   const float T2 = T * T;
@@ -105,6 +107,32 @@ __device__ __forceinline__ void face_series(float a0, float a1, float P, float& 
   gre = fmaf(P, gre, 0.5f);                                // 1/2!
   gre = fmaf(T2, fmaf(P, 8.26719577e-7f, -2.48015873e-5f), gre);   // T^2 (3P/10! - 1/8!)
   const float gim = T * fmaf(P, fmaf(P, -8.26719577e-6f, 3.96825397e-4f), -8.33333333e-3f);  // -T/5! + PT/2520 - P^2 T/120960
+  zr = -gim;
+  zi = gre;
+}
+
+// Long form (P < 9/4, i.e. tau <= 3): h_k through k = 12, with
+//   h9 = 4P^3 T + T^3, h10 = P^5 + 6P^2 T^2, h11 = 5P^4 T + 4P T^3, h12 = P^6 + 10P^3 T^2 + T^4;
+// G_re = A(P) + T^2 (B(P) + T^2/14!),  G_im = T (D(P) + T^2 E(P)); omitted terms < 1e-9 relative.
+__device__ __forceinline__ void face_series_long(float a0, float a1, float P, float& zr, float& zi) {
+  const float T = -(a0 * a1) * (a0 + a1);
+  const float T2 = T * T;
+  float A = fmaf(P, 1.147074536e-11f, -2.087675588e-9f);   // 1/14!, -1/12!
+  A = fmaf(P, A, 2.75573192e-7f);                          // 1/10!
+  A = fmaf(P, A, -2.48015873e-5f);                         // -1/8!
+  A = fmaf(P, A, 1.38888889e-3f);                          // 1/6!
+  A = fmaf(P, A, -4.16666667e-2f);                         // -1/4!
+  A = fmaf(P, A, 0.5f);                                    // 1/2!
+  float B = fmaf(P, 1.147074588e-10f, -1.252605397e-8f);   // 10/14!, -6/12!
+  B = fmaf(P, B, 8.26719577e-7f);                          // 3/10!
+  B = fmaf(P, B, -2.48015873e-5f);                         // -1/8!
+  const float gre = fmaf(T2, fmaf(T2, 1.147074536e-11f, B), A);
+  float D = fmaf(P, -8.029522047e-10f, 1.002084318e-7f);   // -5/13!, 4/11!
+  D = fmaf(P, D, -8.26719577e-6f);                         // -3/9!
+  D = fmaf(P, D, 3.96825397e-4f);                          // 2/7!
+  D = fmaf(P, D, -8.33333333e-3f);                         // -1/5!
+  const float E = fmaf(P, -6.423617749e-10f, 2.505210794e-8f);   // -4/13!, 1/11!
+  const float gim = T * fmaf(T2, E, D);
   zr = -gim;
   zi = gre;
 }
@@ -310,14 +338,17 @@ struct Pol3F32 {
       }
       if (__all_sync(0xffffffffu, all_hi)) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) face_series(a0[r], a1[r], P[r], zr[r], zi[r]);
+        for (int r = 0; r < R; ++r) {
+          if (th.longs) face_series_long(a0[r], a1[r], P[r], zr[r], zi[r]);
+          else face_series(a0[r], a1[r], P[r], zr[r], zi[r]);
+        }
       } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) face_edge(q[r][0], q[r][1], q[r][2], A, B, C, a0[r], a1[r], zr[r], zi[r]);
         if (any_lo) {
 #pragma unroll
           for (int r = 0; r < R; ++r)
-            if (P[r] < th.lo) face_series(a0[r], a1[r], P[r], zr[r], zi[r]);
+            if (P[r] < th.lo) face_series(a0[r], a1[r], P[r], zr[r], zi[r]);   // P < tau_lo^2/4 <= 1/4
         }
       }
 #pragma unroll

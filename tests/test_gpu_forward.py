@@ -84,7 +84,7 @@ def test_3d_box_normals_and_limits(torch_dev, prec):
     assert abs(got[0] - 1.25 * 0.75 * 1.875) < 1e-12
 
 
-@pytest.mark.parametrize("tau", [1e-3, 0.25, 1.0])
+@pytest.mark.parametrize("tau", [1e-3, 0.25, 1.0, 2.0, 3.0])
 def test_3d_face_branch_threshold(torch_dev, tau, rng):
     """Both per-face branches (edge sum of Eq. 14, series of Eq. 13) agree with the oracle."""
     v, f = synth.perturbed_icosphere(3, seed=5, amp=0.05)

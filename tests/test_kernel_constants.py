@@ -51,3 +51,17 @@ def test_face_series_coefficients_are_inverse_factorials():
         assert abs(got - want) <= 1e-6 * abs(want)
     # 2520 = 7!/2 (coefficient 2/7! of P T) and 120960 = 9!/3 (coefficient 3/9! of P^2 T)
     assert f(7) // 2 == 2520 and f(9) // 3 == 120960
+
+
+def test_long_face_series_coefficients():
+    """Long form: A(P) = sum (-1)^j P^j/(2j+2)!, B, D, E from h_9..h_12 (see the kernel comment)."""
+    c = _floats(_body("pft_pairs.cuh", "void face_series_long("))
+    f = math.factorial
+    expected = [1 / f(14), -1 / f(12), 1 / f(10), -1 / f(8), 1 / f(6), -1 / f(4),   # A
+                10 / f(14), -6 / f(12), 3 / f(10), -1 / f(8),                       # B (h8, h10, h12 T^2 terms)
+                1 / f(14),                                                          # T^4 / 14!
+                -5 / f(13), 4 / f(11), -3 / f(9), 2 / f(7), -1 / f(5),              # D
+                -4 / f(13), 1 / f(11)]                                              # E
+    assert len(c) == len(expected)
+    for got, want in zip(c, expected):
+        assert abs(got - want) <= 1e-6 * abs(want)
