@@ -269,6 +269,29 @@ def bench_batched(dev, warmup, steps):
             "l2": "flushed between steps"}
 
 
+def bench_fp64(pft, vd, fd, qd, out_main, lib, dev, n_sample=4096, seed=5):
+    """The plain FP64 GPU path on the same mesh, on a seeded 4,096-point Q subsample (FP64 runs at a
+    small fraction of the FP32 rate on this part), and the FP32 result's deviation from it there."""
+    import torch
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(qd.shape[0], n_sample, replace=False))
+    qs = qd[torch.from_numpy(idx).to(dev)].contiguous()
+    o64 = {"precision": "fp64"}
+    pft.pft3d_mesh(vd, fd, qs, options=o64)          # warm-up
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    r64 = pft.pft3d_mesh(vd, fd, qs, options=o64)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    pairs = float(fd.shape[0]) * float(n_sample)
+    vol = float(pft.pft3d_mesh(vd, fd, torch.zeros(1, 3, dtype=torch.float64, device=dev))[0, 0])
+    dev32 = (out_main[torch.from_numpy(idx).to(dev)] - r64).abs().max().item() / abs(vol)
+    return {"value": pairs / (ms / 1e3) / 1e9, "unit": UNIT, "ms": ms, "sample": f"{n_sample} seeded Q points",
+            "fp32_vs_fp64_max_abs_over_volume": dev32}
+
+
 def bench_adjoint(dev, warmup, steps):
     """Secondary path: vertex gradient of sum_Q (|F|^2 - I)^2 for 16 icospheres (81,920 triangles) on
     a 32^3 grid; a step is one forward plus one adjoint call (the loss weights in between on torch)."""
@@ -504,6 +527,8 @@ def main():
                     np.max(np.abs(gv[:, 0] + 1j * gv[:, 1] - ref)) / vol)
         if variant is not None:
             line["variants"] = [variant]
+        if not args.no_extra and world == 1:
+            line["fp64_gpu"] = bench_fp64(pft, vd, fd, qd, out_main, lib, dev)
         if not args.no_extra and world == 1:
             line["other_paths"] = {"batched2d_4096stars_q64x64": bench_batched(dev, args.warmup, args.steps),
                                    "adjoint3d_union16icospheres4_q32cubed": bench_adjoint(dev, args.warmup,
