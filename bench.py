@@ -35,11 +35,14 @@ UNIT = "Gpair/s"
 WORKLOAD = "icosphere8_perturbed_q128cubed"
 
 # Algorithmic per-pair instruction counts of the 3D FP32 face term (face_common,
-# face_series / face_edge, face_finish in pft_fwd.cu): FP32-pipe operations
-# (add/mul/fma/compare/select, the SFU argument scaling) and SFU operations
-# (sin, cos, reciprocal), per branch.
-OPS_SERIES = {"fp32": 38, "sfu": 2}   # face-integral series (small phase spread)
-OPS_EDGE = {"fp32": 93, "sfu": 7}     # edge sum of Eq. 14, polynomial sinc
+# face_series / face_series_long / face_edge, face_finish in pft_pairs.cuh):
+# FP32-pipe operations (add/mul/fma/compare/select, the SFU argument scaling) and
+# SFU operations (sin, cos, reciprocal), per branch.
+OPS = {
+    "short_series": {"fp32": 35, "sfu": 2},   # face-integral series through k = 7 (P < 1/4)
+    "long_series": {"fp32": 43, "sfu": 2},    # through k = 11 (P < 9/4)
+    "edge_sum": {"fp32": 92, "sfu": 7},       # edge sum of Eq. 14, polynomial sinc
+}
 FP32_LANES, SFU_LANES = 128, 16       # per SM per clock
 
 
@@ -96,12 +99,14 @@ def peaks():
         return {"sm_max_mhz": 2070.0}, "fallback"
 
 
-def branch_mix(v, f, q, tau=1.0, r=2, nt=256, tau_lo=0.05, n_warps=4096, seed=0):
-    """Fraction of (Q, face) pairs the kernel evaluates with the series branch.
+def branch_mix(v, f, q, tau=3.0, r=2, nt=128, n_warps=4096, seed=0):
+    """Fractions of (Q, face) pairs the kernel evaluates with each branch.
 
     Mirrors the kernel's rule on a seeded sample: for one face, a warp holds the
     Q indices base + k*nt + 32*w + lane (k < r, lane < 32); all of them take the
-    series if every one has P < tau^2/4, otherwise only those with P < tau_lo^2/4.
+    short series if every one has P < min(tau, 1)^2/4, the long series if every
+    one has P < tau^2/4, and otherwise the edge sum (the few pairs below
+    tau_lo^2/4 that the edge branch redoes with the series are counted as edge).
     """
     rng = np.random.default_rng(seed)
     fi = rng.integers(0, f.shape[0], n_warps)
@@ -117,13 +122,14 @@ def branch_mix(v, f, q, tau=1.0, r=2, nt=256, tau_lo=0.05, n_warps=4096, seed=0)
     a0 = np.einsum("wlj,wj->wl", qq, p[:, 0] - g)
     a1 = np.einsum("wlj,wj->wl", qq, p[:, 1] - g)
     P = a0 * a0 + a0 * a1 + a1 * a1
-    tl = min(tau, tau_lo)
-    series = np.all(P < 0.25 * tau * tau, axis=1, keepdims=True) | (P < 0.25 * tl * tl)
-    return float(np.mean(series))
+    all_hi = np.all(P < 0.25 * tau * tau, axis=1)
+    short = all_hi & np.all(P < 0.25 * min(tau, 1.0) ** 2, axis=1)
+    return {"short_series": float(np.mean(short)), "long_series": float(np.mean(all_hi & ~short)),
+            "edge_sum": float(np.mean(~all_hi))}
 
 
 def roofline(pairs, t_main_s, mix, n_sm, clk_mhz):
-    ops = {k: mix * OPS_SERIES[k] + (1 - mix) * OPS_EDGE[k] for k in ("fp32", "sfu")}
+    ops = {k: sum(mix[b] * OPS[b][k] for b in OPS) for k in ("fp32", "sfu")}
     issue = ops["fp32"] + ops["sfu"]
     cyc = max(issue / FP32_LANES, ops["sfu"] / SFU_LANES)       # SM cycles per pair at the limit
     peak_ops = n_sm * clk_mhz * 1e6 * issue / cyc                # issue-slot ops/s at the limit
@@ -336,15 +342,26 @@ def bench_adjoint(dev, warmup, steps):
             "launches_adjoint": int(pft.load().pft_backward_last_launch_count())}
 
 
-def traffic_from_profile():
-    """DRAM bytes per main-kernel launch from the committed ncu summary, if it matches this source."""
+KERNEL_SOURCES = ("pft_fwd.cu", "pft_pairs.cuh", "pft_common.cuh", "pft_kernels.cuh")
+
+
+def kernel_source_hash():
+    """First 16 hex digits of the SHA-256 of the main kernel's sources (in a fixed order)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "fwd3d_icosphere8_traffic.txt")
-    src = os.path.join(ROOT, "paper_2104_08309_gb300", "csrc", "pft_fwd.cu")
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2104_08309_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile():
+    """DRAM bytes per main-kernel launch from the committed ncu summary, if it was taken on
+    these kernel sources (None once the kernel has changed since the counters were taken)."""
+    path = os.path.join(ROOT, "profiles", "k_fwd_dram_icosphere8_q128cubed.txt")
     try:
         kv = dict(l.split(":", 1) for l in open(path).read().splitlines() if ":" in l)
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if kv.get("source_sha256_16", "").strip() == sha:
+        if kv.get("source_sha256_16", "").strip() == kernel_source_hash():
             return float(kv["dram_bytes_per_launch_full_size"])
     except (OSError, KeyError, ValueError):
         pass
@@ -459,12 +476,12 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_t = t.item()
 
-    # variant: the same workload with face_series_tau = 3 (longer face series, edge sum only
-    # where the in-face phase spread exceeds 3); one warm-up and one timed call
+    # variant: the same workload with face_series_tau = 1 (short face series only, edge sum
+    # wherever the in-face phase spread reaches 1); one warm-up and one timed call
     variant = None
     out_main = out.clone()          # result of the benchmarked configuration (checked against the oracle)
     if not args.no_extra and world == 1:
-        ov = dict(tune, face_series_tau=3.0)
+        ov = dict(tune, face_series_tau=1.0)
         step(pft.make_options(ov))
         flush.zero_()
         torch.cuda.synchronize()
@@ -476,7 +493,7 @@ def main():
         step(pft.make_options({**ov, "main_start_event": ea.cuda_event, "main_stop_event": eb.cuda_event}))
         b.record(stream)
         b.synchronize()
-        variant = {"face_series_tau": 3.0, "value": pairs / (a.elapsed_time(b) / 1e3) / 1e9, "unit": UNIT,
+        variant = {"face_series_tau": 1.0, "value": pairs / (a.elapsed_time(b) / 1e3) / 1e9, "unit": UNIT,
                    "ms_per_step": a.elapsed_time(b), "main_kernel_ms": ea.elapsed_time(eb),
                    "device_status": int(pft.pft_status(ws))}
 
@@ -484,8 +501,13 @@ def main():
         pk, pk_kind = peaks()
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         clk_max = float(pk.get("sm_max_mhz", 2070.0))
-        mix = branch_mix(v, f, q, tau=args.tau or 1.0, r=args.q_per_thread, nt=args.block_threads)
+        mix = branch_mix(v, f, q, tau=args.tau or 3.0, r=args.q_per_thread, nt=args.block_threads)
         ops, issue, achieved, peak_ops = roofline(pairs, ms_main / 1e3, mix, n_sm, clk_max)
+        if variant is not None:
+            vmix = branch_mix(v, f, q, tau=variant["face_series_tau"], r=args.q_per_thread, nt=args.block_threads)
+            _, _, v_ach, v_peak = roofline(pairs, variant["main_kernel_ms"] / 1e3, vmix, n_sm, clk_max)
+            variant["branch_fractions"] = vmix
+            variant["roofline_frac"] = v_ach / v_peak
         value = world * pairs / (ms_step / 1e3) / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -494,7 +516,7 @@ def main():
             "config": {"workload": WORKLOADS[args.workload][0], "faces": int(f.shape[0]),
                        "q_points": int(q.shape[0]), "pairs_per_step": pairs,
                        "launch": {"q_per_thread": args.q_per_thread, "block_threads": args.block_threads,
-                                  "face_series_tau": opts.face_series_tau or 1.0}, "edge_terms_per_step": 3 * pairs,
+                                  "face_series_tau": opts.face_series_tau or 3.0}, "edge_terms_per_step": 3 * pairs,
                        "l2": "flushed between steps (512 MB write outside the step events)",
                        "parallelism": f"independent replicas x{world}" if world > 1 else "single GPU",
                        "wall_s_timed_region": t_wall, "device_status": int(status)},
@@ -506,7 +528,7 @@ def main():
                          "peak_basis": f"{n_sm} SMs x 128 FP32/SFU issue slots x {clk_max:.0f} MHz "
                                        f"({pk_kind} max SM clock)",
                          "ops_per_pair": {"fp32": ops["fp32"], "sfu": ops["sfu"]},
-                         "series_branch_fraction": mix},
+                         "branch_fractions": mix},
             "clocks": clk,
             "gpu_launches": launches,
             "e2e": {"value": world * pairs / (e2e_t / 1e3) / 1e9, "unit": UNIT,

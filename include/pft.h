@@ -72,10 +72,13 @@ typedef enum {
  *                   P = (a0^2 + a1^2 + a2^2)/2 < tau^2/4 (a_k = Q.(p_k - centroid);
  *                   this implies max_l |Q.d_l| < tau) take the series of the face
  *                   integral (Eq. 13) instead of the edge sum of Eq. 14, which
- *                   cancels there.  0 = default 1.0 (the edge sum keeps every
- *                   face whose spread is at least 1, where it loses nothing to
- *                   cancellation); up to 3.0 is allowed (a longer series, same
- *                   accuracy, fewer operations per pair); must lie in (0, 3].
+ *                   cancels there.  The decision is made per face for each group
+ *                   of 32 threads' Q points; a group whose P are all below 1/4
+ *                   takes a short form of the series, one with P up to 9/4 a
+ *                   longer form.  Must lie in (0, 3]; 0 = default 3.0 (fewest
+ *                   operations per pair and the smallest error; 1.0 keeps the edge
+ *                   sum for every face whose spread is at least 1, where it
+ *                   loses nothing to cancellation).
  *  main_start_event, main_stop_event
  *                   cudaEvent_t handles or NULL.  When set, they are recorded on
  *                   `stream` immediately before and after the main (pair-sum)

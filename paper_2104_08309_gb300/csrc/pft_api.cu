@@ -35,7 +35,7 @@ int resolve(const pft_options* o, int dim, Opts& out) {
   out.k_splits = p.k_splits;
   if (p.tile_items != 0) return PFT_ERR_UNSUPPORTED;
   float tau = p.face_series_tau;
-  if (tau == 0.f) tau = 1.0f;
+  if (tau == 0.f) tau = 3.0f;
   if (!(tau > 0.f && tau <= 3.0f)) return PFT_ERR_INVALID_ARG;
   out.tau = tau;
   out.ev_start = static_cast<cudaEvent_t>(p.main_start_event);

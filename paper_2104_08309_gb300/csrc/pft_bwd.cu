@@ -112,12 +112,14 @@ __device__ __forceinline__ void sinc_d(float u, float& S, float& dS) {
   d = fmaf(v, d, 2.0f * 8.333321661e-3f);
   d = fmaf(v, d, -1.666666567e-1f);
   dS = 2.0f * u * d;
-  if (v > kPi2) {
-    float s, c;
-    sincos_turns(u * kInvTwoPi, &s, &c);
-    const float r = rcp_approx(u);
-    S = s * r;
-    dS = (c - S) * r;
+  if (__any_sync(__activemask(), v > kPi2)) {   // warp-uniform: the SFU work only where some lane needs it
+    if (v > kPi2) {
+      float s, c;
+      sincos_turns(u * kInvTwoPi, &s, &c);
+      const float r = rcp_approx(u);
+      S = s * r;
+      dS = (c - S) * r;
+    }
   }
 }
 
@@ -153,65 +155,58 @@ __device__ __forceinline__ void face_adj(const QRec& Q, const float4 A, const fl
   const float qx = Q.qx, qy = Q.qy, qz = Q.qz;
   float mu, a0, a1, s, P;
   face_common(qx, qy, qz, A, B, C, mu, a0, a1, s, P);
-  const bool series = __all_sync(0xffffffffu, P < th.hi) || (P < th.lo);
+  // the forward kernel's rule over the warp's faces: short series when all have
+  // P < 1/4 (or this one is below p_lo), long series when all are below p_hi
+  const bool all_hi = __all_sync(0xffffffffu, P < th.hi);
+  const bool shorts = (th.longs ? __all_sync(0xffffffffu, P < kPShort) : all_hi) || (P < th.lo);
+  const bool series = shorts || all_hi;
   float sm, cm;
   __sincosf(mu, &sm, &cm);
   float zr, zi;
   // forward Z, then (after the common adjoints below) its reverse pass
   float dGre_dP = 0.f, dGre_dT = 0.f, dGim_dP = 0.f, dGim_dT = 0.f, T = 0.f;
   float Xx = 0.f, Xy = 0.f, Xz = 0.f, x2 = 0.f, inv = 0.f, w[3] = {0.f, 0.f, 0.f}, S[3], dS[3], sp[3], cp[3];
-  if (series && !th.longs) {   // short series (tau <= 1), as face_series
+  if (shorts) {               // short series (P < 1/4, k <= 7), as face_series
     T = -(a0 * a1) * (a0 + a1);
-    const float T2 = T * T;
-    float gre = fmaf(P, 2.75573192e-7f, -2.48015873e-5f);
-    gre = fmaf(P, gre, 1.38888889e-3f);
+    float gre = fmaf(P, -2.48015873e-5f, 1.38888889e-3f);
     gre = fmaf(P, gre, -4.16666667e-2f);
     gre = fmaf(P, gre, 0.5f);
-    const float k2 = fmaf(P, 8.26719577e-7f, -2.48015873e-5f);
-    gre = fmaf(T2, k2, gre);
+    gre = fmaf(T * T, -2.48015873e-5f, gre);
     const float r = fmaf(P, fmaf(P, -8.26719577e-6f, 3.96825397e-4f), -8.33333333e-3f);
-    const float gim = T * r;
-    zr = -gim;
+    zr = -T * r;
     zi = gre;
-    float d = fmaf(P, 4.0f * 2.75573192e-7f, 3.0f * -2.48015873e-5f);
-    d = fmaf(P, d, 2.0f * 1.38888889e-3f);
-    dGre_dP = fmaf(P, d, -4.16666667e-2f) + T2 * 8.26719577e-7f;
-    dGre_dT = 2.0f * T * k2;
+    dGre_dP = fmaf(P, fmaf(P, 3.0f * -2.48015873e-5f, 2.0f * 1.38888889e-3f), -4.16666667e-2f);
+    dGre_dT = 2.0f * T * -2.48015873e-5f;
     dGim_dP = T * fmaf(P, 2.0f * -8.26719577e-6f, 3.96825397e-4f);
     dGim_dT = r;
-  } else if (series) {        // long series (tau <= 3), as face_series_long
+  } else if (series) {        // long series (P < 9/4, k <= 11), as face_series_long
     T = -(a0 * a1) * (a0 + a1);
     const float T2 = T * T;
-    float A = fmaf(P, 1.147074536e-11f, -2.087675588e-9f);
-    A = fmaf(P, A, 2.75573192e-7f);
+    float A = fmaf(P, -2.087675588e-9f, 2.75573192e-7f);
     A = fmaf(P, A, -2.48015873e-5f);
     A = fmaf(P, A, 1.38888889e-3f);
     A = fmaf(P, A, -4.16666667e-2f);
     A = fmaf(P, A, 0.5f);
-    float Bp = fmaf(P, 1.147074588e-10f, -1.252605397e-8f);
-    Bp = fmaf(P, Bp, 8.26719577e-7f);
+    float Bp = fmaf(P, -1.252605397e-8f, 8.26719577e-7f);
     Bp = fmaf(P, Bp, -2.48015873e-5f);
-    const float BC = fmaf(T2, 1.147074536e-11f, Bp);
     float D = fmaf(P, -8.029522047e-10f, 1.002084318e-7f);
     D = fmaf(P, D, -8.26719577e-6f);
     D = fmaf(P, D, 3.96825397e-4f);
     D = fmaf(P, D, -8.33333333e-3f);
     const float E = fmaf(P, -6.423617749e-10f, 2.505210794e-8f);
     zr = -T * fmaf(T2, E, D);
-    zi = fmaf(T2, BC, A);
+    zi = fmaf(T2, Bp, A);
     // derivatives of A, B, D, E in P
-    float dA = fmaf(P, 6.0f * 1.147074536e-11f, 5.0f * -2.087675588e-9f);
-    dA = fmaf(P, dA, 4.0f * 2.75573192e-7f);
+    float dA = fmaf(P, 5.0f * -2.087675588e-9f, 4.0f * 2.75573192e-7f);
     dA = fmaf(P, dA, 3.0f * -2.48015873e-5f);
     dA = fmaf(P, dA, 2.0f * 1.38888889e-3f);
     dA = fmaf(P, dA, -4.16666667e-2f);
-    float dB = fmaf(P, 3.0f * 1.147074588e-10f, 2.0f * -1.252605397e-8f);
-    dB = fmaf(P, dB, 8.26719577e-7f);
+    const float dB = fmaf(P, 2.0f * -1.252605397e-8f, 8.26719577e-7f);
     float dD = fmaf(P, 4.0f * -8.029522047e-10f, 3.0f * 1.002084318e-7f);
     dD = fmaf(P, dD, 2.0f * -8.26719577e-6f);
     dD = fmaf(P, dD, 3.96825397e-4f);
     dGre_dP = fmaf(T2, dB, dA);
-    dGre_dT = 2.0f * T * fmaf(2.0f * T2, 1.147074536e-11f, Bp);
+    dGre_dT = 2.0f * T * Bp;
     dGim_dP = T * fmaf(T2, -6.423617749e-10f, dD);
     dGim_dT = fmaf(3.0f * T2, E, D);
   } else {
@@ -666,7 +661,7 @@ int check_opts(const pft_options* o, Thr& th) {
   if (p.precision != PFT_FP32_COMPENSATED) return PFT_ERR_UNSUPPORTED;   // the adjoint runs in FP32
   if (p.q_per_thread != 0 || p.block_threads != 0 || p.k_splits != 0 || p.tile_items != 0)
     return PFT_ERR_UNSUPPORTED;
-  float tau = p.face_series_tau == 0.f ? 1.0f : p.face_series_tau;
+  float tau = p.face_series_tau == 0.f ? 3.0f : p.face_series_tau;
   if (!(tau > 0.f && tau <= 3.f)) return PFT_ERR_INVALID_ARG;
   const float lo = std::min(tau, 0.05f);
   th = Thr{0.25f * tau * tau, 0.25f * lo * lo, tau > 1.f ? 1 : 0};

@@ -86,18 +86,14 @@ __device__ __forceinline__ float sinc_poly(float u2) {
 
 constexpr float kPi2 = 9.86960440108935861883f;   // pi^2
 
-// sinc(u) for any u: the polynomial on |u| <= pi, otherwise sin of the
-// turn-reduced argument on the SFU times 1/u (relative error ~1e-7 there).
-__device__ __forceinline__ float sinc_f32(float u) {
-  const float u2 = u * u;
-  float r = sinc_poly(u2);
-  if (u2 > kPi2) {
-    float s, c;
-    sincos_turns(u * kInvTwoPi, &s, &c);
-    r = s * rcp_approx(u);
-  }
-  return r;
+// sin(u)/u for |u| > pi: sin of the turn-reduced argument on the SFU times 1/u
+// (relative error ~1e-7).
+__device__ __forceinline__ float sinc_large(float u) {
+  float s, c;
+  sincos_turns(u * kInvTwoPi, &s, &c);
+  return s * rcp_approx(u);
 }
+
 
 // Error-free sum a + b = s + e (Knuth TwoSum).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {

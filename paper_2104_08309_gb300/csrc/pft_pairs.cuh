@@ -12,9 +12,10 @@ constexpr int kStages = 4;
 // Thresholds on P (see the 3D face term below): p_hi = tau^2/4, p_lo = tau_lo^2/4.
 struct Thr {
   float hi, lo;
-  int longs;   // tau > 1: the face series needs its long form
+  int longs;   // tau > 1: warps whose faces are not all below kPShort take the long series
 };
 constexpr float kTauLo = 0.05f;
+constexpr float kPShort = 0.25f;   // P below which the short series suffices (tau = 1)
 
 // Resident blocks per SM the register budget is sized for: 16-24 warps of
 // 256 threads, fewer registers per thread for fewer Q points per thread.
@@ -29,17 +30,8 @@ constexpr int kMinBlocks = sizeof(typename Pol::QT) == 8 ? 1 : (NT == 256 ? 1 : 
 // 2D, Eq. 6 (Sec. 2): the segment p0 -> p1 contributes
 //   -i (Qx Dy - Qy Dx) sinc(Q.D/2) exp(iQ.m)           (times 1/|Q|^2, applied later)
 // Records hold m and D/2, so w below is half the cross product; the factor 2
-// and 1/|Q|^2 are applied in FP64 by the finalize kernel.
-__device__ __forceinline__ void seg_pair_f32(float qx, float qy, const float4 s, float& re, float& im) {
-  const float ph = fmaf(qx, s.x, qy * s.y);    // Q.m
-  const float u = fmaf(qx, s.z, qy * s.w);     // Q.D / 2
-  const float w = fmaf(qx, s.w, -qy * s.z);    // (Qx Dy - Qy Dx) / 2
-  float sn, cs;
-  __sincosf(ph, &sn, &cs);
-  const float ws = w * sinc_f32(u);
-  re = ws * sn;    // -i * ws * (cos + i sin) = ws sin - i ws cos
-  im = -ws * cs;
-}
+// and 1/|Q|^2 are applied in FP64 by the finalize kernel.  The term itself is
+// evaluated in Pol2F32::tile (the sinc of |Q.D/2| > pi is a warp-uniform branch).
 
 __device__ __forceinline__ double sinc_f64(double u) {
   const double u2 = u * u;
@@ -75,16 +67,17 @@ __device__ __forceinline__ void seg_pair_f64(double qx, double qy, const Seg64& 
 // (Eq. 13) is taken from its series, Z = i G,
 //   G = sum_k i^k h_k(a) / (k+2)!,   h_k = P h_{k-2} + T h_{k-3},
 // P = a0^2 + a0 a1 + a1^2 (= h_2), T = a0 a1 a2 (= h_3); P < tau^2/4 implies
-// max_l |Q.d_l| < tau.  For tau <= 1 the series is kept through k = 8, for
-// 1 < tau <= 3 through k = 12; the omitted terms are below 1e-9 relative.
+// max_l |Q.d_l| < tau.  For P < 1/4 the series is kept through k = 7, for
+// P < 9/4 through k = 11; the omitted terms are below 4e-9 (|G| <= 1/2).
 //
 // Branch choice, per face and warp: the series is taken for all of a thread's
-// Q points when every Q point of every lane of the warp has P < p_hi = tau^2/4;
+// Q points when every Q point of every lane of the warp has P < p_hi = tau^2/4
+// -- its short form when every one also has P < 1/4, else its long form;
 // otherwise the edge sum, except for Q points with P < p_lo = tau_lo^2/4
 // (tau_lo = min(tau, 0.05): below it the edge sum would lose more than ~4 bits
-// to cancellation), which are redone with the series.  Both evaluate the same
-// face integral, so the choice only moves rounding; the R Q points of a thread
-// share the branch, so their arithmetic interleaves.
+// to cancellation), which are redone with the short series.  All three evaluate
+// the same face integral, so the choice only moves rounding; the R Q points of
+// a thread share the branch, so their arithmetic interleaves.
 
 // Projections shared by both branches.  A = g.xyz, q0.x  B = q0.yz, q1.xy  C = q1.z, N.xyz
 __device__ __forceinline__ void face_common(float qx, float qy, float qz, const float4 A, const float4 B,
@@ -97,36 +90,35 @@ __device__ __forceinline__ void face_common(float qx, float qy, float qz, const 
 }
 
 // Z = i G from the face-integral series.
-// Short form (P < 1/4, i.e. tau <= 1): h_k through k = 8; omitted terms < 1e-9.
+// Short form (P < 1/4, i.e. tau <= 1): h_k through k = 7,
+//   G_re = 1/2! - P/4! + P^2/6! - (P^3 + T^2)/8!,  G_im = T (-1/5! + 2P/7! - 3P^2/9!);
+// the omitted terms (k >= 8) are below 2e-9 (|G| <= 1/2).
 __device__ __forceinline__ void face_series(float a0, float a1, float P, float& zr, float& zi) {
   const float T = -(a0 * a1) * (a0 + a1);
-  const float T2 = T * T;
-  float gre = fmaf(P, 2.75573192e-7f, -2.48015873e-5f);   // 1/10!, -1/8!
-  gre = fmaf(P, gre, 1.38888889e-3f);                      // 1/6!
+  float gre = fmaf(P, -2.48015873e-5f, 1.38888889e-3f);   // -1/8!, 1/6!
   gre = fmaf(P, gre, -4.16666667e-2f);                     // -1/4!
   gre = fmaf(P, gre, 0.5f);                                // 1/2!
-  gre = fmaf(T2, fmaf(P, 8.26719577e-7f, -2.48015873e-5f), gre);   // T^2 (3P/10! - 1/8!)
-  const float gim = T * fmaf(P, fmaf(P, -8.26719577e-6f, 3.96825397e-4f), -8.33333333e-3f);  // -T/5! + PT/2520 - P^2 T/120960
+  gre = fmaf(T * T, -2.48015873e-5f, gre);                 // -T^2/8!
+  const float gim = T * fmaf(P, fmaf(P, -8.26719577e-6f, 3.96825397e-4f), -8.33333333e-3f);  // -3/9!, 2/7!, -1/5!
   zr = -gim;
   zi = gre;
 }
 
-// Long form (P < 9/4, i.e. tau <= 3): h_k through k = 12, with
-//   h9 = 4P^3 T + T^3, h10 = P^5 + 6P^2 T^2, h11 = 5P^4 T + 4P T^3, h12 = P^6 + 10P^3 T^2 + T^4;
-// G_re = A(P) + T^2 (B(P) + T^2/14!),  G_im = T (D(P) + T^2 E(P)); omitted terms < 1e-9 relative.
+// Long form (P < 9/4, i.e. tau <= 3): h_k through k = 11, with
+//   h8 = P^4 + 3P T^2, h9 = 4P^3 T + T^3, h10 = P^5 + 6P^2 T^2, h11 = 5P^4 T + 4P T^3;
+// G_re = A(P) + T^2 B(P),  G_im = T (D(P) + T^2 E(P)); the omitted terms (k >= 12)
+// are below 4e-9 (|G| <= 1/2).
 __device__ __forceinline__ void face_series_long(float a0, float a1, float P, float& zr, float& zi) {
   const float T = -(a0 * a1) * (a0 + a1);
   const float T2 = T * T;
-  float A = fmaf(P, 1.147074536e-11f, -2.087675588e-9f);   // 1/14!, -1/12!
-  A = fmaf(P, A, 2.75573192e-7f);                          // 1/10!
+  float A = fmaf(P, -2.087675588e-9f, 2.75573192e-7f);    // -1/12!, 1/10!
   A = fmaf(P, A, -2.48015873e-5f);                         // -1/8!
   A = fmaf(P, A, 1.38888889e-3f);                          // 1/6!
   A = fmaf(P, A, -4.16666667e-2f);                         // -1/4!
   A = fmaf(P, A, 0.5f);                                    // 1/2!
-  float B = fmaf(P, 1.147074588e-10f, -1.252605397e-8f);   // 10/14!, -6/12!
-  B = fmaf(P, B, 8.26719577e-7f);                          // 3/10!
+  float B = fmaf(P, -1.252605397e-8f, 8.26719577e-7f);    // -6/12!, 3/10!
   B = fmaf(P, B, -2.48015873e-5f);                         // -1/8!
-  const float gre = fmaf(T2, fmaf(T2, 1.147074536e-11f, B), A);
+  const float gre = fmaf(T2, B, A);
   float D = fmaf(P, -8.029522047e-10f, 1.002084318e-7f);   // -5/13!, 4/11!
   D = fmaf(P, D, -8.26719577e-6f);                         // -3/9!
   D = fmaf(P, D, 3.96825397e-4f);                          // 2/7!
@@ -162,9 +154,11 @@ __device__ __forceinline__ void face_edge(float qx, float qy, float qz, const fl
     u2[l] = u[l] * u[l];
     S[l] = sinc_poly(u2[l]);
   }
-  if (fmaxf(u2[0], fmaxf(u2[1], u2[2])) > kPi2) {   // rare: an edge with |Q.d_l| > 2 pi
+  // rare: an edge with |Q.d_l| > 2 pi somewhere in the warp (face_edge runs warp-converged)
+  if (__any_sync(0xffffffffu, fmaxf(u2[0], fmaxf(u2[1], u2[2])) > kPi2)) {
 #pragma unroll
-    for (int l = 0; l < 3; ++l) S[l] = sinc_f32(u[l]);
+    for (int l = 0; l < 3; ++l)
+      if (u2[l] > kPi2) S[l] = sinc_large(u[l]);
   }
   float sr = 0.f, si = 0.f;
 #pragma unroll
@@ -178,12 +172,13 @@ __device__ __forceinline__ void face_edge(float qx, float qy, float qz, const fl
   zi = si * inv;
 }
 
-// |Q|^2 I_m = -s exp(i mu) Z.
-__device__ __forceinline__ void face_finish(float mu, float s, float zr, float zi, float& re, float& im) {
+// |Q|^2 I_m = -s exp(i mu) Z, added into the tile sums (tre, tim).
+__device__ __forceinline__ void face_finish(float mu, float s, float zr, float zi, float& tre, float& tim) {
   float sm, cm;
   __sincosf(mu, &sm, &cm);
-  re = -s * fmaf(cm, zr, -sm * zi);
-  im = -s * fmaf(cm, zi, sm * zr);
+  const float c = -s * cm, d = -s * sm;   // -s exp(i mu) = c + i d
+  tre = fmaf(c, zr, fmaf(-d, zi, tre));
+  tim = fmaf(c, zi, fmaf(d, zr, tim));
 }
 
 // Same face term in FP64 (comparison path): library sincos, series through k = 16.
@@ -279,13 +274,32 @@ struct Pol2F32 {
     for (int r = 0; r < R; ++r) { tre[r] = 0.f; tim[r] = 0.f; }
 #pragma unroll 2
     for (int i = 0; i < cnt; ++i) {
-      const float4 s = reinterpret_cast<const float4*>(t)[i];
+      const float4 s = reinterpret_cast<const float4*>(t)[i];   // m.x, m.y, D.x/2, D.y/2
+      float ph[R], u[R], u2[R], w[R], S[R];
+      bool big = false;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        float re, im;
-        seg_pair_f32(q[r][0], q[r][1], s, re, im);
-        tre[r] += re;
-        tim[r] += im;
+        const float qx = q[r][0], qy = q[r][1];
+        ph[r] = fmaf(qx, s.x, qy * s.y);      // Q.m
+        u[r] = fmaf(qx, s.z, qy * s.w);       // Q.D / 2
+        w[r] = fmaf(qx, s.w, -qy * s.z);      // (Qx Dy - Qy Dx) / 2
+        u2[r] = u[r] * u[r];
+        S[r] = sinc_poly(u2[r]);
+        big = big || (u2[r] > kPi2);
+      }
+      // segments long against 1/|Q|: the SFU sinc, only in warps where some lane needs it
+      if (__any_sync(0xffffffffu, big)) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (u2[r] > kPi2) S[r] = sinc_large(u[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float sn, cs;
+        __sincosf(ph[r], &sn, &cs);
+        const float ws = w[r] * S[r];
+        tre[r] = fmaf(ws, sn, tre[r]);     // -i ws (cos + i sin) = ws sin - i ws cos
+        tim[r] = fmaf(-ws, cs, tim[r]);
       }
     }
 #pragma unroll
@@ -329,18 +343,22 @@ struct Pol3F32 {
       const float4* p = reinterpret_cast<const float4*>(t + i);
       const float4 A = p[0], B = p[1], C = p[2];
       float mu[R], a0[R], a1[R], s[R], P[R], zr[R], zi[R];
-      bool all_hi = true, any_lo = false;
+      bool all_hi = true, all_short = true, any_lo = false;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         face_common(q[r][0], q[r][1], q[r][2], A, B, C, mu[r], a0[r], a1[r], s[r], P[r]);
         all_hi = all_hi && (P[r] < th.hi);
+        all_short = all_short && (P[r] < kPShort);
         any_lo = any_lo || (P[r] < th.lo);
       }
       if (__all_sync(0xffffffffu, all_hi)) {
+        // th.longs is uniform over the grid, so the second vote is warp-uniform too
+        if (!th.longs || __all_sync(0xffffffffu, all_short)) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          if (th.longs) face_series_long(a0[r], a1[r], P[r], zr[r], zi[r]);
-          else face_series(a0[r], a1[r], P[r], zr[r], zi[r]);
+          for (int r = 0; r < R; ++r) face_series(a0[r], a1[r], P[r], zr[r], zi[r]);
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) face_series_long(a0[r], a1[r], P[r], zr[r], zi[r]);
         }
       } else {
 #pragma unroll
@@ -352,12 +370,7 @@ struct Pol3F32 {
         }
       }
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        float re, im;
-        face_finish(mu[r], s[r], zr[r], zi[r], re, im);
-        tre[r] += re;
-        tim[r] += im;
-      }
+      for (int r = 0; r < R; ++r) face_finish(mu[r], s[r], zr[r], zi[r], tre[r], tim[r]);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) { acc.re[r].add(tre[r]); acc.im[r].add(tim[r]); }

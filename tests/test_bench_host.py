@@ -1,0 +1,56 @@
+"""Host-side pieces of bench.py: the branch-mix mirror of the kernel's rule and
+the roofline arithmetic (no GPU needed)."""
+import numpy as np
+import pytest
+
+import bench
+from paper_2104_08309_gb300 import synth
+
+
+@pytest.fixture(scope="module")
+def mesh():
+    v, f = synth.perturbed_icosphere(4, seed=2, amp=0.05)
+    return v, f
+
+
+def test_branch_fractions_partition_the_pairs(mesh):
+    v, f = mesh
+    q = synth.q_grid_3d(32, 60.0)
+    for tau in (0.5, 1.0, 2.0, 3.0):
+        m = bench.branch_mix(v, f, q, tau=tau, n_warps=512)
+        assert set(m) == set(bench.OPS)
+        assert abs(sum(m.values()) - 1.0) < 1e-12
+        if tau <= 1.0:
+            assert m["long_series"] == 0.0
+    lo = bench.branch_mix(v, f, q, tau=1.0, n_warps=512)
+    hi = bench.branch_mix(v, f, q, tau=3.0, n_warps=512)
+    # the same seeded sample: raising tau only moves warps from the edge sum into the series,
+    # and warps with every P < 1/4 keep the short form
+    assert hi["edge_sum"] <= lo["edge_sum"]
+    assert hi["short_series"] == lo["short_series"]
+
+
+def test_branch_rule_on_hand_made_phases():
+    """One face, Q points along its normal (all phases 0 -> short series) and in its plane
+    at |Q| where P lies between 1/4 and 9/4 (long series at tau = 3, edge sum at tau = 1)."""
+    v = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    f = np.array([[0, 1, 2]], np.int32)
+    along = np.tile([[0.0, 0.0, 5.0]], (256, 1))
+    m = bench.branch_mix(v, f, along, tau=3.0, r=2, nt=128, n_warps=16)
+    assert m["short_series"] == 1.0
+    # a0 = Q.(p0 - g) with g = (1/3, 1/3, 0): Q = (k, 0, 0) gives a = (-k/3, 2k/3, -k/3), P = k^2/3
+    inplane = np.tile([[1.5, 0.0, 0.0]], (256, 1))             # P = 0.75
+    assert bench.branch_mix(v, f, inplane, tau=3.0, r=2, nt=128, n_warps=16)["long_series"] == 1.0
+    assert bench.branch_mix(v, f, inplane, tau=1.0, r=2, nt=128, n_warps=16)["edge_sum"] == 1.0
+
+
+def test_roofline_arithmetic():
+    mix = {"short_series": 0.25, "long_series": 0.5, "edge_sum": 0.25}
+    ops, issue, achieved, peak = bench.roofline(1e12, 1.0, mix, 152, 2070.0)
+    want = {k: 0.25 * bench.OPS["short_series"][k] + 0.5 * bench.OPS["long_series"][k]
+            + 0.25 * bench.OPS["edge_sum"][k] for k in ("fp32", "sfu")}
+    assert ops == pytest.approx(want)
+    assert issue == pytest.approx(want["fp32"] + want["sfu"])
+    assert achieved == pytest.approx(issue * 1e12)
+    # issue-bound for this mix: 152 SMs x 128 lanes x 2070 MHz
+    assert peak == pytest.approx(152 * 128 * 2070e6)

@@ -95,6 +95,20 @@ def test_3d_face_branch_threshold(torch_dev, tau, rng):
         assert rel_err(got, ref, ref[0]) < TOL[prec], (prec, tau)
 
 
+def test_3d_short_series_taken_whatever_tau(torch_dev, rng):
+    """Small faces at small |Q| (every P < 1/4): the short series serves every warp for any
+    tau >= 1, so tau = 1, 2 and 3 give bitwise the same FP32 result; the default is tau = 3."""
+    v, f = synth.icosphere(5)                        # edges ~0.06: P < 1/4 for |Q| < ~8
+    q = rng.uniform(-4.0, 4.0, (3000, 3))
+    q[0] = 0.0
+    a = run3d(torch_dev, v, f, q, face_series_tau=1.0, k_splits=2)
+    for tau in (2.0, 3.0, 0.0):
+        b = run3d(torch_dev, v, f, q, face_series_tau=tau, k_splits=2)
+        assert np.array_equal(a, b), tau
+    ref = oracle.ft3d(v, f, q[:200])
+    assert rel_err(a[:200], ref, ref[0]) < TOL["fp32"]
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_2d_loops_and_limits(torch_dev, prec, rng):
     outer = synth.star_polygon(300, seed=2)

@@ -43,8 +43,8 @@ def test_face_series_coefficients_are_inverse_factorials():
     """G = sum_k i^k h_k/(k+2)!: the constants are +-1/(k+2)! and their combinations."""
     c = _floats(_body("pft_pairs.cuh", "void face_series("))
     f = math.factorial
-    expected = [1 / f(10), -1 / f(8), 1 / f(6), -1 / f(4),           # Horner in P for the real part
-                3 / f(10), -1 / f(8),                                  # T^2 terms
+    expected = [-1 / f(8), 1 / f(6), -1 / f(4),                      # Horner in P for the real part (+ 1/2)
+                -1 / f(8),                                             # T^2 term of h6
                 -1 / 120960, 1 / 2520, -1 / f(5)]                      # imaginary part: -T/5! + PT/2520 - P^2T/120960
     assert len(c) == len(expected)
     for got, want in zip(c, expected):
@@ -54,14 +54,71 @@ def test_face_series_coefficients_are_inverse_factorials():
 
 
 def test_long_face_series_coefficients():
-    """Long form: A(P) = sum (-1)^j P^j/(2j+2)!, B, D, E from h_9..h_12 (see the kernel comment)."""
+    """Long form: A(P) = sum (-1)^j P^j/(2j+2)!, B, D, E from h_8..h_11 (see the kernel comment)."""
     c = _floats(_body("pft_pairs.cuh", "void face_series_long("))
     f = math.factorial
-    expected = [1 / f(14), -1 / f(12), 1 / f(10), -1 / f(8), 1 / f(6), -1 / f(4),   # A
-                10 / f(14), -6 / f(12), 3 / f(10), -1 / f(8),                       # B (h8, h10, h12 T^2 terms)
-                1 / f(14),                                                          # T^4 / 14!
-                -5 / f(13), 4 / f(11), -3 / f(9), 2 / f(7), -1 / f(5),              # D
-                -4 / f(13), 1 / f(11)]                                              # E
+    expected = [-1 / f(12), 1 / f(10), -1 / f(8), 1 / f(6), -1 / f(4),    # A
+                -6 / f(12), 3 / f(10), -1 / f(8),                          # B (T^2 terms of h6, h8, h10)
+                -5 / f(13), 4 / f(11), -3 / f(9), 2 / f(7), -1 / f(5),     # D
+                -4 / f(13), 1 / f(11)]                                     # E
     assert len(c) == len(expected)
     for got, want in zip(c, expected):
         assert abs(got - want) <= 1e-6 * abs(want)
+
+
+def _exact_G(a0, a1, K=40):
+    """G = sum_k i^k h_k/(k+2)! with h_k = P h_{k-2} + T h_{k-3}, summed far past convergence."""
+    P = a0 * a0 + a0 * a1 + a1 * a1
+    T = -(a0 * a1) * (a0 + a1)
+    h = [np.ones_like(P), np.zeros_like(P), P]
+    for k in range(3, K + 1):
+        h.append(P * h[k - 2] + T * h[k - 3])
+    g = np.zeros_like(P, dtype=complex)
+    for k in range(K + 1):
+        g += (1j ** k) * h[k] / math.factorial(k + 2)
+    return P, T, g
+
+
+def _horner(coef, x):
+    acc = np.zeros_like(x)
+    for c in coef:
+        acc = acc * x + c
+    return acc
+
+
+def _phases(pmax, n=200000, seed=3):
+    # a0 = x - y/sqrt3, a1 = 2y/sqrt3 maps the disc x^2 + y^2 < pmax onto P < pmax
+    rng = np.random.default_rng(seed)
+    ang = rng.uniform(0, 2 * np.pi, n)
+    rad = np.sqrt(pmax) * np.sqrt(rng.uniform(0, 1, n))
+    x, y = rad * np.cos(ang), rad * np.sin(ang)
+    return x - y / np.sqrt(3), 2 * y / np.sqrt(3)
+
+
+def test_face_series_truncation_bounds():
+    """The kernel's short form (k <= 7) on P < 1/4 and long form (k <= 11) on P < 9/4, with
+    the constants read from the source, against the converged series: within 2e-9 and 4e-9."""
+    cs = _floats(_body("pft_pairs.cuh", "void face_series("))
+    P, T, g = _exact_G(*_phases(0.25))
+    gre = _horner(cs[0:3] + [0.5], P) + T * T * cs[3]
+    gim = T * _horner(cs[4:7], P)
+    assert np.max(np.abs(gre + 1j * gim - g)) < 2e-9
+    cl = _floats(_body("pft_pairs.cuh", "void face_series_long("))
+    P, T, g = _exact_G(*_phases(2.25))
+    A = _horner(cl[0:5] + [0.5], P)
+    B = _horner(cl[5:8], P)
+    D = _horner(cl[8:13], P)
+    E = _horner(cl[13:15], P)
+    gre = A + T * T * B
+    gim = T * (D + T * T * E)
+    assert np.max(np.abs(gre + 1j * gim - g)) < 4e-9
+    # the converged series itself is the second divided difference of e^z at the points i a_k,
+    # G = sum_k e^{i a_k} / prod_{j != k} (i a_k - i a_j): checked where the corners are well separated
+    a0, a1 = _phases(2.25, n=2000, seed=4)
+    a2 = -(a0 + a1)
+    ok = np.minimum.reduce([abs(a0 - a1), abs(a1 - a2), abs(a2 - a0)]) > 0.3
+    a0, a1, a2 = a0[ok], a1[ok], a2[ok]
+    dd = sum(np.exp(1j * x) / ((1j * x - 1j * y) * (1j * x - 1j * z)) for x, y, z in
+             ((a0, a1, a2), (a1, a2, a0), (a2, a0, a1)))
+    _, _, g = _exact_G(a0, a1)
+    assert np.max(np.abs(g - dd)) < 1e-12
