@@ -286,7 +286,7 @@ __device__ __forceinline__ void finish_out(double qx, double qy, double re, doub
     out[2 * row + 1] = 0.0;
     return;
   }
-  if (sqrt(q2) * (double)pi.rmax < kTauSmallQ) {
+  if (q2 * ((double)pi.rmax * (double)pi.rmax) < kTauSmallQ * kTauSmallQ) {   // |Q| r_max < tau_small
     small[atomicAdd(&h->small_q_count, 1u)] = (uint32_t)row;
     return;
   }

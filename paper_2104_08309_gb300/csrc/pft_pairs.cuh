@@ -272,7 +272,7 @@ struct Pol2F32 {
     float tre[R], tim[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { tre[r] = 0.f; tim[r] = 0.f; }
-#pragma unroll 2
+#pragma unroll 1
     for (int i = 0; i < cnt; ++i) {
       const float4 s = reinterpret_cast<const float4*>(t)[i];   // m.x, m.y, D.x/2, D.y/2
       float ph[R], u[R], u2[R], w[R], S[R];
