@@ -43,6 +43,13 @@ OPS = {
     "long_series": {"fp32": 43, "sfu": 2},    # through k = 11 (P < 9/4)
     "edge_sum": {"fp32": 92, "sfu": 7},       # edge sum of Eq. 14, polynomial sinc
 }
+# 2D segment term (Pol2F32::tile): projections 6, u^2 1, Chebyshev sinc 6, range test 1, the
+# SFU argument scaling 1, w*S 1, accumulation 2; beyond |u| > pi the SFU sinc adds the turn
+# reduction and 1/u (6 FP32-pipe + 2 SFU).
+OPS2D = {
+    "poly_sinc": {"fp32": 18, "sfu": 2},
+    "sfu_sinc": {"fp32": 24, "sfu": 4},
+}
 FP32_LANES, SFU_LANES = 128, 16       # per SM per clock
 
 
@@ -126,6 +133,31 @@ def branch_mix(v, f, q, tau=3.0, r=2, nt=128, n_warps=4096, seed=0):
     short = all_hi & np.all(P < 0.25 * min(tau, 1.0) ** 2, axis=1)
     return {"short_series": float(np.mean(short)), "long_series": float(np.mean(all_hi & ~short)),
             "edge_sum": float(np.mean(~all_hi))}
+
+
+def sfu_sinc_fraction(verts, poly_off, q, n=1 << 16, seed=0):
+    """Fraction of (segment, Q) pairs of a batched 2D problem with |Q.D/2| > pi (the SFU sinc),
+    on a seeded uniform sample of the pairs (every polygon uses the same Q set)."""
+    rng = np.random.default_rng(seed)
+    seg = rng.integers(0, verts.shape[0], n)
+    poly = np.searchsorted(poly_off, seg, side="right") - 1
+    nxt = np.where(seg + 1 == poly_off[poly + 1], poly_off[poly], seg + 1)
+    d = verts[nxt].astype(np.float64) - verts[seg]
+    qq = q[rng.integers(0, q.shape[0], n)]
+    u = 0.5 * np.abs(np.einsum("ij,ij->i", qq, d))
+    return float(np.mean(u > np.pi))
+
+
+def roofline2d(pairs, t_s, f_sfu, n_sm, clk_mhz):
+    """Issue-slot / SFU bound of the 2D segment term for a given SFU-sinc fraction."""
+    mix = {"poly_sinc": 1.0 - f_sfu, "sfu_sinc": f_sfu}
+    ops = {k: sum(mix[b] * OPS2D[b][k] for b in OPS2D) for k in ("fp32", "sfu")}
+    issue = ops["fp32"] + ops["sfu"]
+    cyc = max(issue / FP32_LANES, ops["sfu"] / SFU_LANES)
+    peak_pairs = n_sm * clk_mhz * 1e6 / cyc
+    return {"bound": "alu" if issue / FP32_LANES >= ops["sfu"] / SFU_LANES else "sfu",
+            "ops_per_pair": ops, "sfu_sinc_fraction": f_sfu, "peak_gpair_s": peak_pairs / 1e9,
+            "frac": pairs / t_s / peak_pairs}
 
 
 def roofline(pairs, t_main_s, mix, n_sm, clk_mhz):
@@ -267,7 +299,13 @@ def bench_batched(dev, warmup, steps):
     ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     pairs = float(w.verts.shape[0]) * float(w.q.shape[0])
     status = pft.pft_status(prep.ws)
+    pk, pk_kind = peaks()
+    rl = roofline2d(pairs, ms / 1e3, sfu_sinc_fraction(w.verts, w.poly_off, w.q),
+                    torch.cuda.get_device_properties(dev).multi_processor_count, float(pk.get("sm_max_mhz", 2070.0)))
+    rl["note"] = ("whole 4-launch call timed; the FP64 finish of the 16.8M outputs (2/|Q|^2, e^{iQ.c}) "
+                  "is outside the per-pair count")
     return {"value": pairs / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "pairs_per_step": pairs,
+            "roofline": rl,
             "polygons": int(w.poly_off.size - 1), "segments": int(w.verts.shape[0]), "q_points": int(w.q.shape[0]),
             "launches_per_step": int(launches), "cuda_graph": True, "device_status": int(status),
             "launch": {"q_per_thread": tuned["q_per_thread"], "block_threads": tuned["block_threads"],

@@ -54,3 +54,25 @@ def test_roofline_arithmetic():
     assert achieved == pytest.approx(issue * 1e12)
     # issue-bound for this mix: 152 SMs x 128 lanes x 2070 MHz
     assert peak == pytest.approx(152 * 128 * 2070e6)
+
+
+def test_sfu_sinc_fraction_on_a_square():
+    """Unit square (sides along x and y), Q = (1, 0) and (10, 0): only the two x-directed sides at
+    |Q| = 10 have |Q.D/2| = 5 > pi, i.e. a quarter of the (segment, Q) pairs."""
+    v = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], np.float32)
+    off = np.array([0, 4])
+    q = np.array([[1.0, 0.0], [10.0, 0.0]])
+    assert bench.sfu_sinc_fraction(v, off, q) == pytest.approx(0.25, abs=0.01)
+    # two polygons: the second (a tiny triangle) never needs the SFU sinc
+    v2 = np.concatenate([v, 0.01 * np.array([[0, 0], [1, 0], [0, 1]], np.float32)])
+    off2 = np.array([0, 4, 7])
+    assert bench.sfu_sinc_fraction(v2, off2, q) == pytest.approx(0.25 * 4 / 7, abs=0.01)
+
+
+def test_roofline2d_bounds():
+    r0 = bench.roofline2d(1e12, 1.0, 0.0, 152, 2070.0)
+    assert r0["bound"] == "alu"
+    assert r0["peak_gpair_s"] == pytest.approx(152 * 2070e6 * 128 / 20 / 1e9)
+    r1 = bench.roofline2d(1e12, 1.0, 1.0, 152, 2070.0)
+    assert r1["bound"] == "sfu"                      # 4 SFU results / 16 lanes > 28 issue slots / 128
+    assert r1["peak_gpair_s"] == pytest.approx(152 * 2070e6 * 16 / 4 / 1e9)
