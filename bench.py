@@ -39,9 +39,10 @@ WORKLOAD = "icosphere8_perturbed_q128cubed"
 # FP32-pipe operations (add/mul/fma/compare/select, the SFU argument scaling) and
 # SFU operations (sin, cos, reciprocal), per branch.
 OPS = {
-    "short_series": {"fp32": 35, "sfu": 2},   # face-integral series through k = 7 (P < 1/4)
-    "long_series": {"fp32": 43, "sfu": 2},    # through k = 11 (P < 9/4)
-    "edge_sum": {"fp32": 92, "sfu": 7},       # edge sum of Eq. 14, polynomial sinc
+    "short_series": {"fp32": 34, "sfu": 2},   # face-integral series through k = 7 (P < 1/4)
+    "long_series": {"fp32": 42, "sfu": 2},    # through k = 11 (P < 9/4)
+    "xlong_series": {"fp32": 59, "sfu": 2},   # through k = 17 (P < 9)
+    "edge_sum": {"fp32": 91, "sfu": 7},       # edge sum of Eq. 14, polynomial sinc
 }
 # 2D segment term (Pol2F32::tile): projections 6, u^2 1, Chebyshev sinc 6, range test 1, the
 # SFU argument scaling 1, w*S 1, accumulation 2; beyond |u| > pi the SFU sinc adds the turn
@@ -65,7 +66,7 @@ def parse():
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="c5",
                    help="c5: the benchmark workload; c5small: same mesh family at subdivision 6 on 64^3 Q "
                         "(for profiling captures)")
-    p.add_argument("--q-per-thread", type=int, default=2)
+    p.add_argument("--q-per-thread", type=int, default=4)
     p.add_argument("--block-threads", type=int, default=128)
     p.add_argument("--tau", type=float, default=0.0, help="face_series_tau (0 = library default)")
     p.add_argument("--no-extra", action="store_true", help="skip the secondary paths (batched 2D, adjoint)")
@@ -106,14 +107,15 @@ def peaks():
         return {"sm_max_mhz": 2070.0}, "fallback"
 
 
-def branch_mix(v, f, q, tau=3.0, r=2, nt=128, n_warps=4096, seed=0):
+def branch_mix(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0):
     """Fractions of (Q, face) pairs the kernel evaluates with each branch.
 
     Mirrors the kernel's rule on a seeded sample: for one face, a warp holds the
-    Q indices base + k*nt + 32*w + lane (k < r, lane < 32); all of them take the
-    short series if every one has P < min(tau, 1)^2/4, the long series if every
-    one has P < tau^2/4, and otherwise the edge sum (the few pairs below
-    tau_lo^2/4 that the edge branch redoes with the series are counted as edge).
+    Q indices base + k*nt + 32*w + lane (k < r, lane < 32); if every one has
+    P < tau^2/4 they all take the short series when every P < min(tau, 1)^2/4,
+    else the long series when every P < min(tau, 3)^2/4, else the extra-long
+    series; otherwise the edge sum (the few pairs below tau_lo^2/4 that the edge
+    branch redoes with the series are counted as edge).
     """
     rng = np.random.default_rng(seed)
     fi = rng.integers(0, f.shape[0], n_warps)
@@ -131,8 +133,9 @@ def branch_mix(v, f, q, tau=3.0, r=2, nt=128, n_warps=4096, seed=0):
     P = a0 * a0 + a0 * a1 + a1 * a1
     all_hi = np.all(P < 0.25 * tau * tau, axis=1)
     short = all_hi & np.all(P < 0.25 * min(tau, 1.0) ** 2, axis=1)
-    return {"short_series": float(np.mean(short)), "long_series": float(np.mean(all_hi & ~short)),
-            "edge_sum": float(np.mean(~all_hi))}
+    long_ = all_hi & ~short & np.all(P < 0.25 * min(tau, 3.0) ** 2, axis=1)
+    return {"short_series": float(np.mean(short)), "long_series": float(np.mean(long_)),
+            "xlong_series": float(np.mean(all_hi & ~short & ~long_)), "edge_sum": float(np.mean(~all_hi))}
 
 
 def sfu_sinc_fraction(verts, poly_off, q, n=1 << 16, seed=0):
@@ -514,34 +517,37 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_t = t.item()
 
-    # variant: the same workload with face_series_tau = 1 (short face series only, edge sum
-    # wherever the in-face phase spread reaches 1); one warm-up and one timed call
-    variant = None
+    # variants: the same workload with face_series_tau = 3 (no extra-long series) and 1 (short
+    # series only, edge sum wherever the in-face phase spread reaches 1); one warm-up and one
+    # timed call each
+    variants, variant_out = [], []
     out_main = out.clone()          # result of the benchmarked configuration (checked against the oracle)
     if not args.no_extra and world == 1:
-        ov = dict(tune, face_series_tau=1.0)
-        step(pft.make_options(ov))
-        flush.zero_()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ea.record()
-        eb.record()
-        a.record(stream)
-        step(pft.make_options({**ov, "main_start_event": ea.cuda_event, "main_stop_event": eb.cuda_event}))
-        b.record(stream)
-        b.synchronize()
-        variant = {"face_series_tau": 1.0, "value": pairs / (a.elapsed_time(b) / 1e3) / 1e9, "unit": UNIT,
-                   "ms_per_step": a.elapsed_time(b), "main_kernel_ms": ea.elapsed_time(eb),
-                   "device_status": int(pft.pft_status(ws))}
+        for vt in (3.0, 1.0):
+            ov = dict(tune, face_series_tau=vt)
+            step(pft.make_options(ov))
+            flush.zero_()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record()
+            eb.record()
+            a.record(stream)
+            step(pft.make_options({**ov, "main_start_event": ea.cuda_event, "main_stop_event": eb.cuda_event}))
+            b.record(stream)
+            b.synchronize()
+            variants.append({"face_series_tau": vt, "value": pairs / (a.elapsed_time(b) / 1e3) / 1e9, "unit": UNIT,
+                             "ms_per_step": a.elapsed_time(b), "main_kernel_ms": ea.elapsed_time(eb),
+                             "device_status": int(pft.pft_status(ws))})
+            variant_out.append(out.clone())
 
     if rank == 0:
         pk, pk_kind = peaks()
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         clk_max = float(pk.get("sm_max_mhz", 2070.0))
-        mix = branch_mix(v, f, q, tau=args.tau or 3.0, r=args.q_per_thread, nt=args.block_threads)
+        mix = branch_mix(v, f, q, tau=args.tau or 6.0, r=args.q_per_thread, nt=args.block_threads)
         ops, issue, achieved, peak_ops = roofline(pairs, ms_main / 1e3, mix, n_sm, clk_max)
-        if variant is not None:
+        for variant in variants:
             vmix = branch_mix(v, f, q, tau=variant["face_series_tau"], r=args.q_per_thread, nt=args.block_threads)
             _, _, v_ach, v_peak = roofline(pairs, variant["main_kernel_ms"] / 1e3, vmix, n_sm, clk_max)
             variant["branch_fractions"] = vmix
@@ -554,7 +560,7 @@ def main():
             "config": {"workload": WORKLOADS[args.workload][0], "faces": int(f.shape[0]),
                        "q_points": int(q.shape[0]), "pairs_per_step": pairs,
                        "launch": {"q_per_thread": args.q_per_thread, "block_threads": args.block_threads,
-                                  "face_series_tau": opts.face_series_tau or 3.0}, "edge_terms_per_step": 3 * pairs,
+                                  "face_series_tau": opts.face_series_tau or 6.0}, "edge_terms_per_step": 3 * pairs,
                        "l2": "flushed between steps (512 MB write outside the step events)",
                        "parallelism": f"independent replicas x{world}" if world > 1 else "single GPU",
                        "wall_s_timed_region": t_wall, "device_status": int(status)},
@@ -581,12 +587,12 @@ def main():
             vol = float(np.real(__import__("oracle").ft3d(v, f, np.zeros((1, 3)))[0]))
             cb["max_abs_err_vs_oracle_over_volume"] = float(np.max(np.abs(got[:, 0] + 1j * got[:, 1] - ref)) / vol)
             line["cpu_baseline"] = cb
-            if variant is not None:
-                gv = out.cpu().numpy()[idx]
+            for variant, vo in zip(variants, variant_out):
+                gv = vo.cpu().numpy()[idx]
                 variant["max_abs_err_vs_oracle_over_volume"] = float(
                     np.max(np.abs(gv[:, 0] + 1j * gv[:, 1] - ref)) / vol)
-        if variant is not None:
-            line["variants"] = [variant]
+        if variants:
+            line["variants"] = variants
         if not args.no_extra and world == 1:
             line["fp64_gpu"] = bench_fp64(pft, vd, fd, qd, out_main, lib, dev)
         if not args.no_extra and world == 1:

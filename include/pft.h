@@ -65,8 +65,8 @@ typedef enum {
  *  block_threads    threads per block of the main kernel (0 = default; 128 or 256).
  *  k_splits         number of segment/face chunks summed in the FP64 second pass
  *                   (0 = chosen from the problem size and the GPU).  For a fixed
- *                   value the result is bitwise reproducible; different values
- *                   agree to rounding.
+ *                   value and launch shape the result is bitwise reproducible;
+ *                   different values agree to rounding.
  *  tile_items       must be 0 (the shared-memory tile size is fixed per path).
  *  face_series_tau  3D only: faces whose corner phases satisfy
  *                   P = (a0^2 + a1^2 + a2^2)/2 < tau^2/4 (a_k = Q.(p_k - centroid);
@@ -75,10 +75,11 @@ typedef enum {
  *                   cancels there.  The decision is made per face for each group
  *                   of 32 threads' Q points; a group whose P are all below 1/4
  *                   takes a short form of the series, one with P up to 9/4 a
- *                   longer form.  Must lie in (0, 3]; 0 = default 3.0 (fewest
- *                   operations per pair and the smallest error; 1.0 keeps the edge
- *                   sum for every face whose spread is at least 1, where it
- *                   loses nothing to cancellation).
+ *                   longer form, one with P up to 9 the longest.  Must lie in
+ *                   (0, 6]; 0 = default 6.0 (fewest operations per pair; 1.0
+ *                   keeps the edge sum for every face whose spread is at least
+ *                   1, where it loses nothing to cancellation).  The FP64 path
+ *                   uses at most 3.0 (its series is kept through k = 16).
  *  main_start_event, main_stop_event
  *                   cudaEvent_t handles or NULL.  When set, they are recorded on
  *                   `stream` immediately before and after the main (pair-sum)

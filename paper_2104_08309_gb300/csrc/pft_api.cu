@@ -27,7 +27,7 @@ int resolve(const pft_options* o, int dim, Opts& out) {
   const pft_options& p = o ? *o : z;
   if (p.precision != PFT_FP32_COMPENSATED && p.precision != PFT_FP64) return PFT_ERR_INVALID_ARG;
   out.fp64 = (p.precision == PFT_FP64);
-  out.r = p.q_per_thread ? p.q_per_thread : (out.fp64 ? 1 : (dim == 3 ? 2 : 4));
+  out.r = p.q_per_thread ? p.q_per_thread : (out.fp64 ? 1 : 4);
   out.nt = p.block_threads ? p.block_threads : ((out.fp64 || dim == 3) ? 128 : 256);
   const bool r_ok = out.fp64 ? (out.r == 1 || out.r == 2) : (out.r == 1 || out.r == 2 || out.r == 4 || out.r == 8);
   if (!r_ok || (out.nt != 128 && out.nt != 256)) return PFT_ERR_UNSUPPORTED;
@@ -35,8 +35,8 @@ int resolve(const pft_options* o, int dim, Opts& out) {
   out.k_splits = p.k_splits;
   if (p.tile_items != 0) return PFT_ERR_UNSUPPORTED;
   float tau = p.face_series_tau;
-  if (tau == 0.f) tau = 3.0f;
-  if (!(tau > 0.f && tau <= 3.0f)) return PFT_ERR_INVALID_ARG;
+  if (tau == 0.f) tau = 6.0f;
+  if (!(tau > 0.f && tau <= 6.0f)) return PFT_ERR_INVALID_ARG;
   out.tau = tau;
   out.ev_start = static_cast<cudaEvent_t>(p.main_start_event);
   out.ev_stop = static_cast<cudaEvent_t>(p.main_stop_event);

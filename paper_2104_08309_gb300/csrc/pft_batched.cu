@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_batched(
         ok = false;
         break;
       }
-      Pol::template tile<R>(ring + s * TILE, min(TILE, cnt - t * TILE), qr, acc, Thr{0.f, 0.f, 0});
+      Pol::template tile<R>(ring + s * TILE, min(TILE, cnt - t * TILE), qr, acc, Thr{0.f, 0.f, 0, 0});
       __syncwarp();
       if ((threadIdx.x & 31) == 0) {
         __threadfence_block();

@@ -156,9 +156,14 @@ __device__ __forceinline__ void face_adj(const QRec& Q, const float4 A, const fl
   float mu, a0, a1, s, P;
   face_common(qx, qy, qz, A, B, C, mu, a0, a1, s, P);
   // the forward kernel's rule over the warp's faces: short series when all have
-  // P < 1/4 (or this one is below p_lo), long series when all are below p_hi
+  // P < 1/4 (or this one is below p_lo), long series when all are below 9/4 (and
+  // p_hi), extra-long series when all are below p_hi; the votes are taken by
+  // every lane before any of them branches
   const bool all_hi = __all_sync(0xffffffffu, P < th.hi);
-  const bool shorts = (th.longs ? __all_sync(0xffffffffu, P < kPShort) : all_hi) || (P < th.lo);
+  const bool all_short = __all_sync(0xffffffffu, P < kPShort);
+  const bool all_long = __all_sync(0xffffffffu, P < kPLong);
+  const bool shorts = (th.longs ? all_short : all_hi) || (P < th.lo);
+  const bool longs = !shorts && all_hi && (!th.xlongs || all_long);
   const bool series = shorts || all_hi;
   float sm, cm;
   __sincosf(mu, &sm, &cm);
@@ -179,7 +184,7 @@ __device__ __forceinline__ void face_adj(const QRec& Q, const float4 A, const fl
     dGre_dT = 2.0f * T * -2.48015873e-5f;
     dGim_dP = T * fmaf(P, 2.0f * -8.26719577e-6f, 3.96825397e-4f);
     dGim_dT = r;
-  } else if (series) {        // long series (P < 9/4, k <= 11), as face_series_long
+  } else if (longs) {         // long series (P < 9/4, k <= 11), as face_series_long
     T = -(a0 * a1) * (a0 + a1);
     const float T2 = T * T;
     float A = fmaf(P, -2.087675588e-9f, 2.75573192e-7f);
@@ -209,6 +214,66 @@ __device__ __forceinline__ void face_adj(const QRec& Q, const float4 A, const fl
     dGre_dT = 2.0f * T * Bp;
     dGim_dP = T * fmaf(T2, -6.423617749e-10f, dD);
     dGim_dT = fmaf(3.0f * T2, E, D);
+  } else if (series) {        // extra-long series (P < 9, k <= 17), as face_series_xlong
+    T = -(a0 * a1) * (a0 + a1);
+    const float T2 = T * T;
+    float A0 = fmaf(P, 1.561920697e-16f, -4.779477332e-14f);
+    A0 = fmaf(P, A0, 1.147074560e-11f);
+    A0 = fmaf(P, A0, -2.087675699e-09f);
+    A0 = fmaf(P, A0, 2.755731922e-07f);
+    A0 = fmaf(P, A0, -2.480158730e-05f);
+    A0 = fmaf(P, A0, 1.388888889e-03f);
+    A0 = fmaf(P, A0, -4.166666667e-02f);
+    A0 = fmaf(P, A0, 0.5f);
+    float A2 = fmaf(P, 3.280033463e-15f, -7.169215999e-13f);
+    A2 = fmaf(P, A2, 1.147074560e-10f);
+    A2 = fmaf(P, A2, -1.252605419e-08f);
+    A2 = fmaf(P, A2, 8.267195767e-07f);
+    A2 = fmaf(P, A2, -2.480158730e-05f);
+    float A4 = fmaf(P, 2.342881045e-15f, -2.389738666e-13f);
+    A4 = fmaf(P, A4, 1.147074560e-11f);
+    float D1 = fmaf(P, 6.576508197e-17f, -1.968020078e-14f);
+    D1 = fmaf(P, D1, 4.588298239e-12f);
+    D1 = fmaf(P, D1, -8.029521918e-10f);
+    D1 = fmaf(P, D1, 1.002084335e-07f);
+    D1 = fmaf(P, D1, -8.267195767e-06f);
+    D1 = fmaf(P, D1, 3.968253968e-04f);
+    D1 = fmaf(P, D1, -8.333333333e-03f);
+    float D3 = fmaf(P, 2.877222336e-16f, -5.622914509e-14f);
+    D3 = fmaf(P, D3, 7.647163732e-12f);
+    D3 = fmaf(P, D3, -6.423617535e-10f);
+    D3 = fmaf(P, D3, 2.505210839e-08f);
+    const float D5 = fmaf(P, 4.932381148e-17f, -2.811457254e-15f);
+    const float A24 = fmaf(T2, A4, A2), D35 = fmaf(T2, D5, D3);
+    zr = -T * fmaf(T2, D35, D1);
+    zi = fmaf(T2, A24, A0);
+    // derivatives of A_j, D_j in P (coefficients i c_i)
+    float dA0 = fmaf(P, 8.0f * 1.561920697e-16f, 7.0f * -4.779477332e-14f);
+    dA0 = fmaf(P, dA0, 6.0f * 1.147074560e-11f);
+    dA0 = fmaf(P, dA0, 5.0f * -2.087675699e-09f);
+    dA0 = fmaf(P, dA0, 4.0f * 2.755731922e-07f);
+    dA0 = fmaf(P, dA0, 3.0f * -2.480158730e-05f);
+    dA0 = fmaf(P, dA0, 2.0f * 1.388888889e-03f);
+    dA0 = fmaf(P, dA0, -4.166666667e-02f);
+    float dA2 = fmaf(P, 5.0f * 3.280033463e-15f, 4.0f * -7.169215999e-13f);
+    dA2 = fmaf(P, dA2, 3.0f * 1.147074560e-10f);
+    dA2 = fmaf(P, dA2, 2.0f * -1.252605419e-08f);
+    dA2 = fmaf(P, dA2, 8.267195767e-07f);
+    const float dA4 = fmaf(P, 2.0f * 2.342881045e-15f, -2.389738666e-13f);
+    float dD1 = fmaf(P, 7.0f * 6.576508197e-17f, 6.0f * -1.968020078e-14f);
+    dD1 = fmaf(P, dD1, 5.0f * 4.588298239e-12f);
+    dD1 = fmaf(P, dD1, 4.0f * -8.029521918e-10f);
+    dD1 = fmaf(P, dD1, 3.0f * 1.002084335e-07f);
+    dD1 = fmaf(P, dD1, 2.0f * -8.267195767e-06f);
+    dD1 = fmaf(P, dD1, 3.968253968e-04f);
+    float dD3 = fmaf(P, 4.0f * 2.877222336e-16f, 3.0f * -5.622914509e-14f);
+    dD3 = fmaf(P, dD3, 2.0f * 7.647163732e-12f);
+    dD3 = fmaf(P, dD3, -6.423617535e-10f);
+    const float dD5 = 4.932381148e-17f;
+    dGre_dP = fmaf(T2, fmaf(T2, dA4, dA2), dA0);
+    dGre_dT = 2.0f * T * fmaf(2.0f * T2, A4, A2);                  // d/dT (T^2 A2 + T^4 A4)
+    dGim_dP = T * fmaf(T2, fmaf(T2, dD5, dD3), dD1);
+    dGim_dT = fmaf(T2, fmaf(5.0f * T2, D5, 3.0f * D3), D1);        // d/dT (T D1 + T^3 D3 + T^5 D5)
   } else {
     const float nx = C.y, ny = C.z, nz = C.w;
     Xx = fmaf(ny, qz, -nz * qy);
@@ -661,10 +726,10 @@ int check_opts(const pft_options* o, Thr& th) {
   if (p.precision != PFT_FP32_COMPENSATED) return PFT_ERR_UNSUPPORTED;   // the adjoint runs in FP32
   if (p.q_per_thread != 0 || p.block_threads != 0 || p.k_splits != 0 || p.tile_items != 0)
     return PFT_ERR_UNSUPPORTED;
-  float tau = p.face_series_tau == 0.f ? 3.0f : p.face_series_tau;
-  if (!(tau > 0.f && tau <= 3.f)) return PFT_ERR_INVALID_ARG;
+  float tau = p.face_series_tau == 0.f ? 6.0f : p.face_series_tau;
+  if (!(tau > 0.f && tau <= 6.f)) return PFT_ERR_INVALID_ARG;
   const float lo = std::min(tau, 0.05f);
-  th = Thr{0.25f * tau * tau, 0.25f * lo * lo, tau > 1.f ? 1 : 0};
+  th = Thr{0.25f * tau * tau, 0.25f * lo * lo, tau > 1.f ? 1 : 0, tau > 3.f ? 1 : 0};
   return PFT_OK;
 }
 

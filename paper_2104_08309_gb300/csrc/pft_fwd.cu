@@ -161,8 +161,10 @@ struct OccF {
 
 cudaError_t launch_fwd(int dim, bool fp64, const FwdLaunch& L, const void* items, int64_t n_items, const double* q,
                        int64_t n_q, float tau, double2* partial, uint32_t* status, cudaStream_t st) {
+  // the FP64 path keeps its series (through k = 16) for P < 9/4, where it truncates below 1e-14
+  if (fp64) tau = fminf(tau, 3.0f);
   const float tau_lo = fminf(tau, kTauLo);
-  const Thr th{0.25f * tau * tau, 0.25f * tau_lo * tau_lo, tau > 1.0f ? 1 : 0};
+  const Thr th{0.25f * tau * tau, 0.25f * tau_lo * tau_lo, tau > 1.0f ? 1 : 0, tau > 3.0f ? 1 : 0};
   LaunchF f{L, items, n_items, q, n_q, th, partial, status, st};
   if (dim == 2) return fp64 ? dispatch<Pol2F64>(L.r, L.nt, f) : dispatch<Pol2F32>(L.r, L.nt, f);
   return fp64 ? dispatch<Pol3F64>(L.r, L.nt, f) : dispatch<Pol3F32>(L.r, L.nt, f);

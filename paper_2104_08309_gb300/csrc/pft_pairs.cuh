@@ -12,10 +12,12 @@ constexpr int kStages = 4;
 // Thresholds on P (see the 3D face term below): p_hi = tau^2/4, p_lo = tau_lo^2/4.
 struct Thr {
   float hi, lo;
-  int longs;   // tau > 1: warps whose faces are not all below kPShort take the long series
+  int longs;    // tau > 1: warps whose faces are not all below kPShort take a longer series
+  int xlongs;   // tau > 3: warps whose faces are not all below kPLong take the extra-long series
 };
 constexpr float kTauLo = 0.05f;
 constexpr float kPShort = 0.25f;   // P below which the short series suffices (tau = 1)
+constexpr float kPLong = 2.25f;    // P below which the long series suffices (tau = 3)
 
 // Resident blocks per SM the register budget is sized for: 16-24 warps of
 // 256 threads, fewer registers per thread for fewer Q points per thread.
@@ -68,11 +70,13 @@ __device__ __forceinline__ void seg_pair_f64(double qx, double qy, const Seg64& 
 //   G = sum_k i^k h_k(a) / (k+2)!,   h_k = P h_{k-2} + T h_{k-3},
 // P = a0^2 + a0 a1 + a1^2 (= h_2), T = a0 a1 a2 (= h_3); P < tau^2/4 implies
 // max_l |Q.d_l| < tau.  For P < 1/4 the series is kept through k = 7, for
-// P < 9/4 through k = 11; the omitted terms are below 4e-9 (|G| <= 1/2).
+// P < 9/4 through k = 11, for P < 9 through k = 17; the omitted terms are
+// below 4e-9, 4e-9 and 1e-9 (|G| <= 1/2).
 //
 // Branch choice, per face and warp: the series is taken for all of a thread's
 // Q points when every Q point of every lane of the warp has P < p_hi = tau^2/4
-// -- its short form when every one also has P < 1/4, else its long form;
+// -- its short form when every one also has P < 1/4, else its long form when
+// every one has P < 9/4, else its extra-long form;
 // otherwise the edge sum, except for Q points with P < p_lo = tau_lo^2/4
 // (tau_lo = min(tau, 0.05): below it the edge sum would lose more than ~4 bits
 // to cancellation), which are redone with the short series.  All three evaluate
@@ -125,6 +129,47 @@ __device__ __forceinline__ void face_series_long(float a0, float a1, float P, fl
   D = fmaf(P, D, -8.33333333e-3f);                         // -1/5!
   const float E = fmaf(P, -6.423617749e-10f, 2.505210794e-8f);   // -4/13!, 1/11!
   const float gim = T * fmaf(T2, E, D);
+  zr = -gim;
+  zi = gre;
+}
+
+// Extra-long form (P < 9, i.e. tau <= 6): h_k through k = 17.  With
+// h_k = sum over 2i + 3j = k of C(i + j, i) P^i T^j,
+//   G_re = A0(P) + T^2 (A2(P) + T^2 A4(P)),  G_im = T (D1(P) + T^2 (D3(P) + T^2 D5(P))),
+// the coefficient of P^i in A_j / D_j being +-C(i + j, i)/(2i + 3j + 2)!;
+// the omitted terms (k >= 18) are below 1e-9 (|G| <= 1/2).
+__device__ __forceinline__ void face_series_xlong(float a0, float a1, float P, float& zr, float& zi) {
+  const float T = -(a0 * a1) * (a0 + a1);
+  const float T2 = T * T;
+  float A0 = fmaf(P, 1.561920697e-16f, -4.779477332e-14f);   // 1/18!, -1/16!
+  A0 = fmaf(P, A0, 1.147074560e-11f);                         // 1/14!
+  A0 = fmaf(P, A0, -2.087675699e-09f);                        // -1/12!
+  A0 = fmaf(P, A0, 2.755731922e-07f);                         // 1/10!
+  A0 = fmaf(P, A0, -2.480158730e-05f);                        // -1/8!
+  A0 = fmaf(P, A0, 1.388888889e-03f);                         // 1/6!
+  A0 = fmaf(P, A0, -4.166666667e-02f);                        // -1/4!
+  A0 = fmaf(P, A0, 0.5f);                                     // 1/2!
+  float A2 = fmaf(P, 3.280033463e-15f, -7.169215999e-13f);   // 21/18!, -15/16!
+  A2 = fmaf(P, A2, 1.147074560e-10f);                         // 10/14!
+  A2 = fmaf(P, A2, -1.252605419e-08f);                        // -6/12!
+  A2 = fmaf(P, A2, 8.267195767e-07f);                         // 3/10!
+  A2 = fmaf(P, A2, -2.480158730e-05f);                        // -1/8!
+  float A4 = fmaf(P, 2.342881045e-15f, -2.389738666e-13f);   // 15/18!, -5/16!
+  A4 = fmaf(P, A4, 1.147074560e-11f);                         // 1/14!
+  float D1 = fmaf(P, 6.576508197e-17f, -1.968020078e-14f);   // 8/19!, -7/17!
+  D1 = fmaf(P, D1, 4.588298239e-12f);                         // 6/15!
+  D1 = fmaf(P, D1, -8.029521918e-10f);                        // -5/13!
+  D1 = fmaf(P, D1, 1.002084335e-07f);                         // 4/11!
+  D1 = fmaf(P, D1, -8.267195767e-06f);                        // -3/9!
+  D1 = fmaf(P, D1, 3.968253968e-04f);                         // 2/7!
+  D1 = fmaf(P, D1, -8.333333333e-03f);                        // -1/5!
+  float D3 = fmaf(P, 2.877222336e-16f, -5.622914509e-14f);   // 35/19!, -20/17!
+  D3 = fmaf(P, D3, 7.647163732e-12f);                         // 10/15!
+  D3 = fmaf(P, D3, -6.423617535e-10f);                        // -4/13!
+  D3 = fmaf(P, D3, 2.505210839e-08f);                         // 1/11!
+  const float D5 = fmaf(P, 4.932381148e-17f, -2.811457254e-15f);   // 6/19!, -1/17!
+  const float gre = fmaf(T2, fmaf(T2, A4, A2), A0);
+  const float gim = T * fmaf(T2, fmaf(T2, D5, D3), D1);
   zr = -gim;
   zi = gre;
 }
@@ -343,27 +388,29 @@ struct Pol3F32 {
       const float4* p = reinterpret_cast<const float4*>(t + i);
       const float4 A = p[0], B = p[1], C = p[2];
       float mu[R], a0[R], a1[R], s[R], P[R], zr[R], zi[R];
-      bool all_hi = true, all_short = true, any_lo = false;
+      float pmax = 0.f, pmin = 0.f;   // over the thread's Q points: the branch tests need only these
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         face_common(q[r][0], q[r][1], q[r][2], A, B, C, mu[r], a0[r], a1[r], s[r], P[r]);
-        all_hi = all_hi && (P[r] < th.hi);
-        all_short = all_short && (P[r] < kPShort);
-        any_lo = any_lo || (P[r] < th.lo);
+        pmax = r ? fmaxf(pmax, P[r]) : P[r];
+        pmin = r ? fminf(pmin, P[r]) : P[r];
       }
-      if (__all_sync(0xffffffffu, all_hi)) {
-        // th.longs is uniform over the grid, so the second vote is warp-uniform too
-        if (!th.longs || __all_sync(0xffffffffu, all_short)) {
+      if (__all_sync(0xffffffffu, pmax < th.hi)) {
+        // th.longs and th.xlongs are uniform over the grid, so the inner votes are warp-uniform too
+        if (!th.longs || __all_sync(0xffffffffu, pmax < kPShort)) {
 #pragma unroll
           for (int r = 0; r < R; ++r) face_series(a0[r], a1[r], P[r], zr[r], zi[r]);
-        } else {
+        } else if (!th.xlongs || __all_sync(0xffffffffu, pmax < kPLong)) {
 #pragma unroll
           for (int r = 0; r < R; ++r) face_series_long(a0[r], a1[r], P[r], zr[r], zi[r]);
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) face_series_xlong(a0[r], a1[r], P[r], zr[r], zi[r]);
         }
       } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) face_edge(q[r][0], q[r][1], q[r][2], A, B, C, a0[r], a1[r], zr[r], zi[r]);
-        if (any_lo) {
+        if (pmin < th.lo) {
 #pragma unroll
           for (int r = 0; r < R; ++r)
             if (P[r] < th.lo) face_series(a0[r], a1[r], P[r], zr[r], zi[r]);   // P < tau_lo^2/4 <= 1/4

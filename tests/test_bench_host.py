@@ -16,12 +16,14 @@ def mesh():
 def test_branch_fractions_partition_the_pairs(mesh):
     v, f = mesh
     q = synth.q_grid_3d(32, 60.0)
-    for tau in (0.5, 1.0, 2.0, 3.0):
+    for tau in (0.5, 1.0, 2.0, 3.0, 4.5, 6.0):
         m = bench.branch_mix(v, f, q, tau=tau, n_warps=512)
         assert set(m) == set(bench.OPS)
         assert abs(sum(m.values()) - 1.0) < 1e-12
         if tau <= 1.0:
             assert m["long_series"] == 0.0
+        if tau <= 3.0:
+            assert m["xlong_series"] == 0.0
     lo = bench.branch_mix(v, f, q, tau=1.0, n_warps=512)
     hi = bench.branch_mix(v, f, q, tau=3.0, n_warps=512)
     # the same seeded sample: raising tau only moves warps from the edge sum into the series,
@@ -41,14 +43,17 @@ def test_branch_rule_on_hand_made_phases():
     # a0 = Q.(p0 - g) with g = (1/3, 1/3, 0): Q = (k, 0, 0) gives a = (-k/3, 2k/3, -k/3), P = k^2/3
     inplane = np.tile([[1.5, 0.0, 0.0]], (256, 1))             # P = 0.75
     assert bench.branch_mix(v, f, inplane, tau=3.0, r=2, nt=128, n_warps=16)["long_series"] == 1.0
+    assert bench.branch_mix(v, f, inplane, tau=6.0, r=2, nt=128, n_warps=16)["long_series"] == 1.0
     assert bench.branch_mix(v, f, inplane, tau=1.0, r=2, nt=128, n_warps=16)["edge_sum"] == 1.0
+    far = np.tile([[4.0, 0.0, 0.0]], (256, 1))                 # P = 16/3
+    assert bench.branch_mix(v, f, far, tau=6.0, r=2, nt=128, n_warps=16)["xlong_series"] == 1.0
+    assert bench.branch_mix(v, f, far, tau=3.0, r=2, nt=128, n_warps=16)["edge_sum"] == 1.0
 
 
 def test_roofline_arithmetic():
-    mix = {"short_series": 0.25, "long_series": 0.5, "edge_sum": 0.25}
+    mix = {"short_series": 0.25, "long_series": 0.25, "xlong_series": 0.25, "edge_sum": 0.25}
     ops, issue, achieved, peak = bench.roofline(1e12, 1.0, mix, 152, 2070.0)
-    want = {k: 0.25 * bench.OPS["short_series"][k] + 0.5 * bench.OPS["long_series"][k]
-            + 0.25 * bench.OPS["edge_sum"][k] for k in ("fp32", "sfu")}
+    want = {k: 0.25 * sum(bench.OPS[b][k] for b in bench.OPS) for k in ("fp32", "sfu")}
     assert ops == pytest.approx(want)
     assert issue == pytest.approx(want["fp32"] + want["sfu"])
     assert achieved == pytest.approx(issue * 1e12)

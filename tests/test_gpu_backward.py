@@ -50,7 +50,7 @@ def test_2d_backward_vs_oracle(torch_dev, rng):
     assert _rel(got, ref) < GTOL
 
 
-@pytest.mark.parametrize("tau", [1.0, 0.05, 3.0])
+@pytest.mark.parametrize("tau", [1.0, 0.05, 3.0, 6.0])
 def test_3d_backward_vs_oracle(torch_dev, rng, tau):
     torch, dev = torch_dev
     import paper_2104_08309_gb300 as pft

@@ -122,3 +122,60 @@ def test_face_series_truncation_bounds():
              ((a0, a1, a2), (a1, a2, a0), (a2, a0, a1)))
     _, _, g = _exact_G(a0, a1)
     assert np.max(np.abs(g - dd)) < 1e-12
+
+
+def _xlong_expected():
+    """Coefficients of face_series_xlong in source order: A0, A2, A4, D1, D3, D5, each from its
+    highest power of P down (A0's constant 1/2 is written as 0.5f and not listed)."""
+    from math import comb
+    f = math.factorial
+
+    def c(i, j):
+        k = 2 * i + 3 * j
+        sign = (1 if k % 4 == 0 else -1) if k % 2 == 0 else (1 if k % 4 == 1 else -1)
+        return sign * comb(i + j, i) / f(k + 2)
+
+    out = []
+    for j, imax in ((0, 8), (2, 5), (4, 2), (1, 7), (3, 4), (5, 1)):
+        out += [c(i, j) for i in range(imax, -1, -1) if not (j == 0 and i == 0)]
+    return out
+
+
+def test_xlong_face_series_coefficients():
+    """Extra-long form: the coefficient of P^i T^j is +-C(i + j, i)/(2i + 3j + 2)! (h_k through k = 17)."""
+    c = _floats(_body("pft_pairs.cuh", "void face_series_xlong("))
+    expected = _xlong_expected()
+    assert len(c) == len(expected)
+    for got, want in zip(c, expected):
+        assert abs(got - want) <= 1e-6 * abs(want)
+
+
+def test_xlong_face_series_truncation_bound():
+    """The extra-long form with the source's constants, on P < 9, against the converged series."""
+    c = _floats(_body("pft_pairs.cuh", "void face_series_xlong("))
+    P, T, g = _exact_G(*_phases(9.0))
+    A0 = _horner(c[0:8] + [0.5], P)
+    A2 = _horner(c[8:14], P)
+    A4 = _horner(c[14:17], P)
+    D1 = _horner(c[17:25], P)
+    D3 = _horner(c[25:30], P)
+    D5 = _horner(c[30:32], P)
+    T2 = T * T
+    gre = A0 + T2 * (A2 + T2 * A4)
+    gim = T * (D1 + T2 * (D3 + T2 * D5))
+    assert np.max(np.abs(gre + 1j * gim - g)) < 1e-9
+    # and in float32 (the kernel's precision) within a few units of rounding of |G| <= 1/2
+    f32 = np.float32
+    P32, T32 = P.astype(f32), T.astype(f32)
+    T232 = (T32 * T32).astype(f32)
+    h = lambda cs: _horner32([f32(x) for x in cs], P32)
+    g32 = (h(c[0:8] + [0.5]) + T232 * (h(c[8:14]) + T232 * h(c[14:17]))) + 1j * (
+        T32 * (h(c[17:25]) + T232 * (h(c[25:30]) + T232 * h(c[30:32]))))
+    assert np.max(np.abs(g32 - g)) < 2e-7
+
+
+def _horner32(coef, x):
+    acc = np.zeros_like(x)
+    for c in coef:
+        acc = (acc * x + c).astype(np.float32)
+    return acc

@@ -65,7 +65,7 @@ def test_workspace_sizes(lib):
     assert lib.pft3d_workspace_size(10242, 20480, 262144, ctypes.byref(o64)) > s3   # 96-byte records
     assert lib.pft2d_workspace_size(64, 1, 16384, None) >= 256 + 64 * 16 + 16384 * 16
     assert lib.pft3d_workspace_size(-1, 3, 3, None) == 0
-    bad = _capi.Options(face_series_tau=3.5)
+    bad = _capi.Options(face_series_tau=6.5)
     assert lib.pft3d_workspace_size(3, 1, 1, ctypes.byref(bad)) == 0
 
 
