@@ -307,12 +307,28 @@ def bench_batched(dev, warmup, steps):
                     torch.cuda.get_device_properties(dev).multi_processor_count, float(pk.get("sm_max_mhz", 2070.0)))
     rl["note"] = ("whole 4-launch call timed; the FP64 finish of the 16.8M outputs (2/|Q|^2, e^{iQ.c}) "
                   "is outside the per-pair count")
+    # the plain FP64 GPU path on the same batch (one call), and the FP32 result's deviation from it
+    p64 = pft.pft2d_batched_prepare(w.poly_off, w.q.shape[0], options={"precision": "fp64"}, device=dev)
+    o64 = pft.pft2d_polygons_batched(vd, offd, qd, prepared=p64)
+    torch.cuda.synchronize()
+    flush.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    pft.pft2d_polygons_batched(vd, offd, qd, prepared=p64, out=o64)
+    b.record()
+    b.synchronize()
+    q0 = int(np.flatnonzero(np.all(w.q == 0, axis=1))[0])
+    area = o64[:, q0, 0].abs()
+    dev32 = ((out - o64).abs().amax(dim=(1, 2)) / area).max().item()
+    fp64 = {"value": pairs / (a.elapsed_time(b) / 1e3) / 1e9, "unit": UNIT, "ms": a.elapsed_time(b),
+            "fp32_vs_fp64_max_abs_over_area": dev32}
+    del o64
     return {"value": pairs / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "pairs_per_step": pairs,
             "roofline": rl,
             "polygons": int(w.poly_off.size - 1), "segments": int(w.verts.shape[0]), "q_points": int(w.q.shape[0]),
             "launches_per_step": int(launches), "cuda_graph": True, "device_status": int(status),
             "launch": {"q_per_thread": tuned["q_per_thread"], "block_threads": tuned["block_threads"],
-                       "chosen_by": "autotune"},
+                       "chosen_by": "autotune"}, "fp64_gpu": fp64,
             "l2": "flushed between steps"}
 
 
@@ -383,11 +399,12 @@ def bench_adjoint(dev, warmup, steps):
             "launches_adjoint": int(pft.load().pft_backward_last_launch_count())}
 
 
-KERNEL_SOURCES = ("pft_fwd.cu", "pft_pairs.cuh", "pft_common.cuh", "pft_kernels.cuh")
+KERNEL_SOURCES = ("pft_fwd.cu", "pft_pairs.cuh", "pft_common.cuh", "pft_kernels.cuh", "pft_api.cu")
 
 
 def kernel_source_hash():
-    """First 16 hex digits of the SHA-256 of the main kernel's sources (in a fixed order)."""
+    """First 16 hex digits of the SHA-256 of the main kernel's sources and of the launch planner
+    (in a fixed order): the DRAM traffic of a launch depends on both."""
     import hashlib
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
