@@ -52,6 +52,7 @@ def _load():
             lib.orc_ft2d_batched.argtypes = [_dp, _i64p, _i64, _dp, _i64p, _i64, _dp, ctypes.c_int]
             lib.orc_ft3d.argtypes = [_dp, _i64, _i32p, _i64, _dp, _i64, _dp, ctypes.c_int]
             lib.orc_face_terms3d.argtypes = [_dp, _i64, _i32p, _i64, _dp, _dp]
+            lib.orc_ft3d_poly.argtypes = [_dp, _i64, _i32p, _i64p, _i64, _dp, _i64, _dp, ctypes.c_int]
             lib.orc_grad2d.argtypes = [_dp, _i64p, _i64, _dp, _i64, _dp, _dp, ctypes.c_int]
             lib.orc_grad3d.argtypes = [_dp, _i64, _i32p, _i64, _dp, _i64, _dp, _i64p, _i64, _dp,
                                        ctypes.c_int]
@@ -139,6 +140,26 @@ def ft3d(verts, faces, q, threads=None) -> np.ndarray:
                           q.shape[0], _ptr(out, _dp), _threads(threads))
     if rc:
         raise ValueError("face index out of range")
+    return _complex(out)
+
+
+def ft3d_poly(verts, face_idx, face_off, q, threads=None) -> np.ndarray:
+    """FT_V(Q) of a closed surface of planar polygon faces in CSR form (face m: the vertex
+    indices face_idx[face_off[m]:face_off[m+1]], counter-clockwise seen from outside);
+    Eq. 14 over each face's own edges with its Newell normal."""
+    v = _f64(verts, 3)
+    idx = np.ascontiguousarray(np.asarray(face_idx, dtype=np.int32).reshape(-1))
+    off = np.ascontiguousarray(np.asarray(face_off, dtype=np.int64).reshape(-1))
+    if off.size < 1 or off[-1] != idx.size:
+        raise ValueError("face_off must end at len(face_idx)")
+    q = _f64(q, 3)
+    out = np.empty((q.shape[0], 2))
+    rc = _load().orc_ft3d_poly(_ptr(v, _dp), v.shape[0], _ptr(idx, _i32p), _ptr(off, _i64p), off.size - 1,
+                               _ptr(q, _dp), q.shape[0], _ptr(out, _dp), _threads(threads))
+    if rc == 2:
+        raise ValueError("face index out of range")
+    if rc:
+        raise ValueError("malformed face offsets (each face needs at least 3 vertices)")
     return _complex(out)
 
 

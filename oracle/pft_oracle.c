@@ -1,6 +1,7 @@
 /*
  * pft_oracle.c -- FP64 CPU oracle for the direct Fourier transform of polygonal
- * areas and closed triangulated surfaces (B. B. Maranville, arXiv 2104.08309).
+ * areas and closed surfaces of triangles or planar polygons (B. B. Maranville,
+ * arXiv 2104.08309).
  *
  * TEST INFRASTRUCTURE ONLY.  This is the plain, slow, double-precision
  * statement of what the CUDA library computes.  Only the test suite, the smoke
@@ -332,6 +333,111 @@ int orc_face_terms3d(const double* verts, int64_t n_verts, const int32_t* faces,
     double complex t = face_term(Q, verts + 3 * faces[3 * m], verts + 3 * faces[3 * m + 1],
                                  verts + 3 * faces[3 * m + 2]) / q2;
     out[2 * m] = creal(t); out[2 * m + 1] = cimag(t);
+  }
+  return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * 3D: closed surface of planar polygon faces, CSR: face m has the vertex
+ * indices idx[off[m]] .. idx[off[m+1]-1], counter-clockwise seen from outside.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * One planar polygon face's term I_m of Eq. 14 (sign fixed as for triangles):
+ * the same edge sum over the face's n edges, with the face normal direction
+ * N = sum_k p_k x p_{k+1} (Newell's vector; for a planar polygon |N| = 2 area
+ * and the formula only uses the direction of N, since it is homogeneous of
+ * degree 0 in N).  Where the face's phase spread max_k Q.p_k - min_k Q.p_k is
+ * below TAU_FACE, or Q is parallel to N, the edge sum cancels; there the face
+ * integral is split into the fan triangles (p_0, p_k, p_{k+1}), which tile the
+ * polygon with signed areas (exact by additivity), each taken by face_term.
+ * Returned without the 1/|Q|^2 factor.
+ */
+static double complex poly_face_term(const double* Q, const double* v, const int32_t* idx, int64_t n) {
+  double N[3] = {0.0, 0.0, 0.0}, lo = INFINITY, hi = -INFINITY;
+  for (int64_t k = 0; k < n; ++k) {
+    const double* a = v + 3 * idx[k];
+    const double* b = v + 3 * idx[(k + 1) % n];
+    double c[3];
+    cross3(a, b, c);
+    for (int j = 0; j < 3; ++j) N[j] += c[j];
+    double ph = dot3(Q, a);
+    lo = fmin(lo, ph);
+    hi = fmax(hi, ph);
+  }
+  if (N[0] == 0.0 && N[1] == 0.0 && N[2] == 0.0) return 0.0;   /* no area */
+  double s = dot3(Q, N), X[3];
+  cross3(N, Q, X);
+  double x2 = dot3(X, X);
+  if (hi - lo < TAU_FACE || x2 == 0.0) {
+    csum_t acc = {0, 0, 0, 0};
+    for (int64_t k = 1; k + 1 < n; ++k)
+      csum_add(&acc, face_term(Q, v + 3 * idx[0], v + 3 * idx[k], v + 3 * idx[k + 1]));
+    return csum_get(&acc);
+  }
+  csum_t acc = {0, 0, 0, 0};
+  for (int64_t l = 0; l < n; ++l) {
+    const double* a = v + 3 * idx[l];
+    const double* b = v + 3 * idx[(l + 1) % n];
+    double dl[3], t[3], m[3];
+    for (int c = 0; c < 3; ++c) { dl[c] = b[c] - a[c]; m[c] = 0.5 * (a[c] + b[c]); }
+    cross3(dl, N, t);
+    csum_add(&acc, dot3(Q, t) * sinc(0.5 * dot3(Q, dl)) * cexp(I * dot3(Q, m)));
+  }
+  return -s / x2 * csum_get(&acc);
+}
+
+static int check_poly_faces(const int32_t* idx, const int64_t* off, int64_t n_faces, int64_t n_verts) {
+  if (off[0] != 0) return 8;
+  for (int64_t m = 0; m < n_faces; ++m)
+    if (off[m + 1] - off[m] < 3) return 8;
+  for (int64_t i = 0; i < off[n_faces]; ++i)
+    if (idx[i] < 0 || idx[i] >= n_verts) return 2;
+  return 0;
+}
+
+/* FT_V of the closed surface of planar polygon faces at each of the n_q points q[n_q][3]. */
+int orc_ft3d_poly(const double* verts, int64_t n_verts, const int32_t* idx, const int64_t* off, int64_t n_faces,
+                  const double* q, int64_t n_q, double* out, int n_threads) {
+  init_tables();
+  int e = check_poly_faces(idx, off, n_faces, n_verts);
+  if (e) return e;
+  double rmax = rmax3d(verts, n_verts);
+  /* Q = 0: the volume, as the signed tetrahedra (origin, p_0, p_k, p_{k+1}) of the fans */
+  double vs = 0.0, vc = 0.0;
+  for (int64_t m = 0; m < n_faces; ++m)
+    for (int64_t k = off[m] + 1; k + 1 < off[m + 1]; ++k) {
+      double bxd[3];
+      cross3(verts + 3 * idx[k], verts + 3 * idx[k + 1], bxd);
+      nsum(&vs, &vc, dot3(verts + 3 * idx[off[m]], bxd) / 6.0);
+    }
+  const double vol = vs + vc;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
+  for (int64_t iq = 0; iq < n_q; ++iq) {
+    const double* Q = q + 3 * iq;
+    double q2 = dot3(Q, Q);
+    double complex F;
+    if (q2 == 0.0) {
+      F = vol;
+    } else if (sqrt(q2) * rmax < TAU_Q) {
+      /* |Q| -> 0: the signed tetrahedra of the fans with the simplex series, as for triangles */
+      csum_t acc = {0, 0, 0, 0};
+      for (int64_t m = 0; m < n_faces; ++m)
+        for (int64_t k = off[m] + 1; k + 1 < off[m + 1]; ++k) {
+          const double *a = verts + 3 * idx[off[m]], *b = verts + 3 * idx[k], *d = verts + 3 * idx[k + 1];
+          double bxd[3];
+          cross3(b, d, bxd);
+          double x[3] = {dot3(Q, a), dot3(Q, b), dot3(Q, d)};
+          csum_add(&acc, dot3(a, bxd) * simplex_series(x, 3, 3));
+        }
+      F = csum_get(&acc);
+    } else {
+      csum_t acc = {0, 0, 0, 0};
+      for (int64_t m = 0; m < n_faces; ++m)
+        csum_add(&acc, poly_face_term(Q, verts, idx + off[m], off[m + 1] - off[m]));
+      F = csum_get(&acc) / q2;
+    }
+    out[2 * iq] = creal(F); out[2 * iq + 1] = cimag(F);
   }
   return 0;
 }

@@ -181,6 +181,40 @@ def box_mesh(a: float, b: float, c: float):
 
 
 # ----------------------------------------------------------------------------
+# 3D closed surfaces of planar polygon faces, CSR: verts [V, 3] float32,
+# face_idx [sum of face sizes] int32, face_off [F + 1] int64; each face
+# counter-clockwise seen from outside.
+# ----------------------------------------------------------------------------
+
+def box_quads(a: float, b: float, c: float):
+    """Rectangular prism [0,a] x [0,b] x [0,c] as 6 outward quadrilaterals."""
+    v = np.array([[0, 0, 0], [a, 0, 0], [a, b, 0], [0, b, 0],
+                  [0, 0, c], [a, 0, c], [a, b, c], [0, b, c]], dtype=np.float32)
+    idx = np.array([4, 5, 6, 7,       # top, normal +z
+                    0, 3, 2, 1,       # bottom, normal -z
+                    0, 1, 5, 4,       # y = 0
+                    3, 7, 6, 2,       # y = b
+                    0, 4, 7, 3,       # x = 0
+                    1, 2, 6, 5],      # x = a
+                   dtype=np.int32)
+    return v, idx, np.arange(0, 25, 4, dtype=np.int64)
+
+
+def extruded_polygon(poly, h: float, z0: float = 0.0):
+    """The prism over a counter-clockwise simple polygon poly [n, 2] between z0 and z0 + h:
+    two n-gon caps and n side quadrilaterals (planar faces, caps possibly non-convex)."""
+    poly = np.asarray(poly, dtype=np.float64)
+    n = poly.shape[0]
+    v = np.concatenate([np.column_stack([poly, np.full(n, z0)]),
+                        np.column_stack([poly, np.full(n, z0 + h)])]).astype(np.float32)
+    k = np.arange(n)
+    sides = np.stack([k, (k + 1) % n, n + (k + 1) % n, n + k], axis=1).reshape(-1)
+    idx = np.concatenate([n + k, k[::-1], sides]).astype(np.int32)      # top, bottom, sides
+    off = np.concatenate([[0, n, 2 * n], 2 * n + 4 * np.arange(1, n + 1)]).astype(np.int64)
+    return v, idx, off
+
+
+# ----------------------------------------------------------------------------
 # Q samples (float64 at the boundary).
 # ----------------------------------------------------------------------------
 
