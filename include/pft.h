@@ -167,6 +167,29 @@ int pft3d_mesh(const float* verts, int64_t n_verts, const int32_t* faces, int64_
                void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
 
 /*
+ * 3D: FT_V(Q) of a closed surface of planar polygon faces of any size (Sec. 3:
+ * Eq. 14 is stated for polygon faces and their edges).
+ *  face_idx  [n_idx] int32, 0-based vertex indices of all faces, concatenated;
+ *            each face counter-clockwise seen from outside, planar, at least 3
+ *            vertices; non-convex faces are allowed.
+ *  face_off  [n_faces + 1] int64 on the device: face m is
+ *            face_idx[face_off[m] .. face_off[m+1]-1]; face_off[0] = 0 and
+ *            face_off[n_faces] = n_idx.  Malformed offsets set PFT_ERR_OFFSETS.
+ *  The device splits every face into n - 2 triangles by recursive halving (the
+ *  chain p_i .. p_j becomes the triangle (p_i, p_m, p_j), m = (i + j)/2, and
+ *  the chains p_i .. p_m and p_m .. p_j, from p_0 .. p_{n-1}), which tile a
+ *  planar polygon with signed areas, so the result is the same integral, and
+ *  whose interior diagonals stay short (their terms cancel only up to
+ *  rounding); then it runs the pft3d_mesh path on the n_idx - 2 n_faces
+ *  triangles (same options).  n_idx >= 3 n_faces is required.
+ */
+size_t pft3d_polymesh_workspace_size(int64_t n_verts, int64_t n_idx, int64_t n_faces, int64_t n_q,
+                                     const pft_options* opts);
+int pft3d_polymesh(const float* verts, int64_t n_verts, const int32_t* face_idx, int64_t n_idx,
+                   const int64_t* face_off, int64_t n_faces, const double* q, int64_t n_q, double* out,
+                   void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
+
+/*
  * Backward passes: adjoints of pft2d_polygons / pft3d_mesh with respect to the
  * vertices (the paper has no gradients; they differentiate its sums, Eq. 6 and
  * Eq. 14, term by term).

@@ -19,7 +19,8 @@ from ._capi import (PFT_FP32_COMPENSATED, PFT_FP64, BatchedPlan, Options, PFTErr
                     status_string)
 
 __all__ = [
-    "pft2d_polygons", "pft2d_batched_prepare", "pft2d_polygons_batched", "BatchedPrepared", "pft3d_mesh", "pft2d_polygons_backward",
+    "pft2d_polygons", "pft2d_batched_prepare", "pft2d_polygons_batched", "BatchedPrepared", "pft3d_mesh",
+    "pft3d_polymesh", "pft2d_polygons_backward",
     "pft3d_mesh_backward", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft3d", "make_options", "Options",
     "PFTError",
     "launch_count", "version",
@@ -193,6 +194,32 @@ def pft3d_mesh(verts, faces, q, *, options=None, out=None, ws=None, stream=None,
                          ws.numel(), ctypes.byref(o), st), "pft3d_mesh")
     if check_status:
         check(lib.pft_status(ws.data_ptr(), st), "pft3d_mesh (device status)")
+    return out
+
+
+def pft3d_polymesh(verts, face_idx, face_off, q, *, options=None, out=None, ws=None, stream=None,
+                   check_status=False):
+    """FT_V(Q) of a closed surface of planar polygon faces in CSR form: face m is
+    face_idx[face_off[m]:face_off[m+1]] (int32 indices, int64 offsets, counter-clockwise seen
+    from outside).  Returns float64 [n_q, 2]."""
+    torch = _torch()
+    v = _dev(verts, torch.float32, "verts", 3)
+    idx = _dev(face_idx, torch.int32, "face_idx").reshape(-1)
+    off = _dev(face_off, torch.int64, "face_off").reshape(-1)
+    qq = _dev(q, torch.float64, "q", 3)
+    o = make_options(options)
+    lib = load()
+    nv, ni, nf, nq = v.shape[0], idx.shape[0], max(off.shape[0] - 1, 0), qq.shape[0]
+    nb = lib.pft3d_polymesh_workspace_size(nv, ni, nf, nq, ctypes.byref(o))
+    if nb == 0:
+        raise PFTError(1, "pft3d_polymesh (each face needs at least 3 vertices)")
+    ws = _ws(nb, v.device, ws)
+    out = torch.empty(nq, 2, dtype=torch.float64, device=v.device) if out is None else out
+    st = _stream(stream, v.device)
+    check(lib.pft3d_polymesh(v.data_ptr(), nv, idx.data_ptr(), ni, off.data_ptr(), nf, qq.data_ptr(), nq,
+                             out.data_ptr(), ws.data_ptr(), ws.numel(), ctypes.byref(o), st), "pft3d_polymesh")
+    if check_status:
+        check(lib.pft_status(ws.data_ptr(), st), "pft3d_polymesh (device status)")
     return out
 
 

@@ -202,6 +202,54 @@ int pft3d_mesh(const float* verts, int64_t n_verts, const int32_t* faces, int64_
   return PFT_OK;
 }
 
+size_t pft3d_polymesh_workspace_size(int64_t n_verts, int64_t n_idx, int64_t n_faces, int64_t n_q,
+                                     const pft_options* opts) {
+  Opts o;
+  if (n_verts < 0 || n_idx < 0 || n_faces < 0 || n_q < 0 || n_idx < 3 * n_faces || resolve(opts, 3, o) != PFT_OK)
+    return 0;
+  const int64_t n_tris = n_idx - 2 * n_faces;
+  return layout_fwd(3, o, n_tris, n_tris, n_q).total + align_up(sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(n_tris, 1));
+}
+
+int pft3d_polymesh(const float* verts, int64_t n_verts, const int32_t* face_idx, int64_t n_idx,
+                   const int64_t* face_off, int64_t n_faces, const double* q, int64_t n_q, double* out,
+                   void* ws, size_t ws_bytes, const pft_options* opts, void* stream) {
+  g_last_launches = 0;
+  Opts o;
+  if (int e = resolve(opts, 3, o)) return e;
+  if (n_verts < 0 || n_idx < 0 || n_faces < 0 || n_q < 0 || n_idx < 3 * n_faces) return PFT_ERR_INVALID_ARG;
+  if (n_q > 0 && (q == nullptr || out == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (n_faces > 0 && (face_idx == nullptr || face_off == nullptr || verts == nullptr || n_verts == 0))
+    return PFT_ERR_INVALID_ARG;
+  if (n_q > INT32_MAX || n_verts > INT32_MAX) return PFT_ERR_UNSUPPORTED;
+  const int64_t n_tris = n_idx - 2 * n_faces;
+  const FwdLayout y = layout_fwd(3, o, n_tris, n_tris, n_q);
+  const size_t tri_off = y.total;
+  if (bad_ws(ws, ws_bytes, tri_off + align_up(sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(n_tris, 1))))
+    return PFT_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader* h = at<WsHeader>(ws, 0);
+  PFT_LAUNCH(launch_init_header(h, st));
+  if (n_q == 0) return PFT_OK;
+  if (n_faces == 0) {
+    if (cudaMemsetAsync(out, 0, sizeof(double) * 2 * (size_t)n_q, st) != cudaSuccess) return PFT_ERR_CUDA;
+    return PFT_OK;
+  }
+  int32_t* tris = at<int32_t>(ws, tri_off);
+  double* mp = at<double>(ws, y.mparts);
+  PFT_LAUNCH(launch_fan3d(face_idx, n_idx, face_off, n_faces, tris, n_tris, h, st));
+  PFT_LAUNCH(launch_bbox(verts, n_verts, 3, h, st));
+  PFT_LAUNCH(launch_prep3d(verts, n_verts, tris, n_tris, h, at<void>(ws, y.items), o.fp64, mp, y.nblk, st));
+  if (mark(o.ev_start, st) != cudaSuccess) return PFT_ERR_CUDA;
+  PFT_LAUNCH(launch_fwd(3, o.fp64, y.L, at<void>(ws, y.items), n_tris, q, n_q, o.tau, at<double2>(ws, y.partial),
+                        &h->status, st));
+  if (mark(o.ev_stop, st) != cudaSuccess) return PFT_ERR_CUDA;
+  PFT_LAUNCH(launch_finalize(3, q, n_q, at<double2>(ws, y.partial), y.L.k_splits, o.fp64, h, mp, y.nblk,
+                             at<int32_t>(ws, y.small), out, st));
+  PFT_LAUNCH(launch_smallq3d(verts, n_verts, tris, n_tris, q, o.fp64, h, at<int32_t>(ws, y.small), out, st));
+  return PFT_OK;
+}
+
 int pft_status(const void* ws, void* stream) {
   if (ws == nullptr) return PFT_ERR_INVALID_ARG;
   uint32_t word = 0;

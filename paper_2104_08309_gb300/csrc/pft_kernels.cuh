@@ -55,6 +55,8 @@ cudaError_t launch_prep3d(const float* v, int64_t nv, const int32_t* f, int64_t 
 cudaError_t launch_fwd(int dim, bool fp64, const FwdLaunch& L, const void* items, int64_t n_items,
                        const double* q, int64_t n_q, float tau, double2* partial, uint32_t* status,
                        cudaStream_t st);
+cudaError_t launch_fan3d(const int32_t* idx, int64_t n_idx, const int64_t* off, int64_t n_faces, int32_t* tris,
+                         int64_t n_tris, WsHeader* h, cudaStream_t st);
 cudaError_t launch_finalize(int dim, const double* q, int64_t n_q, const double2* partial, int k_splits,
                             bool fp64, WsHeader* h, const double* measure_partials, int n_measure,
                             int32_t* small_list, double* out, cudaStream_t st);

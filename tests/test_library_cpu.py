@@ -65,6 +65,8 @@ def test_workspace_sizes(lib):
     assert lib.pft3d_workspace_size(10242, 20480, 262144, ctypes.byref(o64)) > s3   # 96-byte records
     assert lib.pft2d_workspace_size(64, 1, 16384, None) >= 256 + 64 * 16 + 16384 * 16
     assert lib.pft3d_workspace_size(-1, 3, 3, None) == 0
+    assert lib.pft3d_polymesh_workspace_size(8, 24, 6, 100, ctypes.byref(o)) >= s3 * 0 + 256 + 12 * 48
+    assert lib.pft3d_polymesh_workspace_size(8, 17, 6, 100, ctypes.byref(o)) == 0     # < 3 indices per face
     bad = _capi.Options(face_series_tau=6.5)
     assert lib.pft3d_workspace_size(3, 1, 1, ctypes.byref(bad)) == 0
 
