@@ -70,7 +70,7 @@ def parse():
     p.add_argument("--block-threads", type=int, default=128)
     p.add_argument("--tau", type=float, default=0.0, help="face_series_tau (0 = library default)")
     p.add_argument("--no-extra", action="store_true", help="skip the secondary paths (batched 2D, adjoint)")
-    p.add_argument("--only", choices=["batched", "adjoint"], default=None,
+    p.add_argument("--only", choices=["batched", "adjoint", "polymesh"], default=None,
                    help="run one secondary path alone and print its result (for profiler captures)")
     return p.parse_args()
 
@@ -355,6 +355,71 @@ def bench_fp64(pft, vd, fd, qd, out_main, lib, dev, n_sample=4096, seed=5):
             "fp32_vs_fp64_max_abs_over_volume": dev32}
 
 
+def halving_triangles(idx, off):
+    """The library's split of planar polygon faces into triangles (recursive halving, pre-order),
+    on the host: only for the branch-mix sample of the roofline."""
+    tris = []
+    for m in range(off.size - 1):
+        f = idx[off[m]:off[m + 1]]
+        stack = [(0, f.size - 1)]
+        while stack:
+            i, j = stack.pop()
+            if j - i < 2:
+                continue
+            k = (i + j) // 2
+            tris.append((f[i], f[k], f[j]))
+            stack += [(k, j), (i, k)]
+    return np.array(tris, dtype=np.int32)
+
+
+def bench_polymesh(dev, warmup, steps):
+    """Secondary path: a prism over a 65,536-vertex non-convex star (two 65,536-gon caps and
+    65,536 side quadrilaterals = 262,140 triangles) on a 64^3 grid through pft3d_polymesh; also
+    its largest deviation from the 2D path times the extrusion factor (e^{iQz h} - 1)/(iQz)."""
+    import torch
+    import paper_2104_08309_gb300 as pft
+    from paper_2104_08309_gb300 import synth
+    star = synth.star_polygon(65536, seed=11).astype(np.float32)
+    h = 0.75
+    v, idx, off = synth.extruded_polygon(star, h)
+    q = synth.q_grid_3d(64, 30.0)
+    vd, idd, od, qd = (torch.from_numpy(a).to(dev) for a in (v, idx, off, q))
+    out = torch.empty(q.shape[0], 2, dtype=torch.float64, device=dev)
+    for _ in range(max(3, warmup)):
+        pft.pft3d_polymesh(vd, idd, od, qd, out=out)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        pft.pft3d_polymesh(vd, idd, od, qd, out=out)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = float(np.mean(ts))
+    launches = int(pft.launch_count())
+    n_tris = int(idx.size - 2 * (off.size - 1))
+    pairs = float(n_tris) * float(q.shape[0])
+    got = out.cpu().numpy()
+    got = got[:, 0] + 1j * got[:, 1]
+    f2 = pft.pft2d_polygons(torch.from_numpy(star).to(dev), torch.from_numpy(np.ascontiguousarray(q[:, :2])).to(dev))
+    f2 = f2.cpu().numpy()
+    x = 0.5 * q[:, 2] * h
+    ref = (f2[:, 0] + 1j * f2[:, 1]) * h * np.sinc(x / np.pi) * np.exp(1j * x)
+    vol = abs(got[int(np.flatnonzero(np.all(q == 0, axis=1))[0])])
+    pk, _ = peaks()
+    mix = branch_mix(v, halving_triangles(idx, off), q, tau=6.0, r=4, nt=128)
+    _, _, ach, peak = roofline(pairs, ms / 1e3, mix, torch.cuda.get_device_properties(dev).multi_processor_count,
+                               float(pk.get("sm_max_mhz", 2070.0)))
+    return {"value": pairs / (ms / 1e3) / 1e9, "unit": UNIT + " (Q, triangle)", "ms_per_call": ms,
+            "faces": int(off.size - 1), "triangles": n_tris, "q_points": int(q.shape[0]), "pairs_per_call": pairs,
+            "launches_per_call": launches, "roofline_frac": ach / peak, "branch_fractions": mix,
+            "vs_2d_path_times_extrusion_max_abs_over_volume": float(np.max(np.abs(got - ref)) / vol),
+            "l2": "flushed between calls"}
+
+
 def bench_adjoint(dev, warmup, steps):
     """Secondary path: vertex gradient of sum_Q (|F|^2 - I)^2 for 16 icospheres (81,920 triangles) on
     a 32^3 grid; a step is one forward plus one adjoint call (the loss weights in between on torch)."""
@@ -436,7 +501,7 @@ def main():
         torch.cuda.set_device(dev)
         from paper_2104_08309_gb300 import build as pbuild
         pbuild.build()
-        fn = bench_batched if args.only == "batched" else bench_adjoint
+        fn = {"batched": bench_batched, "adjoint": bench_adjoint, "polymesh": bench_polymesh}[args.only]
         print(json.dumps({"path": args.only, **fn(dev, args.warmup, args.steps)}))
         return 0
     import torch
@@ -615,7 +680,9 @@ def main():
         if not args.no_extra and world == 1:
             line["other_paths"] = {"batched2d_4096stars_q64x64": bench_batched(dev, args.warmup, args.steps),
                                    "adjoint3d_union16icospheres4_q32cubed": bench_adjoint(dev, args.warmup,
-                                                                                          args.steps)}
+                                                                                          args.steps),
+                                   "polymesh3d_star65536prism_q64cubed": bench_polymesh(dev, args.warmup,
+                                                                                        args.steps)}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
