@@ -213,6 +213,16 @@ int pft3d_mesh_backward(const float* verts, int64_t n_verts, const int32_t* face
                         const double* q, int64_t n_q, const double* grad_out, float* grad_verts,
                         void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
 
+/* Adjoint of pft3d_polymesh (same faces, same split into triangles): grad_verts
+ * [n_verts][3] float32 from grad_out as for pft3d_mesh_backward.  The workspace
+ * must also hold the triangle list (see the size function). */
+size_t pft3d_polymesh_backward_workspace_size(int64_t n_verts, int64_t n_idx, int64_t n_faces, int64_t n_q,
+                                              const pft_options* opts);
+int pft3d_polymesh_backward(const float* verts, int64_t n_verts, const int32_t* face_idx, int64_t n_idx,
+                            const int64_t* face_off, int64_t n_faces, const double* q, int64_t n_q,
+                            const double* grad_out, float* grad_verts, void* ws, size_t ws_bytes,
+                            const pft_options* opts, void* stream);
+
 /* Kernel launches enqueued by the most recent backward call on this host thread. */
 int pft_backward_last_launch_count(void);
 

@@ -20,7 +20,7 @@ from ._capi import (PFT_FP32_COMPENSATED, PFT_FP64, BatchedPlan, Options, PFTErr
 
 __all__ = [
     "pft2d_polygons", "pft2d_batched_prepare", "pft2d_polygons_batched", "BatchedPrepared", "pft3d_mesh",
-    "pft3d_polymesh", "pft2d_polygons_backward",
+    "pft3d_polymesh", "pft3d_polymesh_backward", "ft3d_poly", "pft2d_polygons_backward",
     "pft3d_mesh_backward", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft3d", "make_options", "Options",
     "PFTError",
     "launch_count", "version",
@@ -294,6 +294,32 @@ def pft3d_mesh_backward(verts, faces, q, grad_out, *, options=None, out=None, ws
     return out
 
 
+def pft3d_polymesh_backward(verts, face_idx, face_off, q, grad_out, *, options=None, out=None, ws=None,
+                            stream=None, check_status=False):
+    """dL/dverts [n_v, 3] float32 for pft3d_polymesh, from grad_out [n_q, 2] = (dL/dRe F, dL/dIm F)."""
+    torch = _torch()
+    v = _dev(verts, torch.float32, "verts", 3)
+    idx = _dev(face_idx, torch.int32, "face_idx").reshape(-1)
+    off = _dev(face_off, torch.int64, "face_off").reshape(-1)
+    qq = _dev(q, torch.float64, "q", 3)
+    g = _dev(grad_out, torch.float64, "grad_out", 2)
+    o = make_options(options)
+    lib = load()
+    nv, ni, nf, nq = v.shape[0], idx.shape[0], max(off.shape[0] - 1, 0), qq.shape[0]
+    nb = lib.pft3d_polymesh_backward_workspace_size(nv, ni, nf, nq, ctypes.byref(o))
+    if nb == 0:
+        raise PFTError(1, "pft3d_polymesh_backward (each face needs at least 3 vertices)")
+    ws = _ws(nb, v.device, ws)
+    out = torch.empty(nv, 3, dtype=torch.float32, device=v.device) if out is None else out
+    st = _stream(stream, v.device)
+    check(lib.pft3d_polymesh_backward(v.data_ptr(), nv, idx.data_ptr(), ni, off.data_ptr(), nf, qq.data_ptr(), nq,
+                                      g.data_ptr(), out.data_ptr(), ws.data_ptr(), ws.numel(), ctypes.byref(o), st),
+          "pft3d_polymesh_backward")
+    if check_status:
+        check(lib.pft_status(ws.data_ptr(), st), "pft3d_polymesh_backward (device status)")
+    return out
+
+
 def pft_status(ws, stream=None) -> int:
     """Device-detected status of the last call on this workspace (synchronises the stream)."""
     return int(load().pft_status(ws.data_ptr(), _stream(stream, ws.device)))
@@ -341,7 +367,20 @@ def _autograd():
             gv = pft3d_mesh_backward(verts.detach(), faces, q, g.contiguous(), options=ctx.options)
             return gv, None, None, None
 
-    return _FT2D, _FT3D
+    class _FT3DPoly(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, verts, face_idx, face_off, q, options):
+            ctx.save_for_backward(verts, face_idx, face_off, q)
+            ctx.options = options
+            return pft3d_polymesh(verts.detach(), face_idx, face_off, q, options=options)
+
+        @staticmethod
+        def backward(ctx, g):
+            verts, face_idx, face_off, q = ctx.saved_tensors
+            gv = pft3d_polymesh_backward(verts.detach(), face_idx, face_off, q, g.contiguous(), options=ctx.options)
+            return gv, None, None, None, None
+
+    return _FT2D, _FT3D, _FT3DPoly
 
 
 _FNS = None
@@ -363,3 +402,12 @@ def ft3d(verts, faces, q, options=None):
     torch = _torch()
     _FNS = _FNS or _autograd()
     return torch.view_as_complex(_FNS[1].apply(verts, faces, q, options))
+
+
+def ft3d_poly(verts, face_idx, face_off, q, options=None):
+    """Differentiable FT_V(Q) of a planar-polygon-face surface as complex128 [n_q]; grad w.r.t. verts
+    via the adjoint kernel."""
+    global _FNS
+    torch = _torch()
+    _FNS = _FNS or _autograd()
+    return torch.view_as_complex(_FNS[2].apply(verts, face_idx, face_off, q, options))

@@ -744,6 +744,57 @@ int check_opts(const pft_options* o, Thr& th) {
 
 using namespace pft;
 
+namespace pft {
+namespace {
+
+// The 3D adjoint after argument checks and the header reset: records, Q weights, the pair
+// kernel, corner adjoints, the vertex -> corner CSR and the fixed-order gather.
+int mesh3d_backward_body(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces,
+                         const double* q, int64_t n_q, const double* grad_out, float* grad_verts, void* ws,
+                         const BwdLayout& y, const Thr& th, WsHeader* h, cudaStream_t st) {
+  if (launch_bbox(verts, n_verts, 3, h, st) != cudaSuccess) return PFT_ERR_CUDA;
+  if (launch_prep3d(verts, n_verts, faces, n_faces, h, at<void>(ws, y.items), false, at<double>(ws, y.mparts),
+                    y.nblk, st) != cudaSuccess)
+    return PFT_ERR_CUDA;
+  g_bwd_launches += 2;
+  k_bq<3><<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, h, 1.0, at<QRec>(ws, y.qrec), at<int32_t>(ws, y.small));
+  PFT_BWD_LAUNCH();
+  dim3 grid(blocks(n_faces, kBwdNT), (unsigned)y.ks);
+  k_bwd<3, 12><<<grid, kBwdNT, 0, st>>>(at<void>(ws, y.items), n_faces, at<QRec>(ws, y.qrec), n_q, y.per_split, th,
+                                        at<double>(ws, y.partial), &h->status);
+  PFT_BWD_LAUNCH();
+  k_bcorner3d<<<blocks(n_faces, kAux), kAux, 0, st>>>(verts, n_verts, faces, n_faces, at<double>(ws, y.partial),
+                                                      y.ks, h, at<int32_t>(ws, y.small), q, grad_out,
+                                                      at<double>(ws, y.corner));
+  PFT_BWD_LAUNCH();
+  int32_t* deg = at<int32_t>(ws, y.deg);
+  int32_t* cursor = at<int32_t>(ws, y.cursor);
+  int64_t* start = at<int64_t>(ws, y.start);
+  int64_t* btot = at<int64_t>(ws, y.btot);
+  k_zero_i32<<<blocks(n_verts, kAux), kAux, 0, st>>>(deg, n_verts);
+  PFT_BWD_LAUNCH();
+  k_zero_i32<<<blocks(n_verts, kAux), kAux, 0, st>>>(cursor, n_verts);
+  PFT_BWD_LAUNCH();
+  k_deg<<<blocks(3 * n_faces, kAux), kAux, 0, st>>>(faces, n_faces, n_verts, deg);
+  PFT_BWD_LAUNCH();
+  const unsigned nb = blocks(n_verts, kAux);
+  k_scan_block<<<nb, kAux, 0, st>>>(deg, n_verts, start, btot);
+  PFT_BWD_LAUNCH();
+  k_scan_totals<<<1, 32, 0, st>>>(btot, nb);
+  PFT_BWD_LAUNCH();
+  k_scan_add<<<nb, kAux, 0, st>>>(start, n_verts, btot);
+  PFT_BWD_LAUNCH();
+  k_fill<<<blocks(3 * n_faces, kAux), kAux, 0, st>>>(faces, n_faces, n_verts, start, cursor, at<int32_t>(ws, y.list));
+  PFT_BWD_LAUNCH();
+  k_gather3d<<<blocks(n_verts, kAux), kAux, 0, st>>>(n_verts, start, deg, at<int32_t>(ws, y.list),
+                                                     at<double>(ws, y.corner), grad_verts);
+  PFT_BWD_LAUNCH();
+  return PFT_OK;
+}
+
+}  // namespace
+}  // namespace pft
+
 extern "C" {
 
 size_t pft2d_backward_workspace_size(int64_t n_verts, int64_t n_loops, int64_t n_q, const pft_options* opts) {
@@ -819,44 +870,48 @@ int pft3d_mesh_backward(const float* verts, int64_t n_verts, const int32_t* face
     return cudaMemsetAsync(grad_verts, 0, sizeof(float) * 3 * (size_t)n_verts, st) == cudaSuccess ? PFT_OK
                                                                                                   : PFT_ERR_CUDA;
   }
-  if (launch_bbox(verts, n_verts, 3, h, st) != cudaSuccess) return PFT_ERR_CUDA;
-  if (launch_prep3d(verts, n_verts, faces, n_faces, h, at<void>(ws, y.items), false, at<double>(ws, y.mparts),
-                    y.nblk, st) != cudaSuccess)
-    return PFT_ERR_CUDA;
-  g_bwd_launches += 2;
-  k_bq<3><<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, h, 1.0, at<QRec>(ws, y.qrec), at<int32_t>(ws, y.small));
-  PFT_BWD_LAUNCH();
-  dim3 grid(blocks(n_faces, kBwdNT), (unsigned)y.ks);
-  k_bwd<3, 12><<<grid, kBwdNT, 0, st>>>(at<void>(ws, y.items), n_faces, at<QRec>(ws, y.qrec), n_q, y.per_split, th,
-                                        at<double>(ws, y.partial), &h->status);
-  PFT_BWD_LAUNCH();
-  k_bcorner3d<<<blocks(n_faces, kAux), kAux, 0, st>>>(verts, n_verts, faces, n_faces, at<double>(ws, y.partial),
-                                                      y.ks, h, at<int32_t>(ws, y.small), q, grad_out,
-                                                      at<double>(ws, y.corner));
-  PFT_BWD_LAUNCH();
-  int32_t* deg = at<int32_t>(ws, y.deg);
-  int32_t* cursor = at<int32_t>(ws, y.cursor);
-  int64_t* start = at<int64_t>(ws, y.start);
-  int64_t* btot = at<int64_t>(ws, y.btot);
-  k_zero_i32<<<blocks(n_verts, kAux), kAux, 0, st>>>(deg, n_verts);
-  PFT_BWD_LAUNCH();
-  k_zero_i32<<<blocks(n_verts, kAux), kAux, 0, st>>>(cursor, n_verts);
-  PFT_BWD_LAUNCH();
-  k_deg<<<blocks(3 * n_faces, kAux), kAux, 0, st>>>(faces, n_faces, n_verts, deg);
-  PFT_BWD_LAUNCH();
-  const unsigned nb = blocks(n_verts, kAux);
-  k_scan_block<<<nb, kAux, 0, st>>>(deg, n_verts, start, btot);
-  PFT_BWD_LAUNCH();
-  k_scan_totals<<<1, 32, 0, st>>>(btot, nb);
-  PFT_BWD_LAUNCH();
-  k_scan_add<<<nb, kAux, 0, st>>>(start, n_verts, btot);
-  PFT_BWD_LAUNCH();
-  k_fill<<<blocks(3 * n_faces, kAux), kAux, 0, st>>>(faces, n_faces, n_verts, start, cursor, at<int32_t>(ws, y.list));
-  PFT_BWD_LAUNCH();
-  k_gather3d<<<blocks(n_verts, kAux), kAux, 0, st>>>(n_verts, start, deg, at<int32_t>(ws, y.list),
-                                                     at<double>(ws, y.corner), grad_verts);
-  PFT_BWD_LAUNCH();
-  return PFT_OK;
+  return mesh3d_backward_body(verts, n_verts, faces, n_faces, q, n_q, grad_out, grad_verts, ws, y, th, h, st);
+}
+
+size_t pft3d_polymesh_backward_workspace_size(int64_t n_verts, int64_t n_idx, int64_t n_faces, int64_t n_q,
+                                              const pft_options* opts) {
+  Thr th;
+  if (n_verts < 0 || n_idx < 0 || n_faces < 0 || n_q < 0 || n_idx < 3 * n_faces || check_opts(opts, th) != PFT_OK)
+    return 0;
+  const int64_t nt = n_idx - 2 * n_faces;
+  const size_t tri_bytes = (sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(nt, 1) + 255) / 256 * 256;
+  return bwd_layout(3, n_verts, nt, nt, n_q).total + tri_bytes;
+}
+
+int pft3d_polymesh_backward(const float* verts, int64_t n_verts, const int32_t* face_idx, int64_t n_idx,
+                            const int64_t* face_off, int64_t n_faces, const double* q, int64_t n_q,
+                            const double* grad_out, float* grad_verts, void* ws, size_t ws_bytes,
+                            const pft_options* opts, void* stream) {
+  g_bwd_launches = 0;
+  Thr th;
+  if (int e = check_opts(opts, th)) return e;
+  if (n_verts < 0 || n_idx < 0 || n_faces < 0 || n_q < 0 || n_idx < 3 * n_faces) return PFT_ERR_INVALID_ARG;
+  if (n_verts > 0 && (verts == nullptr || grad_verts == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (n_faces > 0 && (face_idx == nullptr || face_off == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (n_q > 0 && (q == nullptr || grad_out == nullptr)) return PFT_ERR_INVALID_ARG;
+  const int64_t n_tris = n_idx - 2 * n_faces;
+  if (n_q > INT32_MAX || n_verts > INT32_MAX || 3 * n_tris > INT32_MAX) return PFT_ERR_UNSUPPORTED;
+  const BwdLayout y = bwd_layout(3, n_verts, n_tris, n_tris, n_q);
+  const size_t need = pft3d_polymesh_backward_workspace_size(n_verts, n_idx, n_faces, n_q, opts);
+  if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < need) return PFT_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader* h = at<WsHeader>(ws, 0);
+  if (launch_init_header(h, st) != cudaSuccess) return PFT_ERR_CUDA;
+  ++g_bwd_launches;
+  if (n_verts == 0) return PFT_OK;
+  if (n_faces == 0 || n_q == 0) {
+    return cudaMemsetAsync(grad_verts, 0, sizeof(float) * 3 * (size_t)n_verts, st) == cudaSuccess ? PFT_OK
+                                                                                                  : PFT_ERR_CUDA;
+  }
+  int32_t* tris = at<int32_t>(ws, y.total);
+  if (launch_fan3d(face_idx, n_idx, face_off, n_faces, tris, n_tris, h, st) != cudaSuccess) return PFT_ERR_CUDA;
+  ++g_bwd_launches;
+  return mesh3d_backward_body(verts, n_verts, tris, n_tris, q, n_q, grad_out, grad_verts, ws, y, th, h, st);
 }
 
 int pft_backward_last_launch_count(void) { return g_bwd_launches; }

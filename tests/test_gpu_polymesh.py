@@ -133,3 +133,30 @@ def test_large_star_prism_extrusion_identity(torch_dev):
     sel = rng.choice(q.shape[0], 256, replace=False)
     ref = oracle.ft3d_poly(v, idx, off, q[sel])
     assert np.max(np.abs(got[sel] - ref)) / vol < TOL["fp32"]
+
+
+def test_polymesh_backward(torch_dev, rng):
+    """Vertex gradients of the polygon-face path: against the oracle's shape-derivative gradient of
+    the same triangle split (1e-4 of max|grad|), bitwise against pft3d_mesh_backward on those
+    triangles, and through the autograd wrapper."""
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    v, idx, off = synth.extruded_polygon(synth.star_polygon(120, seed=5).astype(np.float32), 1.25, z0=-0.5)
+    q = np.concatenate([[[0, 0, 0], [0, 0, 2.0], [1e-4, 0, 2e-4]], rng.uniform(-20, 20, (1500, 3))])
+    g = rng.normal(size=q.shape[0]) + 1j * rng.normal(size=q.shape[0])
+    gd = torch.from_numpy(np.ascontiguousarray(np.stack([g.real, g.imag], axis=1))).to(dev)
+    vd, idd, od, qd = (torch.from_numpy(a).to(dev) for a in (v, idx, off, q))
+    got = pft.pft3d_polymesh_backward(vd, idd, od, qd, gd, check_status=True).cpu().numpy()
+    tris = _halving(idx, off)
+    ref = oracle.grad3d(v, tris, q, g)
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-4
+    same = pft.pft3d_mesh_backward(vd, torch.from_numpy(tris).to(dev), qd, gd, check_status=True).cpu().numpy()
+    assert np.array_equal(got, same)
+    # autograd: L = sum |F|^2 w  ->  g = 2 w F
+    vt = vd.clone().requires_grad_(True)
+    w = torch.rand(q.shape[0], dtype=torch.float64, device=dev)
+    F = pft.ft3d_poly(vt, idd, od, qd)
+    (w * F.abs() ** 2).sum().backward()
+    Fn = F.detach().cpu().numpy()
+    ref2 = oracle.grad3d(v, tris, q, 2.0 * w.cpu().numpy() * Fn)
+    assert np.max(np.abs(vt.grad.cpu().numpy() - ref2)) / np.max(np.abs(ref2)) < 1e-4
