@@ -151,7 +151,32 @@ int pft2d_polygons_batched(const float* verts, int64_t n_verts, const int64_t* p
                            const double* q, const int64_t* q_off, int64_t n_q, double* out,
                            void* ws, size_t ws_bytes, const pft_batched_plan* plan, void* stream);
 
-/* Kernel launches enqueued by the most recent pft2d_polygons_batched on this host thread. */
+/*
+ * Batched 3D: one FT_V per closed triangle mesh, for many meshes of uneven size,
+ * in one persistent launch (the same design as the batched 2D calls above).
+ *  verts     [n_verts][3] float32, shared by all meshes.
+ *  faces     [n_faces][3] int32 indices into verts, each triangle counter-
+ *            clockwise seen from outside its mesh.
+ *  mesh_off  [n_meshes + 1] int64 (CSR over faces): mesh i is faces
+ *            mesh_off[i] .. mesh_off[i+1]-1.  The host copy given to
+ *            pft3d_batched_prepare and the device copy given to
+ *            pft3d_meshes_batched must hold the same values.
+ *  q, q_off, out   as for pft2d_polygons_batched, with 3 coordinates per Q.
+ * Options as for pft3d_mesh (face_series_tau included); launch shapes: FP32
+ * 2 or 4 Q points per thread with 128 threads (default 4), FP64 1 with 128.
+ * The plan from pft3d_batched_prepare is only valid for pft3d_meshes_batched.
+ */
+size_t pft3d_batched_workspace_size(int64_t n_faces, const int64_t* mesh_off_host, int64_t n_meshes,
+                                    const int64_t* q_off_host, int64_t n_q, const pft_options* opts);
+int pft3d_batched_prepare(const int64_t* mesh_off_host, int64_t n_meshes, const int64_t* q_off_host, int64_t n_q,
+                          void* ws, size_t ws_bytes, const pft_options* opts, pft_batched_plan* plan,
+                          void* stream);
+int pft3d_meshes_batched(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces,
+                         const int64_t* mesh_off, int64_t n_meshes, const double* q, const int64_t* q_off,
+                         int64_t n_q, double* out, void* ws, size_t ws_bytes, const pft_batched_plan* plan,
+                         void* stream);
+
+/* Kernel launches enqueued by the most recent batched call (2D or 3D) on this host thread. */
 int pft_batched_last_launch_count(void);
 
 /*

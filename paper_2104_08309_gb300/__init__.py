@@ -20,7 +20,8 @@ from ._capi import (PFT_FP32_COMPENSATED, PFT_FP64, BatchedPlan, Options, PFTErr
 
 __all__ = [
     "pft2d_polygons", "pft2d_batched_prepare", "pft2d_polygons_batched", "BatchedPrepared", "pft3d_mesh",
-    "pft3d_polymesh", "pft3d_polymesh_backward", "ft3d_poly", "pft2d_polygons_backward",
+    "pft3d_polymesh", "pft3d_polymesh_backward", "ft3d_poly", "pft3d_batched_prepare", "pft3d_meshes_batched",
+    "pft2d_polygons_backward",
     "pft3d_mesh_backward", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft3d", "make_options", "Options",
     "PFTError",
     "launch_count", "version",
@@ -100,7 +101,8 @@ def pft2d_polygons(verts, q, loop_off=None, *, options=None, out=None, ws=None, 
 
 
 class BatchedPrepared:
-    """Workspace and schedule from pft2d_batched_prepare, reusable while the offsets stay the same."""
+    """Workspace and schedule from pft2d_batched_prepare or pft3d_batched_prepare, reusable while the
+    offsets stay the same."""
 
     def __init__(self, ws, plan, n_verts, n_polys, n_q, shared):
         self.ws, self.plan = ws, plan
@@ -175,6 +177,63 @@ def pft2d_polygons_batched(verts, poly_off, q, q_off=None, *, prepared=None, opt
     if check_status:
         check(lib.pft_status(prepared.ws.data_ptr(), st), "pft2d_polygons_batched (device status)")
     return out.view(npoly, nq, 2) if q_off is None else out
+
+
+def pft3d_batched_prepare(mesh_off, n_q, q_off=None, *, options=None, device=None, stream=None):
+    """Schedule for a batch of closed triangle meshes (CSR over faces), as pft2d_batched_prepare."""
+    torch = _torch()
+    off_h = _host_i64(mesh_off)
+    qo_h = None if q_off is None else _host_i64(q_off)
+    device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    o = make_options(options)
+    lib = load()
+    n_meshes = off_h.numel() - 1
+    n_faces = int(off_h[-1]) if n_meshes > 0 else 0
+    qo_ptr = None if qo_h is None else qo_h.data_ptr()
+    nb = lib.pft3d_batched_workspace_size(n_faces, off_h.data_ptr(), n_meshes, qo_ptr, int(n_q), ctypes.byref(o))
+    if nb == 0:
+        raise ValueError("pft3d_batched_workspace_size rejected the offsets, sizes or options")
+    ws = torch.empty(int(nb), dtype=torch.uint8, device=device)
+    plan = BatchedPlan()
+    check(lib.pft3d_batched_prepare(off_h.data_ptr(), n_meshes, qo_ptr, int(n_q), ws.data_ptr(), ws.numel(),
+                                    ctypes.byref(o), ctypes.byref(plan), _stream(stream, device)),
+          "pft3d_batched_prepare")
+    return BatchedPrepared(ws, plan, n_faces, n_meshes, int(n_q), q_off is None)
+
+
+def pft3d_meshes_batched(verts, faces, mesh_off, q, q_off=None, *, prepared=None, options=None, out=None,
+                         stream=None, check_status=False):
+    """One FT_V per closed triangle mesh in one persistent launch; meshes share verts and the
+    faces of mesh i are faces[mesh_off[i]:mesh_off[i+1]].  Result [n_meshes, n_q, 2] for a shared
+    Q set, else [n_q, 2] with mesh i on q[q_off[i]:q_off[i+1]].  With ``prepared`` (from
+    pft3d_batched_prepare) the call only launches kernels (CUDA-graph capturable)."""
+    torch = _torch()
+    v = _dev(verts, torch.float32, "verts", 3)
+    f = _dev(faces, torch.int32, "faces", 3)
+    qq = _dev(q, torch.float64, "q", 3)
+    if prepared is None:
+        prepared = pft3d_batched_prepare(mesh_off, qq.shape[0], q_off, options=options, device=v.device,
+                                         stream=stream)
+    off_d = mesh_off if (isinstance(mesh_off, torch.Tensor) and mesh_off.is_cuda) else \
+        _host_i64(mesh_off).to(v.device)
+    off_d = _dev(off_d, torch.int64, "mesh_off")
+    qo_d = None
+    if q_off is not None:
+        qo_d = q_off if (isinstance(q_off, torch.Tensor) and q_off.is_cuda) else _host_i64(q_off).to(v.device)
+        qo_d = _dev(qo_d, torch.int64, "q_off")
+    nm, nq = off_d.numel() - 1, qq.shape[0]
+    n_out = nm * nq if q_off is None else nq
+    if out is None:
+        out = torch.empty(n_out, 2, dtype=torch.float64, device=v.device)
+    st = _stream(stream, v.device)
+    lib = load()
+    check(lib.pft3d_meshes_batched(v.data_ptr(), v.shape[0], f.data_ptr(), f.shape[0], off_d.data_ptr(), nm,
+                                   qq.data_ptr(), None if qo_d is None else qo_d.data_ptr(), nq, out.data_ptr(),
+                                   prepared.ws.data_ptr(), prepared.ws.numel(), ctypes.byref(prepared.plan), st),
+          "pft3d_meshes_batched")
+    if check_status:
+        check(lib.pft_status(prepared.ws.data_ptr(), st), "pft3d_meshes_batched (device status)")
+    return out.view(nm, nq, 2) if q_off is None else out
 
 
 def pft3d_mesh(verts, faces, q, *, options=None, out=None, ws=None, stream=None, check_status=False):

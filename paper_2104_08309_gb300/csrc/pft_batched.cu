@@ -1,20 +1,21 @@
-// pft_batched.cu -- many polygons in one persistent launch (batched 2D).
+// pft_batched.cu -- many polygons (2D) or closed triangle meshes (3D) in one
+// persistent launch.
 //
-// Host (pft2d_batched_prepare): every polygon i is cut into work items
-// (polygon, segment chunk, Q tile) whose cost is segments x Q points (+ a fixed
-// per-item charge for the finalize arithmetic).  Items are sorted by cost and
+// Host (pft2d_batched_prepare / pft3d_batched_prepare): every shape i is cut into
+// work items (shape, chunk of segments or faces, Q tile) whose cost is items x Q
+// points (+ a fixed per-item charge for the finalize arithmetic).  Items are sorted by cost and
 // dealt to the G = SMs x resident-blocks persistent blocks, each to the least
 // loaded one so far (longest-processing-time first); every block gets a fixed
 // list, so the schedule, and with it every floating-point sum, is the same on
 // every call.  The plan is copied once into the workspace.
 //
-// Device (pft2d_polygons_batched, kernels only, so a CUDA graph can capture and
-// replay it): k_bprep builds per-polygon centres, areas and segment records;
-// k_batched walks each block's item list with the same bulk-copy ring as the
-// single-shape kernel (the tile stream runs across item boundaries) and
-// finishes single-chunk polygons in place; k_bfinal adds the chunk partials of
-// the rare multi-chunk polygons; k_bsmall redoes points with |Q| R < 0.25 in
-// FP64.
+// Device (pft2d_polygons_batched / pft3d_meshes_batched, kernels only, so a CUDA
+// graph can capture and replay it): k_bprep / k_bprep3 build per-shape centres,
+// areas or volumes and segment or face records; k_batched walks each block's
+// item list with the same bulk-copy ring as the single-shape kernel (the tile
+// stream runs across item boundaries) and finishes single-chunk shapes in
+// place; k_bfinal adds the chunk partials of multi-chunk shapes; k_bsmall /
+// k_bsmall3 redo points with |Q| R < 0.25 in FP64.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -27,26 +28,27 @@ namespace pft {
 namespace {
 
 constexpr uint64_t kPlanMagic = 0x706674626174636bULL;   // "pftbatck"
-constexpr int64_t kChunk = 4096;                          // segments per item at most
+constexpr int64_t kChunk = 4096;                          // segments or faces per item at most
 constexpr int kBThreads = 256;                            // prep / finalize block size
 
 struct BPlanHeader {
   uint64_t magic;
-  int64_t n_polys, n_verts, n_q, n_items, n_cta, n_mc, part_rows, n_out;
-  int32_t r, nt, shared_q, fp64;
-  uint8_t pad[256 - 8 * 9 - 4 * 4];
+  int64_t n_polys, n_verts, n_q, n_items, n_cta, n_mc, part_rows, n_out;   // n_verts: segments or faces
+  int32_t r, nt, shared_q, fp64, dim;
+  float tau;
+  uint8_t pad[256 - 8 * 9 - 4 * 6];
 };
 static_assert(sizeof(BPlanHeader) == 256, "plan header is 256 bytes");
 
-struct PolyPlan {       // per polygon
+struct PolyPlan {       // per shape; "seg" counts segments (2D) or faces (3D)
   int64_t seg_begin, q_begin, out_base, part_base;
   int32_t n_seg, n_q, n_chunks, pad;
 };
 struct BItem {          // per work item
   int32_t poly, chunk, qtile, pad;
 };
-struct PolyInfo {       // written by k_bprep
-  double cx, cy, area;
+struct PolyInfo {       // written by k_bprep / k_bprep3: centre, area or volume, max radius
+  double cx, cy, cz, measure;
   float rmax;
   uint32_t pad;
 };
@@ -57,8 +59,9 @@ struct BLayout {
 
 inline size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
-BLayout layout(int64_t n_polys, int64_t n_verts, int64_t n_items, int64_t n_cta, int64_t n_mc, int64_t part_rows,
-               int64_t n_out, bool fp64) {
+BLayout layout(int dim, int64_t n_polys, int64_t n_verts, int64_t n_items, int64_t n_cta, int64_t n_mc,
+               int64_t part_rows, int64_t n_out, bool fp64) {
+  const size_t rec = dim == 2 ? (fp64 ? sizeof(Seg64) : sizeof(Seg32)) : (fp64 ? sizeof(Face64) : sizeof(Face32));
   BLayout y{};
   size_t o = al(sizeof(WsHeader));
   y.plan_hdr = o; o = al(o + sizeof(BPlanHeader));
@@ -67,7 +70,7 @@ BLayout layout(int64_t n_polys, int64_t n_verts, int64_t n_items, int64_t n_cta,
   y.pplan = o;    o = al(o + sizeof(PolyPlan) * (size_t)std::max<int64_t>(n_polys, 1));
   y.mc = o;       o = al(o + sizeof(int32_t) * (size_t)std::max<int64_t>(n_mc, 1));
   y.info = o;     o = al(o + sizeof(PolyInfo) * (size_t)std::max<int64_t>(n_polys, 1));
-  y.segs = o;     o = al(o + (fp64 ? sizeof(Seg64) : sizeof(Seg32)) * (size_t)std::max<int64_t>(n_verts, 1));
+  y.segs = o;     o = al(o + rec * (size_t)std::max<int64_t>(n_verts, 1));
   y.partial = o;  o = al(o + sizeof(double2) * (size_t)std::max<int64_t>(part_rows, 1));
   y.small = o;    o = al(o + sizeof(uint32_t) * (size_t)std::max<int64_t>(n_out, 1));
   y.total = o;
@@ -88,7 +91,9 @@ struct HostPlan {
   std::vector<int32_t> mc;
 };
 
-int resolve_batched(const pft_options* o, bool& fp64, int& r, int& nt) {
+bool batched_config(int dim, bool fp64, int r, int nt);
+
+int resolve_batched(int dim, const pft_options* o, bool& fp64, int& r, int& nt, float& tau) {
   pft_options z;
   std::memset(&z, 0, sizeof(z));
   const pft_options& p = o ? *o : z;
@@ -96,18 +101,21 @@ int resolve_batched(const pft_options* o, bool& fp64, int& r, int& nt) {
   fp64 = p.precision == PFT_FP64;
   r = p.q_per_thread ? p.q_per_thread : (fp64 ? 1 : 4);
   nt = p.block_threads ? p.block_threads : 128;
-  const bool ok = fp64 ? (r == 1 || r == 2) : (r == 1 || r == 2 || r == 4 || r == 8);
-  if (!ok || (nt != 128 && nt != 256) || p.tile_items != 0 || p.k_splits != 0) return PFT_ERR_UNSUPPORTED;
+  if (!batched_config(dim, fp64, r, nt) || p.tile_items != 0 || p.k_splits != 0) return PFT_ERR_UNSUPPORTED;
+  tau = p.face_series_tau == 0.f ? 6.0f : p.face_series_tau;
+  if (!(tau > 0.f && tau <= 6.0f)) return PFT_ERR_INVALID_ARG;
+  if (fp64) tau = std::min(tau, 3.0f);   // the FP64 series is kept for P < 9/4 (as in the single-shape path)
   return PFT_OK;
 }
 
-int batched_blocks_per_sm(bool fp64, int r, int nt);
+int batched_blocks_per_sm(int dim, bool fp64, int r, int nt);
 
-int build_plan(const int64_t* poly_off, int64_t n_polys, const int64_t* q_off, int64_t n_q,
+int build_plan(int dim, const int64_t* poly_off, int64_t n_polys, const int64_t* q_off, int64_t n_q,
                const pft_options* opts, HostPlan& P) {
   bool fp64;
   int r, nt;
-  if (int e = resolve_batched(opts, fp64, r, nt)) return e;
+  float tau;
+  if (int e = resolve_batched(dim, opts, fp64, r, nt, tau)) return e;
   if (n_polys < 0 || n_q < 0 || (n_polys > 0 && poly_off == nullptr)) return PFT_ERR_INVALID_ARG;
   if (n_polys > 0 && poly_off[0] != 0) return PFT_ERR_OFFSETS;
   for (int64_t i = 0; i < n_polys; ++i)
@@ -124,7 +132,7 @@ int build_plan(const int64_t* poly_off, int64_t n_polys, const int64_t* q_off, i
   const int64_t qt = (int64_t)r * nt;
   int dev = 0, sms = 1;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t G = std::max(1, sms) * (int64_t)batched_blocks_per_sm(fp64, r, nt);
+  const int64_t G = std::max(1, sms) * (int64_t)batched_blocks_per_sm(dim, fp64, r, nt);
 
   P.pplan.resize((size_t)n_polys);
   std::vector<int64_t> cost;
@@ -191,11 +199,13 @@ int build_plan(const int64_t* poly_off, int64_t n_polys, const int64_t* q_off, i
   P.h.nt = nt;
   P.h.shared_q = q_off ? 0 : 1;
   P.h.fp64 = fp64 ? 1 : 0;
+  P.h.dim = dim;
+  P.h.tau = tau;
   return PFT_OK;
 }
 
 BLayout layout_of(const BPlanHeader& h) {
-  return layout(h.n_polys, h.n_verts, h.n_items, h.n_cta, h.n_mc, h.part_rows, h.n_out, h.fp64 != 0);
+  return layout(h.dim, h.n_polys, h.n_verts, h.n_items, h.n_cta, h.n_mc, h.part_rows, h.n_out, h.fp64 != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -274,15 +284,111 @@ __global__ void __launch_bounds__(kBThreads) k_bprep(const float* __restrict__ v
   }
   area = bsum(area, shd);
   rm = bminmax(rm, true, shf);
-  if (threadIdx.x == 0) info[i] = PolyInfo{c[0], c[1], area, rm, 0u};
+  if (threadIdx.x == 0) info[i] = PolyInfo{c[0], c[1], 0.0, area, rm, 0u};
 }
 
-// Shared finish of one output: 2/|Q|^2 * exp(iQ.c) * sum, Q = 0 -> area, small |Q| -> FP64 list.
-__device__ __forceinline__ void finish_out(double qx, double qy, double re, double im, const PolyInfo& pi,
-                                           int64_t row, double* out, uint32_t* small, WsHeader* h) {
-  const double q2 = qx * qx + qy * qy;
+// One block per mesh (3D): plan check, bounding-box centre of the face corners, face records
+// (as k_prep3d: centroid, corners 0 and 1 relative to it, N, all relative to the centre),
+// FP64 volume from the signed tetrahedra, max radius.  Bad indices or coordinates set the
+// status and the face is written empty (it contributes 0).
+template <bool FP64>
+__global__ void __launch_bounds__(kBThreads) k_bprep3(const float* __restrict__ v, int64_t nv,
+                                                      const int32_t* __restrict__ f,
+                                                      const int64_t* __restrict__ mesh_off, const BPlanHeader* ph,
+                                                      const PolyPlan* __restrict__ pplan, PolyInfo* info,
+                                                      void* recs, WsHeader* h) {
+  __shared__ double shd[kBThreads / 32];
+  __shared__ float shf[kBThreads / 32];
+  const int64_t i = blockIdx.x;
+  const PolyPlan pp = pplan[i];
+  const int64_t s0 = mesh_off[i], s1 = mesh_off[i + 1];
+  if (threadIdx.x == 0 && (s0 != pp.seg_begin || s1 - s0 != pp.n_seg || ph->magic != kPlanMagic))
+    set_status(&h->status, ST_OFFSETS);   // offsets differ from the prepared plan
+  const int64_t n = min((int64_t)pp.n_seg, max((int64_t)0, s1 - s0));
+  auto corner_ok = [&](int64_t m) {
+    const int32_t a = f[3 * m], b = f[3 * m + 1], c = f[3 * m + 2];
+    return a >= 0 && b >= 0 && c >= 0 && a < nv && b < nv && c < nv;
+  };
+  float mn[3] = {3.4e38f, 3.4e38f, 3.4e38f}, mx[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+  bool bad_idx = false, bad_val = false;
+  for (int64_t j = threadIdx.x; j < n; j += kBThreads) {
+    const int64_t m = pp.seg_begin + j;
+    if (!corner_ok(m)) { bad_idx = true; continue; }
+    for (int k = 0; k < 3; ++k)
+      for (int d = 0; d < 3; ++d) {
+        const float x = v[3 * (int64_t)f[3 * m + k] + d];
+        if (!isfinite(x)) { bad_val = true; continue; }
+        mn[d] = fminf(mn[d], x);
+        mx[d] = fmaxf(mx[d], x);
+      }
+  }
+  if (bad_idx) set_status(&h->status, ST_INDEX);
+  if (bad_val) set_status(&h->status, ST_NONFINITE);
+  double c[3];
+  for (int d = 0; d < 3; ++d) {
+    const float lo = bminmax(mn[d], false, shf), hi = bminmax(mx[d], true, shf);
+    c[d] = (n > 0 && lo <= hi) ? 0.5 * ((double)lo + (double)hi) : 0.0;
+  }
+  double vol = 0.0;
+  float rm = 0.f;
+  for (int64_t j = threadIdx.x; j < n; j += kBThreads) {
+    const int64_t m = pp.seg_begin + j;
+    double g[3] = {0, 0, 0}, q0[3] = {0, 0, 0}, q1[3] = {0, 0, 0}, N[3] = {0, 0, 0};
+    if (corner_ok(m)) {
+      double P[3][3];
+      bool fin = true;
+      for (int k = 0; k < 3; ++k)
+        for (int d = 0; d < 3; ++d) {
+          P[k][d] = (double)v[3 * (int64_t)f[3 * m + k] + d] - c[d];
+          fin = fin && isfinite(P[k][d]);
+        }
+      if (fin) {
+        for (int d = 0; d < 3; ++d) {
+          g[d] = (P[0][d] + P[1][d] + P[2][d]) / 3.0;
+          q0[d] = P[0][d] - g[d];
+          q1[d] = P[1][d] - g[d];
+        }
+        const double e1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+        const double e2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+        N[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        N[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        N[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        vol += (P[0][0] * (P[1][1] * P[2][2] - P[1][2] * P[2][1]) +
+                P[0][1] * (P[1][2] * P[2][0] - P[1][0] * P[2][2]) +
+                P[0][2] * (P[1][0] * P[2][1] - P[1][1] * P[2][0])) / 6.0;
+        double r2 = 0.0;
+        for (int k = 0; k < 3; ++k) r2 = fmax(r2, P[k][0] * P[k][0] + P[k][1] * P[k][1] + P[k][2] * P[k][2]);
+        rm = fmaxf(rm, __double2float_ru(sqrt(r2)));
+      }
+    }
+    if (FP64) {
+      reinterpret_cast<Face64*>(recs)[m] = Face64{g[0], g[1], g[2], q0[0], q0[1], q0[2], q1[0], q1[1], q1[2],
+                                                  N[0], N[1], N[2]};
+    } else {
+      reinterpret_cast<Face32*>(recs)[m] =
+          Face32{(float)g[0], (float)g[1], (float)g[2], (float)q0[0], (float)q0[1], (float)q0[2],
+                 (float)q1[0], (float)q1[1], (float)q1[2], (float)N[0], (float)N[1], (float)N[2]};
+    }
+  }
+  vol = bsum(vol, shd);
+  rm = bminmax(rm, true, shf);
+  if (threadIdx.x == 0) info[i] = PolyInfo{c[0], c[1], c[2], vol, rm, 0u};
+}
+
+// Shared finish of one output: s/|Q|^2 * exp(iQ.c) * sum (s = 2 in 2D, where the records hold
+// half the cross product; 1 in 3D), Q = 0 -> area or volume, small |Q| -> FP64 list.
+template <int D>
+__device__ __forceinline__ void finish_out(const double* Q, double re, double im, const PolyInfo& pi, int64_t row,
+                                           double* out, uint32_t* small, WsHeader* h) {
+  double q2 = 0.0, ph = 0.0;
+  const double c[3] = {pi.cx, pi.cy, pi.cz};
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    q2 += Q[d] * Q[d];
+    ph += Q[d] * c[d];
+  }
   if (q2 == 0.0) {
-    out[2 * row] = pi.area;
+    out[2 * row] = pi.measure;
     out[2 * row + 1] = 0.0;
     return;
   }
@@ -290,9 +396,9 @@ __device__ __forceinline__ void finish_out(double qx, double qy, double re, doub
     small[atomicAdd(&h->small_q_count, 1u)] = (uint32_t)row;
     return;
   }
-  const double k = 2.0 / q2;
+  const double k = (D == 2 ? 2.0 : 1.0) / q2;
   double sp, cp;
-  sincos(qx * pi.cx + qy * pi.cy, &sp, &cp);
+  sincos(ph, &sp, &cp);
   out[2 * row] = k * (re * cp - im * sp);
   out[2 * row + 1] = k * (re * sp + im * cp);
 }
@@ -300,15 +406,22 @@ __device__ __forceinline__ void finish_out(double qx, double qy, double re, doub
 // Persistent kernel: block b runs items [cta_off[b], cta_off[b+1]) in order.  The
 // segment tiles of consecutive items form one stream through the ring; the last
 // warp to finish a slot issues the tile kStages further on (as in k_fwd).
+// Register budget: as the single-shape kernel, except that the 3D default (4 Q points,
+// 128 threads) keeps 4 blocks per SM here, where the item loop and the in-place finish
+// would otherwise spill at 5.
 template <class Pol, int R, int NT>
-__global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_batched(
+constexpr int kBatchedMinBlocks = (Pol::kDim == 3 && R == 4 && NT == 128) ? 4 : kMinBlocks<Pol, R, NT>;
+
+template <class Pol, int R, int NT>
+__global__ void __launch_bounds__(NT, kBatchedMinBlocks<Pol, R, NT>) k_batched(
     const BPlanHeader* __restrict__ ph, const int32_t* __restrict__ cta_off, const BItem* __restrict__ items,
     const PolyPlan* __restrict__ pplan, const PolyInfo* __restrict__ info, const typename Pol::Item* __restrict__ segs,
     const double* __restrict__ q, double2* __restrict__ partial, double* __restrict__ out, uint32_t* small,
-    WsHeader* h) {
+    WsHeader* h, Thr th) {
   using Item = typename Pol::Item;
   using QT = typename Pol::QT;
   constexpr int TILE = Pol::kTile;
+  constexpr int D = Pol::kDim;
   constexpr int NW = NT / 32;
   __shared__ __align__(128) Item ring[kStages * TILE];
   __shared__ __align__(8) uint64_t full[kStages];
@@ -387,8 +500,8 @@ __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_batched(
       const int64_t iq = q0 + (int64_t)r * NT + threadIdx.x;
       qr[r][0] = qr[r][1] = qr[r][2] = (QT)0;
       if (iq < qend) {
-        qr[r][0] = (QT)q[2 * iq];
-        qr[r][1] = (QT)q[2 * iq + 1];
+#pragma unroll
+        for (int d = 0; d < D; ++d) qr[r][d] = (QT)q[D * iq + d];
       }
     }
     typename Pol::template Acc<R> acc;
@@ -401,7 +514,7 @@ __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_batched(
         ok = false;
         break;
       }
-      Pol::template tile<R>(ring + s * TILE, min(TILE, cnt - t * TILE), qr, acc, Thr{0.f, 0.f, 0, 0});
+      Pol::template tile<R>(ring + s * TILE, min(TILE, cnt - t * TILE), qr, acc, th);
       __syncwarp();
       if ((threadIdx.x & 31) == 0) {
         __threadfence_block();
@@ -426,7 +539,8 @@ __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_batched(
       if (pp.n_chunks > 1) {
         partial[pp.part_base + (int64_t)it.chunk * pp.n_q + local] = f;
       } else {
-        finish_out((double)qr[r][0], (double)qr[r][1], f.x, f.y, pi, pp.out_base + local, out, small, h);
+        const double Qd[3] = {(double)qr[r][0], (double)qr[r][1], (double)qr[r][2]};
+        finish_out<D>(Qd, f.x, f.y, pi, pp.out_base + local, out, small, h);
       }
     }
   }
@@ -439,7 +553,7 @@ __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_batched(
   }
 }
 
-// Multi-chunk polygons: fixed-order FP64 sum of their chunk partials, then the finish.
+// Multi-chunk shapes: fixed-order FP64 sum of their chunk partials, then the finish.
 __global__ void __launch_bounds__(kBThreads) k_bfinal(const BPlanHeader* ph, const int32_t* __restrict__ mc,
                                                       const PolyPlan* __restrict__ pplan,
                                                       const PolyInfo* __restrict__ info, const double* __restrict__ q,
@@ -449,6 +563,7 @@ __global__ void __launch_bounds__(kBThreads) k_bfinal(const BPlanHeader* ph, con
   const PolyPlan pp = pplan[i];
   const PolyInfo pi = info[i];
   const bool fp64 = ph->fp64 != 0;
+  const int D = ph->dim;
   for (int64_t l = threadIdx.x; l < pp.n_q; l += kBThreads) {
     double re = 0.0, im = 0.0;
     for (int c = 0; c < pp.n_chunks; ++c) {
@@ -457,9 +572,10 @@ __global__ void __launch_bounds__(kBThreads) k_bfinal(const BPlanHeader* ph, con
       im += p.y;
     }
     const int64_t iq = pp.q_begin + l;
-    const double qx = fp64 ? q[2 * iq] : (double)(float)q[2 * iq];
-    const double qy = fp64 ? q[2 * iq + 1] : (double)(float)q[2 * iq + 1];
-    finish_out(qx, qy, re, im, pi, pp.out_base + l, out, small, h);
+    double Q[3] = {0.0, 0.0, 0.0};
+    for (int d = 0; d < D; ++d) Q[d] = fp64 ? q[D * iq + d] : (double)(float)q[D * iq + d];
+    if (D == 2) finish_out<2>(Q, re, im, pi, pp.out_base + l, out, small, h);
+    else finish_out<3>(Q, re, im, pi, pp.out_base + l, out, small, h);
   }
 }
 
@@ -523,6 +639,67 @@ __global__ void __launch_bounds__(kBThreads) k_bsmall(const float* __restrict__ 
   }
 }
 
+// FP64 small-|Q| pass in 3D: the mesh's signed tetrahedra (c, p0, p1, p2) with the simplex
+// series (as k_smallq3d for one mesh).
+__global__ void __launch_bounds__(kBThreads) k_bsmall3(const float* __restrict__ v, int64_t nv,
+                                                       const int32_t* __restrict__ f, const BPlanHeader* ph,
+                                                       const PolyPlan* __restrict__ pplan,
+                                                       const PolyInfo* __restrict__ info,
+                                                       const int64_t* __restrict__ q_off,
+                                                       const double* __restrict__ q, const uint32_t* small,
+                                                       double* out, const WsHeader* h) {
+  __shared__ double sh[kBThreads / 32];
+  const uint32_t count = h->small_q_count;
+  const int64_t n_q = ph->n_q, n_polys = ph->n_polys;
+  for (uint32_t e = blockIdx.x; e < count; e += gridDim.x) {
+    const int64_t row = small[e];
+    int64_t i, iq;
+    if (ph->shared_q) {
+      i = row / n_q;
+      iq = row % n_q;
+    } else {
+      int64_t lo = 0, hi = n_polys;   // last mesh whose Q range starts at or before row
+      while (lo + 1 < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (q_off[mid] <= row) lo = mid; else hi = mid;
+      }
+      i = lo;
+      iq = row;
+    }
+    const PolyPlan pp = pplan[i];
+    const PolyInfo pi = info[i];
+    const double c[3] = {pi.cx, pi.cy, pi.cz};
+    double Q[3];
+    for (int d = 0; d < 3; ++d) Q[d] = ph->fp64 ? q[3 * iq + d] : (double)(float)q[3 * iq + d];
+    double re = 0.0, im = 0.0;
+    for (int64_t j = threadIdx.x; j < pp.n_seg; j += kBThreads) {
+      const int64_t m = pp.seg_begin + j;
+      const int32_t id[3] = {f[3 * m], f[3 * m + 1], f[3 * m + 2]};
+      if (id[0] < 0 || id[1] < 0 || id[2] < 0 || id[0] >= nv || id[1] >= nv || id[2] >= nv) continue;
+      double P[3][3], x[3];
+      for (int k = 0; k < 3; ++k) {
+        for (int d = 0; d < 3; ++d) P[k][d] = (double)v[3 * (int64_t)id[k] + d] - c[d];
+        x[k] = Q[0] * P[k][0] + Q[1] * P[k][1] + Q[2] * P[k][2];
+      }
+      const double det = P[0][0] * (P[1][1] * P[2][2] - P[1][2] * P[2][1]) +
+                         P[0][1] * (P[1][2] * P[2][0] - P[1][0] * P[2][2]) +
+                         P[0][2] * (P[1][0] * P[2][1] - P[1][1] * P[2][0]);
+      double sr, si;
+      simplex_series<3, 3, 16>(x, sr, si);
+      re += det * sr;
+      im += det * si;
+    }
+    re = bsum(re, sh);
+    im = bsum(im, sh);
+    if (threadIdx.x == 0) {
+      double sp, cp;
+      sincos(Q[0] * c[0] + Q[1] * c[1] + Q[2] * c[2], &sp, &cp);
+      out[2 * row] = re * cp - im * sp;
+      out[2 * row + 1] = re * sp + im * cp;
+    }
+  }
+}
+
 template <class Pol, int R, int NT>
 int occ_batched() {
   int b = 0;
@@ -533,33 +710,46 @@ int occ_batched() {
 template <class Pol, int R, int NT>
 cudaError_t launch_batched_one(int grid, const BPlanHeader* ph, const int32_t* cta_off, const BItem* items,
                                const PolyPlan* pplan, const PolyInfo* info, const void* segs, const double* q,
-                               double2* partial, double* out, uint32_t* small, WsHeader* h, cudaStream_t st) {
+                               double2* partial, double* out, uint32_t* small, WsHeader* h, Thr th, cudaStream_t st) {
   k_batched<Pol, R, NT><<<grid, NT, 0, st>>>(ph, cta_off, items, pplan, info,
-                                             static_cast<const typename Pol::Item*>(segs), q, partial, out, small, h);
+                                             static_cast<const typename Pol::Item*>(segs), q, partial, out, small, h,
+                                             th);
   return cudaGetLastError();
 }
 
+// Instantiated configurations: (policy, Q points per thread, threads per block).
 #define PFT_BATCHED_CASES(X)                                                                          \
   X(Pol2F32, 1, 128) X(Pol2F32, 2, 128) X(Pol2F32, 4, 128) X(Pol2F32, 8, 128) X(Pol2F32, 1, 256)      \
   X(Pol2F32, 2, 256) X(Pol2F32, 4, 256) X(Pol2F32, 8, 256) X(Pol2F64, 1, 128) X(Pol2F64, 2, 128)      \
-  X(Pol2F64, 1, 256) X(Pol2F64, 2, 256)
+  X(Pol2F64, 1, 256) X(Pol2F64, 2, 256) X(Pol3F32, 2, 128) X(Pol3F32, 4, 128) X(Pol3F64, 1, 128)
 
-int batched_blocks_per_sm(bool fp64, int r, int nt) {
+#define PFT_BATCHED_MATCH(P, RR, NN) \
+  (P::kDim == dim && (sizeof(P::QT) == 8) == fp64 && r == RR && nt == NN)
+
+bool batched_config(int dim, bool fp64, int r, int nt) {
 #define X(P, RR, NN) \
-  if ((sizeof(P::QT) == 8) == fp64 && r == RR && nt == NN) return occ_batched<P, RR, NN>();
+  if (PFT_BATCHED_MATCH(P, RR, NN)) return true;
+  PFT_BATCHED_CASES(X)
+#undef X
+  return false;
+}
+
+int batched_blocks_per_sm(int dim, bool fp64, int r, int nt) {
+#define X(P, RR, NN) \
+  if (PFT_BATCHED_MATCH(P, RR, NN)) return occ_batched<P, RR, NN>();
   PFT_BATCHED_CASES(X)
 #undef X
   return 1;
 }
 
-cudaError_t launch_batched(bool fp64, int r, int nt, int grid, const BPlanHeader* ph, const int32_t* cta_off,
+cudaError_t launch_batched(int dim, bool fp64, int r, int nt, int grid, const BPlanHeader* ph, const int32_t* cta_off,
                            const BItem* items, const PolyPlan* pplan, const PolyInfo* info, const void* segs,
-                           const double* q, double2* partial, double* out, uint32_t* small, WsHeader* h,
+                           const double* q, double2* partial, double* out, uint32_t* small, WsHeader* h, Thr th,
                            cudaStream_t st) {
-#define X(P, RR, NN)                                                                                     \
-  if ((sizeof(P::QT) == 8) == fp64 && r == RR && nt == NN)                                              \
+#define X(P, RR, NN)                                                                                      \
+  if (PFT_BATCHED_MATCH(P, RR, NN))                                                                      \
     return launch_batched_one<P, RR, NN>(grid, ph, cta_off, items, pplan, info, segs, q, partial, out, small, h, \
-                                         st);
+                                         th, st);
   PFT_BATCHED_CASES(X)
 #undef X
   return cudaErrorInvalidConfiguration;
@@ -571,31 +761,25 @@ thread_local int g_batched_launches = 0;
 struct PlanHandle {
   int64_t magic, n_polys, n_verts, n_q, shared_q, fp64, r, nt, grid, n_mc;
   int64_t plan_hdr, cta_off, items, pplan, mc, info, segs, partial, small, total;
+  int64_t dim;
+  double tau;
 };
 static_assert(sizeof(PlanHandle) <= sizeof(pft_batched_plan), "plan handle fits the public struct");
 
-}  // namespace
-}  // namespace pft
-
-using namespace pft;
-
-extern "C" {
-
-size_t pft2d_batched_workspace_size(int64_t n_verts, const int64_t* poly_off_host, int64_t n_polys,
-                                    const int64_t* q_off_host, int64_t n_q, const pft_options* opts) {
+size_t workspace_impl(int dim, int64_t n_items, const int64_t* off_host, int64_t n_shapes, const int64_t* q_off_host,
+                      int64_t n_q, const pft_options* opts) {
   HostPlan P;
-  if (n_verts < 0 || build_plan(poly_off_host, n_polys, q_off_host, n_q, opts, P) != PFT_OK) return 0;
-  if (P.h.n_verts != n_verts) return 0;
+  if (n_items < 0 || build_plan(dim, off_host, n_shapes, q_off_host, n_q, opts, P) != PFT_OK) return 0;
+  if (P.h.n_verts != n_items) return 0;
   return layout_of(P.h).total;
 }
 
-int pft2d_batched_prepare(const int64_t* poly_off_host, int64_t n_polys, const int64_t* q_off_host, int64_t n_q,
-                          void* ws, size_t ws_bytes, const pft_options* opts, pft_batched_plan* plan,
-                          void* stream) {
+int prepare_impl(int dim, const int64_t* off_host, int64_t n_shapes, const int64_t* q_off_host, int64_t n_q,
+                 void* ws, size_t ws_bytes, const pft_options* opts, pft_batched_plan* plan, void* stream) {
   if (plan == nullptr) return PFT_ERR_INVALID_ARG;
   std::memset(plan, 0, sizeof(*plan));
   HostPlan P;
-  if (int e = build_plan(poly_off_host, n_polys, q_off_host, n_q, opts, P)) return e;
+  if (int e = build_plan(dim, off_host, n_shapes, q_off_host, n_q, opts, P)) return e;
   const BLayout y = layout_of(P.h);
   if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < y.total) return PFT_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -611,7 +795,7 @@ int pft2d_batched_prepare(const int64_t* poly_off_host, int64_t n_polys, const i
   if (!ok) return PFT_ERR_CUDA;
   PlanHandle ph{};
   ph.magic = (int64_t)kPlanMagic;
-  ph.n_polys = n_polys;
+  ph.n_polys = n_shapes;
   ph.n_verts = P.h.n_verts;
   ph.n_q = n_q;
   ph.shared_q = P.h.shared_q;
@@ -623,24 +807,84 @@ int pft2d_batched_prepare(const int64_t* poly_off_host, int64_t n_polys, const i
   ph.plan_hdr = (int64_t)y.plan_hdr; ph.cta_off = (int64_t)y.cta_off; ph.items = (int64_t)y.items;
   ph.pplan = (int64_t)y.pplan; ph.mc = (int64_t)y.mc; ph.info = (int64_t)y.info; ph.segs = (int64_t)y.segs;
   ph.partial = (int64_t)y.partial; ph.small = (int64_t)y.small; ph.total = (int64_t)y.total;
+  ph.dim = dim;
+  ph.tau = P.h.tau;
   std::memcpy(plan, &ph, sizeof(ph));
   return PFT_OK;
+}
+
+// Checks shared by both batched calls; on success fills p and the header pointer.
+int check_call(int dim, const pft_batched_plan* plan, int64_t n_items, int64_t n_shapes, int64_t n_q,
+               const int64_t* q_off, const void* verts, const int64_t* off, const double* q, double* out, void* ws,
+               size_t ws_bytes, PlanHandle& p) {
+  if (plan == nullptr) return PFT_ERR_INVALID_ARG;
+  std::memcpy(&p, plan, sizeof(p));
+  if (p.magic != (int64_t)kPlanMagic || p.dim != dim) return PFT_ERR_INVALID_ARG;
+  if (n_items != p.n_verts || n_shapes != p.n_polys || n_q != p.n_q || (q_off == nullptr) != (p.shared_q != 0))
+    return PFT_ERR_INVALID_ARG;   // not the shape the plan was prepared for
+  if (n_shapes > 0 && (off == nullptr || verts == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (n_q > 0 && (q == nullptr || out == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < (size_t)p.total)
+    return PFT_ERR_WORKSPACE;
+  return PFT_OK;
+}
+
+Thr plan_thr(const PlanHandle& p) {
+  const float tau = (float)p.tau, lo = std::min(tau, kTauLo);
+  return Thr{0.25f * tau * tau, 0.25f * lo * lo, tau > 1.f ? 1 : 0, tau > 3.f ? 1 : 0};
+}
+
+// Pair kernel, multi-chunk finish and the small-|Q| pass (the last is dimension-specific).
+int run_rest(const PlanHandle& p, void* ws, const double* q, double* out, WsHeader* h, cudaStream_t st) {
+  const BPlanHeader* phd = at<BPlanHeader>(ws, (size_t)p.plan_hdr);
+  const PolyPlan* pplan = at<PolyPlan>(ws, (size_t)p.pplan);
+  PolyInfo* info = at<PolyInfo>(ws, (size_t)p.info);
+  uint32_t* small = at<uint32_t>(ws, (size_t)p.small);
+  double2* partial = at<double2>(ws, (size_t)p.partial);
+  if (launch_batched((int)p.dim, p.fp64 != 0, (int)p.r, (int)p.nt, (int)p.grid, phd,
+                     at<int32_t>(ws, (size_t)p.cta_off), at<BItem>(ws, (size_t)p.items), pplan, info,
+                     at<void>(ws, (size_t)p.segs), q, partial, out, small, h, plan_thr(p), st) != cudaSuccess)
+    return PFT_ERR_CUDA;
+  ++g_batched_launches;
+  if (p.n_mc > 0) {
+    k_bfinal<<<(unsigned)p.n_mc, kBThreads, 0, st>>>(phd, at<int32_t>(ws, (size_t)p.mc), pplan, info, q, partial,
+                                                      out, small, h);
+    if (cudaGetLastError() != cudaSuccess) return PFT_ERR_CUDA;
+    ++g_batched_launches;
+  }
+  return PFT_OK;
+}
+
+int sm_count() {
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, sms);
+}
+
+}  // namespace
+}  // namespace pft
+
+using namespace pft;
+
+extern "C" {
+
+size_t pft2d_batched_workspace_size(int64_t n_verts, const int64_t* poly_off_host, int64_t n_polys,
+                                    const int64_t* q_off_host, int64_t n_q, const pft_options* opts) {
+  return workspace_impl(2, n_verts, poly_off_host, n_polys, q_off_host, n_q, opts);
+}
+
+int pft2d_batched_prepare(const int64_t* poly_off_host, int64_t n_polys, const int64_t* q_off_host, int64_t n_q,
+                          void* ws, size_t ws_bytes, const pft_options* opts, pft_batched_plan* plan,
+                          void* stream) {
+  return prepare_impl(2, poly_off_host, n_polys, q_off_host, n_q, ws, ws_bytes, opts, plan, stream);
 }
 
 int pft2d_polygons_batched(const float* verts, int64_t n_verts, const int64_t* poly_off, int64_t n_polys,
                            const double* q, const int64_t* q_off, int64_t n_q, double* out, void* ws,
                            size_t ws_bytes, const pft_batched_plan* plan, void* stream) {
   g_batched_launches = 0;
-  if (plan == nullptr) return PFT_ERR_INVALID_ARG;
   PlanHandle p;
-  std::memcpy(&p, plan, sizeof(p));
-  if (p.magic != (int64_t)kPlanMagic) return PFT_ERR_INVALID_ARG;
-  if (n_verts != p.n_verts || n_polys != p.n_polys || n_q != p.n_q || (q_off == nullptr) != (p.shared_q != 0))
-    return PFT_ERR_INVALID_ARG;   // not the shape the plan was prepared for
-  if (n_polys > 0 && (poly_off == nullptr || verts == nullptr)) return PFT_ERR_INVALID_ARG;
-  if (n_q > 0 && (q == nullptr || out == nullptr)) return PFT_ERR_INVALID_ARG;
-  if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < (size_t)p.total)
-    return PFT_ERR_WORKSPACE;
+  if (int e = check_call(2, plan, n_verts, n_polys, n_q, q_off, verts, poly_off, q, out, ws, ws_bytes, p)) return e;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   WsHeader* h = at<WsHeader>(ws, 0);
   if (launch_init_header(h, st) != cudaSuccess) return PFT_ERR_CUDA;
@@ -650,25 +894,57 @@ int pft2d_polygons_batched(const float* verts, int64_t n_verts, const int64_t* p
   const PolyPlan* pplan = at<PolyPlan>(ws, (size_t)p.pplan);
   PolyInfo* info = at<PolyInfo>(ws, (size_t)p.info);
   void* segs = at<void>(ws, (size_t)p.segs);
-  uint32_t* small = at<uint32_t>(ws, (size_t)p.small);
-  double2* partial = at<double2>(ws, (size_t)p.partial);
   if (p.fp64) k_bprep<true><<<(unsigned)n_polys, kBThreads, 0, st>>>(verts, poly_off, phd, pplan, info, segs, h);
   else k_bprep<false><<<(unsigned)n_polys, kBThreads, 0, st>>>(verts, poly_off, phd, pplan, info, segs, h);
   if (cudaGetLastError() != cudaSuccess) return PFT_ERR_CUDA;
   ++g_batched_launches;
-  if (launch_batched(p.fp64 != 0, (int)p.r, (int)p.nt, (int)p.grid, phd, at<int32_t>(ws, (size_t)p.cta_off),
-                     at<BItem>(ws, (size_t)p.items), pplan, info, segs, q, partial, out, small, h, st) != cudaSuccess)
-    return PFT_ERR_CUDA;
+  if (int e = run_rest(p, ws, q, out, h, st)) return e;
+  k_bsmall<<<sm_count(), kBThreads, 0, st>>>(verts, phd, pplan, info, q_off, q, at<uint32_t>(ws, (size_t)p.small),
+                                              out, h);
+  if (cudaGetLastError() != cudaSuccess) return PFT_ERR_CUDA;
   ++g_batched_launches;
-  if (p.n_mc > 0) {
-    k_bfinal<<<(unsigned)p.n_mc, kBThreads, 0, st>>>(phd, at<int32_t>(ws, (size_t)p.mc), pplan, info, q, partial,
-                                                      out, small, h);
-    if (cudaGetLastError() != cudaSuccess) return PFT_ERR_CUDA;
-    ++g_batched_launches;
-  }
-  int dev = 0, sms = 1;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  k_bsmall<<<std::max(1, sms), kBThreads, 0, st>>>(verts, phd, pplan, info, q_off, q, small, out, h);
+  return PFT_OK;
+}
+
+size_t pft3d_batched_workspace_size(int64_t n_faces, const int64_t* mesh_off_host, int64_t n_meshes,
+                                    const int64_t* q_off_host, int64_t n_q, const pft_options* opts) {
+  return workspace_impl(3, n_faces, mesh_off_host, n_meshes, q_off_host, n_q, opts);
+}
+
+int pft3d_batched_prepare(const int64_t* mesh_off_host, int64_t n_meshes, const int64_t* q_off_host, int64_t n_q,
+                          void* ws, size_t ws_bytes, const pft_options* opts, pft_batched_plan* plan,
+                          void* stream) {
+  return prepare_impl(3, mesh_off_host, n_meshes, q_off_host, n_q, ws, ws_bytes, opts, plan, stream);
+}
+
+int pft3d_meshes_batched(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces,
+                         const int64_t* mesh_off, int64_t n_meshes, const double* q, const int64_t* q_off,
+                         int64_t n_q, double* out, void* ws, size_t ws_bytes, const pft_batched_plan* plan,
+                         void* stream) {
+  g_batched_launches = 0;
+  PlanHandle p;
+  if (int e = check_call(3, plan, n_faces, n_meshes, n_q, q_off, verts, mesh_off, q, out, ws, ws_bytes, p)) return e;
+  if (n_verts < 0 || (n_faces > 0 && (faces == nullptr || n_verts == 0))) return PFT_ERR_INVALID_ARG;
+  if (n_verts > INT32_MAX) return PFT_ERR_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader* h = at<WsHeader>(ws, 0);
+  if (launch_init_header(h, st) != cudaSuccess) return PFT_ERR_CUDA;
+  ++g_batched_launches;
+  if (n_meshes == 0 || n_q == 0) return PFT_OK;
+  const BPlanHeader* phd = at<BPlanHeader>(ws, (size_t)p.plan_hdr);
+  const PolyPlan* pplan = at<PolyPlan>(ws, (size_t)p.pplan);
+  PolyInfo* info = at<PolyInfo>(ws, (size_t)p.info);
+  void* recs = at<void>(ws, (size_t)p.segs);
+  if (p.fp64)
+    k_bprep3<true><<<(unsigned)n_meshes, kBThreads, 0, st>>>(verts, n_verts, faces, mesh_off, phd, pplan, info, recs, h);
+  else
+    k_bprep3<false><<<(unsigned)n_meshes, kBThreads, 0, st>>>(verts, n_verts, faces, mesh_off, phd, pplan, info, recs,
+                                                              h);
+  if (cudaGetLastError() != cudaSuccess) return PFT_ERR_CUDA;
+  ++g_batched_launches;
+  if (int e = run_rest(p, ws, q, out, h, st)) return e;
+  k_bsmall3<<<sm_count(), kBThreads, 0, st>>>(verts, n_verts, faces, phd, pplan, info, q_off, q,
+                                              at<uint32_t>(ws, (size_t)p.small), out, h);
   if (cudaGetLastError() != cudaSuccess) return PFT_ERR_CUDA;
   ++g_batched_launches;
   return PFT_OK;

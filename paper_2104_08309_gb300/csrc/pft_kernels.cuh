@@ -36,6 +36,31 @@ static_assert(sizeof(Face32) == 48 && sizeof(Face64) == 96, "face record sizes")
 // boundary sum (which cancels to O(|Q|^2 R^2) of its terms there).
 constexpr double kTauSmallQ = 0.25;
 
+// sum_k i^k h_k(x) / (k + p)! for the n nodes x (FP64), K terms: the integral of exp(i Q.r)
+// over a simplex divided by p! times its volume, from its corner phases x (small-|Q| passes).
+template <int N, int P, int K>
+__device__ __forceinline__ void simplex_series(const double* x, double& re, double& im) {
+  double h[K + 1];
+  h[0] = 1.0;
+#pragma unroll
+  for (int k = 1; k <= K; ++k) h[k] = 0.0;
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+#pragma unroll
+    for (int k = 1; k <= K; ++k) h[k] = fma(x[j], h[k - 1], h[k]);
+  double inv = 1.0;
+#pragma unroll
+  for (int k = 2; k <= P; ++k) inv /= (double)k;   // 1/P!
+  re = 0.0;
+  im = 0.0;
+#pragma unroll
+  for (int k = 0; k <= K; ++k) {
+    const double t = h[k] * inv;
+    switch (k & 3) { case 0: re += t; break; case 1: im += t; break; case 2: re -= t; break; default: im -= t; }
+    inv /= (double)(k + P + 1);
+  }
+}
+
 // Launch description computed on the host.
 struct FwdLaunch {
   int r;              // Q points per thread

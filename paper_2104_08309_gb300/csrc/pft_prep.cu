@@ -284,30 +284,6 @@ __global__ void k_finalize(int dim, const double* __restrict__ q, int64_t n_q, c
   out[2 * i + 1] = re * sp + im * cp;
 }
 
-// sum_k i^k h_k(x) / (k + p)! for the n nodes x (FP64), K terms.
-template <int N, int P, int K>
-__device__ __forceinline__ void simplex_series(const double* x, double& re, double& im) {
-  double h[K + 1];
-  h[0] = 1.0;
-#pragma unroll
-  for (int k = 1; k <= K; ++k) h[k] = 0.0;
-#pragma unroll
-  for (int j = 0; j < N; ++j)
-#pragma unroll
-    for (int k = 1; k <= K; ++k) h[k] = fma(x[j], h[k - 1], h[k]);
-  double inv = 1.0;
-#pragma unroll
-  for (int k = 2; k <= P; ++k) inv /= (double)k;   // 1/P!
-  re = 0.0;
-  im = 0.0;
-#pragma unroll
-  for (int k = 0; k <= K; ++k) {
-    const double t = h[k] * inv;
-    switch (k & 3) { case 0: re += t; break; case 1: im += t; break; case 2: re -= t; break; default: im -= t; }
-    inv /= (double)(k + P + 1);
-  }
-}
-
 constexpr int kSmallThreads = 256;
 
 // Small |Q|: the integral of exp(iQ.(r - c)) over the signed tetrahedra (c, p0, p1, p2)

@@ -162,6 +162,31 @@ def sphere_union(n_spheres: int, level: int, seed: int, rmin: float = 0.2, rmax:
     return np.concatenate(vs).astype(np.float32), np.concatenate(fs).astype(np.int32)
 
 
+def mesh_batch(n_meshes: int, seed: int, levels=(1, 2, 3, 4), rmin: float = 0.2, rmax: float = 0.5,
+               amp: float = 0.05):
+    """Many separate closed meshes for a batched transform: mesh i is an icosphere of a level drawn
+    uniformly from ``levels``, radius U[rmin, rmax], centre U[-1, 1)^3, each vertex moved radially
+    by 1 + amp * U[-1, 1).  Returns verts [V, 3] float32 (all meshes), faces [F, 3] int32 (global
+    indices, mesh after mesh) and mesh_off [n_meshes + 1] int64 (CSR over faces)."""
+    rng = np.random.default_rng(seed)
+    lv = rng.choice(np.asarray(levels), n_meshes)
+    radii = rng.uniform(rmin, rmax, n_meshes)
+    centers = rng.uniform(-1.0, 1.0, size=(n_meshes, 3))
+    cache = {}
+    vs, fs, off, nv = [], [], [0], 0
+    for i in range(n_meshes):
+        if lv[i] not in cache:
+            cache[lv[i]] = _unit_icosphere(int(lv[i]))
+        uv, uf = cache[lv[i]]
+        fac = radii[i] * (1.0 + amp * rng.uniform(-1.0, 1.0, uv.shape[0]))
+        vs.append(uv * fac[:, None] + centers[i])
+        fs.append(uf + nv)
+        nv += uv.shape[0]
+        off.append(off[-1] + uf.shape[0])
+    return (np.concatenate(vs).astype(np.float32), np.concatenate(fs).astype(np.int32),
+            np.asarray(off, dtype=np.int64))
+
+
 def box_mesh(a: float, b: float, c: float):
     """Rectangular prism [0,a] x [0,b] x [0,c] as 12 outward triangles (Sec. 4.2).
 
