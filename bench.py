@@ -70,7 +70,7 @@ def parse():
     p.add_argument("--block-threads", type=int, default=128)
     p.add_argument("--tau", type=float, default=0.0, help="face_series_tau (0 = library default)")
     p.add_argument("--no-extra", action="store_true", help="skip the secondary paths (batched 2D, adjoint)")
-    p.add_argument("--only", choices=["batched", "adjoint", "polymesh"], default=None,
+    p.add_argument("--only", choices=["batched", "adjoint", "polymesh", "batched3d"], default=None,
                    help="run one secondary path alone and print its result (for profiler captures)")
     return p.parse_args()
 
@@ -332,6 +332,54 @@ def bench_batched(dev, warmup, steps):
             "l2": "flushed between steps"}
 
 
+def bench_batched3d(dev, warmup, steps):
+    """Secondary path: 1,024 separate closed meshes (perturbed icospheres of levels 1-4: 80 to 5,120
+    faces, 1.68M faces in all) on a shared 32^3 grid, one prepared schedule replayed from a CUDA
+    graph; each replay is one full batched transform."""
+    import torch
+    import paper_2104_08309_gb300 as pft
+    from paper_2104_08309_gb300 import synth
+    v, f, off = synth.mesh_batch(1024, seed=21)
+    q = synth.q_grid_3d(32, 30.0)
+    vd, fd, qd, offd = (torch.from_numpy(a).to(dev) for a in (v, f, q, off))
+    prep = pft.pft3d_batched_prepare(off, q.shape[0], device=dev)
+    out = torch.empty(off.size - 1, q.shape[0], 2, dtype=torch.float64, device=dev)
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        pft.pft3d_meshes_batched(vd, fd, offd, qd, prepared=prep, out=out)
+    torch.cuda.current_stream(dev).wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        pft.pft3d_meshes_batched(vd, fd, offd, qd, prepared=prep, out=out)
+    launches = pft.load().pft_batched_last_launch_count()
+    for _ in range(max(3, warmup)):
+        g.replay()
+    torch.cuda.synchronize()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = float(np.mean(ts))
+    pairs = float(f.shape[0]) * float(q.shape[0])
+    pk, _ = peaks()
+    mix = branch_mix(v, f, q, tau=6.0, r=4, nt=128)
+    _, _, ach, peak = roofline(pairs, ms / 1e3, mix, torch.cuda.get_device_properties(dev).multi_processor_count,
+                               float(pk.get("sm_max_mhz", 2070.0)))
+    return {"value": pairs / (ms / 1e3) / 1e9, "unit": UNIT + " (Q, triangle)", "ms_per_step": ms,
+            "pairs_per_step": pairs, "meshes": int(off.size - 1), "faces": int(f.shape[0]),
+            "q_points": int(q.shape[0]), "launches_per_step": int(launches), "cuda_graph": True,
+            "device_status": int(pft.pft_status(prep.ws)), "roofline_frac": ach / peak, "branch_fractions": mix,
+            "note": "whole batched call timed (prep, pair kernel, multi-chunk finish, small-|Q| pass)",
+            "l2": "flushed between steps"}
+
+
 def bench_fp64(pft, vd, fd, qd, out_main, lib, dev, n_sample=4096, seed=5):
     """The plain FP64 GPU path on the same mesh, on a seeded 4,096-point Q subsample (FP64 runs at a
     small fraction of the FP32 rate on this part), and the FP32 result's deviation from it there."""
@@ -501,7 +549,8 @@ def main():
         torch.cuda.set_device(dev)
         from paper_2104_08309_gb300 import build as pbuild
         pbuild.build()
-        fn = {"batched": bench_batched, "adjoint": bench_adjoint, "polymesh": bench_polymesh}[args.only]
+        fn = {"batched": bench_batched, "adjoint": bench_adjoint, "polymesh": bench_polymesh,
+              "batched3d": bench_batched3d}[args.only]
         print(json.dumps({"path": args.only, **fn(dev, args.warmup, args.steps)}))
         return 0
     import torch
@@ -682,7 +731,8 @@ def main():
                                    "adjoint3d_union16icospheres4_q32cubed": bench_adjoint(dev, args.warmup,
                                                                                           args.steps),
                                    "polymesh3d_star65536prism_q64cubed": bench_polymesh(dev, args.warmup,
-                                                                                        args.steps)}
+                                                                                        args.steps),
+                                   "batched3d_1024meshes_q32cubed": bench_batched3d(dev, args.warmup, args.steps)}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
