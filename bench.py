@@ -75,6 +75,27 @@ def parse():
     return p.parse_args()
 
 
+def replica_seed(rank):
+    """Seed of the mesh rank `rank` transforms: every rank an independent problem of the same size."""
+    return 5 + rank
+
+
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank timings over all ranks (one all-reduce; identity at N = 1)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(x) for x in values]
+    t = torch.tensor([float(x) for x in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_rate(world, pairs_per_rank, ms):
+    """G pairs/s of the whole job: all ranks' pairs over the slowest rank's time."""
+    return world * pairs_per_rank / (ms / 1e3) / 1e9
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
@@ -92,7 +113,7 @@ WORKLOADS = {
 def workload(rank, name="c5"):
     from paper_2104_08309_gb300 import synth
     _, stride = WORKLOADS[name]
-    v, f = synth.perturbed_icosphere(8, seed=5 + rank, amp=0.05)
+    v, f = synth.perturbed_icosphere(8, seed=replica_seed(rank), amp=0.05)
     q = synth.q_grid_3d(128, 60.0)
     if stride > 1:
         q = np.ascontiguousarray(q.reshape(128, 128, 128, 3)[::stride, ::stride].reshape(-1, 3))
@@ -619,10 +640,7 @@ def main():
     clk = clocks.stop()
     ms_step = float(np.mean([a.elapsed_time(b) for a, b in e_step]))
     ms_main = float(np.mean([a.elapsed_time(b) for a, b in e_main]))
-    if world > 1:
-        t = torch.tensor([ms_step, ms_main], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step, ms_main = t.tolist()
+    ms_step, ms_main = max_over_ranks([ms_step, ms_main], dev)
     status = pft.pft_status(ws)
 
     # end to end: pinned host buffers, H2D of the inputs and D2H of the result inside the timed region
@@ -643,10 +661,7 @@ def main():
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     e2e_t = float(np.mean(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_t = t.item()
+    e2e_t = max_over_ranks([e2e_t], dev)[0]
 
     # variants: the same workload with face_series_tau = 3 (no extra-long series) and 1 (short
     # series only, edge sum wherever the in-face phase spread reaches 1); one warm-up and one
@@ -683,7 +698,7 @@ def main():
             _, _, v_ach, v_peak = roofline(pairs, variant["main_kernel_ms"] / 1e3, vmix, n_sm, clk_max)
             variant["branch_fractions"] = vmix
             variant["roofline_frac"] = v_ach / v_peak
-        value = world * pairs / (ms_step / 1e3) / 1e9
+        value = whole_job_rate(world, pairs, ms_step)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -706,7 +721,7 @@ def main():
                          "branch_fractions": mix},
             "clocks": clk,
             "gpu_launches": launches,
-            "e2e": {"value": world * pairs / (e2e_t / 1e3) / 1e9, "unit": UNIT,
+            "e2e": {"value": whole_job_rate(world, pairs, e2e_t), "unit": UNIT,
                     "h2d_bytes_per_step": int(v.nbytes + f.nbytes + q.nbytes),
                     "d2h_bytes_per_step": int(q.shape[0] * 16)},
         }
