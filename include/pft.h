@@ -1,6 +1,7 @@
 /*
  * pft.h -- C ABI of libpft: direct (non-FFT) Fourier transform of polygonal
- * areas and closed triangulated surfaces on one NVIDIA GB300 (sm_103a).
+ * areas and of closed surfaces of triangles or planar polygons, one shape or
+ * batches of many, with adjoints, on one NVIDIA GB300 (sm_103a).
  *
  * Method: B. B. Maranville, "An implementation of an efficient direct Fourier
  * transform of polygonal areas and volumes", arXiv 2104.08309.
@@ -24,8 +25,9 @@
  *    pairs and are fully overwritten.
  *  - Results are deterministic: no floating-point atomics; every reduction runs
  *    in a fixed order.
- *  - Thread safety: no mutable global state; concurrent calls need separate
- *    workspaces.
+ *  - Thread safety: no mutable global state apart from the fixed scratch of
+ *    pft3d_mesh_noalloc (see there) and per-thread launch counters; concurrent
+ *    calls need separate workspaces.
  */
 #ifndef PFT_H
 #define PFT_H
