@@ -138,3 +138,19 @@ def test_plan_mismatch_and_bad_offsets(torch_dev):
     bad[2] += 3
     pft.pft3d_meshes_batched(vd, fd, torch.from_numpy(bad).to(dev), q, prepared=prep, out=out)
     assert pft.pft_status(prep.ws) == 8
+
+
+def test_empty_mesh_in_batch(torch_dev, rng):
+    """A mesh with no faces between two others: its transform is 0 everywhere, the others unchanged."""
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    v, f, off = synth.mesh_batch(2, seed=8, levels=(2,))
+    off3 = np.array([0, off[1], off[1], off[2]], dtype=np.int64)
+    q = _q_mix(rng, 300, 15.0)
+    got = _c(pft.pft3d_meshes_batched(torch.from_numpy(v).to(dev), torch.from_numpy(f).to(dev), off3,
+                                      torch.from_numpy(q).to(dev), check_status=True))
+    assert np.all(got[1] == 0)
+    for k, i in ((0, 0), (2, 1)):
+        vi, fi = _mesh(v, f, off, i)
+        ref = oracle.ft3d(vi, fi, q)
+        assert np.max(np.abs(got[k] - ref)) / abs(ref[0]) < TOL["fp32"]

@@ -160,3 +160,17 @@ def test_polymesh_backward(torch_dev, rng):
     Fn = F.detach().cpu().numpy()
     ref2 = oracle.grad3d(v, tris, q, 2.0 * w.cpu().numpy() * Fn)
     assert np.max(np.abs(vt.grad.cpu().numpy() - ref2)) / np.max(np.abs(ref2)) < 1e-4
+
+
+def test_polymesh_empty_and_single_face_types(torch_dev, rng):
+    """No faces: zeros.  Triangles given as 3-vertex polygon faces: the triangle path, bitwise."""
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    q = rng.uniform(-10, 10, (200, 3))
+    v = np.zeros((3, 3), np.float32)
+    out = _run(torch_dev, v, np.zeros(0, np.int32), np.zeros(1, np.int64), q)
+    assert np.all(out == 0)
+    vi, fi = synth.icosphere(2)
+    a = _run(torch_dev, vi, fi.reshape(-1), np.arange(0, 3 * fi.shape[0] + 1, 3, dtype=np.int64), q)
+    b = _c(pft.pft3d_mesh(torch.from_numpy(vi).to(dev), torch.from_numpy(fi).to(dev), torch.from_numpy(q).to(dev)))
+    assert np.array_equal(a, b)
