@@ -205,5 +205,32 @@ def grad3d(verts, faces, q, g, vsel=None, threads=None) -> np.ndarray:
     return out
 
 
+def qgrad3d(verts, faces, q, g, threads=None) -> np.ndarray:
+    """dL/dQ [n_q, 3] = Re(conj(g_Q) dF/dQ) for g_Q = dL/dRe F + i dL/dIm F.
+
+    The derivative is taken from its definition, as the limit of difference quotients of ft3d:
+    central differences at steps h and h/2 combined by Richardson extrapolation (error O(h^4)),
+    h = 1e-3 / max|r| (max over the vertices), in FP64.
+    """
+    v, f = _mesh(verts, faces)
+    q = _f64(q, 3)
+    g = np.asarray(g).reshape(-1)
+    h = 1e-3 / max(float(np.max(np.linalg.norm(v, axis=1))), 1e-300)
+    steps = []
+    for j in range(3):
+        for hh in (h, 0.5 * h):
+            e = np.zeros(3)
+            e[j] = hh
+            steps += [q + e, q - e]
+    F = ft3d(v, f, np.concatenate(steps), threads=threads).reshape(len(steps), q.shape[0])
+    out = np.empty((q.shape[0], 3))
+    for j in range(3):
+        d1 = (F[4 * j] - F[4 * j + 1]) / (2 * h)
+        d2 = (F[4 * j + 2] - F[4 * j + 3]) / h
+        dF = (4.0 * d2 - d1) / 3.0
+        out[:, j] = np.real(np.conj(g) * dF)
+    return out
+
+
 def max_threads() -> int:
     return int(_load().orc_max_threads())
