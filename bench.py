@@ -527,10 +527,27 @@ def bench_adjoint(dev, warmup, steps):
     ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     ms_b = float(np.mean([c.elapsed_time(d) for c, d in eb]))
     pairs = float(w.faces.shape[0]) * float(w.q.shape[0])
+    launches_adj = int(pft.load().pft_backward_last_launch_count())
+    # the Q-gradient of the same loss (one call per step, same weights)
+    for _ in range(3):
+        pft.pft3d_mesh_qgrad(vd, fd, qd, g)
+    torch.cuda.synchronize()
+    tq = []
+    for _ in range(steps):
+        flush.zero_()
+        c, d = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c.record()
+        pft.pft3d_mesh_qgrad(vd, fd, qd, g)
+        d.record()
+        d.synchronize()
+        tq.append(c.elapsed_time(d))
+    ms_q = float(np.mean(tq))
     return {"value": pairs / (ms_b / 1e3) / 1e9, "unit": UNIT + " (adjoint call)", "ms_adjoint": ms_b,
+            "qgrad": {"value": pairs / (ms_q / 1e3) / 1e9, "unit": UNIT + " (Q-gradient call)", "ms": ms_q,
+                      "launches": int(pft.load().pft_backward_last_launch_count())},
             "ms_forward_plus_adjoint": ms, "pairs_per_call": pairs, "faces": int(w.faces.shape[0]),
             "q_points": int(w.q.shape[0]), "finite": bool(torch.isfinite(grad).all().item()),
-            "launches_adjoint": int(pft.load().pft_backward_last_launch_count())}
+            "launches_adjoint": launches_adj}
 
 
 KERNEL_SOURCES = ("pft_fwd.cu", "pft_pairs.cuh", "pft_common.cuh", "pft_kernels.cuh", "pft_api.cu")

@@ -250,6 +250,20 @@ int pft3d_polymesh_backward(const float* verts, int64_t n_verts, const int32_t* 
                             const double* grad_out, float* grad_verts, void* ws, size_t ws_bytes,
                             const pft_options* opts, void* stream);
 
+/*
+ * Q-gradient of a loss on FT_V (3D triangles): grad_q[n_q][3] float64 receives
+ * dL/dQ = Re(conj(g_Q) dF(Q)/dQ) for grad_out as above.  Not in the paper; it
+ * is the derivative of the forward sum (Eq. 14 and its series) with respect to
+ * Q: dF/dQ = F (i c - 2Q/|Q|^2) + e^{iQ.c}/|Q|^2 dS/dQ, the last term from the
+ * same reverse pass per (Q, face) pair as the vertex adjoint, accumulated per
+ * Q instead of per face; Q = 0 and small |Q| in FP64 from the derivative of the
+ * tetrahedron series.  Options and errors as for pft3d_mesh_backward.
+ */
+size_t pft3d_qgrad_workspace_size(int64_t n_verts, int64_t n_faces, int64_t n_q, const pft_options* opts);
+int pft3d_mesh_qgrad(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces,
+                     const double* q, int64_t n_q, const double* grad_out, double* grad_q,
+                     void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
+
 /* Kernel launches enqueued by the most recent backward call on this host thread. */
 int pft_backward_last_launch_count(void);
 

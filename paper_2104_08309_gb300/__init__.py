@@ -22,7 +22,7 @@ __all__ = [
     "pft2d_polygons", "pft2d_batched_prepare", "pft2d_polygons_batched", "BatchedPrepared", "pft3d_mesh",
     "pft3d_polymesh", "pft3d_polymesh_backward", "ft3d_poly", "pft3d_batched_prepare", "pft3d_meshes_batched",
     "pft2d_polygons_backward",
-    "pft3d_mesh_backward", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft3d", "make_options", "Options",
+    "pft3d_mesh_backward", "pft3d_mesh_qgrad", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft3d", "make_options", "Options",
     "PFTError",
     "launch_count", "version",
 ]
@@ -379,6 +379,28 @@ def pft3d_polymesh_backward(verts, face_idx, face_off, q, grad_out, *, options=N
     return out
 
 
+def pft3d_mesh_qgrad(verts, faces, q, grad_out, *, options=None, out=None, ws=None, stream=None,
+                     check_status=False):
+    """dL/dQ [n_q, 3] float64 from grad_out [n_q, 2] = (dL/dRe F, dL/dIm F) (3D triangles)."""
+    torch = _torch()
+    v = _dev(verts, torch.float32, "verts", 3)
+    f = _dev(faces, torch.int32, "faces", 3)
+    qq = _dev(q, torch.float64, "q", 3)
+    g = _dev(grad_out, torch.float64, "grad_out", 2)
+    o = make_options(options)
+    lib = load()
+    nv, nf, nq = v.shape[0], f.shape[0], qq.shape[0]
+    nb = lib.pft3d_qgrad_workspace_size(nv, nf, nq, ctypes.byref(o))
+    ws = _ws(nb, v.device, ws)
+    out = torch.empty(nq, 3, dtype=torch.float64, device=v.device) if out is None else out
+    st = _stream(stream, v.device)
+    check(lib.pft3d_mesh_qgrad(v.data_ptr(), nv, f.data_ptr(), nf, qq.data_ptr(), nq, g.data_ptr(), out.data_ptr(),
+                               ws.data_ptr(), ws.numel(), ctypes.byref(o), st), "pft3d_mesh_qgrad")
+    if check_status:
+        check(lib.pft_status(ws.data_ptr(), st), "pft3d_mesh_qgrad (device status)")
+    return out
+
+
 def pft_status(ws, stream=None) -> int:
     """Device-detected status of the last call on this workspace (synchronises the stream)."""
     return int(load().pft_status(ws.data_ptr(), _stream(stream, ws.device)))
@@ -418,13 +440,17 @@ def _autograd():
         def forward(ctx, verts, faces, q, options):
             ctx.save_for_backward(verts, faces, q)
             ctx.options = options
-            return pft3d_mesh(verts.detach(), faces, q, options=options)
+            return pft3d_mesh(verts.detach(), faces, q.detach(), options=options)
 
         @staticmethod
         def backward(ctx, g):
             verts, faces, q = ctx.saved_tensors
-            gv = pft3d_mesh_backward(verts.detach(), faces, q, g.contiguous(), options=ctx.options)
-            return gv, None, None, None
+            g = g.contiguous()
+            gv = pft3d_mesh_backward(verts.detach(), faces, q, g, options=ctx.options) \
+                if ctx.needs_input_grad[0] else None
+            gq = pft3d_mesh_qgrad(verts.detach(), faces, q.detach(), g, options=ctx.options) \
+                if ctx.needs_input_grad[2] else None
+            return gv, None, gq, None
 
     class _FT3DPoly(torch.autograd.Function):
         @staticmethod
@@ -456,7 +482,7 @@ def ft2d(verts, q, loop_off=None, options=None):
 
 
 def ft3d(verts, faces, q, options=None):
-    """Differentiable FT_V(Q) as complex128 [n_q]; grad w.r.t. verts via the adjoint kernel."""
+    """Differentiable FT_V(Q) as complex128 [n_q]; gradients w.r.t. verts and q via the adjoint kernels."""
     global _FNS
     torch = _torch()
     _FNS = _FNS or _autograd()

@@ -148,10 +148,14 @@ __device__ __forceinline__ void seg_adj(const QRec& Q, const float4 s, float (&a
 }
 
 // 3D: face term J = -s exp(i mu) Z (series or edge branch, chosen as in the
-// forward kernel, warp-uniform over the lanes' faces) with weight gt; adds the
-// adjoints of the 12 record fields g, q0, q1, N (same order as Face32).
-__device__ __forceinline__ void face_adj(const QRec& Q, const float4 A, const float4 B, const float4 C, Thr th,
-                                         float (&a)[12]) {
+// forward kernel, warp-uniform over the lanes) with weight gt, differentiated in
+// reverse mode.  The adjoints of the projections mu = Q.g, a0 = Q.q0, a1 = Q.q1,
+// s = Q.N (and, in the edge branch, of X = N x Q and b_k = q_k.X) go to `out`,
+// which turns them into record adjoints (RecAdj) or Q adjoints (QAdj): the
+// projections are bilinear in Q and the record, so the two are mirror images.
+template <class Out>
+__device__ __forceinline__ void face_adj_t(const QRec& Q, const float4 A, const float4 B, const float4 C, Thr th,
+                                           Out& out) {
   const float qx = Q.qx, qy = Q.qy, qz = Q.qz;
   float mu, a0, a1, s, P;
   face_common(qx, qy, qz, A, B, C, mu, a0, a1, s, P);
@@ -305,6 +309,7 @@ __device__ __forceinline__ void face_adj(const QRec& Q, const float4 A, const fl
   }
   // J = -s W, W = exp(i mu) Z
   const float Wr = fmaf(cm, zr, -sm * zi), Wi = fmaf(cm, zi, sm * zr);
+  out.value(-s * Wr, -s * Wi);
   const float sb = -fmaf(Q.gr, Wr, Q.gi * Wi);       // dc/ds
   const float mub = s * fmaf(Q.gr, Wi, -Q.gi * Wr);  // dc/dmu
   const float ghr = -s * fmaf(Q.gr, cm, Q.gi * sm);  // ghat = -s gt exp(-i mu): dc = Re(conj(ghat) dZ)
@@ -337,6 +342,19 @@ __device__ __forceinline__ void face_adj(const QRec& Q, const float4 A, const fl
     const float Xbx = fmaf(b0b, A.w, fmaf(b1b, B.z, 2.0f * x2b * Xx));
     const float Xby = fmaf(b0b, B.x, fmaf(b1b, B.w, 2.0f * x2b * Xy));
     const float Xbz = fmaf(b0b, B.y, fmaf(b1b, C.x, 2.0f * x2b * Xz));
+    out.edge(b0b, b1b, Xx, Xy, Xz, Xbx, Xby, Xbz);
+  }
+  out.common(mub, a0b, a1b, sb);
+}
+
+// Record adjoints of one (Q, face) pair: g += mub Q, q0 += a0b Q (+ b0b X), q1 += a1b Q (+ b1b X),
+// N += sb Q (+ Q x Xbar), in the order of Face32's 12 fields.
+struct RecAdj {
+  float (&a)[12];
+  float qx, qy, qz;
+  __device__ __forceinline__ void value(float, float) {}
+  __device__ __forceinline__ void edge(float b0b, float b1b, float Xx, float Xy, float Xz, float Xbx, float Xby,
+                                       float Xbz) {
     a[3] = fmaf(b0b, Xx, a[3]);
     a[4] = fmaf(b0b, Xy, a[4]);
     a[5] = fmaf(b0b, Xz, a[5]);
@@ -347,19 +365,48 @@ __device__ __forceinline__ void face_adj(const QRec& Q, const float4 A, const fl
     a[10] = fmaf(qz, Xbx, fmaf(-qx, Xbz, a[10]));
     a[11] = fmaf(qx, Xby, fmaf(-qy, Xbx, a[11]));
   }
-  a[0] = fmaf(mub, qx, a[0]);
-  a[1] = fmaf(mub, qy, a[1]);
-  a[2] = fmaf(mub, qz, a[2]);
-  a[3] = fmaf(a0b, qx, a[3]);
-  a[4] = fmaf(a0b, qy, a[4]);
-  a[5] = fmaf(a0b, qz, a[5]);
-  a[6] = fmaf(a1b, qx, a[6]);
-  a[7] = fmaf(a1b, qy, a[7]);
-  a[8] = fmaf(a1b, qz, a[8]);
-  a[9] = fmaf(sb, qx, a[9]);
-  a[10] = fmaf(sb, qy, a[10]);
-  a[11] = fmaf(sb, qz, a[11]);
+  __device__ __forceinline__ void common(float mub, float a0b, float a1b, float sb) {
+    a[0] = fmaf(mub, qx, a[0]);
+    a[1] = fmaf(mub, qy, a[1]);
+    a[2] = fmaf(mub, qz, a[2]);
+    a[3] = fmaf(a0b, qx, a[3]);
+    a[4] = fmaf(a0b, qy, a[4]);
+    a[5] = fmaf(a0b, qz, a[5]);
+    a[6] = fmaf(a1b, qx, a[6]);
+    a[7] = fmaf(a1b, qy, a[7]);
+    a[8] = fmaf(a1b, qz, a[8]);
+    a[9] = fmaf(sb, qx, a[9]);
+    a[10] = fmaf(sb, qy, a[10]);
+    a[11] = fmaf(sb, qz, a[11]);
+  }
+};
+
+__device__ __forceinline__ void face_adj(const QRec& Q, const float4 A, const float4 B, const float4 C, Thr th,
+                                         float (&a)[12]) {
+  RecAdj o{a, Q.qx, Q.qy, Q.qz};
+  face_adj_t(Q, A, B, C, th, o);
 }
+
+// Q adjoint of one (Q, face) pair, and the pair's term J itself (tile sums):
+// Qbar += mub g + a0b q0 + a1b q1 + sb N (+ Xbar x N, since X = N x Q).
+struct QAdj {
+  float jr, ji, bx, by, bz;
+  float4 A, B, C;   // the face record: g = A.xyz, q0 = (A.w, B.x, B.y), q1 = (B.z, B.w, C.x), N = C.yzw
+  __device__ __forceinline__ void value(float Jr, float Ji) {
+    jr += Jr;
+    ji += Ji;
+  }
+  __device__ __forceinline__ void edge(float, float, float, float, float, float Xbx, float Xby, float Xbz) {
+    bx = fmaf(Xby, C.w, fmaf(-Xbz, C.z, bx));
+    by = fmaf(Xbz, C.y, fmaf(-Xbx, C.w, by));
+    bz = fmaf(Xbx, C.z, fmaf(-Xby, C.y, bz));
+  }
+  __device__ __forceinline__ void common(float mub, float a0b, float a1b, float sb) {
+    bx = fmaf(mub, A.x, fmaf(a0b, A.w, fmaf(a1b, B.z, fmaf(sb, C.y, bx))));
+    by = fmaf(mub, A.y, fmaf(a0b, B.x, fmaf(a1b, B.w, fmaf(sb, C.z, by))));
+    bz = fmaf(mub, A.z, fmaf(a0b, B.y, fmaf(a1b, C.x, fmaf(sb, C.w, bz))));
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Kernels.
@@ -391,6 +438,159 @@ __global__ void k_bq(const double* __restrict__ q, const double* __restrict__ g,
 }
 
 // Thread <-> item (segment or face); Q chunk blockIdx.y; FP64 partial per (chunk, item, field).
+// ---------------------------------------------------------------------------
+// Q-gradient (3D): dL/dQ = Re(conj(g) dF/dQ) per Q.  With F = e^{iQ.c} S / |Q|^2,
+// S = sum over faces of J,
+//   dF/dQ = F (i c - 2 Q/|Q|^2) + e^{iQ.c}/|Q|^2 dS/dQ,
+// and the second part is sum over faces of Re(conj(gt) dJ/dQ) with the same
+// weight gt = g e^{-iQ.c}/|Q|^2 as the vertex adjoint (k_bq).  k_qgrad: thread
+// <-> Q (one per thread), face records streamed through the bulk-copy ring, the
+// reverse pass of each pair into Q (QAdj), S accumulated alongside; FP64
+// partials per face chunk (blockIdx.y).
+// ---------------------------------------------------------------------------
+constexpr int kFTile = 64;          // face records per shared-memory tile of k_qgrad
+constexpr int kQG = 5;              // partial fields per (chunk, Q): S.re, S.im, Qbar.xyz
+
+__global__ void __launch_bounds__(kBwdNT) k_qgrad(const Face32* __restrict__ faces, int64_t n_faces,
+                                                  int64_t per_split, const QRec* __restrict__ rec, int64_t n_q,
+                                                  Thr th, double* __restrict__ partial, uint32_t* status) {
+  __shared__ __align__(128) Face32 slots[kStages * kFTile];
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ int done[kStages];
+  __shared__ int issued;
+  const int64_t i = blockIdx.x * (int64_t)kBwdNT + threadIdx.x;
+  QRec Q{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // lanes past the end: Q = 0, weight 0
+  if (i < n_q) Q = rec[i];
+  const int64_t f0 = (int64_t)blockIdx.y * per_split;
+  const int64_t nf = max((int64_t)0, min(per_split, n_faces - f0));
+  Ring<Face32, kFTile, kBwdNT> ring{slots, full, done, &issued, faces + f0, nf, (int)((nf + kFTile - 1) / kFTile)};
+  ring.start();
+  CAcc acc[kQG];
+#pragma unroll
+  for (int f = 0; f < kQG; ++f) acc[f].init();
+  bool ok = true;
+  for (int t = 0; t < ring.ntiles; ++t) {
+    if (!ring.wait(t)) { ok = false; break; }
+    const Face32* tf = ring.tile(t);
+    const int cnt = ring.count(t);
+    QAdj o{0.f, 0.f, 0.f, 0.f, 0.f, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+           make_float4(0.f, 0.f, 0.f, 0.f)};
+#pragma unroll 1
+    for (int j = 0; j < cnt; ++j) {
+      const float4* p = reinterpret_cast<const float4*>(tf + j);
+      o.A = p[0];
+      o.B = p[1];
+      o.C = p[2];
+      face_adj_t(Q, o.A, o.B, o.C, th, o);
+    }
+    acc[0].add(o.jr);
+    acc[1].add(o.ji);
+    acc[2].add(o.bx);
+    acc[3].add(o.by);
+    acc[4].add(o.bz);
+    ring.release(t);
+  }
+  if (!ok) set_status(status, ST_TIMEOUT);
+  ring.finish();
+  if (!ok || i >= n_q) return;
+  double* dst = partial + ((int64_t)blockIdx.y * n_q + i) * kQG;
+#pragma unroll
+  for (int f = 0; f < kQG; ++f) dst[f] = (double)acc[f].hi + (double)acc[f].lo;
+}
+
+// Per Q (not in the small-|Q| list): fixed-order FP64 sum of the chunk partials, F, and
+// dL/dQ = Re(conj(g) F (i c - 2Q/|Q|^2)) + Qbar.
+__global__ void k_qfinal(const double* __restrict__ q, const double* __restrict__ g, int64_t n_q,
+                         const double* __restrict__ partial, int ks, const WsHeader* h, double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_q) return;
+  double Q[3];
+  for (int d = 0; d < 3; ++d) Q[d] = (double)(float)q[3 * i + d];   // the Q the FP32 pairs used
+  const double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
+  const double rmax = (double)__uint_as_float(h->rmax_bits);
+  if (q2 == 0.0 || sqrt(q2) * rmax < kTauSmallQ) return;   // k_qsmall's (same test as k_bq)
+  double v[kQG] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int k = 0; k < ks; ++k)
+    for (int f = 0; f < kQG; ++f) v[f] += partial[((int64_t)k * n_q + i) * kQG + f];
+  const double c[3] = {h->center[0], h->center[1], h->center[2]};
+  double sp, cp;
+  sincos(Q[0] * c[0] + Q[1] * c[1] + Q[2] * c[2], &sp, &cp);
+  const double Fr = (v[0] * cp - v[1] * sp) / q2, Fi = (v[0] * sp + v[1] * cp) / q2;
+  const double gr = g[2 * i], gi = g[2 * i + 1];
+  // Re(conj(g) F w) for w = i c_d - 2 Q_d/|Q|^2:  Re(conj(g) F) (-2Q_d/q2) - Im(conj(g) F) c_d
+  const double re = gr * Fr + gi * Fi, im = gr * Fi - gi * Fr;
+  for (int d = 0; d < 3; ++d) out[3 * i + d] = re * (-2.0 * Q[d] / q2) - im * c[d] + v[2 + d];
+}
+
+// Sum over a block of kAux threads (fixed order); every thread gets the total.
+__device__ __forceinline__ double block_sum_aux(double x, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = x;
+  __syncthreads();
+  double r = 0.0;
+  for (int w = 0; w < kAux / 32; ++w) r += sh[w];
+  __syncthreads();
+  return r;
+}
+
+// Q = 0 and small |Q| in FP64: S0 = sum over the signed tetrahedra (c, p0, p1, p2) of
+// det * series3(x), x_k = Q.(p_k - c); dS0/dQ = sum det * sum_k i series4(x, x_k) (p_k - c),
+// since d h_n(x)/d x_k = h_{n-1}(x, x_k) for the complete homogeneous polynomials; then
+// dF/dQ = e^{iQ.c} (i c S0 + dS0/dQ).
+__global__ void __launch_bounds__(kAux) k_qsmall(const float* __restrict__ v, int64_t nv,
+                                                 const int32_t* __restrict__ f, int64_t nf,
+                                                 const double* __restrict__ q, const double* __restrict__ g,
+                                                 const WsHeader* h, const int32_t* list, double* __restrict__ out) {
+  __shared__ double sh[kAux / 32];
+  const uint32_t count = h->small_q_count;
+  const double c[3] = {h->center[0], h->center[1], h->center[2]};
+  for (uint32_t e = blockIdx.x; e < count; e += gridDim.x) {
+    const int64_t i = list[e];
+    double Q[3];
+    for (int d = 0; d < 3; ++d) Q[d] = (double)(float)q[3 * i + d];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // S0 (re, im), dS0/dQ (re, im) x 3
+    for (int64_t m = threadIdx.x; m < nf; m += kAux) {
+      const int32_t id[3] = {f[3 * m], f[3 * m + 1], f[3 * m + 2]};
+      if (id[0] < 0 || id[1] < 0 || id[2] < 0 || id[0] >= nv || id[1] >= nv || id[2] >= nv) continue;
+      double P[3][3], x[4];
+      for (int k = 0; k < 3; ++k) {
+        for (int d = 0; d < 3; ++d) P[k][d] = (double)v[3 * (int64_t)id[k] + d] - c[d];
+        x[k] = Q[0] * P[k][0] + Q[1] * P[k][1] + Q[2] * P[k][2];
+      }
+      const double det = P[0][0] * (P[1][1] * P[2][2] - P[1][2] * P[2][1]) +
+                         P[0][1] * (P[1][2] * P[2][0] - P[1][0] * P[2][2]) +
+                         P[0][2] * (P[1][0] * P[2][1] - P[1][1] * P[2][0]);
+      double sr, si;
+      simplex_series<3, 3, 16>(x, sr, si);
+      acc[0] += det * sr;
+      acc[1] += det * si;
+      for (int k = 0; k < 3; ++k) {
+        x[3] = x[k];
+        double tr, ti;
+        simplex_series<4, 4, 16>(x, tr, ti);
+        for (int d = 0; d < 3; ++d) {   // i (tr + i ti) P_kd = (-ti + i tr) P_kd
+          acc[2 + 2 * d] += -det * ti * P[k][d];
+          acc[3 + 2 * d] += det * tr * P[k][d];
+        }
+      }
+    }
+    for (int k = 0; k < 8; ++k) acc[k] = block_sum_aux(acc[k], sh);
+    if (threadIdx.x == 0) {
+      double sp, cp;
+      sincos(Q[0] * c[0] + Q[1] * c[1] + Q[2] * c[2], &sp, &cp);
+      const double gr = g[2 * i], gi = g[2 * i + 1];
+      for (int d = 0; d < 3; ++d) {
+        // D = i c_d S0 + dS0_d, dF = e^{iQ.c} D, out = Re(conj(g) dF)
+        const double Dr = -c[d] * acc[1] + acc[2 + 2 * d], Di = c[d] * acc[0] + acc[3 + 2 * d];
+        const double dr = Dr * cp - Di * sp, di = Dr * sp + Di * cp;
+        out[3 * i + d] = gr * dr + gi * di;
+      }
+    }
+  }
+}
+
 template <int D, int NF>
 __global__ void __launch_bounds__(kBwdNT) k_bwd(const void* __restrict__ items, int64_t n_items,
                                                 const QRec* __restrict__ rec, int64_t n_q, int64_t per_split,
@@ -719,6 +919,45 @@ BwdLayout bwd_layout(int dim, int64_t n_verts, int64_t n_items, int64_t n_prep, 
   return y;
 }
 
+// Q-gradient workspace: header, volume partials (written by the prep kernel), face
+// records, Q records, small-|Q| list, kQG FP64 partials per (face chunk, Q).
+struct QgLayout {
+  size_t mparts, items, qrec, small, partial, total;
+  int nblk, ks;
+  int64_t per_split;
+};
+
+QgLayout qg_layout(int64_t n_faces, int64_t n_q) {
+  QgLayout y{};
+  const int64_t face_tiles = std::max<int64_t>(1, (n_faces + kFTile - 1) / kFTile);
+  const int64_t q_blocks = std::max<int64_t>(1, (n_q + kBwdNT - 1) / kBwdNT);
+  int occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_qgrad, kBwdNT, 0) != cudaSuccess || occ < 1) occ = 1;
+  const int64_t slots = (int64_t)sm_count() * occ;
+  const int kmax = (int)std::max<int64_t>(1, std::min<int64_t>(64, face_tiles / 2));
+  int k = 0, best_k = 1;
+  double best_eff = -1.0;
+  for (int c = 1; c <= kmax; ++c) {   // smallest split that fills whole waves (last one >= 97 %)
+    const double waves = (double)(q_blocks * c) / (double)slots;
+    const double eff = waves / std::ceil(waves);
+    if (q_blocks * c >= slots && eff >= 0.97) { k = c; break; }
+    if (eff > best_eff + 1e-9) { best_eff = eff; best_k = c; }
+  }
+  if (k == 0) k = best_k;
+  const int64_t tiles_per = (face_tiles + k - 1) / k;
+  y.per_split = tiles_per * kFTile;
+  y.ks = (int)((face_tiles + tiles_per - 1) / tiles_per);
+  y.nblk = std::max(1, prep_blocks(n_faces));
+  size_t o = al(sizeof(WsHeader));
+  y.mparts = o;  o = al(o + sizeof(double) * (size_t)y.nblk);
+  y.items = o;   o = al(o + sizeof(Face32) * (size_t)std::max<int64_t>(n_faces, 1));
+  y.qrec = o;    o = al(o + sizeof(QRec) * (size_t)std::max<int64_t>(n_q, 1));
+  y.small = o;   o = al(o + sizeof(int32_t) * (size_t)std::max<int64_t>(n_q, 1));
+  y.partial = o; o = al(o + sizeof(double) * kQG * (size_t)y.ks * (size_t)std::max<int64_t>(n_q, 1));
+  y.total = o;
+  return y;
+}
+
 int check_opts(const pft_options* o, Thr& th) {
   pft_options z;
   std::memset(&z, 0, sizeof(z));
@@ -912,6 +1151,50 @@ int pft3d_polymesh_backward(const float* verts, int64_t n_verts, const int32_t* 
   if (launch_fan3d(face_idx, n_idx, face_off, n_faces, tris, n_tris, h, st) != cudaSuccess) return PFT_ERR_CUDA;
   ++g_bwd_launches;
   return mesh3d_backward_body(verts, n_verts, tris, n_tris, q, n_q, grad_out, grad_verts, ws, y, th, h, st);
+}
+
+size_t pft3d_qgrad_workspace_size(int64_t n_verts, int64_t n_faces, int64_t n_q, const pft_options* opts) {
+  Thr th;
+  if (n_verts < 0 || n_faces < 0 || n_q < 0 || check_opts(opts, th) != PFT_OK) return 0;
+  return qg_layout(n_faces, n_q).total;
+}
+
+int pft3d_mesh_qgrad(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces, const double* q,
+                     int64_t n_q, const double* grad_out, double* grad_q, void* ws, size_t ws_bytes,
+                     const pft_options* opts, void* stream) {
+  g_bwd_launches = 0;
+  Thr th;
+  if (int e = check_opts(opts, th)) return e;
+  if (n_verts < 0 || n_faces < 0 || n_q < 0) return PFT_ERR_INVALID_ARG;
+  if (n_faces > 0 && (faces == nullptr || verts == nullptr || n_verts == 0)) return PFT_ERR_INVALID_ARG;
+  if (n_q > 0 && (q == nullptr || grad_out == nullptr || grad_q == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (n_q > INT32_MAX || n_verts > INT32_MAX) return PFT_ERR_UNSUPPORTED;
+  const QgLayout y = qg_layout(n_faces, n_q);
+  if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < y.total) return PFT_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader* h = at<WsHeader>(ws, 0);
+  if (launch_init_header(h, st) != cudaSuccess) return PFT_ERR_CUDA;
+  ++g_bwd_launches;
+  if (n_q == 0) return PFT_OK;
+  if (n_faces == 0)
+    return cudaMemsetAsync(grad_q, 0, sizeof(double) * 3 * (size_t)n_q, st) == cudaSuccess ? PFT_OK : PFT_ERR_CUDA;
+  if (launch_bbox(verts, n_verts, 3, h, st) != cudaSuccess) return PFT_ERR_CUDA;
+  if (launch_prep3d(verts, n_verts, faces, n_faces, h, at<void>(ws, y.items), false, at<double>(ws, y.mparts),
+                    y.nblk, st) != cudaSuccess)
+    return PFT_ERR_CUDA;
+  g_bwd_launches += 2;
+  k_bq<3><<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, h, 1.0, at<QRec>(ws, y.qrec), at<int32_t>(ws, y.small));
+  PFT_BWD_LAUNCH();
+  dim3 grid(blocks(n_q, kBwdNT), (unsigned)y.ks);
+  k_qgrad<<<grid, kBwdNT, 0, st>>>(at<Face32>(ws, y.items), n_faces, y.per_split, at<QRec>(ws, y.qrec), n_q, th,
+                                   at<double>(ws, y.partial), &h->status);
+  PFT_BWD_LAUNCH();
+  k_qfinal<<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, at<double>(ws, y.partial), y.ks, h, grad_q);
+  PFT_BWD_LAUNCH();
+  k_qsmall<<<(unsigned)sm_count(), kAux, 0, st>>>(verts, n_verts, faces, n_faces, q, grad_out, h,
+                                                 at<int32_t>(ws, y.small), grad_q);
+  PFT_BWD_LAUNCH();
+  return PFT_OK;
 }
 
 int pft_backward_last_launch_count(void) { return g_bwd_launches; }
