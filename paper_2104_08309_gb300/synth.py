@@ -239,6 +239,49 @@ def extruded_polygon(poly, h: float, z0: float = 0.0):
     return v, idx, off
 
 
+def voxel_ball(n: int, radius: float, d: float):
+    """Occupancy [n, n, n] of the cubes of side d (grid centred on the origin) whose centres lie
+    inside the ball of the given radius."""
+    c = (np.arange(n) + 0.5 - 0.5 * n) * d
+    x, y, z = np.meshgrid(c, c, c, indexing="ij")
+    return x * x + y * y + z * z < radius * radius
+
+
+def voxel_surface(occ, d: float):
+    """The closed boundary of a set of cubes as outward quadrilaterals (CSR polygon mesh).
+
+    occ [nx, ny, nz] bool; cube (i, j, k) spans [i d, (i+1) d] x ... shifted so the grid is centred
+    on the origin.  A face is emitted wherever an occupied cube meets an empty one (or the grid's
+    edge).  Returns verts [V, 3] float32 (grid points), face_idx int32, face_off int64.
+    """
+    occ = np.asarray(occ, dtype=bool)
+    nx, ny, nz = occ.shape
+    pad = np.zeros((nx + 2, ny + 2, nz + 2), dtype=bool)
+    pad[1:-1, 1:-1, 1:-1] = occ
+    quads = []
+    # unit offsets of the 4 corners of the +axis face of a cube, counter-clockwise seen from outside
+    corner = {0: [(1, 0, 0), (1, 1, 0), (1, 1, 1), (1, 0, 1)],
+              1: [(0, 1, 0), (0, 1, 1), (1, 1, 1), (1, 1, 0)],
+              2: [(0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]}
+    for ax in range(3):
+        e = np.zeros(3, dtype=int)
+        e[ax] = 1
+        nb = pad[1 + e[0]:nx + 1 + e[0], 1 + e[1]:ny + 1 + e[1], 1 + e[2]:nz + 1 + e[2]]
+        nbm = pad[1 - e[0]:nx + 1 - e[0], 1 - e[1]:ny + 1 - e[1], 1 - e[2]:nz + 1 - e[2]]
+        for sign, other in ((1, nb), (-1, nbm)):
+            cells = np.argwhere(occ & ~other)
+            # the -axis face: the same corners moved to the cube's low side, in reverse order
+            offs = np.array(corner[ax]) if sign > 0 else \
+                np.array([[0 if a == ax else c[a] for a in range(3)] for c in corner[ax]])[::-1]
+            quads.append(cells[:, None, :] + offs[None, :, :])
+    q = np.concatenate(quads).reshape(-1, 3)
+    keys, inv = np.unique(q, axis=0, return_inverse=True)
+    verts = ((keys - 0.5 * np.array([nx, ny, nz])) * d).astype(np.float32)
+    idx = inv.reshape(-1).astype(np.int32)
+    off = np.arange(0, idx.size + 1, 4, dtype=np.int64)
+    return verts, idx, off
+
+
 # ----------------------------------------------------------------------------
 # Q samples (float64 at the boundary).
 # ----------------------------------------------------------------------------

@@ -174,3 +174,21 @@ def test_polymesh_empty_and_single_face_types(torch_dev, rng):
     a = _run(torch_dev, vi, fi.reshape(-1), np.arange(0, 3 * fi.shape[0] + 1, 3, dtype=np.int64), q)
     b = _c(pft.pft3d_mesh(torch.from_numpy(vi).to(dev), torch.from_numpy(fi).to(dev), torch.from_numpy(q).to(dev)))
     assert np.array_equal(a, b)
+
+
+def test_voxelised_ball_surface(torch_dev, rng):
+    """The boundary of a voxelised ball (quadrilaterals on a cubic grid, many coplanar, Q along the
+    face normals included) against the plain sum over its cubes of the box closed form."""
+    d = 1.0 / 16.0
+    occ = synth.voxel_ball(48, 1.3, d)
+    v, idx, off = synth.voxel_surface(occ, d)
+    q = np.concatenate([[[0, 0, 0], [8.0, 0, 0], [0, 0, -40.0], [0, 3.0, 0]], rng.uniform(-60, 60, (800, 3))])
+    got = _run(torch_dev, v, idx, off, q)
+    n = np.array(occ.shape)
+    r = (np.argwhere(occ) - 0.5 * n) * d
+    ref = np.empty(q.shape[0], dtype=complex)
+    for i, Q in enumerate(q):
+        box = np.prod([d * np.sinc(0.5 * Q[c] * d / np.pi) * np.exp(0.5j * Q[c] * d) for c in range(3)])
+        ref[i] = box * np.sum(np.exp(1j * (r @ Q)))
+    vol = occ.sum() * d ** 3
+    assert np.max(np.abs(got - ref)) / vol < TOL["fp32"]
