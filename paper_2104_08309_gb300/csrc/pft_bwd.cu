@@ -538,20 +538,37 @@ __device__ __forceinline__ double block_sum_aux(double x, double* sh) {
 // Q = 0 and small |Q| in FP64: S0 = sum over the signed tetrahedra (c, p0, p1, p2) of
 // det * series3(x), x_k = Q.(p_k - c); dS0/dQ = sum det * sum_k i series4(x, x_k) (p_k - c),
 // since d h_n(x)/d x_k = h_{n-1}(x, x_k) for the complete homogeneous polynomials; then
-// dF/dQ = e^{iQ.c} (i c S0 + dS0/dQ).
-__global__ void __launch_bounds__(kAux) k_qsmall(const float* __restrict__ v, int64_t nv,
-                                                 const int32_t* __restrict__ f, int64_t nf,
-                                                 const double* __restrict__ q, const double* __restrict__ g,
-                                                 const WsHeader* h, const int32_t* list, double* __restrict__ out) {
+// dF/dQ = e^{iQ.c} (i c S0 + dS0/dQ).  The faces of each listed Q are cut into chunks so that
+// all blocks share the work even for a single listed Q (usually Q = 0 alone): k_qsmall_part
+// writes one partial per (listed Q, chunk) into at most kQsUnits slots, k_qsmall_fin adds the
+// chunks of each listed Q in order.  There are max(kQsUnits, n_q) slots, so every listed Q
+// has at least one.
+constexpr int kQsUnits = 8192;      // (listed Q, face chunk) partial slots at least
+constexpr int kQsF = 8;             // FP64 fields per slot: S0 (re, im), dS0/dQ (re, im) x 3
+
+__device__ __forceinline__ int64_t qsmall_chunks(uint32_t count, int64_t nf, int64_t slots) {
+  const int64_t most = max((int64_t)1, (nf + kAux - 1) / kAux);   // at least kAux faces per chunk
+  return max((int64_t)1, min(most, slots / max((int64_t)count, (int64_t)1)));
+}
+
+__global__ void __launch_bounds__(kAux) k_qsmall_part(const float* __restrict__ v, int64_t nv,
+                                                      const int32_t* __restrict__ f, int64_t nf,
+                                                      const double* __restrict__ q, const WsHeader* h,
+                                                      const int32_t* list, int64_t slots,
+                                                      double* __restrict__ part) {
   __shared__ double sh[kAux / 32];
-  const uint32_t count = h->small_q_count;
+  const uint32_t count = h->small_q_count;   // <= n_q <= slots
+  const int64_t nch = qsmall_chunks(count, nf, slots);
+  const int64_t per = (nf + nch - 1) / nch;
   const double c[3] = {h->center[0], h->center[1], h->center[2]};
-  for (uint32_t e = blockIdx.x; e < count; e += gridDim.x) {
+  for (int64_t u = blockIdx.x; u < (int64_t)count * nch; u += gridDim.x) {
+    const int64_t e = u / nch, ch = u % nch;
     const int64_t i = list[e];
     double Q[3];
     for (int d = 0; d < 3; ++d) Q[d] = (double)(float)q[3 * i + d];
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // S0 (re, im), dS0/dQ (re, im) x 3
-    for (int64_t m = threadIdx.x; m < nf; m += kAux) {
+    double acc[kQsF] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int64_t m1 = min(nf, (ch + 1) * per);
+    for (int64_t m = ch * per + threadIdx.x; m < m1; m += kAux) {
       const int32_t id[3] = {f[3 * m], f[3 * m + 1], f[3 * m + 2]};
       if (id[0] < 0 || id[1] < 0 || id[2] < 0 || id[0] >= nv || id[1] >= nv || id[2] >= nv) continue;
       double P[3][3], x[4];
@@ -576,17 +593,34 @@ __global__ void __launch_bounds__(kAux) k_qsmall(const float* __restrict__ v, in
         }
       }
     }
-    for (int k = 0; k < 8; ++k) acc[k] = block_sum_aux(acc[k], sh);
-    if (threadIdx.x == 0) {
-      double sp, cp;
-      sincos(Q[0] * c[0] + Q[1] * c[1] + Q[2] * c[2], &sp, &cp);
-      const double gr = g[2 * i], gi = g[2 * i + 1];
-      for (int d = 0; d < 3; ++d) {
-        // D = i c_d S0 + dS0_d, dF = e^{iQ.c} D, out = Re(conj(g) dF)
-        const double Dr = -c[d] * acc[1] + acc[2 + 2 * d], Di = c[d] * acc[0] + acc[3 + 2 * d];
-        const double dr = Dr * cp - Di * sp, di = Dr * sp + Di * cp;
-        out[3 * i + d] = gr * dr + gi * di;
-      }
+    for (int k = 0; k < kQsF; ++k) {
+      const double t = block_sum_aux(acc[k], sh);
+      if (threadIdx.x == 0) part[u * kQsF + k] = t;
+    }
+  }
+}
+
+__global__ void k_qsmall_fin(int64_t nf, const double* __restrict__ q, const double* __restrict__ g,
+                             const WsHeader* h, const int32_t* list, int64_t slots, const double* __restrict__ part,
+                             double* __restrict__ out) {
+  const uint32_t count = h->small_q_count;
+  const int64_t nch = qsmall_chunks(count, nf, slots);
+  const double c[3] = {h->center[0], h->center[1], h->center[2]};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = list[e];
+    double acc[kQsF] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t ch = 0; ch < nch; ++ch)
+      for (int k = 0; k < kQsF; ++k) acc[k] += part[(e * nch + ch) * kQsF + k];
+    double Q[3];
+    for (int d = 0; d < 3; ++d) Q[d] = (double)(float)q[3 * i + d];
+    double sp, cp;
+    sincos(Q[0] * c[0] + Q[1] * c[1] + Q[2] * c[2], &sp, &cp);
+    const double gr = g[2 * i], gi = g[2 * i + 1];
+    for (int d = 0; d < 3; ++d) {
+      // D = i c_d S0 + dS0_d, dF = e^{iQ.c} D, out = Re(conj(g) dF)
+      const double Dr = -c[d] * acc[1] + acc[2 + 2 * d], Di = c[d] * acc[0] + acc[3 + 2 * d];
+      const double dr = Dr * cp - Di * sp, di = Dr * sp + Di * cp;
+      out[3 * i + d] = gr * dr + gi * di;
     }
   }
 }
@@ -922,9 +956,9 @@ BwdLayout bwd_layout(int dim, int64_t n_verts, int64_t n_items, int64_t n_prep, 
 // Q-gradient workspace: header, volume partials (written by the prep kernel), face
 // records, Q records, small-|Q| list, kQG FP64 partials per (face chunk, Q).
 struct QgLayout {
-  size_t mparts, items, qrec, small, partial, total;
+  size_t mparts, items, qrec, small, partial, spart, total;
   int nblk, ks;
-  int64_t per_split;
+  int64_t per_split, slots;
 };
 
 QgLayout qg_layout(int64_t n_faces, int64_t n_q) {
@@ -954,6 +988,8 @@ QgLayout qg_layout(int64_t n_faces, int64_t n_q) {
   y.qrec = o;    o = al(o + sizeof(QRec) * (size_t)std::max<int64_t>(n_q, 1));
   y.small = o;   o = al(o + sizeof(int32_t) * (size_t)std::max<int64_t>(n_q, 1));
   y.partial = o; o = al(o + sizeof(double) * kQG * (size_t)y.ks * (size_t)std::max<int64_t>(n_q, 1));
+  y.slots = std::max<int64_t>(kQsUnits, n_q);
+  y.spart = o;   o = al(o + sizeof(double) * kQsF * (size_t)y.slots);
   y.total = o;
   return y;
 }
@@ -1191,8 +1227,12 @@ int pft3d_mesh_qgrad(const float* verts, int64_t n_verts, const int32_t* faces, 
   PFT_BWD_LAUNCH();
   k_qfinal<<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, at<double>(ws, y.partial), y.ks, h, grad_q);
   PFT_BWD_LAUNCH();
-  k_qsmall<<<(unsigned)sm_count(), kAux, 0, st>>>(verts, n_verts, faces, n_faces, q, grad_out, h,
-                                                 at<int32_t>(ws, y.small), grad_q);
+  k_qsmall_part<<<(unsigned)(4 * sm_count()), kAux, 0, st>>>(verts, n_verts, faces, n_faces, q, h,
+                                                             at<int32_t>(ws, y.small), y.slots,
+                                                             at<double>(ws, y.spart));
+  PFT_BWD_LAUNCH();
+  k_qsmall_fin<<<blocks(n_q, kAux), kAux, 0, st>>>(n_faces, q, grad_out, h, at<int32_t>(ws, y.small), y.slots,
+                                                   at<double>(ws, y.spart), grad_q);
   PFT_BWD_LAUNCH();
   return PFT_OK;
 }

@@ -76,3 +76,15 @@ def test_c4_size_sampled(torch_dev):
     ref = oracle.qgrad3d(w.verts, w.faces, w.q[sel], g[sel])
     assert np.all(np.isfinite(got))
     assert np.max(np.abs(got[sel] - ref)) < 1e-5 * _scale(w.verts, w.faces, g)
+
+
+def test_many_small_q(torch_dev, rng):
+    """Hundreds of Q with |Q| R < 0.25 (the FP64 series path, faces split into chunks per Q)."""
+    v, f = synth.perturbed_icosphere(3, seed=15, amp=0.05)
+    r = float(np.max(np.linalg.norm(v.astype(np.float64), axis=1)))
+    q = (rng.uniform(-1, 1, (400, 3)) * 0.12 / r).astype(np.float32).astype(np.float64)
+    q[0] = 0.0
+    g = rng.normal(size=q.shape[0]) + 1j * rng.normal(size=q.shape[0])
+    got = _qgrad(torch_dev, v, f, q, g)
+    ref = oracle.qgrad3d(v, f, q, g)
+    assert np.max(np.abs(got - ref)) < 1e-9 * _scale(v, f, g)
