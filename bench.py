@@ -75,6 +75,15 @@ def parse():
     return p.parse_args()
 
 
+def bench_out_dir():
+    """Where the bench leaves its side files (clock samples, the autotuner's cache): $PFT_BENCH_OUT,
+    else a folder in the system's temporary directory."""
+    import tempfile
+    d = os.environ.get("PFT_BENCH_OUT") or os.path.join(tempfile.gettempdir(), "pft_bench")
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
 def replica_seed(rank):
     """Seed of the mesh rank `rank` transforms: every rank an independent problem of the same size."""
     return 5 + rank
@@ -204,7 +213,7 @@ class ClockSampler:
 
     def start(self):
         try:
-            out = os.path.join(ROOT, "gpurun_out")
+            out = bench_out_dir()
             os.makedirs(out, exist_ok=True)
             self.path = os.path.join(out, f"clocks_{os.getpid()}.csv")
             self.fh = open(self.path, "w")
@@ -297,7 +306,7 @@ def bench_batched(dev, warmup, steps):
     offd = torch.from_numpy(w.poly_off).to(dev)
     from paper_2104_08309_gb300 import autotune
     tuned = autotune.tune_batched2d(vd, w.poly_off, qd,
-                                    path=os.path.join(ROOT, "gpurun_out", "tune_cache.json"))
+                                    path=os.path.join(bench_out_dir(), "tune_cache.json"))
     prep = pft.pft2d_batched_prepare(w.poly_off, w.q.shape[0], options=tuned, device=dev)
     out = torch.empty(w.poly_off.size - 1, w.q.shape[0], 2, dtype=torch.float64, device=dev)
     s = torch.cuda.Stream(dev)
