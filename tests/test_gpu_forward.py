@@ -229,3 +229,23 @@ def test_main_kernel_events(torch_dev):
     torch.cuda.synchronize()
     assert e0.elapsed_time(e1) > 0.0
     assert pft.launch_count() >= 4
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_degenerate_faces_and_segments(torch_dev, prec, rng):
+    """Zero-area faces (repeated or collinear corners) and zero-length segments (repeated vertices)
+    contribute nothing: the results match the shapes without them."""
+    v, f = synth.perturbed_icosphere(3, seed=6, amp=0.05)
+    q = _q3_mix(rng, 800, 20.0)
+    n = v.shape[0]
+    v2 = np.concatenate([v, [[0.25, 0.5, 0.75], [0.5, 1.0, 1.5], [0.75, 1.5, 2.25]]]).astype(np.float32)
+    extra = np.array([[0, 0, 5], [7, 3, 7], [n, n + 1, n + 2]] * 20, np.int32)
+    ref = oracle.ft3d(v, f, q)
+    got = run3d(torch_dev, v2, np.concatenate([f, extra]), q, precision=prec)
+    assert rel_err(got, ref, ref[0]) < TOL[prec]
+    p = synth.star_polygon(50, seed=8)
+    p2 = np.repeat(p, 2, axis=0)                       # every vertex twice: 50 zero-length segments
+    q2 = np.concatenate([[[0.0, 0.0]], rng.uniform(-30, 30, (600, 2))])
+    ref2 = oracle.ft2d(p, q2)
+    got2 = run2d(torch_dev, p2, q2, precision=prec)
+    assert rel_err(got2, ref2, ref2[0]) < TOL[prec]

@@ -194,3 +194,15 @@ def test_branches_agree_at_the_same_q():
             integral = np.sum(w * np.exp(1j * pts @ Q))     # area 1/2 * 2 = weights sum 1/2
             ref = -1j * Q[2] / (Q @ Q) * integral
             assert abs(term - ref) < 1e-14, (qz, eps, term, ref)
+
+
+def test_degenerate_faces_contribute_nothing(rng):
+    """Zero-area faces (a repeated corner, or three collinear corners) add nothing."""
+    v, f = synth.perturbed_icosphere(2, seed=6, amp=0.05)
+    q = rng.uniform(-12, 12, (100, 3))
+    base = oracle.ft3d(v, f, q)
+    v2 = np.concatenate([v, [[0.25, 0.5, 0.75], [0.5, 1.0, 1.5], [0.75, 1.5, 2.25]]]).astype(np.float32)
+    n = v.shape[0]
+    extra = np.array([[0, 0, 5], [7, 3, 7], [n, n + 1, n + 2]], np.int32)
+    got = oracle.ft3d(v2, np.concatenate([f, extra]), q)
+    assert np.max(np.abs(got - base)) < 1e-13 * abs(oracle.ft3d(v, f, [[0.0, 0.0, 0.0]])[0])
