@@ -353,12 +353,29 @@ def bench_batched(dev, warmup, steps):
     fp64 = {"value": pairs / (a.elapsed_time(b) / 1e3) / 1e9, "unit": UNIT, "ms": a.elapsed_time(b),
             "fp32_vs_fp64_max_abs_over_area": dev32}
     del o64
+    # the batched adjoint (vertex gradients of every polygon for seeded weights on the same grid)
+    gb = torch.randn(w.poly_off.size - 1, w.q.shape[0], 2, dtype=torch.float64, device=dev,
+                     generator=torch.Generator(device=dev).manual_seed(7))
+    for _ in range(2):
+        pft.pft2d_polygons_batched_backward(vd, offd, qd, gb)
+    tb = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        pft.pft2d_polygons_batched_backward(vd, offd, qd, gb)
+        b.record()
+        b.synchronize()
+        tb.append(a.elapsed_time(b))
+    backward = {"value": pairs / (float(np.mean(tb)) / 1e3) / 1e9, "unit": UNIT + " (adjoint call)",
+                "ms": float(np.mean(tb)), "launches": int(pft.load().pft_backward_last_launch_count())}
+    del gb
     return {"value": pairs / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "pairs_per_step": pairs,
             "roofline": rl,
             "polygons": int(w.poly_off.size - 1), "segments": int(w.verts.shape[0]), "q_points": int(w.q.shape[0]),
             "launches_per_step": int(launches), "cuda_graph": True, "device_status": int(status),
             "launch": {"q_per_thread": tuned["q_per_thread"], "block_threads": tuned["block_threads"],
-                       "chosen_by": "autotune"}, "fp64_gpu": fp64,
+                       "chosen_by": "autotune"}, "fp64_gpu": fp64, "backward": backward,
             "l2": "flushed between steps"}
 
 

@@ -20,7 +20,7 @@ from ._capi import (PFT_FP32_COMPENSATED, PFT_FP64, BatchedPlan, Options, PFTErr
 
 __all__ = [
     "pft2d_polygons", "pft2d_batched_prepare", "pft2d_polygons_batched", "BatchedPrepared", "pft3d_mesh",
-    "pft3d_polymesh", "pft3d_polymesh_backward", "ft3d_poly", "pft3d_batched_prepare", "pft3d_meshes_batched",
+    "pft3d_polymesh", "pft3d_polymesh_backward", "ft3d_poly", "pft2d_polygons_batched_backward", "pft3d_batched_prepare", "pft3d_meshes_batched",
     "pft2d_polygons_backward",
     "pft3d_mesh_backward", "pft3d_mesh_qgrad", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft3d", "make_options", "Options",
     "PFTError",
@@ -398,6 +398,31 @@ def pft3d_mesh_qgrad(verts, faces, q, grad_out, *, options=None, out=None, ws=No
                                ws.data_ptr(), ws.numel(), ctypes.byref(o), st), "pft3d_mesh_qgrad")
     if check_status:
         check(lib.pft_status(ws.data_ptr(), st), "pft3d_mesh_qgrad (device status)")
+    return out
+
+
+def pft2d_polygons_batched_backward(verts, poly_off, q, grad_out, *, options=None, out=None, ws=None, stream=None,
+                                    check_status=False):
+    """dL/dverts [n_v, 2] float32 for a batch of polygons on a shared Q set, from grad_out
+    [n_polys, n_q, 2] = (dL/dRe F_i(Q), dL/dIm F_i(Q))."""
+    torch = _torch()
+    v = _dev(verts, torch.float32, "verts", 2)
+    off = poly_off if (isinstance(poly_off, torch.Tensor) and poly_off.is_cuda) else _host_i64(poly_off).to(v.device)
+    off = _dev(off, torch.int64, "poly_off").reshape(-1)
+    qq = _dev(q, torch.float64, "q", 2)
+    np_, nq = off.shape[0] - 1, qq.shape[0]
+    g = _dev(grad_out, torch.float64, "grad_out").reshape(np_ * nq, 2)
+    o = make_options(options)
+    lib = load()
+    nb = lib.pft2d_batched_backward_workspace_size(v.shape[0], np_, nq, ctypes.byref(o))
+    ws = _ws(nb, v.device, ws)
+    out = torch.empty(v.shape[0], 2, dtype=torch.float32, device=v.device) if out is None else out
+    st = _stream(stream, v.device)
+    check(lib.pft2d_polygons_batched_backward(v.data_ptr(), v.shape[0], off.data_ptr(), np_, qq.data_ptr(), nq,
+                                              g.data_ptr(), out.data_ptr(), ws.data_ptr(), ws.numel(),
+                                              ctypes.byref(o), st), "pft2d_polygons_batched_backward")
+    if check_status:
+        check(lib.pft_status(ws.data_ptr(), st), "pft2d_polygons_batched_backward (device status)")
     return out
 
 

@@ -744,6 +744,225 @@ __global__ void k_bvert2d(const float* __restrict__ v, int64_t nv, const int64_t
   grad[2 * j + 1] = (float)gy;
 }
 
+// ---------------------------------------------------------------------------
+// Batched 2D adjoint: many polygons, each with its own weights g_i(Q) on a shared Q set.
+// Each polygon is centred on its own bounding box (as the batched forward does); Q records
+// carry gt_i(Q) = 2 g_i(Q) e^{-iQ.c_i}/|Q|^2 per (polygon, Q) row; pair blocks never straddle
+// polygons; the vertex gather adds each polygon's own small-|Q| rows in FP64.
+// ---------------------------------------------------------------------------
+struct PolyC {
+  double cx, cy;
+  float rmax;
+  int32_t pad;
+};
+
+__device__ __forceinline__ float block_minmax_f(float x, bool is_max, float* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = is_max ? fmaxf(x, y) : fminf(x, y);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = x;
+  __syncthreads();
+  float r = sh[0];
+  for (int w = 1; w < kAux / 32; ++w) r = is_max ? fmaxf(r, sh[w]) : fminf(r, sh[w]);
+  __syncthreads();
+  return r;
+}
+
+// One block per polygon: offset checks, bounding-box centre, segment records relative to it,
+// max radius, and the number of pair blocks (kBwdNT segments each) the polygon needs.
+__global__ void __launch_bounds__(kAux) k_bbprep(const float* __restrict__ v, int64_t nv,
+                                                 const int64_t* __restrict__ off, int64_t np, Seg32* segs,
+                                                 PolyC* pc, int32_t* nblk, WsHeader* h) {
+  __shared__ float sh[kAux / 32];
+  const int64_t i = blockIdx.x;
+  const int64_t s0 = off[i], s1 = off[i + 1];
+  if (threadIdx.x == 0 && (s1 < s0 || s0 < 0 || s1 > nv || (i == 0 && s0 != 0) || (i == np - 1 && s1 != nv)))
+    set_status(&h->status, ST_OFFSETS);
+  const int64_t b0 = max((int64_t)0, min(s0, nv)), n = max((int64_t)0, min(s1, nv) - b0);
+  float mn[2] = {3.4e38f, 3.4e38f}, mx[2] = {-3.4e38f, -3.4e38f};
+  bool bad = false;
+  for (int64_t j = threadIdx.x; j < n; j += kAux)
+    for (int d = 0; d < 2; ++d) {
+      const float x = v[2 * (b0 + j) + d];
+      if (!isfinite(x)) { bad = true; continue; }
+      mn[d] = fminf(mn[d], x);
+      mx[d] = fmaxf(mx[d], x);
+    }
+  if (bad) set_status(&h->status, ST_NONFINITE);
+  double c[2];
+  for (int d = 0; d < 2; ++d) {
+    const float lo = block_minmax_f(mn[d], false, sh), hi = block_minmax_f(mx[d], true, sh);
+    c[d] = (n > 0 && lo <= hi) ? 0.5 * ((double)lo + (double)hi) : 0.0;
+  }
+  float rm = 0.f;
+  for (int64_t j = threadIdx.x; j < n; j += kAux) {
+    const int64_t a = b0 + j, b = b0 + (j + 1 < n ? j + 1 : 0);
+    const double x0 = (double)v[2 * a] - c[0], y0 = (double)v[2 * a + 1] - c[1];
+    const double x1 = (double)v[2 * b] - c[0], y1 = (double)v[2 * b + 1] - c[1];
+    segs[a] = Seg32{(float)(0.5 * (x0 + x1)), (float)(0.5 * (y0 + y1)), (float)(0.5 * (x1 - x0)),
+                    (float)(0.5 * (y1 - y0))};
+    rm = fmaxf(rm, __double2float_ru(sqrt(x0 * x0 + y0 * y0)));
+  }
+  rm = block_minmax_f(rm, true, sh);
+  if (threadIdx.x == 0) {
+    pc[i] = PolyC{c[0], c[1], rm, 0};
+    nblk[i] = (int32_t)((n + kBwdNT - 1) / kBwdNT);
+  }
+}
+
+// One block per polygon: its Q records (weight 0 on small rows) and its small rows, listed in
+// Q order (a block-wide ordered compaction, so the gather below is deterministic).
+__global__ void __launch_bounds__(kAux) k_bbq(const double* __restrict__ q, const double* __restrict__ g, int64_t n_q,
+                                              const PolyC* __restrict__ pc, QRec* rec, int32_t* small,
+                                              int32_t* small_cnt) {
+  __shared__ int wcount[kAux / 32];
+  __shared__ int base;
+  const int64_t i = blockIdx.x;
+  const PolyC P = pc[i];
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int64_t l0 = 0; l0 < n_q; l0 += kAux) {
+    const int64_t l = l0 + threadIdx.x;
+    bool is_small = false;
+    if (l < n_q) {
+      const float qx = (float)q[2 * l], qy = (float)q[2 * l + 1];
+      const double Qx = qx, Qy = qy, q2 = Qx * Qx + Qy * Qy;
+      QRec r{qx, qy, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (q2 == 0.0 || sqrt(q2) * (double)P.rmax < kTauSmallQ) {
+        is_small = true;
+      } else {
+        double sp, cp;
+        sincos(-(Qx * P.cx + Qy * P.cy), &sp, &cp);
+        const double gr = g[2 * (i * n_q + l)], gi = g[2 * (i * n_q + l) + 1], k = 2.0 / q2;
+        r.gr = (float)(k * (gr * cp - gi * sp));
+        r.gi = (float)(k * (gr * sp + gi * cp));
+      }
+      rec[i * n_q + l] = r;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, is_small);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) wcount[wid] = __popc(m);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < kAux / 32; ++w) {
+      if (w < wid) before += wcount[w];
+      total += wcount[w];
+    }
+    if (is_small) small[i * n_q + base + before + __popc(m & ((1u << lane) - 1u))] = (int32_t)l;
+    __syncthreads();
+    if (threadIdx.x == 0) base += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) small_cnt[i] = base;
+}
+
+// Pair blocks: block b is pair block b - bstart[i] of polygon i (bisection over the exclusive
+// scan bstart of the blocks per polygon); threads <-> its segments; the polygon's Q records
+// stream through the ring (Q chunk blockIdx.y).  Blocks past the last polygon leave at once.
+__global__ void __launch_bounds__(kBwdNT) k_bbwd(const Seg32* __restrict__ segs, int64_t nv,
+                                                 const int64_t* __restrict__ off, int64_t np,
+                                                 const int64_t* __restrict__ bstart, const int32_t* __restrict__ nblk,
+                                                 const QRec* __restrict__ rec, int64_t n_q, int64_t per_split, Thr th,
+                                                 double* __restrict__ partial, uint32_t* status) {
+  __shared__ __align__(128) QRec slots[kStages * kQTile];
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ int done[kStages];
+  __shared__ int issued;
+  const int64_t b = blockIdx.x;
+  if (b >= bstart[np - 1] + nblk[np - 1]) return;   // uniform over the block
+  int64_t lo = 0, hi = np - 1;                      // the last polygon whose blocks start at or before b
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (bstart[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const int64_t s0 = max((int64_t)0, min(off[lo], nv)), s1 = max(s0, min(off[lo + 1], nv));
+  const int64_t m = s0 + (b - bstart[lo]) * kBwdNT + threadIdx.x;
+  const bool mine = m < s1;
+  float4 F = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (mine) F = reinterpret_cast<const float4*>(segs)[m];
+  const int64_t q0 = (int64_t)blockIdx.y * per_split;
+  const int64_t nq = max((int64_t)0, min(per_split, n_q - q0));
+  Ring<QRec, kQTile, kBwdNT> ring{slots, full, done, &issued, rec + lo * n_q + q0, nq,
+                                  (int)((nq + kQTile - 1) / kQTile)};
+  ring.start();
+  CAcc acc[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) acc[f].init();
+  bool ok = true;
+  for (int t = 0; t < ring.ntiles; ++t) {
+    if (!ring.wait(t)) { ok = false; break; }
+    const QRec* tq = ring.tile(t);
+    const int cnt = ring.count(t);
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int j = 0; j < cnt; ++j) seg_adj(tq[j], F, a);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) acc[f].add(a[f]);
+    ring.release(t);
+  }
+  if (!ok) set_status(status, ST_TIMEOUT);
+  ring.finish();
+  if (!ok || !mine) return;
+  double* dst = partial + ((int64_t)blockIdx.y * nv + m) * 4;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) dst[f] = (double)acc[f].hi + (double)acc[f].lo;
+}
+
+// Per vertex: record adjoints of the segment it starts and of the one it ends (Q chunks in
+// order), and the FP64 small-|Q| boundary-flux terms of its polygon's small rows.
+__global__ void k_bbvert(const float* __restrict__ v, int64_t nv, const int64_t* __restrict__ off, int64_t np,
+                         const double* __restrict__ partial, int ks, const PolyC* __restrict__ pc,
+                         const int32_t* __restrict__ small, const int32_t* __restrict__ small_cnt,
+                         const double* __restrict__ q, int64_t n_q, const double* __restrict__ g,
+                         float* __restrict__ grad) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= nv) return;
+  int64_t lo = 0, hi = np;
+  while (lo + 1 < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (off[mid] <= j) lo = mid; else hi = mid;
+  }
+  const int64_t s0 = off[lo], s1 = off[lo + 1];
+  int64_t jp = (j > s0) ? j - 1 : s1 - 1;   // segment ending at j
+  int64_t jn = (j + 1 < s1) ? j + 1 : s0;    // end of segment j
+  if (jp < 0 || jp >= nv) jp = j;
+  if (jn < 0 || jn >= nv) jn = j;
+  double mS[2] = {0, 0}, hS[2] = {0, 0}, mP[2] = {0, 0}, hP[2] = {0, 0};
+  for (int s = 0; s < ks; ++s) {
+    const double* a = partial + ((int64_t)s * nv + j) * 4;
+    const double* b = partial + ((int64_t)s * nv + jp) * 4;
+    mS[0] += a[0]; mS[1] += a[1]; hS[0] += a[2]; hS[1] += a[3];
+    mP[0] += b[0]; mP[1] += b[1]; hP[0] += b[2]; hP[1] += b[3];
+  }
+  double gx = 0.5 * (mS[0] - hS[0]) + 0.5 * (mP[0] + hP[0]);
+  double gy = 0.5 * (mS[1] - hS[1]) + 0.5 * (mP[1] + hP[1]);
+  const PolyC P = pc[lo];
+  const int32_t ns = small_cnt[lo];
+  if (ns > 0) {
+    const double c[2] = {P.cx, P.cy};
+    const double pj[2] = {(double)v[2 * j] - c[0], (double)v[2 * j + 1] - c[1]};
+    const double pn[2] = {(double)v[2 * jn] - c[0], (double)v[2 * jn + 1] - c[1]};
+    const double pp[2] = {(double)v[2 * jp] - c[0], (double)v[2 * jp + 1] - c[1]};
+    for (int32_t e = 0; e < ns; ++e) {
+      const int64_t l = small[lo * n_q + e];
+      const double qx = (double)(float)q[2 * l], qy = (double)(float)q[2 * l + 1];
+      const double phc = qx * c[0] + qy * c[1];
+      const double gr = g[2 * (lo * n_q + l)], gi = g[2 * (lo * n_q + l) + 1];
+      double d0[2] = {0, 0}, d1[2] = {0, 0}, e0[2] = {0, 0}, e1[2] = {0, 0};
+      seg_small(pj, pn, qx, qy, gr, gi, phc, d0, d1);   // j is the start
+      seg_small(pp, pj, qx, qy, gr, gi, phc, e0, e1);   // j is the end
+      gx += d0[0] + e1[0];
+      gy += d0[1] + e1[1];
+    }
+  }
+  grad[2 * j] = (float)gx;
+  grad[2 * j + 1] = (float)gy;
+}
+
 // 3D: per face, chunk sums of the record adjoints -> corner adjoints (FP64), plus
 // small-|Q| corner terms dF/dp_k = exp(iQ.c) N sum_j i^j h_j(a, a_k)/(j+3)!.
 __global__ void k_bcorner3d(const float* __restrict__ v, int64_t nv, const int32_t* __restrict__ f, int64_t nf,
@@ -994,6 +1213,36 @@ QgLayout qg_layout(int64_t n_faces, int64_t n_q) {
   return y;
 }
 
+// Batched 2D adjoint workspace.
+struct BbLayout {
+  size_t segs, pc, nblk, bstart, btot, rec, small, scnt, partial, total;
+  int ks;
+  int64_t per_split, grid;
+};
+
+BbLayout bb_layout(int64_t nv, int64_t np, int64_t n_q) {
+  BbLayout y{};
+  y.grid = std::max<int64_t>(1, np + (nv + kBwdNT - 1) / kBwdNT);   // at least the pair blocks needed
+  const int64_t slots = (int64_t)sm_count() * 8;
+  const int64_t q_tiles = std::max<int64_t>(1, (n_q + kQTile - 1) / kQTile);
+  const int64_t k = std::min<int64_t>({std::max<int64_t>(1, (4 * slots + y.grid - 1) / y.grid), q_tiles, 256});
+  y.per_split = ((q_tiles + k - 1) / k) * kQTile;
+  y.ks = (int)std::max<int64_t>(1, (n_q + y.per_split - 1) / y.per_split);
+  const int64_t rows = std::max<int64_t>(np * n_q, 1);
+  size_t o = al(sizeof(WsHeader));
+  y.segs = o;    o = al(o + sizeof(Seg32) * (size_t)std::max<int64_t>(nv, 1));
+  y.pc = o;      o = al(o + sizeof(PolyC) * (size_t)std::max<int64_t>(np, 1));
+  y.nblk = o;    o = al(o + sizeof(int32_t) * (size_t)std::max<int64_t>(np, 1));
+  y.bstart = o;  o = al(o + sizeof(int64_t) * (size_t)std::max<int64_t>(np, 1));
+  y.btot = o;    o = al(o + sizeof(int64_t) * (size_t)blocks(np, kAux));
+  y.rec = o;     o = al(o + sizeof(QRec) * (size_t)rows);
+  y.small = o;   o = al(o + sizeof(int32_t) * (size_t)rows);
+  y.scnt = o;    o = al(o + sizeof(int32_t) * (size_t)std::max<int64_t>(np, 1));
+  y.partial = o; o = al(o + sizeof(double) * 4 * (size_t)y.ks * (size_t)std::max<int64_t>(nv, 1));
+  y.total = o;
+  return y;
+}
+
 int check_opts(const pft_options* o, Thr& th) {
   pft_options z;
   std::memset(&z, 0, sizeof(z));
@@ -1233,6 +1482,62 @@ int pft3d_mesh_qgrad(const float* verts, int64_t n_verts, const int32_t* faces, 
   PFT_BWD_LAUNCH();
   k_qsmall_fin<<<blocks(n_q, kAux), kAux, 0, st>>>(n_faces, q, grad_out, h, at<int32_t>(ws, y.small), y.slots,
                                                    at<double>(ws, y.spart), grad_q);
+  PFT_BWD_LAUNCH();
+  return PFT_OK;
+}
+
+size_t pft2d_batched_backward_workspace_size(int64_t n_verts, int64_t n_polys, int64_t n_q, const pft_options* opts) {
+  Thr th;
+  if (n_verts < 0 || n_polys < 0 || n_q < 0 || check_opts(opts, th) != PFT_OK) return 0;
+  return bb_layout(n_verts, n_polys, n_q).total;
+}
+
+int pft2d_polygons_batched_backward(const float* verts, int64_t n_verts, const int64_t* poly_off, int64_t n_polys,
+                                    const double* q, int64_t n_q, const double* grad_out, float* grad_verts,
+                                    void* ws, size_t ws_bytes, const pft_options* opts, void* stream) {
+  g_bwd_launches = 0;
+  Thr th;
+  if (int e = check_opts(opts, th)) return e;
+  if (n_verts < 0 || n_polys < 0 || n_q < 0) return PFT_ERR_INVALID_ARG;
+  if (n_verts > 0 && (verts == nullptr || poly_off == nullptr || grad_verts == nullptr || n_polys == 0))
+    return PFT_ERR_INVALID_ARG;
+  if (n_q > 0 && (q == nullptr || grad_out == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (n_q > INT32_MAX || n_polys > INT32_MAX || n_polys * n_q > (int64_t)1 << 40) return PFT_ERR_UNSUPPORTED;
+  const BbLayout y = bb_layout(n_verts, n_polys, n_q);
+  if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < y.total) return PFT_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader* h = at<WsHeader>(ws, 0);
+  if (launch_init_header(h, st) != cudaSuccess) return PFT_ERR_CUDA;
+  ++g_bwd_launches;
+  if (n_verts == 0) return PFT_OK;
+  if (n_q == 0)
+    return cudaMemsetAsync(grad_verts, 0, sizeof(float) * 2 * (size_t)n_verts, st) == cudaSuccess ? PFT_OK
+                                                                                                 : PFT_ERR_CUDA;
+  Seg32* segs = at<Seg32>(ws, y.segs);
+  PolyC* pc = at<PolyC>(ws, y.pc);
+  int32_t* nblk = at<int32_t>(ws, y.nblk);
+  int64_t* bstart = at<int64_t>(ws, y.bstart);
+  int64_t* btot = at<int64_t>(ws, y.btot);
+  k_bbprep<<<(unsigned)n_polys, kAux, 0, st>>>(verts, n_verts, poly_off, n_polys, segs, pc, nblk, h);
+  PFT_BWD_LAUNCH();
+  const unsigned nb = blocks(n_polys, kAux);
+  k_scan_block<<<nb, kAux, 0, st>>>(nblk, n_polys, bstart, btot);
+  PFT_BWD_LAUNCH();
+  k_scan_totals<<<1, 32, 0, st>>>(btot, nb);
+  PFT_BWD_LAUNCH();
+  k_scan_add<<<nb, kAux, 0, st>>>(bstart, n_polys, btot);
+  PFT_BWD_LAUNCH();
+  k_bbq<<<(unsigned)n_polys, kAux, 0, st>>>(q, grad_out, n_q, pc, at<QRec>(ws, y.rec), at<int32_t>(ws, y.small),
+                                            at<int32_t>(ws, y.scnt));
+  PFT_BWD_LAUNCH();
+  if (y.grid > INT32_MAX) return PFT_ERR_UNSUPPORTED;
+  dim3 grid((unsigned)y.grid, (unsigned)y.ks);
+  k_bbwd<<<grid, kBwdNT, 0, st>>>(segs, n_verts, poly_off, n_polys, bstart, nblk, at<QRec>(ws, y.rec), n_q,
+                                  y.per_split, th, at<double>(ws, y.partial), &h->status);
+  PFT_BWD_LAUNCH();
+  k_bbvert<<<blocks(n_verts, kAux), kAux, 0, st>>>(verts, n_verts, poly_off, n_polys, at<double>(ws, y.partial), y.ks,
+                                                   pc, at<int32_t>(ws, y.small), at<int32_t>(ws, y.scnt), q, n_q,
+                                                   grad_out, grad_verts);
   PFT_BWD_LAUNCH();
   return PFT_OK;
 }

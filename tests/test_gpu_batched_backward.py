@@ -1,0 +1,92 @@
+"""Batched 2D adjoint (vertex gradients of many polygons, each with its own weights on a shared
+Q set) through the C ABI, polygon by polygon against the oracle's shape-derivative gradient and
+the single-polygon adjoint.  Tolerance: 1e-4 of each polygon's max |gradient|."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_08309_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GTOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_08309_gb300 import build as pbuild
+    pbuild.build()
+    return torch, torch.device("cuda:0")
+
+
+def _batch():
+    polys = [synth.star_polygon(3, seed=1), synth.star_polygon(300, seed=2, center=(0.5, -0.25)),
+             synth.regular_polygon(17, 0.4), synth.star_polygon(129, seed=3, center=(-0.75, 0.5)),
+             synth.star_polygon(40, seed=4)]
+    off = np.concatenate([[0], np.cumsum([p.shape[0] for p in polys])]).astype(np.int64)
+    return np.concatenate(polys).astype(np.float32), off
+
+
+def _run(td, v, off, q, g):
+    torch, dev = td
+    import paper_2104_08309_gb300 as pft
+    gd = np.ascontiguousarray(np.stack([g.real, g.imag], axis=-1))
+    return pft.pft2d_polygons_batched_backward(torch.from_numpy(v).to(dev), torch.from_numpy(off).to(dev),
+                                               torch.from_numpy(q).to(dev), torch.from_numpy(gd).to(dev),
+                                               check_status=True).cpu().numpy()
+
+
+def test_batched_backward_vs_oracle_and_single(torch_dev, rng):
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    v, off = _batch()
+    q = np.concatenate([[[0.0, 0.0], [1e-4, 2e-4], [0.0, 0.05]], rng.uniform(-30, 30, (1500, 2))])
+    g = rng.normal(size=(off.size - 1, q.shape[0])) + 1j * rng.normal(size=(off.size - 1, q.shape[0]))
+    got = _run(torch_dev, v, off, q, g)
+    for i in range(off.size - 1):
+        vi = v[off[i]:off[i + 1]]
+        ref = oracle.grad2d(vi, q, g[i])
+        gi = got[off[i]:off[i + 1]]
+        assert np.max(np.abs(gi - ref)) / np.max(np.abs(ref)) < GTOL, i
+        single = pft.pft2d_polygons_backward(torch.from_numpy(vi).to(dev), torch.from_numpy(q).to(dev),
+                                             torch.from_numpy(np.ascontiguousarray(np.stack([g[i].real, g[i].imag], 1))).to(dev),
+                                             check_status=True).cpu().numpy()
+        assert np.max(np.abs(gi - single)) / np.max(np.abs(ref)) < GTOL, i
+
+
+def test_c3_batch_sampled(torch_dev):
+    """4,096 polygons on the 64 x 64 grid with seeded weights: 8 sampled polygons against the oracle."""
+    w = synth.workload_c3()
+    rng = np.random.default_rng(46)
+    n = w.poly_off.size - 1
+    g = rng.normal(size=(n, w.q.shape[0])) + 1j * rng.normal(size=(n, w.q.shape[0]))
+    got = _run(torch_dev, w.verts, w.poly_off, w.q, g)
+    assert np.all(np.isfinite(got))
+    for i in np.sort(rng.choice(n, 8, replace=False)):
+        vi = w.verts[w.poly_off[i]:w.poly_off[i + 1]]
+        ref = oracle.grad2d(vi, w.q, g[i])
+        assert np.max(np.abs(got[w.poly_off[i]:w.poly_off[i + 1]] - ref)) / np.max(np.abs(ref)) < GTOL, i
+
+
+def test_bad_offsets_reported(torch_dev):
+    torch, dev = torch_dev
+    import ctypes
+    import paper_2104_08309_gb300 as pft
+    v, off = _batch()
+    bad = off.copy()
+    bad[-1] -= 1                                   # last offset short of n_verts
+    lib = pft.load()
+    o = pft.make_options(None)
+    q = torch.ones(8, 2, dtype=torch.float64, device=dev)
+    g = torch.ones(off.size - 1, 8, 2, dtype=torch.float64, device=dev)
+    nb = lib.pft2d_batched_backward_workspace_size(v.shape[0], off.size - 1, 8, ctypes.byref(o))
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    out = torch.empty(v.shape[0], 2, dtype=torch.float32, device=dev)
+    vd, bd = torch.from_numpy(v).to(dev), torch.from_numpy(bad).to(dev)
+    rc = lib.pft2d_polygons_batched_backward(vd.data_ptr(), v.shape[0], bd.data_ptr(), off.size - 1, q.data_ptr(), 8,
+                                             g.data_ptr(), out.data_ptr(), ws.data_ptr(), nb, ctypes.byref(o), None)
+    assert rc == 0
+    assert lib.pft_status(ws.data_ptr(), None) == 8
