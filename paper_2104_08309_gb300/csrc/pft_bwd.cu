@@ -676,14 +676,19 @@ __global__ void __launch_bounds__(kBwdNT) k_bwd(const void* __restrict__ items, 
 // ending at j, summed over Q chunks in order, plus FP64 small-|Q| terms.
 // Small |Q|: dF/dp0 = nu e^{i a0} (J0 - J1), dF/dp1 = nu e^{i a0} J1 with
 // nu = (dy, -dx), J0 = int_0^1 e^{itd}, J1 = int_0^1 t e^{itd} (series, |d| small).
+// Both ends lie within r_max of the centre and |Q| r_max < 1/4, so |d| < 1/2 and the
+// 20 terms kept leave a remainder below 0.5^20/20! ~ 4e-25.
 __device__ __forceinline__ void seg_small(const double* p0, const double* p1, double qx, double qy, double gr,
                                           double gi, double ph_c, double* g0, double* g1) {
   const double a0 = qx * p0[0] + qy * p0[1], d = qx * (p1[0] - p0[0]) + qy * (p1[1] - p0[1]);
   double j0r = 0, j0i = 0, j1r = 0, j1i = 0, tr = 1, ti = 0;   // term (i d)^n / n!
-  for (int n = 0; n < 24; ++n) {
-    j0r += tr / (n + 1); j0i += ti / (n + 1);
-    j1r += tr / (n + 2); j1i += ti / (n + 2);
-    const double nr = -ti * d / (n + 1), ni = tr * d / (n + 1);
+#pragma unroll
+  for (int n = 0; n < 20; ++n) {
+    const double r1 = 1.0 / (double)(n + 1), r2 = 1.0 / (double)(n + 2);   // constants once unrolled
+    j0r = fma(tr, r1, j0r); j0i = fma(ti, r1, j0i);
+    j1r = fma(tr, r2, j1r); j1i = fma(ti, r2, j1i);
+    const double dn = d * r1;
+    const double nr = -ti * dn, ni = tr * dn;
     tr = nr; ti = ni;
   }
   double se, ce;
