@@ -23,8 +23,11 @@ namespace pft {
 namespace {
 
 constexpr int kBwdNT = 128;        // threads per block of the pair kernels (one item each)
+constexpr int kBbSegs = 2 * kBwdNT;  // segments per pair block of the batched 2D adjoint (two a thread)
 constexpr int kQTile = 128;        // Q records per shared-memory tile
 constexpr int kAux = 256;          // threads per block of the auxiliary kernels
+constexpr double kTwoPiD = 6.283185307179586477;      // 2 pi (FP64)
+constexpr double kInvTwoPiD = 0.1591549430918953358;  // 1 / (2 pi) (FP64)
 
 struct __align__(16) QRec {
   float qx, qy, qz, gr, gi, pad0, pad1, pad2;
@@ -676,20 +679,25 @@ __global__ void __launch_bounds__(kBwdNT) k_bwd(const void* __restrict__ items, 
 // ending at j, summed over Q chunks in order, plus FP64 small-|Q| terms.
 // Small |Q|: dF/dp0 = nu e^{i a0} (J0 - J1), dF/dp1 = nu e^{i a0} J1 with
 // nu = (dy, -dx), J0 = int_0^1 e^{itd}, J1 = int_0^1 t e^{itd} (series, |d| small).
-// Both ends lie within r_max of the centre and |Q| r_max < 1/4, so |d| < 1/2 and the
-// 20 terms kept leave a remainder below 0.5^20/20! ~ 4e-25.
+// Both ends lie within r_max of the centre and |Q| r_max < 1/4, so |d| < 1/2: the terms
+// fall faster than 2^-n/n!, the series stops once one is below 1e-18 (J0 is near 1), and
+// 20 terms bound it (remainder below 0.5^20/20! ~ 4e-25).  Q = 0 takes one term.
+__constant__ double kInvN[22] = {1.0,        1.0 / 1,  1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,
+                                 1.0 / 6,    1.0 / 7,  1.0 / 8,  1.0 / 9,  1.0 / 10, 1.0 / 11,
+                                 1.0 / 12,   1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17,
+                                 1.0 / 18,   1.0 / 19, 1.0 / 20, 1.0 / 21};   // kInvN[k] = 1/k
 __device__ __forceinline__ void seg_small(const double* p0, const double* p1, double qx, double qy, double gr,
                                           double gi, double ph_c, double* g0, double* g1) {
   const double a0 = qx * p0[0] + qy * p0[1], d = qx * (p1[0] - p0[0]) + qy * (p1[1] - p0[1]);
   double j0r = 0, j0i = 0, j1r = 0, j1i = 0, tr = 1, ti = 0;   // term (i d)^n / n!
-#pragma unroll
   for (int n = 0; n < 20; ++n) {
-    const double r1 = 1.0 / (double)(n + 1), r2 = 1.0 / (double)(n + 2);   // constants once unrolled
+    const double r1 = kInvN[n + 1], r2 = kInvN[n + 2];
     j0r = fma(tr, r1, j0r); j0i = fma(ti, r1, j0i);
     j1r = fma(tr, r2, j1r); j1i = fma(ti, r2, j1i);
     const double dn = d * r1;
     const double nr = -ti * dn, ni = tr * dn;
     tr = nr; ti = ni;
+    if (fabs(tr) + fabs(ti) < 1e-18) break;
   }
   double se, ce;
   sincos(a0 + ph_c, &se, &ce);   // exp(i(Q.c + Q.(p0 - c)))
@@ -777,7 +785,7 @@ __device__ __forceinline__ float block_minmax_f(float x, bool is_max, float* sh)
 }
 
 // One block per polygon: offset checks, bounding-box centre, segment records relative to it,
-// max radius, and the number of pair blocks (kBwdNT segments each) the polygon needs.
+// max radius, and the number of pair blocks (kBbSegs segments each) the polygon needs.
 __global__ void __launch_bounds__(kAux) k_bbprep(const float* __restrict__ v, int64_t nv,
                                                  const int64_t* __restrict__ off, int64_t np, Seg32* segs,
                                                  PolyC* pc, int32_t* nblk, WsHeader* h) {
@@ -814,7 +822,7 @@ __global__ void __launch_bounds__(kAux) k_bbprep(const float* __restrict__ v, in
   rm = block_minmax_f(rm, true, sh);
   if (threadIdx.x == 0) {
     pc[i] = PolyC{c[0], c[1], rm, 0};
-    nblk[i] = (int32_t)((n + kBwdNT - 1) / kBwdNT);
+    nblk[i] = (int32_t)((n + kBbSegs - 1) / kBbSegs);
   }
 }
 
@@ -836,14 +844,19 @@ __global__ void __launch_bounds__(kAux) k_bbq(const double* __restrict__ q, cons
       const float qx = (float)q[2 * l], qy = (float)q[2 * l + 1];
       const double Qx = qx, Qy = qy, q2 = Qx * Qx + Qy * Qy;
       QRec r{qx, qy, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (q2 == 0.0 || sqrt(q2) * (double)P.rmax < kTauSmallQ) {
+      if (q2 == 0.0 || q2 * ((double)P.rmax * (double)P.rmax) < kTauSmallQ * kTauSmallQ) {
         is_small = true;
       } else {
-        double sp, cp;
-        sincos(-(Qx * P.cx + Qy * P.cy), &sp, &cp);
-        const double gr = g[2 * (i * n_q + l)], gi = g[2 * (i * n_q + l) + 1], k = 2.0 / q2;
-        r.gr = (float)(k * (gr * cp - gi * sp));
-        r.gi = (float)(k * (gr * sp + gi * cp));
+        // e^{-iQ.c}: the phase in FP64, less its nearest multiple of 2 pi (FP64), then an FP32
+        // sincos on [-pi, pi]; the record holds FP32 weights, so this loses nothing further
+        const double ph = -(Qx * P.cx + Qy * P.cy);
+        const float pr = (float)fma(-rint(ph * kInvTwoPiD), kTwoPiD, ph);
+        float sp, cp;
+        sincosf(pr, &sp, &cp);
+        const float gr = (float)g[2 * (i * n_q + l)], gi = (float)g[2 * (i * n_q + l) + 1];
+        const float k = 2.0f / (float)q2;
+        r.gr = k * fmaf(gr, cp, -gi * sp);
+        r.gi = k * fmaf(gr, sp, gi * cp);
       }
       rec[i * n_q + l] = r;
     }
@@ -865,8 +878,10 @@ __global__ void __launch_bounds__(kAux) k_bbq(const double* __restrict__ q, cons
 }
 
 // Pair blocks: block b is pair block b - bstart[i] of polygon i (bisection over the exclusive
-// scan bstart of the blocks per polygon); threads <-> its segments; the polygon's Q records
-// stream through the ring (Q chunk blockIdx.y).  Blocks past the last polygon leave at once.
+// scan bstart of the blocks per polygon); thread t <-> its segments t and t + kBwdNT (one Q record
+// load feeds two pairs); the polygon's Q records stream through the ring (Q chunk blockIdx.y).
+// Warps with no segment only wait for and release the tiles (polygons end mid-block: the sizes
+// vary).  Blocks past the last polygon leave at once.
 __global__ void __launch_bounds__(kBwdNT) k_bbwd(const Seg32* __restrict__ segs, int64_t nv,
                                                  const int64_t* __restrict__ off, int64_t np,
                                                  const int64_t* __restrict__ bstart, const int32_t* __restrict__ nblk,
@@ -885,36 +900,54 @@ __global__ void __launch_bounds__(kBwdNT) k_bbwd(const Seg32* __restrict__ segs,
     else hi = mid - 1;
   }
   const int64_t s0 = max((int64_t)0, min(off[lo], nv)), s1 = max(s0, min(off[lo + 1], nv));
-  const int64_t m = s0 + (b - bstart[lo]) * kBwdNT + threadIdx.x;
-  const bool mine = m < s1;
-  float4 F = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int64_t m = s0 + (b - bstart[lo]) * kBbSegs + threadIdx.x, m2 = m + kBwdNT;
+  const bool mine = m < s1, mine2 = m2 < s1;
+  float4 F = make_float4(0.f, 0.f, 0.f, 0.f), F2 = F;
   if (mine) F = reinterpret_cast<const float4*>(segs)[m];
+  if (mine2) F2 = reinterpret_cast<const float4*>(segs)[m2];
+  const bool live = __any_sync(0xffffffffu, mine), live2 = __any_sync(0xffffffffu, mine2);
   const int64_t q0 = (int64_t)blockIdx.y * per_split;
   const int64_t nq = max((int64_t)0, min(per_split, n_q - q0));
   Ring<QRec, kQTile, kBwdNT> ring{slots, full, done, &issued, rec + lo * n_q + q0, nq,
                                   (int)((nq + kQTile - 1) / kQTile)};
   ring.start();
-  CAcc acc[4];
+  CAcc acc[4], acc2[4];
 #pragma unroll
-  for (int f = 0; f < 4; ++f) acc[f].init();
+  for (int f = 0; f < 4; ++f) { acc[f].init(); acc2[f].init(); }
   bool ok = true;
   for (int t = 0; t < ring.ntiles; ++t) {
     if (!ring.wait(t)) { ok = false; break; }
     const QRec* tq = ring.tile(t);
     const int cnt = ring.count(t);
-    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    float a[4] = {0.f, 0.f, 0.f, 0.f}, a2[4] = {0.f, 0.f, 0.f, 0.f};
+    if (live2) {
 #pragma unroll 1
-    for (int j = 0; j < cnt; ++j) seg_adj(tq[j], F, a);
+      for (int j = 0; j < cnt; ++j) {
+        const QRec Q = tq[j];
+        seg_adj(Q, F, a);
+        seg_adj(Q, F2, a2);
+      }
+    } else if (live) {
+#pragma unroll 1
+      for (int j = 0; j < cnt; ++j) seg_adj(tq[j], F, a);
+    }
 #pragma unroll
-    for (int f = 0; f < 4; ++f) acc[f].add(a[f]);
+    for (int f = 0; f < 4; ++f) { acc[f].add(a[f]); acc2[f].add(a2[f]); }
     ring.release(t);
   }
   if (!ok) set_status(status, ST_TIMEOUT);
   ring.finish();
-  if (!ok || !mine) return;
-  double* dst = partial + ((int64_t)blockIdx.y * nv + m) * 4;
+  if (!ok) return;
+  if (mine) {
+    double* dst = partial + ((int64_t)blockIdx.y * nv + m) * 4;
 #pragma unroll
-  for (int f = 0; f < 4; ++f) dst[f] = (double)acc[f].hi + (double)acc[f].lo;
+    for (int f = 0; f < 4; ++f) dst[f] = (double)acc[f].hi + (double)acc[f].lo;
+  }
+  if (mine2) {
+    double* dst = partial + ((int64_t)blockIdx.y * nv + m2) * 4;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) dst[f] = (double)acc2[f].hi + (double)acc2[f].lo;
+  }
 }
 
 // Per vertex: record adjoints of the segment it starts and of the one it ends (Q chunks in
@@ -1227,7 +1260,7 @@ struct BbLayout {
 
 BbLayout bb_layout(int64_t nv, int64_t np, int64_t n_q) {
   BbLayout y{};
-  y.grid = std::max<int64_t>(1, np + (nv + kBwdNT - 1) / kBwdNT);   // at least the pair blocks needed
+  y.grid = std::max<int64_t>(1, np + (nv + kBbSegs - 1) / kBbSegs);   // at least the pair blocks needed
   const int64_t slots = (int64_t)sm_count() * 8;
   const int64_t q_tiles = std::max<int64_t>(1, (n_q + kQTile - 1) / kQTile);
   const int64_t k = std::min<int64_t>({std::max<int64_t>(1, (4 * slots + y.grid - 1) / y.grid), q_tiles, 256});

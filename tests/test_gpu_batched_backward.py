@@ -23,9 +23,11 @@ def torch_dev():
 
 
 def _batch():
-    polys = [synth.star_polygon(3, seed=1), synth.star_polygon(300, seed=2, center=(0.5, -0.25)),
+    # pair blocks hold 256 segments (two per thread): 600 spans three, 257 ends one past a block,
+    # 129 ends one past the first half of a block
+    polys = [synth.star_polygon(3, seed=1), synth.star_polygon(600, seed=2, center=(0.5, -0.25)),
              synth.regular_polygon(17, 0.4), synth.star_polygon(129, seed=3, center=(-0.75, 0.5)),
-             synth.star_polygon(40, seed=4)]
+             synth.star_polygon(40, seed=4), synth.star_polygon(257, seed=5, center=(0.25, 0.75))]
     off = np.concatenate([[0], np.cumsum([p.shape[0] for p in polys])]).astype(np.int64)
     return np.concatenate(polys).astype(np.float32), off
 
