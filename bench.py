@@ -35,15 +35,21 @@ UNIT = "Gpair/s"
 WORKLOAD = "icosphere8_perturbed_q128cubed"
 
 # Algorithmic per-pair instruction counts of the 3D FP32 face term (face_common,
-# face_series / face_series_long / face_edge, face_finish in pft_pairs.cuh):
-# FP32-pipe operations (add/mul/fma/compare/select, the SFU argument scaling) and
-# SFU operations (sin, cos, reciprocal), per branch.
+# face_series* / face_edge, face_finish in pft_pairs.cuh): FP32-pipe operations
+# (add/mul/fma/compare/select, the SFU argument scaling) and SFU operations (sin,
+# cos, reciprocal), per branch.  Each series form costs 24 ops outside the series
+# (projections 15, branch tests 2, finish 7) plus its own: T and T^2 3 and one
+# FMA per coefficient beyond the first of each polynomial in P, and the nesting in T^2.
 OPS = {
-    "short_series": {"fp32": 34, "sfu": 2},   # face-integral series through k = 7 (P < 1/4)
-    "long_series": {"fp32": 42, "sfu": 2},    # through k = 11 (P < 9/4)
-    "xlong_series": {"fp32": 59, "sfu": 2},   # through k = 17 (P < 9)
+    "series_k7": {"fp32": 34, "sfu": 2},      # face-integral series through k = 7 (P < 1/4)
+    "series_k9": {"fp32": 38, "sfu": 2},      # through k = 9 (P < 1)
+    "series_k11": {"fp32": 42, "sfu": 2},     # through k = 11 (P < 9/4)
+    "series_k13": {"fp32": 47, "sfu": 2},     # through k = 13 (P < 4)
+    "series_k17": {"fp32": 59, "sfu": 2},     # through k = 17 (P < 9)
     "edge_sum": {"fp32": 91, "sfu": 7},       # edge sum of Eq. 14, polynomial sinc
 }
+SERIES_BOUNDS = [("series_k7", 0.25), ("series_k9", 1.0), ("series_k11", 2.25),
+                 ("series_k13", 4.0)]         # P bounds of the forms below k = 17 (kP* in pft_pairs.cuh)
 # 2D segment term (Pol2F32::tile): projections 6, u^2 1, Chebyshev sinc 6, range test 1, the
 # SFU argument scaling 1, w*S 1, accumulation 2; beyond |u| > pi the SFU sinc adds the turn
 # reduction and 1/u (6 FP32-pipe + 2 SFU).
@@ -142,10 +148,10 @@ def branch_mix(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0):
 
     Mirrors the kernel's rule on a seeded sample: for one face, a warp holds the
     Q indices base + k*nt + 32*w + lane (k < r, lane < 32); if every one has
-    P < tau^2/4 they all take the short series when every P < min(tau, 1)^2/4,
-    else the long series when every P < min(tau, 3)^2/4, else the extra-long
-    series; otherwise the edge sum (the few pairs below tau_lo^2/4 that the edge
-    branch redoes with the series are counted as edge).
+    P < p_hi = tau^2/4 they all take the first series form whose bound b has
+    p_hi <= b or every P < b (k = 17 when none has); otherwise the edge sum (the
+    few pairs below tau_lo^2/4 that the edge branch redoes with the series are
+    counted as edge).  Thresholds are compared in float32, as the kernel does.
     """
     rng = np.random.default_rng(seed)
     fi = rng.integers(0, f.shape[0], n_warps)
@@ -160,12 +166,16 @@ def branch_mix(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0):
     qq = q[idx]                                          # [w, r*32, 3]
     a0 = np.einsum("wlj,wj->wl", qq, p[:, 0] - g)
     a1 = np.einsum("wlj,wj->wl", qq, p[:, 1] - g)
-    P = a0 * a0 + a0 * a1 + a1 * a1
-    all_hi = np.all(P < 0.25 * tau * tau, axis=1)
-    short = all_hi & np.all(P < 0.25 * min(tau, 1.0) ** 2, axis=1)
-    long_ = all_hi & ~short & np.all(P < 0.25 * min(tau, 3.0) ** 2, axis=1)
-    return {"short_series": float(np.mean(short)), "long_series": float(np.mean(long_)),
-            "xlong_series": float(np.mean(all_hi & ~short & ~long_)), "edge_sum": float(np.mean(~all_hi))}
+    pmax = (a0 * a0 + a0 * a1 + a1 * a1).max(axis=1).astype(np.float32)
+    p_hi = np.float32(0.25 * tau * tau)
+    left = pmax < p_hi                                   # warps that take a series form
+    out = {"edge_sum": float(np.mean(~left))}
+    for name, b in SERIES_BOUNDS:
+        take = left & ((p_hi <= np.float32(b)) | (pmax < np.float32(b)))
+        out[name] = float(np.mean(take))
+        left &= ~take
+    out["series_k17"] = float(np.mean(left))
+    return {k: out[k] for k in OPS}
 
 
 def sfu_sinc_fraction(verts, poly_off, q, n=1 << 16, seed=0):

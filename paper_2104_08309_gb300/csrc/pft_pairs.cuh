@@ -12,12 +12,14 @@ constexpr int kStages = 4;
 // Thresholds on P (see the 3D face term below): p_hi = tau^2/4, p_lo = tau_lo^2/4.
 struct Thr {
   float hi, lo;
-  int longs;    // tau > 1: warps whose faces are not all below kPShort take a longer series
-  int xlongs;   // tau > 3: warps whose faces are not all below kPLong take the extra-long series
+  int longs;    // tau > 1: warps whose faces are not all below kPShort take a longer series (adjoint)
+  int xlongs;   // tau > 3: warps whose faces are not all below kPLong take the extra-long series (adjoint)
 };
 constexpr float kTauLo = 0.05f;
-constexpr float kPShort = 0.25f;   // P below which the short series suffices (tau = 1)
-constexpr float kPLong = 2.25f;    // P below which the long series suffices (tau = 3)
+constexpr float kPShort = 0.25f;   // P below which the short series (k <= 7) suffices (tau = 1)
+constexpr float kP9 = 1.0f;        // P below which the k <= 9 series suffices (tau = 2)
+constexpr float kPLong = 2.25f;    // P below which the long series (k <= 11) suffices (tau = 3)
+constexpr float kP13 = 4.0f;       // P below which the k <= 13 series suffices (tau = 4)
 
 // Resident blocks per SM the register budget is sized for: 16-24 warps of
 // 256 threads, fewer registers per thread for fewer Q points per thread.  The
@@ -73,14 +75,13 @@ __device__ __forceinline__ void seg_pair_f64(double qx, double qy, const Seg64& 
 // (Eq. 13) is taken from its series, Z = i G,
 //   G = sum_k i^k h_k(a) / (k+2)!,   h_k = P h_{k-2} + T h_{k-3},
 // P = a0^2 + a0 a1 + a1^2 (= h_2), T = a0 a1 a2 (= h_3); P < tau^2/4 implies
-// max_l |Q.d_l| < tau.  For P < 1/4 the series is kept through k = 7, for
-// P < 9/4 through k = 11, for P < 9 through k = 17; the omitted terms are
-// below 4e-9, 4e-9 and 1e-9 (|G| <= 1/2).
+// max_l |Q.d_l| < tau.  The series is kept through k = 7 for P < 1/4, k = 9 for
+// P < 1, k = 11 for P < 9/4, k = 13 for P < 4 and k = 17 for P < 9; the omitted
+// terms stay below 4e-9 in each (|G| <= 1/2).
 //
 // Branch choice, per face and warp: the series is taken for all of a thread's
-// Q points when every Q point of every lane of the warp has P < p_hi = tau^2/4
-// -- its short form when every one also has P < 1/4, else its long form when
-// every one has P < 9/4, else its extra-long form;
+// Q points when every Q point of every lane of the warp has P < p_hi = tau^2/4,
+// in the shortest of the five forms whose bound every one of them meets;
 // otherwise the edge sum, except for Q points with P < p_lo = tau_lo^2/4
 // (tau_lo = min(tau, 0.05): below it the edge sum would lose more than ~4 bits
 // to cancellation), which are redone with the short series.  All three evaluate
@@ -133,6 +134,54 @@ __device__ __forceinline__ void face_series_long(float a0, float a1, float P, fl
   D = fmaf(P, D, -8.33333333e-3f);                         // -1/5!
   const float E = fmaf(P, -6.423617749e-10f, 2.505210794e-8f);   // -4/13!, 1/11!
   const float gim = T * fmaf(T2, E, D);
+  zr = -gim;
+  zi = gre;
+}
+
+// Intermediate forms.  With h_k = sum over 2i + 3j = k of C(i + j, i) P^i T^j, the
+// coefficient of P^i T^j is +-C(i + j, i)/(2i + 3j + 2)! (the sign that of i^k), and
+//   G_re = A0(P) + T^2 (A2(P) + T^2 A4(P)),  G_im = T (D1(P) + T^2 (D3(P) + T^2 D5(P)))
+// keep the terms with k <= K.  Omitted terms: k <= 9 on P < 1 below 4e-9, k <= 13 on
+// P < 4 below 3e-9 (|G| <= 1/2).  (A k <= 15 form for 4 <= P < 25/4 would save a
+// further 6 operations per pair there, but the larger loop body ran slower.)
+__device__ __forceinline__ void face_series_k9(float a0, float a1, float P, float& zr, float& zi) {
+  const float T = -(a0 * a1) * (a0 + a1);
+  const float T2 = T * T;
+  float A0 = fmaf(P, 2.755731922e-07f, -2.480158730e-05f);   // 1/10!, -1/8!
+  A0 = fmaf(P, A0, 1.388888889e-03f);                         // 1/6!
+  A0 = fmaf(P, A0, -4.166666667e-02f);                        // -1/4!
+  A0 = fmaf(P, A0, 0.5f);                                     // 1/2!
+  const float A2 = fmaf(P, 8.267195767e-07f, -2.480158730e-05f);   // 3/10!, -1/8!
+  float D1 = fmaf(P, 1.002084335e-07f, -8.267195767e-06f);   // 4/11!, -3/9!
+  D1 = fmaf(P, D1, 3.968253968e-04f);                         // 2/7!
+  D1 = fmaf(P, D1, -8.333333333e-03f);                        // -1/5!
+  const float gre = fmaf(T2, A2, A0);
+  const float gim = T * fmaf(T2, 2.505210839e-08f, D1);      // 1/11!
+  zr = -gim;
+  zi = gre;
+}
+
+__device__ __forceinline__ void face_series_k13(float a0, float a1, float P, float& zr, float& zi) {
+  const float T = -(a0 * a1) * (a0 + a1);
+  const float T2 = T * T;
+  float A0 = fmaf(P, 1.147074560e-11f, -2.087675699e-09f);   // 1/14!, -1/12!
+  A0 = fmaf(P, A0, 2.755731922e-07f);                         // 1/10!
+  A0 = fmaf(P, A0, -2.480158730e-05f);                        // -1/8!
+  A0 = fmaf(P, A0, 1.388888889e-03f);                         // 1/6!
+  A0 = fmaf(P, A0, -4.166666667e-02f);                        // -1/4!
+  A0 = fmaf(P, A0, 0.5f);                                     // 1/2!
+  float A2 = fmaf(P, 1.147074560e-10f, -1.252605419e-08f);   // 10/14!, -6/12!
+  A2 = fmaf(P, A2, 8.267195767e-07f);                         // 3/10!
+  A2 = fmaf(P, A2, -2.480158730e-05f);                        // -1/8!
+  float D1 = fmaf(P, 4.588298239e-12f, -8.029521918e-10f);   // 6/15!, -5/13!
+  D1 = fmaf(P, D1, 1.002084335e-07f);                         // 4/11!
+  D1 = fmaf(P, D1, -8.267195767e-06f);                        // -3/9!
+  D1 = fmaf(P, D1, 3.968253968e-04f);                         // 2/7!
+  D1 = fmaf(P, D1, -8.333333333e-03f);                        // -1/5!
+  float D3 = fmaf(P, 7.647163732e-12f, -6.423617535e-10f);   // 10/15!, -4/13!
+  D3 = fmaf(P, D3, 2.505210839e-08f);                         // 1/11!
+  const float gre = fmaf(T2, fmaf(T2, 1.147074560e-11f, A2), A0);   // 1/14!
+  const float gim = T * fmaf(T2, D3, D1);
   zr = -gim;
   zi = gre;
 }
@@ -400,13 +449,20 @@ struct Pol3F32 {
         pmin = r ? fminf(pmin, P[r]) : P[r];
       }
       if (__all_sync(0xffffffffu, pmax < th.hi)) {
-        // th.longs and th.xlongs are uniform over the grid, so the inner votes are warp-uniform too
-        if (!th.longs || __all_sync(0xffffffffu, pmax < kPShort)) {
+        // the shortest series whose bound holds for the whole warp; th.hi is uniform over the
+        // grid, so a bound at or above it needs no vote and every vote is warp-uniform
+        if (th.hi <= kPShort || __all_sync(0xffffffffu, pmax < kPShort)) {
 #pragma unroll
           for (int r = 0; r < R; ++r) face_series(a0[r], a1[r], P[r], zr[r], zi[r]);
-        } else if (!th.xlongs || __all_sync(0xffffffffu, pmax < kPLong)) {
+        } else if (th.hi <= kP9 || __all_sync(0xffffffffu, pmax < kP9)) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) face_series_k9(a0[r], a1[r], P[r], zr[r], zi[r]);
+        } else if (th.hi <= kPLong || __all_sync(0xffffffffu, pmax < kPLong)) {
 #pragma unroll
           for (int r = 0; r < R; ++r) face_series_long(a0[r], a1[r], P[r], zr[r], zi[r]);
+        } else if (th.hi <= kP13 || __all_sync(0xffffffffu, pmax < kP13)) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) face_series_k13(a0[r], a1[r], P[r], zr[r], zi[r]);
         } else {
 #pragma unroll
           for (int r = 0; r < R; ++r) face_series_xlong(a0[r], a1[r], P[r], zr[r], zi[r]);

@@ -20,40 +20,43 @@ def test_branch_fractions_partition_the_pairs(mesh):
         m = bench.branch_mix(v, f, q, tau=tau, n_warps=512)
         assert set(m) == set(bench.OPS)
         assert abs(sum(m.values()) - 1.0) < 1e-12
-        if tau <= 1.0:
-            assert m["long_series"] == 0.0
-        if tau <= 3.0:
-            assert m["xlong_series"] == 0.0
+        # no form beyond the one whose bound covers p_hi = tau^2/4
+        for name, b in bench.SERIES_BOUNDS:
+            if 0.25 * tau * tau <= b:
+                later = list(bench.OPS)[list(bench.OPS).index(name) + 1:-1]
+                assert all(m[k] == 0.0 for k in later), (tau, name)
+                break
     lo = bench.branch_mix(v, f, q, tau=1.0, n_warps=512)
     hi = bench.branch_mix(v, f, q, tau=3.0, n_warps=512)
     # the same seeded sample: raising tau only moves warps from the edge sum into the series,
-    # and warps with every P < 1/4 keep the short form
+    # and warps with every P < 1/4 keep the k <= 7 form
     assert hi["edge_sum"] <= lo["edge_sum"]
-    assert hi["short_series"] == lo["short_series"]
+    assert hi["series_k7"] == lo["series_k7"]
 
 
 def test_branch_rule_on_hand_made_phases():
-    """One face, Q points along its normal (all phases 0 -> short series) and in its plane
-    at |Q| where P lies between 1/4 and 9/4 (long series at tau = 3, edge sum at tau = 1)."""
+    """One face, Q points along its normal (all phases 0 -> the k <= 7 form) and in its plane
+    at |Q| where P falls into each form's interval, or above tau^2/4 (edge sum)."""
     v = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
     f = np.array([[0, 1, 2]], np.int32)
     along = np.tile([[0.0, 0.0, 5.0]], (256, 1))
     m = bench.branch_mix(v, f, along, tau=3.0, r=2, nt=128, n_warps=16)
-    assert m["short_series"] == 1.0
+    assert m["series_k7"] == 1.0
     # a0 = Q.(p0 - g) with g = (1/3, 1/3, 0): Q = (k, 0, 0) gives a = (-k/3, 2k/3, -k/3), P = k^2/3
-    inplane = np.tile([[1.5, 0.0, 0.0]], (256, 1))             # P = 0.75
-    assert bench.branch_mix(v, f, inplane, tau=3.0, r=2, nt=128, n_warps=16)["long_series"] == 1.0
-    assert bench.branch_mix(v, f, inplane, tau=6.0, r=2, nt=128, n_warps=16)["long_series"] == 1.0
-    assert bench.branch_mix(v, f, inplane, tau=1.0, r=2, nt=128, n_warps=16)["edge_sum"] == 1.0
-    far = np.tile([[4.0, 0.0, 0.0]], (256, 1))                 # P = 16/3
-    assert bench.branch_mix(v, f, far, tau=6.0, r=2, nt=128, n_warps=16)["xlong_series"] == 1.0
-    assert bench.branch_mix(v, f, far, tau=3.0, r=2, nt=128, n_warps=16)["edge_sum"] == 1.0
+    mix = lambda k, tau: bench.branch_mix(v, f, np.tile([[k, 0.0, 0.0]], (256, 1)), tau=tau, r=2, nt=128,
+                                          n_warps=16)
+    for k, form in ((0.75, "series_k7"), (1.5, "series_k9"), (2.25, "series_k11"), (3.0, "series_k13"),
+                    (4.0, "series_k17"), (5.0, "series_k17")):   # P = 0.1875, 0.75, 1.6875, 3, 5.33, 8.33
+        assert mix(k, 6.0)[form] == 1.0, (k, form)
+    assert mix(1.5, 1.0)["edge_sum"] == 1.0
+    assert mix(1.5, 3.0)["series_k9"] == 1.0
+    assert mix(4.0, 3.0)["edge_sum"] == 1.0
 
 
 def test_roofline_arithmetic():
-    mix = {"short_series": 0.25, "long_series": 0.25, "xlong_series": 0.25, "edge_sum": 0.25}
+    mix = {b: 1.0 / len(bench.OPS) for b in bench.OPS}
     ops, issue, achieved, peak = bench.roofline(1e12, 1.0, mix, 152, 2070.0)
-    want = {k: 0.25 * sum(bench.OPS[b][k] for b in bench.OPS) for k in ("fp32", "sfu")}
+    want = {k: sum(bench.OPS[b][k] for b in bench.OPS) / len(bench.OPS) for k in ("fp32", "sfu")}
     assert ops == pytest.approx(want)
     assert issue == pytest.approx(want["fp32"] + want["sfu"])
     assert achieved == pytest.approx(issue * 1e12)

@@ -179,3 +179,62 @@ def _horner32(coef, x):
     for c in coef:
         acc = (acc * x + c).astype(np.float32)
     return acc
+
+
+# Intermediate forms: (j, highest i .. lowest i) of each polynomial, in the order the constants
+# appear in the source (the 1/2 of A0 is written as 0.5f and not listed).
+_MID_LAYOUT = {
+    "void face_series_k9(": (9, 1.0, [(0, 4, 1), (2, 1, 0), (1, 3, 0), (3, 0, 0)]),
+    "void face_series_k13(": (13, 4.0, [(0, 6, 1), (2, 3, 0), (1, 5, 0), (3, 2, 0), (4, 0, 0)]),
+}
+
+
+def _coef(i, j):
+    from math import comb
+    k = 2 * i + 3 * j
+    sign = (1 if k % 4 == 0 else -1) if k % 2 == 0 else (1 if k % 4 == 1 else -1)
+    return sign * comb(i + j, i) / math.factorial(k + 2)
+
+
+def _mid_coefficients(name):
+    K, bound, layout = _MID_LAYOUT[name]
+    c = _floats(_body("pft_pairs.cuh", name))
+    keys = [(i, j) for j, hi, lo in layout for i in range(hi, lo - 1, -1)]
+    assert len(c) == len(keys), name
+    got = dict(zip(keys, c))
+    got[(0, 0)] = 0.5
+    return K, bound, got
+
+
+def test_intermediate_face_series_coefficients():
+    """k <= 9 and k <= 13 forms: the coefficient of P^i T^j is +-C(i + j, i)/(2i + 3j + 2)!, every term
+    with 2i + 3j <= K present exactly once."""
+    for name in _MID_LAYOUT:
+        K, _, got = _mid_coefficients(name)
+        assert set(got) == {(i, j) for j in range(K // 3 + 1) for i in range((K - 3 * j) // 2 + 1)}, name
+        for (i, j), v in got.items():
+            assert abs(v - _coef(i, j)) <= 1e-6 * abs(_coef(i, j)), (name, i, j)
+
+
+def test_intermediate_face_series_truncation_bounds():
+    """With the source's constants, on P below each form's bound, against the converged series:
+    within 4e-9 in FP64 and within a few float32 roundings of |G| <= 1/2 in float32."""
+    for name in _MID_LAYOUT:
+        K, bound, got = _mid_coefficients(name)
+        P, T, g = _exact_G(*_phases(bound))
+        gre = sum(v * P ** i * T ** j for (i, j), v in got.items() if j % 2 == 0)
+        gim = sum(v * P ** i * T ** j for (i, j), v in got.items() if j % 2 == 1)
+        assert np.max(np.abs(gre + 1j * gim - g)) < 4e-9, name
+        f32 = np.float32
+        P32, T32 = P.astype(f32), T.astype(f32)
+        T232 = (T32 * T32).astype(f32)
+        polys = {}
+        for j in sorted({j for _, j in got}):
+            polys[j] = _horner32([f32(got[(i, j)]) for i in range(max(i for i, jj in got if jj == j), -1, -1)], P32)
+        re = np.zeros_like(P32)
+        for j in sorted((j for j in polys if j % 2 == 0), reverse=True):
+            re = (re * T232 + polys[j]).astype(f32)
+        im = np.zeros_like(P32)
+        for j in sorted((j for j in polys if j % 2 == 1), reverse=True):
+            im = (im * T232 + polys[j]).astype(f32)
+        assert np.max(np.abs(re + 1j * (T32 * im) - g)) < 2e-7, name
