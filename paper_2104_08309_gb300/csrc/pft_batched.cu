@@ -30,6 +30,8 @@ namespace {
 constexpr uint64_t kPlanMagic = 0x706674626174636bULL;   // "pftbatck"
 constexpr int64_t kChunk = 4096;                          // segments or faces per item at most
 constexpr int kBThreads = 256;                            // prep / finalize block size
+constexpr double kTwoPiD = 6.283185307179586477;          // 2 pi (FP64)
+constexpr double kInvTwoPiD = 0.1591549430918953358;      // 1 / (2 pi) (FP64)
 
 struct BPlanHeader {
   uint64_t magic;
@@ -377,7 +379,12 @@ __global__ void __launch_bounds__(kBThreads) k_bprep3(const float* __restrict__ 
 
 // Shared finish of one output: s/|Q|^2 * exp(iQ.c) * sum (s = 2 in 2D, where the records hold
 // half the cross product; 1 in 3D), Q = 0 -> area or volume, small |Q| -> FP64 list.
-template <int D>
+// kF32: the sums come from the FP32 policies (relative error ~1e-7), so the factor 2/|Q|^2 (1/|Q|^2
+// in 3D) is an FP32 division and the translation phase an FP32 sincos of Q.c less its nearest
+// multiple of 2 pi (both taken in FP64): about 15 FP64 operations per output instead of about 65,
+// which keeps GB300's narrow FP64 pipe from stalling the warps at the end of every item, for at
+// most ~3e-7 of |F| more error.  The FP64 policies keep FP64 throughout.
+template <int D, bool kF32>
 __device__ __forceinline__ void finish_out(const double* Q, double re, double im, const PolyInfo& pi, int64_t row,
                                            double* out, uint32_t* small, WsHeader* h) {
   double q2 = 0.0, ph = 0.0;
@@ -396,9 +403,18 @@ __device__ __forceinline__ void finish_out(const double* Q, double re, double im
     small[atomicAdd(&h->small_q_count, 1u)] = (uint32_t)row;
     return;
   }
-  const double k = (D == 2 ? 2.0 : 1.0) / q2;
-  double sp, cp;
-  sincos(ph, &sp, &cp);
+  double k, sp, cp;
+  if constexpr (kF32) {
+    const float pr = (float)fma(-rint(ph * kInvTwoPiD), kTwoPiD, ph);
+    float sf, cf;
+    sincosf(pr, &sf, &cf);
+    sp = sf;
+    cp = cf;
+    k = (double)((D == 2 ? 2.0f : 1.0f) / (float)q2);
+  } else {
+    sincos(ph, &sp, &cp);
+    k = (D == 2 ? 2.0 : 1.0) / q2;
+  }
   out[2 * row] = k * (re * cp - im * sp);
   out[2 * row + 1] = k * (re * sp + im * cp);
 }
@@ -540,7 +556,7 @@ __global__ void __launch_bounds__(NT, kBatchedMinBlocks<Pol, R, NT>) k_batched(
         partial[pp.part_base + (int64_t)it.chunk * pp.n_q + local] = f;
       } else {
         const double Qd[3] = {(double)qr[r][0], (double)qr[r][1], (double)qr[r][2]};
-        finish_out<D>(Qd, f.x, f.y, pi, pp.out_base + local, out, small, h);
+        finish_out<D, sizeof(QT) == 4>(Qd, f.x, f.y, pi, pp.out_base + local, out, small, h);
       }
     }
   }
@@ -574,8 +590,13 @@ __global__ void __launch_bounds__(kBThreads) k_bfinal(const BPlanHeader* ph, con
     const int64_t iq = pp.q_begin + l;
     double Q[3] = {0.0, 0.0, 0.0};
     for (int d = 0; d < D; ++d) Q[d] = fp64 ? q[D * iq + d] : (double)(float)q[D * iq + d];
-    if (D == 2) finish_out<2>(Q, re, im, pi, pp.out_base + l, out, small, h);
-    else finish_out<3>(Q, re, im, pi, pp.out_base + l, out, small, h);
+    if (fp64) {
+      if (D == 2) finish_out<2, false>(Q, re, im, pi, pp.out_base + l, out, small, h);
+      else finish_out<3, false>(Q, re, im, pi, pp.out_base + l, out, small, h);
+    } else {
+      if (D == 2) finish_out<2, true>(Q, re, im, pi, pp.out_base + l, out, small, h);
+      else finish_out<3, true>(Q, re, im, pi, pp.out_base + l, out, small, h);
+    }
   }
 }
 

@@ -95,6 +95,28 @@ def test_3d_face_branch_threshold(torch_dev, tau, rng):
         assert rel_err(got, ref, ref[0]) < TOL[prec], (prec, tau)
 
 
+def test_3d_every_series_form(torch_dev):
+    """Each Q point repeated over a whole block (R x NT = 4 x 128), so for every face a warp's P values
+    are equal and the ladder takes exactly the form for that P. |Q| sweeps the box's faces across all
+    five series bounds (k <= 7, 9, 11, 13, 17 for P < 1/4, 1, 9/4, 4, 9) and past tau^2/4 = 9 (edge sum);
+    every output matches the oracle."""
+    v, f = synth.box_mesh(1.25, 0.75, 1.875)
+    d = np.array([0.48, -0.6, 0.64])
+    qd = np.linspace(0.05, 6.0, 120)[:, None] * d[None, :]
+    got = run3d(torch_dev, v, f, np.repeat(qd, 512, axis=0), q_per_thread=4, block_threads=128,
+                face_series_tau=6.0)
+    ref = oracle.ft3d(v, f, qd)
+    assert rel_err(got, np.repeat(ref, 512), 1.25 * 0.75 * 1.875) < TOL["fp32"]
+    # P = a0^2 + a0 a1 + a1^2 of the corner phases about each face's centroid, for every (face, Q)
+    p = v.astype(np.float64)[f]
+    g = p.mean(axis=1)
+    a0, a1 = (np.einsum("kj,fj->kf", qd, p[:, i] - g) for i in (0, 1))
+    P = (a0 * a0 + a0 * a1 + a1 * a1).ravel()
+    edges = [0.0, 0.25, 1.0, 2.25, 4.0, 9.0, np.inf]
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        assert np.count_nonzero((P > lo) & (P < hi)) >= 5, (lo, hi)
+
+
 def test_3d_short_series_taken_whatever_tau(torch_dev, rng):
     """Small faces at small |Q| (every P < 1/4): the short series serves every warp for any
     tau >= 1, so tau = 1, 2, 3 and 6 give bitwise the same FP32 result; the default is tau = 6."""
