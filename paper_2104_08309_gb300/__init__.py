@@ -22,7 +22,7 @@ __all__ = [
     "pft2d_polygons", "pft2d_batched_prepare", "pft2d_polygons_batched", "BatchedPrepared", "pft3d_mesh",
     "pft3d_polymesh", "pft3d_polymesh_backward", "ft3d_poly", "pft2d_polygons_batched_backward", "pft3d_batched_prepare", "pft3d_meshes_batched",
     "pft2d_polygons_backward",
-    "pft3d_mesh_backward", "pft3d_mesh_qgrad", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft3d", "make_options", "Options",
+    "pft3d_mesh_backward", "pft3d_mesh_qgrad", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft2d_batched", "ft3d", "make_options", "Options",
     "PFTError",
     "launch_count", "version",
 ]
@@ -490,7 +490,19 @@ def _autograd():
             gv = pft3d_polymesh_backward(verts.detach(), face_idx, face_off, q, g.contiguous(), options=ctx.options)
             return gv, None, None, None, None
 
-    return _FT2D, _FT3D, _FT3DPoly
+    class _FT2DBatched(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, verts, poly_off, q, options):
+            ctx.save_for_backward(verts, poly_off, q)
+            return pft2d_polygons_batched(verts.detach(), poly_off, q, options=options)
+
+        @staticmethod
+        def backward(ctx, g):
+            verts, poly_off, q = ctx.saved_tensors
+            gv = pft2d_polygons_batched_backward(verts.detach(), poly_off, q, g.contiguous())
+            return gv, None, None, None
+
+    return _FT2D, _FT3D, _FT3DPoly, _FT2DBatched
 
 
 _FNS = None
@@ -512,6 +524,18 @@ def ft3d(verts, faces, q, options=None):
     torch = _torch()
     _FNS = _FNS or _autograd()
     return torch.view_as_complex(_FNS[1].apply(verts, faces, q, options))
+
+
+def ft2d_batched(verts, poly_off, q, options=None):
+    """Differentiable FT_A of each polygon of a batch on a shared Q set, complex128 [n_polys, n_q];
+    grad w.r.t. verts via the batched adjoint (always FP32-compensated: ``options`` go to the forward
+    call only, e.g. its launch shape or precision)."""
+    global _FNS
+    torch = _torch()
+    _FNS = _FNS or _autograd()
+    off = poly_off if (isinstance(poly_off, torch.Tensor) and poly_off.is_cuda) else \
+        _host_i64(poly_off).to(verts.device)
+    return torch.view_as_complex(_FNS[3].apply(verts, off, q, options))
 
 
 def ft3d_poly(verts, face_idx, face_off, q, options=None):
