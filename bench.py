@@ -37,16 +37,16 @@ WORKLOAD = "icosphere8_perturbed_q128cubed"
 # Algorithmic per-pair instruction counts of the 3D FP32 face term (face_common,
 # face_series* / face_edge, face_finish in pft_pairs.cuh): FP32-pipe operations
 # (add/mul/fma/compare/select, the SFU argument scaling) and SFU operations (sin,
-# cos, reciprocal), per branch.  Each series form costs 24 ops outside the series
-# (projections 15, branch tests 2, finish 7) plus its own: T and T^2 3 and one
-# FMA per coefficient beyond the first of each polynomial in P, and the nesting in T^2.
+# cos, reciprocal), per branch.  Each series form costs 25 ops outside the series
+# (projections with P and T 16, branch tests 2, finish 7) plus its own: T^2 1 and
+# one FMA per coefficient beyond the first of each polynomial in P, and the nesting in T^2.
 OPS = {
-    "series_k7": {"fp32": 34, "sfu": 2},      # face-integral series through k = 7 (P < 1/4)
-    "series_k9": {"fp32": 38, "sfu": 2},      # through k = 9 (P < 1)
-    "series_k11": {"fp32": 42, "sfu": 2},     # through k = 11 (P < 9/4)
-    "series_k13": {"fp32": 47, "sfu": 2},     # through k = 13 (P < 4)
-    "series_k17": {"fp32": 59, "sfu": 2},     # through k = 17 (P < 9)
-    "edge_sum": {"fp32": 91, "sfu": 7},       # edge sum of Eq. 14, polynomial sinc
+    "series_k7": {"fp32": 33, "sfu": 2},      # face-integral series through k = 7 (P < 1/4)
+    "series_k9": {"fp32": 37, "sfu": 2},      # through k = 9 (P < 1)
+    "series_k11": {"fp32": 41, "sfu": 2},     # through k = 11 (P < 9/4)
+    "series_k13": {"fp32": 46, "sfu": 2},     # through k = 13 (P < 4)
+    "series_k17": {"fp32": 58, "sfu": 2},     # through k = 17 (P < 9)
+    "edge_sum": {"fp32": 92, "sfu": 7},       # edge sum of Eq. 14, polynomial sinc
 }
 SERIES_BOUNDS = [("series_k7", 0.25), ("series_k9", 1.0), ("series_k11", 2.25),
                  ("series_k13", 4.0)]         # P bounds of the forms below k = 17 (kP* in pft_pairs.cuh)

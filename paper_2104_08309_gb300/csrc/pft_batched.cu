@@ -422,11 +422,14 @@ __device__ __forceinline__ void finish_out(const double* Q, double re, double im
 // Persistent kernel: block b runs items [cta_off[b], cta_off[b+1]) in order.  The
 // segment tiles of consecutive items form one stream through the ring; the last
 // warp to finish a slot issues the tile kStages further on (as in k_fwd).
-// Register budget: as the single-shape kernel, except that the 3D default (4 Q points,
-// 128 threads) keeps 4 blocks per SM here, where the item loop and the in-place finish
-// would otherwise spill at 5.
+// Register budget: as the single-shape kernel, except that the 3D FP32 shapes with 128 threads
+// keep one block per SM fewer here (4 at 4 Q points, 5 at 2), where the item loop and the
+// in-place finish would otherwise spill.
 template <class Pol, int R, int NT>
-constexpr int kBatchedMinBlocks = (Pol::kDim == 3 && R == 4 && NT == 128) ? 4 : kMinBlocks<Pol, R, NT>;
+constexpr int kBatchedMinBlocks = (Pol::kDim == 3 && R == 4 && NT == 128) ? 4
+                                  : (Pol::kDim == 3 && R == 2 && NT == 128 && sizeof(typename Pol::QT) == 4)
+                                      ? 5
+                                      : kMinBlocks<Pol, R, NT>;
 
 template <class Pol, int R, int NT>
 __global__ void __launch_bounds__(NT, kBatchedMinBlocks<Pol, R, NT>) k_batched(

@@ -98,12 +98,25 @@ __device__ __forceinline__ void face_common(float qx, float qy, float qz, const 
   P = fmaf(a0, a0 + a1, a1 * a1);
 }
 
+// As face_common, with T = a0 a1 a2 as well: s1 = a0 + a1 and p1 = a0 a1 give
+// P = s1^2 - p1 and T = -p1 s1.
+__device__ __forceinline__ void face_common_pt(float qx, float qy, float qz, const float4 A, const float4 B,
+                                               const float4 C, float& mu, float& a0, float& a1, float& s, float& P,
+                                               float& T) {
+  mu = fmaf(qx, A.x, fmaf(qy, A.y, qz * A.z));
+  a0 = fmaf(qx, A.w, fmaf(qy, B.x, qz * B.y));
+  a1 = fmaf(qx, B.z, fmaf(qy, B.w, qz * C.x));
+  s = fmaf(qx, C.y, fmaf(qy, C.z, qz * C.w));
+  const float s1 = a0 + a1, p1 = a0 * a1;
+  P = fmaf(s1, s1, -p1);
+  T = -p1 * s1;
+}
+
 // Z = i G from the face-integral series.
 // Short form (P < 1/4, i.e. tau <= 1): h_k through k = 7,
 //   G_re = 1/2! - P/4! + P^2/6! - (P^3 + T^2)/8!,  G_im = T (-1/5! + 2P/7! - 3P^2/9!);
 // the omitted terms (k >= 8) are below 2e-9 (|G| <= 1/2).
-__device__ __forceinline__ void face_series(float a0, float a1, float P, float& zr, float& zi) {
-  const float T = -(a0 * a1) * (a0 + a1);
+__device__ __forceinline__ void face_series(float T, float P, float& zr, float& zi) {
   float gre = fmaf(P, -2.48015873e-5f, 1.38888889e-3f);   // -1/8!, 1/6!
   gre = fmaf(P, gre, -4.16666667e-2f);                     // -1/4!
   gre = fmaf(P, gre, 0.5f);                                // 1/2!
@@ -117,8 +130,7 @@ __device__ __forceinline__ void face_series(float a0, float a1, float P, float& 
 //   h8 = P^4 + 3P T^2, h9 = 4P^3 T + T^3, h10 = P^5 + 6P^2 T^2, h11 = 5P^4 T + 4P T^3;
 // G_re = A(P) + T^2 B(P),  G_im = T (D(P) + T^2 E(P)); the omitted terms (k >= 12)
 // are below 4e-9 (|G| <= 1/2).
-__device__ __forceinline__ void face_series_long(float a0, float a1, float P, float& zr, float& zi) {
-  const float T = -(a0 * a1) * (a0 + a1);
+__device__ __forceinline__ void face_series_long(float T, float P, float& zr, float& zi) {
   const float T2 = T * T;
   float A = fmaf(P, -2.087675588e-9f, 2.75573192e-7f);    // -1/12!, 1/10!
   A = fmaf(P, A, -2.48015873e-5f);                         // -1/8!
@@ -144,8 +156,7 @@ __device__ __forceinline__ void face_series_long(float a0, float a1, float P, fl
 // keep the terms with k <= K.  Omitted terms: k <= 9 on P < 1 below 4e-9, k <= 13 on
 // P < 4 below 3e-9 (|G| <= 1/2).  (A k <= 15 form for 4 <= P < 25/4 would save a
 // further 6 operations per pair there, but the larger loop body ran slower.)
-__device__ __forceinline__ void face_series_k9(float a0, float a1, float P, float& zr, float& zi) {
-  const float T = -(a0 * a1) * (a0 + a1);
+__device__ __forceinline__ void face_series_k9(float T, float P, float& zr, float& zi) {
   const float T2 = T * T;
   float A0 = fmaf(P, 2.755731922e-07f, -2.480158730e-05f);   // 1/10!, -1/8!
   A0 = fmaf(P, A0, 1.388888889e-03f);                         // 1/6!
@@ -161,8 +172,7 @@ __device__ __forceinline__ void face_series_k9(float a0, float a1, float P, floa
   zi = gre;
 }
 
-__device__ __forceinline__ void face_series_k13(float a0, float a1, float P, float& zr, float& zi) {
-  const float T = -(a0 * a1) * (a0 + a1);
+__device__ __forceinline__ void face_series_k13(float T, float P, float& zr, float& zi) {
   const float T2 = T * T;
   float A0 = fmaf(P, 1.147074560e-11f, -2.087675699e-09f);   // 1/14!, -1/12!
   A0 = fmaf(P, A0, 2.755731922e-07f);                         // 1/10!
@@ -191,8 +201,7 @@ __device__ __forceinline__ void face_series_k13(float a0, float a1, float P, flo
 //   G_re = A0(P) + T^2 (A2(P) + T^2 A4(P)),  G_im = T (D1(P) + T^2 (D3(P) + T^2 D5(P))),
 // the coefficient of P^i in A_j / D_j being +-C(i + j, i)/(2i + 3j + 2)!;
 // the omitted terms (k >= 18) are below 1e-9 (|G| <= 1/2).
-__device__ __forceinline__ void face_series_xlong(float a0, float a1, float P, float& zr, float& zi) {
-  const float T = -(a0 * a1) * (a0 + a1);
+__device__ __forceinline__ void face_series_xlong(float T, float P, float& zr, float& zi) {
   const float T2 = T * T;
   float A0 = fmaf(P, 1.561920697e-16f, -4.779477332e-14f);   // 1/18!, -1/16!
   A0 = fmaf(P, A0, 1.147074560e-11f);                         // 1/14!
@@ -440,11 +449,11 @@ struct Pol3F32 {
     for (int i = 0; i < cnt; ++i) {
       const float4* p = reinterpret_cast<const float4*>(t + i);
       const float4 A = p[0], B = p[1], C = p[2];
-      float mu[R], a0[R], a1[R], s[R], P[R], zr[R], zi[R];
+      float mu[R], a0[R], a1[R], s[R], P[R], T[R], zr[R], zi[R];
       float pmax = 0.f, pmin = 0.f;   // over the thread's Q points: the branch tests need only these
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        face_common(q[r][0], q[r][1], q[r][2], A, B, C, mu[r], a0[r], a1[r], s[r], P[r]);
+        face_common_pt(q[r][0], q[r][1], q[r][2], A, B, C, mu[r], a0[r], a1[r], s[r], P[r], T[r]);
         pmax = r ? fmaxf(pmax, P[r]) : P[r];
         pmin = r ? fminf(pmin, P[r]) : P[r];
       }
@@ -453,19 +462,19 @@ struct Pol3F32 {
         // grid, so a bound at or above it needs no vote and every vote is warp-uniform
         if (th.hi <= kPShort || __all_sync(0xffffffffu, pmax < kPShort)) {
 #pragma unroll
-          for (int r = 0; r < R; ++r) face_series(a0[r], a1[r], P[r], zr[r], zi[r]);
+          for (int r = 0; r < R; ++r) face_series(T[r], P[r], zr[r], zi[r]);
         } else if (th.hi <= kP9 || __all_sync(0xffffffffu, pmax < kP9)) {
 #pragma unroll
-          for (int r = 0; r < R; ++r) face_series_k9(a0[r], a1[r], P[r], zr[r], zi[r]);
+          for (int r = 0; r < R; ++r) face_series_k9(T[r], P[r], zr[r], zi[r]);
         } else if (th.hi <= kPLong || __all_sync(0xffffffffu, pmax < kPLong)) {
 #pragma unroll
-          for (int r = 0; r < R; ++r) face_series_long(a0[r], a1[r], P[r], zr[r], zi[r]);
+          for (int r = 0; r < R; ++r) face_series_long(T[r], P[r], zr[r], zi[r]);
         } else if (th.hi <= kP13 || __all_sync(0xffffffffu, pmax < kP13)) {
 #pragma unroll
-          for (int r = 0; r < R; ++r) face_series_k13(a0[r], a1[r], P[r], zr[r], zi[r]);
+          for (int r = 0; r < R; ++r) face_series_k13(T[r], P[r], zr[r], zi[r]);
         } else {
 #pragma unroll
-          for (int r = 0; r < R; ++r) face_series_xlong(a0[r], a1[r], P[r], zr[r], zi[r]);
+          for (int r = 0; r < R; ++r) face_series_xlong(T[r], P[r], zr[r], zi[r]);
         }
       } else {
 #pragma unroll
@@ -473,7 +482,7 @@ struct Pol3F32 {
         if (pmin < th.lo) {
 #pragma unroll
           for (int r = 0; r < R; ++r)
-            if (P[r] < th.lo) face_series(a0[r], a1[r], P[r], zr[r], zi[r]);   // P < tau_lo^2/4 <= 1/4
+            if (P[r] < th.lo) face_series(T[r], P[r], zr[r], zi[r]);   // P < tau_lo^2/4 <= 1/4
         }
       }
 #pragma unroll
