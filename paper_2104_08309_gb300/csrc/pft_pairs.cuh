@@ -457,19 +457,21 @@ struct Pol3F32 {
         pmax = r ? fmaxf(pmax, P[r]) : P[r];
         pmin = r ? fminf(pmin, P[r]) : P[r];
       }
-      if (__all_sync(0xffffffffu, pmax < th.hi)) {
-        // the shortest series whose bound holds for the whole warp; th.hi is uniform over the
-        // grid, so a bound at or above it needs no vote and every vote is warp-uniform
-        if (th.hi <= kPShort || __all_sync(0xffffffffu, pmax < kPShort)) {
+      // the warp's largest P: P >= +0 (it is s1^2 - a0 a1 = a0^2 + a0 a1 + a1^2) or NaN, so its bits
+      // order as unsigned integers, and one reduction replaces a vote per rung of the ladder
+      const float wmax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(pmax)));
+      if (wmax < th.hi) {
+        // the shortest series whose bound holds for the whole warp (wmax and th.hi are uniform)
+        if (th.hi <= kPShort || wmax < kPShort) {
 #pragma unroll
           for (int r = 0; r < R; ++r) face_series(T[r], P[r], zr[r], zi[r]);
-        } else if (th.hi <= kP9 || __all_sync(0xffffffffu, pmax < kP9)) {
+        } else if (th.hi <= kP9 || wmax < kP9) {
 #pragma unroll
           for (int r = 0; r < R; ++r) face_series_k9(T[r], P[r], zr[r], zi[r]);
-        } else if (th.hi <= kPLong || __all_sync(0xffffffffu, pmax < kPLong)) {
+        } else if (th.hi <= kPLong || wmax < kPLong) {
 #pragma unroll
           for (int r = 0; r < R; ++r) face_series_long(T[r], P[r], zr[r], zi[r]);
-        } else if (th.hi <= kP13 || __all_sync(0xffffffffu, pmax < kP13)) {
+        } else if (th.hi <= kP13 || wmax < kP13) {
 #pragma unroll
           for (int r = 0; r < R; ++r) face_series_k13(T[r], P[r], zr[r], zi[r]);
         } else {
