@@ -164,11 +164,13 @@ __device__ __forceinline__ void face_adj_t(const QRec& Q, const float4 A, const 
   face_common(qx, qy, qz, A, B, C, mu, a0, a1, s, P);
   // the forward kernel's rule over the warp's faces: short series when all have
   // P < 1/4 (or this one is below p_lo), long series when all are below 9/4 (and
-  // p_hi), extra-long series when all are below p_hi; the votes are taken by
-  // every lane before any of them branches
-  const bool all_hi = __all_sync(0xffffffffu, P < th.hi);
-  const bool all_short = __all_sync(0xffffffffu, P < kPShort);
-  const bool all_long = __all_sync(0xffffffffu, P < kPLong);
+  // p_hi), extra-long series when all are below p_hi.  All three tests read the
+  // warp's largest P, taken by every lane before any of them branches: P >= +0 or
+  // NaN, so its bits order as unsigned integers and one reduction serves them all.
+  const float wmax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(P)));
+  const bool all_hi = wmax < th.hi;
+  const bool all_short = wmax < kPShort;
+  const bool all_long = wmax < kPLong;
   const bool shorts = (th.longs ? all_short : all_hi) || (P < th.lo);
   const bool longs = !shorts && all_hi && (!th.xlongs || all_long);
   const bool series = shorts || all_hi;
