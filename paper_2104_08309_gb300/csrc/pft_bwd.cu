@@ -165,9 +165,13 @@ __device__ __forceinline__ void face_adj_t(const QRec& Q, const float4 A, const 
   // the forward kernel's rule over the warp's faces: short series when all have
   // P < 1/4 (or this one is below p_lo), long series when all are below 9/4 (and
   // p_hi), extra-long series when all are below p_hi.  All three tests read the
-  // warp's largest P, taken by every lane before any of them branches: P >= +0 or
-  // NaN, so its bits order as unsigned integers and one reduction serves them all.
-  const float wmax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(P)));
+  // warp's largest |P|, taken by every lane before any of them branches.  Here P can
+  // be -0 or a tiny negative subnormal (a1 a1 underflows before the fused add when
+  // the phases are below ~1e-20, as for a tiny Q beside large ones in k_qgrad), so
+  // the sign bit is cleared: the bits of |P| (and of NaN, above +inf) order as
+  // unsigned integers, and one reduction serves all three tests.
+  const float wmax =
+      __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(P) & 0x7fffffffu));
   const bool all_hi = wmax < th.hi;
   const bool all_short = wmax < kPShort;
   const bool all_long = wmax < kPLong;

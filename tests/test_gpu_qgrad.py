@@ -88,3 +88,20 @@ def test_many_small_q(torch_dev, rng):
     got = _qgrad(torch_dev, v, f, q, g)
     ref = oracle.qgrad3d(v, f, q, g)
     assert np.max(np.abs(got - ref)) < 1e-9 * _scale(v, f, g)
+
+
+def test_tiny_q_beside_large_q(torch_dev, rng):
+    """A Q of size ~1e-25 as the first lane of every warp (one Q per thread), the other 31 lanes at
+    |Q| up to 25: the tiny Q's P can round to -0 or a negative subnormal, and must not pull its
+    warp onto the k <= 7 series.  Every entry against the oracle."""
+    v, f = synth.perturbed_icosphere(3, seed=16, amp=0.08)
+    v = (v + np.array([0.125, -0.25, 0.1875], np.float32)).astype(np.float32)
+    q = rng.uniform(-25, 25, (1024, 3))
+    d = rng.normal(size=(32, 3))
+    q[::32] = d * 1e-25
+    q = q.astype(np.float32).astype(np.float64)
+    g = rng.normal(size=q.shape[0]) + 1j * rng.normal(size=q.shape[0])
+    got = _qgrad(torch_dev, v, f, q, g)
+    ref = oracle.qgrad3d(v, f, q, g)
+    assert np.max(np.abs(got - ref)) < 1e-5 * _scale(v, f, g)
+    assert np.max(np.abs(got[::32] - ref[::32])) < 1e-9 * _scale(v, f, g)

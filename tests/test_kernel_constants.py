@@ -238,3 +238,36 @@ def test_intermediate_face_series_truncation_bounds():
         for j in sorted((j for j in polys if j % 2 == 1), reverse=True):
             im = (im * T232 + polys[j]).astype(f32)
         assert np.max(np.abs(re + 1j * (T32 * im) - g)) < 2e-7, name
+
+
+def test_p_bits_order_as_unsigned():
+    """The 3D branch ladders take the warp's largest P as the unsigned maximum of float32 bits.
+    Forward: P = fmaf(s1, s1, -p1) with s1 = a0 + a1, p1 = a0 a1 is never negative nor -0, so its
+    bits are used as they are.  Adjoint: P = fmaf(a0, a0 + a1, a1 a1) can be -0 or a negative
+    subnormal (a1 a1 underflows before the fused add), so the kernel clears the sign bit; those
+    values are far below every threshold, so ordering by |P| takes the same branch.  Emulated in
+    float32 (the product inside the FMA is exact in float64; the sum is rounded to float64 and then
+    to float32, which can move the value but not its sign), with signed zeros, subnormals and huge
+    values."""
+    rng = np.random.default_rng(11)
+    f32 = np.float32
+    vals = np.concatenate([rng.normal(size=200000) * 10.0 ** rng.uniform(-40, 18, 200000),
+                           [0.0, -0.0, 1e-45, -1e-45, 1e-38, -1e-38, 3e38, -3e38]]).astype(f32)
+    a0 = rng.choice(vals, 400000)
+    a1 = np.where(rng.uniform(size=400000) < 0.2, -a0 / f32(2), rng.choice(vals, 400000)).astype(f32)
+    with np.errstate(over="ignore", invalid="ignore"):
+        s1 = (a0 + a1).astype(f32)
+        p1 = (a0 * a1).astype(f32)
+        P_fwd = (s1.astype(np.float64) * s1.astype(np.float64) - p1.astype(np.float64)).astype(f32)
+        P_adj = (a0.astype(np.float64) * (a0 + a1).astype(f32).astype(np.float64)
+                 + (a1 * a1).astype(f32).astype(np.float64)).astype(f32)
+    fin = np.isfinite(P_fwd)
+    assert np.all(P_fwd[fin] >= 0) and not np.any(np.signbit(P_fwd[fin]))
+    neg = np.isfinite(P_adj) & np.signbit(P_adj)
+    assert np.any(neg)                                   # the case the kernel guards against occurs
+    assert np.all(np.abs(P_adj[neg]) < 1e-37)            # and only far below kPShort = 1/4
+    # unsigned order of the bits of non-negative floats (and +inf, NaN above them) follows the values
+    x = np.sort(np.abs(vals[np.isfinite(vals)]))
+    bits = x.view(np.uint32)
+    assert np.all(np.diff(bits.astype(np.int64)) >= 0)
+    assert np.uint32(0x7F800000) > bits.max() and np.float32(np.nan).view(np.uint32) > np.uint32(0x7F800000)
