@@ -232,5 +232,30 @@ def qgrad3d(verts, faces, q, g, threads=None) -> np.ndarray:
     return out
 
 
+def qgrad2d(verts, q, g, loop_off=None, threads=None) -> np.ndarray:
+    """dL/dQ [n_q, 2] = Re(conj(g_Q) dF/dQ) of the 2D transform, g_Q = dL/dRe F + i dL/dIm F.
+
+    As qgrad3d: the derivative from its definition, central differences of ft2d at steps h and h/2
+    combined by Richardson extrapolation (error O(h^4)), h = 1e-3 / max|r|, in FP64.
+    """
+    v, _ = _loops(verts, loop_off)
+    q = _f64(q, 2)
+    g = np.asarray(g).reshape(-1)
+    h = 1e-3 / max(float(np.max(np.linalg.norm(v, axis=1))), 1e-300)
+    steps = []
+    for j in range(2):
+        for hh in (h, 0.5 * h):
+            e = np.zeros(2)
+            e[j] = hh
+            steps += [q + e, q - e]
+    F = ft2d(verts, np.concatenate(steps), loop_off, threads=threads).reshape(len(steps), q.shape[0])
+    out = np.empty((q.shape[0], 2))
+    for j in range(2):
+        d1 = (F[4 * j] - F[4 * j + 1]) / (2 * h)
+        d2 = (F[4 * j + 2] - F[4 * j + 3]) / h
+        out[:, j] = np.real(np.conj(g) * (4.0 * d2 - d1) / 3.0)
+    return out
+
+
 def max_threads() -> int:
     return int(_load().orc_max_threads())

@@ -63,3 +63,19 @@ def ft3d_tets(verts, faces, q, n=14):
         ph = np.exp(1j * (l1[None, :] * qa[:, None] + l2[None, :] * qb[:, None] + l3[None, :] * qc[:, None]))
         out[i] = np.sum(det[:, None] * w[None, :] * ph)
     return out
+
+
+def moment2d_fan(verts, q, n=24):
+    """i times the first moment, i * integral of r exp(iQ.r) over a CCW polygon ([n_q, 2]): the
+    Q-derivative of the transform, by the same signed triangles (0, p_j, p_{j+1})."""
+    v = np.asarray(verts, dtype=np.float64)
+    q = np.atleast_2d(np.asarray(q, dtype=np.float64))
+    l1, l2, w = tri_rule(n)
+    p0, p1 = v, np.roll(v, -1, axis=0)
+    det = p0[:, 0] * p1[:, 1] - p0[:, 1] * p1[:, 0]
+    pts = l1[None, :, None] * p0[:, None, :] + l2[None, :, None] * p1[:, None, :]
+    out = np.empty((q.shape[0], 2), dtype=np.complex128)
+    for i, Q in enumerate(q):
+        ph = (det[:, None] * w[None, :]) * np.exp(1j * (pts @ Q))
+        out[i] = 1j * np.einsum("sp,spd->d", ph, pts)
+    return out
