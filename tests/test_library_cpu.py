@@ -69,6 +69,16 @@ def test_workspace_sizes(lib):
     assert lib.pft3d_polymesh_workspace_size(8, 17, 6, 100, ctypes.byref(o)) == 0     # < 3 indices per face
     bad = _capi.Options(face_series_tau=6.5)
     assert lib.pft3d_workspace_size(3, 1, 1, ctypes.byref(bad)) == 0
+    # adjoint-side sizes: Q records (32 B) and small-row lists (4 B) per (polygon, Q) row, segment records
+    # and FP64 partials per vertex; the adjoints run in FP32 only, so FP64 options size to 0
+    nv, npol, nq = 2675209, 4096, 4096
+    sb = lib.pft2d_batched_backward_workspace_size(nv, npol, nq, ctypes.byref(o))
+    assert sb >= 256 + 36 * npol * nq + 16 * nv + 32 * nv and sb % 256 == 0
+    assert lib.pft2d_batched_backward_workspace_size(nv, npol, nq, ctypes.byref(o64)) == 0
+    assert lib.pft2d_batched_backward_workspace_size(-1, npol, nq, ctypes.byref(o)) == 0
+    sq = lib.pft3d_qgrad_workspace_size(40992, 81920, 32768, ctypes.byref(o))
+    assert sq >= 256 + 81920 * 48 + 32768 * 32 and sq % 256 == 0
+    assert lib.pft3d_qgrad_workspace_size(40992, 81920, 32768, ctypes.byref(o64)) == 0
 
 
 def test_argument_errors_are_synchronous(lib):
