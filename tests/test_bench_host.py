@@ -84,3 +84,21 @@ def test_roofline2d_bounds():
     r1 = bench.roofline2d(1e12, 1.0, 1.0, 152, 2070.0)
     assert r1["bound"] == "sfu"                      # 4 SFU results / 16 lanes > 28 issue slots / 128
     assert r1["peak_gpair_s"] == pytest.approx(152 * 2070e6 * 16 / 4 / 1e9)
+
+
+def test_traffic_figure_only_for_the_profiled_sources(monkeypatch):
+    """roofline.traffic comes from the committed ncu summary while the kernel sources hash to the value
+    recorded there, and is None as soon as they differ."""
+    h = bench.kernel_source_hash()
+    assert len(h) == 16 and int(h, 16) >= 0
+    path = bench.os.path.join(bench.ROOT, "profiles", "k_fwd_dram_icosphere8_q128cubed.txt")
+    kv = dict(l.split(":", 1) for l in open(path).read().splitlines() if ":" in l)
+    recorded = kv["source_sha256_16"].strip()
+    t = bench.traffic_from_profile()
+    if recorded == h:
+        assert t == float(kv["dram_bytes_per_launch_full_size"])
+        assert t == float(kv["dram_bytes_read"]) + float(kv["dram_bytes_write"])
+    else:
+        assert t is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.traffic_from_profile() is None
