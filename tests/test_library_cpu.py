@@ -92,6 +92,8 @@ def test_argument_errors_are_synchronous(lib):
     assert lib.pft3d_mesh(fake, 3, fake, 1, fake, 1, fake, fake, 16, ctypes.byref(o), None) == 4
     bad = _capi.Options(q_per_thread=3)
     assert lib.pft3d_mesh(fake, 3, fake, 1, fake, 1, fake, fake, 1 << 20, ctypes.byref(bad), None) == 7
+    bad = _capi.Options(precision=1, q_per_thread=4, block_threads=256)      # FP64: at most 2 Q per thread
+    assert lib.pft3d_mesh(fake, 3, fake, 1, fake, 1, fake, fake, 1 << 20, ctypes.byref(bad), None) == 7
     bad = _capi.Options(precision=5)
     assert lib.pft2d_polygons(fake, 3, fake, 1, fake, 1, fake, fake, 1 << 20, ctypes.byref(bad), None) == 1
     assert lib.pft2d_polygons(None, 3, fake, 1, fake, 1, fake, fake, 1 << 20, None, None) == 1
