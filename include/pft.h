@@ -311,6 +311,20 @@ int pft3d_mesh_noalloc(const float* verts, int64_t n_verts, const int32_t* faces
  */
 int pft_status(const void* ws, void* stream);
 
+/*
+ * Self-test of the failure handling around the copies (no counterpart in the paper).
+ * Every wait of the kernels on an mbarrier is bounded; when it runs out the kernel
+ * sets the timeout bit of the status word in its workspace and returns, so the
+ * context stays usable.  This call exercises that path: it clears the 256-byte
+ * header at `ws` (device, 256-byte aligned, ws_bytes >= 256) and launches one block
+ * that polls an mbarrier `polls` times (1 .. 2^20).  With arrive = 0 nothing
+ * completes the barrier's phase, the wait runs out, and pft_status(ws) then returns
+ * PFT_ERR_TIMEOUT; with arrive = 1 the block arrives first, the wait succeeds and
+ * pft_status returns PFT_OK.  Errors: PFT_ERR_WORKSPACE (ws), PFT_ERR_INVALID_ARG
+ * (polls, arrive), PFT_ERR_CUDA (launch).  Asynchronous on `stream`.
+ */
+int pft_selftest_wait(void* ws, size_t ws_bytes, uint32_t polls, int arrive, void* stream);
+
 /* Static English text for a code (never NULL). */
 const char* pft_status_string(int code);
 

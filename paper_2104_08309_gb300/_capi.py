@@ -48,6 +48,7 @@ SIGNATURES = {
     "pft2d_polygons_batched": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_size,
                                               c_vp, c_vp]),
     "pft3d_mesh": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_size, c_vp, c_vp]),
+    "pft_selftest_wait": (ctypes.c_int, [c_vp, c_size, ctypes.c_uint32, ctypes.c_int, c_vp]),
     "pft3d_batched_workspace_size": (c_size, [c_i64, c_vp, c_i64, c_vp, c_i64, c_vp]),
     "pft3d_batched_prepare": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_size, c_vp, c_vp, c_vp]),
     "pft3d_meshes_batched": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp,

@@ -97,6 +97,13 @@ def test_argument_errors_are_synchronous(lib):
     bad = _capi.Options(precision=5)
     assert lib.pft2d_polygons(fake, 3, fake, 1, fake, 1, fake, fake, 1 << 20, ctypes.byref(bad), None) == 1
     assert lib.pft2d_polygons(None, 3, fake, 1, fake, 1, fake, fake, 1 << 20, None, None) == 1
+    # the bounded-wait self-test checks its arguments before any device work
+    assert lib.pft_selftest_wait(None, 256, 64, 0, None) == 4
+    assert lib.pft_selftest_wait(ctypes.c_void_p(256 + 8), 256, 64, 0, None) == 4
+    assert lib.pft_selftest_wait(fake, 16, 64, 0, None) == 4
+    assert lib.pft_selftest_wait(fake, 256, 0, 0, None) == 1
+    assert lib.pft_selftest_wait(fake, 256, (1 << 20) + 1, 0, None) == 1
+    assert lib.pft_selftest_wait(fake, 256, 64, 2, None) == 1
 
 
 def test_python_binding_refuses_cpu_tensors():
