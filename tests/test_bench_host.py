@@ -102,3 +102,38 @@ def test_traffic_figure_only_for_the_profiled_sources(monkeypatch):
         assert t is None
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
     assert bench.traffic_from_profile() is None
+
+
+def _fn_body(name):
+    import os
+    import re
+    text = open(os.path.join(bench.ROOT, "paper_2104_08309_gb300", "csrc", "pft_pairs.cuh")).read()
+    i = text.index(name)
+    body = text[text.index("{", i) + 1:text.index("\n}\n", i)]
+    return re.sub(r"//[^\n]*", "", body)
+
+
+def _arith_ops(body):
+    """FP32-pipe operations written in a device function body: each fmaf, each binary * + -
+    between operands (unary minus on a product folds into the FMA or multiply, so it is not
+    counted)."""
+    import re
+    n = body.count("fmaf(")
+    n += len(re.findall(r"[\w\)\]] \* [\w\(-]", body))
+    n += len(re.findall(r"[\w\)\]] [+-] [\w\(]", body))
+    return n
+
+
+def test_ops_table_matches_the_source():
+    """bench.OPS is the roofline's per-pair operation count: each series form's entry is the 25
+    operations outside the series plus the arithmetic written in its function, and the 16
+    projection operations (mu, a0, a1, s, then s1, p1, P, T) are those of face_common_pt."""
+    assert _arith_ops(_fn_body("void face_common_pt(")) == 16
+    # the finish: 6 written here plus the argument scaling inside __sincosf = the 7 of the count
+    assert _arith_ops(_fn_body("void face_finish(")) == 6
+    forms = {"series_k7": "void face_series(", "series_k9": "void face_series_k9(",
+             "series_k11": "void face_series_long(", "series_k13": "void face_series_k13(",
+             "series_k17": "void face_series_xlong("}
+    for key, fn in forms.items():
+        assert bench.OPS[key]["fp32"] == 25 + _arith_ops(_fn_body(fn)), key
+        assert bench.OPS[key]["sfu"] == 2
