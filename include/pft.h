@@ -295,7 +295,12 @@ int pft_backward_last_launch_count(void);
  *    contents; calls whose GPU work overlaps (several streams or host threads)
  *    race on it, so serialise them.
  *  - The first call on each device looks up the array's address (with that
- *    device current); make it before any stream capture begins.
+ *    device current); make it before any stream capture begins.  Later calls
+ *    made outside stream capture look it up again (so a context recreated after
+ *    cudaDeviceReset is followed); a call inside a capture uses the address
+ *    cached by the last call outside one, so do not reset the device between
+ *    that call and the capture.
+ *  - Sizes or options that pft3d_mesh rejects are rejected with the same code.
  *  - Device-detected input errors are recorded in the shared scratch, which
  *    callers cannot read: validate indices and coordinates beforehand, or use
  *    pft3d_mesh and pft_status() where that matters.

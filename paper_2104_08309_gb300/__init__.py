@@ -287,11 +287,15 @@ def pft3d_mesh_noalloc(verts, faces, q, out, *, options=None, stream=None):
 
     For callers that must not allocate at call time (stream capture, host
     applications that own all device memory): ``out`` ([n_q, 2] float64, CUDA)
-    is required and nothing is allocated here or in the library.  Calls whose
+    is required, every tensor must already be contiguous (no copies are made),
+    and nothing is allocated here or in the library.  Calls whose
     GPU work overlaps share the scratch and race; the first call on a device
     must come before any stream capture.
     """
     torch = _torch()
+    for t, name in ((verts, "verts"), (faces, "faces"), (q, "q")):
+        if isinstance(t, torch.Tensor) and not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous: pft3d_mesh_noalloc makes no copies")
     v = _dev(verts, torch.float32, "verts", 3)
     f = _dev(faces, torch.int32, "faces", 3)
     qq = _dev(q, torch.float64, "q", 3)
@@ -494,12 +498,16 @@ def _autograd():
         @staticmethod
         def forward(ctx, verts, poly_off, q, options):
             ctx.save_for_backward(verts, poly_off, q)
+            ctx.precision = make_options(options).precision
             return pft2d_polygons_batched(verts.detach(), poly_off, q, options=options)
 
         @staticmethod
         def backward(ctx, g):
             verts, poly_off, q = ctx.saved_tensors
-            gv = pft2d_polygons_batched_backward(verts.detach(), poly_off, q, g.contiguous())
+            # the forward's precision goes to the adjoint, which refuses FP64 (it has an FP32 path
+            # only); the forward's launch shape does not apply to it
+            gv = pft2d_polygons_batched_backward(verts.detach(), poly_off, q, g.contiguous(),
+                                                 options={"precision": ctx.precision})
             return gv, None, None, None
 
     return _FT2D, _FT3D, _FT3DPoly, _FT2DBatched
@@ -528,11 +536,16 @@ def ft3d(verts, faces, q, options=None):
 
 def ft2d_batched(verts, poly_off, q, options=None):
     """Differentiable FT_A of each polygon of a batch on a shared Q set, complex128 [n_polys, n_q];
-    grad w.r.t. verts via the batched adjoint (always FP32-compensated: ``options`` go to the forward
-    call only, e.g. its launch shape or precision)."""
+    grad w.r.t. verts via the batched adjoint, which runs in FP32 with compensated sums.  ``options``
+    set the forward call (launch shape, precision); a gradient of an FP64 forward is refused (raised
+    here when ``verts`` requires grad) rather than silently computed in FP32."""
     global _FNS
     torch = _torch()
     _FNS = _FNS or _autograd()
+    if (make_options(options).precision == PFT_FP64 and torch.is_grad_enabled()
+            and isinstance(verts, torch.Tensor) and verts.requires_grad):
+        raise ValueError("ft2d_batched: the batched adjoint has no FP64 path; use precision='fp32' "
+                         "for a differentiable batch, or detach verts")
     off = poly_off if (isinstance(poly_off, torch.Tensor) and poly_off.is_cuda) else \
         _host_i64(poly_off).to(verts.device)
     return torch.view_as_complex(_FNS[3].apply(verts, off, q, options))

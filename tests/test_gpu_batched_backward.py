@@ -115,3 +115,18 @@ def test_ft2d_batched_autograd(torch_dev, rng):
     for i in range(off.size - 1):
         ref = oracle.grad2d(v[off[i]:off[i + 1]], q, g[i])
         assert np.max(np.abs(got[off[i]:off[i + 1]] - ref)) / np.max(np.abs(ref)) < GTOL, i
+
+
+def test_ft2d_batched_refuses_fp64_gradient(torch_dev):
+    """The batched adjoint has only an FP32 path: asking for a gradient of an FP64 forward raises
+    instead of silently differentiating in FP32; without grad the FP64 forward runs."""
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    v, off = _batch()
+    qd = torch.from_numpy(np.array([[0.0, 0.0], [1.5, -2.0]])).to(dev)
+    vt = torch.from_numpy(v).to(dev).requires_grad_(True)
+    with pytest.raises(ValueError):
+        pft.ft2d_batched(vt, off, qd, options={"precision": "fp64"})
+    F = pft.ft2d_batched(vt.detach(), off, qd, options={"precision": "fp64"})
+    ref = oracle.ft2d_batched(v, off, qd.cpu().numpy())
+    assert np.max(np.abs(F.cpu().numpy() - ref)) < 1e-12 * np.max(np.abs(ref))

@@ -89,17 +89,18 @@ def test_mesh_vs_bruteforce_tets(level, amp, rng):
 
 
 def _paper_mesh():
-    path = os.environ.get("PFT_PAPER_PATH", "/root/reference/PAPER.md")
-    if not os.path.exists(path):
-        pytest.skip("paper text not available")
-    text = open(path).read()
-    start = text.index('twospheres_surfacemesh = """')
-    body = text[start:].split('"""')[1].lstrip("\\\n").splitlines()
-    assert body[0].strip() == "surfacemesh"
-    n = int(body[1])
-    pts = np.array([[float(x) for x in line.split()] for line in body[2:2 + n]])
-    m = int(body[2 + n])
-    tri = np.array([[int(x) for x in line.split()] for line in body[3 + n:3 + n + m]]) - 1
+    """The two-sphere surface mesh of Sec. 4.4 (83 nodes, 160 triangles), stored as printed in the
+    paper's appendix data under tests/golden/."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "two_spheres_mesh.txt")
+    lines = [l for l in open(path).read().splitlines() if l and not l.startswith("#")]
+    tag, n = lines[0].split()
+    assert tag == "points"
+    n = int(n)
+    pts = np.array([[float(x) for x in line.split()] for line in lines[1:1 + n]])
+    tag, m = lines[1 + n].split()
+    assert tag == "triangles"
+    m = int(m)
+    tri = np.array([[int(x) for x in line.split()] for line in lines[2 + n:2 + n + m]]) - 1
     return pts, tri
 
 

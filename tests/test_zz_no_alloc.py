@@ -2,8 +2,9 @@
 
 It serves callers that cannot allocate device memory when they need a
 transform (stream capture, host applications that own all device memory).
-Its result must match pft3d_mesh with a caller workspace, on two calls in a
-row (the second sees the first call's leftovers in the shared scratch), and
+Its result must equal pft3d_mesh with a caller workspace bit for bit, on two
+calls in a row (the second sees the first call's leftovers in the shared
+scratch), and
 problems too large for its fixed 32 MiB scratch must be refused up front.
 This file is named to run last, so a failure here cannot hide other tests.
 """
@@ -43,7 +44,6 @@ def test_noalloc_matches_workspace_call_twice(torch_dev):
     assert lib.pft3d_mesh(vd.data_ptr(), v.shape[0], fd.data_ptr(), f.shape[0], qd.data_ptr(), q.shape[0],
                           ref.data_ptr(), ws.data_ptr(), need, ctypes.byref(opts), stream) == 0
     assert lib.pft_status(ws.data_ptr(), stream) == 0
-    vol = abs(float(ref[np.flatnonzero(np.all(q == 0, axis=1))[0], 0]))
     for call in range(2):
         out = torch.full((q.shape[0], 2), float("nan"), dtype=torch.float64, device=dev)
         rc = lib.pft3d_mesh_noalloc(vd.data_ptr(), v.shape[0], fd.data_ptr(), f.shape[0], qd.data_ptr(),
@@ -51,8 +51,8 @@ def test_noalloc_matches_workspace_call_twice(torch_dev):
         assert rc == 0, (call, lib.pft_status_string(rc))
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
-        err = (out - ref).abs().max().item() / vol
-        assert err < 1e-5, (call, err)
+        # the same kernels with the same launch plan in a fixed summation order: bit for bit
+        assert torch.equal(out, ref), (call, (out - ref).abs().max().item())
 
 
 def test_noalloc_refuses_problems_beyond_its_scratch(torch_dev):
@@ -60,8 +60,12 @@ def test_noalloc_refuses_problems_beyond_its_scratch(torch_dev):
     from paper_2104_08309_gb300 import _capi
     lib = _capi.load()
     fake = ctypes.c_void_p(256)          # never dereferenced: the size check comes first
-    # 2M Q points need > 32 MiB of partial sums alone
-    rc = lib.pft3d_mesh_noalloc(fake, 3, fake, 1, fake, 2_000_000, fake, None, None)
+    # 3M Q points: their partial sums alone (3e6 x 16 B = 45.8 MiB) exceed the 32 MiB
+    rc = lib.pft3d_mesh_noalloc(fake, 3, fake, 1, fake, 3_000_000, fake, None, None)
     assert rc == 9
     assert b"32 MiB" in lib.pft_status_string(rc)
+    # what pft3d_mesh refuses is refused with its code: a negative size, an unsupported launch shape
     assert lib.pft3d_mesh_noalloc(fake, -1, fake, 1, fake, 1, fake, None, None) == 1
+    bad = _capi.Options()
+    bad.q_per_thread = 3
+    assert lib.pft3d_mesh_noalloc(fake, 3, fake, 1, fake, 1, fake, ctypes.byref(bad), None) == 7
