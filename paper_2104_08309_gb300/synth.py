@@ -303,15 +303,30 @@ def q_grid_3d(n: int, L: float) -> np.ndarray:
     return np.stack([qx.ravel(), qy.ravel(), qz.ravel()], axis=1)
 
 
-def q_subsample(q: np.ndarray, n: int, seed: int, include_zero: bool = True) -> np.ndarray:
-    """Seeded subset of the rows of q (without replacement); keeps Q = 0 if present."""
+def q_subsample_indices(q: np.ndarray, n: int, seed: int, include_zero: bool = True) -> np.ndarray:
+    """Sorted indices of a seeded subset of the rows of q (without replacement); keeps Q = 0 if present."""
     rng = np.random.default_rng(seed)
     idx = rng.choice(q.shape[0], size=min(n, q.shape[0]), replace=False)
     if include_zero:
         z = np.flatnonzero(np.all(q == 0.0, axis=1))
         if z.size and z[0] not in idx:
             idx[0] = z[0]
-    return q[np.sort(idx)]
+    return np.sort(idx)
+
+
+def q_subsample(q: np.ndarray, n: int, seed: int, include_zero: bool = True) -> np.ndarray:
+    """Seeded subset of the rows of q (without replacement); keeps Q = 0 if present."""
+    return q[q_subsample_indices(q, n, seed, include_zero)]
+
+
+# The seeded 4,096-point Q subsample of the 128^3 grid on which the 1.31M-face mesh is checked
+# against the FP64 oracle (it includes Q = 0).
+C5_SUBSAMPLE = (4096, 5)
+
+
+def c5_subsample_indices(q: np.ndarray) -> np.ndarray:
+    n, seed = C5_SUBSAMPLE
+    return q_subsample_indices(q, n, seed, include_zero=True)
 
 
 # ----------------------------------------------------------------------------

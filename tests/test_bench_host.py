@@ -137,3 +137,16 @@ def test_ops_table_matches_the_source():
     for key, fn in forms.items():
         assert bench.OPS[key]["fp32"] == 25 + _arith_ops(_fn_body(fn)), key
         assert bench.OPS[key]["sfu"] == 2
+
+
+def test_survey_count_fraction_and_error_stats():
+    # 82 FP32-pipe ops per pair on 128 lanes bound the SFU's 7/16: 0.640625 SM cycles per pair
+    n_sm, clk = 152, 2070.0
+    peak = n_sm * clk * 1e6 / (82 / 128)
+    assert abs(bench.survey_count_frac(peak * 2.0, 2.0, n_sm, clk) - 1.0) < 1e-12
+    assert abs(bench.survey_count_frac(peak * 0.5, 1.0, n_sm, clk) - 0.5) < 1e-12
+    got = np.array([1.0, 2.0, 3.0 + 1j, 4.0]) + 0j
+    ref = np.array([1.0, 2.5, 3.0, 1.0]) + 0j
+    st = bench.err_stats(got, ref, -2.0)      # |errors| / 2 = 0, 0.25, 0.5, 1.5
+    assert st["max"] == 1.5 and st["median"] == 0.375
+    assert abs(st["p99"] - (0.5 + 0.97 * 1.0)) < 1e-12
