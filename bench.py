@@ -79,7 +79,7 @@ def parse():
     p.add_argument("--block-threads", type=int, default=128)
     p.add_argument("--tau", type=float, default=0.0, help="face_series_tau (0 = library default)")
     p.add_argument("--no-extra", action="store_true", help="skip the secondary paths (batched 2D, adjoint)")
-    p.add_argument("--only", choices=["batched", "adjoint", "polymesh", "batched3d"], default=None,
+    p.add_argument("--only", choices=["batched", "adjoint", "polymesh", "batched3d", "voxels"], default=None,
                    help="run one secondary path alone and print its result (for profiler captures)")
     return p.parse_args()
 
@@ -599,6 +599,50 @@ def bench_adjoint(dev, warmup, steps):
             "launches_adjoint": launches_adj}
 
 
+def bench_sphere_voxels(dev):
+    """Sec. 4.3's comparison along Q_x = 0 .. 60 through the GPU path: the unit sphere voxelised with
+    cube side d = 0.2 (the closed surface of the 552 cubes, pft3d_polymesh) and icospheres of
+    subdivision 2 and 5 (pft3d_mesh), each against the sphere's closed form (Eq. 23); a table at
+    a few Q_x and where the voxel transform's deviation peaks beyond Q_x = 15."""
+    import torch
+    import paper_2104_08309_gb300 as pft
+    from paper_2104_08309_gb300 import synth
+    d = 0.2
+    qx = np.arange(0, 241) * 0.25
+    q = np.stack([qx, 0 * qx, 0 * qx], axis=1)
+    qd = torch.from_numpy(q).to(dev)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        exact = np.where(qx == 0, 4 * np.pi / 3, 4 * np.pi * (np.sin(qx) - qx * np.cos(qx)) / qx ** 3)
+
+    def c(out):
+        o = out.cpu().numpy()
+        return o[:, 0] + 1j * o[:, 1]
+
+    occ = synth.voxel_ball(10, 1.0, d)
+    v, idx, off = synth.voxel_surface(occ, d)
+    vox = c(pft.pft3d_polymesh(torch.from_numpy(v).to(dev), torch.from_numpy(idx).to(dev),
+                               torch.from_numpy(off).to(dev), qd, check_status=True))
+    ico = {}
+    for level in (2, 5):
+        vi, fi = synth.icosphere(level)
+        ico[level] = c(pft.pft3d_mesh(torch.from_numpy(vi).to(dev), torch.from_numpy(fi).to(dev), qd,
+                                      check_status=True))
+    far = qx >= 15.0
+    dev_vox = np.abs(vox - exact)
+    pick = [0, 20, 40, 80, 100, 112, 117, 120, 126, 140, 160, 200, 240]
+    return {"workload": "unit sphere: 552 cubes of side 0.2 (voxels) vs icospheres of subdivision 2 (320 "
+                        "triangles) and 5 (20,480), Q along x from 0 to 60",
+            "voxel_cubes": int(occ.sum()), "two_pi_over_d": 2 * np.pi / d,
+            "voxel_peak_deviation_qx": float(qx[far][np.argmax(dev_vox[far])]),
+            "max_deviation_qx_ge_15": {"voxels": float(np.max(dev_vox[far])),
+                                       "icosphere2": float(np.max(np.abs(ico[2] - exact)[far])),
+                                       "icosphere5": float(np.max(np.abs(ico[5] - exact)[far]))},
+            "table": {"qx": [float(qx[i]) for i in pick], "sphere_eq23": [float(exact[i]) for i in pick],
+                      "voxels": [float(vox[i].real) for i in pick],
+                      "icosphere2": [float(ico[2][i].real) for i in pick],
+                      "icosphere5": [float(ico[5][i].real) for i in pick]}}
+
+
 KERNEL_SOURCES = ("pft_fwd.cu", "pft_pairs.cuh", "pft_common.cuh", "pft_kernels.cuh", "pft_api.cu")
 
 
@@ -642,7 +686,7 @@ def main():
         from paper_2104_08309_gb300 import build as pbuild
         pbuild.build()
         fn = {"batched": bench_batched, "adjoint": bench_adjoint, "polymesh": bench_polymesh,
-              "batched3d": bench_batched3d}[args.only]
+              "batched3d": bench_batched3d, "voxels": lambda d, w, s: bench_sphere_voxels(d)}[args.only]
         print(json.dumps({"path": args.only, **fn(dev, args.warmup, args.steps)}))
         return 0
     import torch
@@ -836,7 +880,8 @@ def main():
                                                                                           args.steps),
                                    "polymesh3d_star65536prism_q64cubed": bench_polymesh(dev, args.warmup,
                                                                                         args.steps),
-                                   "batched3d_1024meshes_q32cubed": bench_batched3d(dev, args.warmup, args.steps)}
+                                   "batched3d_1024meshes_q32cubed": bench_batched3d(dev, args.warmup, args.steps),
+                                   "sphere_vs_voxels_qx": bench_sphere_voxels(dev)}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

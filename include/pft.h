@@ -277,6 +277,24 @@ int pft3d_mesh_qgrad(const float* verts, int64_t n_verts, const int32_t* faces, 
                      const double* q, int64_t n_q, const double* grad_out, double* grad_q,
                      void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
 
+/*
+ * Q-gradient of a loss on FT_A (2D loops): grad_q[n_q][2] float64 receives
+ * dL/dQ = Re(conj(g_Q) dF(Q)/dQ) for grad_out [n_q][2] as above.  Not in the
+ * paper; the derivative of its segment sum (Sec. 2, Eq. 6) with respect to Q:
+ * with F = e^{iQ.c} (2/|Q|^2) S and S = sum over segments of
+ * -i w sinc(u) e^{i phi} (phi = Q.m, u = Q.h, w = Qx hy - Qy hx for the midpoint
+ * m and half edge vector h, relative to the bounding-box centre c),
+ *   dF/dQ = F (i c - 2Q/|Q|^2) + e^{iQ.c} (2/|Q|^2) dS/dQ,
+ * the last term from the reverse pass of every (Q, segment) pair in FP32 with
+ * compensated sums, accumulated per Q; Q = 0 and |Q| max|r - c| < 0.25 in FP64 from
+ * the derivative of the fan-triangle series.  Arguments, options and errors as
+ * for pft2d_polygons_backward (malformed loop_off sets PFT_ERR_OFFSETS).
+ */
+size_t pft2d_qgrad_workspace_size(int64_t n_verts, int64_t n_loops, int64_t n_q, const pft_options* opts);
+int pft2d_polygons_qgrad(const float* verts, int64_t n_verts, const int64_t* loop_off, int64_t n_loops,
+                         const double* q, int64_t n_q, const double* grad_out, double* grad_q,
+                         void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
+
 /* Kernel launches enqueued by the most recent backward call on this host thread. */
 int pft_backward_last_launch_count(void);
 

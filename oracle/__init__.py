@@ -257,5 +257,38 @@ def qgrad2d(verts, q, g, loop_off=None, threads=None) -> np.ndarray:
     return out
 
 
+def _voxel_centres(occ, d):
+    """Centres of the occupied cubes of side d on the grid centred on the origin: cube (i, j, k)
+    spans [(i - n_x/2) d, (i + 1 - n_x/2) d] x ... (the layout of synth.voxel_surface)."""
+    occ = np.asarray(occ, dtype=bool)
+    n = np.array(occ.shape, dtype=np.float64)
+    return (np.argwhere(occ).astype(np.float64) + 0.5 - 0.5 * n) * d
+
+
+def ft3d_voxels(occ, d, q) -> np.ndarray:
+    """FT of the solid union of the occupied cubes (the voxelised shape of Sec. 4.3), by its plain
+    definition: the sum over the cubes of the integral of exp(iQ.r) over each, i.e. the box closed
+    form of Sec. 4.2 for a = b = c = d about the cube's centre c_v,
+    exp(iQ.c_v) prod_k d sin(Q_k d/2)/(Q_k d/2)."""
+    c = _voxel_centres(occ, d)
+    q = _f64(q, 3)
+    u = 0.5 * d * q
+    with np.errstate(invalid="ignore", divide="ignore"):
+        s = np.where(u == 0.0, 1.0, np.sin(u) / np.where(u == 0.0, 1.0, u))
+    box = d ** 3 * np.prod(s, axis=1)
+    return box * np.exp(1j * (q @ c.T)).sum(axis=1)
+
+
+def ft3d_voxel_points(occ, d, q) -> np.ndarray:
+    """The gridded transform of the same voxels: each occupied cube taken as a point of weight d^3
+    at its centre, d^3 sum_v exp(iQ.c_v) -- what a direct sum over the voxel grid (or a DFT of the
+    occupancy) gives.  Shifting one component of Q by 2 pi / d multiplies every term by the same
+phase (-1 when the grid has an even number of cubes along that axis), so |F| repeats with that
+period: the replica of the Q = 0 peak is the gridding artefact."""
+    c = _voxel_centres(occ, d)
+    q = _f64(q, 3)
+    return d ** 3 * np.exp(1j * (q @ c.T)).sum(axis=1)
+
+
 def max_threads() -> int:
     return int(_load().orc_max_threads())

@@ -22,7 +22,7 @@ __all__ = [
     "pft2d_polygons", "pft2d_batched_prepare", "pft2d_polygons_batched", "BatchedPrepared", "pft3d_mesh",
     "pft3d_polymesh", "pft3d_polymesh_backward", "ft3d_poly", "pft2d_polygons_batched_backward", "pft3d_batched_prepare", "pft3d_meshes_batched",
     "pft2d_polygons_backward",
-    "pft3d_mesh_backward", "pft3d_mesh_qgrad", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft2d_batched", "ft3d", "make_options", "Options",
+    "pft3d_mesh_backward", "pft3d_mesh_qgrad", "pft2d_polygons_qgrad", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft2d_batched", "ft3d", "make_options", "Options",
     "PFTError",
     "launch_count", "version",
 ]
@@ -405,6 +405,31 @@ def pft3d_mesh_qgrad(verts, faces, q, grad_out, *, options=None, out=None, ws=No
     return out
 
 
+def pft2d_polygons_qgrad(verts, q, grad_out, loop_off=None, *, options=None, out=None, ws=None, stream=None,
+                         check_status=False):
+    """dL/dQ [n_q, 2] float64 from grad_out [n_q, 2] = (dL/dRe F, dL/dIm F) (2D loops)."""
+    torch = _torch()
+    v = _dev(verts, torch.float32, "verts", 2)
+    qq = _dev(q, torch.float64, "q", 2)
+    g = _dev(grad_out, torch.float64, "grad_out", 2)
+    if loop_off is None:
+        loop_off = torch.tensor([0, v.shape[0]], dtype=torch.int64, device=v.device)
+    off = _dev(loop_off.to(v.device), torch.int64, "loop_off")
+    o = make_options(options)
+    lib = load()
+    nv, nl, nq = v.shape[0], off.numel() - 1, qq.shape[0]
+    nb = lib.pft2d_qgrad_workspace_size(nv, nl, nq, ctypes.byref(o))
+    ws = _ws(nb, v.device, ws)
+    out = torch.empty(nq, 2, dtype=torch.float64, device=v.device) if out is None else out
+    st = _stream(stream, v.device)
+    check(lib.pft2d_polygons_qgrad(v.data_ptr(), nv, off.data_ptr(), nl, qq.data_ptr(), nq, g.data_ptr(),
+                                   out.data_ptr(), ws.data_ptr(), ws.numel(), ctypes.byref(o), st),
+          "pft2d_polygons_qgrad")
+    if check_status:
+        check(lib.pft_status(ws.data_ptr(), st), "pft2d_polygons_qgrad (device status)")
+    return out
+
+
 def pft2d_polygons_batched_backward(verts, poly_off, q, grad_out, *, options=None, out=None, ws=None, stream=None,
                                     check_status=False):
     """dL/dverts [n_v, 2] float32 for a batch of polygons on a shared Q set, from grad_out
@@ -456,13 +481,17 @@ def _autograd():
         def forward(ctx, verts, q, loop_off, options):
             ctx.save_for_backward(verts, q, loop_off)
             ctx.options = options
-            return pft2d_polygons(verts.detach(), q, loop_off, options=options)
+            return pft2d_polygons(verts.detach(), q.detach(), loop_off, options=options)
 
         @staticmethod
         def backward(ctx, g):
             verts, q, loop_off = ctx.saved_tensors
-            gv = pft2d_polygons_backward(verts.detach(), q, g.contiguous(), loop_off, options=ctx.options)
-            return gv, None, None, None
+            g = g.contiguous()
+            gv = pft2d_polygons_backward(verts.detach(), q.detach(), g, loop_off, options=ctx.options) \
+                if ctx.needs_input_grad[0] else None
+            gq = pft2d_polygons_qgrad(verts.detach(), q.detach(), g, loop_off, options=ctx.options) \
+                if ctx.needs_input_grad[1] else None
+            return gv, gq, None, None
 
     class _FT3D(torch.autograd.Function):
         @staticmethod
@@ -517,7 +546,7 @@ _FNS = None
 
 
 def ft2d(verts, q, loop_off=None, options=None):
-    """Differentiable FT_A(Q) as complex128 [n_q]; grad w.r.t. verts via the adjoint kernel."""
+    """Differentiable FT_A(Q) as complex128 [n_q]; gradients w.r.t. verts and q via the adjoint kernels."""
     global _FNS
     torch = _torch()
     _FNS = _FNS or _autograd()

@@ -63,6 +63,9 @@ SIGNATURES = {
                                                        c_size, c_vp, c_vp]),
     "pft3d_qgrad_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_vp]),
     "pft3d_mesh_qgrad": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp, c_size, c_vp, c_vp]),
+    "pft2d_qgrad_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_vp]),
+    "pft2d_polygons_qgrad": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp, c_size,
+                                            c_vp, c_vp]),
     "pft3d_polymesh_backward_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_i64, c_vp]),
     "pft3d_polymesh_backward": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp,
                                                c_vp, c_size, c_vp, c_vp]),

@@ -634,6 +634,177 @@ __global__ void k_qsmall_fin(int64_t nf, const double* __restrict__ q, const dou
   }
 }
 
+// ---------------------------------------------------------------------------
+// Q-gradient (2D): the same structure in the plane.  F = e^{iQ.c} (2/|Q|^2) S with
+// S = sum over segments of T = -i w sinc(u) e^{i phi}, phi = Q.m, u = Q.h,
+// w = Qx hy - Qy hx (m the midpoint, h half the edge vector; Sec. 2, Eq. 6), so
+//   dF/dQ = F (i c - 2 Q/|Q|^2) + e^{iQ.c} (2/|Q|^2) dS/dQ,
+// the second part being sum over segments of Re(conj(gt) dT/dQ) with gt from k_bq<2>
+// (scale 2).  phi, u and w are bilinear in Q and the record, so the reverse pass of
+// a pair gives Qbar = phib m + ub h + wb (hy, -hx).  k_qgrad2d: thread <-> Q, segment
+// records streamed through the bulk-copy ring, FP64 partials per segment chunk.
+// ---------------------------------------------------------------------------
+constexpr int kSTile = 128;         // segment records per shared-memory tile of k_qgrad2d
+constexpr int kQG2 = 4;             // partial fields per (chunk, Q): S.re, S.im, Qbar.xy
+
+__device__ __forceinline__ void seg_qadj(const QRec& Q, const float4 s, float& jr, float& ji, float& bx, float& by) {
+  const float ph = fmaf(Q.qx, s.x, Q.qy * s.y);
+  const float u = fmaf(Q.qx, s.z, Q.qy * s.w);
+  const float w = fmaf(Q.qx, s.w, -Q.qy * s.z);
+  float sn, cs;
+  __sincosf(ph, &sn, &cs);
+  float S, dS;
+  sinc_d(u, S, dS);
+  const float ws = w * S;
+  jr = fmaf(ws, sn, jr);                        // T = w S (sin - i cos), as the forward's segment term
+  ji = fmaf(-ws, cs, ji);
+  const float A = fmaf(Q.gr, sn, -Q.gi * cs);   // Re(conj(gt)(sin - i cos))
+  const float B = fmaf(Q.gr, cs, Q.gi * sn);    // dA/dph
+  const float wb = S * A, ub = w * A * dS, phb = ws * B;
+  bx = fmaf(phb, s.x, fmaf(ub, s.z, fmaf(wb, s.w, bx)));
+  by = fmaf(phb, s.y, fmaf(ub, s.w, fmaf(-wb, s.z, by)));
+}
+
+__global__ void __launch_bounds__(kBwdNT) k_qgrad2d(const Seg32* __restrict__ segs, int64_t n_segs,
+                                                    int64_t per_split, const QRec* __restrict__ rec, int64_t n_q,
+                                                    double* __restrict__ partial, uint32_t* status) {
+  __shared__ __align__(128) Seg32 slots[kStages * kSTile];
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ int done[kStages];
+  __shared__ int issued;
+  const int64_t i = blockIdx.x * (int64_t)kBwdNT + threadIdx.x;
+  QRec Q{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // lanes past the end: Q = 0, weight 0
+  if (i < n_q) Q = rec[i];
+  const int64_t s0 = (int64_t)blockIdx.y * per_split;
+  const int64_t ns = max((int64_t)0, min(per_split, n_segs - s0));
+  Ring<Seg32, kSTile, kBwdNT> ring{slots, full, done, &issued, segs + s0, ns, (int)((ns + kSTile - 1) / kSTile)};
+  ring.start();
+  CAcc acc[kQG2];
+#pragma unroll
+  for (int f = 0; f < kQG2; ++f) acc[f].init();
+  bool ok = true;
+  for (int t = 0; t < ring.ntiles; ++t) {
+    if (!ring.wait(t)) { ok = false; break; }
+    const float4* ts = reinterpret_cast<const float4*>(ring.tile(t));
+    const int cnt = ring.count(t);
+    float jr = 0.f, ji = 0.f, bx = 0.f, by = 0.f;
+#pragma unroll 2
+    for (int j = 0; j < cnt; ++j) seg_qadj(Q, ts[j], jr, ji, bx, by);
+    acc[0].add(jr);
+    acc[1].add(ji);
+    acc[2].add(bx);
+    acc[3].add(by);
+    ring.release(t);
+  }
+  if (!ok) set_status(status, ST_TIMEOUT);
+  ring.finish();
+  if (!ok || i >= n_q) return;
+  double* dst = partial + ((int64_t)blockIdx.y * n_q + i) * kQG2;
+#pragma unroll
+  for (int f = 0; f < kQG2; ++f) dst[f] = (double)acc[f].hi + (double)acc[f].lo;
+}
+
+// Per Q (not in the small-|Q| list): fixed-order FP64 sum of the chunk partials,
+// F = e^{iQ.c} 2 S/|Q|^2 and dL/dQ = Re(conj(g) F (i c - 2Q/|Q|^2)) + Qbar.
+__global__ void k_qfinal2d(const double* __restrict__ q, const double* __restrict__ g, int64_t n_q,
+                           const double* __restrict__ partial, int ks, const WsHeader* h, double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_q) return;
+  const double Q[2] = {(double)(float)q[2 * i], (double)(float)q[2 * i + 1]};   // as the FP32 pairs used it
+  const double q2 = Q[0] * Q[0] + Q[1] * Q[1];
+  const double rmax = (double)__uint_as_float(h->rmax_bits);
+  if (q2 == 0.0 || sqrt(q2) * rmax < kTauSmallQ) return;   // k_qsmall2d's (same test as k_bq)
+  double v[kQG2] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = 0; k < ks; ++k)
+    for (int f = 0; f < kQG2; ++f) v[f] += partial[((int64_t)k * n_q + i) * kQG2 + f];
+  const double c[2] = {h->center[0], h->center[1]};
+  double sp, cp;
+  sincos(Q[0] * c[0] + Q[1] * c[1], &sp, &cp);
+  const double Fr = 2.0 * (v[0] * cp - v[1] * sp) / q2, Fi = 2.0 * (v[0] * sp + v[1] * cp) / q2;
+  const double gr = g[2 * i], gi = g[2 * i + 1];
+  const double re = gr * Fr + gi * Fi, im = gr * Fi - gi * Fr;   // Re and Im of conj(g) F
+  for (int d = 0; d < 2; ++d) out[2 * i + d] = re * (-2.0 * Q[d] / q2) - im * c[d] + v[2 + d];
+}
+
+// Q = 0 and small |Q| in 2D, FP64: the fan of signed triangles (c, p_j, p_{j+1}) of every
+// loop, S0 = sum det * series2(x) with x_k = Q.(p_k - c) (the apex node is 0), and
+// dS0/dQ = sum det * sum_k i series3(x, x_k) (p_k - c) (a node repeated: the derivative of
+// the complete homogeneous polynomials); dF/dQ = e^{iQ.c} (i c S0 + dS0/dQ).  Chunked over
+// the segments and spread over all blocks as k_qsmall_part.
+constexpr int kQsF2 = 6;            // FP64 fields per slot: S0 (re, im), dS0/dQ (re, im) x 2
+
+__global__ void __launch_bounds__(kAux) k_qsmall2d_part(const float* __restrict__ v, int64_t nv,
+                                                        const int64_t* __restrict__ off, int64_t nl,
+                                                        const double* __restrict__ q, const WsHeader* h,
+                                                        const int32_t* list, int64_t slots,
+                                                        double* __restrict__ part) {
+  __shared__ double sh[kAux / 32];
+  const uint32_t count = h->small_q_count;   // <= n_q <= slots
+  const int64_t nch = qsmall_chunks(count, nv, slots);
+  const int64_t per = (nv + nch - 1) / nch;
+  const double c[2] = {h->center[0], h->center[1]};
+  for (int64_t u = blockIdx.x; u < (int64_t)count * nch; u += gridDim.x) {
+    const int64_t e = u / nch, ch = u % nch;
+    const int64_t i = list[e];
+    const double Q[2] = {(double)(float)q[2 * i], (double)(float)q[2 * i + 1]};
+    double acc[kQsF2] = {0, 0, 0, 0, 0, 0};
+    const int64_t j1 = min(nv, (ch + 1) * per);
+    for (int64_t j = ch * per + threadIdx.x; j < j1; j += kAux) {
+      int64_t lo = 0, hi = nl;   // loop of vertex j
+      while (lo + 1 < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= j) lo = mid; else hi = mid;
+      }
+      const int64_t k = (j + 1 < off[lo + 1]) ? j + 1 : off[lo];
+      if (k < 0 || k >= nv) continue;
+      const double P[2][2] = {{(double)v[2 * j] - c[0], (double)v[2 * j + 1] - c[1]},
+                              {(double)v[2 * k] - c[0], (double)v[2 * k + 1] - c[1]}};
+      double x[3] = {Q[0] * P[0][0] + Q[1] * P[0][1], Q[0] * P[1][0] + Q[1] * P[1][1], 0.0};
+      const double det = P[0][0] * P[1][1] - P[1][0] * P[0][1];
+      double sr, si;
+      simplex_series<2, 2, 16>(x, sr, si);
+      acc[0] += det * sr;
+      acc[1] += det * si;
+      for (int n = 0; n < 2; ++n) {
+        x[2] = x[n];
+        double tr, ti;
+        simplex_series<3, 3, 16>(x, tr, ti);
+        for (int d = 0; d < 2; ++d) {   // i (tr + i ti) P_nd = (-ti + i tr) P_nd
+          acc[2 + 2 * d] += -det * ti * P[n][d];
+          acc[3 + 2 * d] += det * tr * P[n][d];
+        }
+      }
+    }
+    for (int k = 0; k < kQsF2; ++k) {
+      const double t = block_sum_aux(acc[k], sh);
+      if (threadIdx.x == 0) part[u * kQsF2 + k] = t;
+    }
+  }
+}
+
+__global__ void k_qsmall2d_fin(int64_t nv, const double* __restrict__ q, const double* __restrict__ g,
+                               const WsHeader* h, const int32_t* list, int64_t slots,
+                               const double* __restrict__ part, double* __restrict__ out) {
+  const uint32_t count = h->small_q_count;
+  const int64_t nch = qsmall_chunks(count, nv, slots);
+  const double c[2] = {h->center[0], h->center[1]};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = list[e];
+    double acc[kQsF2] = {0, 0, 0, 0, 0, 0};
+    for (int64_t ch = 0; ch < nch; ++ch)
+      for (int k = 0; k < kQsF2; ++k) acc[k] += part[(e * nch + ch) * kQsF2 + k];
+    const double Q[2] = {(double)(float)q[2 * i], (double)(float)q[2 * i + 1]};
+    double sp, cp;
+    sincos(Q[0] * c[0] + Q[1] * c[1], &sp, &cp);
+    const double gr = g[2 * i], gi = g[2 * i + 1];
+    for (int d = 0; d < 2; ++d) {
+      const double Dr = -c[d] * acc[1] + acc[2 + 2 * d], Di = c[d] * acc[0] + acc[3 + 2 * d];
+      const double dr = Dr * cp - Di * sp, di = Dr * sp + Di * cp;
+      out[2 * i + d] = gr * dr + gi * di;
+    }
+  }
+}
+
 template <int D, int NF>
 __global__ void __launch_bounds__(kBwdNT) k_bwd(const void* __restrict__ items, int64_t n_items,
                                                 const QRec* __restrict__ rec, int64_t n_q, int64_t per_split,
@@ -1257,6 +1428,41 @@ QgLayout qg_layout(int64_t n_faces, int64_t n_q) {
   return y;
 }
 
+// 2D Q-gradient workspace: header, area partials, segment records, Q records, small-|Q|
+// list, kQG2 FP64 partials per (segment chunk, Q), small-|Q| slots.
+QgLayout qg2_layout(int64_t n_segs, int64_t n_prep, int64_t n_q) {
+  QgLayout y{};
+  const int64_t seg_tiles = std::max<int64_t>(1, (n_segs + kSTile - 1) / kSTile);
+  const int64_t q_blocks = std::max<int64_t>(1, (n_q + kBwdNT - 1) / kBwdNT);
+  int occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_qgrad2d, kBwdNT, 0) != cudaSuccess || occ < 1) occ = 1;
+  const int64_t slots = (int64_t)sm_count() * occ;
+  const int kmax = (int)std::max<int64_t>(1, std::min<int64_t>(64, seg_tiles / 2));
+  int k = 0, best_k = 1;
+  double best_eff = -1.0;
+  for (int c = 1; c <= kmax; ++c) {   // smallest split that fills whole waves (last one >= 97 %)
+    const double waves = (double)(q_blocks * c) / (double)slots;
+    const double eff = waves / std::ceil(waves);
+    if (q_blocks * c >= slots && eff >= 0.97) { k = c; break; }
+    if (eff > best_eff + 1e-9) { best_eff = eff; best_k = c; }
+  }
+  if (k == 0) k = best_k;
+  const int64_t tiles_per = (seg_tiles + k - 1) / k;
+  y.per_split = tiles_per * kSTile;
+  y.ks = (int)((seg_tiles + tiles_per - 1) / tiles_per);
+  y.nblk = std::max(1, prep_blocks(n_prep));
+  size_t o = al(sizeof(WsHeader));
+  y.mparts = o;  o = al(o + sizeof(double) * (size_t)y.nblk);
+  y.items = o;   o = al(o + sizeof(Seg32) * (size_t)std::max<int64_t>(n_segs, 1));
+  y.qrec = o;    o = al(o + sizeof(QRec) * (size_t)std::max<int64_t>(n_q, 1));
+  y.small = o;   o = al(o + sizeof(int32_t) * (size_t)std::max<int64_t>(n_q, 1));
+  y.partial = o; o = al(o + sizeof(double) * kQG2 * (size_t)y.ks * (size_t)std::max<int64_t>(n_q, 1));
+  y.slots = std::max<int64_t>(kQsUnits, n_q);
+  y.spart = o;   o = al(o + sizeof(double) * kQsF2 * (size_t)y.slots);
+  y.total = o;
+  return y;
+}
+
 // Batched 2D adjoint workspace.
 struct BbLayout {
   size_t segs, pc, nblk, bstart, btot, rec, small, scnt, partial, total;
@@ -1526,6 +1732,54 @@ int pft3d_mesh_qgrad(const float* verts, int64_t n_verts, const int32_t* faces, 
   PFT_BWD_LAUNCH();
   k_qsmall_fin<<<blocks(n_q, kAux), kAux, 0, st>>>(n_faces, q, grad_out, h, at<int32_t>(ws, y.small), y.slots,
                                                    at<double>(ws, y.spart), grad_q);
+  PFT_BWD_LAUNCH();
+  return PFT_OK;
+}
+
+size_t pft2d_qgrad_workspace_size(int64_t n_verts, int64_t n_loops, int64_t n_q, const pft_options* opts) {
+  Thr th;
+  if (n_verts < 0 || n_loops < 0 || n_q < 0 || check_opts(opts, th) != PFT_OK) return 0;
+  return qg2_layout(n_verts, std::max<int64_t>(n_verts, n_loops + 1), n_q).total;
+}
+
+int pft2d_polygons_qgrad(const float* verts, int64_t n_verts, const int64_t* loop_off, int64_t n_loops,
+                         const double* q, int64_t n_q, const double* grad_out, double* grad_q, void* ws,
+                         size_t ws_bytes, const pft_options* opts, void* stream) {
+  g_bwd_launches = 0;
+  Thr th;
+  if (int e = check_opts(opts, th)) return e;
+  if (n_verts < 0 || n_loops < 0 || n_q < 0) return PFT_ERR_INVALID_ARG;
+  if (n_verts > 0 && (verts == nullptr || loop_off == nullptr || n_loops == 0)) return PFT_ERR_INVALID_ARG;
+  if (n_q > 0 && (q == nullptr || grad_out == nullptr || grad_q == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (n_q > INT32_MAX) return PFT_ERR_UNSUPPORTED;
+  const QgLayout y = qg2_layout(n_verts, std::max<int64_t>(n_verts, n_loops + 1), n_q);
+  if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < y.total) return PFT_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader* h = at<WsHeader>(ws, 0);
+  if (launch_init_header(h, st) != cudaSuccess) return PFT_ERR_CUDA;
+  ++g_bwd_launches;
+  if (n_q == 0) return PFT_OK;
+  if (n_verts == 0)
+    return cudaMemsetAsync(grad_q, 0, sizeof(double) * 2 * (size_t)n_q, st) == cudaSuccess ? PFT_OK : PFT_ERR_CUDA;
+  if (launch_bbox(verts, n_verts, 2, h, st) != cudaSuccess) return PFT_ERR_CUDA;
+  if (launch_prep2d(verts, n_verts, loop_off, n_loops, h, at<void>(ws, y.items), false, at<double>(ws, y.mparts),
+                    y.nblk, st) != cudaSuccess)
+    return PFT_ERR_CUDA;
+  g_bwd_launches += 2;
+  k_bq<2><<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, h, 2.0, at<QRec>(ws, y.qrec), at<int32_t>(ws, y.small));
+  PFT_BWD_LAUNCH();
+  dim3 grid(blocks(n_q, kBwdNT), (unsigned)y.ks);
+  k_qgrad2d<<<grid, kBwdNT, 0, st>>>(at<Seg32>(ws, y.items), n_verts, y.per_split, at<QRec>(ws, y.qrec), n_q,
+                                     at<double>(ws, y.partial), &h->status);
+  PFT_BWD_LAUNCH();
+  k_qfinal2d<<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, at<double>(ws, y.partial), y.ks, h, grad_q);
+  PFT_BWD_LAUNCH();
+  k_qsmall2d_part<<<(unsigned)(4 * sm_count()), kAux, 0, st>>>(verts, n_verts, loop_off, n_loops, q, h,
+                                                               at<int32_t>(ws, y.small), y.slots,
+                                                               at<double>(ws, y.spart));
+  PFT_BWD_LAUNCH();
+  k_qsmall2d_fin<<<blocks(n_q, kAux), kAux, 0, st>>>(n_verts, q, grad_out, h, at<int32_t>(ws, y.small), y.slots,
+                                                     at<double>(ws, y.spart), grad_q);
   PFT_BWD_LAUNCH();
   return PFT_OK;
 }
