@@ -57,6 +57,23 @@ OPS2D = {
     "poly_sinc": {"fp32": 18, "sfu": 2},
     "sfu_sinc": {"fp32": 24, "sfu": 4},
 }
+# Per-pair operation counts of the 3D pair adjoint (face_adj_t in pft_bwd.cu, forward recomputed
+# and differentiated in reverse mode), as a part every pair pays plus one part per branch; a warp
+# whose lanes take two branches issues both.  Common to every branch: the projections (face_common,
+# 15), the branch selection (one warp reduction of |P|, four compares and the predicate logic, 10),
+# the argument scaling of sincos(mu) (1) and its 2 SFU operations, the weights W = e^{i mu} Z and
+# the adjoints of s and mu (15), and the 12 updates of the record (vertex adjoint, RecAdj) or, for
+# the Q-gradient (QAdj), the 12 updates of Q plus the 2 adds of the pair's own term.  Per branch:
+# the series forms' forward part and derivatives in P and T (k <= 7, 9, 11, 17: 18 / 29 / 40 / 89)
+# plus their adjoint (10); the edge sum's forward part (32 written, three sinc_d of 22, two sincos scalings, the
+# 1/|X|^2 test and select: 102, with 5 SFU operations) plus its adjoint (36) and the X-adjoint
+# terms (12 record updates, or 6 for Q).
+OPS_ADJ = {"common": {"fp32": 53, "sfu": 2},
+           "short": {"fp32": 28, "sfu": 0}, "k9": {"fp32": 39, "sfu": 0}, "long": {"fp32": 50, "sfu": 0},
+           "xlong": {"fp32": 99, "sfu": 0}, "edge": {"fp32": 150, "sfu": 5}}
+OPS_QADJ = {"common": {"fp32": 57, "sfu": 2},
+            "short": {"fp32": 28, "sfu": 0}, "k9": {"fp32": 39, "sfu": 0}, "long": {"fp32": 50, "sfu": 0},
+            "xlong": {"fp32": 99, "sfu": 0}, "edge": {"fp32": 144, "sfu": 5}}
 FP32_LANES, SFU_LANES = 128, 16       # per SM per clock
 # A fixed per-pair count of the triangle term taken as the edge sum of Eq. 14 with a polynomial sinc
 # (projections, three edges' phase/sinc/term, face factor): the basis of frac_vs_survey_count.
@@ -179,6 +196,50 @@ def branch_mix(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0):
         left &= ~take
     out["series_k17"] = float(np.mean(left))
     return {k: out[k] for k in OPS}
+
+
+def adjoint_branch_mix(v, f, q, tau=6.0, lanes="faces", n_warps=4096, seed=0):
+    """The pair adjoint's branch rule on a seeded sample of warps, and the per-pair cost it implies.
+
+    lanes="faces" (k_bwd: a warp holds 32 consecutive faces and takes one Q record at a time) or
+    "q" (k_qgrad: 32 consecutive Q points, one face at a time).  Per lane, with P in float32 and
+    wmax the warp's largest P: short when every P < 1/4 (tau > 1; else every P < tau^2/4) or its
+    own P < tau_lo^2/4; the k <= 9 form when not short and every P < 1 (and < tau^2/4); long when
+    neither and every P < 9/4 (and < tau^2/4); extra-long when none of these but every P < tau^2/4;
+    else the edge sum.  Returns the fraction of lanes in
+    each branch, the fraction of warps issuing each, and the mean count of issued operations per
+    pair (a warp pays the common part once and the part of every branch one of its lanes takes)."""
+    rng = np.random.default_rng(seed)
+    v64 = v.astype(np.float64)
+    if lanes == "faces":
+        fi = 32 * rng.integers(0, max(1, f.shape[0] // 32), n_warps)[:, None] + np.arange(32)[None, :]
+        fi = np.minimum(fi, f.shape[0] - 1)
+        qq = np.broadcast_to(q[rng.integers(0, q.shape[0], n_warps)][:, None, :], (n_warps, 32, 3))
+    else:
+        qi = 32 * rng.integers(0, max(1, q.shape[0] // 32), n_warps)[:, None] + np.arange(32)[None, :]
+        qq = q[np.minimum(qi, q.shape[0] - 1)]
+        fi = np.broadcast_to(rng.integers(0, f.shape[0], n_warps)[:, None], (n_warps, 32))
+    p = v64[f[fi]]                                        # [w, 32, 3, 3]
+    g = p.mean(axis=2)
+    a0 = np.einsum("wlj,wlj->wl", qq, p[:, :, 0] - g)
+    a1 = np.einsum("wlj,wlj->wl", qq, p[:, :, 1] - g)
+    P = (a0 * a0 + a0 * a1 + a1 * a1).astype(np.float32)
+    wmax = P.max(axis=1)[:, None]
+    hi, lo = np.float32(0.25 * tau * tau), np.float32(0.25 * min(tau, 0.05) ** 2)
+    all_hi = wmax < hi
+    shorts = ((wmax < np.float32(0.25)) if tau > 1 else all_hi) | (P < lo)
+    k9 = ~shorts & all_hi & (wmax < np.float32(1.0))
+    longs = ~shorts & ~k9 & all_hi & ((wmax < np.float32(2.25)) if tau > 3 else True)
+    series = shorts | all_hi
+    br = {"short": shorts, "k9": k9, "long": longs, "xlong": series & ~shorts & ~k9 & ~longs, "edge": ~series}
+    lane = {k: float(m.mean()) for k, m in br.items()}
+    warp = {k: float(m.any(axis=1).mean()) for k, m in br.items()}
+    return lane, warp
+
+
+def adjoint_ops(warp_fracs, table):
+    """Mean issued FP32-pipe and SFU operations per pair for the branch-issue fractions of warps."""
+    return {k: table["common"][k] + sum(warp_fracs[b] * table[b][k] for b in warp_fracs) for k in ("fp32", "sfu")}
 
 
 def sfu_sinc_fraction(verts, poly_off, q, n=1 << 16, seed=0):
@@ -577,6 +638,21 @@ def bench_adjoint(dev, warmup, steps):
     ms_b = float(np.mean([c.elapsed_time(d) for c, d in eb]))
     pairs = float(w.faces.shape[0]) * float(w.q.shape[0])
     launches_adj = int(pft.load().pft_backward_last_launch_count())
+
+    def kernel_ms(fn):
+        """The call's pair kernel alone: caller events the library records around it."""
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            b.record()
+            fn({"main_start_event": a.cuda_event, "main_stop_event": b.cuda_event})
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.mean(ts))
+
+    ms_kbwd = kernel_ms(lambda o: pft.pft3d_mesh_backward(vd, fd, qd, g, options=o))
     # the Q-gradient of the same loss (one call per step, same weights)
     for _ in range(3):
         pft.pft3d_mesh_qgrad(vd, fd, qd, g)
@@ -591,9 +667,27 @@ def bench_adjoint(dev, warmup, steps):
         d.synchronize()
         tq.append(c.elapsed_time(d))
     ms_q = float(np.mean(tq))
+    launches_q = int(pft.load().pft_backward_last_launch_count())
+    ms_kq = kernel_ms(lambda o: pft.pft3d_mesh_qgrad(vd, fd, qd, g, options=o))
+    pk, pk_kind = peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk = float(pk.get("sm_max_mhz", 2070.0))
+
+    def rl(kernel, ms_k, lanes, table):
+        lane, warp = adjoint_branch_mix(w.verts, w.faces, w.q, lanes=lanes)
+        ops = adjoint_ops(warp, table)
+        issue = ops["fp32"] + ops["sfu"]
+        cyc = max(issue / FP32_LANES, ops["sfu"] / SFU_LANES)
+        peak = n_sm * clk * 1e6 * issue / cyc
+        return {"bound": "alu", "kernel": kernel, "kernel_ms": ms_k, "achieved": issue * pairs / (ms_k / 1e3) / 1e12,
+                "peak": peak / 1e12, "unit": "Tops/s", "frac": issue * pairs / (ms_k / 1e3) / peak,
+                "ops_per_pair": ops, "branch_lanes": lane, "branch_warps": warp,
+                "peak_basis": f"{n_sm} SMs x 128 issue slots x {clk:.0f} MHz ({pk_kind} max SM clock)"}
+
     return {"value": pairs / (ms_b / 1e3) / 1e9, "unit": UNIT + " (adjoint call)", "ms_adjoint": ms_b,
+            "roofline": rl("k_bwd<3,12>", ms_kbwd, "faces", OPS_ADJ),
             "qgrad": {"value": pairs / (ms_q / 1e3) / 1e9, "unit": UNIT + " (Q-gradient call)", "ms": ms_q,
-                      "launches": int(pft.load().pft_backward_last_launch_count())},
+                      "launches": launches_q, "roofline": rl("k_qgrad", ms_kq, "q", OPS_QADJ)},
             "ms_forward_plus_adjoint": ms, "pairs_per_call": pairs, "faces": int(w.faces.shape[0]),
             "q_points": int(w.q.shape[0]), "finite": bool(torch.isfinite(grad).all().item()),
             "launches_adjoint": launches_adj}

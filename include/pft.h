@@ -84,8 +84,10 @@ typedef enum {
  *                   uses at most 3.0 (its series is kept through k = 16).
  *  main_start_event, main_stop_event
  *                   cudaEvent_t handles or NULL.  When set, they are recorded on
- *                   `stream` immediately before and after the main (pair-sum)
- *                   kernel, so that a caller can time it alone.
+ *                   `stream` immediately before and after the main pair kernel
+ *                   (the pair sum of a forward call, the pair adjoint of a
+ *                   backward or Q-gradient call), so that a caller can time it
+ *                   alone.
  */
 typedef struct {
   int32_t precision;

@@ -163,8 +163,9 @@ __device__ __forceinline__ void face_adj_t(const QRec& Q, const float4 A, const 
   float mu, a0, a1, s, P;
   face_common(qx, qy, qz, A, B, C, mu, a0, a1, s, P);
   // the forward kernel's rule over the warp's faces: short series when all have
-  // P < 1/4 (or this one is below p_lo), long series when all are below 9/4 (and
-  // p_hi), extra-long series when all are below p_hi.  All three tests read the
+  // P < 1/4 (or this one is below p_lo), the k <= 9 form when all are below 1, long
+  // series when all are below 9/4 (and p_hi), extra-long series when all are below
+  // p_hi, else the edge sum.  All the tests read the
   // warp's largest |P|, taken by every lane before any of them branches.  Here P can
   // be -0 or a tiny negative subnormal (a1 a1 underflows before the fused add when
   // the phases are below ~1e-20, as for a tiny Q beside large ones in k_qgrad), so
@@ -176,7 +177,8 @@ __device__ __forceinline__ void face_adj_t(const QRec& Q, const float4 A, const 
   const bool all_short = wmax < kPShort;
   const bool all_long = wmax < kPLong;
   const bool shorts = (th.longs ? all_short : all_hi) || (P < th.lo);
-  const bool longs = !shorts && all_hi && (!th.xlongs || all_long);
+  const bool k9s = !shorts && all_hi && wmax < kP9;   // tau > 1 here (else every series lane is short)
+  const bool longs = !shorts && !k9s && all_hi && (!th.xlongs || all_long);
   const bool series = shorts || all_hi;
   float sm, cm;
   __sincosf(mu, &sm, &cm);
@@ -197,6 +199,29 @@ __device__ __forceinline__ void face_adj_t(const QRec& Q, const float4 A, const 
     dGre_dT = 2.0f * T * -2.48015873e-5f;
     dGim_dP = T * fmaf(P, 2.0f * -8.26719577e-6f, 3.96825397e-4f);
     dGim_dT = r;
+  } else if (k9s) {          // k <= 9 series (P < 1), as face_series_k9
+    T = -(a0 * a1) * (a0 + a1);
+    const float T2 = T * T;
+    float A0 = fmaf(P, 2.755731922e-07f, -2.480158730e-05f);
+    A0 = fmaf(P, A0, 1.388888889e-03f);
+    A0 = fmaf(P, A0, -4.166666667e-02f);
+    A0 = fmaf(P, A0, 0.5f);
+    const float A2 = fmaf(P, 8.267195767e-07f, -2.480158730e-05f);
+    float D1 = fmaf(P, 1.002084335e-07f, -8.267195767e-06f);
+    D1 = fmaf(P, D1, 3.968253968e-04f);
+    D1 = fmaf(P, D1, -8.333333333e-03f);
+    zr = -T * fmaf(T2, 2.505210839e-08f, D1);
+    zi = fmaf(T2, A2, A0);
+    // derivatives of A0, A2, D1 in P (coefficients i c_i); the T^3 coefficient is constant
+    float dA0 = fmaf(P, 4.0f * 2.755731922e-07f, 3.0f * -2.480158730e-05f);
+    dA0 = fmaf(P, dA0, 2.0f * 1.388888889e-03f);
+    dA0 = fmaf(P, dA0, -4.166666667e-02f);
+    float dD1 = fmaf(P, 3.0f * 1.002084335e-07f, 2.0f * -8.267195767e-06f);
+    dD1 = fmaf(P, dD1, 3.968253968e-04f);
+    dGre_dP = fmaf(T2, 8.267195767e-07f, dA0);
+    dGre_dT = 2.0f * T * A2;
+    dGim_dP = T * dD1;
+    dGim_dT = fmaf(3.0f * T2, 2.505210839e-08f, D1);
   } else if (longs) {         // long series (P < 9/4, k <= 11), as face_series_long
     T = -(a0 * a1) * (a0 + a1);
     const float T2 = T * T;
@@ -1493,10 +1518,15 @@ BbLayout bb_layout(int64_t nv, int64_t np, int64_t n_q) {
   return y;
 }
 
+// Caller events recorded around the main pair kernel of the current call (set by check_opts).
+thread_local cudaEvent_t g_ev_start = nullptr, g_ev_stop = nullptr;
+
 int check_opts(const pft_options* o, Thr& th) {
   pft_options z;
   std::memset(&z, 0, sizeof(z));
   const pft_options& p = o ? *o : z;
+  g_ev_start = static_cast<cudaEvent_t>(p.main_start_event);
+  g_ev_stop = static_cast<cudaEvent_t>(p.main_stop_event);
   if (p.precision != PFT_FP32_COMPENSATED) return PFT_ERR_UNSUPPORTED;   // the adjoint runs in FP32
   if (p.q_per_thread != 0 || p.block_threads != 0 || p.k_splits != 0 || p.tile_items != 0)
     return PFT_ERR_UNSUPPORTED;
@@ -1506,6 +1536,11 @@ int check_opts(const pft_options* o, Thr& th) {
   th = Thr{0.25f * tau * tau, 0.25f * lo * lo, tau > 1.f ? 1 : 0, tau > 3.f ? 1 : 0};
   return PFT_OK;
 }
+
+#define PFT_MARK(ev)                                                                        \
+  do {                                                                                      \
+    if ((ev) != nullptr && cudaEventRecord((ev), st) != cudaSuccess) return PFT_ERR_CUDA; \
+  } while (0)
 
 #define PFT_BWD_LAUNCH()                                   \
   do {                                                     \
@@ -1534,9 +1569,11 @@ int mesh3d_backward_body(const float* verts, int64_t n_verts, const int32_t* fac
   k_bq<3><<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, h, 1.0, at<QRec>(ws, y.qrec), at<int32_t>(ws, y.small));
   PFT_BWD_LAUNCH();
   dim3 grid(blocks(n_faces, kBwdNT), (unsigned)y.ks);
+  PFT_MARK(g_ev_start);
   k_bwd<3, 12><<<grid, kBwdNT, 0, st>>>(at<void>(ws, y.items), n_faces, at<QRec>(ws, y.qrec), n_q, y.per_split, th,
                                         at<double>(ws, y.partial), &h->status);
   PFT_BWD_LAUNCH();
+  PFT_MARK(g_ev_stop);
   k_bcorner3d<<<blocks(n_faces, kAux), kAux, 0, st>>>(verts, n_verts, faces, n_faces, at<double>(ws, y.partial),
                                                       y.ks, h, at<int32_t>(ws, y.small), q, grad_out,
                                                       at<double>(ws, y.corner));
@@ -1613,9 +1650,11 @@ int pft2d_polygons_backward(const float* verts, int64_t n_verts, const int64_t* 
   k_bq<2><<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, h, 2.0, at<QRec>(ws, y.qrec), at<int32_t>(ws, y.small));
   PFT_BWD_LAUNCH();
   dim3 grid(blocks(n_verts, kBwdNT), (unsigned)y.ks);
+  PFT_MARK(g_ev_start);
   k_bwd<2, 4><<<grid, kBwdNT, 0, st>>>(at<void>(ws, y.items), n_verts, at<QRec>(ws, y.qrec), n_q, y.per_split, th,
                                        at<double>(ws, y.partial), &h->status);
   PFT_BWD_LAUNCH();
+  PFT_MARK(g_ev_stop);
   k_bvert2d<<<blocks(n_verts, kAux), kAux, 0, st>>>(verts, n_verts, loop_off, n_loops, at<double>(ws, y.partial),
                                                     y.ks, h, at<int32_t>(ws, y.small), q, grad_out, grad_verts);
   PFT_BWD_LAUNCH();
@@ -1721,9 +1760,11 @@ int pft3d_mesh_qgrad(const float* verts, int64_t n_verts, const int32_t* faces, 
   k_bq<3><<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, h, 1.0, at<QRec>(ws, y.qrec), at<int32_t>(ws, y.small));
   PFT_BWD_LAUNCH();
   dim3 grid(blocks(n_q, kBwdNT), (unsigned)y.ks);
+  PFT_MARK(g_ev_start);
   k_qgrad<<<grid, kBwdNT, 0, st>>>(at<Face32>(ws, y.items), n_faces, y.per_split, at<QRec>(ws, y.qrec), n_q, th,
                                    at<double>(ws, y.partial), &h->status);
   PFT_BWD_LAUNCH();
+  PFT_MARK(g_ev_stop);
   k_qfinal<<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, at<double>(ws, y.partial), y.ks, h, grad_q);
   PFT_BWD_LAUNCH();
   k_qsmall_part<<<(unsigned)(4 * sm_count()), kAux, 0, st>>>(verts, n_verts, faces, n_faces, q, h,
@@ -1769,9 +1810,11 @@ int pft2d_polygons_qgrad(const float* verts, int64_t n_verts, const int64_t* loo
   k_bq<2><<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, h, 2.0, at<QRec>(ws, y.qrec), at<int32_t>(ws, y.small));
   PFT_BWD_LAUNCH();
   dim3 grid(blocks(n_q, kBwdNT), (unsigned)y.ks);
+  PFT_MARK(g_ev_start);
   k_qgrad2d<<<grid, kBwdNT, 0, st>>>(at<Seg32>(ws, y.items), n_verts, y.per_split, at<QRec>(ws, y.qrec), n_q,
                                      at<double>(ws, y.partial), &h->status);
   PFT_BWD_LAUNCH();
+  PFT_MARK(g_ev_stop);
   k_qfinal2d<<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, at<double>(ws, y.partial), y.ks, h, grad_q);
   PFT_BWD_LAUNCH();
   k_qsmall2d_part<<<(unsigned)(4 * sm_count()), kAux, 0, st>>>(verts, n_verts, loop_off, n_loops, q, h,
@@ -1830,9 +1873,11 @@ int pft2d_polygons_batched_backward(const float* verts, int64_t n_verts, const i
   PFT_BWD_LAUNCH();
   if (y.grid > INT32_MAX) return PFT_ERR_UNSUPPORTED;
   dim3 grid((unsigned)y.grid, (unsigned)y.ks);
+  PFT_MARK(g_ev_start);
   k_bbwd<<<grid, kBwdNT, 0, st>>>(segs, n_verts, poly_off, n_polys, bstart, nblk, at<QRec>(ws, y.rec), n_q,
                                   y.per_split, th, at<double>(ws, y.partial), &h->status);
   PFT_BWD_LAUNCH();
+  PFT_MARK(g_ev_stop);
   k_bbvert<<<blocks(n_verts, kAux), kAux, 0, st>>>(verts, n_verts, poly_off, n_polys, at<double>(ws, y.partial), y.ks,
                                                    pc, at<int32_t>(ws, y.small), at<int32_t>(ws, y.scnt), q, n_q,
                                                    grad_out, grad_verts);

@@ -150,3 +150,73 @@ def test_survey_count_fraction_and_error_stats():
     st = bench.err_stats(got, ref, -2.0)      # |errors| / 2 = 0, 0.25, 0.5, 1.5
     assert st["max"] == 1.5 and st["median"] == 0.375
     assert abs(st["p99"] - (0.5 + 0.97 * 1.0)) < 1e-12
+
+
+def _bwd_body(start, stop=None, struct=False):
+    """Text of pft_bwd.cu from `start` to `stop` (or to the end of the function / struct), comments
+    removed."""
+    import os
+    import re
+    text = open(os.path.join(bench.ROOT, "paper_2104_08309_gb300", "csrc", "pft_bwd.cu")).read()
+    text = re.sub(r"//[^\n]*", "", text)
+    i = text.index(start)
+    j = text.index(stop, i) if stop else text.index("\n};\n" if struct else "\n}\n", i)
+    return text[i:j]
+
+
+def _ops_no_literal_products(body):
+    """As _arith_ops, but a product or sum of two numeric literals (folded by the compiler) is not
+    counted."""
+    import re
+    num = r"-?\d+\.?\d*(?:e[-+]?\d+)?f?"
+    n = body.count("fmaf(")
+    for m in re.finditer(r"([\w\.\)\]]+) ([*+-]) (-?[\w\.\(]+)", body):
+        if not (re.fullmatch(num, m.group(1)) and re.fullmatch(num, m.group(3))):
+            n += 1
+    return n
+
+
+def test_adjoint_ops_table_matches_the_source():
+    """bench.OPS_ADJ / OPS_QADJ: each branch part is the arithmetic written in that branch of
+    face_adj_t plus its adjoint; the edge part adds three sinc_d, and the record or Q updates of
+    the X adjoint; the common part adds face_common, the 10 branch-selection operations, the
+    sincos scaling, the code after the branches and the 12 record or Q updates."""
+    c = _ops_no_literal_products
+    fwd = {"short": c(_bwd_body("if (shorts) {", "} else if (k9s) {")),
+           "k9": c(_bwd_body("} else if (k9s) {", "} else if (longs) {")),
+           "long": c(_bwd_body("} else if (longs) {", "} else if (series) {")),
+           "xlong": c(_bwd_body("} else if (series) {", "} else {\n    const float nx"))}
+    series_adj = c(_bwd_body("if (series) {\n    const float Pb", "} else {\n    const float Sr"))
+    edge_fwd = c(_bwd_body("} else {\n    const float nx", "const float Wr"))
+    edge_adj = c(_bwd_body("} else {\n    const float Sr", "out.common("))
+    post = c(_bwd_body("const float Wr", "float a0b, a1b;"))
+    sinc_d = c(_bwd_body("void sinc_d("))
+    rec_edge = c(_bwd_body("void edge(float b0b", "__device__ __forceinline__ void common"))
+    q_edge = c(_bwd_body("void edge(float, float", "__device__ __forceinline__ void common"))
+    assert (rec_edge, q_edge) == (12, 6)
+    assert _arith_ops(_fn_body("void face_common(")) == 15
+    for key in ("short", "k9", "long", "xlong"):
+        assert bench.OPS_ADJ[key]["fp32"] == fwd[key] + series_adj, key
+        assert bench.OPS_QADJ[key]["fp32"] == fwd[key] + series_adj, key
+    # two sincos argument scalings and the 1/|X|^2 test and select are not written as arithmetic
+    assert bench.OPS_ADJ["edge"]["fp32"] == edge_fwd + 3 * sinc_d + 2 + 2 + edge_adj + rec_edge
+    assert bench.OPS_QADJ["edge"]["fp32"] == edge_fwd + 3 * sinc_d + 2 + 2 + edge_adj + q_edge
+    # common: projections 15, branch selection 10, sincos(mu) scaling 1, the code after the branches
+    # (whose two products -s W feed only the Q-gradient's own term), 12 updates (+2 adds for QAdj)
+    assert bench.OPS_ADJ["common"]["fp32"] == 15 + 10 + 1 + (post - 2) + 12
+    assert bench.OPS_QADJ["common"]["fp32"] == 15 + 10 + 1 + post + 2 + 12
+    assert bench.OPS_ADJ["edge"]["sfu"] == 5 and bench.OPS_ADJ["common"]["sfu"] == 2
+
+
+def test_adjoint_branch_mix_partitions_the_lanes(mesh):
+    v, f = mesh
+    q = synth.q_grid_3d(24, 40.0)
+    for lanes in ("faces", "q"):
+        for tau in (0.5, 1.0, 3.0, 6.0):
+            lane, warp = bench.adjoint_branch_mix(v, f, q, tau=tau, lanes=lanes, n_warps=256)
+            assert abs(sum(lane.values()) - 1.0) < 1e-12
+            assert all(warp[k] >= lane[k] for k in lane)
+            ops = bench.adjoint_ops(warp, bench.OPS_ADJ)
+            assert bench.OPS_ADJ["common"]["fp32"] < ops["fp32"] <= sum(x["fp32"] for x in bench.OPS_ADJ.values())
+            if tau <= 3.0:
+                assert lane["xlong"] == 0.0
