@@ -47,6 +47,9 @@ OPS = {
     "series_k13": {"fp32": 46, "sfu": 2},     # through k = 13 (P < 4)
     "series_k17": {"fp32": 58, "sfu": 2},     # through k = 17 (P < 9)
     "edge_sum": {"fp32": 92, "sfu": 7},       # edge sum of Eq. 14, polynomial sinc
+    # a face of a pair whose two faces both take the edge sum (face_pairs option): the second face
+    # skips the shared edge's u^2, Chebyshev sinc and range test (8), so each face costs 88 on average
+    "edge_sum_shared": {"fp32": 88, "sfu": 7},
 }
 SERIES_BOUNDS = [("series_k7", 0.25), ("series_k9", 1.0), ("series_k11", 2.25),
                  ("series_k13", 4.0)]         # P bounds of the forms below k = 17 (kP* in pft_pairs.cuh)
@@ -163,7 +166,7 @@ def peaks():
         return {"sm_max_mhz": 2070.0}, "fallback"
 
 
-def branch_mix(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0):
+def branch_mix(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0, n_pairs=0):
     """Fractions of (Q, face) pairs the kernel evaluates with each branch.
 
     Mirrors the kernel's rule on a seeded sample: for one face, a warp holds the
@@ -171,7 +174,9 @@ def branch_mix(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0):
     P < p_hi = tau^2/4 they all take the first series form whose bound b has
     p_hi <= b or every P < b (k = 17 when none has); otherwise the edge sum (the
     few pairs below tau_lo^2/4 that the edge branch redoes with the series are
-    counted as edge).  Thresholds are compared in float32, as the kernel does.
+    counted as edge).  Thresholds are compared in float32, as the kernel does.  With n_pairs > 0
+    (faces 2k, 2k+1 paired, k < n_pairs) a paired face whose partner takes the edge sum in the same
+    warp as well is counted as edge_sum_shared.
     """
     rng = np.random.default_rng(seed)
     fi = rng.integers(0, f.shape[0], n_warps)
@@ -181,15 +186,23 @@ def branch_mix(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0):
     idx = (base[:, None, None] + np.arange(r)[None, :, None] * nt + 32 * w[:, None, None]
            + np.arange(32)[None, None, :]).reshape(n_warps, -1)
     idx = np.minimum(idx, q.shape[0] - 1)
-    p = v.astype(np.float64)[f[fi]]                      # [w, 3, 3]
-    g = p.mean(axis=1)
     qq = q[idx]                                          # [w, r*32, 3]
-    a0 = np.einsum("wlj,wj->wl", qq, p[:, 0] - g)
-    a1 = np.einsum("wlj,wj->wl", qq, p[:, 1] - g)
-    pmax = (a0 * a0 + a0 * a1 + a1 * a1).max(axis=1).astype(np.float32)
+
+    def warp_pmax(faces):
+        p = v.astype(np.float64)[f[faces]]               # [w, 3, 3]
+        g = p.mean(axis=1)
+        a0 = np.einsum("wlj,wj->wl", qq, p[:, 0] - g)
+        a1 = np.einsum("wlj,wj->wl", qq, p[:, 1] - g)
+        return (a0 * a0 + a0 * a1 + a1 * a1).max(axis=1).astype(np.float32)
+
+    pmax = warp_pmax(fi)
     p_hi = np.float32(0.25 * tau * tau)
     left = pmax < p_hi                                   # warps that take a series form
-    out = {"edge_sum": float(np.mean(~left))}
+    shared = np.zeros(n_warps, dtype=bool)
+    if n_pairs > 0:
+        partner = np.where(fi < 2 * n_pairs, fi ^ 1, fi)
+        shared = (fi < 2 * n_pairs) & ~left & (warp_pmax(partner) >= p_hi)
+    out = {"edge_sum": float(np.mean(~left & ~shared)), "edge_sum_shared": float(np.mean(shared))}
     for name, b in SERIES_BOUNDS:
         take = left & ((p_hi <= np.float32(b)) | (pmax < np.float32(b)))
         out[name] = float(np.mean(take))
@@ -814,8 +827,9 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)    # > 129 MB L2
     stream = torch.cuda.current_stream(dev)
 
-    def step(o):
-        rc = lib.pft3d_mesh(vd.data_ptr(), v.shape[0], fd.data_ptr(), f.shape[0], qd.data_ptr(), q.shape[0],
+    def step(o, faces_dev=None):
+        faces_dev = fd if faces_dev is None else faces_dev
+        rc = lib.pft3d_mesh(vd.data_ptr(), v.shape[0], faces_dev.data_ptr(), f.shape[0], qd.data_ptr(), q.shape[0],
                             out.data_ptr(), ws.data_ptr(), nbytes, ctypes.byref(o), stream.cuda_stream)
         if rc:
             raise RuntimeError(f"pft3d_mesh failed: {pft.status_string(rc)}")
@@ -877,10 +891,17 @@ def main():
     # timed call each
     variants, variant_out = [], []
     out_main = out.clone()          # result of the benchmarked configuration (checked against the oracle)
+    f_pairs, n_pairs = None, 0
     if not args.no_extra and world == 1:
-        for vt in (3.0, 1.0):
-            ov = dict(tune, face_series_tau=vt)
-            step(pft.make_options(ov))
+        # the faces reordered into pairs that share an edge (host helper), for the paired variant
+        t_pair = time.perf_counter()
+        f_pairs, n_pairs = pft.pair_faces(f)
+        t_pair = time.perf_counter() - t_pair
+        fd_pairs = torch.from_numpy(f_pairs).to(dev)
+        for vt, paired in ((3.0, False), (1.0, False), (1.0, True)):
+            ov = dict(tune, face_series_tau=vt, face_pairs=n_pairs if paired else 0)
+            faces_dev = fd_pairs if paired else fd
+            step(pft.make_options(ov), faces_dev)
             flush.zero_()
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -888,12 +909,17 @@ def main():
             ea.record()
             eb.record()
             a.record(stream)
-            step(pft.make_options({**ov, "main_start_event": ea.cuda_event, "main_stop_event": eb.cuda_event}))
+            step(pft.make_options({**ov, "main_start_event": ea.cuda_event, "main_stop_event": eb.cuda_event}),
+                 faces_dev)
             b.record(stream)
             b.synchronize()
-            variants.append({"face_series_tau": vt, "value": pairs / (a.elapsed_time(b) / 1e3) / 1e9, "unit": UNIT,
-                             "ms_per_step": a.elapsed_time(b), "main_kernel_ms": ea.elapsed_time(eb),
-                             "device_status": int(pft.pft_status(ws))})
+            vr = {"face_series_tau": vt, "value": pairs / (a.elapsed_time(b) / 1e3) / 1e9, "unit": UNIT,
+                  "ms_per_step": a.elapsed_time(b), "main_kernel_ms": ea.elapsed_time(eb),
+                  "device_status": int(pft.pft_status(ws))}
+            if paired:
+                vr["face_pairs"] = {"pairs": n_pairs, "faces_paired": 2 * n_pairs / f.shape[0],
+                                    "host_pairing_s": t_pair}
+            variants.append(vr)
             variant_out.append(out.clone())
 
     if rank == 0:
@@ -903,7 +929,11 @@ def main():
         mix = branch_mix(v, f, q, tau=args.tau or 6.0, r=args.q_per_thread, nt=args.block_threads)
         ops, issue, achieved, peak_ops = roofline(pairs, ms_main / 1e3, mix, n_sm, clk_max)
         for variant in variants:
-            vmix = branch_mix(v, f, q, tau=variant["face_series_tau"], r=args.q_per_thread, nt=args.block_threads)
+            if "face_pairs" in variant:
+                vmix = branch_mix(v, f_pairs, q, tau=variant["face_series_tau"], r=args.q_per_thread,
+                                  nt=args.block_threads, n_pairs=n_pairs)
+            else:
+                vmix = branch_mix(v, f, q, tau=variant["face_series_tau"], r=args.q_per_thread, nt=args.block_threads)
             _, _, v_ach, v_peak = roofline(pairs, variant["main_kernel_ms"] / 1e3, vmix, n_sm, clk_max)
             variant["branch_fractions"] = vmix
             variant["roofline_frac"] = v_ach / v_peak

@@ -50,7 +50,8 @@ typedef enum {
   PFT_ERR_TIMEOUT = 6,       /* a bounded wait on a copy gave up (status word)    */
   PFT_ERR_UNSUPPORTED = 7,   /* option combination not implemented                */
   PFT_ERR_OFFSETS = 8,       /* CSR offsets not non-decreasing / inconsistent     */
-  PFT_ERR_SCRATCH_LIMIT = 9  /* problem too large for pft3d_mesh_noalloc's scratch */
+  PFT_ERR_SCRATCH_LIMIT = 9, /* problem too large for pft3d_mesh_noalloc's scratch */
+  PFT_ERR_PAIRS = 10         /* faces given as pairs do not share their first edge (status word) */
 } pft_status_code;
 
 typedef enum {
@@ -82,6 +83,16 @@ typedef enum {
  *                   keeps the edge sum for every face whose spread is at least
  *                   1, where it loses nothing to cancellation).  The FP64 path
  *                   uses at most 3.0 (its series is kept through k = 16).
+ *  face_pairs       3D triangle calls (pft3d_mesh and its no-workspace form): the
+ *                   number of leading face pairs.  For k < face_pairs, faces 2k
+ *                   and 2k+1 must share their first edge in opposite directions,
+ *                   (a, b, c) and (b, a, d), as pft3d_pair_faces writes them; the
+ *                   FP32 path then evaluates that edge's sinc(Q.d/2) once for both
+ *                   faces where a group of 32 threads takes the edge sum of Eq. 14
+ *                   for both.  The device checks every pair (a pair that does not
+ *                   share its first edge contributes nothing and sets
+ *                   PFT_ERR_PAIRS).  0 = no pairs; 2 face_pairs <= n_faces.  Other
+ *                   calls ignore it.
  *  main_start_event, main_stop_event
  *                   cudaEvent_t handles or NULL.  When set, they are recorded on
  *                   `stream` immediately before and after the main pair kernel
@@ -98,7 +109,8 @@ typedef struct {
   float face_series_tau;
   void* main_start_event;
   void* main_stop_event;
-  int32_t reserved[4];
+  int32_t face_pairs;
+  int32_t reserved[3];
 } pft_options;
 
 /* Bytes of workspace the matching call needs for these sizes and options. */
@@ -194,6 +206,28 @@ int pft_batched_last_launch_count(void);
 int pft3d_mesh(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces,
                const double* q, int64_t n_q, double* out,
                void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
+
+/*
+ * Host helper for the face_pairs option (Sec. 3, Eq. 14: on a closed surface every
+ * edge belongs to two faces, and its sinc(Q.d/2) is the same for both, since sinc
+ * is even and d only flips sign).  Reorders a triangle list so that as many faces
+ * as possible come in pairs that share an edge: faces_out[2k], faces_out[2k+1] =
+ * (a, b, c), (b, a, d) for k < *n_pairs, then the faces left unpaired in their
+ * input order and vertex order.  Pairs join faces that hold a common edge in
+ * opposite directions (an edge of more than two faces, or of two faces in the
+ * same direction, pairs nothing), chosen by a deterministic Karp-Sipser matching:
+ * a face with one free neighbour is matched to it first, else the lowest-numbered
+ * free face to its first free neighbour (about 98 % of an icosphere's faces end
+ * up in pairs; O(n) time and memory on the host).  The result
+ * describes the same surface (a rotation of a triangle's corners keeps it), so
+ * every transform of it is unchanged.
+ *  faces_host  [n_faces][3] int32, HOST memory, indices >= 0.
+ *  faces_out   [n_faces][3] int32, HOST memory, written (may not alias faces_host).
+ *  n_pairs     receives the number of pairs.
+ * Returns PFT_OK, PFT_ERR_INVALID_ARG (null pointer, negative count or index).
+ * Synchronous host work; no GPU is touched.
+ */
+int pft3d_pair_faces(const int32_t* faces_host, int64_t n_faces, int32_t* faces_out, int64_t* n_pairs);
 
 /*
  * 3D: FT_V(Q) of a closed surface of planar polygon faces of any size (Sec. 3:

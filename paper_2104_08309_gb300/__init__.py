@@ -22,7 +22,7 @@ __all__ = [
     "pft2d_polygons", "pft2d_batched_prepare", "pft2d_polygons_batched", "BatchedPrepared", "pft3d_mesh",
     "pft3d_polymesh", "pft3d_polymesh_backward", "ft3d_poly", "pft2d_polygons_batched_backward", "pft3d_batched_prepare", "pft3d_meshes_batched",
     "pft2d_polygons_backward",
-    "pft3d_mesh_backward", "pft3d_mesh_qgrad", "pft2d_polygons_qgrad", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft2d_batched", "ft3d", "make_options", "Options",
+    "pft3d_mesh_backward", "pft3d_mesh_qgrad", "pft2d_polygons_qgrad", "pair_faces", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft2d_batched", "ft3d", "make_options", "Options",
     "PFTError",
     "launch_count", "version",
 ]
@@ -254,6 +254,20 @@ def pft3d_mesh(verts, faces, q, *, options=None, out=None, ws=None, stream=None,
     if check_status:
         check(lib.pft_status(ws.data_ptr(), st), "pft3d_mesh (device status)")
     return out
+
+
+def pair_faces(faces):
+    """Host helper (no GPU): reorder a triangle list [n, 3] so that faces 2k and 2k+1 share their first
+    edge in opposite directions, for k < n_pairs, followed by the unpaired faces.  Returns
+    (faces_out int32 [n, 3], n_pairs); pass n_pairs as the ``face_pairs`` option of pft3d_mesh."""
+    import numpy as np
+    f = np.ascontiguousarray(np.asarray(faces.detach().cpu() if hasattr(faces, "detach") else faces,
+                                        dtype=np.int32).reshape(-1, 3))
+    out = np.empty_like(f)
+    n = ctypes.c_int64(0)
+    check(load().pft3d_pair_faces(f.ctypes.data, f.shape[0], out.ctypes.data, ctypes.byref(n)),
+          "pft3d_pair_faces")
+    return out, int(n.value)
 
 
 def pft3d_polymesh(verts, face_idx, face_off, q, *, options=None, out=None, ws=None, stream=None,

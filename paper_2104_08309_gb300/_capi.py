@@ -33,7 +33,8 @@ class Options(ctypes.Structure):
         ("face_series_tau", ctypes.c_float),
         ("main_start_event", ctypes.c_void_p),
         ("main_stop_event", ctypes.c_void_p),
-        ("reserved", ctypes.c_int32 * 4),
+        ("face_pairs", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -53,6 +54,7 @@ SIGNATURES = {
     "pft3d_batched_prepare": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_size, c_vp, c_vp, c_vp]),
     "pft3d_meshes_batched": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp,
                                             c_size, c_vp, c_vp]),
+    "pft3d_pair_faces": (ctypes.c_int, [c_vp, c_i64, c_vp, c_vp]),
     "pft3d_polymesh_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_i64, c_vp]),
     "pft3d_polymesh": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_size,
                                       c_vp, c_vp]),

@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <unordered_map>
+#include <vector>
 
 #include "pft_kernels.cuh"
 
@@ -19,6 +21,7 @@ struct Opts {
   int r, nt, k_splits;
   float tau;
   cudaEvent_t ev_start, ev_stop;
+  int64_t face_pairs;
 };
 
 int resolve(const pft_options* o, int dim, Opts& out) {
@@ -40,6 +43,9 @@ int resolve(const pft_options* o, int dim, Opts& out) {
   out.tau = tau;
   out.ev_start = static_cast<cudaEvent_t>(p.main_start_event);
   out.ev_stop = static_cast<cudaEvent_t>(p.main_stop_event);
+  if (p.face_pairs < 0) return PFT_ERR_INVALID_ARG;
+  if (p.face_pairs > 0 && dim == 3 && !out.fp64 && out.r > 4) return PFT_ERR_UNSUPPORTED;
+  out.face_pairs = dim == 3 ? p.face_pairs : 0;
   return PFT_OK;
 }
 
@@ -63,7 +69,7 @@ FwdLaunch plan_fwd(int dim, const Opts& o, int64_t n_items, int64_t n_q) {
   const int64_t item_tiles = std::max<int64_t>(1, (n_items + tile - 1) / tile);
   int k = o.k_splits;
   if (k == 0) {
-    const int64_t slots = (int64_t)device_sms() * fwd_blocks_per_sm(dim, o.fp64, o.r, o.nt);
+    const int64_t slots = (int64_t)device_sms() * fwd_blocks_per_sm(dim, o.fp64, o.r, o.nt, o.face_pairs > 0);
     const int kmax = (int)std::max<int64_t>(1, std::min<int64_t>(64, item_tiles / 2));
     double best_eff = -1.0;
     int best_k = 1;
@@ -179,6 +185,7 @@ int pft3d_mesh(const float* verts, int64_t n_verts, const int32_t* faces, int64_
   if (n_q > 0 && (q == nullptr || out == nullptr)) return PFT_ERR_INVALID_ARG;
   if (n_faces > 0 && (faces == nullptr || verts == nullptr || n_verts == 0)) return PFT_ERR_INVALID_ARG;
   if (n_q > INT32_MAX || n_verts > INT32_MAX) return PFT_ERR_UNSUPPORTED;
+  if (2 * o.face_pairs > n_faces) return PFT_ERR_INVALID_ARG;
   const FwdLayout y = layout_fwd(3, o, n_faces, n_faces, n_q);
   if (bad_ws(ws, ws_bytes, y.total)) return PFT_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -191,10 +198,11 @@ int pft3d_mesh(const float* verts, int64_t n_verts, const int32_t* faces, int64_
   }
   double* mp = at<double>(ws, y.mparts);
   PFT_LAUNCH(launch_bbox(verts, n_verts, 3, h, st));
-  PFT_LAUNCH(launch_prep3d(verts, n_verts, faces, n_faces, h, at<void>(ws, y.items), o.fp64, mp, y.nblk, st));
+  PFT_LAUNCH(launch_prep3d(verts, n_verts, faces, n_faces, h, at<void>(ws, y.items), o.fp64, mp, y.nblk, st,
+                           2 * o.face_pairs));
   if (mark(o.ev_start, st) != cudaSuccess) return PFT_ERR_CUDA;
   PFT_LAUNCH(launch_fwd(3, o.fp64, y.L, at<void>(ws, y.items), n_faces, q, n_q, o.tau, at<double2>(ws, y.partial),
-                        &h->status, st));
+                        &h->status, st, 2 * o.face_pairs));
   if (mark(o.ev_stop, st) != cudaSuccess) return PFT_ERR_CUDA;
   PFT_LAUNCH(launch_finalize(3, q, n_q, at<double2>(ws, y.partial), y.L.k_splits, o.fp64, h, mp, y.nblk,
                              at<int32_t>(ws, y.small), out, st));
@@ -259,6 +267,7 @@ int pft_status(const void* ws, void* stream) {
   if (word & ST_INDEX) return PFT_ERR_INDEX_RANGE;
   if (word & ST_NONFINITE) return PFT_ERR_NONFINITE;
   if (word & ST_OFFSETS) return PFT_ERR_OFFSETS;
+  if (word & ST_PAIRS) return PFT_ERR_PAIRS;
   if (word & ST_TIMEOUT) return PFT_ERR_TIMEOUT;
   return PFT_OK;
 }
@@ -275,8 +284,112 @@ const char* pft_status_string(int code) {
     case PFT_ERR_UNSUPPORTED: return "unsupported option combination";
     case PFT_ERR_OFFSETS: return "malformed CSR offsets";
     case PFT_ERR_SCRATCH_LIMIT: return "problem exceeds the 32 MiB static scratch of pft3d_mesh_noalloc";
+    case PFT_ERR_PAIRS: return "faces given as pairs do not share their first edge";
     default: return "unknown status code";
   }
+}
+
+int pft3d_pair_faces(const int32_t* f, int64_t nf, int32_t* out, int64_t* n_pairs) {
+  if (nf < 0 || n_pairs == nullptr || (nf > 0 && (f == nullptr || out == nullptr || f == out)))
+    return PFT_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < 3 * nf; ++i)
+    if (f[i] < 0) return PFT_ERR_INVALID_ARG;
+  // undirected edge -> the first two (face, slot) that hold it, and how many faces do
+  struct Uses {
+    int64_t face[2];
+    int8_t slot[2];
+    int32_t count;
+  };
+  auto key = [](uint32_t u, uint32_t v) {
+    return u < v ? ((uint64_t)u << 32) | v : ((uint64_t)v << 32) | u;
+  };
+  std::unordered_map<uint64_t, Uses> edges;
+  edges.reserve((size_t)(3 * nf / 2 + 1));
+  for (int64_t m = 0; m < nf; ++m)
+    for (int l = 0; l < 3; ++l) {
+      Uses& e = edges[key((uint32_t)f[3 * m + l], (uint32_t)f[3 * m + (l + 1) % 3])];
+      if (e.count < 2) {
+        e.face[e.count] = m;
+        e.slot[e.count] = (int8_t)l;
+      }
+      ++e.count;
+    }
+  // pairable neighbours: faces that hold a common edge (of exactly two faces) the other way round
+  std::vector<int64_t> nb((size_t)(3 * nf), -1);
+  std::vector<int8_t> nb_slot((size_t)(3 * nf), 0);
+  for (int64_t m = 0; m < nf; ++m)
+    for (int l = 0; l < 3; ++l) {
+      const int32_t u = f[3 * m + l], v = f[3 * m + (l + 1) % 3];
+      if (u == v) continue;
+      const Uses& e = edges.at(key((uint32_t)u, (uint32_t)v));
+      if (e.count != 2) continue;
+      const int j = (e.face[0] == m && e.slot[0] == l) ? 1 : 0;
+      const int64_t o = e.face[j];
+      const int lo = e.slot[j];
+      if (o == m || f[3 * o + lo] != v || f[3 * o + (lo + 1) % 3] != u) continue;
+      nb[(size_t)(3 * m + l)] = o;
+      nb_slot[(size_t)(3 * m + l)] = (int8_t)lo;
+    }
+  // maximum-cardinality-seeking matching (Karp-Sipser): a face with one free neighbour is matched
+  // to it first; otherwise the lowest-numbered free face with a free neighbour is matched to its
+  // first free neighbour.  Deterministic.
+  std::vector<int64_t> partner((size_t)nf, -1);
+  std::vector<int8_t> first((size_t)nf, 0);
+  std::vector<int8_t> deg((size_t)nf, 0);
+  for (int64_t m = 0; m < nf; ++m)
+    for (int l = 0; l < 3; ++l) deg[(size_t)m] += nb[(size_t)(3 * m + l)] >= 0;
+  std::vector<int64_t> ones;
+  for (int64_t m = nf - 1; m >= 0; --m)
+    if (deg[(size_t)m] == 1) ones.push_back(m);
+  auto match = [&](int64_t m, int l) {
+    const int64_t o = nb[(size_t)(3 * m + l)];
+    partner[(size_t)m] = o;
+    partner[(size_t)o] = m;
+    first[(size_t)m] = (int8_t)l;
+    first[(size_t)o] = nb_slot[(size_t)(3 * m + l)];
+    for (const int64_t x : {m, o})
+      for (int c = 0; c < 3; ++c) {
+        const int64_t y = nb[(size_t)(3 * x + c)];
+        if (y >= 0 && partner[(size_t)y] < 0 && --deg[(size_t)y] == 1) ones.push_back(y);
+      }
+  };
+  auto free_slot = [&](int64_t m) {
+    for (int l = 0; l < 3; ++l) {
+      const int64_t o = nb[(size_t)(3 * m + l)];
+      if (o >= 0 && partner[(size_t)o] < 0) return l;
+    }
+    return -1;
+  };
+  int64_t scan = 0;
+  for (;;) {
+    int64_t m = -1;
+    while (!ones.empty() && m < 0) {
+      const int64_t c = ones.back();
+      ones.pop_back();
+      if (partner[(size_t)c] < 0 && free_slot(c) >= 0) m = c;
+    }
+    while (m < 0 && scan < nf) {
+      if (partner[(size_t)scan] < 0 && free_slot(scan) >= 0) m = scan;
+      ++scan;
+    }
+    if (m < 0) break;
+    match(m, free_slot(m));
+  }
+  int64_t k = 0;
+  auto put = [&](int64_t dst, int64_t m, int l) {
+    for (int c = 0; c < 3; ++c) out[3 * dst + c] = f[3 * m + (l + c) % 3];
+  };
+  for (int64_t m = 0; m < nf; ++m)
+    if (partner[(size_t)m] > m) {
+      put(2 * k, m, first[(size_t)m]);
+      put(2 * k + 1, partner[(size_t)m], first[(size_t)partner[(size_t)m]]);
+      ++k;
+    }
+  int64_t w = 2 * k;
+  for (int64_t m = 0; m < nf; ++m)
+    if (partner[(size_t)m] < 0) put(w++, m, 0);
+  *n_pairs = k;
+  return PFT_OK;
 }
 
 int pft_version(void) { return 10000 * 0 + 100 * 1 + 0; }

@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(NT, kBatchedMinBlocks<Pol, R, NT>) k_batched(
         ok = false;
         break;
       }
-      Pol::template tile<R>(ring + s * TILE, min(TILE, cnt - t * TILE), qr, acc, th);
+      Pol::template tile<R>(ring + s * TILE, min(TILE, cnt - t * TILE), qr, acc, th, 0);
       __syncwarp();
       if ((threadIdx.x & 31) == 0) {
         __threadfence_block();

@@ -20,6 +20,7 @@ enum : uint32_t {
   ST_NONFINITE = 1u << 1,
   ST_TIMEOUT = 1u << 2,
   ST_OFFSETS = 1u << 3,
+  ST_PAIRS = 1u << 4,
 };
 
 __device__ __forceinline__ void set_status(uint32_t* st, uint32_t bit) { atomicOr(st, bit); }

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_fwd(const typena
     const int s = t % kStages;
     if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], (uint32_t)((t / kStages) & 1)))) { ok = false; break; }
     const int cnt = (int)min((int64_t)TILE, n - (int64_t)t * TILE);
-    Pol::template tile<R>(ring + s * TILE, cnt, qr, acc, th);
+    Pol::template tile<R>(ring + s * TILE, cnt, qr, acc, th, i0 + (int64_t)t * TILE);
     __syncwarp();
     if ((threadIdx.x & 31) == 0) {
       __threadfence_block();                       // this warp's reads of slot s come first
@@ -144,6 +144,16 @@ cudaError_t dispatch(int r, int nt, F&& f) {
   return cudaErrorInvalidConfiguration;
 }
 
+// The paired-face policy: the FP32 launch shapes with R <= 4.
+template <class F>
+cudaError_t dispatch_pairs(int r, int nt, F&& f) {
+#define PFT_CASE(RR, NN) \
+  if (r == RR && nt == NN) return f.template operator()<Pol3F32Pair, RR, NN>();
+  PFT_CASE(1, 128) PFT_CASE(2, 128) PFT_CASE(4, 128) PFT_CASE(1, 256) PFT_CASE(2, 256) PFT_CASE(4, 256)
+#undef PFT_CASE
+  return cudaErrorInvalidConfiguration;
+}
+
 struct LaunchF {
   const FwdLaunch& L; const void* items; int64_t n_items; const double* q; int64_t n_q; Thr th;
   double2* partial; uint32_t* status; cudaStream_t st;
@@ -160,21 +170,25 @@ struct OccF {
 }  // namespace
 
 cudaError_t launch_fwd(int dim, bool fp64, const FwdLaunch& L, const void* items, int64_t n_items, const double* q,
-                       int64_t n_q, float tau, double2* partial, uint32_t* status, cudaStream_t st) {
+                       int64_t n_q, float tau, double2* partial, uint32_t* status, cudaStream_t st,
+                       int64_t pair_faces) {
   // the FP64 path keeps its series (through k = 16) for P < 9/4, where it truncates below 1e-14
   if (fp64) tau = fminf(tau, 3.0f);
   const float tau_lo = fminf(tau, kTauLo);
-  const Thr th{0.25f * tau * tau, 0.25f * tau_lo * tau_lo, tau > 1.0f ? 1 : 0, tau > 3.0f ? 1 : 0};
+  const Thr th{0.25f * tau * tau, 0.25f * tau_lo * tau_lo, tau > 1.0f ? 1 : 0, tau > 3.0f ? 1 : 0,
+               dim == 3 && !fp64 ? pair_faces : 0};
   LaunchF f{L, items, n_items, q, n_q, th, partial, status, st};
   if (dim == 2) return fp64 ? dispatch<Pol2F64>(L.r, L.nt, f) : dispatch<Pol2F32>(L.r, L.nt, f);
+  if (!fp64 && th.pair_end > 0) return dispatch_pairs(L.r, L.nt, f);
   return fp64 ? dispatch<Pol3F64>(L.r, L.nt, f) : dispatch<Pol3F32>(L.r, L.nt, f);
 }
 
-int fwd_blocks_per_sm(int dim, bool fp64, int r, int nt) {
+int fwd_blocks_per_sm(int dim, bool fp64, int r, int nt, bool pairs) {
   int b = 1;
   OccF f{&b};
   cudaError_t e;
   if (dim == 2) e = fp64 ? dispatch<Pol2F64>(r, nt, f) : dispatch<Pol2F32>(r, nt, f);
+  else if (!fp64 && pairs) e = dispatch_pairs(r, nt, f);
   else e = fp64 ? dispatch<Pol3F64>(r, nt, f) : dispatch<Pol3F32>(r, nt, f);
   return e == cudaSuccess ? b : 1;
 }

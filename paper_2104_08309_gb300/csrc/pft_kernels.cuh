@@ -75,11 +75,14 @@ cudaError_t launch_init_header(WsHeader* h, cudaStream_t st);
 cudaError_t launch_bbox(const float* v, int64_t n, int dim, WsHeader* h, cudaStream_t st);
 cudaError_t launch_prep2d(const float* v, int64_t nv, const int64_t* off, int64_t nl, WsHeader* h,
                           void* segs, bool fp64, double* partials, int nblk, cudaStream_t st);
+// pair_faces: the faces [0, pair_faces) come in pairs (2k, 2k+1) that share their first edge in
+// opposite directions (face_pairs option); k_prep3d checks them, k_fwd shares the edge's sinc.
 cudaError_t launch_prep3d(const float* v, int64_t nv, const int32_t* f, int64_t nf, WsHeader* h,
-                          void* faces, bool fp64, double* partials, int nblk, cudaStream_t st);
+                          void* faces, bool fp64, double* partials, int nblk, cudaStream_t st,
+                          int64_t pair_faces = 0);
 cudaError_t launch_fwd(int dim, bool fp64, const FwdLaunch& L, const void* items, int64_t n_items,
                        const double* q, int64_t n_q, float tau, double2* partial, uint32_t* status,
-                       cudaStream_t st);
+                       cudaStream_t st, int64_t pair_faces = 0);
 cudaError_t launch_fan3d(const int32_t* idx, int64_t n_idx, const int64_t* off, int64_t n_faces, int32_t* tris,
                          int64_t n_tris, WsHeader* h, cudaStream_t st);
 cudaError_t launch_finalize(int dim, const double* q, int64_t n_q, const double2* partial, int k_splits,
@@ -95,7 +98,7 @@ constexpr int kPrepThreads = 256;
 inline int prep_blocks(int64_t n) { return (int)((n + kPrepThreads - 1) / kPrepThreads); }
 
 // Occupancy query for the main kernel of a configuration (blocks per SM).
-int fwd_blocks_per_sm(int dim, bool fp64, int r, int nt);
+int fwd_blocks_per_sm(int dim, bool fp64, int r, int nt, bool pairs = false);
 int fwd_tile(int dim, bool fp64);
 
 }  // namespace pft

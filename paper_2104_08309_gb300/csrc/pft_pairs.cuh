@@ -14,6 +14,7 @@ struct Thr {
   float hi, lo;
   int longs;    // tau > 1: warps whose faces are not all below kPShort take a longer series (adjoint)
   int xlongs;   // tau > 3: warps whose faces are not all below kPLong take the extra-long series (adjoint)
+  int64_t pair_end;   // faces [0, pair_end) come in pairs sharing their first edge (forward, 3D FP32)
 };
 constexpr float kTauLo = 0.05f;
 constexpr float kPShort = 0.25f;   // P below which the short series (k <= 7) suffices (tau = 1)
@@ -26,9 +27,10 @@ constexpr float kP13 = 4.0f;       // P below which the k <= 13 series suffices 
 // 3D default (R = 4, 128 threads) is held to 102 registers for 5 blocks (20
 // warps), which it fits without spilling and which ran 9 % faster than 4 blocks.
 // (FP64 paths: one block, so that the double-precision temporaries never spill.)
+// The paired-face kernel (two faces' projections held at once) gets 4 blocks, 128 registers.
 template <class Pol, int R, int NT>
 constexpr int kMinBlocks = sizeof(typename Pol::QT) == 8 ? 1
-                           : (Pol::kDim == 3 && R == 4 && NT == 128) ? 5
+                           : (Pol::kDim == 3 && R == 4 && NT == 128) ? (Pol::kPaired ? 4 : 5)
                            : (NT == 256 ? 1 : 2) * (R >= 8 ? 1 : (R == 4 ? 2 : 3));
 
 // ---------------------------------------------------------------------------
@@ -236,9 +238,13 @@ __device__ __forceinline__ void face_series_xlong(float T, float P, float& zr, f
   zi = gre;
 }
 
-// Z from the edge sum of Eq. 14.
+// Z from the edge sum of Eq. 14.  The first edge's sinc(u_0) comes in through S0 when kShared
+// (the other face of a pair evaluated it: the same edge run the other way, and sinc is even) and
+// goes out through it otherwise.
+template <bool kShared = false>
 __device__ __forceinline__ void face_edge(float qx, float qy, float qz, const float4 A, const float4 B,
-                                          const float4 C, float a0, float a1, float& zr, float& zi) {
+                                          const float4 C, float a0, float a1, float& zr, float& zi,
+                                          float& S0) {
   const float nx = C.y, ny = C.z, nz = C.w;
   const float Xx = fmaf(ny, qz, -nz * qy), Xy = fmaf(nz, qx, -nx * qz), Xz = fmaf(nx, qy, -ny * qx);
   const float x2 = fmaf(Xx, Xx, fmaf(Xy, Xy, Xz * Xz));
@@ -257,16 +263,18 @@ __device__ __forceinline__ void face_edge(float qx, float qy, float qz, const fl
   sp[0] = -fmaf(sp[1], cp[2], cp[1] * sp[2]);
   float u2[3], S[3];
 #pragma unroll
-  for (int l = 0; l < 3; ++l) {
+  for (int l = kShared ? 1 : 0; l < 3; ++l) {
     u2[l] = u[l] * u[l];
     S[l] = sinc_poly(u2[l]);
   }
   // rare: an edge with |Q.d_l| > 2 pi somewhere in the warp (face_edge runs warp-converged)
-  if (__any_sync(0xffffffffu, fmaxf(u2[0], fmaxf(u2[1], u2[2])) > kPi2)) {
+  if (__any_sync(0xffffffffu, fmaxf(kShared ? 0.f : u2[0], fmaxf(u2[1], u2[2])) > kPi2)) {
 #pragma unroll
-    for (int l = 0; l < 3; ++l)
+    for (int l = kShared ? 1 : 0; l < 3; ++l)
       if (u2[l] > kPi2) S[l] = sinc_large(u[l]);
   }
+  if (kShared) S[0] = S0;
+  else S0 = S[0];
   float sr = 0.f, si = 0.f;
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
@@ -372,10 +380,12 @@ struct Acc64 {
 struct Pol2F32 {
   using Item = Seg32;
   static constexpr int kDim = 2, kTile = 128;
+  static constexpr bool kPaired = false;
   template <int R> using Acc = Acc32<R>;
   using QT = float;
   template <int R>
-  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc, Thr) {
+  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc, Thr,
+                                              int64_t) {
     float tre[R], tim[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { tre[r] = 0.f; tim[r] = 0.f; }
@@ -417,10 +427,12 @@ struct Pol2F32 {
 struct Pol2F64 {
   using Item = Seg64;
   static constexpr int kDim = 2, kTile = 64;
+  static constexpr bool kPaired = false;
   template <int R> using Acc = Acc64<R>;
   using QT = double;
   template <int R>
-  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc, Thr) {
+  __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc, Thr,
+                                              int64_t) {
     for (int i = 0; i < cnt; ++i) {
       const Seg64 s = t[i];
 #pragma unroll
@@ -434,14 +446,78 @@ struct Pol2F64 {
   }
 };
 
-struct Pol3F32 {
+// One face of the 3D FP32 policy for a thread's R Q points: the projections, their branch
+// quantities and the warp's largest P (the branch tests need only it and the thread's smallest P).
+template <int R>
+struct FaceQ {
+  float mu[R], a0[R], a1[R], s[R], P[R], T[R];
+  float pmin, wmax;
+  __device__ __forceinline__ void load(const float (&q)[R][3], const float4 A, const float4 B, const float4 C) {
+    float pmax = 0.f;
+    pmin = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      face_common_pt(q[r][0], q[r][1], q[r][2], A, B, C, mu[r], a0[r], a1[r], s[r], P[r], T[r]);
+      pmax = r ? fmaxf(pmax, P[r]) : P[r];
+      pmin = r ? fminf(pmin, P[r]) : P[r];
+    }
+    // P >= +0 (it is s1^2 - a0 a1 = a0^2 + a0 a1 + a1^2) or NaN, so its bits order as unsigned
+    // integers, and one reduction replaces a vote per rung of the ladder
+    wmax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(pmax)));
+  }
+  // the shortest series whose bound holds for the whole warp (wmax and th.hi are uniform)
+  __device__ __forceinline__ void series(const Thr& th, float (&zr)[R], float (&zi)[R]) const {
+    if (th.hi <= kPShort || wmax < kPShort) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) face_series(T[r], P[r], zr[r], zi[r]);
+    } else if (th.hi <= kP9 || wmax < kP9) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) face_series_k9(T[r], P[r], zr[r], zi[r]);
+    } else if (th.hi <= kPLong || wmax < kPLong) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) face_series_long(T[r], P[r], zr[r], zi[r]);
+    } else if (th.hi <= kP13 || wmax < kP13) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) face_series_k13(T[r], P[r], zr[r], zi[r]);
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) face_series_xlong(T[r], P[r], zr[r], zi[r]);
+    }
+  }
+  // the edge sum, with the few Q points below tau_lo^2/4 redone by the short series
+  template <bool kShared>
+  __device__ __forceinline__ void edge(const Thr& th, const float (&q)[R][3], const float4 A, const float4 B,
+                                       const float4 C, float (&zr)[R], float (&zi)[R], float (&S0)[R]) const {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      face_edge<kShared>(q[r][0], q[r][1], q[r][2], A, B, C, a0[r], a1[r], zr[r], zi[r], S0[r]);
+    if (pmin < th.lo) {
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (P[r] < th.lo) face_series(T[r], P[r], zr[r], zi[r]);   // P < tau_lo^2/4 <= 1/4
+    }
+  }
+  __device__ __forceinline__ void finish(const float (&zr)[R], const float (&zi)[R], float (&tre)[R],
+                                         float (&tim)[R]) const {
+#pragma unroll
+    for (int r = 0; r < R; ++r) face_finish(mu[r], s[r], zr[r], zi[r], tre[r], tim[r]);
+  }
+};
+
+// kPairs: faces [0, th.pair_end) come in pairs that share their first edge (face_pairs option); a
+// separate instantiation, so that the single-face kernel keeps its register budget.
+template <bool kPairs>
+struct Pol3F32T {
   using Item = Face32;
   static constexpr int kDim = 3, kTile = 64;
+  static constexpr bool kPaired = kPairs;
   template <int R> using Acc = Acc32<R>;
   using QT = float;
+  // `first`: index of the tile's first face among all faces (pairs start at even indices, and tiles
+  // start at multiples of kTile, so a pair never straddles two tiles).
   template <int R>
   __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc,
-                                              Thr th) {
+                                              Thr th, int64_t first) {
     float tre[R], tim[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { tre[r] = 0.f; tim[r] = 0.f; }
@@ -449,60 +525,49 @@ struct Pol3F32 {
     for (int i = 0; i < cnt; ++i) {
       const float4* p = reinterpret_cast<const float4*>(t + i);
       const float4 A = p[0], B = p[1], C = p[2];
-      float mu[R], a0[R], a1[R], s[R], P[R], T[R], zr[R], zi[R];
-      float pmax = 0.f, pmin = 0.f;   // over the thread's Q points: the branch tests need only these
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        face_common_pt(q[r][0], q[r][1], q[r][2], A, B, C, mu[r], a0[r], a1[r], s[r], P[r], T[r]);
-        pmax = r ? fmaxf(pmax, P[r]) : P[r];
-        pmin = r ? fminf(pmin, P[r]) : P[r];
-      }
-      // the warp's largest P: P >= +0 (it is s1^2 - a0 a1 = a0^2 + a0 a1 + a1^2) or NaN, so its bits
-      // order as unsigned integers, and one reduction replaces a vote per rung of the ladder
-      const float wmax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(pmax)));
-      if (wmax < th.hi) {
-        // the shortest series whose bound holds for the whole warp (wmax and th.hi are uniform)
-        if (th.hi <= kPShort || wmax < kPShort) {
-#pragma unroll
-          for (int r = 0; r < R; ++r) face_series(T[r], P[r], zr[r], zi[r]);
-        } else if (th.hi <= kP9 || wmax < kP9) {
-#pragma unroll
-          for (int r = 0; r < R; ++r) face_series_k9(T[r], P[r], zr[r], zi[r]);
-        } else if (th.hi <= kPLong || wmax < kPLong) {
-#pragma unroll
-          for (int r = 0; r < R; ++r) face_series_long(T[r], P[r], zr[r], zi[r]);
-        } else if (th.hi <= kP13 || wmax < kP13) {
-#pragma unroll
-          for (int r = 0; r < R; ++r) face_series_k13(T[r], P[r], zr[r], zi[r]);
+      FaceQ<R> f;
+      f.load(q, A, B, C);
+      float zr[R], zi[R], S0[R];
+      if (kPairs && first + i < th.pair_end) {   // faces i and i + 1 share their first edge (warp-uniform)
+        const float4* p2 = reinterpret_cast<const float4*>(t + i + 1);
+        const float4 A2 = p2[0], B2 = p2[1], C2 = p2[2];
+        FaceQ<R> f2;
+        f2.load(q, A2, B2, C2);
+        float zr2[R], zi2[R];
+        if (f.wmax >= th.hi && f2.wmax >= th.hi) {   // both edge sums: the shared edge's sinc once
+          f.template edge<false>(th, q, A, B, C, zr, zi, S0);
+          f2.template edge<true>(th, q, A2, B2, C2, zr2, zi2, S0);
         } else {
-#pragma unroll
-          for (int r = 0; r < R; ++r) face_series_xlong(T[r], P[r], zr[r], zi[r]);
+          if (f.wmax < th.hi) f.series(th, zr, zi);
+          else f.template edge<false>(th, q, A, B, C, zr, zi, S0);
+          if (f2.wmax < th.hi) f2.series(th, zr2, zi2);
+          else f2.template edge<false>(th, q, A2, B2, C2, zr2, zi2, S0);
         }
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) face_edge(q[r][0], q[r][1], q[r][2], A, B, C, a0[r], a1[r], zr[r], zi[r]);
-        if (pmin < th.lo) {
-#pragma unroll
-          for (int r = 0; r < R; ++r)
-            if (P[r] < th.lo) face_series(T[r], P[r], zr[r], zi[r]);   // P < tau_lo^2/4 <= 1/4
-        }
+        f.finish(zr, zi, tre, tim);
+        f2.finish(zr2, zi2, tre, tim);
+        ++i;
+        continue;
       }
-#pragma unroll
-      for (int r = 0; r < R; ++r) face_finish(mu[r], s[r], zr[r], zi[r], tre[r], tim[r]);
+      if (f.wmax < th.hi) f.series(th, zr, zi);
+      else f.template edge<false>(th, q, A, B, C, zr, zi, S0);
+      f.finish(zr, zi, tre, tim);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) { acc.re[r].add(tre[r]); acc.im[r].add(tim[r]); }
   }
 };
+using Pol3F32 = Pol3F32T<false>;
+using Pol3F32Pair = Pol3F32T<true>;
 
 struct Pol3F64 {
   using Item = Face64;
   static constexpr int kDim = 3, kTile = 32;
+  static constexpr bool kPaired = false;
   template <int R> using Acc = Acc64<R>;
   using QT = double;
   template <int R>
   __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc,
-                                              Thr th) {
+                                              Thr th, int64_t) {
     for (int i = 0; i < cnt; ++i) {
       const Face64 f = t[i];
 #pragma unroll

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep2d(const float* __restrict
 template <bool FP64>
 __global__ void __launch_bounds__(kPrepThreads) k_prep3d(const float* __restrict__ v, int64_t nv,
                                                          const int32_t* __restrict__ f, int64_t nf, WsHeader* h,
-                                                         void* items, double* partials) {
+                                                         void* items, double* partials, int64_t pair_faces) {
   __shared__ double sh[kPrepThreads / 32];
   const int64_t m = blockIdx.x * (int64_t)kPrepThreads + threadIdx.x;
   double c[3];
@@ -145,8 +145,15 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep3d(const float* __restrict
   if (m < nf) {
     const int32_t i0 = f[3 * m], i1 = f[3 * m + 1], i2 = f[3 * m + 2];
     double g[3] = {0, 0, 0}, q0[3] = {0, 0, 0}, q1[3] = {0, 0, 0}, N[3] = {0, 0, 0};
+    bool paired_ok = true;   // a face of a pair: the pair's first edges must be (a, b) and (b, a)
+    if (m < pair_faces) {
+      const int64_t a = m & ~(int64_t)1;
+      paired_ok = f[3 * a] == f[3 * (a + 1) + 1] && f[3 * a + 1] == f[3 * (a + 1)];
+    }
     if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nv || i1 >= nv || i2 >= nv) {
       set_status(&h->status, ST_INDEX);   // the face is skipped (all-zero record contributes 0)
+    } else if (!paired_ok) {
+      set_status(&h->status, ST_PAIRS);   // both faces of the pair are skipped
     } else {
       double P[3][3];
       const int32_t id[3] = {i0, i1, i2};
@@ -397,9 +404,9 @@ cudaError_t launch_prep2d(const float* v, int64_t nv, const int64_t* off, int64_
 }
 
 cudaError_t launch_prep3d(const float* v, int64_t nv, const int32_t* f, int64_t nf, WsHeader* h, void* faces,
-                          bool fp64, double* partials, int nblk, cudaStream_t st) {
-  if (fp64) k_prep3d<true><<<nblk, kPrepThreads, 0, st>>>(v, nv, f, nf, h, faces, partials);
-  else k_prep3d<false><<<nblk, kPrepThreads, 0, st>>>(v, nv, f, nf, h, faces, partials);
+                          bool fp64, double* partials, int nblk, cudaStream_t st, int64_t pair_faces) {
+  if (fp64) k_prep3d<true><<<nblk, kPrepThreads, 0, st>>>(v, nv, f, nf, h, faces, partials, pair_faces);
+  else k_prep3d<false><<<nblk, kPrepThreads, 0, st>>>(v, nv, f, nf, h, faces, partials, pair_faces);
   return cudaGetLastError();
 }
 

@@ -23,7 +23,7 @@ def test_branch_fractions_partition_the_pairs(mesh):
         # no form beyond the one whose bound covers p_hi = tau^2/4
         for name, b in bench.SERIES_BOUNDS:
             if 0.25 * tau * tau <= b:
-                later = list(bench.OPS)[list(bench.OPS).index(name) + 1:-1]
+                later = [k for k in list(bench.OPS)[list(bench.OPS).index(name) + 1:] if k.startswith("series")]
                 assert all(m[k] == 0.0 for k in later), (tau, name)
                 break
     lo = bench.branch_mix(v, f, q, tau=1.0, n_warps=512)
@@ -220,3 +220,19 @@ def test_adjoint_branch_mix_partitions_the_lanes(mesh):
             assert bench.OPS_ADJ["common"]["fp32"] < ops["fp32"] <= sum(x["fp32"] for x in bench.OPS_ADJ.values())
             if tau <= 3.0:
                 assert lane["xlong"] == 0.0
+
+
+def test_branch_mix_with_pairs_splits_the_edge_sums(mesh):
+    """Pairing moves edge-sum units into edge_sum_shared and leaves every other fraction as it was."""
+    import paper_2104_08309_gb300 as pft
+    v, f = mesh
+    fp, n = pft.pair_faces(f)
+    q = synth.q_grid_3d(32, 60.0)
+    plain = bench.branch_mix(v, fp, q, tau=1.0, n_warps=512)
+    paired = bench.branch_mix(v, fp, q, tau=1.0, n_warps=512, n_pairs=n)
+    assert plain["edge_sum_shared"] == 0.0
+    assert abs(paired["edge_sum"] + paired["edge_sum_shared"] - plain["edge_sum"]) < 1e-12
+    assert paired["edge_sum_shared"] > 0.5 * plain["edge_sum"]
+    for k in plain:
+        if not k.startswith("edge"):
+            assert paired[k] == plain[k]
