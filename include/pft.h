@@ -276,18 +276,23 @@ int pft3d_mesh_backward(const float* verts, int64_t n_verts, const int32_t* face
                         const double* q, int64_t n_q, const double* grad_out, float* grad_verts,
                         void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
 
-/* Adjoint of a batch of polygons on a shared Q set (the forward is
- * pft2d_polygons_batched with q_off = NULL): poly_off [n_polys + 1] int64 on the
- * device (each polygon one counter-clockwise loop; malformed offsets set
- * PFT_ERR_OFFSETS), grad_out [n_polys][n_q][2] = (dL/dRe F_i(Q), dL/dIm F_i(Q)),
- * grad_verts [n_verts][2] float32 overwritten with sum_Q Re(conj(g_i) dF_i/dv)
- * for the vertices of polygon i.  The workspace holds one Q record per (polygon,
- * Q) row: 36 bytes x n_polys x n_q plus per-vertex terms. */
-size_t pft2d_batched_backward_workspace_size(int64_t n_verts, int64_t n_polys, int64_t n_q,
+/* Adjoint of a batch of polygons, the backward of pft2d_polygons_batched: poly_off
+ * [n_polys + 1] int64 on the device (each polygon one counter-clockwise loop;
+ * malformed offsets set PFT_ERR_OFFSETS); Q as in the forward call: q_off == NULL
+ * for one shared list of n_q points (grad_out [n_polys][n_q][2]), or q_off
+ * [n_polys + 1] int64 on the device giving polygon i the points q[q_off[i] ..
+ * q_off[i+1]-1] (grad_out [n_q][2] in the same order; malformed q_off sets
+ * PFT_ERR_OFFSETS).  grad_out holds (dL/dRe F_i(Q), dL/dIm F_i(Q)); grad_verts
+ * [n_verts][2] float32 is overwritten with sum_Q Re(conj(g_i) dF_i/dv) for the
+ * vertices of polygon i.  The workspace holds one 36-byte Q record per (polygon,
+ * Q) row (n_polys x n_q rows shared, n_q rows with q_off) plus per-vertex terms;
+ * per_polygon_q tells the size function which (0: shared, 1: q_off). */
+size_t pft2d_batched_backward_workspace_size(int64_t n_verts, int64_t n_polys, int64_t n_q, int per_polygon_q,
                                              const pft_options* opts);
 int pft2d_polygons_batched_backward(const float* verts, int64_t n_verts, const int64_t* poly_off, int64_t n_polys,
-                                    const double* q, int64_t n_q, const double* grad_out, float* grad_verts,
-                                    void* ws, size_t ws_bytes, const pft_options* opts, void* stream);
+                                    const double* q, const int64_t* q_off, int64_t n_q, const double* grad_out,
+                                    float* grad_verts, void* ws, size_t ws_bytes, const pft_options* opts,
+                                    void* stream);
 
 /* Adjoint of pft3d_polymesh (same faces, same split into triangles): grad_verts
  * [n_verts][3] float32 from grad_out as for pft3d_mesh_backward.  The workspace

@@ -444,26 +444,31 @@ def pft2d_polygons_qgrad(verts, q, grad_out, loop_off=None, *, options=None, out
     return out
 
 
-def pft2d_polygons_batched_backward(verts, poly_off, q, grad_out, *, options=None, out=None, ws=None, stream=None,
-                                    check_status=False):
-    """dL/dverts [n_v, 2] float32 for a batch of polygons on a shared Q set, from grad_out
-    [n_polys, n_q, 2] = (dL/dRe F_i(Q), dL/dIm F_i(Q))."""
+def pft2d_polygons_batched_backward(verts, poly_off, q, grad_out, q_off=None, *, options=None, out=None, ws=None,
+                                    stream=None, check_status=False):
+    """dL/dverts [n_v, 2] float32 for a batch of polygons, from grad_out = (dL/dRe F_i(Q), dL/dIm F_i(Q)):
+    [n_polys, n_q, 2] on a shared Q set (q_off None), or [n_q, 2] with polygon i on q[q_off[i]:q_off[i+1]]."""
     torch = _torch()
     v = _dev(verts, torch.float32, "verts", 2)
     off = poly_off if (isinstance(poly_off, torch.Tensor) and poly_off.is_cuda) else _host_i64(poly_off).to(v.device)
     off = _dev(off, torch.int64, "poly_off").reshape(-1)
     qq = _dev(q, torch.float64, "q", 2)
     np_, nq = off.shape[0] - 1, qq.shape[0]
-    g = _dev(grad_out, torch.float64, "grad_out").reshape(np_ * nq, 2)
+    qo = None
+    if q_off is not None:
+        qo = q_off if (isinstance(q_off, torch.Tensor) and q_off.is_cuda) else _host_i64(q_off).to(v.device)
+        qo = _dev(qo, torch.int64, "q_off").reshape(-1)
+    g = _dev(grad_out, torch.float64, "grad_out").reshape(nq if qo is not None else np_ * nq, 2)
     o = make_options(options)
     lib = load()
-    nb = lib.pft2d_batched_backward_workspace_size(v.shape[0], np_, nq, ctypes.byref(o))
+    nb = lib.pft2d_batched_backward_workspace_size(v.shape[0], np_, nq, int(qo is not None), ctypes.byref(o))
     ws = _ws(nb, v.device, ws)
     out = torch.empty(v.shape[0], 2, dtype=torch.float32, device=v.device) if out is None else out
     st = _stream(stream, v.device)
-    check(lib.pft2d_polygons_batched_backward(v.data_ptr(), v.shape[0], off.data_ptr(), np_, qq.data_ptr(), nq,
-                                              g.data_ptr(), out.data_ptr(), ws.data_ptr(), ws.numel(),
-                                              ctypes.byref(o), st), "pft2d_polygons_batched_backward")
+    check(lib.pft2d_polygons_batched_backward(v.data_ptr(), v.shape[0], off.data_ptr(), np_, qq.data_ptr(),
+                                              None if qo is None else qo.data_ptr(), nq, g.data_ptr(),
+                                              out.data_ptr(), ws.data_ptr(), ws.numel(), ctypes.byref(o), st),
+          "pft2d_polygons_batched_backward")
     if check_status:
         check(lib.pft_status(ws.data_ptr(), st), "pft2d_polygons_batched_backward (device status)")
     return out
@@ -539,19 +544,19 @@ def _autograd():
 
     class _FT2DBatched(torch.autograd.Function):
         @staticmethod
-        def forward(ctx, verts, poly_off, q, options):
-            ctx.save_for_backward(verts, poly_off, q)
+        def forward(ctx, verts, poly_off, q, q_off, options):
+            ctx.save_for_backward(verts, poly_off, q, q_off)
             ctx.precision = make_options(options).precision
-            return pft2d_polygons_batched(verts.detach(), poly_off, q, options=options)
+            return pft2d_polygons_batched(verts.detach(), poly_off, q, q_off, options=options)
 
         @staticmethod
         def backward(ctx, g):
-            verts, poly_off, q = ctx.saved_tensors
+            verts, poly_off, q, q_off = ctx.saved_tensors
             # the forward's precision goes to the adjoint, which refuses FP64 (it has an FP32 path
             # only); the forward's launch shape does not apply to it
-            gv = pft2d_polygons_batched_backward(verts.detach(), poly_off, q, g.contiguous(),
+            gv = pft2d_polygons_batched_backward(verts.detach(), poly_off, q, g.contiguous(), q_off,
                                                  options={"precision": ctx.precision})
-            return gv, None, None, None
+            return gv, None, None, None, None
 
     return _FT2D, _FT3D, _FT3DPoly, _FT2DBatched
 
@@ -577,8 +582,9 @@ def ft3d(verts, faces, q, options=None):
     return torch.view_as_complex(_FNS[1].apply(verts, faces, q, options))
 
 
-def ft2d_batched(verts, poly_off, q, options=None):
-    """Differentiable FT_A of each polygon of a batch on a shared Q set, complex128 [n_polys, n_q];
+def ft2d_batched(verts, poly_off, q, options=None, q_off=None):
+    """Differentiable FT_A of each polygon of a batch, complex128 [n_polys, n_q] on a shared Q set, or
+    [n_q] with polygon i on q[q_off[i]:q_off[i+1]];
     grad w.r.t. verts via the batched adjoint, which runs in FP32 with compensated sums.  ``options``
     set the forward call (launch shape, precision); a gradient of an FP64 forward is refused (raised
     here when ``verts`` requires grad) rather than silently computed in FP32."""
@@ -591,7 +597,10 @@ def ft2d_batched(verts, poly_off, q, options=None):
                          "for a differentiable batch, or detach verts")
     off = poly_off if (isinstance(poly_off, torch.Tensor) and poly_off.is_cuda) else \
         _host_i64(poly_off).to(verts.device)
-    return torch.view_as_complex(_FNS[3].apply(verts, off, q, options))
+    qo = None
+    if q_off is not None:
+        qo = q_off if (isinstance(q_off, torch.Tensor) and q_off.is_cuda) else _host_i64(q_off).to(verts.device)
+    return torch.view_as_complex(_FNS[3].apply(verts, off, q, qo, options))
 
 
 def ft3d_poly(verts, face_idx, face_off, q, options=None):

@@ -1030,20 +1030,43 @@ __global__ void __launch_bounds__(kAux) k_bbprep(const float* __restrict__ v, in
 
 // One block per polygon: its Q records (weight 0 on small rows) and its small rows, listed in
 // Q order (a block-wide ordered compaction, so the gather below is deterministic).
-__global__ void __launch_bounds__(kAux) k_bbq(const double* __restrict__ q, const double* __restrict__ g, int64_t n_q,
+// Rows of polygon i: with q_off (per-polygon Q lists) rows q_off[i] .. q_off[i+1]-1 of q and g;
+// without, all n_q points of the shared q and rows i n_q .. (i+1) n_q - 1 of g.  Malformed
+// offsets set ST_OFFSETS and are clamped to [0, n_q].
+__device__ __forceinline__ void bb_rows(const int64_t* q_off, int64_t i, int64_t n_q, int64_t& qb, int64_t& gb,
+                                        int64_t& nqi) {
+  if (q_off == nullptr) {
+    qb = 0;
+    gb = i * n_q;
+    nqi = n_q;
+  } else {
+    const int64_t a = max((int64_t)0, min(q_off[i], n_q)), b = max(a, min(q_off[i + 1], n_q));
+    qb = gb = a;
+    nqi = b - a;
+  }
+}
+
+__global__ void __launch_bounds__(kAux) k_bbq(const double* __restrict__ q, const int64_t* __restrict__ q_off,
+                                              const double* __restrict__ g, int64_t n_q, int64_t np,
                                               const PolyC* __restrict__ pc, QRec* rec, int32_t* small,
-                                              int32_t* small_cnt) {
+                                              int32_t* small_cnt, WsHeader* h) {
   __shared__ int wcount[kAux / 32];
   __shared__ int base;
   const int64_t i = blockIdx.x;
   const PolyC P = pc[i];
+  if (q_off != nullptr && threadIdx.x == 0 &&
+      (q_off[i + 1] < q_off[i] || q_off[i] < 0 || q_off[i + 1] > n_q || (i == 0 && q_off[0] != 0) ||
+       (i == np - 1 && q_off[np] != n_q)))
+    set_status(&h->status, ST_OFFSETS);
+  int64_t qb, gb, nqi;
+  bb_rows(q_off, i, n_q, qb, gb, nqi);
   if (threadIdx.x == 0) base = 0;
   __syncthreads();
-  for (int64_t l0 = 0; l0 < n_q; l0 += kAux) {
+  for (int64_t l0 = 0; l0 < nqi; l0 += kAux) {
     const int64_t l = l0 + threadIdx.x;
     bool is_small = false;
-    if (l < n_q) {
-      const float qx = (float)q[2 * l], qy = (float)q[2 * l + 1];
+    if (l < nqi) {
+      const float qx = (float)q[2 * (qb + l)], qy = (float)q[2 * (qb + l) + 1];
       const double Qx = qx, Qy = qy, q2 = Qx * Qx + Qy * Qy;
       QRec r{qx, qy, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (q2 == 0.0 || q2 * ((double)P.rmax * (double)P.rmax) < kTauSmallQ * kTauSmallQ) {
@@ -1055,12 +1078,12 @@ __global__ void __launch_bounds__(kAux) k_bbq(const double* __restrict__ q, cons
         const float pr = (float)fma(-rint(ph * kInvTwoPiD), kTwoPiD, ph);
         float sp, cp;
         sincosf(pr, &sp, &cp);
-        const float gr = (float)g[2 * (i * n_q + l)], gi = (float)g[2 * (i * n_q + l) + 1];
+        const float gr = (float)g[2 * (gb + l)], gi = (float)g[2 * (gb + l) + 1];
         const float k = 2.0f / (float)q2;
         r.gr = k * fmaf(gr, cp, -gi * sp);
         r.gi = k * fmaf(gr, sp, gi * cp);
       }
-      rec[i * n_q + l] = r;
+      rec[gb + l] = r;
     }
     const unsigned m = __ballot_sync(0xffffffffu, is_small);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1071,7 +1094,7 @@ __global__ void __launch_bounds__(kAux) k_bbq(const double* __restrict__ q, cons
       if (w < wid) before += wcount[w];
       total += wcount[w];
     }
-    if (is_small) small[i * n_q + base + before + __popc(m & ((1u << lane) - 1u))] = (int32_t)l;
+    if (is_small) small[gb + base + before + __popc(m & ((1u << lane) - 1u))] = (int32_t)l;
     __syncthreads();
     if (threadIdx.x == 0) base += total;
     __syncthreads();
@@ -1087,7 +1110,8 @@ __global__ void __launch_bounds__(kAux) k_bbq(const double* __restrict__ q, cons
 __global__ void __launch_bounds__(kBwdNT) k_bbwd(const Seg32* __restrict__ segs, int64_t nv,
                                                  const int64_t* __restrict__ off, int64_t np,
                                                  const int64_t* __restrict__ bstart, const int32_t* __restrict__ nblk,
-                                                 const QRec* __restrict__ rec, int64_t n_q, int64_t per_split, Thr th,
+                                                 const QRec* __restrict__ rec, const int64_t* __restrict__ q_off,
+                                                 int64_t n_q, int64_t per_split, Thr th,
                                                  double* __restrict__ partial, uint32_t* status) {
   __shared__ __align__(128) QRec slots[kStages * kQTile];
   __shared__ __align__(8) uint64_t full[kStages];
@@ -1108,9 +1132,11 @@ __global__ void __launch_bounds__(kBwdNT) k_bbwd(const Seg32* __restrict__ segs,
   if (mine) F = reinterpret_cast<const float4*>(segs)[m];
   if (mine2) F2 = reinterpret_cast<const float4*>(segs)[m2];
   const bool live = __any_sync(0xffffffffu, mine), live2 = __any_sync(0xffffffffu, mine2);
+  int64_t qb, gb, nqi;
+  bb_rows(q_off, lo, n_q, qb, gb, nqi);
   const int64_t q0 = (int64_t)blockIdx.y * per_split;
-  const int64_t nq = max((int64_t)0, min(per_split, n_q - q0));
-  Ring<QRec, kQTile, kBwdNT> ring{slots, full, done, &issued, rec + lo * n_q + q0, nq,
+  const int64_t nq = max((int64_t)0, min(per_split, nqi - q0));
+  Ring<QRec, kQTile, kBwdNT> ring{slots, full, done, &issued, rec + gb + q0, nq,
                                   (int)((nq + kQTile - 1) / kQTile)};
   ring.start();
   CAcc acc[4], acc2[4];
@@ -1157,8 +1183,8 @@ __global__ void __launch_bounds__(kBwdNT) k_bbwd(const Seg32* __restrict__ segs,
 __global__ void k_bbvert(const float* __restrict__ v, int64_t nv, const int64_t* __restrict__ off, int64_t np,
                          const double* __restrict__ partial, int ks, const PolyC* __restrict__ pc,
                          const int32_t* __restrict__ small, const int32_t* __restrict__ small_cnt,
-                         const double* __restrict__ q, int64_t n_q, const double* __restrict__ g,
-                         float* __restrict__ grad) {
+                         const double* __restrict__ q, const int64_t* __restrict__ q_off, int64_t n_q,
+                         const double* __restrict__ g, float* __restrict__ grad) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= nv) return;
   int64_t lo = 0, hi = np;
@@ -1183,15 +1209,17 @@ __global__ void k_bbvert(const float* __restrict__ v, int64_t nv, const int64_t*
   const PolyC P = pc[lo];
   const int32_t ns = small_cnt[lo];
   if (ns > 0) {
+    int64_t qb, gb, nqi;
+    bb_rows(q_off, lo, n_q, qb, gb, nqi);
     const double c[2] = {P.cx, P.cy};
     const double pj[2] = {(double)v[2 * j] - c[0], (double)v[2 * j + 1] - c[1]};
     const double pn[2] = {(double)v[2 * jn] - c[0], (double)v[2 * jn + 1] - c[1]};
     const double pp[2] = {(double)v[2 * jp] - c[0], (double)v[2 * jp + 1] - c[1]};
     for (int32_t e = 0; e < ns; ++e) {
-      const int64_t l = small[lo * n_q + e];
-      const double qx = (double)(float)q[2 * l], qy = (double)(float)q[2 * l + 1];
+      const int64_t l = small[gb + e];
+      const double qx = (double)(float)q[2 * (qb + l)], qy = (double)(float)q[2 * (qb + l) + 1];
       const double phc = qx * c[0] + qy * c[1];
-      const double gr = g[2 * (lo * n_q + l)], gi = g[2 * (lo * n_q + l) + 1];
+      const double gr = g[2 * (gb + l)], gi = g[2 * (gb + l) + 1];
       double d0[2] = {0, 0}, d1[2] = {0, 0}, e0[2] = {0, 0}, e1[2] = {0, 0};
       seg_small(pj, pn, qx, qy, gr, gi, phc, d0, d1);   // j is the start
       seg_small(pp, pj, qx, qy, gr, gi, phc, e0, e1);   // j is the end
@@ -1495,7 +1523,9 @@ struct BbLayout {
   int64_t per_split, grid;
 };
 
-BbLayout bb_layout(int64_t nv, int64_t np, int64_t n_q) {
+// per_poly_q: Q lists per polygon (q_off), n_q rows in all; else a shared list, n_polys x n_q
+// rows.  Either way every polygon has at most n_q rows, which the Q chunking covers.
+BbLayout bb_layout(int64_t nv, int64_t np, int64_t n_q, bool per_poly_q) {
   BbLayout y{};
   y.grid = std::max<int64_t>(1, np + (nv + kBbSegs - 1) / kBbSegs);   // at least the pair blocks needed
   const int64_t slots = (int64_t)sm_count() * 8;
@@ -1503,7 +1533,7 @@ BbLayout bb_layout(int64_t nv, int64_t np, int64_t n_q) {
   const int64_t k = std::min<int64_t>({std::max<int64_t>(1, (4 * slots + y.grid - 1) / y.grid), q_tiles, 256});
   y.per_split = ((q_tiles + k - 1) / k) * kQTile;
   y.ks = (int)std::max<int64_t>(1, (n_q + y.per_split - 1) / y.per_split);
-  const int64_t rows = std::max<int64_t>(np * n_q, 1);
+  const int64_t rows = std::max<int64_t>(per_poly_q ? n_q : np * n_q, 1);
   size_t o = al(sizeof(WsHeader));
   y.segs = o;    o = al(o + sizeof(Seg32) * (size_t)std::max<int64_t>(nv, 1));
   y.pc = o;      o = al(o + sizeof(PolyC) * (size_t)std::max<int64_t>(np, 1));
@@ -1827,15 +1857,17 @@ int pft2d_polygons_qgrad(const float* verts, int64_t n_verts, const int64_t* loo
   return PFT_OK;
 }
 
-size_t pft2d_batched_backward_workspace_size(int64_t n_verts, int64_t n_polys, int64_t n_q, const pft_options* opts) {
+size_t pft2d_batched_backward_workspace_size(int64_t n_verts, int64_t n_polys, int64_t n_q, int per_polygon_q,
+                                             const pft_options* opts) {
   Thr th;
   if (n_verts < 0 || n_polys < 0 || n_q < 0 || check_opts(opts, th) != PFT_OK) return 0;
-  return bb_layout(n_verts, n_polys, n_q).total;
+  return bb_layout(n_verts, n_polys, n_q, per_polygon_q != 0).total;
 }
 
 int pft2d_polygons_batched_backward(const float* verts, int64_t n_verts, const int64_t* poly_off, int64_t n_polys,
-                                    const double* q, int64_t n_q, const double* grad_out, float* grad_verts,
-                                    void* ws, size_t ws_bytes, const pft_options* opts, void* stream) {
+                                    const double* q, const int64_t* q_off, int64_t n_q, const double* grad_out,
+                                    float* grad_verts, void* ws, size_t ws_bytes, const pft_options* opts,
+                                    void* stream) {
   g_bwd_launches = 0;
   Thr th;
   if (int e = check_opts(opts, th)) return e;
@@ -1844,7 +1876,8 @@ int pft2d_polygons_batched_backward(const float* verts, int64_t n_verts, const i
     return PFT_ERR_INVALID_ARG;
   if (n_q > 0 && (q == nullptr || grad_out == nullptr)) return PFT_ERR_INVALID_ARG;
   if (n_q > INT32_MAX || n_polys > INT32_MAX || n_polys * n_q > (int64_t)1 << 40) return PFT_ERR_UNSUPPORTED;
-  const BbLayout y = bb_layout(n_verts, n_polys, n_q);
+  if (q_off != nullptr && n_polys == 0) return PFT_ERR_INVALID_ARG;
+  const BbLayout y = bb_layout(n_verts, n_polys, n_q, q_off != nullptr);
   if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < y.total) return PFT_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   WsHeader* h = at<WsHeader>(ws, 0);
@@ -1868,19 +1901,19 @@ int pft2d_polygons_batched_backward(const float* verts, int64_t n_verts, const i
   PFT_BWD_LAUNCH();
   k_scan_add<<<nb, kAux, 0, st>>>(bstart, n_polys, btot);
   PFT_BWD_LAUNCH();
-  k_bbq<<<(unsigned)n_polys, kAux, 0, st>>>(q, grad_out, n_q, pc, at<QRec>(ws, y.rec), at<int32_t>(ws, y.small),
-                                            at<int32_t>(ws, y.scnt));
+  k_bbq<<<(unsigned)n_polys, kAux, 0, st>>>(q, q_off, grad_out, n_q, n_polys, pc, at<QRec>(ws, y.rec),
+                                            at<int32_t>(ws, y.small), at<int32_t>(ws, y.scnt), h);
   PFT_BWD_LAUNCH();
   if (y.grid > INT32_MAX) return PFT_ERR_UNSUPPORTED;
   dim3 grid((unsigned)y.grid, (unsigned)y.ks);
   PFT_MARK(g_ev_start);
-  k_bbwd<<<grid, kBwdNT, 0, st>>>(segs, n_verts, poly_off, n_polys, bstart, nblk, at<QRec>(ws, y.rec), n_q,
+  k_bbwd<<<grid, kBwdNT, 0, st>>>(segs, n_verts, poly_off, n_polys, bstart, nblk, at<QRec>(ws, y.rec), q_off, n_q,
                                   y.per_split, th, at<double>(ws, y.partial), &h->status);
   PFT_BWD_LAUNCH();
   PFT_MARK(g_ev_stop);
   k_bbvert<<<blocks(n_verts, kAux), kAux, 0, st>>>(verts, n_verts, poly_off, n_polys, at<double>(ws, y.partial), y.ks,
-                                                   pc, at<int32_t>(ws, y.small), at<int32_t>(ws, y.scnt), q, n_q,
-                                                   grad_out, grad_verts);
+                                                   pc, at<int32_t>(ws, y.small), at<int32_t>(ws, y.scnt), q, q_off,
+                                                   n_q, grad_out, grad_verts);
   PFT_BWD_LAUNCH();
   return PFT_OK;
 }

@@ -72,10 +72,13 @@ def test_workspace_sizes(lib):
     # adjoint-side sizes: Q records (32 B) and small-row lists (4 B) per (polygon, Q) row, segment records
     # and FP64 partials per vertex; the adjoints run in FP32 only, so FP64 options size to 0
     nv, npol, nq = 2675209, 4096, 4096
-    sb = lib.pft2d_batched_backward_workspace_size(nv, npol, nq, ctypes.byref(o))
+    sb = lib.pft2d_batched_backward_workspace_size(nv, npol, nq, 0, ctypes.byref(o))
     assert sb >= 256 + 36 * npol * nq + 16 * nv + 32 * nv and sb % 256 == 0
-    assert lib.pft2d_batched_backward_workspace_size(nv, npol, nq, ctypes.byref(o64)) == 0
-    assert lib.pft2d_batched_backward_workspace_size(-1, npol, nq, ctypes.byref(o)) == 0
+    assert lib.pft2d_batched_backward_workspace_size(nv, npol, nq, 0, ctypes.byref(o64)) == 0
+    assert lib.pft2d_batched_backward_workspace_size(-1, npol, nq, 0, ctypes.byref(o)) == 0
+    # per-polygon Q lists: n_q rows in all instead of n_polys x n_q
+    sp = lib.pft2d_batched_backward_workspace_size(nv, npol, nq * 16, 1, ctypes.byref(o))
+    assert 256 + 36 * nq * 16 + 16 * nv <= sp < sb
     sq = lib.pft3d_qgrad_workspace_size(40992, 81920, 32768, ctypes.byref(o))
     assert sq >= 256 + 81920 * 48 + 32768 * 32 and sq % 256 == 0
     assert lib.pft3d_qgrad_workspace_size(40992, 81920, 32768, ctypes.byref(o64)) == 0
