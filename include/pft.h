@@ -294,6 +294,28 @@ int pft2d_polygons_batched_backward(const float* verts, int64_t n_verts, const i
                                     float* grad_verts, void* ws, size_t ws_bytes, const pft_options* opts,
                                     void* stream);
 
+/* Adjoint of a batch of closed triangle meshes, the backward of pft3d_meshes_batched:
+ * verts [n_verts][3] float32 shared by all meshes, faces [n_faces][3] int32 (global
+ * vertex indices), mesh_off [n_meshes + 1] int64 on the device (CSR over faces:
+ * mesh i is faces mesh_off[i] .. mesh_off[i+1]-1; malformed offsets set
+ * PFT_ERR_OFFSETS); Q as in the forward call: q_off == NULL for one shared list of
+ * n_q points (grad_out [n_meshes][n_q][2]) or per-mesh lists q[q_off[i] ..
+ * q_off[i+1]-1] (grad_out [n_q][2]).  grad_verts [n_verts][3] float32 is overwritten
+ * with sum over meshes and their Q of Re(conj(g_i) dF_i/dv) (vertices used by no mesh
+ * get 0).  Each mesh is centred on the bounding box of its own corners; the pair
+ * adjoint is that of pft3d_mesh_backward (Eq. 14 and its series differentiated in
+ * reverse mode, FP32 with compensated sums; |Q| r_max < 0.25 in FP64 from the corner
+ * series), the vertex sums in a fixed order.  Options and errors as for
+ * pft3d_mesh_backward; the workspace holds one 36-byte Q record per (mesh, Q) row
+ * (n_meshes x n_q rows shared, n_q rows with q_off) plus 204 bytes per face.
+ * per_mesh_q tells the size function which (0: shared, 1: q_off). */
+size_t pft3d_batched_backward_workspace_size(int64_t n_verts, int64_t n_faces, int64_t n_meshes, int64_t n_q,
+                                             int per_mesh_q, const pft_options* opts);
+int pft3d_meshes_batched_backward(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces,
+                                  const int64_t* mesh_off, int64_t n_meshes, const double* q, const int64_t* q_off,
+                                  int64_t n_q, const double* grad_out, float* grad_verts, void* ws, size_t ws_bytes,
+                                  const pft_options* opts, void* stream);
+
 /* Adjoint of pft3d_polymesh (same faces, same split into triangles): grad_verts
  * [n_verts][3] float32 from grad_out as for pft3d_mesh_backward.  The workspace
  * must also hold the triangle list (see the size function). */

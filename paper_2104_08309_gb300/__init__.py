@@ -22,7 +22,8 @@ __all__ = [
     "pft2d_polygons", "pft2d_batched_prepare", "pft2d_polygons_batched", "BatchedPrepared", "pft3d_mesh",
     "pft3d_polymesh", "pft3d_polymesh_backward", "ft3d_poly", "pft2d_polygons_batched_backward", "pft3d_batched_prepare", "pft3d_meshes_batched",
     "pft2d_polygons_backward",
-    "pft3d_mesh_backward", "pft3d_mesh_qgrad", "pft2d_polygons_qgrad", "pair_faces", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft2d_batched", "ft3d", "make_options", "Options",
+    "pft3d_mesh_backward", "pft3d_mesh_qgrad", "pft2d_polygons_qgrad", "pair_faces",
+    "pft3d_meshes_batched_backward", "ft3d_batched", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft2d_batched", "ft3d", "make_options", "Options",
     "PFTError",
     "launch_count", "version",
 ]
@@ -474,6 +475,39 @@ def pft2d_polygons_batched_backward(verts, poly_off, q, grad_out, q_off=None, *,
     return out
 
 
+def pft3d_meshes_batched_backward(verts, faces, mesh_off, q, grad_out, q_off=None, *, options=None, out=None,
+                                  ws=None, stream=None, check_status=False):
+    """dL/dverts [n_v, 3] float32 for a batch of closed meshes (faces of mesh i: faces[mesh_off[i]:
+    mesh_off[i+1]]), from grad_out = (dL/dRe F_i(Q), dL/dIm F_i(Q)): [n_meshes, n_q, 2] on a shared Q
+    set (q_off None), or [n_q, 2] with mesh i on q[q_off[i]:q_off[i+1]]."""
+    torch = _torch()
+    v = _dev(verts, torch.float32, "verts", 3)
+    f = _dev(faces, torch.int32, "faces", 3)
+    off = mesh_off if (isinstance(mesh_off, torch.Tensor) and mesh_off.is_cuda) else _host_i64(mesh_off).to(v.device)
+    off = _dev(off, torch.int64, "mesh_off").reshape(-1)
+    qq = _dev(q, torch.float64, "q", 3)
+    nm, nq = off.shape[0] - 1, qq.shape[0]
+    qo = None
+    if q_off is not None:
+        qo = q_off if (isinstance(q_off, torch.Tensor) and q_off.is_cuda) else _host_i64(q_off).to(v.device)
+        qo = _dev(qo, torch.int64, "q_off").reshape(-1)
+    g = _dev(grad_out, torch.float64, "grad_out").reshape(nq if qo is not None else nm * nq, 2)
+    o = make_options(options)
+    lib = load()
+    nb = lib.pft3d_batched_backward_workspace_size(v.shape[0], f.shape[0], nm, nq, int(qo is not None),
+                                                   ctypes.byref(o))
+    ws = _ws(nb, v.device, ws)
+    out = torch.empty(v.shape[0], 3, dtype=torch.float32, device=v.device) if out is None else out
+    st = _stream(stream, v.device)
+    check(lib.pft3d_meshes_batched_backward(v.data_ptr(), v.shape[0], f.data_ptr(), f.shape[0], off.data_ptr(), nm,
+                                            qq.data_ptr(), None if qo is None else qo.data_ptr(), nq, g.data_ptr(),
+                                            out.data_ptr(), ws.data_ptr(), ws.numel(), ctypes.byref(o), st),
+          "pft3d_meshes_batched_backward")
+    if check_status:
+        check(lib.pft_status(ws.data_ptr(), st), "pft3d_meshes_batched_backward (device status)")
+    return out
+
+
 def pft_status(ws, stream=None) -> int:
     """Device-detected status of the last call on this workspace (synchronises the stream)."""
     return int(load().pft_status(ws.data_ptr(), _stream(stream, ws.device)))
@@ -558,7 +592,22 @@ def _autograd():
                                                  options={"precision": ctx.precision})
             return gv, None, None, None, None
 
-    return _FT2D, _FT3D, _FT3DPoly, _FT2DBatched
+    class _FT3DBatched(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, verts, faces, mesh_off, q, q_off, options):
+            ctx.save_for_backward(verts, faces, mesh_off, q, q_off)
+            ctx.precision = make_options(options).precision
+            ctx.tau = make_options(options).face_series_tau
+            return pft3d_meshes_batched(verts.detach(), faces, mesh_off, q, q_off, options=options)
+
+        @staticmethod
+        def backward(ctx, g):
+            verts, faces, mesh_off, q, q_off = ctx.saved_tensors
+            gv = pft3d_meshes_batched_backward(verts.detach(), faces, mesh_off, q, g.contiguous(), q_off,
+                                               options={"precision": ctx.precision, "face_series_tau": ctx.tau})
+            return gv, None, None, None, None, None
+
+    return _FT2D, _FT3D, _FT3DPoly, _FT2DBatched, _FT3DBatched
 
 
 _FNS = None
@@ -601,6 +650,25 @@ def ft2d_batched(verts, poly_off, q, options=None, q_off=None):
     if q_off is not None:
         qo = q_off if (isinstance(q_off, torch.Tensor) and q_off.is_cuda) else _host_i64(q_off).to(verts.device)
     return torch.view_as_complex(_FNS[3].apply(verts, off, q, qo, options))
+
+
+def ft3d_batched(verts, faces, mesh_off, q, options=None, q_off=None):
+    """Differentiable FT_V of each closed mesh of a batch, complex128 [n_meshes, n_q] on a shared Q set,
+    or [n_q] with mesh i on q[q_off[i]:q_off[i+1]]; grad w.r.t. verts via the batched adjoint (FP32 with
+    compensated sums: a gradient of an FP64 forward is refused)."""
+    global _FNS
+    torch = _torch()
+    _FNS = _FNS or _autograd()
+    if (make_options(options).precision == PFT_FP64 and torch.is_grad_enabled()
+            and isinstance(verts, torch.Tensor) and verts.requires_grad):
+        raise ValueError("ft3d_batched: the batched adjoint has no FP64 path; use precision='fp32' "
+                         "for a differentiable batch, or detach verts")
+    off = mesh_off if (isinstance(mesh_off, torch.Tensor) and mesh_off.is_cuda) else \
+        _host_i64(mesh_off).to(verts.device)
+    qo = None
+    if q_off is not None:
+        qo = q_off if (isinstance(q_off, torch.Tensor) and q_off.is_cuda) else _host_i64(q_off).to(verts.device)
+    return torch.view_as_complex(_FNS[4].apply(verts, faces, off, q, qo, options))
 
 
 def ft3d_poly(verts, face_idx, face_off, q, options=None):

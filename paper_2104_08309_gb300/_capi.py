@@ -63,6 +63,9 @@ SIGNATURES = {
     "pft2d_batched_backward_workspace_size": (c_size, [c_i64, c_i64, c_i64, ctypes.c_int, c_vp]),
     "pft2d_polygons_batched_backward": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp,
                                                        c_vp, c_size, c_vp, c_vp]),
+    "pft3d_batched_backward_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_i64, ctypes.c_int, c_vp]),
+    "pft3d_meshes_batched_backward": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_i64,
+                                                     c_vp, c_vp, c_vp, c_size, c_vp, c_vp]),
     "pft3d_qgrad_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_vp]),
     "pft3d_mesh_qgrad": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp, c_size, c_vp, c_vp]),
     "pft2d_qgrad_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_vp]),

@@ -965,8 +965,9 @@ __global__ void k_bvert2d(const float* __restrict__ v, int64_t nv, const int64_t
 // carry gt_i(Q) = 2 g_i(Q) e^{-iQ.c_i}/|Q|^2 per (polygon, Q) row; pair blocks never straddle
 // polygons; the vertex gather adds each polygon's own small-|Q| rows in FP64.
 // ---------------------------------------------------------------------------
+// Per shape of a batch (polygon or mesh): bounding-box centre (cz = 0 in 2D) and max radius.
 struct PolyC {
-  double cx, cy;
+  double cx, cy, cz;
   float rmax;
   int32_t pad;
 };
@@ -1023,7 +1024,7 @@ __global__ void __launch_bounds__(kAux) k_bbprep(const float* __restrict__ v, in
   }
   rm = block_minmax_f(rm, true, sh);
   if (threadIdx.x == 0) {
-    pc[i] = PolyC{c[0], c[1], rm, 0};
+    pc[i] = PolyC{c[0], c[1], 0.0, rm, 0};
     nblk[i] = (int32_t)((n + kBbSegs - 1) / kBbSegs);
   }
 }
@@ -1046,6 +1047,8 @@ __device__ __forceinline__ void bb_rows(const int64_t* q_off, int64_t i, int64_t
   }
 }
 
+// D = 2: weight 2 g e^{-iQ.c}/|Q|^2 (records hold half segment vectors); D = 3: g e^{-iQ.c}/|Q|^2.
+template <int D>
 __global__ void __launch_bounds__(kAux) k_bbq(const double* __restrict__ q, const int64_t* __restrict__ q_off,
                                               const double* __restrict__ g, int64_t n_q, int64_t np,
                                               const PolyC* __restrict__ pc, QRec* rec, int32_t* small,
@@ -1066,20 +1069,21 @@ __global__ void __launch_bounds__(kAux) k_bbq(const double* __restrict__ q, cons
     const int64_t l = l0 + threadIdx.x;
     bool is_small = false;
     if (l < nqi) {
-      const float qx = (float)q[2 * (qb + l)], qy = (float)q[2 * (qb + l) + 1];
-      const double Qx = qx, Qy = qy, q2 = Qx * Qx + Qy * Qy;
-      QRec r{qx, qy, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      const float qx = (float)q[D * (qb + l)], qy = (float)q[D * (qb + l) + 1];
+      const float qz = D == 3 ? (float)q[D * (qb + l) + D - 1] : 0.f;
+      const double Qx = qx, Qy = qy, Qz = qz, q2 = Qx * Qx + Qy * Qy + Qz * Qz;
+      QRec r{qx, qy, qz, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (q2 == 0.0 || q2 * ((double)P.rmax * (double)P.rmax) < kTauSmallQ * kTauSmallQ) {
         is_small = true;
       } else {
         // e^{-iQ.c}: the phase in FP64, less its nearest multiple of 2 pi (FP64), then an FP32
         // sincos on [-pi, pi]; the record holds FP32 weights, so this loses nothing further
-        const double ph = -(Qx * P.cx + Qy * P.cy);
+        const double ph = -(Qx * P.cx + Qy * P.cy + Qz * P.cz);
         const float pr = (float)fma(-rint(ph * kInvTwoPiD), kTwoPiD, ph);
         float sp, cp;
         sincosf(pr, &sp, &cp);
         const float gr = (float)g[2 * (gb + l)], gi = (float)g[2 * (gb + l) + 1];
-        const float k = 2.0f / (float)q2;
+        const float k = (D == 2 ? 2.0f : 1.0f) / (float)q2;
         r.gr = k * fmaf(gr, cp, -gi * sp);
         r.gi = k * fmaf(gr, sp, gi * cp);
       }
@@ -1231,15 +1235,177 @@ __global__ void k_bbvert(const float* __restrict__ v, int64_t nv, const int64_t*
   grad[2 * j + 1] = (float)gy;
 }
 
-// 3D: per face, chunk sums of the record adjoints -> corner adjoints (FP64), plus
-// small-|Q| corner terms dF/dp_k = exp(iQ.c) N sum_j i^j h_j(a, a_k)/(j+3)!.
-__global__ void k_bcorner3d(const float* __restrict__ v, int64_t nv, const int32_t* __restrict__ f, int64_t nf,
-                            const double* __restrict__ partial, int ks, const WsHeader* h,
-                            const int32_t* __restrict__ small, const double* __restrict__ q,
-                            const double* __restrict__ g, double* __restrict__ corner) {
+// ---------------------------------------------------------------------------
+// Batched 3D adjoint: many closed meshes (CSR mesh_off over the faces, one shared vertex
+// array), each centred on the bounding box of its own faces' corners, on a shared Q list or
+// per-mesh Q lists.  The structure of the batched 2D adjoint with the 3D pair adjoint:
+// k_bbprep3 (one block per mesh: checks, centre, face records, max radius, pair blocks needed),
+// the block scan, k_bbq<3> (per (mesh, Q row) records and small-|Q| lists), k_bbwd3 (blocks
+// that never straddle meshes, thread <-> face, the mesh's Q records through the bulk-copy ring),
+// k_bbcorner3 (corner adjoints with the mesh's small-|Q| rows), and the vertex gather of the
+// single-mesh adjoint over all faces.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kAux) k_bbprep3(const float* __restrict__ v, int64_t nv,
+                                                  const int32_t* __restrict__ f, int64_t nf,
+                                                  const int64_t* __restrict__ off, int64_t nm, Face32* recs,
+                                                  PolyC* mc, int32_t* nblk, WsHeader* h) {
+  __shared__ float sh[kAux / 32];
+  const int64_t i = blockIdx.x;
+  const int64_t s0 = off[i], s1 = off[i + 1];
+  if (threadIdx.x == 0 && (s1 < s0 || s0 < 0 || s1 > nf || (i == 0 && s0 != 0) || (i == nm - 1 && s1 != nf)))
+    set_status(&h->status, ST_OFFSETS);
+  const int64_t b0 = max((int64_t)0, min(s0, nf)), n = max((int64_t)0, min(s1, nf) - b0);
+  auto valid = [&](int64_t m) {
+    const int32_t a = f[3 * m], b = f[3 * m + 1], c = f[3 * m + 2];
+    return a >= 0 && b >= 0 && c >= 0 && a < nv && b < nv && c < nv;
+  };
+  float mn[3] = {3.4e38f, 3.4e38f, 3.4e38f}, mx[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+  bool bad_index = false, bad_value = false;
+  for (int64_t j = threadIdx.x; j < n; j += kAux) {
+    const int64_t m = b0 + j;
+    if (!valid(m)) { bad_index = true; continue; }
+    for (int k = 0; k < 3; ++k)
+      for (int d = 0; d < 3; ++d) {
+        const float x = v[3 * (int64_t)f[3 * m + k] + d];
+        if (!isfinite(x)) { bad_value = true; continue; }
+        mn[d] = fminf(mn[d], x);
+        mx[d] = fmaxf(mx[d], x);
+      }
+  }
+  if (bad_index) set_status(&h->status, ST_INDEX);
+  if (bad_value) set_status(&h->status, ST_NONFINITE);
+  double c[3];
+  for (int d = 0; d < 3; ++d) {
+    const float lo = block_minmax_f(mn[d], false, sh), hi = block_minmax_f(mx[d], true, sh);
+    c[d] = (n > 0 && lo <= hi) ? 0.5 * ((double)lo + (double)hi) : 0.0;
+  }
+  float rm = 0.f;
+  for (int64_t j = threadIdx.x; j < n; j += kAux) {
+    const int64_t m = b0 + j;
+    Face32 r{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // skipped faces contribute 0
+    if (valid(m)) {
+      double P[3][3], g[3], q0[3], q1[3];
+      for (int k = 0; k < 3; ++k)
+        for (int d = 0; d < 3; ++d) P[k][d] = (double)v[3 * (int64_t)f[3 * m + k] + d] - c[d];
+      for (int d = 0; d < 3; ++d) {
+        g[d] = (P[0][d] + P[1][d] + P[2][d]) / 3.0;
+        q0[d] = P[0][d] - g[d];
+        q1[d] = P[1][d] - g[d];
+      }
+      const double e1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+      const double e2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+      const double N[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                           e1[0] * e2[1] - e1[1] * e2[0]};
+      r = Face32{(float)g[0], (float)g[1], (float)g[2], (float)q0[0], (float)q0[1], (float)q0[2],
+                 (float)q1[0], (float)q1[1], (float)q1[2], (float)N[0], (float)N[1], (float)N[2]};
+      for (int k = 0; k < 3; ++k)
+        rm = fmaxf(rm, __double2float_ru(sqrt(P[k][0] * P[k][0] + P[k][1] * P[k][1] + P[k][2] * P[k][2])));
+    }
+    recs[m] = r;
+  }
+  rm = block_minmax_f(rm, true, sh);
+  if (threadIdx.x == 0) {
+    mc[i] = PolyC{c[0], c[1], c[2], rm, 0};
+    nblk[i] = (int32_t)((n + kBwdNT - 1) / kBwdNT);
+  }
+}
+
+// Pair blocks: block b is pair block b - bstart[i] of mesh i; thread t <-> face t of that block;
+// the mesh's Q records stream through the ring (Q chunk blockIdx.y).  Warps with no face only wait
+// for and release the tiles.  Blocks past the last mesh leave at once.
+__global__ void __launch_bounds__(kBwdNT) k_bbwd3(const Face32* __restrict__ recs, int64_t nf,
+                                                  const int64_t* __restrict__ off, int64_t nm,
+                                                  const int64_t* __restrict__ bstart, const int32_t* __restrict__ nblk,
+                                                  const QRec* __restrict__ rec, const int64_t* __restrict__ q_off,
+                                                  int64_t n_q, int64_t per_split, Thr th,
+                                                  double* __restrict__ partial, uint32_t* status) {
+  __shared__ __align__(128) QRec slots[kStages * kQTile];
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ int done[kStages];
+  __shared__ int issued;
+  const int64_t b = blockIdx.x;
+  if (b >= bstart[nm - 1] + nblk[nm - 1]) return;   // uniform over the block
+  int64_t lo = 0, hi = nm - 1;                      // the last mesh whose blocks start at or before b
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (bstart[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const int64_t s0 = max((int64_t)0, min(off[lo], nf)), s1 = max(s0, min(off[lo + 1], nf));
+  const int64_t m = s0 + (b - bstart[lo]) * kBwdNT + threadIdx.x;
+  const bool mine = m < s1;
+  float4 F[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+  if (mine)
+    for (int k = 0; k < 3; ++k) F[k] = reinterpret_cast<const float4*>(recs)[3 * m + k];
+  const bool live = __any_sync(0xffffffffu, mine);
+  int64_t qb, gb, nqi;
+  bb_rows(q_off, lo, n_q, qb, gb, nqi);
+  const int64_t q0 = (int64_t)blockIdx.y * per_split;
+  const int64_t nq = max((int64_t)0, min(per_split, nqi - q0));
+  Ring<QRec, kQTile, kBwdNT> ring{slots, full, done, &issued, rec + gb + q0, nq, (int)((nq + kQTile - 1) / kQTile)};
+  ring.start();
+  CAcc acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k].init();
+  bool ok = true;
+  for (int t = 0; t < ring.ntiles; ++t) {
+    if (!ring.wait(t)) { ok = false; break; }
+    const QRec* tq = ring.tile(t);
+    const int cnt = ring.count(t);
+    float a[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (live) {
+#pragma unroll 1
+      for (int j = 0; j < cnt; ++j) face_adj(tq[j], F[0], F[1], F[2], th, a);
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k].add(a[k]);
+    ring.release(t);
+  }
+  if (!ok) set_status(status, ST_TIMEOUT);
+  ring.finish();
+  if (!ok || !mine) return;
+  double* dst = partial + ((int64_t)blockIdx.y * nf + m) * 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) dst[k] = (double)acc[k].hi + (double)acc[k].lo;
+}
+
+__device__ void corner_adj(int64_t m, const float* __restrict__ v, int64_t nv, const int32_t* __restrict__ f,
+                           int64_t nf, const double* __restrict__ partial, int ks, const double* c,
+                           const int32_t* __restrict__ small, uint32_t ns, int64_t q_base, int64_t g_base,
+                           const double* __restrict__ q, const double* __restrict__ g, double* __restrict__ out);
+
+// Per face: its mesh (bisection over the offsets), then the corner adjoints with that mesh's
+// centre and small-|Q| rows.
+__global__ void k_bbcorner3(const float* __restrict__ v, int64_t nv, const int32_t* __restrict__ f, int64_t nf,
+                            const int64_t* __restrict__ off, int64_t nm, const double* __restrict__ partial, int ks,
+                            const PolyC* __restrict__ mc, const int32_t* __restrict__ small,
+                            const int32_t* __restrict__ small_cnt, const double* __restrict__ q,
+                            const int64_t* __restrict__ q_off, int64_t n_q, const double* __restrict__ g,
+                            double* __restrict__ corner) {
   const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (m >= nf) return;
-  double* out = corner + 9 * m;
+  int64_t lo = 0, hi = nm;   // the last mesh whose faces start at or before m
+  while (lo + 1 < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (off[mid] <= m) lo = mid; else hi = mid;
+  }
+  int64_t qb, gb, nqi;
+  bb_rows(q_off, lo, n_q, qb, gb, nqi);
+  const PolyC C = mc[lo];
+  const double c[3] = {C.cx, C.cy, C.cz};
+  const uint32_t ns = (uint32_t)max(0, min(small_cnt[lo], (int32_t)nqi));
+  corner_adj(m, v, nv, f, nf, partial, ks, c, small + gb, ns, qb, gb, q, g, corner + 9 * m);
+}
+
+// 3D: per face, chunk sums of the record adjoints -> corner adjoints (FP64), plus
+// small-|Q| corner terms dF/dp_k = exp(iQ.c) N sum_j i^j h_j(a, a_k)/(j+3)!.
+// Corner adjoints of face m (FP64): the record adjoints summed over the Q chunks, mapped to the
+// three corners, plus the small-|Q| terms of the ns listed Q rows small[0 .. ns-1] (rows of q from
+// q_base, of g from g_base) about the centre c.
+__device__ void corner_adj(int64_t m, const float* __restrict__ v, int64_t nv, const int32_t* __restrict__ f,
+                           int64_t nf, const double* __restrict__ partial, int ks, const double* c,
+                           const int32_t* __restrict__ small, uint32_t ns, int64_t q_base, int64_t g_base,
+                           const double* __restrict__ q, const double* __restrict__ g, double* __restrict__ out) {
   const int32_t id[3] = {f[3 * m], f[3 * m + 1], f[3 * m + 2]};
   if (id[0] < 0 || id[1] < 0 || id[2] < 0 || id[0] >= nv || id[1] >= nv || id[2] >= nv) {
     for (int k = 0; k < 9; ++k) out[k] = 0.0;
@@ -1250,7 +1416,6 @@ __global__ void k_bcorner3d(const float* __restrict__ v, int64_t nv, const int32
     const double* a = partial + ((int64_t)s * nf + m) * 12;
     for (int k = 0; k < 12; ++k) ab[k] += a[k];
   }
-  const double c[3] = {h->center[0], h->center[1], h->center[2]};
   double P[3][3];
   for (int k = 0; k < 3; ++k)
     for (int d = 0; d < 3; ++d) P[k][d] = (double)v[3 * (int64_t)id[k] + d] - c[d];
@@ -1272,11 +1437,10 @@ __global__ void k_bcorner3d(const float* __restrict__ v, int64_t nv, const int32
     pb[2][d] += e2b[d];
     pb[0][d] -= e1b[d] + e2b[d];
   }
-  const uint32_t ns = h->small_q_count;
   if (ns) {
     const double N[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
     for (uint32_t e = 0; e < ns; ++e) {
-      const int64_t iq = small[e];
+      const int64_t iq = q_base + small[e], ig = g_base + small[e];
       const double Q[3] = {(double)(float)q[3 * iq], (double)(float)q[3 * iq + 1], (double)(float)q[3 * iq + 2]};
       const double al[3] = {Q[0] * P[0][0] + Q[1] * P[0][1] + Q[2] * P[0][2],
                             Q[0] * P[1][0] + Q[1] * P[1][1] + Q[2] * P[1][2],
@@ -1299,13 +1463,23 @@ __global__ void k_bcorner3d(const float* __restrict__ v, int64_t nv, const int32
           inv /= (double)(j + 4);
         }
         const double hr = ce * sr - se * si, hi = ce * si + se * sr;
-        const double cf = g[2 * iq] * hr + g[2 * iq + 1] * hi;   // Re(conj(g) * H)
+        const double cf = g[2 * ig] * hr + g[2 * ig + 1] * hi;   // Re(conj(g) * H)
         for (int d = 0; d < 3; ++d) pb[k][d] += cf * N[d];
       }
     }
   }
   for (int k = 0; k < 3; ++k)
     for (int d = 0; d < 3; ++d) out[3 * k + d] = pb[k][d];
+}
+
+__global__ void k_bcorner3d(const float* __restrict__ v, int64_t nv, const int32_t* __restrict__ f, int64_t nf,
+                            const double* __restrict__ partial, int ks, const WsHeader* h,
+                            const int32_t* __restrict__ small, const double* __restrict__ q,
+                            const double* __restrict__ g, double* __restrict__ corner) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= nf) return;
+  const double c[3] = {h->center[0], h->center[1], h->center[2]};
+  corner_adj(m, v, nv, f, nf, partial, ks, c, small, h->small_q_count, 0, 0, q, g, corner + 9 * m);
 }
 
 // Vertex -> face-corner CSR: degrees, exclusive scan, fill, per-vertex sort.
@@ -1544,6 +1718,46 @@ BbLayout bb_layout(int64_t nv, int64_t np, int64_t n_q, bool per_poly_q) {
   y.small = o;   o = al(o + sizeof(int32_t) * (size_t)rows);
   y.scnt = o;    o = al(o + sizeof(int32_t) * (size_t)std::max<int64_t>(np, 1));
   y.partial = o; o = al(o + sizeof(double) * 4 * (size_t)y.ks * (size_t)std::max<int64_t>(nv, 1));
+  y.total = o;
+  return y;
+}
+
+// Batched 3D adjoint workspace: face records, per-mesh centres and block counts, the block scan,
+// Q records and small lists per (mesh, Q) row, FP64 partials per (Q chunk, face), corner adjoints
+// and the vertex -> face-corner CSR of the vertex gather.
+struct Bb3Layout {
+  size_t recs, mc, nblk, bstart, btot, rec, small, scnt, partial, corner, deg, cursor, start, vtot, list, total;
+  int ks;
+  int64_t per_split, grid;
+};
+
+Bb3Layout bb3_layout(int64_t nv, int64_t nf, int64_t nm, int64_t n_q, bool per_mesh_q) {
+  Bb3Layout y{};
+  y.grid = std::max<int64_t>(1, nm + (nf + kBwdNT - 1) / kBwdNT);   // at least the pair blocks needed
+  const int64_t slots = (int64_t)sm_count() * 8;
+  const int64_t q_tiles = std::max<int64_t>(1, (n_q + kQTile - 1) / kQTile);
+  const int64_t k = std::min<int64_t>({std::max<int64_t>(1, (4 * slots + y.grid - 1) / y.grid), q_tiles, 256});
+  y.per_split = ((q_tiles + k - 1) / k) * kQTile;
+  y.ks = (int)std::max<int64_t>(1, (n_q + y.per_split - 1) / y.per_split);
+  const int64_t rows = std::max<int64_t>(per_mesh_q ? n_q : nm * n_q, 1);
+  const size_t nf1 = (size_t)std::max<int64_t>(nf, 1), nm1 = (size_t)std::max<int64_t>(nm, 1),
+               nv1 = (size_t)std::max<int64_t>(nv, 1);
+  size_t o = al(sizeof(WsHeader));
+  y.recs = o;    o = al(o + sizeof(Face32) * nf1);
+  y.mc = o;      o = al(o + sizeof(PolyC) * nm1);
+  y.nblk = o;    o = al(o + sizeof(int32_t) * nm1);
+  y.bstart = o;  o = al(o + sizeof(int64_t) * nm1);
+  y.btot = o;    o = al(o + sizeof(int64_t) * (size_t)blocks(nm, kAux));
+  y.rec = o;     o = al(o + sizeof(QRec) * (size_t)rows);
+  y.small = o;   o = al(o + sizeof(int32_t) * (size_t)rows);
+  y.scnt = o;    o = al(o + sizeof(int32_t) * nm1);
+  y.partial = o; o = al(o + sizeof(double) * 12 * (size_t)y.ks * nf1);
+  y.corner = o;  o = al(o + sizeof(double) * 9 * nf1);
+  y.deg = o;     o = al(o + sizeof(int32_t) * nv1);
+  y.cursor = o;  o = al(o + sizeof(int32_t) * nv1);
+  y.start = o;   o = al(o + sizeof(int64_t) * nv1);
+  y.vtot = o;    o = al(o + sizeof(int64_t) * (size_t)blocks(nv, kAux));
+  y.list = o;    o = al(o + sizeof(int32_t) * 3 * nf1);
   y.total = o;
   return y;
 }
@@ -1901,7 +2115,7 @@ int pft2d_polygons_batched_backward(const float* verts, int64_t n_verts, const i
   PFT_BWD_LAUNCH();
   k_scan_add<<<nb, kAux, 0, st>>>(bstart, n_polys, btot);
   PFT_BWD_LAUNCH();
-  k_bbq<<<(unsigned)n_polys, kAux, 0, st>>>(q, q_off, grad_out, n_q, n_polys, pc, at<QRec>(ws, y.rec),
+  k_bbq<2><<<(unsigned)n_polys, kAux, 0, st>>>(q, q_off, grad_out, n_q, n_polys, pc, at<QRec>(ws, y.rec),
                                             at<int32_t>(ws, y.small), at<int32_t>(ws, y.scnt), h);
   PFT_BWD_LAUNCH();
   if (y.grid > INT32_MAX) return PFT_ERR_UNSUPPORTED;
@@ -1914,6 +2128,94 @@ int pft2d_polygons_batched_backward(const float* verts, int64_t n_verts, const i
   k_bbvert<<<blocks(n_verts, kAux), kAux, 0, st>>>(verts, n_verts, poly_off, n_polys, at<double>(ws, y.partial), y.ks,
                                                    pc, at<int32_t>(ws, y.small), at<int32_t>(ws, y.scnt), q, q_off,
                                                    n_q, grad_out, grad_verts);
+  PFT_BWD_LAUNCH();
+  return PFT_OK;
+}
+
+size_t pft3d_batched_backward_workspace_size(int64_t n_verts, int64_t n_faces, int64_t n_meshes, int64_t n_q,
+                                             int per_mesh_q, const pft_options* opts) {
+  Thr th;
+  if (n_verts < 0 || n_faces < 0 || n_meshes < 0 || n_q < 0 || check_opts(opts, th) != PFT_OK) return 0;
+  return bb3_layout(n_verts, n_faces, n_meshes, n_q, per_mesh_q != 0).total;
+}
+
+int pft3d_meshes_batched_backward(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces,
+                                  const int64_t* mesh_off, int64_t n_meshes, const double* q, const int64_t* q_off,
+                                  int64_t n_q, const double* grad_out, float* grad_verts, void* ws, size_t ws_bytes,
+                                  const pft_options* opts, void* stream) {
+  g_bwd_launches = 0;
+  Thr th;
+  if (int e = check_opts(opts, th)) return e;
+  if (n_verts < 0 || n_faces < 0 || n_meshes < 0 || n_q < 0) return PFT_ERR_INVALID_ARG;
+  if (n_verts > 0 && (verts == nullptr || grad_verts == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (n_faces > 0 && (faces == nullptr || mesh_off == nullptr || n_meshes == 0 || n_verts == 0))
+    return PFT_ERR_INVALID_ARG;
+  if (n_q > 0 && (q == nullptr || grad_out == nullptr)) return PFT_ERR_INVALID_ARG;
+  if (q_off != nullptr && n_meshes == 0) return PFT_ERR_INVALID_ARG;
+  if (n_q > INT32_MAX || n_verts > INT32_MAX || 3 * n_faces > INT32_MAX || n_meshes > INT32_MAX ||
+      n_meshes * n_q > (int64_t)1 << 40)
+    return PFT_ERR_UNSUPPORTED;
+  const Bb3Layout y = bb3_layout(n_verts, n_faces, n_meshes, n_q, q_off != nullptr);
+  if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < y.total) return PFT_ERR_WORKSPACE;
+  if (y.grid > INT32_MAX) return PFT_ERR_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader* h = at<WsHeader>(ws, 0);
+  if (launch_init_header(h, st) != cudaSuccess) return PFT_ERR_CUDA;
+  ++g_bwd_launches;
+  if (n_verts == 0) return PFT_OK;
+  if (n_q == 0 || n_faces == 0)
+    return cudaMemsetAsync(grad_verts, 0, sizeof(float) * 3 * (size_t)n_verts, st) == cudaSuccess ? PFT_OK
+                                                                                                 : PFT_ERR_CUDA;
+  Face32* recs = at<Face32>(ws, y.recs);
+  PolyC* mc = at<PolyC>(ws, y.mc);
+  int32_t* nblk = at<int32_t>(ws, y.nblk);
+  int64_t* bstart = at<int64_t>(ws, y.bstart);
+  int64_t* btot = at<int64_t>(ws, y.btot);
+  k_bbprep3<<<(unsigned)n_meshes, kAux, 0, st>>>(verts, n_verts, faces, n_faces, mesh_off, n_meshes, recs, mc, nblk,
+                                                 h);
+  PFT_BWD_LAUNCH();
+  const unsigned nb = blocks(n_meshes, kAux);
+  k_scan_block<<<nb, kAux, 0, st>>>(nblk, n_meshes, bstart, btot);
+  PFT_BWD_LAUNCH();
+  k_scan_totals<<<1, 32, 0, st>>>(btot, nb);
+  PFT_BWD_LAUNCH();
+  k_scan_add<<<nb, kAux, 0, st>>>(bstart, n_meshes, btot);
+  PFT_BWD_LAUNCH();
+  k_bbq<3><<<(unsigned)n_meshes, kAux, 0, st>>>(q, q_off, grad_out, n_q, n_meshes, mc, at<QRec>(ws, y.rec),
+                                                at<int32_t>(ws, y.small), at<int32_t>(ws, y.scnt), h);
+  PFT_BWD_LAUNCH();
+  dim3 grid((unsigned)y.grid, (unsigned)y.ks);
+  PFT_MARK(g_ev_start);
+  k_bbwd3<<<grid, kBwdNT, 0, st>>>(recs, n_faces, mesh_off, n_meshes, bstart, nblk, at<QRec>(ws, y.rec), q_off, n_q,
+                                   y.per_split, th, at<double>(ws, y.partial), &h->status);
+  PFT_BWD_LAUNCH();
+  PFT_MARK(g_ev_stop);
+  k_bbcorner3<<<blocks(n_faces, kAux), kAux, 0, st>>>(verts, n_verts, faces, n_faces, mesh_off, n_meshes,
+                                                      at<double>(ws, y.partial), y.ks, mc, at<int32_t>(ws, y.small),
+                                                      at<int32_t>(ws, y.scnt), q, q_off, n_q, grad_out,
+                                                      at<double>(ws, y.corner));
+  PFT_BWD_LAUNCH();
+  int32_t* deg = at<int32_t>(ws, y.deg);
+  int32_t* cursor = at<int32_t>(ws, y.cursor);
+  int64_t* start = at<int64_t>(ws, y.start);
+  int64_t* vtot = at<int64_t>(ws, y.vtot);
+  k_zero_i32<<<blocks(n_verts, kAux), kAux, 0, st>>>(deg, n_verts);
+  PFT_BWD_LAUNCH();
+  k_zero_i32<<<blocks(n_verts, kAux), kAux, 0, st>>>(cursor, n_verts);
+  PFT_BWD_LAUNCH();
+  k_deg<<<blocks(3 * n_faces, kAux), kAux, 0, st>>>(faces, n_faces, n_verts, deg);
+  PFT_BWD_LAUNCH();
+  const unsigned nbv = blocks(n_verts, kAux);
+  k_scan_block<<<nbv, kAux, 0, st>>>(deg, n_verts, start, vtot);
+  PFT_BWD_LAUNCH();
+  k_scan_totals<<<1, 32, 0, st>>>(vtot, nbv);
+  PFT_BWD_LAUNCH();
+  k_scan_add<<<nbv, kAux, 0, st>>>(start, n_verts, vtot);
+  PFT_BWD_LAUNCH();
+  k_fill<<<blocks(3 * n_faces, kAux), kAux, 0, st>>>(faces, n_faces, n_verts, start, cursor, at<int32_t>(ws, y.list));
+  PFT_BWD_LAUNCH();
+  k_gather3d<<<blocks(n_verts, kAux), kAux, 0, st>>>(n_verts, start, deg, at<int32_t>(ws, y.list),
+                                                     at<double>(ws, y.corner), grad_verts);
   PFT_BWD_LAUNCH();
   return PFT_OK;
 }
