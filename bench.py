@@ -519,10 +519,30 @@ def bench_batched3d(dev, warmup, steps):
     mix = branch_mix(v, f, q, tau=6.0, r=4, nt=128)
     _, _, ach, peak = roofline(pairs, ms / 1e3, mix, torch.cuda.get_device_properties(dev).multi_processor_count,
                                float(pk.get("sm_max_mhz", 2070.0)))
+    status = int(pft.pft_status(prep.ws))
+    del g                                    # the CUDA graph
+    # the batched adjoint: vertex gradients of every mesh for seeded weights on the same grid
+    gb = torch.randn(off.size - 1, q.shape[0], 2, dtype=torch.float64, device=dev,
+                     generator=torch.Generator(device=dev).manual_seed(9))
+    for _ in range(2):
+        pft.pft3d_meshes_batched_backward(vd, fd, offd, qd, gb)
+    tb = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        pft.pft3d_meshes_batched_backward(vd, fd, offd, qd, gb)
+        b.record()
+        b.synchronize()
+        tb.append(a.elapsed_time(b))
+    backward = {"value": pairs / (float(np.mean(tb)) / 1e3) / 1e9, "unit": UNIT + " (adjoint call)",
+                "ms": float(np.mean(tb)), "launches": int(pft.load().pft_backward_last_launch_count())}
+    del gb
     return {"value": pairs / (ms / 1e3) / 1e9, "unit": UNIT + " (Q, triangle)", "ms_per_step": ms,
             "pairs_per_step": pairs, "meshes": int(off.size - 1), "faces": int(f.shape[0]),
             "q_points": int(q.shape[0]), "launches_per_step": int(launches), "cuda_graph": True,
-            "device_status": int(pft.pft_status(prep.ws)), "roofline_frac": ach / peak, "branch_fractions": mix,
+            "device_status": status, "roofline_frac": ach / peak, "branch_fractions": mix,
+            "backward": backward,
             "note": "whole batched call timed (prep, pair kernel, multi-chunk finish, small-|Q| pass)",
             "l2": "flushed between steps"}
 
