@@ -842,6 +842,9 @@ def main():
             "face_series_tau": args.tau}
     opts = pft.make_options(tune)
     nbytes = lib.pft3d_workspace_size(v.shape[0], f.shape[0], q.shape[0], ctypes.byref(opts))
+    # the paired variant's launch plan (another kernel, other occupancy) may want a larger workspace
+    paired_opts = pft.make_options({**tune, "face_pairs": f.shape[0] // 2})
+    nbytes = max(nbytes, lib.pft3d_workspace_size(v.shape[0], f.shape[0], q.shape[0], ctypes.byref(paired_opts)))
     ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     out = torch.empty(q.shape[0], 2, dtype=torch.float64, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)    # > 129 MB L2
