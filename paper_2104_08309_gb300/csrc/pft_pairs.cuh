@@ -27,10 +27,9 @@ constexpr float kP13 = 4.0f;       // P below which the k <= 13 series suffices 
 // 3D default (R = 4, 128 threads) is held to 102 registers for 5 blocks (20
 // warps), which it fits without spilling and which ran 9 % faster than 4 blocks.
 // (FP64 paths: one block, so that the double-precision temporaries never spill.)
-// The paired-face kernel (two faces' projections held at once) gets 4 blocks, 128 registers.
 template <class Pol, int R, int NT>
 constexpr int kMinBlocks = sizeof(typename Pol::QT) == 8 ? 1
-                           : (Pol::kDim == 3 && R == 4 && NT == 128) ? (Pol::kPaired ? 4 : 5)
+                           : (Pol::kDim == 3 && R == 4 && NT == 128) ? 5
                            : (NT == 256 ? 1 : 2) * (R >= 8 ? 1 : (R == 4 ? 2 : 3));
 
 // ---------------------------------------------------------------------------
@@ -504,8 +503,10 @@ struct FaceQ {
   }
 };
 
-// kPairs: faces [0, th.pair_end) come in pairs that share their first edge (face_pairs option); a
-// separate instantiation, so that the single-face kernel keeps its register budget.
+// kPairs: faces [0, th.pair_end) come in pairs that share their first edge (face_pairs option): when
+// both faces of a pair take the edge sum in a warp, the second takes the shared edge's sinc from the
+// first (carried in registers from one face to the next).  A separate instantiation, so that the
+// single-face kernel is unchanged.
 template <bool kPairs>
 struct Pol3F32T {
   using Item = Face32;
@@ -521,35 +522,29 @@ struct Pol3F32T {
     float tre[R], tim[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { tre[r] = 0.f; tim[r] = 0.f; }
+    // S0 carries the first edge's sinc from the first face of a pair to the second; `held` says
+    // that it does (warp-uniform: it follows the warp-uniform branch decisions)
+    float S0[R];
+    bool held = false;
 #pragma unroll 1
     for (int i = 0; i < cnt; ++i) {
       const float4* p = reinterpret_cast<const float4*>(t + i);
       const float4 A = p[0], B = p[1], C = p[2];
       FaceQ<R> f;
       f.load(q, A, B, C);
-      float zr[R], zi[R], S0[R];
-      if (kPairs && first + i < th.pair_end) {   // faces i and i + 1 share their first edge (warp-uniform)
-        const float4* p2 = reinterpret_cast<const float4*>(t + i + 1);
-        const float4 A2 = p2[0], B2 = p2[1], C2 = p2[2];
-        FaceQ<R> f2;
-        f2.load(q, A2, B2, C2);
-        float zr2[R], zi2[R];
-        if (f.wmax >= th.hi && f2.wmax >= th.hi) {   // both edge sums: the shared edge's sinc once
-          f.template edge<false>(th, q, A, B, C, zr, zi, S0);
-          f2.template edge<true>(th, q, A2, B2, C2, zr2, zi2, S0);
-        } else {
-          if (f.wmax < th.hi) f.series(th, zr, zi);
-          else f.template edge<false>(th, q, A, B, C, zr, zi, S0);
-          if (f2.wmax < th.hi) f2.series(th, zr2, zi2);
-          else f2.template edge<false>(th, q, A2, B2, C2, zr2, zi2, S0);
-        }
-        f.finish(zr, zi, tre, tim);
-        f2.finish(zr2, zi2, tre, tim);
-        ++i;
-        continue;
+      float zr[R], zi[R];
+      if (f.wmax < th.hi) {
+        f.series(th, zr, zi);
+        held = false;
+      } else if (kPairs && held && first + i < th.pair_end) {
+        // the second face of a pair whose first face took the edge sum in this warp: the shared
+        // edge's sinc comes from it
+        f.template edge<true>(th, q, A, B, C, zr, zi, S0);
+        held = false;
+      } else {
+        f.template edge<false>(th, q, A, B, C, zr, zi, S0);
+        held = kPairs && ((first + i) & 1) == 0 && first + i < th.pair_end;   // the first face of a pair
       }
-      if (f.wmax < th.hi) f.series(th, zr, zi);
-      else f.template edge<false>(th, q, A, B, C, zr, zi, S0);
       f.finish(zr, zi, tre, tim);
     }
 #pragma unroll
