@@ -123,3 +123,23 @@ def test_bad_mesh_offsets_reported(torch_dev):
                                            ctypes.byref(o), None)
     assert rc == 0
     assert lib.pft_status(ws.data_ptr(), None) == 8
+
+
+def test_empty_inputs(torch_dev):
+    """No Q points, or no faces: every vertex gradient is 0."""
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    v, f, off = _batch()
+    vd, fd = torch.from_numpy(v).to(dev), torch.from_numpy(f).to(dev)
+    n = off.size - 1
+    q0 = torch.empty(0, 3, dtype=torch.float64, device=dev)
+    g0 = torch.empty(n, 0, 2, dtype=torch.float64, device=dev)
+    out = torch.full((v.shape[0], 3), float("nan"), dtype=torch.float32, device=dev)
+    pft.pft3d_meshes_batched_backward(vd, fd, off, q0, g0, out=out, check_status=True)
+    assert torch.equal(out, torch.zeros_like(out))
+    q = torch.from_numpy(np.array([[1.0, 2.0, 0.5]])).to(dev)
+    g = torch.ones(1, 1, 2, dtype=torch.float64, device=dev)
+    out.fill_(float("nan"))
+    pft.pft3d_meshes_batched_backward(vd, torch.empty(0, 3, dtype=torch.int32, device=dev), np.array([0, 0]), q, g,
+                                      out=out)
+    assert torch.equal(out, torch.zeros_like(out))

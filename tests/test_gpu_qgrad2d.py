@@ -107,3 +107,18 @@ def test_qgrad2d_bad_offsets_reported(torch_dev):
                                   out.data_ptr(), ws.data_ptr(), nb, ctypes.byref(o), None)
     assert rc == 0
     assert lib.pft_status(ws.data_ptr(), None) == 8
+
+
+def test_qgrad2d_empty_inputs(torch_dev):
+    """No Q points: nothing to write; no vertices: dL/dQ = 0 for every Q."""
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    v = torch.from_numpy(synth.star_polygon(12, seed=3)).to(dev)
+    q0 = torch.empty(0, 2, dtype=torch.float64, device=dev)
+    assert pft.pft2d_polygons_qgrad(v, q0, torch.empty(0, 2, dtype=torch.float64, device=dev)).shape == (0, 2)
+    q = torch.from_numpy(np.array([[1.0, 2.0], [0.0, 0.0]])).to(dev)
+    g = torch.ones(2, 2, dtype=torch.float64, device=dev)
+    ve = torch.empty(0, 2, dtype=torch.float32, device=dev)
+    out = pft.pft2d_polygons_qgrad(ve, q, g, torch.tensor([0, 0], dtype=torch.int64, device=dev),
+                                   out=torch.full((2, 2), float("nan"), dtype=torch.float64, device=dev))
+    assert torch.equal(out, torch.zeros_like(out))
