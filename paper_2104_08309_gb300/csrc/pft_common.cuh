@@ -72,18 +72,36 @@ __device__ __forceinline__ void sincos_turns(float t, float* s, float* c) {
   __sincosf(kTwoPi * r, s, c);
 }
 
+// Scalar (float) and packed (float2: two values in one register pair) arithmetic.  The packed
+// forms are the sm_100+ paired FP32 instructions (one issue slot for two fused multiply-adds,
+// each rounded as fmaf), so a function written once with these helpers gives bit-identical
+// results in either form.
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float vmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+template <class V> __device__ __forceinline__ V vs(float c);
+template <> __device__ __forceinline__ float vs<float>(float c) { return c; }
+template <> __device__ __forceinline__ float2 vs<float2>(float c) { return make_float2(c, c); }
+
 // sinc(u) = sin(u)/u from v = u^2 <= pi^2: the degree-6 polynomial in v that
 // interpolates sinc(sqrt(v)) at the 7 Chebyshev nodes of [0, pi^2] (our own fit;
 // max abs error 7.5e-10 in exact arithmetic, ~1.6e-7 after FP32 rounding, the
 // same as the 8-term Taylor series it replaces at two fewer FMAs).
-__device__ __forceinline__ float sinc_poly(float u2) {
-  float p = fmaf(u2, 1.361159657e-10f, -2.472836691e-8f);
-  p = fmaf(u2, p, 2.753580020e-6f);
-  p = fmaf(u2, p, -1.984053088e-4f);
-  p = fmaf(u2, p, 8.333321661e-3f);
-  p = fmaf(u2, p, -1.666666567e-1f);
-  return fmaf(u2, p, 1.0f);
+template <class V>
+__device__ __forceinline__ V sinc_poly_v(V u2) {
+  V p = vfma(u2, vs<V>(1.361159657e-10f), vs<V>(-2.472836691e-8f));
+  p = vfma(u2, p, vs<V>(2.753580020e-6f));
+  p = vfma(u2, p, vs<V>(-1.984053088e-4f));
+  p = vfma(u2, p, vs<V>(8.333321661e-3f));
+  p = vfma(u2, p, vs<V>(-1.666666567e-1f));
+  return vfma(u2, p, vs<V>(1.0f));
 }
+__device__ __forceinline__ float sinc_poly(float u2) { return sinc_poly_v(u2); }
 
 constexpr float kPi2 = 9.86960440108935861883f;   // pi^2
 

@@ -3,6 +3,8 @@
 // forward kernels (single shape and batched).
 #pragma once
 
+#include <type_traits>
+
 #include "pft_kernels.cuh"
 
 namespace pft {
@@ -101,29 +103,31 @@ __device__ __forceinline__ void face_common(float qx, float qy, float qz, const 
 
 // As face_common, with T = a0 a1 a2 as well: s1 = a0 + a1 and p1 = a0 a1 give
 // P = s1^2 - p1 and T = -p1 s1.
-__device__ __forceinline__ void face_common_pt(float qx, float qy, float qz, const float4 A, const float4 B,
-                                               const float4 C, float& mu, float& a0, float& a1, float& s, float& P,
-                                               float& T) {
-  mu = fmaf(qx, A.x, fmaf(qy, A.y, qz * A.z));
-  a0 = fmaf(qx, A.w, fmaf(qy, B.x, qz * B.y));
-  a1 = fmaf(qx, B.z, fmaf(qy, B.w, qz * C.x));
-  s = fmaf(qx, C.y, fmaf(qy, C.z, qz * C.w));
-  const float s1 = a0 + a1, p1 = a0 * a1;
-  P = fmaf(s1, s1, -p1);
-  T = -p1 * s1;
+template <class V>
+__device__ __forceinline__ void face_common_pt(V qx, V qy, V qz, const float4 A, const float4 B,
+                                               const float4 C, V& mu, V& a0, V& a1, V& s, V& P,
+                                               V& T) {
+  mu = vfma(qx, vs<V>(A.x), vfma(qy, vs<V>(A.y), vmul(qz, vs<V>(A.z))));
+  a0 = vfma(qx, vs<V>(A.w), vfma(qy, vs<V>(B.x), vmul(qz, vs<V>(B.y))));
+  a1 = vfma(qx, vs<V>(B.z), vfma(qy, vs<V>(B.w), vmul(qz, vs<V>(C.x))));
+  s = vfma(qx, vs<V>(C.y), vfma(qy, vs<V>(C.z), vmul(qz, vs<V>(C.w))));
+  const V s1 = vadd(a0, a1), p1 = vmul(a0, a1);
+  P = vfma(s1, s1, vneg(p1));
+  T = vmul(vneg(p1), s1);
 }
 
 // Z = i G from the face-integral series.
 // Short form (P < 1/4, i.e. tau <= 1): h_k through k = 7,
 //   G_re = 1/2! - P/4! + P^2/6! - (P^3 + T^2)/8!,  G_im = T (-1/5! + 2P/7! - 3P^2/9!);
 // the omitted terms (k >= 8) are below 2e-9 (|G| <= 1/2).
-__device__ __forceinline__ void face_series(float T, float P, float& zr, float& zi) {
-  float gre = fmaf(P, -2.48015873e-5f, 1.38888889e-3f);   // -1/8!, 1/6!
-  gre = fmaf(P, gre, -4.16666667e-2f);                     // -1/4!
-  gre = fmaf(P, gre, 0.5f);                                // 1/2!
-  gre = fmaf(T * T, -2.48015873e-5f, gre);                 // -T^2/8!
-  const float gim = T * fmaf(P, fmaf(P, -8.26719577e-6f, 3.96825397e-4f), -8.33333333e-3f);  // -3/9!, 2/7!, -1/5!
-  zr = -gim;
+template <class V>
+__device__ __forceinline__ void face_series(V T, V P, V& zr, V& zi) {
+  V gre = vfma(P, vs<V>(-2.48015873e-5f), vs<V>(1.38888889e-3f));   // -1/8!, 1/6!
+  gre = vfma(P, gre, vs<V>(-4.16666667e-2f));                     // -1/4!
+  gre = vfma(P, gre, vs<V>(0.5f));                                // 1/2!
+  gre = vfma(vmul(T, T), vs<V>(-2.48015873e-5f), gre);                 // -T^2/8!
+  const V gim = vmul(T, vfma(P, vfma(P, vs<V>(-8.26719577e-6f), vs<V>(3.96825397e-4f)), vs<V>(-8.33333333e-3f)));  // -3/9!, 2/7!, -1/5!
+  zr = vneg(gim);
   zi = gre;
 }
 
@@ -131,23 +135,24 @@ __device__ __forceinline__ void face_series(float T, float P, float& zr, float& 
 //   h8 = P^4 + 3P T^2, h9 = 4P^3 T + T^3, h10 = P^5 + 6P^2 T^2, h11 = 5P^4 T + 4P T^3;
 // G_re = A(P) + T^2 B(P),  G_im = T (D(P) + T^2 E(P)); the omitted terms (k >= 12)
 // are below 4e-9 (|G| <= 1/2).
-__device__ __forceinline__ void face_series_long(float T, float P, float& zr, float& zi) {
-  const float T2 = T * T;
-  float A = fmaf(P, -2.087675588e-9f, 2.75573192e-7f);    // -1/12!, 1/10!
-  A = fmaf(P, A, -2.48015873e-5f);                         // -1/8!
-  A = fmaf(P, A, 1.38888889e-3f);                          // 1/6!
-  A = fmaf(P, A, -4.16666667e-2f);                         // -1/4!
-  A = fmaf(P, A, 0.5f);                                    // 1/2!
-  float B = fmaf(P, -1.252605397e-8f, 8.26719577e-7f);    // -6/12!, 3/10!
-  B = fmaf(P, B, -2.48015873e-5f);                         // -1/8!
-  const float gre = fmaf(T2, B, A);
-  float D = fmaf(P, -8.029522047e-10f, 1.002084318e-7f);   // -5/13!, 4/11!
-  D = fmaf(P, D, -8.26719577e-6f);                         // -3/9!
-  D = fmaf(P, D, 3.96825397e-4f);                          // 2/7!
-  D = fmaf(P, D, -8.33333333e-3f);                         // -1/5!
-  const float E = fmaf(P, -6.423617749e-10f, 2.505210794e-8f);   // -4/13!, 1/11!
-  const float gim = T * fmaf(T2, E, D);
-  zr = -gim;
+template <class V>
+__device__ __forceinline__ void face_series_long(V T, V P, V& zr, V& zi) {
+  const V T2 = vmul(T, T);
+  V A = vfma(P, vs<V>(-2.087675588e-9f), vs<V>(2.75573192e-7f));    // -1/12!, 1/10!
+  A = vfma(P, A, vs<V>(-2.48015873e-5f));                         // -1/8!
+  A = vfma(P, A, vs<V>(1.38888889e-3f));                          // 1/6!
+  A = vfma(P, A, vs<V>(-4.16666667e-2f));                         // -1/4!
+  A = vfma(P, A, vs<V>(0.5f));                                    // 1/2!
+  V B = vfma(P, vs<V>(-1.252605397e-8f), vs<V>(8.26719577e-7f));    // -6/12!, 3/10!
+  B = vfma(P, B, vs<V>(-2.48015873e-5f));                         // -1/8!
+  const V gre = vfma(T2, B, A);
+  V D = vfma(P, vs<V>(-8.029522047e-10f), vs<V>(1.002084318e-7f));   // -5/13!, 4/11!
+  D = vfma(P, D, vs<V>(-8.26719577e-6f));                         // -3/9!
+  D = vfma(P, D, vs<V>(3.96825397e-4f));                          // 2/7!
+  D = vfma(P, D, vs<V>(-8.33333333e-3f));                         // -1/5!
+  const V E = vfma(P, vs<V>(-6.423617749e-10f), vs<V>(2.505210794e-8f));   // -4/13!, 1/11!
+  const V gim = vmul(T, vfma(T2, E, D));
+  zr = vneg(gim);
   zi = gre;
 }
 
@@ -157,43 +162,45 @@ __device__ __forceinline__ void face_series_long(float T, float P, float& zr, fl
 // keep the terms with k <= K.  Omitted terms: k <= 9 on P < 1 below 4e-9, k <= 13 on
 // P < 4 below 3e-9 (|G| <= 1/2).  (A k <= 15 form for 4 <= P < 25/4 would save a
 // further 6 operations per pair there, but the larger loop body ran slower.)
-__device__ __forceinline__ void face_series_k9(float T, float P, float& zr, float& zi) {
-  const float T2 = T * T;
-  float A0 = fmaf(P, 2.755731922e-07f, -2.480158730e-05f);   // 1/10!, -1/8!
-  A0 = fmaf(P, A0, 1.388888889e-03f);                         // 1/6!
-  A0 = fmaf(P, A0, -4.166666667e-02f);                        // -1/4!
-  A0 = fmaf(P, A0, 0.5f);                                     // 1/2!
-  const float A2 = fmaf(P, 8.267195767e-07f, -2.480158730e-05f);   // 3/10!, -1/8!
-  float D1 = fmaf(P, 1.002084335e-07f, -8.267195767e-06f);   // 4/11!, -3/9!
-  D1 = fmaf(P, D1, 3.968253968e-04f);                         // 2/7!
-  D1 = fmaf(P, D1, -8.333333333e-03f);                        // -1/5!
-  const float gre = fmaf(T2, A2, A0);
-  const float gim = T * fmaf(T2, 2.505210839e-08f, D1);      // 1/11!
-  zr = -gim;
+template <class V>
+__device__ __forceinline__ void face_series_k9(V T, V P, V& zr, V& zi) {
+  const V T2 = vmul(T, T);
+  V A0 = vfma(P, vs<V>(2.755731922e-07f), vs<V>(-2.480158730e-05f));   // 1/10!, -1/8!
+  A0 = vfma(P, A0, vs<V>(1.388888889e-03f));                         // 1/6!
+  A0 = vfma(P, A0, vs<V>(-4.166666667e-02f));                        // -1/4!
+  A0 = vfma(P, A0, vs<V>(0.5f));                                     // 1/2!
+  const V A2 = vfma(P, vs<V>(8.267195767e-07f), vs<V>(-2.480158730e-05f));   // 3/10!, -1/8!
+  V D1 = vfma(P, vs<V>(1.002084335e-07f), vs<V>(-8.267195767e-06f));   // 4/11!, -3/9!
+  D1 = vfma(P, D1, vs<V>(3.968253968e-04f));                         // 2/7!
+  D1 = vfma(P, D1, vs<V>(-8.333333333e-03f));                        // -1/5!
+  const V gre = vfma(T2, A2, A0);
+  const V gim = vmul(T, vfma(T2, vs<V>(2.505210839e-08f), D1));      // 1/11!
+  zr = vneg(gim);
   zi = gre;
 }
 
-__device__ __forceinline__ void face_series_k13(float T, float P, float& zr, float& zi) {
-  const float T2 = T * T;
-  float A0 = fmaf(P, 1.147074560e-11f, -2.087675699e-09f);   // 1/14!, -1/12!
-  A0 = fmaf(P, A0, 2.755731922e-07f);                         // 1/10!
-  A0 = fmaf(P, A0, -2.480158730e-05f);                        // -1/8!
-  A0 = fmaf(P, A0, 1.388888889e-03f);                         // 1/6!
-  A0 = fmaf(P, A0, -4.166666667e-02f);                        // -1/4!
-  A0 = fmaf(P, A0, 0.5f);                                     // 1/2!
-  float A2 = fmaf(P, 1.147074560e-10f, -1.252605419e-08f);   // 10/14!, -6/12!
-  A2 = fmaf(P, A2, 8.267195767e-07f);                         // 3/10!
-  A2 = fmaf(P, A2, -2.480158730e-05f);                        // -1/8!
-  float D1 = fmaf(P, 4.588298239e-12f, -8.029521918e-10f);   // 6/15!, -5/13!
-  D1 = fmaf(P, D1, 1.002084335e-07f);                         // 4/11!
-  D1 = fmaf(P, D1, -8.267195767e-06f);                        // -3/9!
-  D1 = fmaf(P, D1, 3.968253968e-04f);                         // 2/7!
-  D1 = fmaf(P, D1, -8.333333333e-03f);                        // -1/5!
-  float D3 = fmaf(P, 7.647163732e-12f, -6.423617535e-10f);   // 10/15!, -4/13!
-  D3 = fmaf(P, D3, 2.505210839e-08f);                         // 1/11!
-  const float gre = fmaf(T2, fmaf(T2, 1.147074560e-11f, A2), A0);   // 1/14!
-  const float gim = T * fmaf(T2, D3, D1);
-  zr = -gim;
+template <class V>
+__device__ __forceinline__ void face_series_k13(V T, V P, V& zr, V& zi) {
+  const V T2 = vmul(T, T);
+  V A0 = vfma(P, vs<V>(1.147074560e-11f), vs<V>(-2.087675699e-09f));   // 1/14!, -1/12!
+  A0 = vfma(P, A0, vs<V>(2.755731922e-07f));                         // 1/10!
+  A0 = vfma(P, A0, vs<V>(-2.480158730e-05f));                        // -1/8!
+  A0 = vfma(P, A0, vs<V>(1.388888889e-03f));                         // 1/6!
+  A0 = vfma(P, A0, vs<V>(-4.166666667e-02f));                        // -1/4!
+  A0 = vfma(P, A0, vs<V>(0.5f));                                     // 1/2!
+  V A2 = vfma(P, vs<V>(1.147074560e-10f), vs<V>(-1.252605419e-08f));   // 10/14!, -6/12!
+  A2 = vfma(P, A2, vs<V>(8.267195767e-07f));                         // 3/10!
+  A2 = vfma(P, A2, vs<V>(-2.480158730e-05f));                        // -1/8!
+  V D1 = vfma(P, vs<V>(4.588298239e-12f), vs<V>(-8.029521918e-10f));   // 6/15!, -5/13!
+  D1 = vfma(P, D1, vs<V>(1.002084335e-07f));                         // 4/11!
+  D1 = vfma(P, D1, vs<V>(-8.267195767e-06f));                        // -3/9!
+  D1 = vfma(P, D1, vs<V>(3.968253968e-04f));                         // 2/7!
+  D1 = vfma(P, D1, vs<V>(-8.333333333e-03f));                        // -1/5!
+  V D3 = vfma(P, vs<V>(7.647163732e-12f), vs<V>(-6.423617535e-10f));   // 10/15!, -4/13!
+  D3 = vfma(P, D3, vs<V>(2.505210839e-08f));                         // 1/11!
+  const V gre = vfma(T2, vfma(T2, vs<V>(1.147074560e-11f), A2), A0);   // 1/14!
+  const V gim = vmul(T, vfma(T2, D3, D1));
+  zr = vneg(gim);
   zi = gre;
 }
 
@@ -202,38 +209,39 @@ __device__ __forceinline__ void face_series_k13(float T, float P, float& zr, flo
 //   G_re = A0(P) + T^2 (A2(P) + T^2 A4(P)),  G_im = T (D1(P) + T^2 (D3(P) + T^2 D5(P))),
 // the coefficient of P^i in A_j / D_j being +-C(i + j, i)/(2i + 3j + 2)!;
 // the omitted terms (k >= 18) are below 1e-9 (|G| <= 1/2).
-__device__ __forceinline__ void face_series_xlong(float T, float P, float& zr, float& zi) {
-  const float T2 = T * T;
-  float A0 = fmaf(P, 1.561920697e-16f, -4.779477332e-14f);   // 1/18!, -1/16!
-  A0 = fmaf(P, A0, 1.147074560e-11f);                         // 1/14!
-  A0 = fmaf(P, A0, -2.087675699e-09f);                        // -1/12!
-  A0 = fmaf(P, A0, 2.755731922e-07f);                         // 1/10!
-  A0 = fmaf(P, A0, -2.480158730e-05f);                        // -1/8!
-  A0 = fmaf(P, A0, 1.388888889e-03f);                         // 1/6!
-  A0 = fmaf(P, A0, -4.166666667e-02f);                        // -1/4!
-  A0 = fmaf(P, A0, 0.5f);                                     // 1/2!
-  float A2 = fmaf(P, 3.280033463e-15f, -7.169215999e-13f);   // 21/18!, -15/16!
-  A2 = fmaf(P, A2, 1.147074560e-10f);                         // 10/14!
-  A2 = fmaf(P, A2, -1.252605419e-08f);                        // -6/12!
-  A2 = fmaf(P, A2, 8.267195767e-07f);                         // 3/10!
-  A2 = fmaf(P, A2, -2.480158730e-05f);                        // -1/8!
-  float A4 = fmaf(P, 2.342881045e-15f, -2.389738666e-13f);   // 15/18!, -5/16!
-  A4 = fmaf(P, A4, 1.147074560e-11f);                         // 1/14!
-  float D1 = fmaf(P, 6.576508197e-17f, -1.968020078e-14f);   // 8/19!, -7/17!
-  D1 = fmaf(P, D1, 4.588298239e-12f);                         // 6/15!
-  D1 = fmaf(P, D1, -8.029521918e-10f);                        // -5/13!
-  D1 = fmaf(P, D1, 1.002084335e-07f);                         // 4/11!
-  D1 = fmaf(P, D1, -8.267195767e-06f);                        // -3/9!
-  D1 = fmaf(P, D1, 3.968253968e-04f);                         // 2/7!
-  D1 = fmaf(P, D1, -8.333333333e-03f);                        // -1/5!
-  float D3 = fmaf(P, 2.877222336e-16f, -5.622914509e-14f);   // 35/19!, -20/17!
-  D3 = fmaf(P, D3, 7.647163732e-12f);                         // 10/15!
-  D3 = fmaf(P, D3, -6.423617535e-10f);                        // -4/13!
-  D3 = fmaf(P, D3, 2.505210839e-08f);                         // 1/11!
-  const float D5 = fmaf(P, 4.932381148e-17f, -2.811457254e-15f);   // 6/19!, -1/17!
-  const float gre = fmaf(T2, fmaf(T2, A4, A2), A0);
-  const float gim = T * fmaf(T2, fmaf(T2, D5, D3), D1);
-  zr = -gim;
+template <class V>
+__device__ __forceinline__ void face_series_xlong(V T, V P, V& zr, V& zi) {
+  const V T2 = vmul(T, T);
+  V A0 = vfma(P, vs<V>(1.561920697e-16f), vs<V>(-4.779477332e-14f));   // 1/18!, -1/16!
+  A0 = vfma(P, A0, vs<V>(1.147074560e-11f));                         // 1/14!
+  A0 = vfma(P, A0, vs<V>(-2.087675699e-09f));                        // -1/12!
+  A0 = vfma(P, A0, vs<V>(2.755731922e-07f));                         // 1/10!
+  A0 = vfma(P, A0, vs<V>(-2.480158730e-05f));                        // -1/8!
+  A0 = vfma(P, A0, vs<V>(1.388888889e-03f));                         // 1/6!
+  A0 = vfma(P, A0, vs<V>(-4.166666667e-02f));                        // -1/4!
+  A0 = vfma(P, A0, vs<V>(0.5f));                                     // 1/2!
+  V A2 = vfma(P, vs<V>(3.280033463e-15f), vs<V>(-7.169215999e-13f));   // 21/18!, -15/16!
+  A2 = vfma(P, A2, vs<V>(1.147074560e-10f));                         // 10/14!
+  A2 = vfma(P, A2, vs<V>(-1.252605419e-08f));                        // -6/12!
+  A2 = vfma(P, A2, vs<V>(8.267195767e-07f));                         // 3/10!
+  A2 = vfma(P, A2, vs<V>(-2.480158730e-05f));                        // -1/8!
+  V A4 = vfma(P, vs<V>(2.342881045e-15f), vs<V>(-2.389738666e-13f));   // 15/18!, -5/16!
+  A4 = vfma(P, A4, vs<V>(1.147074560e-11f));                         // 1/14!
+  V D1 = vfma(P, vs<V>(6.576508197e-17f), vs<V>(-1.968020078e-14f));   // 8/19!, -7/17!
+  D1 = vfma(P, D1, vs<V>(4.588298239e-12f));                         // 6/15!
+  D1 = vfma(P, D1, vs<V>(-8.029521918e-10f));                        // -5/13!
+  D1 = vfma(P, D1, vs<V>(1.002084335e-07f));                         // 4/11!
+  D1 = vfma(P, D1, vs<V>(-8.267195767e-06f));                        // -3/9!
+  D1 = vfma(P, D1, vs<V>(3.968253968e-04f));                         // 2/7!
+  D1 = vfma(P, D1, vs<V>(-8.333333333e-03f));                        // -1/5!
+  V D3 = vfma(P, vs<V>(2.877222336e-16f), vs<V>(-5.622914509e-14f));   // 35/19!, -20/17!
+  D3 = vfma(P, D3, vs<V>(7.647163732e-12f));                         // 10/15!
+  D3 = vfma(P, D3, vs<V>(-6.423617535e-10f));                        // -4/13!
+  D3 = vfma(P, D3, vs<V>(2.505210839e-08f));                         // 1/11!
+  const V D5 = vfma(P, vs<V>(4.932381148e-17f), vs<V>(-2.811457254e-15f));   // 6/19!, -1/17!
+  const V gre = vfma(T2, vfma(T2, A4, A2), A0);
+  const V gim = vmul(T, vfma(T2, vfma(T2, D5, D3), D1));
+  zr = vneg(gim);
   zi = gre;
 }
 
@@ -287,12 +295,19 @@ __device__ __forceinline__ void face_edge(float qx, float qy, float qz, const fl
 }
 
 // |Q|^2 I_m = -s exp(i mu) Z, added into the tile sums (tre, tim).
-__device__ __forceinline__ void face_finish(float mu, float s, float zr, float zi, float& tre, float& tim) {
-  float sm, cm;
-  __sincosf(mu, &sm, &cm);
-  const float c = -s * cm, d = -s * sm;   // -s exp(i mu) = c + i d
-  tre = fmaf(c, zr, fmaf(-d, zi, tre));
-  tim = fmaf(c, zi, fmaf(d, zr, tim));
+__device__ __forceinline__ void sincos_v(float x, float& sn, float& cs) { __sincosf(x, &sn, &cs); }
+__device__ __forceinline__ void sincos_v(float2 x, float2& sn, float2& cs) {
+  __sincosf(x.x, &sn.x, &cs.x);
+  __sincosf(x.y, &sn.y, &cs.y);
+}
+
+template <class V>
+__device__ __forceinline__ void face_finish(V mu, V s, V zr, V zi, V& tre, V& tim) {
+  V sm, cm;
+  sincos_v(mu, sm, cm);
+  const V c = vmul(vneg(s), cm), d = vmul(vneg(s), sm);   // -s exp(i mu) = c + i d
+  tre = vfma(c, zr, vfma(vneg(d), zi, tre));
+  tim = vfma(c, zi, vfma(d, zr, tim));
 }
 
 // Same face term in FP64 (comparison path): library sincos, series through k = 16.
@@ -376,6 +391,31 @@ struct Acc64 {
   __device__ __forceinline__ double2 get(int r) const { return make_double2(re[r], im[r]); }
 };
 
+// Element r of a thread's R per-Q values, stored as R floats or, for even R, as R/2 float2 pairs.
+__device__ __forceinline__ float& el(float* a, int r) { return a[r]; }
+__device__ __forceinline__ float& el(float2* a, int r) { return (r & 1) ? a[r >> 1].y : a[r >> 1].x; }
+__device__ __forceinline__ float el(const float* a, int r) { return a[r]; }
+__device__ __forceinline__ float el(const float2* a, int r) { return (r & 1) ? a[r >> 1].y : a[r >> 1].x; }
+
+// Per-Q values of a thread: R floats, or R/2 float2 pairs when R is even, so that the per-pair
+// arithmetic runs as paired FP32 instructions (two Q points per issue slot).
+template <int R>
+struct QPack {
+  static constexpr bool kPacked = (R % 2) == 0;
+  static constexpr int N = kPacked ? R / 2 : R;
+  using V = typename std::conditional<kPacked, float2, float>::type;
+  template <int D>
+  __device__ static __forceinline__ void pack(const float (&q)[R][3], V (&qv)[N][3]) {
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        if constexpr (kPacked) qv[j][d] = make_float2(q[2 * j][d], q[2 * j + 1][d]);
+        else qv[j][d] = q[j][d];
+      }
+  }
+};
+
 struct Pol2F32 {
   using Item = Seg32;
   static constexpr int kDim = 2, kTile = 128;
@@ -385,41 +425,45 @@ struct Pol2F32 {
   template <int R>
   __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc, Thr,
                                               int64_t) {
-    float tre[R], tim[R];
+    using V = typename QPack<R>::V;
+    constexpr int N = QPack<R>::N;
+    V qv[N][3], tre[N], tim[N];
+    QPack<R>::template pack<2>(q, qv);
 #pragma unroll
-    for (int r = 0; r < R; ++r) { tre[r] = 0.f; tim[r] = 0.f; }
+    for (int j = 0; j < N; ++j) { tre[j] = vs<V>(0.f); tim[j] = vs<V>(0.f); }
 #pragma unroll 1
     for (int i = 0; i < cnt; ++i) {
       const float4 s = reinterpret_cast<const float4*>(t)[i];   // m.x, m.y, D.x/2, D.y/2
-      float ph[R], u[R], u2[R], w[R], S[R];
+      V ph[N], u[N], u2[N], w[N], S[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const V qx = qv[j][0], qy = qv[j][1];
+        ph[j] = vfma(qx, vs<V>(s.x), vmul(qy, vs<V>(s.y)));          // Q.m
+        u[j] = vfma(qx, vs<V>(s.z), vmul(qy, vs<V>(s.w)));           // Q.D / 2
+        w[j] = vfma(qx, vs<V>(s.w), vmul(vneg(qy), vs<V>(s.z)));     // (Qx Dy - Qy Dx) / 2
+        u2[j] = vmul(u[j], u[j]);
+        S[j] = sinc_poly_v(u2[j]);
+      }
       bool big = false;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const float qx = q[r][0], qy = q[r][1];
-        ph[r] = fmaf(qx, s.x, qy * s.y);      // Q.m
-        u[r] = fmaf(qx, s.z, qy * s.w);       // Q.D / 2
-        w[r] = fmaf(qx, s.w, -qy * s.z);      // (Qx Dy - Qy Dx) / 2
-        u2[r] = u[r] * u[r];
-        S[r] = sinc_poly(u2[r]);
-        big = big || (u2[r] > kPi2);
-      }
+      for (int r = 0; r < R; ++r) big = big || (el(u2, r) > kPi2);
       // segments long against 1/|Q|: the SFU sinc, only in warps where some lane needs it
       if (__any_sync(0xffffffffu, big)) {
 #pragma unroll
         for (int r = 0; r < R; ++r)
-          if (u2[r] > kPi2) S[r] = sinc_large(u[r]);
+          if (el(u2, r) > kPi2) el(S, r) = sinc_large(el(u, r));
       }
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        float sn, cs;
-        __sincosf(ph[r], &sn, &cs);
-        const float ws = w[r] * S[r];
-        tre[r] = fmaf(ws, sn, tre[r]);     // -i ws (cos + i sin) = ws sin - i ws cos
-        tim[r] = fmaf(-ws, cs, tim[r]);
+      for (int j = 0; j < N; ++j) {
+        V sn, cs;
+        sincos_v(ph[j], sn, cs);
+        const V ws = vmul(w[j], S[j]);
+        tre[j] = vfma(ws, sn, tre[j]);     // -i ws (cos + i sin) = ws sin - i ws cos
+        tim[j] = vfma(vneg(ws), cs, tim[j]);
       }
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) { acc.re[r].add(tre[r]); acc.im[r].add(tim[r]); }
+    for (int r = 0; r < R; ++r) { acc.re[r].add(el(tre, r)); acc.im[r].add(el(tim, r)); }
   }
 };
 
@@ -449,57 +493,60 @@ struct Pol2F64 {
 // quantities and the warp's largest P (the branch tests need only it and the thread's smallest P).
 template <int R>
 struct FaceQ {
-  float mu[R], a0[R], a1[R], s[R], P[R], T[R];
+  using V = typename QPack<R>::V;
+  static constexpr int N = QPack<R>::N;
+  V mu[N], a0[N], a1[N], s[N], P[N], T[N];
   float pmin, wmax;
-  __device__ __forceinline__ void load(const float (&q)[R][3], const float4 A, const float4 B, const float4 C) {
-    float pmax = 0.f;
-    pmin = 0.f;
+  __device__ __forceinline__ void load(const V (&qv)[N][3], const float4 A, const float4 B, const float4 C) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      face_common_pt(q[r][0], q[r][1], q[r][2], A, B, C, mu[r], a0[r], a1[r], s[r], P[r], T[r]);
-      pmax = r ? fmaxf(pmax, P[r]) : P[r];
-      pmin = r ? fminf(pmin, P[r]) : P[r];
+    for (int j = 0; j < N; ++j)
+      face_common_pt(qv[j][0], qv[j][1], qv[j][2], A, B, C, mu[j], a0[j], a1[j], s[j], P[j], T[j]);
+    float pmax = el(P, 0);
+    pmin = el(P, 0);
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      pmax = fmaxf(pmax, el(P, r));
+      pmin = fminf(pmin, el(P, r));
     }
     // P >= +0 (it is s1^2 - a0 a1 = a0^2 + a0 a1 + a1^2) or NaN, so its bits order as unsigned
     // integers, and one reduction replaces a vote per rung of the ladder
     wmax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(pmax)));
   }
   // the shortest series whose bound holds for the whole warp (wmax and th.hi are uniform)
-  __device__ __forceinline__ void series(const Thr& th, float (&zr)[R], float (&zi)[R]) const {
+  __device__ __forceinline__ void series(const Thr& th, V (&zr)[N], V (&zi)[N]) const {
     if (th.hi <= kPShort || wmax < kPShort) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) face_series(T[r], P[r], zr[r], zi[r]);
+      for (int j = 0; j < N; ++j) face_series(T[j], P[j], zr[j], zi[j]);
     } else if (th.hi <= kP9 || wmax < kP9) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) face_series_k9(T[r], P[r], zr[r], zi[r]);
+      for (int j = 0; j < N; ++j) face_series_k9(T[j], P[j], zr[j], zi[j]);
     } else if (th.hi <= kPLong || wmax < kPLong) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) face_series_long(T[r], P[r], zr[r], zi[r]);
+      for (int j = 0; j < N; ++j) face_series_long(T[j], P[j], zr[j], zi[j]);
     } else if (th.hi <= kP13 || wmax < kP13) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) face_series_k13(T[r], P[r], zr[r], zi[r]);
+      for (int j = 0; j < N; ++j) face_series_k13(T[j], P[j], zr[j], zi[j]);
     } else {
 #pragma unroll
-      for (int r = 0; r < R; ++r) face_series_xlong(T[r], P[r], zr[r], zi[r]);
+      for (int j = 0; j < N; ++j) face_series_xlong(T[j], P[j], zr[j], zi[j]);
     }
   }
-  // the edge sum, with the few Q points below tau_lo^2/4 redone by the short series
+  // the edge sum (per Q point), with the few Q points below tau_lo^2/4 redone by the short series
   template <bool kShared>
   __device__ __forceinline__ void edge(const Thr& th, const float (&q)[R][3], const float4 A, const float4 B,
-                                       const float4 C, float (&zr)[R], float (&zi)[R], float (&S0)[R]) const {
+                                       const float4 C, V (&zr)[N], V (&zi)[N], float (&S0)[R]) const {
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      face_edge<kShared>(q[r][0], q[r][1], q[r][2], A, B, C, a0[r], a1[r], zr[r], zi[r], S0[r]);
+      face_edge<kShared>(q[r][0], q[r][1], q[r][2], A, B, C, el(a0, r), el(a1, r), el(zr, r), el(zi, r), S0[r]);
     if (pmin < th.lo) {
 #pragma unroll
       for (int r = 0; r < R; ++r)
-        if (P[r] < th.lo) face_series(T[r], P[r], zr[r], zi[r]);   // P < tau_lo^2/4 <= 1/4
+        if (el(P, r) < th.lo) face_series(el(T, r), el(P, r), el(zr, r), el(zi, r));   // P < tau_lo^2/4 <= 1/4
     }
   }
-  __device__ __forceinline__ void finish(const float (&zr)[R], const float (&zi)[R], float (&tre)[R],
-                                         float (&tim)[R]) const {
+  __device__ __forceinline__ void finish(const V (&zr)[N], const V (&zi)[N], V (&tre)[N], V (&tim)[N]) const {
 #pragma unroll
-    for (int r = 0; r < R; ++r) face_finish(mu[r], s[r], zr[r], zi[r], tre[r], tim[r]);
+    for (int j = 0; j < N; ++j) face_finish(mu[j], s[j], zr[j], zi[j], tre[j], tim[j]);
   }
 };
 
@@ -519,9 +566,12 @@ struct Pol3F32T {
   template <int R>
   __device__ static __forceinline__ void tile(const Item* t, int cnt, const QT (&q)[R][3], Acc<R>& acc,
                                               Thr th, int64_t first) {
-    float tre[R], tim[R];
+    using V = typename QPack<R>::V;
+    constexpr int N = QPack<R>::N;
+    V qv[N][3], tre[N], tim[N];
+    QPack<R>::template pack<3>(q, qv);
 #pragma unroll
-    for (int r = 0; r < R; ++r) { tre[r] = 0.f; tim[r] = 0.f; }
+    for (int j = 0; j < N; ++j) { tre[j] = vs<V>(0.f); tim[j] = vs<V>(0.f); }
     // S0 carries the first edge's sinc from the first face of a pair to the second; `held` says
     // that it does (warp-uniform: it follows the warp-uniform branch decisions)
     float S0[R];
@@ -531,8 +581,8 @@ struct Pol3F32T {
       const float4* p = reinterpret_cast<const float4*>(t + i);
       const float4 A = p[0], B = p[1], C = p[2];
       FaceQ<R> f;
-      f.load(q, A, B, C);
-      float zr[R], zi[R];
+      f.load(qv, A, B, C);
+      V zr[N], zi[N];
       if (f.wmax < th.hi) {
         f.series(th, zr, zi);
         held = false;
@@ -548,7 +598,7 @@ struct Pol3F32T {
       f.finish(zr, zi, tre, tim);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) { acc.re[r].add(tre[r]); acc.im[r].add(tim[r]); }
+    for (int r = 0; r < R; ++r) { acc.re[r].add(el(tre, r)); acc.im[r].add(el(tim, r)); }
   }
 };
 using Pol3F32 = Pol3F32T<false>;

@@ -115,10 +115,11 @@ def _fn_body(name):
 
 def _arith_ops(body):
     """FP32-pipe operations written in a device function body: each fmaf, each binary * + -
-    between operands (unary minus on a product folds into the FMA or multiply, so it is not
-    counted)."""
+    between operands, and each call of the scalar-or-packed helpers vfma / vmul / vadd (one
+    operation per Q point; unary minus, also as vneg, folds into the FMA or multiply, so it is
+    not counted)."""
     import re
-    n = body.count("fmaf(")
+    n = body.count("fmaf(") + body.count("vfma(") + body.count("vmul(") + body.count("vadd(")
     n += len(re.findall(r"[\w\)\]] \* [\w\(-]", body))
     n += len(re.findall(r"[\w\)\]] [+-] [\w\(]", body))
     return n

@@ -26,7 +26,7 @@ def _floats(body):
 
 def test_sinc_polynomial_accuracy():
     """sinc(u) on |u| <= pi from the degree-6 polynomial in u^2."""
-    c = _floats(_body("pft_common.cuh", "float sinc_poly("))
+    c = _floats(_body("pft_common.cuh", "V sinc_poly_v("))
     assert len(c) == 6
     # Horner order in the source: c6, c5, then c4..c1, constant 1
     coef = np.array([1.0] + c[::-1], dtype=np.float32)     # c0..c6
