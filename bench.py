@@ -60,6 +60,14 @@ OPS2D = {
     "poly_sinc": {"fp32": 18, "sfu": 2},
     "sfu_sinc": {"fp32": 24, "sfu": 4},
 }
+# 2D pair adjoint (seg_adj in pft_bwd.cu: the term recomputed and differentiated, four record
+# adjoints updated): 21 written, sinc_d's polynomial and derivative 14, range test 1, the sincos
+# argument scaling 1, with 2 SFU operations; beyond |u| > pi sinc_d adds the turn reduction, sin,
+# cos and 1/u and the two quotients (8 FP32-pipe + 3 SFU).
+OPS2D_ADJ = {
+    "poly_sinc": {"fp32": 37, "sfu": 2},
+    "sfu_sinc": {"fp32": 45, "sfu": 5},
+}
 # Per-pair operation counts of the 3D pair adjoint (face_adj_t in pft_bwd.cu, forward recomputed
 # and differentiated in reverse mode), as a part every pair pays plus one part per branch; a warp
 # whose lanes take two branches issues both.  Common to every branch: the projections (face_common,
@@ -67,16 +75,17 @@ OPS2D = {
 # the argument scaling of sincos(mu) (1) and its 2 SFU operations, the weights W = e^{i mu} Z and
 # the adjoints of s and mu (15), and the 12 updates of the record (vertex adjoint, RecAdj) or, for
 # the Q-gradient (QAdj), the 12 updates of Q plus the 2 adds of the pair's own term.  Per branch:
-# the series forms' forward part and derivatives in P and T (k <= 7, 9, 11, 17: 18 / 29 / 40 / 89)
-# plus their adjoint (10); the edge sum's forward part (32 written, three sinc_d of 22, two sincos scalings, the
-# 1/|X|^2 test and select: 102, with 5 SFU operations) plus its adjoint (36) and the X-adjoint
-# terms (12 record updates, or 6 for Q).
+# the series forms' forward part and derivatives in P and T (k <= 7, 9, 11, 17: 17 / 26 / 34 / 70)
+# plus their adjoint (10); the edge sum's forward part (38, three sinc_d on the polynomial path of
+# 15, two sincos scalings, the 1/|X|^2 test and select: 87, with 5 SFU operations) plus its adjoint
+# (62) and the X-adjoint terms (12 record updates, or 6 for Q).  Products of two literals are
+# folded by the compiler and not counted; the SFU sinc beyond |u| > pi is the rare branch.
 OPS_ADJ = {"common": {"fp32": 53, "sfu": 2},
-           "short": {"fp32": 28, "sfu": 0}, "k9": {"fp32": 39, "sfu": 0}, "long": {"fp32": 50, "sfu": 0},
-           "xlong": {"fp32": 99, "sfu": 0}, "edge": {"fp32": 150, "sfu": 5}}
+           "short": {"fp32": 27, "sfu": 0}, "k9": {"fp32": 36, "sfu": 0}, "long": {"fp32": 44, "sfu": 0},
+           "xlong": {"fp32": 80, "sfu": 0}, "edge": {"fp32": 161, "sfu": 5}}
 OPS_QADJ = {"common": {"fp32": 57, "sfu": 2},
-            "short": {"fp32": 28, "sfu": 0}, "k9": {"fp32": 39, "sfu": 0}, "long": {"fp32": 50, "sfu": 0},
-            "xlong": {"fp32": 99, "sfu": 0}, "edge": {"fp32": 144, "sfu": 5}}
+            "short": {"fp32": 27, "sfu": 0}, "k9": {"fp32": 36, "sfu": 0}, "long": {"fp32": 44, "sfu": 0},
+            "xlong": {"fp32": 80, "sfu": 0}, "edge": {"fp32": 155, "sfu": 5}}
 FP32_LANES, SFU_LANES = 128, 16       # per SM per clock
 # A fixed per-pair count of the triangle term taken as the edge sum of Eq. 14 with a polynomial sinc
 # (projections, three edges' phase/sinc/term, face factor): the basis of frac_vs_survey_count.
@@ -268,10 +277,12 @@ def sfu_sinc_fraction(verts, poly_off, q, n=1 << 16, seed=0):
     return float(np.mean(u > np.pi))
 
 
-def roofline2d(pairs, t_s, f_sfu, n_sm, clk_mhz):
-    """Issue-slot / SFU bound of the 2D segment term for a given SFU-sinc fraction."""
+def roofline2d(pairs, t_s, f_sfu, n_sm, clk_mhz, table=None):
+    """Issue-slot / SFU bound of the 2D segment term (or, with table=OPS2D_ADJ, of its adjoint)
+    for a given SFU-sinc fraction."""
+    table = OPS2D if table is None else table
     mix = {"poly_sinc": 1.0 - f_sfu, "sfu_sinc": f_sfu}
-    ops = {k: sum(mix[b] * OPS2D[b][k] for b in OPS2D) for k in ("fp32", "sfu")}
+    ops = {k: sum(mix[b] * table[b][k] for b in table) for k in ("fp32", "sfu")}
     issue = ops["fp32"] + ops["sfu"]
     cyc = max(issue / FP32_LANES, ops["sfu"] / SFU_LANES)
     peak_pairs = n_sm * clk_mhz * 1e6 / cyc
@@ -467,8 +478,23 @@ def bench_batched(dev, warmup, steps):
         b.record()
         b.synchronize()
         tb.append(a.elapsed_time(b))
+    launches_b = int(pft.load().pft_backward_last_launch_count())
+    tk = []   # the pair kernel k_bbwd alone: caller events the library records around it
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        b.record()
+        pft.pft2d_polygons_batched_backward(vd, offd, qd, gb, options={"main_start_event": a.cuda_event,
+                                                                       "main_stop_event": b.cuda_event})
+        torch.cuda.synchronize()
+        tk.append(a.elapsed_time(b))
+    rlb = roofline2d(pairs, float(np.mean(tk)) / 1e3, rl["sfu_sinc_fraction"],
+                     torch.cuda.get_device_properties(dev).multi_processor_count, float(pk.get("sm_max_mhz", 2070.0)),
+                     table=OPS2D_ADJ)
+    rlb.update({"kernel": "k_bbwd", "kernel_ms": float(np.mean(tk))})
     backward = {"value": pairs / (float(np.mean(tb)) / 1e3) / 1e9, "unit": UNIT + " (adjoint call)",
-                "ms": float(np.mean(tb)), "launches": int(pft.load().pft_backward_last_launch_count())}
+                "ms": float(np.mean(tb)), "launches": launches_b, "roofline": rlb}
     del gb
     return {"value": pairs / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "pairs_per_step": pairs,
             "roofline": rl,

@@ -100,28 +100,39 @@ struct Ring {
 };
 
 // sinc(u) and its derivative: the Chebyshev polynomial and its derivative on
-// |u| <= pi, sin and cos of the turn-reduced argument beyond.
-__device__ __forceinline__ void sinc_d(float u, float& S, float& dS) {
-  const float v = u * u;
-  float p = fmaf(v, 1.361159657e-10f, -2.472836691e-8f);
-  p = fmaf(v, p, 2.753580020e-6f);
-  p = fmaf(v, p, -1.984053088e-4f);
-  p = fmaf(v, p, 8.333321661e-3f);
-  p = fmaf(v, p, -1.666666567e-1f);
-  S = fmaf(v, p, 1.0f);
-  float d = fmaf(v, 6.0f * 1.361159657e-10f, 5.0f * -2.472836691e-8f);   // p'(v)
-  d = fmaf(v, d, 4.0f * 2.753580020e-6f);
-  d = fmaf(v, d, 3.0f * -1.984053088e-4f);
-  d = fmaf(v, d, 2.0f * 8.333321661e-3f);
-  d = fmaf(v, d, -1.666666567e-1f);
-  dS = 2.0f * u * d;
-  if (__any_sync(__activemask(), v > kPi2)) {   // warp-uniform: the SFU work only where some lane needs it
-    if (v > kPi2) {
-      float s, c;
-      sincos_turns(u * kInvTwoPi, &s, &c);
-      const float r = rcp_approx(u);
-      S = s * r;
-      dS = (c - S) * r;
+// |u| <= pi, sin and cos of the turn-reduced argument beyond.  V = float2 takes two
+// arguments through the same (paired) instructions.
+template <class V>
+__device__ __forceinline__ void sinc_d(V u, V& S, V& dS) {
+  const V v = vmul(u, u);
+  V p = vfma(v, vs<V>(1.361159657e-10f), vs<V>(-2.472836691e-8f));
+  p = vfma(v, p, vs<V>(2.753580020e-6f));
+  p = vfma(v, p, vs<V>(-1.984053088e-4f));
+  p = vfma(v, p, vs<V>(8.333321661e-3f));
+  p = vfma(v, p, vs<V>(-1.666666567e-1f));
+  S = vfma(v, p, vs<V>(1.0f));
+  V d = vfma(v, vs<V>(6.0f * 1.361159657e-10f), vs<V>(5.0f * -2.472836691e-8f));   // p'(v)
+  d = vfma(v, d, vs<V>(4.0f * 2.753580020e-6f));
+  d = vfma(v, d, vs<V>(3.0f * -1.984053088e-4f));
+  d = vfma(v, d, vs<V>(2.0f * 8.333321661e-3f));
+  d = vfma(v, d, vs<V>(-1.666666567e-1f));
+  dS = vmul(vmul(vs<V>(2.0f), u), d);
+  constexpr int kE = sizeof(V) / sizeof(float);
+  bool big = false;
+#pragma unroll
+  for (int e = 0; e < kE; ++e) big = big || (el(&v, e) > kPi2);
+  if (__any_sync(__activemask(), big)) {   // warp-uniform: the SFU work only where some lane needs it
+#pragma unroll
+    for (int e = 0; e < kE; ++e) {
+      if (el(&v, e) > kPi2) {
+        const float ue = el(&u, e);
+        float s, c;
+        sincos_turns(ue * kInvTwoPi, &s, &c);
+        const float r = rcp_approx(ue);
+        const float Se = s * r;
+        el(&S, e) = Se;
+        el(&dS, e) = (c - Se) * r;
+      }
     }
   }
 }
@@ -131,23 +142,26 @@ __device__ __forceinline__ void sinc_d(float u, float& S, float& dS) {
 // ---------------------------------------------------------------------------
 
 // 2D: term -i w S(u) exp(i ph) of one (Q, segment) pair with weight gt; adds the
-// adjoints of the record fields (m.x, m.y, h.x, h.y).
-__device__ __forceinline__ void seg_adj(const QRec& Q, const float4 s, float (&a)[4]) {
-  const float ph = fmaf(Q.qx, s.x, Q.qy * s.y);
-  const float u = fmaf(Q.qx, s.z, Q.qy * s.w);
-  const float w = fmaf(Q.qx, s.w, -Q.qy * s.z);
-  float sn, cs;
-  __sincosf(ph, &sn, &cs);
-  float S, dS;
+// adjoints of the record fields s = (m.x, m.y, h.x, h.y).  V = float2 holds two
+// segments (one Q record feeds both).
+template <class V>
+__device__ __forceinline__ void seg_adj(const QRec& Q, const V (&s)[4], V (&a)[4]) {
+  const V qx = vs<V>(Q.qx), qy = vs<V>(Q.qy);
+  const V ph = vfma(qx, s[0], vmul(qy, s[1]));
+  const V u = vfma(qx, s[2], vmul(qy, s[3]));
+  const V w = vfma(qx, s[3], vmul(vneg(qy), s[2]));
+  V sn, cs;
+  sincos_v(ph, sn, cs);
+  V S, dS;
   sinc_d(u, S, dS);
-  const float A = fmaf(Q.gr, sn, -Q.gi * cs);   // Re(conj(gt)(sin - i cos))
-  const float B = fmaf(Q.gr, cs, Q.gi * sn);    // dA/dph
-  const float wb = S * A, Sb = w * A, phb = w * S * B;
-  const float ub = Sb * dS;
-  a[0] = fmaf(phb, Q.qx, a[0]);
-  a[1] = fmaf(phb, Q.qy, a[1]);
-  a[2] = fmaf(ub, Q.qx, fmaf(-wb, Q.qy, a[2]));
-  a[3] = fmaf(ub, Q.qy, fmaf(wb, Q.qx, a[3]));
+  const V A = vfma(vs<V>(Q.gr), sn, vmul(vs<V>(-Q.gi), cs));   // Re(conj(gt)(sin - i cos))
+  const V B = vfma(vs<V>(Q.gr), cs, vmul(vs<V>(Q.gi), sn));    // dA/dph
+  const V wb = vmul(S, A), Sb = vmul(w, A), phb = vmul(vmul(w, S), B);
+  const V ub = vmul(Sb, dS);
+  a[0] = vfma(phb, qx, a[0]);
+  a[1] = vfma(phb, qy, a[1]);
+  a[2] = vfma(ub, qx, vfma(vneg(wb), qy, a[2]));
+  a[3] = vfma(ub, qy, vfma(wb, qx, a[3]));
 }
 
 // 3D: face term J = -s exp(i mu) Z (series or edge branch, chosen as in the
@@ -862,7 +876,7 @@ __global__ void __launch_bounds__(kBwdNT) k_bwd(const void* __restrict__ items, 
 #pragma unroll 1
     for (int j = 0; j < cnt; ++j) {
       const QRec Q = tq[j];
-      if constexpr (D == 2) seg_adj(Q, F[0], *reinterpret_cast<float(*)[4]>(a));
+      if constexpr (D == 2) seg_adj(Q, *reinterpret_cast<const float(*)[4]>(&F[0]), *reinterpret_cast<float(*)[4]>(a));
       else face_adj(Q, F[0], F[1], F[2], th, *reinterpret_cast<float(*)[12]>(a));
     }
 #pragma unroll
@@ -1152,16 +1166,18 @@ __global__ void __launch_bounds__(kBwdNT) k_bbwd(const Seg32* __restrict__ segs,
     const QRec* tq = ring.tile(t);
     const int cnt = ring.count(t);
     float a[4] = {0.f, 0.f, 0.f, 0.f}, a2[4] = {0.f, 0.f, 0.f, 0.f};
-    if (live2) {
+    if (live2) {   // both segments in paired registers: .x the first, .y the second
+      const float2 sv[4] = {make_float2(F.x, F2.x), make_float2(F.y, F2.y), make_float2(F.z, F2.z),
+                            make_float2(F.w, F2.w)};
+      float2 ap[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll 1
-      for (int j = 0; j < cnt; ++j) {
-        const QRec Q = tq[j];
-        seg_adj(Q, F, a);
-        seg_adj(Q, F2, a2);
-      }
+      for (int j = 0; j < cnt; ++j) seg_adj(tq[j], sv, ap);
+#pragma unroll
+      for (int f = 0; f < 4; ++f) { a[f] = ap[f].x; a2[f] = ap[f].y; }
     } else if (live) {
+      const float sv[4] = {F.x, F.y, F.z, F.w};
 #pragma unroll 1
-      for (int j = 0; j < cnt; ++j) seg_adj(tq[j], F, a);
+      for (int j = 0; j < cnt; ++j) seg_adj(tq[j], sv, a);
     }
 #pragma unroll
     for (int f = 0; f < 4; ++f) { acc[f].add(a[f]); acc2[f].add(a2[f]); }

@@ -87,6 +87,11 @@ __device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y
 template <class V> __device__ __forceinline__ V vs(float c);
 template <> __device__ __forceinline__ float vs<float>(float c) { return c; }
 template <> __device__ __forceinline__ float2 vs<float2>(float c) { return make_float2(c, c); }
+// Element r of a thread's R per-Q values, stored as R floats or, for even R, as R/2 float2 pairs.
+__device__ __forceinline__ float& el(float* a, int r) { return a[r]; }
+__device__ __forceinline__ float& el(float2* a, int r) { return (r & 1) ? a[r >> 1].y : a[r >> 1].x; }
+__device__ __forceinline__ float el(const float* a, int r) { return a[r]; }
+__device__ __forceinline__ float el(const float2* a, int r) { return (r & 1) ? a[r >> 1].y : a[r >> 1].x; }
 
 // sinc(u) = sin(u)/u from v = u^2 <= pi^2: the degree-6 polynomial in v that
 // interpolates sinc(sqrt(v)) at the 7 Chebyshev nodes of [0, pi^2] (our own fit;

@@ -247,59 +247,72 @@ __device__ __forceinline__ void face_series_xlong(V T, V P, V& zr, V& zi) {
 
 // Z from the edge sum of Eq. 14.  The first edge's sinc(u_0) comes in through S0 when kShared
 // (the other face of a pair evaluated it: the same edge run the other way, and sinc is even) and
-// goes out through it otherwise.
-template <bool kShared = false>
-__device__ __forceinline__ void face_edge(float qx, float qy, float qz, const float4 A, const float4 B,
-                                          const float4 C, float a0, float a1, float& zr, float& zi,
-                                          float& S0) {
-  const float nx = C.y, ny = C.z, nz = C.w;
-  const float Xx = fmaf(ny, qz, -nz * qy), Xy = fmaf(nz, qx, -nx * qz), Xz = fmaf(nx, qy, -ny * qx);
-  const float x2 = fmaf(Xx, Xx, fmaf(Xy, Xy, Xz * Xz));
-  const float b0 = fmaf(A.w, Xx, fmaf(B.x, Xy, B.y * Xz));
-  const float b1 = fmaf(B.z, Xx, fmaf(B.w, Xy, C.x * Xz));
-  const float b2 = -(b0 + b1);
-  const float w[3] = {b1 - b0, b2 - b1, b0 - b2};
-  const float h0 = 0.5f * a0, h1 = 0.5f * a1;
-  const float u[3] = {h1 - h0, fmaf(-2.0f, h1, -h0), fmaf(2.0f, h0, h1)};  // (a_{l+1} - a_l)/2
-  // exp(i psi_l), psi_l = -a_{l+2}/2: psi_1 = -h0 and psi_2 = -h1 on the SFU,
-  // psi_0 = h0 + h1 as the conjugate of their product.
-  float sp[3], cp[3];
-  __sincosf(-h0, &sp[1], &cp[1]);
-  __sincosf(-h1, &sp[2], &cp[2]);
-  cp[0] = fmaf(cp[1], cp[2], -sp[1] * sp[2]);
-  sp[0] = -fmaf(sp[1], cp[2], cp[1] * sp[2]);
-  float u2[3], S[3];
-#pragma unroll
-  for (int l = kShared ? 1 : 0; l < 3; ++l) {
-    u2[l] = u[l] * u[l];
-    S[l] = sinc_poly(u2[l]);
-  }
-  // rare: an edge with |Q.d_l| > 2 pi somewhere in the warp (face_edge runs warp-converged)
-  if (__any_sync(0xffffffffu, fmaxf(kShared ? 0.f : u2[0], fmaxf(u2[1], u2[2])) > kPi2)) {
-#pragma unroll
-    for (int l = kShared ? 1 : 0; l < 3; ++l)
-      if (u2[l] > kPi2) S[l] = sinc_large(u[l]);
-  }
-  if (kShared) S[0] = S0;
-  else S0 = S[0];
-  float sr = 0.f, si = 0.f;
-#pragma unroll
-  for (int l = 0; l < 3; ++l) {
-    const float ws = w[l] * S[l];
-    sr = fmaf(ws, cp[l], sr);
-    si = fmaf(ws, sp[l], si);
-  }
-  const float inv = (x2 > 0.f) ? rcp_approx(x2) : 0.f;   // x2 = 0 only for Q parallel to N (series then)
-  zr = sr * inv;
-  zi = si * inv;
-}
-
-// |Q|^2 I_m = -s exp(i mu) Z, added into the tile sums (tre, tim).
+// goes out through it otherwise.  V = float2 carries two Q points through the same arithmetic.
 __device__ __forceinline__ void sincos_v(float x, float& sn, float& cs) { __sincosf(x, &sn, &cs); }
 __device__ __forceinline__ void sincos_v(float2 x, float2& sn, float2& cs) {
   __sincosf(x.x, &sn.x, &cs.x);
   __sincosf(x.y, &sn.y, &cs.y);
 }
+// 1/x2, and 0 for x2 = 0 (Q parallel to N: the series is taken there)
+__device__ __forceinline__ float rcp_or0(float x2) { return x2 > 0.f ? rcp_approx(x2) : 0.f; }
+__device__ __forceinline__ float2 rcp_or0(float2 x2) { return make_float2(rcp_or0(x2.x), rcp_or0(x2.y)); }
+
+template <bool kShared, class V>
+__device__ __forceinline__ void face_edge(V qx, V qy, V qz, const float4 A, const float4 B, const float4 C,
+                                          V a0, V a1, V& zr, V& zi, V& S0) {
+  const float nx = C.y, ny = C.z, nz = C.w;
+  const V Xx = vfma(vs<V>(ny), qz, vmul(vs<V>(-nz), qy));
+  const V Xy = vfma(vs<V>(nz), qx, vmul(vs<V>(-nx), qz));
+  const V Xz = vfma(vs<V>(nx), qy, vmul(vs<V>(-ny), qx));
+  const V x2 = vfma(Xx, Xx, vfma(Xy, Xy, vmul(Xz, Xz)));
+  const V b0 = vfma(vs<V>(A.w), Xx, vfma(vs<V>(B.x), Xy, vmul(vs<V>(B.y), Xz)));
+  const V b1 = vfma(vs<V>(B.z), Xx, vfma(vs<V>(B.w), Xy, vmul(vs<V>(C.x), Xz)));
+  const V b2 = vneg(vadd(b0, b1));
+  const V w[3] = {vadd(b1, vneg(b0)), vadd(b2, vneg(b1)), vadd(b0, vneg(b2))};
+  const V h0 = vmul(vs<V>(0.5f), a0), h1 = vmul(vs<V>(0.5f), a1);
+  const V u[3] = {vadd(h1, vneg(h0)), vfma(vs<V>(-2.0f), h1, vneg(h0)), vfma(vs<V>(2.0f), h0, h1)};   // (a_{l+1} - a_l)/2
+  // exp(i psi_l), psi_l = -a_{l+2}/2: psi_1 = -h0 and psi_2 = -h1 on the SFU,
+  // psi_0 = h0 + h1 as the conjugate of their product.
+  V sp[3], cp[3];
+  sincos_v(vneg(h0), sp[1], cp[1]);
+  sincos_v(vneg(h1), sp[2], cp[2]);
+  cp[0] = vfma(cp[1], cp[2], vneg(vmul(sp[1], sp[2])));
+  sp[0] = vneg(vfma(sp[1], cp[2], vmul(cp[1], sp[2])));
+  V u2[3], S[3];
+#pragma unroll
+  for (int l = kShared ? 1 : 0; l < 3; ++l) {
+    u2[l] = vmul(u[l], u[l]);
+    S[l] = sinc_poly_v(u2[l]);
+  }
+  // rare: an edge with |Q.d_l| > 2 pi somewhere in the warp (face_edge runs warp-converged)
+  constexpr int kE = sizeof(V) / sizeof(float);
+  bool big = false;
+#pragma unroll
+  for (int l = kShared ? 1 : 0; l < 3; ++l)
+#pragma unroll
+    for (int e = 0; e < kE; ++e) big = big || (el(&u2[l], e) > kPi2);
+  if (__any_sync(0xffffffffu, big)) {
+#pragma unroll
+    for (int l = kShared ? 1 : 0; l < 3; ++l)
+#pragma unroll
+      for (int e = 0; e < kE; ++e)
+        if (el(&u2[l], e) > kPi2) el(&S[l], e) = sinc_large(el(&u[l], e));
+  }
+  if (kShared) S[0] = S0;
+  else S0 = S[0];
+  V sr = vs<V>(0.f), si = vs<V>(0.f);
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const V ws = vmul(w[l], S[l]);
+    sr = vfma(ws, cp[l], sr);
+    si = vfma(ws, sp[l], si);
+  }
+  const V inv = rcp_or0(x2);
+  zr = vmul(sr, inv);
+  zi = vmul(si, inv);
+}
+
+// |Q|^2 I_m = -s exp(i mu) Z, added into the tile sums (tre, tim).
 
 template <class V>
 __device__ __forceinline__ void face_finish(V mu, V s, V zr, V zi, V& tre, V& tim) {
@@ -390,12 +403,6 @@ struct Acc64 {
   }
   __device__ __forceinline__ double2 get(int r) const { return make_double2(re[r], im[r]); }
 };
-
-// Element r of a thread's R per-Q values, stored as R floats or, for even R, as R/2 float2 pairs.
-__device__ __forceinline__ float& el(float* a, int r) { return a[r]; }
-__device__ __forceinline__ float& el(float2* a, int r) { return (r & 1) ? a[r >> 1].y : a[r >> 1].x; }
-__device__ __forceinline__ float el(const float* a, int r) { return a[r]; }
-__device__ __forceinline__ float el(const float2* a, int r) { return (r & 1) ? a[r >> 1].y : a[r >> 1].x; }
 
 // Per-Q values of a thread: R floats, or R/2 float2 pairs when R is even, so that the per-pair
 // arithmetic runs as paired FP32 instructions (two Q points per issue slot).
@@ -533,11 +540,11 @@ struct FaceQ {
   }
   // the edge sum (per Q point), with the few Q points below tau_lo^2/4 redone by the short series
   template <bool kShared>
-  __device__ __forceinline__ void edge(const Thr& th, const float (&q)[R][3], const float4 A, const float4 B,
-                                       const float4 C, V (&zr)[N], V (&zi)[N], float (&S0)[R]) const {
+  __device__ __forceinline__ void edge(const Thr& th, const V (&qv)[N][3], const float4 A, const float4 B,
+                                       const float4 C, V (&zr)[N], V (&zi)[N], V (&S0)[N]) const {
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-      face_edge<kShared>(q[r][0], q[r][1], q[r][2], A, B, C, el(a0, r), el(a1, r), el(zr, r), el(zi, r), S0[r]);
+    for (int j = 0; j < N; ++j)
+      face_edge<kShared>(qv[j][0], qv[j][1], qv[j][2], A, B, C, a0[j], a1[j], zr[j], zi[j], S0[j]);
     if (pmin < th.lo) {
 #pragma unroll
       for (int r = 0; r < R; ++r)
@@ -574,7 +581,7 @@ struct Pol3F32T {
     for (int j = 0; j < N; ++j) { tre[j] = vs<V>(0.f); tim[j] = vs<V>(0.f); }
     // S0 carries the first edge's sinc from the first face of a pair to the second; `held` says
     // that it does (warp-uniform: it follows the warp-uniform branch decisions)
-    float S0[R];
+    V S0[N];
     bool held = false;
 #pragma unroll 1
     for (int i = 0; i < cnt; ++i) {
@@ -589,10 +596,10 @@ struct Pol3F32T {
       } else if (kPairs && held && first + i < th.pair_end) {
         // the second face of a pair whose first face took the edge sum in this warp: the shared
         // edge's sinc comes from it
-        f.template edge<true>(th, q, A, B, C, zr, zi, S0);
+        f.template edge<true>(th, qv, A, B, C, zr, zi, S0);
         held = false;
       } else {
-        f.template edge<false>(th, q, A, B, C, zr, zi, S0);
+        f.template edge<false>(th, qv, A, B, C, zr, zi, S0);
         held = kPairs && ((first + i) & 1) == 0 && first + i < th.pair_end;   // the first face of a pair
       }
       f.finish(zr, zi, tre, tim);

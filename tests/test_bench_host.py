@@ -166,22 +166,49 @@ def _bwd_body(start, stop=None, struct=False):
 
 
 def _ops_no_literal_products(body):
-    """As _arith_ops, but a product or sum of two numeric literals (folded by the compiler) is not
-    counted."""
+    """FP32-pipe operations a device-code body executes: each fmaf and each call of the packed
+    helpers vfma / vmul / vadd, and each binary * + - whose operands are not both numeric literals
+    (those products are folded by the compiler; a chain a * b * c counts two); the body of each
+    `for (int l = 0; l < 3; ++l)` loop counts three times (the loops are unrolled)."""
     import re
-    num = r"-?\d+\.?\d*(?:e[-+]?\d+)?f?"
-    n = body.count("fmaf(")
-    for m in re.finditer(r"([\w\.\)\]]+) ([*+-]) (-?[\w\.\(]+)", body):
-        if not (re.fullmatch(num, m.group(1)) and re.fullmatch(num, m.group(3))):
-            n += 1
+    lit = r"(?<![\w.])\d+\.?\d*(?:e[-+]?\d+)?f?(?![\w.])"
+
+    def flat(text):
+        n = sum(text.count(f + "(") for f in ("fmaf", "vfma", "vmul", "vadd"))
+        b = re.sub(lit, "LIT", text)
+        for m in re.finditer(r"(?<=[\w\.\)\]]) ([*+-]) (?=-?[\w\.\(])", b):
+            left = re.search(r"([\w\.]+|\))$", b[:m.start()])
+            right = re.match(r"-?([\w\.]+|\()", b[m.end():])
+            if not (left and right and left.group(1) == "LIT" and right.group(1) == "LIT"):
+                n += 1
+        return n
+
+    n = flat(body)
+    head = "for (int l = 0; l < 3; ++l)"
+    k = body.find(head)
+    while k >= 0:
+        a = k + len(head)
+        rest = body[a:].lstrip()
+        if rest.startswith("{"):
+            depth, e = 0, a + body[a:].index("{")
+            for e in range(e, len(body)):
+                depth += {"{": 1, "}": -1}.get(body[e], 0)
+                if depth == 0:
+                    break
+            loop = body[a:e + 1]
+        else:
+            loop = body[a:body.index(";", a) + 1]
+        n += 2 * flat(loop)
+        k = body.find(head, a)
     return n
 
 
 def test_adjoint_ops_table_matches_the_source():
-    """bench.OPS_ADJ / OPS_QADJ: each branch part is the arithmetic written in that branch of
-    face_adj_t plus its adjoint; the edge part adds three sinc_d, and the record or Q updates of
-    the X adjoint; the common part adds face_common, the 10 branch-selection operations, the
-    sincos scaling, the code after the branches and the 12 record or Q updates."""
+    """bench.OPS_ADJ / OPS_QADJ: each branch part is the arithmetic that branch of face_adj_t and
+    its adjoint execute; the edge part adds three sinc_d on their polynomial path (with the range
+    test; the SFU form beyond |u| > pi is the rare branch) and the record or Q updates of the X
+    adjoint; the common part adds face_common, the 10 branch-selection operations, the sincos
+    scaling, the code after the branches and the 12 record or Q updates."""
     c = _ops_no_literal_products
     fwd = {"short": c(_bwd_body("if (shorts) {", "} else if (k9s) {")),
            "k9": c(_bwd_body("} else if (k9s) {", "} else if (longs) {")),
@@ -191,10 +218,12 @@ def test_adjoint_ops_table_matches_the_source():
     edge_fwd = c(_bwd_body("} else {\n    const float nx", "const float Wr"))
     edge_adj = c(_bwd_body("} else {\n    const float Sr", "out.common("))
     post = c(_bwd_body("const float Wr", "float a0b, a1b;"))
-    sinc_d = c(_bwd_body("void sinc_d("))
+    sinc_d = c(_bwd_body("void sinc_d(", "constexpr int kE")) + 1   # polynomial path + range test
     rec_edge = c(_bwd_body("void edge(float b0b", "__device__ __forceinline__ void common"))
     q_edge = c(_bwd_body("void edge(float, float", "__device__ __forceinline__ void common"))
     assert (rec_edge, q_edge) == (12, 6)
+    # hand counts: the short series' 17, the edge sum's forward 38 and adjoint 62, sinc_d's 14 + 1
+    assert (fwd["short"], edge_fwd, edge_adj, sinc_d) == (17, 38, 62, 15)
     assert _arith_ops(_fn_body("void face_common(")) == 15
     for key in ("short", "k9", "long", "xlong"):
         assert bench.OPS_ADJ[key]["fp32"] == fwd[key] + series_adj, key
@@ -207,6 +236,19 @@ def test_adjoint_ops_table_matches_the_source():
     assert bench.OPS_ADJ["common"]["fp32"] == 15 + 10 + 1 + (post - 2) + 12
     assert bench.OPS_QADJ["common"]["fp32"] == 15 + 10 + 1 + post + 2 + 12
     assert bench.OPS_ADJ["edge"]["sfu"] == 5 and bench.OPS_ADJ["common"]["sfu"] == 2
+
+
+def test_2d_adjoint_ops_match_the_source():
+    """bench.OPS2D_ADJ: seg_adj's arithmetic plus sinc_d's polynomial path, its range test and the
+    sincos argument scaling; the SFU sinc adds sinc_d's quotients and the turn reduction (rint,
+    subtract, scale) with the sincos argument scaling."""
+    c = _ops_no_literal_products
+    seg = c(_bwd_body("void seg_adj("))
+    poly = c(_bwd_body("void sinc_d(", "constexpr int kE"))
+    large = c(_bwd_body("constexpr int kE", "void seg_adj("))
+    assert (seg, poly, large) == (21, 14, 4)
+    assert bench.OPS2D_ADJ["poly_sinc"] == {"fp32": seg + poly + 1 + 1, "sfu": 2}
+    assert bench.OPS2D_ADJ["sfu_sinc"] == {"fp32": seg + poly + 1 + 1 + large + 3 + 1, "sfu": 2 + 3}
 
 
 def test_adjoint_branch_mix_partitions_the_lanes(mesh):
