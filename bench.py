@@ -7,7 +7,7 @@ grid over [-60, 60)^3 -- 2.75e12 (Q, triangle) pairs -- through the C ABI
 (pft3d_mesh, FP32 arithmetic with compensated sums and an FP64 finish).
 
 Prints one JSON line: G pair-evaluations/s, the main kernel's roofline
-fraction against the FP32/SFU issue limit, the end-to-end rate with host
+fraction against the FP32-lane / SFU limit, the end-to-end rate with host
 buffers, and the FP64 CPU oracle's rate on a bounded sample of the same
 workload.  ``--impl reference`` times that oracle alone (the reference arm).
 
@@ -277,27 +277,38 @@ def sfu_sinc_fraction(verts, poly_off, q, n=1 << 16, seed=0):
     return float(np.mean(u > np.pi))
 
 
-def roofline2d(pairs, t_s, f_sfu, n_sm, clk_mhz, table=None):
-    """Issue-slot / SFU bound of the 2D segment term (or, with table=OPS2D_ADJ, of its adjoint)
-    for a given SFU-sinc fraction."""
+def bound_cycles(ops, paired):
+    """SM cycles per pair at the limit, and the operations per pair that bind.  An SM has 128
+    FP32 lanes and 16 SFU lanes per clock and issues 128 thread-instructions per clock: one per
+    scalar FP32 or SFU operation, one per paired FP32 instruction (two operations, each on its
+    own lane).  Scalar code is issue-bound at (fp32 + sfu) / 128.  In the paired kernels more
+    than 2 sfu of the fp32 operations issue in pairs, so their issue count stays below fp32 and
+    the FP32 lanes bind at fp32 / 128.  Either way the SFU lanes bound at sfu / 16."""
+    lanes = ops["fp32"] if paired else ops["fp32"] + ops["sfu"]
+    return max(lanes / FP32_LANES, ops["sfu"] / SFU_LANES), lanes
+
+
+def roofline2d(pairs, t_s, f_sfu, n_sm, clk_mhz, table=None, paired=True):
+    """FP32-lane (paired) or issue-slot (scalar) / SFU bound of the 2D segment term (or, with
+    table=OPS2D_ADJ, of its adjoint) for a given SFU-sinc fraction."""
     table = OPS2D if table is None else table
     mix = {"poly_sinc": 1.0 - f_sfu, "sfu_sinc": f_sfu}
     ops = {k: sum(mix[b] * table[b][k] for b in table) for k in ("fp32", "sfu")}
-    issue = ops["fp32"] + ops["sfu"]
-    cyc = max(issue / FP32_LANES, ops["sfu"] / SFU_LANES)
+    cyc, lanes = bound_cycles(ops, paired)
     peak_pairs = n_sm * clk_mhz * 1e6 / cyc
-    return {"bound": "alu" if issue / FP32_LANES >= ops["sfu"] / SFU_LANES else "sfu",
+    return {"bound": "alu" if lanes / FP32_LANES >= ops["sfu"] / SFU_LANES else "sfu",
             "ops_per_pair": ops, "sfu_sinc_fraction": f_sfu, "peak_gpair_s": peak_pairs / 1e9,
-            "frac": pairs / t_s / peak_pairs}
+            "frac": pairs / t_s / peak_pairs,
+            "peak_basis": "128 FP32 lanes" if paired else "128 FP32/SFU issue slots"}
 
 
-def roofline(pairs, t_main_s, mix, n_sm, clk_mhz):
+def roofline(pairs, t_main_s, mix, n_sm, clk_mhz, paired=True):
+    """3D face term: (ops per pair, binding ops per pair, achieved and peak binding ops/s)."""
     ops = {k: sum(mix[b] * OPS[b][k] for b in OPS) for k in ("fp32", "sfu")}
-    issue = ops["fp32"] + ops["sfu"]
-    cyc = max(issue / FP32_LANES, ops["sfu"] / SFU_LANES)       # SM cycles per pair at the limit
-    peak_ops = n_sm * clk_mhz * 1e6 * issue / cyc                # issue-slot ops/s at the limit
-    achieved = issue * pairs / t_main_s
-    return ops, issue, achieved, peak_ops
+    cyc, lanes = bound_cycles(ops, paired)                       # SM cycles per pair at the limit
+    peak_ops = n_sm * clk_mhz * 1e6 * lanes / cyc                # binding ops/s at the limit
+    achieved = lanes * pairs / t_main_s
+    return ops, lanes, achieved, peak_ops
 
 
 def survey_count_frac(pairs, t_s, n_sm, clk_mhz):
@@ -445,7 +456,8 @@ def bench_batched(dev, warmup, steps):
     status = pft.pft_status(prep.ws)
     pk, pk_kind = peaks()
     rl = roofline2d(pairs, ms / 1e3, sfu_sinc_fraction(w.verts, w.poly_off, w.q),
-                    torch.cuda.get_device_properties(dev).multi_processor_count, float(pk.get("sm_max_mhz", 2070.0)))
+                    torch.cuda.get_device_properties(dev).multi_processor_count, float(pk.get("sm_max_mhz", 2070.0)),
+                    paired=tuned["q_per_thread"] % 2 == 0)
     rl["note"] = ("whole 4-launch call timed; the finish of the 16.8M outputs (2/|Q|^2, e^{iQ.c}) "
                   "is outside the per-pair count")
     # the plain FP64 GPU path on the same batch (one call), and the FP32 result's deviation from it
@@ -976,14 +988,15 @@ def main():
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         clk_max = float(pk.get("sm_max_mhz", 2070.0))
         mix = branch_mix(v, f, q, tau=args.tau or 6.0, r=args.q_per_thread, nt=args.block_threads)
-        ops, issue, achieved, peak_ops = roofline(pairs, ms_main / 1e3, mix, n_sm, clk_max)
+        paired = args.q_per_thread % 2 == 0        # even R: Q points in paired FP32 registers
+        ops, lanes, achieved, peak_ops = roofline(pairs, ms_main / 1e3, mix, n_sm, clk_max, paired)
         for variant in variants:
             if "face_pairs" in variant:
                 vmix = branch_mix(v, f_pairs, q, tau=variant["face_series_tau"], r=args.q_per_thread,
                                   nt=args.block_threads, n_pairs=n_pairs)
             else:
                 vmix = branch_mix(v, f, q, tau=variant["face_series_tau"], r=args.q_per_thread, nt=args.block_threads)
-            _, _, v_ach, v_peak = roofline(pairs, variant["main_kernel_ms"] / 1e3, vmix, n_sm, clk_max)
+            _, _, v_ach, v_peak = roofline(pairs, variant["main_kernel_ms"] / 1e3, vmix, n_sm, clk_max, paired)
             variant["branch_fractions"] = vmix
             variant["roofline_frac"] = v_ach / v_peak
         value = whole_job_rate(world, pairs, ms_step)
@@ -1003,8 +1016,11 @@ def main():
                          "traffic": traffic_from_profile(),
                          "kernel": f"k_fwd<Pol3F32,{args.q_per_thread},{args.block_threads}>",
                          "main_kernel_ms": ms_main,
-                         "peak_basis": f"{n_sm} SMs x 128 FP32/SFU issue slots x {clk_max:.0f} MHz "
-                                       f"({pk_kind} max SM clock)",
+                         "peak_basis": (f"{n_sm} SMs x 128 FP32 lanes x {clk_max:.0f} MHz ({pk_kind} max SM "
+                                        "clock); paired FP32 instructions keep issue below the FP32 lanes, so "
+                                        "achieved counts FP32-pipe operations" if paired else
+                                        f"{n_sm} SMs x 128 FP32/SFU issue slots x {clk_max:.0f} MHz "
+                                        f"({pk_kind} max SM clock)"),
                          "ops_per_pair": {"fp32": ops["fp32"], "sfu": ops["sfu"]},
                          "branch_fractions": mix},
             "clocks": clk,

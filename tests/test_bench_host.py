@@ -55,13 +55,20 @@ def test_branch_rule_on_hand_made_phases():
 
 def test_roofline_arithmetic():
     mix = {b: 1.0 / len(bench.OPS) for b in bench.OPS}
-    ops, issue, achieved, peak = bench.roofline(1e12, 1.0, mix, 152, 2070.0)
     want = {k: sum(bench.OPS[b][k] for b in bench.OPS) / len(bench.OPS) for k in ("fp32", "sfu")}
+    # scalar code: issue-bound, every FP32 and SFU operation takes one of 128 slots per SM clock
+    ops, issue, achieved, peak = bench.roofline(1e12, 1.0, mix, 152, 2070.0, paired=False)
     assert ops == pytest.approx(want)
     assert issue == pytest.approx(want["fp32"] + want["sfu"])
     assert achieved == pytest.approx(issue * 1e12)
-    # issue-bound for this mix: 152 SMs x 128 lanes x 2070 MHz
     assert peak == pytest.approx(152 * 128 * 2070e6)
+    # paired code: the 128 FP32 lanes bind, and only FP32-pipe operations count against them
+    ops, lanes, achieved_p, peak_p = bench.roofline(1e12, 1.0, mix, 152, 2070.0, paired=True)
+    assert lanes == pytest.approx(want["fp32"])
+    assert achieved_p == pytest.approx(want["fp32"] * 1e12)
+    assert peak_p == pytest.approx(152 * 128 * 2070e6)
+    # the pair rate at the limit: 128 / fp32 pairs per SM clock, against 128 / (fp32 + sfu)
+    assert achieved_p / peak_p < achieved / peak
 
 
 def test_sfu_sinc_fraction_on_a_square():
@@ -78,12 +85,17 @@ def test_sfu_sinc_fraction_on_a_square():
 
 
 def test_roofline2d_bounds():
-    r0 = bench.roofline2d(1e12, 1.0, 0.0, 152, 2070.0)
+    r0 = bench.roofline2d(1e12, 1.0, 0.0, 152, 2070.0, paired=False)
     assert r0["bound"] == "alu"
     assert r0["peak_gpair_s"] == pytest.approx(152 * 2070e6 * 128 / 20 / 1e9)
-    r1 = bench.roofline2d(1e12, 1.0, 1.0, 152, 2070.0)
+    r1 = bench.roofline2d(1e12, 1.0, 1.0, 152, 2070.0, paired=False)
     assert r1["bound"] == "sfu"                      # 4 SFU results / 16 lanes > 28 issue slots / 128
     assert r1["peak_gpair_s"] == pytest.approx(152 * 2070e6 * 16 / 4 / 1e9)
+    p0 = bench.roofline2d(1e12, 1.0, 0.0, 152, 2070.0, paired=True)
+    assert p0["bound"] == "alu"                      # 18 FP32 ops / 128 lanes > 2 SFU / 16
+    assert p0["peak_gpair_s"] == pytest.approx(152 * 2070e6 * 128 / 18 / 1e9)
+    p1 = bench.roofline2d(1e12, 1.0, 1.0, 152, 2070.0, paired=True)
+    assert p1["bound"] == "sfu" and p1["peak_gpair_s"] == pytest.approx(r1["peak_gpair_s"])
 
 
 def test_traffic_figure_only_for_the_profiled_sources(monkeypatch):
