@@ -220,6 +220,15 @@ def branch_mix(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0, n_pairs=0):
     return {k: out[k] for k in OPS}
 
 
+def kernel_order(pft, q, qd, r, nt, n_items):
+    """q in the order the main kernel visits it (the q_order option's default): the library orders
+    the Q points when there are at least two blocks' worth of them and 2^30 pairs or more, and
+    pft.q_order returns that order (slot -> Q index)."""
+    if q.shape[0] >= 2 * r * nt and float(q.shape[0]) * float(n_items) >= 2.0 ** 30:
+        return q[pft.q_order(qd, r, nt).cpu().numpy()]
+    return q
+
+
 def adjoint_branch_mix(v, f, q, tau=6.0, lanes="faces", n_warps=4096, seed=0):
     """The pair adjoint's branch rule on a seeded sample of warps, and the per-pair cost it implies.
 
@@ -554,7 +563,7 @@ def bench_batched3d(dev, warmup, steps):
     ms = float(np.mean(ts))
     pairs = float(f.shape[0]) * float(q.shape[0])
     pk, _ = peaks()
-    mix = branch_mix(v, f, q, tau=6.0, r=4, nt=128)
+    mix = branch_mix(v, f, kernel_order(pft, q, qd, 4, 128, f.shape[0]), tau=6.0, r=4, nt=128)
     _, _, ach, peak = roofline(pairs, ms / 1e3, mix, torch.cuda.get_device_properties(dev).multi_processor_count,
                                float(pk.get("sm_max_mhz", 2070.0)))
     status = int(pft.pft_status(prep.ws))
@@ -660,7 +669,7 @@ def bench_polymesh(dev, warmup, steps):
     ref = (f2[:, 0] + 1j * f2[:, 1]) * h * np.sinc(x / np.pi) * np.exp(1j * x)
     vol = abs(got[int(np.flatnonzero(np.all(q == 0, axis=1))[0])])
     pk, _ = peaks()
-    mix = branch_mix(v, halving_triangles(idx, off), q, tau=6.0, r=4, nt=128)
+    mix = branch_mix(v, halving_triangles(idx, off), kernel_order(pft, q, qd, 4, 128, n_tris), tau=6.0, r=4, nt=128)
     _, _, ach, peak = roofline(pairs, ms / 1e3, mix, torch.cuda.get_device_properties(dev).multi_processor_count,
                                float(pk.get("sm_max_mhz", 2070.0)))
     return {"value": pairs / (ms / 1e3) / 1e9, "unit": UNIT + " (Q, triangle)", "ms_per_call": ms,
@@ -987,15 +996,16 @@ def main():
         pk, pk_kind = peaks()
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         clk_max = float(pk.get("sm_max_mhz", 2070.0))
-        mix = branch_mix(v, f, q, tau=args.tau or 6.0, r=args.q_per_thread, nt=args.block_threads)
+        qk = kernel_order(pft, q, qd, args.q_per_thread, args.block_threads, f.shape[0])
+        mix = branch_mix(v, f, qk, tau=args.tau or 6.0, r=args.q_per_thread, nt=args.block_threads)
         paired = args.q_per_thread % 2 == 0        # even R: Q points in paired FP32 registers
         ops, lanes, achieved, peak_ops = roofline(pairs, ms_main / 1e3, mix, n_sm, clk_max, paired)
         for variant in variants:
             if "face_pairs" in variant:
-                vmix = branch_mix(v, f_pairs, q, tau=variant["face_series_tau"], r=args.q_per_thread,
+                vmix = branch_mix(v, f_pairs, qk, tau=variant["face_series_tau"], r=args.q_per_thread,
                                   nt=args.block_threads, n_pairs=n_pairs)
             else:
-                vmix = branch_mix(v, f, q, tau=variant["face_series_tau"], r=args.q_per_thread, nt=args.block_threads)
+                vmix = branch_mix(v, f, qk, tau=variant["face_series_tau"], r=args.q_per_thread, nt=args.block_threads)
             _, _, v_ach, v_peak = roofline(pairs, variant["main_kernel_ms"] / 1e3, vmix, n_sm, clk_max, paired)
             variant["branch_fractions"] = vmix
             variant["roofline_frac"] = v_ach / v_peak

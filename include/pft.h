@@ -59,6 +59,11 @@ typedef enum {
   PFT_FP64 = 1               /* plain FP64 throughout (comparison path)             */
 } pft_precision;
 
+typedef enum {
+  PFT_Q_TILED = 0,           /* the main kernel visits Q points in the library's order */
+  PFT_Q_AS_GIVEN = 1         /* ... in the caller's order                              */
+} pft_q_order_mode;
+
 /*
  * Options.  Zero-initialised means "defaults".  A NULL pointer is the same as
  * all defaults.
@@ -93,6 +98,20 @@ typedef enum {
  *                   share its first edge contributes nothing and sets
  *                   PFT_ERR_PAIRS).  0 = no pairs; 2 face_pairs <= n_faces.  Other
  *                   calls ignore it.
+ *  q_order          forward calls (pft2d_polygons, pft3d_mesh, pft3d_polymesh, the
+ *                   no-workspace form, and the batched calls on a shared Q set):
+ *                   PFT_Q_TILED (0, default) lets the library choose the order in
+ *                   which the main kernel visits the Q points.  It sorts them along
+ *                   a Z-order curve of their coordinates (quantised over their
+ *                   bounding box) and gives each group of 32 threads a run of nearby
+ *                   points, because the 3D series-or-edge-sum choice and the 2D SFU
+ *                   sinc are decided per group.  It does so only when there are at
+ *                   least two blocks' worth of Q points and about 1e9 pairs or more.
+ *                   PFT_Q_AS_GIVEN (1) keeps the caller's order.  Outputs are in the
+ *                   caller's order either way.  The two agree bitwise in 2D and to
+ *                   rounding in 3D (another grouping can switch a face between the
+ *                   series and the edge sum for some Q points).  Other values:
+ *                   PFT_ERR_INVALID_ARG.
  *  main_start_event, main_stop_event
  *                   cudaEvent_t handles or NULL.  When set, they are recorded on
  *                   `stream` immediately before and after the main pair kernel
@@ -110,7 +129,8 @@ typedef struct {
   void* main_start_event;
   void* main_stop_event;
   int32_t face_pairs;
-  int32_t reserved[3];
+  int32_t q_order;
+  int32_t reserved[2];
 } pft_options;
 
 /* Bytes of workspace the matching call needs for these sizes and options. */
@@ -151,7 +171,8 @@ int pft2d_polygons(const float* verts, int64_t n_verts, const int64_t* loop_off,
  *               points and out is [n_polys][n_q][2]; otherwise polygon i uses
  *               q[q_off[i] .. q_off[i+1]-1] and out is [n_q][2] in the same order
  *               (q_off: HOST copy for prepare, DEVICE copy for the call).
- *  opts         precision, q_per_thread, block_threads (k_splits, tile_items 0).
+ *  opts         precision, q_per_thread, block_threads, q_order (shared Q set only:
+ *               per-polygon Q lists keep their order) (k_splits, tile_items 0).
  * Workspace size from pft2d_batched_workspace_size (same host arguments).
  */
 typedef struct {
@@ -228,6 +249,26 @@ int pft3d_mesh(const float* verts, int64_t n_verts, const int32_t* faces, int64_
  * Synchronous host work; no GPU is touched.
  */
 int pft3d_pair_faces(const int32_t* faces_host, int64_t n_faces, int32_t* faces_out, int64_t* n_pairs);
+
+/*
+ * The Q order of the q_order option (PFT_Q_TILED) as a slot -> Q index map, for a
+ * caller that wants to see it or reuse it.  The main kernel with q_per_thread Q
+ * points per thread and block_threads threads per block visits Q point perm[s] in
+ * slot s, and the slots base + r*block_threads + 32*w + lane (r < q_per_thread,
+ * lane < 32) of a block form group w of 32 threads.  The Q points are sorted along
+ * a Z-order curve of their FP32 coordinates, quantised over their bounding box
+ * (10 bits per axis in 3D, 16 in 2D; NaN coordinates count as the lowest level),
+ * by a stable radix sort, and each run of 32 q_per_thread sorted points fills one
+ * group's slots; the last, partial block keeps the sorted order.
+ *  q          [n_q][dim] float64, device.      perm  [n_q] int32, device, written.
+ *  dim        2 or 3; q_per_thread 1, 2, 4 or 8; block_threads 128 or 256.
+ * Workspace: pft_q_order_workspace_size(n_q) bytes, 256-byte aligned.
+ * Returns PFT_OK, PFT_ERR_INVALID_ARG, PFT_ERR_UNSUPPORTED (n_q > INT32_MAX or
+ * another shape), PFT_ERR_WORKSPACE, PFT_ERR_CUDA.  Asynchronous on `stream`.
+ */
+size_t pft_q_order_workspace_size(int64_t n_q);
+int pft_q_order(const double* q, int64_t n_q, int dim, int q_per_thread, int block_threads, int32_t* perm, void* ws,
+                size_t ws_bytes, void* stream);
 
 /*
  * 3D: FT_V(Q) of a closed surface of planar polygon faces of any size (Sec. 3:

@@ -22,7 +22,7 @@ __all__ = [
     "pft2d_polygons", "pft2d_batched_prepare", "pft2d_polygons_batched", "BatchedPrepared", "pft3d_mesh",
     "pft3d_polymesh", "pft3d_polymesh_backward", "ft3d_poly", "pft2d_polygons_batched_backward", "pft3d_batched_prepare", "pft3d_meshes_batched",
     "pft2d_polygons_backward",
-    "pft3d_mesh_backward", "pft3d_mesh_qgrad", "pft2d_polygons_qgrad", "pair_faces",
+    "pft3d_mesh_backward", "pft3d_mesh_qgrad", "pft2d_polygons_qgrad", "pair_faces", "q_order",
     "pft3d_meshes_batched_backward", "ft3d_batched", "pft3d_mesh_noalloc", "pft_status", "ft2d", "ft2d_batched", "ft3d", "make_options", "Options",
     "PFTError",
     "launch_count", "version",
@@ -37,7 +37,8 @@ def _torch():
 def make_options(options=None) -> Options:
     """Build a pft_options struct from None, an Options, or a dict of its fields.
 
-    ``precision`` may be "fp32" (FP32 with compensated sums, the default) or "fp64".
+    ``precision`` may be "fp32" (FP32 with compensated sums, the default) or "fp64"; ``q_order``
+    "tiled" (the default: the library orders the Q points for the main kernel) or "as_given".
     """
     if isinstance(options, Options):
         return options
@@ -45,6 +46,8 @@ def make_options(options=None) -> Options:
     for k, v in (options or {}).items():
         if k == "precision":
             v = {"fp32": PFT_FP32_COMPENSATED, "fp64": PFT_FP64}.get(v, v)
+        if k == "q_order":
+            v = {"tiled": 0, "as_given": 1}.get(v, v)
         if not hasattr(o, k):
             raise KeyError(f"unknown pft option {k!r}")
         setattr(o, k, v)
@@ -269,6 +272,23 @@ def pair_faces(faces):
     check(load().pft3d_pair_faces(f.ctypes.data, f.shape[0], out.ctypes.data, ctypes.byref(n)),
           "pft3d_pair_faces")
     return out, int(n.value)
+
+
+def q_order(q, q_per_thread=4, block_threads=128, *, stream=None):
+    """The slot -> Q index map (int32 [n_q], on q's device) by which the main kernel visits the Q
+    points under the default ``q_order`` option, for q [n_q, 2] or [n_q, 3] float64 on a GPU and the
+    given launch shape: slot s holds Q point perm[s]."""
+    torch = _torch()
+    if not isinstance(q, torch.Tensor) or not q.is_cuda or q.dim() != 2 or q.shape[1] not in (2, 3):
+        raise ValueError("q must be a CUDA tensor [n_q, 2] or [n_q, 3]")
+    qq = _dev(q, torch.float64, "q")
+    lib = load()
+    nq = qq.shape[0]
+    perm = torch.empty(nq, dtype=torch.int32, device=qq.device)
+    ws = _ws(lib.pft_q_order_workspace_size(nq), qq.device, None)
+    check(lib.pft_q_order(qq.data_ptr(), nq, qq.shape[1], q_per_thread, block_threads, perm.data_ptr(),
+                          ws.data_ptr(), ws.numel(), _stream(stream, qq.device)), "pft_q_order")
+    return perm
 
 
 def pft3d_polymesh(verts, face_idx, face_off, q, *, options=None, out=None, ws=None, stream=None,

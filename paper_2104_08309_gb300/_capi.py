@@ -34,13 +34,16 @@ class Options(ctypes.Structure):
         ("main_start_event", ctypes.c_void_p),
         ("main_stop_event", ctypes.c_void_p),
         ("face_pairs", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("q_order", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 
 # name -> (restype, argtypes); exactly the entry points include/pft.h declares.
 SIGNATURES = {
     "pft2d_workspace_size": (c_size, [c_i64, c_i64, c_i64, c_vp]),
+    "pft_q_order_workspace_size": (c_size, [c_i64]),
+    "pft_q_order": (ctypes.c_int, [c_vp, c_i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_vp, c_vp, c_size, c_vp]),
     "pft2d_batched_workspace_size": (c_size, [c_i64, c_vp, c_i64, c_vp, c_i64, c_vp]),
     "pft2d_batched_prepare": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_size, c_vp, c_vp, c_vp]),
     "pft_batched_last_launch_count": (ctypes.c_int, []),

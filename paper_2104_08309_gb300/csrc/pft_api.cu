@@ -22,6 +22,7 @@ struct Opts {
   float tau;
   cudaEvent_t ev_start, ev_stop;
   int64_t face_pairs;
+  int q_order;
 };
 
 int resolve(const pft_options* o, int dim, Opts& out) {
@@ -46,6 +47,8 @@ int resolve(const pft_options* o, int dim, Opts& out) {
   if (p.face_pairs < 0) return PFT_ERR_INVALID_ARG;
   if (p.face_pairs > 0 && dim == 3 && !out.fp64 && out.r > 4) return PFT_ERR_UNSUPPORTED;
   out.face_pairs = dim == 3 ? p.face_pairs : 0;
+  if (p.q_order != PFT_Q_TILED && p.q_order != PFT_Q_AS_GIVEN) return PFT_ERR_INVALID_ARG;
+  out.q_order = p.q_order;
   return PFT_OK;
 }
 
@@ -90,8 +93,9 @@ FwdLaunch plan_fwd(int dim, const Opts& o, int64_t n_items, int64_t n_q) {
 }
 
 struct FwdLayout {
-  size_t mparts, items, partial, small, total;
+  size_t mparts, items, partial, small, qperm, qscratch, total;
   int nblk;
+  bool tiled;   // the main kernel visits the Q points in the library's order (q_order option)
   FwdLaunch L;
 };
 
@@ -105,15 +109,33 @@ FwdLayout layout_fwd(int dim, const Opts& o, int64_t n_items, int64_t n_prep, in
   y.items = off;   off = align_up(off + item_bytes * (size_t)std::max<int64_t>(n_items, 1));
   y.partial = off; off = align_up(off + sizeof(double2) * (size_t)y.L.k_splits * (size_t)std::max<int64_t>(n_q, 1));
   y.small = off;   off = align_up(off + sizeof(int32_t) * (size_t)std::max<int64_t>(n_q, 1));
+  y.tiled = o.q_order == PFT_Q_TILED && qorder_wanted(n_q, n_items, o.r, o.nt);
+  if (y.tiled) {
+    y.qperm = off;    off = align_up(off + sizeof(int32_t) * (size_t)n_q);
+    y.qscratch = off; off = align_up(off + qorder_layout(n_q).total);
+  }
   y.total = off;
   return y;
 }
+
 
 template <typename T>
 T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(ws) + off); }
 
 bool bad_ws(const void* ws, size_t bytes, size_t need) {
   return ws == nullptr || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0 || bytes < need;
+}
+
+// The slot -> Q map of the main kernel (NULL: the caller's order), computed on the stream.
+int fwd_qorder(int dim, const FwdLayout& y, const double* q, int64_t n_q, void* ws, cudaStream_t st,
+               const int32_t*& qperm) {
+  qperm = nullptr;
+  if (!y.tiled) return PFT_OK;
+  int32_t* perm = at<int32_t>(ws, y.qperm);
+  if (launch_qorder(dim, q, n_q, y.L.r, y.L.nt, at<void>(ws, y.qscratch), perm, st, &g_last_launches) != cudaSuccess)
+    return PFT_ERR_CUDA;
+  qperm = perm;
+  return PFT_OK;
 }
 
 // Records an optional caller event on the stream (timing of the main kernel alone).
@@ -166,9 +188,11 @@ int pft2d_polygons(const float* verts, int64_t n_verts, const int64_t* loop_off,
   double* mp = at<double>(ws, y.mparts);
   PFT_LAUNCH(launch_bbox(verts, n_verts, 2, h, st));
   PFT_LAUNCH(launch_prep2d(verts, n_verts, loop_off, n_loops, h, at<void>(ws, y.items), o.fp64, mp, y.nblk, st));
+  const int32_t* qperm;
+  if (int e = fwd_qorder(2, y, q, n_q, ws, st, qperm)) return e;
   if (mark(o.ev_start, st) != cudaSuccess) return PFT_ERR_CUDA;
   PFT_LAUNCH(launch_fwd(2, o.fp64, y.L, at<void>(ws, y.items), n_verts, q, n_q, o.tau, at<double2>(ws, y.partial),
-                        &h->status, st));
+                        &h->status, st, 0, qperm));
   if (mark(o.ev_stop, st) != cudaSuccess) return PFT_ERR_CUDA;
   PFT_LAUNCH(launch_finalize(2, q, n_q, at<double2>(ws, y.partial), y.L.k_splits, o.fp64, h, mp, y.nblk,
                              at<int32_t>(ws, y.small), out, st));
@@ -200,9 +224,11 @@ int pft3d_mesh(const float* verts, int64_t n_verts, const int32_t* faces, int64_
   PFT_LAUNCH(launch_bbox(verts, n_verts, 3, h, st));
   PFT_LAUNCH(launch_prep3d(verts, n_verts, faces, n_faces, h, at<void>(ws, y.items), o.fp64, mp, y.nblk, st,
                            2 * o.face_pairs));
+  const int32_t* qperm;
+  if (int e = fwd_qorder(3, y, q, n_q, ws, st, qperm)) return e;
   if (mark(o.ev_start, st) != cudaSuccess) return PFT_ERR_CUDA;
   PFT_LAUNCH(launch_fwd(3, o.fp64, y.L, at<void>(ws, y.items), n_faces, q, n_q, o.tau, at<double2>(ws, y.partial),
-                        &h->status, st, 2 * o.face_pairs));
+                        &h->status, st, 2 * o.face_pairs, qperm));
   if (mark(o.ev_stop, st) != cudaSuccess) return PFT_ERR_CUDA;
   PFT_LAUNCH(launch_finalize(3, q, n_q, at<double2>(ws, y.partial), y.L.k_splits, o.fp64, h, mp, y.nblk,
                              at<int32_t>(ws, y.small), out, st));
@@ -248,9 +274,11 @@ int pft3d_polymesh(const float* verts, int64_t n_verts, const int32_t* face_idx,
   PFT_LAUNCH(launch_fan3d(face_idx, n_idx, face_off, n_faces, tris, n_tris, h, st));
   PFT_LAUNCH(launch_bbox(verts, n_verts, 3, h, st));
   PFT_LAUNCH(launch_prep3d(verts, n_verts, tris, n_tris, h, at<void>(ws, y.items), o.fp64, mp, y.nblk, st));
+  const int32_t* qperm;
+  if (int e = fwd_qorder(3, y, q, n_q, ws, st, qperm)) return e;
   if (mark(o.ev_start, st) != cudaSuccess) return PFT_ERR_CUDA;
   PFT_LAUNCH(launch_fwd(3, o.fp64, y.L, at<void>(ws, y.items), n_tris, q, n_q, o.tau, at<double2>(ws, y.partial),
-                        &h->status, st));
+                        &h->status, st, 0, qperm));
   if (mark(o.ev_stop, st) != cudaSuccess) return PFT_ERR_CUDA;
   PFT_LAUNCH(launch_finalize(3, q, n_q, at<double2>(ws, y.partial), y.L.k_splits, o.fp64, h, mp, y.nblk,
                              at<int32_t>(ws, y.small), out, st));
@@ -287,6 +315,27 @@ const char* pft_status_string(int code) {
     case PFT_ERR_PAIRS: return "faces given as pairs do not share their first edge";
     default: return "unknown status code";
   }
+}
+
+size_t pft_q_order_workspace_size(int64_t n_q) {
+  if (n_q < 0 || n_q > INT32_MAX) return 0;
+  return qorder_layout(n_q).total;
+}
+
+int pft_q_order(const double* q, int64_t n_q, int dim, int q_per_thread, int block_threads, int32_t* perm, void* ws,
+                size_t ws_bytes, void* stream) {
+  g_last_launches = 0;
+  if (n_q < 0 || (dim != 2 && dim != 3)) return PFT_ERR_INVALID_ARG;
+  if (n_q > INT32_MAX) return PFT_ERR_UNSUPPORTED;
+  const int r = q_per_thread, nt = block_threads;
+  if (!(r == 1 || r == 2 || r == 4 || r == 8) || (nt != 128 && nt != 256)) return PFT_ERR_UNSUPPORTED;
+  if (n_q == 0) return PFT_OK;
+  if (q == nullptr || perm == nullptr) return PFT_ERR_INVALID_ARG;
+  if (bad_ws(ws, ws_bytes, qorder_layout(n_q).total)) return PFT_ERR_WORKSPACE;
+  return launch_qorder(dim, q, n_q, r, nt, ws, perm, static_cast<cudaStream_t>(stream), &g_last_launches) ==
+                 cudaSuccess
+             ? PFT_OK
+             : PFT_ERR_CUDA;
 }
 
 int pft3d_pair_faces(const int32_t* f, int64_t nf, int32_t* out, int64_t* n_pairs) {

@@ -38,7 +38,8 @@ struct BPlanHeader {
   int64_t n_polys, n_verts, n_q, n_items, n_cta, n_mc, part_rows, n_out;   // n_verts: segments or faces
   int32_t r, nt, shared_q, fp64, dim;
   float tau;
-  uint8_t pad[256 - 8 * 9 - 4 * 6];
+  int32_t q_tiled, pad1;   // q_tiled: the pair kernel visits the shared Q set in the library's order
+  uint8_t pad[256 - 8 * 9 - 4 * 8];
 };
 static_assert(sizeof(BPlanHeader) == 256, "plan header is 256 bytes");
 
@@ -56,13 +57,13 @@ struct PolyInfo {       // written by k_bprep / k_bprep3: centre, area or volume
 };
 
 struct BLayout {
-  size_t plan_hdr, cta_off, items, pplan, mc, info, segs, partial, small, total;
+  size_t plan_hdr, cta_off, items, pplan, mc, info, segs, partial, small, qperm, qscratch, total;
 };
 
 inline size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
 BLayout layout(int dim, int64_t n_polys, int64_t n_verts, int64_t n_items, int64_t n_cta, int64_t n_mc,
-               int64_t part_rows, int64_t n_out, bool fp64) {
+               int64_t part_rows, int64_t n_out, bool fp64, int64_t n_q, bool q_tiled) {
   const size_t rec = dim == 2 ? (fp64 ? sizeof(Seg64) : sizeof(Seg32)) : (fp64 ? sizeof(Face64) : sizeof(Face32));
   BLayout y{};
   size_t o = al(sizeof(WsHeader));
@@ -75,6 +76,10 @@ BLayout layout(int dim, int64_t n_polys, int64_t n_verts, int64_t n_items, int64
   y.segs = o;     o = al(o + rec * (size_t)std::max<int64_t>(n_verts, 1));
   y.partial = o;  o = al(o + sizeof(double2) * (size_t)std::max<int64_t>(part_rows, 1));
   y.small = o;    o = al(o + sizeof(uint32_t) * (size_t)std::max<int64_t>(n_out, 1));
+  if (q_tiled) {
+    y.qperm = o;    o = al(o + sizeof(int32_t) * (size_t)n_q);
+    y.qscratch = o; o = al(o + qorder_layout(n_q).total);
+  }
   y.total = o;
   return y;
 }
@@ -95,7 +100,7 @@ struct HostPlan {
 
 bool batched_config(int dim, bool fp64, int r, int nt);
 
-int resolve_batched(int dim, const pft_options* o, bool& fp64, int& r, int& nt, float& tau) {
+int resolve_batched(int dim, const pft_options* o, bool& fp64, int& r, int& nt, float& tau, int& q_order) {
   pft_options z;
   std::memset(&z, 0, sizeof(z));
   const pft_options& p = o ? *o : z;
@@ -107,6 +112,8 @@ int resolve_batched(int dim, const pft_options* o, bool& fp64, int& r, int& nt, 
   tau = p.face_series_tau == 0.f ? 6.0f : p.face_series_tau;
   if (!(tau > 0.f && tau <= 6.0f)) return PFT_ERR_INVALID_ARG;
   if (fp64) tau = std::min(tau, 3.0f);   // the FP64 series is kept for P < 9/4 (as in the single-shape path)
+  if (p.q_order != PFT_Q_TILED && p.q_order != PFT_Q_AS_GIVEN) return PFT_ERR_INVALID_ARG;
+  q_order = p.q_order;
   return PFT_OK;
 }
 
@@ -115,9 +122,9 @@ int batched_blocks_per_sm(int dim, bool fp64, int r, int nt);
 int build_plan(int dim, const int64_t* poly_off, int64_t n_polys, const int64_t* q_off, int64_t n_q,
                const pft_options* opts, HostPlan& P) {
   bool fp64;
-  int r, nt;
+  int r, nt, q_order;
   float tau;
-  if (int e = resolve_batched(dim, opts, fp64, r, nt, tau)) return e;
+  if (int e = resolve_batched(dim, opts, fp64, r, nt, tau, q_order)) return e;
   if (n_polys < 0 || n_q < 0 || (n_polys > 0 && poly_off == nullptr)) return PFT_ERR_INVALID_ARG;
   if (n_polys > 0 && poly_off[0] != 0) return PFT_ERR_OFFSETS;
   for (int64_t i = 0; i < n_polys; ++i)
@@ -200,6 +207,8 @@ int build_plan(int dim, const int64_t* poly_off, int64_t n_polys, const int64_t*
   P.h.r = r;
   P.h.nt = nt;
   P.h.shared_q = q_off ? 0 : 1;
+  // per-shape Q lists keep their order; a shared Q set is ordered once for every shape
+  P.h.q_tiled = (!q_off && q_order == PFT_Q_TILED && qorder_wanted(n_q, P.h.n_verts, r, nt)) ? 1 : 0;
   P.h.fp64 = fp64 ? 1 : 0;
   P.h.dim = dim;
   P.h.tau = tau;
@@ -207,7 +216,8 @@ int build_plan(int dim, const int64_t* poly_off, int64_t n_polys, const int64_t*
 }
 
 BLayout layout_of(const BPlanHeader& h) {
-  return layout(h.dim, h.n_polys, h.n_verts, h.n_items, h.n_cta, h.n_mc, h.part_rows, h.n_out, h.fp64 != 0);
+  return layout(h.dim, h.n_polys, h.n_verts, h.n_items, h.n_cta, h.n_mc, h.part_rows, h.n_out, h.fp64 != 0, h.n_q,
+                h.q_tiled != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -436,7 +446,7 @@ __global__ void __launch_bounds__(NT, kBatchedMinBlocks<Pol, R, NT>) k_batched(
     const BPlanHeader* __restrict__ ph, const int32_t* __restrict__ cta_off, const BItem* __restrict__ items,
     const PolyPlan* __restrict__ pplan, const PolyInfo* __restrict__ info, const typename Pol::Item* __restrict__ segs,
     const double* __restrict__ q, double2* __restrict__ partial, double* __restrict__ out, uint32_t* small,
-    WsHeader* h, Thr th) {
+    WsHeader* h, Thr th, const int32_t* __restrict__ qperm) {
   using Item = typename Pol::Item;
   using QT = typename Pol::QT;
   constexpr int TILE = Pol::kTile;
@@ -513,14 +523,16 @@ __global__ void __launch_bounds__(NT, kBatchedMinBlocks<Pol, R, NT>) k_batched(
     seg_range(k, sb, cnt);
     const int64_t q0 = pp.q_begin + (int64_t)it.qtile * (NT * R);
     const int64_t qend = pp.q_begin + pp.n_q;
+    // slot iq holds Q row qperm[iq] (shared Q set, q_begin = 0), else row iq itself
     QT qr[R][3];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int64_t iq = q0 + (int64_t)r * NT + threadIdx.x;
       qr[r][0] = qr[r][1] = qr[r][2] = (QT)0;
       if (iq < qend) {
+        const int64_t src = qperm ? (int64_t)qperm[iq] : iq;
 #pragma unroll
-        for (int d = 0; d < D; ++d) qr[r][d] = (QT)q[D * iq + d];
+        for (int d = 0; d < D; ++d) qr[r][d] = (QT)q[D * src + d];
       }
     }
     typename Pol::template Acc<R> acc;
@@ -554,7 +566,7 @@ __global__ void __launch_bounds__(NT, kBatchedMinBlocks<Pol, R, NT>) k_batched(
       const int64_t iq = q0 + (int64_t)r * NT + threadIdx.x;
       if (iq >= qend) continue;
       const double2 f = acc.get(r);
-      const int64_t local = iq - pp.q_begin;
+      const int64_t local = (qperm ? (int64_t)qperm[iq] : iq) - pp.q_begin;
       if (pp.n_chunks > 1) {
         partial[pp.part_base + (int64_t)it.chunk * pp.n_q + local] = f;
       } else {
@@ -734,10 +746,11 @@ int occ_batched() {
 template <class Pol, int R, int NT>
 cudaError_t launch_batched_one(int grid, const BPlanHeader* ph, const int32_t* cta_off, const BItem* items,
                                const PolyPlan* pplan, const PolyInfo* info, const void* segs, const double* q,
-                               double2* partial, double* out, uint32_t* small, WsHeader* h, Thr th, cudaStream_t st) {
+                               double2* partial, double* out, uint32_t* small, WsHeader* h, Thr th, cudaStream_t st,
+                               const int32_t* qperm) {
   k_batched<Pol, R, NT><<<grid, NT, 0, st>>>(ph, cta_off, items, pplan, info,
                                              static_cast<const typename Pol::Item*>(segs), q, partial, out, small, h,
-                                             th);
+                                             th, qperm);
   return cudaGetLastError();
 }
 
@@ -769,11 +782,11 @@ int batched_blocks_per_sm(int dim, bool fp64, int r, int nt) {
 cudaError_t launch_batched(int dim, bool fp64, int r, int nt, int grid, const BPlanHeader* ph, const int32_t* cta_off,
                            const BItem* items, const PolyPlan* pplan, const PolyInfo* info, const void* segs,
                            const double* q, double2* partial, double* out, uint32_t* small, WsHeader* h, Thr th,
-                           cudaStream_t st) {
+                           cudaStream_t st, const int32_t* qperm) {
 #define X(P, RR, NN)                                                                                      \
   if (PFT_BATCHED_MATCH(P, RR, NN))                                                                      \
     return launch_batched_one<P, RR, NN>(grid, ph, cta_off, items, pplan, info, segs, q, partial, out, small, h, \
-                                         th, st);
+                                         th, st, qperm);
   PFT_BATCHED_CASES(X)
 #undef X
   return cudaErrorInvalidConfiguration;
@@ -787,6 +800,7 @@ struct PlanHandle {
   int64_t plan_hdr, cta_off, items, pplan, mc, info, segs, partial, small, total;
   int64_t dim;
   double tau;
+  int64_t qperm, qscratch;   // 0: the caller's Q order
 };
 static_assert(sizeof(PlanHandle) <= sizeof(pft_batched_plan), "plan handle fits the public struct");
 
@@ -833,6 +847,8 @@ int prepare_impl(int dim, const int64_t* off_host, int64_t n_shapes, const int64
   ph.partial = (int64_t)y.partial; ph.small = (int64_t)y.small; ph.total = (int64_t)y.total;
   ph.dim = dim;
   ph.tau = P.h.tau;
+  ph.qperm = P.h.q_tiled ? (int64_t)y.qperm : 0;
+  ph.qscratch = P.h.q_tiled ? (int64_t)y.qscratch : 0;
   std::memcpy(plan, &ph, sizeof(ph));
   return PFT_OK;
 }
@@ -865,9 +881,16 @@ int run_rest(const PlanHandle& p, void* ws, const double* q, double* out, WsHead
   PolyInfo* info = at<PolyInfo>(ws, (size_t)p.info);
   uint32_t* small = at<uint32_t>(ws, (size_t)p.small);
   double2* partial = at<double2>(ws, (size_t)p.partial);
+  int32_t* qperm = nullptr;
+  if (p.qperm != 0) {
+    qperm = at<int32_t>(ws, (size_t)p.qperm);
+    if (launch_qorder((int)p.dim, q, p.n_q, (int)p.r, (int)p.nt, at<void>(ws, (size_t)p.qscratch), qperm, st,
+                      &g_batched_launches) != cudaSuccess)
+      return PFT_ERR_CUDA;
+  }
   if (launch_batched((int)p.dim, p.fp64 != 0, (int)p.r, (int)p.nt, (int)p.grid, phd,
                      at<int32_t>(ws, (size_t)p.cta_off), at<BItem>(ws, (size_t)p.items), pplan, info,
-                     at<void>(ws, (size_t)p.segs), q, partial, out, small, h, plan_thr(p), st) != cudaSuccess)
+                     at<void>(ws, (size_t)p.segs), q, partial, out, small, h, plan_thr(p), st, qperm) != cudaSuccess)
     return PFT_ERR_CUDA;
   ++g_batched_launches;
   if (p.n_mc > 0) {

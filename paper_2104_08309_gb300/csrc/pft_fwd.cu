@@ -30,7 +30,8 @@ namespace {
 template <class Pol, int R, int NT>
 __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_fwd(const typename Pol::Item* __restrict__ items, int64_t n_items,
                                             int64_t per_split, const double* __restrict__ q, int64_t n_q,
-                                            Thr th, double2* __restrict__ partial, uint32_t* status) {
+                                            Thr th, double2* __restrict__ partial, uint32_t* status,
+                                            const int32_t* __restrict__ qperm) {
   using Item = typename Pol::Item;
   using QT = typename Pol::QT;
   constexpr int TILE = Pol::kTile;
@@ -46,6 +47,7 @@ __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_fwd(const typena
   const int ntiles = (int)((n + TILE - 1) / TILE);
   const Item* src = items + i0;
 
+  // slot qbase + r NT holds Q point qperm[slot] (the caller's index; without qperm the slot itself)
   QT qr[R][3];
   const int64_t qbase = (int64_t)blockIdx.x * (NT * R) + threadIdx.x;
 #pragma unroll
@@ -54,8 +56,9 @@ __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_fwd(const typena
 #pragma unroll
     for (int d = 0; d < 3; ++d) qr[r][d] = (QT)0;
     if (iq < n_q) {
+      const int64_t src = qperm ? (int64_t)qperm[iq] : iq;
 #pragma unroll
-      for (int d = 0; d < D; ++d) qr[r][d] = (QT)q[iq * D + d];
+      for (int d = 0; d < D; ++d) qr[r][d] = (QT)q[src * D + d];
     }
   }
   typename Pol::template Acc<R> acc;
@@ -110,16 +113,16 @@ __global__ void __launch_bounds__(NT, kMinBlocks<Pol, R, NT>) k_fwd(const typena
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int64_t iq = qbase + (int64_t)r * NT;
-    if (iq < n_q) partial[(int64_t)blockIdx.y * n_q + iq] = acc.get(r);
+    if (iq < n_q) partial[(int64_t)blockIdx.y * n_q + (qperm ? (int64_t)qperm[iq] : iq)] = acc.get(r);
   }
 }
 
 template <class Pol, int R, int NT>
 cudaError_t launch_one(const FwdLaunch& L, const void* items, int64_t n_items, const double* q, int64_t n_q,
-                       Thr th, double2* partial, uint32_t* status, cudaStream_t st) {
+                       Thr th, double2* partial, uint32_t* status, cudaStream_t st, const int32_t* qperm) {
   dim3 grid((unsigned)L.q_tiles, (unsigned)L.k_splits);
   k_fwd<Pol, R, NT><<<grid, NT, 0, st>>>(static_cast<const typename Pol::Item*>(items), n_items, L.per_split, q,
-                                         n_q, th, partial, status);
+                                         n_q, th, partial, status, qperm);
   return cudaGetLastError();
 }
 
@@ -156,9 +159,11 @@ cudaError_t dispatch_pairs(int r, int nt, F&& f) {
 
 struct LaunchF {
   const FwdLaunch& L; const void* items; int64_t n_items; const double* q; int64_t n_q; Thr th;
-  double2* partial; uint32_t* status; cudaStream_t st;
+  double2* partial; uint32_t* status; cudaStream_t st; const int32_t* qperm;
   template <class Pol, int R, int NT>
-  cudaError_t operator()() const { return launch_one<Pol, R, NT>(L, items, n_items, q, n_q, th, partial, status, st); }
+  cudaError_t operator()() const {
+    return launch_one<Pol, R, NT>(L, items, n_items, q, n_q, th, partial, status, st, qperm);
+  }
 };
 
 struct OccF {
@@ -171,13 +176,13 @@ struct OccF {
 
 cudaError_t launch_fwd(int dim, bool fp64, const FwdLaunch& L, const void* items, int64_t n_items, const double* q,
                        int64_t n_q, float tau, double2* partial, uint32_t* status, cudaStream_t st,
-                       int64_t pair_faces) {
+                       int64_t pair_faces, const int32_t* qperm) {
   // the FP64 path keeps its series (through k = 16) for P < 9/4, where it truncates below 1e-14
   if (fp64) tau = fminf(tau, 3.0f);
   const float tau_lo = fminf(tau, kTauLo);
   const Thr th{0.25f * tau * tau, 0.25f * tau_lo * tau_lo, tau > 1.0f ? 1 : 0, tau > 3.0f ? 1 : 0,
                dim == 3 && !fp64 ? pair_faces : 0};
-  LaunchF f{L, items, n_items, q, n_q, th, partial, status, st};
+  LaunchF f{L, items, n_items, q, n_q, th, partial, status, st, qperm};
   if (dim == 2) return fp64 ? dispatch<Pol2F64>(L.r, L.nt, f) : dispatch<Pol2F32>(L.r, L.nt, f);
   if (!fp64 && th.pair_end > 0) return dispatch_pairs(L.r, L.nt, f);
   return fp64 ? dispatch<Pol3F64>(L.r, L.nt, f) : dispatch<Pol3F32>(L.r, L.nt, f);

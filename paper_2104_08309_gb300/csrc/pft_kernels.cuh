@@ -80,9 +80,11 @@ cudaError_t launch_prep2d(const float* v, int64_t nv, const int64_t* off, int64_
 cudaError_t launch_prep3d(const float* v, int64_t nv, const int32_t* f, int64_t nf, WsHeader* h,
                           void* faces, bool fp64, double* partials, int nblk, cudaStream_t st,
                           int64_t pair_faces = 0);
+// qperm: NULL, or the slot -> Q index map of launch_qorder (the kernel reads Q point qperm[slot]
+// and writes its partial sums at that index).
 cudaError_t launch_fwd(int dim, bool fp64, const FwdLaunch& L, const void* items, int64_t n_items,
                        const double* q, int64_t n_q, float tau, double2* partial, uint32_t* status,
-                       cudaStream_t st, int64_t pair_faces = 0);
+                       cudaStream_t st, int64_t pair_faces = 0, const int32_t* qperm = nullptr);
 cudaError_t launch_fan3d(const int32_t* idx, int64_t n_idx, const int64_t* off, int64_t n_faces, int32_t* tris,
                          int64_t n_tris, WsHeader* h, cudaStream_t st);
 cudaError_t launch_finalize(int dim, const double* q, int64_t n_q, const double2* partial, int k_splits,
@@ -96,6 +98,20 @@ cudaError_t launch_smallq3d(const float* v, int64_t nv, const int32_t* f, int64_
 // Prep blocks used for the per-block FP64 area/volume partial sums.
 constexpr int kPrepThreads = 256;
 inline int prep_blocks(int64_t n) { return (int)((n + kPrepThreads - 1) / kPrepThreads); }
+
+// Q order (pft_qorder.cu): a slot -> Q index map that puts Q points close together in Q space
+// into the same group of 32 threads of a pair kernel with r Q points per thread and nt threads
+// per block.  Scratch regions (byte offsets from the scratch base, 256-byte aligned):
+struct QOrderLayout {
+  size_t box, keys0, keys1, vals0, vals1, hist, tot, total;
+  int64_t nb, nh, nt;   // sort blocks, histogram length, scan blocks
+};
+QOrderLayout qorder_layout(int64_t n_q);
+// Whether a call with n_q Q points and n_items segments or faces orders its Q points.
+bool qorder_wanted(int64_t n_q, int64_t n_items, int r, int nt);
+// perm[n_q] <- the map; q is [n_q x dim] FP64 on the device; adds its launches to *launches.
+cudaError_t launch_qorder(int dim, const double* q, int64_t n_q, int r, int nt, void* scratch, int32_t* perm,
+                          cudaStream_t st, int* launches);
 
 // Occupancy query for the main kernel of a configuration (blocks per SM).
 int fwd_blocks_per_sm(int dim, bool fp64, int r, int nt, bool pairs = false);

@@ -47,6 +47,7 @@ def test_options_struct_layout_matches_header():
     # int32 x5, float, two pointers (8-aligned at offset 24), int32[4]
     assert ctypes.sizeof(_capi.Options) == 24 + 16 + 16
     assert _capi.Options.main_start_event.offset == 24
+    assert (_capi.Options.face_pairs.offset, _capi.Options.q_order.offset) == (40, 44)
 
 
 def test_status_strings_and_version(lib):
@@ -82,6 +83,30 @@ def test_workspace_sizes(lib):
     sq = lib.pft3d_qgrad_workspace_size(40992, 81920, 32768, ctypes.byref(o))
     assert sq >= 256 + 81920 * 48 + 32768 * 32 and sq % 256 == 0
     assert lib.pft3d_qgrad_workspace_size(40992, 81920, 32768, ctypes.byref(o64)) == 0
+
+
+def test_q_order_option_and_workspace(lib):
+    """The Q ordering adds workspace only where it runs (two blocks of Q points and about 1e9 pairs
+    or more, PFT_Q_TILED); PFT_Q_AS_GIVEN never orders; other values are refused."""
+    tiled, given = _capi.Options(), _capi.Options(q_order=1)
+    big = lib.pft3d_workspace_size(655362, 1310720, 2097152, ctypes.byref(tiled))
+    plain = lib.pft3d_workspace_size(655362, 1310720, 2097152, ctypes.byref(given))
+    assert big - plain >= 2097152 * (4 + 16) + lib.pft_q_order_workspace_size(0)
+    assert big - plain >= lib.pft_q_order_workspace_size(2097152)
+    # a small problem (1e6 pairs) is not ordered
+    assert (lib.pft2d_workspace_size(64, 1, 16384, ctypes.byref(tiled))
+            == lib.pft2d_workspace_size(64, 1, 16384, ctypes.byref(given)))
+    assert lib.pft3d_workspace_size(10, 16, 100, ctypes.byref(_capi.Options(q_order=2))) == 0
+    assert lib.pft3d_workspace_size(10, 16, 100, ctypes.byref(_capi.Options(q_order=-1))) == 0
+    assert lib.pft_q_order_workspace_size(-1) == 0
+    # pft_q_order checks its arguments before any device work
+    fake = ctypes.c_void_p(256)
+    assert lib.pft_q_order(fake, 10, 4, 4, 128, fake, fake, 1 << 20, None) == 1             # dim
+    assert lib.pft_q_order(fake, 10, 3, 3, 128, fake, fake, 1 << 20, None) == 7             # R
+    assert lib.pft_q_order(fake, 10, 3, 4, 64, fake, fake, 1 << 20, None) == 7              # NT
+    assert lib.pft_q_order(None, 10, 3, 4, 128, fake, fake, 1 << 20, None) == 1
+    assert lib.pft_q_order(fake, 10, 3, 4, 128, fake, fake, 16, None) == 4                  # workspace
+    assert lib.pft_q_order(fake, 0, 3, 4, 128, None, None, 0, None) == 0                     # nothing to do
 
 
 def test_argument_errors_are_synchronous(lib):
