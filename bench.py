@@ -754,7 +754,9 @@ def bench_adjoint(dev, warmup, steps):
     clk = float(pk.get("sm_max_mhz", 2070.0))
 
     def rl(kernel, ms_k, lanes, table):
-        lane, warp = adjoint_branch_mix(w.verts, w.faces, w.q, lanes=lanes)
+        # k_qgrad holds one Q point per thread, in the library's order (q_order's default)
+        qm = kernel_order(pft, w.q, qd, 1, 128, w.faces.shape[0]) if lanes == "q" else w.q
+        lane, warp = adjoint_branch_mix(w.verts, w.faces, qm, lanes=lanes)
         ops = adjoint_ops(warp, table)
         issue = ops["fp32"] + ops["sfu"]
         cyc = max(issue / FP32_LANES, ops["sfu"] / SFU_LANES)

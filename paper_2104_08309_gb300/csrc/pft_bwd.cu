@@ -464,9 +464,10 @@ struct QAdj {
 // |Q| go to the FP64 list with a zero weight here.
 template <int D>
 __global__ void k_bq(const double* __restrict__ q, const double* __restrict__ g, int64_t n_q, WsHeader* h,
-                     double scale, QRec* rec, int32_t* small) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n_q) return;
+                     double scale, QRec* rec, int32_t* small, const int32_t* __restrict__ perm = nullptr) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // record slot
+  if (s >= n_q) return;
+  const int64_t i = perm ? (int64_t)perm[s] : s;                      // its Q point (caller's index)
   float qf[3] = {0.f, 0.f, 0.f};
   for (int d = 0; d < D; ++d) qf[d] = (float)q[D * i + d];
   const double Q[3] = {qf[0], qf[1], qf[2]};
@@ -482,7 +483,7 @@ __global__ void k_bq(const double* __restrict__ q, const double* __restrict__ g,
     r.gr = (float)(k * (gr * cp - gi * sp));
     r.gi = (float)(k * (gr * sp + gi * cp));
   }
-  rec[i] = r;
+  rec[s] = r;
 }
 
 // Thread <-> item (segment or face); Q chunk blockIdx.y; FP64 partial per (chunk, item, field).
@@ -501,7 +502,8 @@ constexpr int kQG = 5;              // partial fields per (chunk, Q): S.re, S.im
 
 __global__ void __launch_bounds__(kBwdNT) k_qgrad(const Face32* __restrict__ faces, int64_t n_faces,
                                                   int64_t per_split, const QRec* __restrict__ rec, int64_t n_q,
-                                                  Thr th, double* __restrict__ partial, uint32_t* status) {
+                                                  Thr th, double* __restrict__ partial, uint32_t* status,
+                                                  const int32_t* __restrict__ perm) {
   __shared__ __align__(128) Face32 slots[kStages * kFTile];
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ int done[kStages];
@@ -541,7 +543,7 @@ __global__ void __launch_bounds__(kBwdNT) k_qgrad(const Face32* __restrict__ fac
   if (!ok) set_status(status, ST_TIMEOUT);
   ring.finish();
   if (!ok || i >= n_q) return;
-  double* dst = partial + ((int64_t)blockIdx.y * n_q + i) * kQG;
+  double* dst = partial + ((int64_t)blockIdx.y * n_q + (perm ? (int64_t)perm[i] : i)) * kQG;   // caller's index
 #pragma unroll
   for (int f = 0; f < kQG; ++f) dst[f] = (double)acc[f].hi + (double)acc[f].lo;
 }
@@ -706,7 +708,8 @@ __device__ __forceinline__ void seg_qadj(const QRec& Q, const float4 s, float& j
 
 __global__ void __launch_bounds__(kBwdNT) k_qgrad2d(const Seg32* __restrict__ segs, int64_t n_segs,
                                                     int64_t per_split, const QRec* __restrict__ rec, int64_t n_q,
-                                                    double* __restrict__ partial, uint32_t* status) {
+                                                    double* __restrict__ partial, uint32_t* status,
+                                                    const int32_t* __restrict__ perm) {
   __shared__ __align__(128) Seg32 slots[kStages * kSTile];
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ int done[kStages];
@@ -738,7 +741,7 @@ __global__ void __launch_bounds__(kBwdNT) k_qgrad2d(const Seg32* __restrict__ se
   if (!ok) set_status(status, ST_TIMEOUT);
   ring.finish();
   if (!ok || i >= n_q) return;
-  double* dst = partial + ((int64_t)blockIdx.y * n_q + i) * kQG2;
+  double* dst = partial + ((int64_t)blockIdx.y * n_q + (perm ? (int64_t)perm[i] : i)) * kQG2;   // caller's index
 #pragma unroll
   for (int f = 0; f < kQG2; ++f) dst[f] = (double)acc[f].hi + (double)acc[f].lo;
 }
@@ -1633,12 +1636,22 @@ BwdLayout bwd_layout(int dim, int64_t n_verts, int64_t n_items, int64_t n_prep, 
 // Q-gradient workspace: header, volume partials (written by the prep kernel), face
 // records, Q records, small-|Q| list, kQG FP64 partials per (face chunk, Q).
 struct QgLayout {
-  size_t mparts, items, qrec, small, partial, spart, total;
+  size_t mparts, items, qrec, small, partial, spart, qperm, qscratch, total;
+  bool tiled;   // the pair kernel visits the Q points in the library's order (q_order option)
   int nblk, ks;
   int64_t per_split, slots;
 };
 
-QgLayout qg_layout(int64_t n_faces, int64_t n_q) {
+// The Q-gradient kernels hold one Q point per thread, so a group of 32 threads is 32 consecutive
+// slots: with the library's order (q_order option) those are 32 consecutive points of the Z-order.
+void qg_order_regions(QgLayout& y, size_t& o, int64_t n_q, int64_t n_items, bool tiled) {
+  y.tiled = tiled && qorder_wanted(n_q, n_items, 1, kBwdNT);
+  if (!y.tiled) return;
+  y.qperm = o;    o = al(o + sizeof(int32_t) * (size_t)n_q);
+  y.qscratch = o; o = al(o + qorder_layout(n_q).total);
+}
+
+QgLayout qg_layout(int64_t n_faces, int64_t n_q, bool tiled) {
   QgLayout y{};
   const int64_t face_tiles = std::max<int64_t>(1, (n_faces + kFTile - 1) / kFTile);
   const int64_t q_blocks = std::max<int64_t>(1, (n_q + kBwdNT - 1) / kBwdNT);
@@ -1667,13 +1680,14 @@ QgLayout qg_layout(int64_t n_faces, int64_t n_q) {
   y.partial = o; o = al(o + sizeof(double) * kQG * (size_t)y.ks * (size_t)std::max<int64_t>(n_q, 1));
   y.slots = std::max<int64_t>(kQsUnits, n_q);
   y.spart = o;   o = al(o + sizeof(double) * kQsF * (size_t)y.slots);
+  qg_order_regions(y, o, n_q, n_faces, tiled);
   y.total = o;
   return y;
 }
 
 // 2D Q-gradient workspace: header, area partials, segment records, Q records, small-|Q|
 // list, kQG2 FP64 partials per (segment chunk, Q), small-|Q| slots.
-QgLayout qg2_layout(int64_t n_segs, int64_t n_prep, int64_t n_q) {
+QgLayout qg2_layout(int64_t n_segs, int64_t n_prep, int64_t n_q, bool tiled) {
   QgLayout y{};
   const int64_t seg_tiles = std::max<int64_t>(1, (n_segs + kSTile - 1) / kSTile);
   const int64_t q_blocks = std::max<int64_t>(1, (n_q + kBwdNT - 1) / kBwdNT);
@@ -1702,6 +1716,7 @@ QgLayout qg2_layout(int64_t n_segs, int64_t n_prep, int64_t n_q) {
   y.partial = o; o = al(o + sizeof(double) * kQG2 * (size_t)y.ks * (size_t)std::max<int64_t>(n_q, 1));
   y.slots = std::max<int64_t>(kQsUnits, n_q);
   y.spart = o;   o = al(o + sizeof(double) * kQsF2 * (size_t)y.slots);
+  qg_order_regions(y, o, n_q, n_segs, tiled);
   y.total = o;
   return y;
 }
@@ -1781,10 +1796,12 @@ Bb3Layout bb3_layout(int64_t nv, int64_t nf, int64_t nm, int64_t n_q, bool per_m
 // Caller events recorded around the main pair kernel of the current call (set by check_opts).
 thread_local cudaEvent_t g_ev_start = nullptr, g_ev_stop = nullptr;
 
-int check_opts(const pft_options* o, Thr& th) {
+int check_opts(const pft_options* o, Thr& th, bool* tiled = nullptr) {
   pft_options z;
   std::memset(&z, 0, sizeof(z));
   const pft_options& p = o ? *o : z;
+  if (p.q_order != PFT_Q_TILED && p.q_order != PFT_Q_AS_GIVEN) return PFT_ERR_INVALID_ARG;
+  if (tiled) *tiled = p.q_order == PFT_Q_TILED;
   g_ev_start = static_cast<cudaEvent_t>(p.main_start_event);
   g_ev_stop = static_cast<cudaEvent_t>(p.main_stop_event);
   if (p.precision != PFT_FP32_COMPENSATED) return PFT_ERR_UNSUPPORTED;   // the adjoint runs in FP32
@@ -1807,6 +1824,18 @@ int check_opts(const pft_options* o, Thr& th) {
     if (cudaGetLastError() != cudaSuccess) return PFT_ERR_CUDA; \
     ++g_bwd_launches;                                      \
   } while (0)
+
+// The slot -> Q map of a Q-gradient call (NULL: the caller's order), computed on the stream.
+int qg_order(int dim, const QgLayout& y, const double* q, int64_t n_q, void* ws, cudaStream_t st,
+             const int32_t*& perm) {
+  perm = nullptr;
+  if (!y.tiled) return PFT_OK;
+  int32_t* p = at<int32_t>(ws, y.qperm);
+  if (launch_qorder(dim, q, n_q, 1, kBwdNT, at<void>(ws, y.qscratch), p, st, &g_bwd_launches) != cudaSuccess)
+    return PFT_ERR_CUDA;
+  perm = p;
+  return PFT_OK;
+}
 
 }  // namespace
 }  // namespace pft
@@ -1989,8 +2018,9 @@ int pft3d_polymesh_backward(const float* verts, int64_t n_verts, const int32_t* 
 
 size_t pft3d_qgrad_workspace_size(int64_t n_verts, int64_t n_faces, int64_t n_q, const pft_options* opts) {
   Thr th;
-  if (n_verts < 0 || n_faces < 0 || n_q < 0 || check_opts(opts, th) != PFT_OK) return 0;
-  return qg_layout(n_faces, n_q).total;
+  bool tiled;
+  if (n_verts < 0 || n_faces < 0 || n_q < 0 || check_opts(opts, th, &tiled) != PFT_OK) return 0;
+  return qg_layout(n_faces, n_q, tiled).total;
 }
 
 int pft3d_mesh_qgrad(const float* verts, int64_t n_verts, const int32_t* faces, int64_t n_faces, const double* q,
@@ -1998,12 +2028,13 @@ int pft3d_mesh_qgrad(const float* verts, int64_t n_verts, const int32_t* faces, 
                      const pft_options* opts, void* stream) {
   g_bwd_launches = 0;
   Thr th;
-  if (int e = check_opts(opts, th)) return e;
+  bool tiled;
+  if (int e = check_opts(opts, th, &tiled)) return e;
   if (n_verts < 0 || n_faces < 0 || n_q < 0) return PFT_ERR_INVALID_ARG;
   if (n_faces > 0 && (faces == nullptr || verts == nullptr || n_verts == 0)) return PFT_ERR_INVALID_ARG;
   if (n_q > 0 && (q == nullptr || grad_out == nullptr || grad_q == nullptr)) return PFT_ERR_INVALID_ARG;
   if (n_q > INT32_MAX || n_verts > INT32_MAX) return PFT_ERR_UNSUPPORTED;
-  const QgLayout y = qg_layout(n_faces, n_q);
+  const QgLayout y = qg_layout(n_faces, n_q, tiled);
   if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < y.total) return PFT_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   WsHeader* h = at<WsHeader>(ws, 0);
@@ -2017,12 +2048,15 @@ int pft3d_mesh_qgrad(const float* verts, int64_t n_verts, const int32_t* faces, 
                     y.nblk, st) != cudaSuccess)
     return PFT_ERR_CUDA;
   g_bwd_launches += 2;
-  k_bq<3><<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, h, 1.0, at<QRec>(ws, y.qrec), at<int32_t>(ws, y.small));
+  const int32_t* perm = nullptr;
+  if (int e = qg_order(3, y, q, n_q, ws, st, perm)) return e;
+  k_bq<3><<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, h, 1.0, at<QRec>(ws, y.qrec), at<int32_t>(ws, y.small),
+                                              perm);
   PFT_BWD_LAUNCH();
   dim3 grid(blocks(n_q, kBwdNT), (unsigned)y.ks);
   PFT_MARK(g_ev_start);
   k_qgrad<<<grid, kBwdNT, 0, st>>>(at<Face32>(ws, y.items), n_faces, y.per_split, at<QRec>(ws, y.qrec), n_q, th,
-                                   at<double>(ws, y.partial), &h->status);
+                                   at<double>(ws, y.partial), &h->status, perm);
   PFT_BWD_LAUNCH();
   PFT_MARK(g_ev_stop);
   k_qfinal<<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, at<double>(ws, y.partial), y.ks, h, grad_q);
@@ -2039,8 +2073,9 @@ int pft3d_mesh_qgrad(const float* verts, int64_t n_verts, const int32_t* faces, 
 
 size_t pft2d_qgrad_workspace_size(int64_t n_verts, int64_t n_loops, int64_t n_q, const pft_options* opts) {
   Thr th;
-  if (n_verts < 0 || n_loops < 0 || n_q < 0 || check_opts(opts, th) != PFT_OK) return 0;
-  return qg2_layout(n_verts, std::max<int64_t>(n_verts, n_loops + 1), n_q).total;
+  bool tiled;
+  if (n_verts < 0 || n_loops < 0 || n_q < 0 || check_opts(opts, th, &tiled) != PFT_OK) return 0;
+  return qg2_layout(n_verts, std::max<int64_t>(n_verts, n_loops + 1), n_q, tiled).total;
 }
 
 int pft2d_polygons_qgrad(const float* verts, int64_t n_verts, const int64_t* loop_off, int64_t n_loops,
@@ -2048,12 +2083,13 @@ int pft2d_polygons_qgrad(const float* verts, int64_t n_verts, const int64_t* loo
                          size_t ws_bytes, const pft_options* opts, void* stream) {
   g_bwd_launches = 0;
   Thr th;
-  if (int e = check_opts(opts, th)) return e;
+  bool tiled;
+  if (int e = check_opts(opts, th, &tiled)) return e;
   if (n_verts < 0 || n_loops < 0 || n_q < 0) return PFT_ERR_INVALID_ARG;
   if (n_verts > 0 && (verts == nullptr || loop_off == nullptr || n_loops == 0)) return PFT_ERR_INVALID_ARG;
   if (n_q > 0 && (q == nullptr || grad_out == nullptr || grad_q == nullptr)) return PFT_ERR_INVALID_ARG;
   if (n_q > INT32_MAX) return PFT_ERR_UNSUPPORTED;
-  const QgLayout y = qg2_layout(n_verts, std::max<int64_t>(n_verts, n_loops + 1), n_q);
+  const QgLayout y = qg2_layout(n_verts, std::max<int64_t>(n_verts, n_loops + 1), n_q, tiled);
   if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < y.total) return PFT_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   WsHeader* h = at<WsHeader>(ws, 0);
@@ -2067,12 +2103,15 @@ int pft2d_polygons_qgrad(const float* verts, int64_t n_verts, const int64_t* loo
                     y.nblk, st) != cudaSuccess)
     return PFT_ERR_CUDA;
   g_bwd_launches += 2;
-  k_bq<2><<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, h, 2.0, at<QRec>(ws, y.qrec), at<int32_t>(ws, y.small));
+  const int32_t* perm = nullptr;
+  if (int e = qg_order(2, y, q, n_q, ws, st, perm)) return e;
+  k_bq<2><<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, h, 2.0, at<QRec>(ws, y.qrec), at<int32_t>(ws, y.small),
+                                              perm);
   PFT_BWD_LAUNCH();
   dim3 grid(blocks(n_q, kBwdNT), (unsigned)y.ks);
   PFT_MARK(g_ev_start);
   k_qgrad2d<<<grid, kBwdNT, 0, st>>>(at<Seg32>(ws, y.items), n_verts, y.per_split, at<QRec>(ws, y.qrec), n_q,
-                                     at<double>(ws, y.partial), &h->status);
+                                     at<double>(ws, y.partial), &h->status, perm);
   PFT_BWD_LAUNCH();
   PFT_MARK(g_ev_stop);
   k_qfinal2d<<<blocks(n_q, kAux), kAux, 0, st>>>(q, grad_out, n_q, at<double>(ws, y.partial), y.ks, h, grad_q);
