@@ -55,6 +55,31 @@ def test_noalloc_matches_workspace_call_twice(torch_dev):
         assert torch.equal(out, ref), (call, (out - ref).abs().max().item())
 
 
+def test_noalloc_with_the_q_order(torch_dev):
+    """A problem large enough for the library's Q order (81,920 faces x 32^3 Q, 2.7e9 pairs) whose
+    workspace, ordering scratch included, fits the fixed scratch: bitwise the workspace call."""
+    torch, dev = torch_dev
+    from paper_2104_08309_gb300 import _capi
+    lib = _capi.load()
+    v, f = synth.icosphere(6)
+    q = synth.q_grid_3d(32, 30.0)
+    vd, fd, qd = (torch.from_numpy(a).to(dev) for a in (v, f, q))
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    tiled, given = _capi.Options(), _capi.Options(q_order=1)
+    need = lib.pft3d_workspace_size(v.shape[0], f.shape[0], q.shape[0], ctypes.byref(tiled))
+    assert lib.pft3d_workspace_size(v.shape[0], f.shape[0], q.shape[0], ctypes.byref(given)) < need <= 32 << 20
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    ref = torch.empty(q.shape[0], 2, dtype=torch.float64, device=dev)
+    assert lib.pft3d_mesh(vd.data_ptr(), v.shape[0], fd.data_ptr(), f.shape[0], qd.data_ptr(), q.shape[0],
+                          ref.data_ptr(), ws.data_ptr(), need, ctypes.byref(tiled), stream) == 0
+    out = torch.full((q.shape[0], 2), float("nan"), dtype=torch.float64, device=dev)
+    rc = lib.pft3d_mesh_noalloc(vd.data_ptr(), v.shape[0], fd.data_ptr(), f.shape[0], qd.data_ptr(),
+                                q.shape[0], out.data_ptr(), ctypes.byref(tiled), stream)
+    assert rc == 0, lib.pft_status_string(rc)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+
+
 def test_noalloc_refuses_problems_beyond_its_scratch(torch_dev):
     torch, dev = torch_dev
     from paper_2104_08309_gb300 import _capi
