@@ -536,7 +536,9 @@ def bench_batched3d(dev, warmup, steps):
     v, f, off = synth.mesh_batch(1024, seed=21)
     q = synth.q_grid_3d(32, 30.0)
     vd, fd, qd, offd = (torch.from_numpy(a).to(dev) for a in (v, f, q, off))
-    prep = pft.pft3d_batched_prepare(off, q.shape[0], device=dev)
+    r, nt = 4, 512                           # the default launch shape on this shared Q set
+    prep = pft.pft3d_batched_prepare(off, q.shape[0], options={"q_per_thread": r, "block_threads": nt},
+                                     device=dev)
     out = torch.empty(off.size - 1, q.shape[0], 2, dtype=torch.float64, device=dev)
     s = torch.cuda.Stream(dev)
     s.wait_stream(torch.cuda.current_stream(dev))
@@ -563,7 +565,7 @@ def bench_batched3d(dev, warmup, steps):
     ms = float(np.mean(ts))
     pairs = float(f.shape[0]) * float(q.shape[0])
     pk, _ = peaks()
-    mix = branch_mix(v, f, kernel_order(pft, q, qd, 4, 128, f.shape[0]), tau=6.0, r=4, nt=128)
+    mix = branch_mix(v, f, kernel_order(pft, q, qd, r, nt, f.shape[0]), tau=6.0, r=r, nt=nt)
     _, _, ach, peak = roofline(pairs, ms / 1e3, mix, torch.cuda.get_device_properties(dev).multi_processor_count,
                                float(pk.get("sm_max_mhz", 2070.0)))
     status = int(pft.pft_status(prep.ws))
@@ -587,7 +589,8 @@ def bench_batched3d(dev, warmup, steps):
     del gb
     return {"value": pairs / (ms / 1e3) / 1e9, "unit": UNIT + " (Q, triangle)", "ms_per_step": ms,
             "pairs_per_step": pairs, "meshes": int(off.size - 1), "faces": int(f.shape[0]),
-            "q_points": int(q.shape[0]), "launches_per_step": int(launches), "cuda_graph": True,
+            "q_points": int(q.shape[0]), "launch_shape": [r, nt], "launches_per_step": int(launches),
+            "cuda_graph": True,
             "device_status": status, "roofline_frac": ach / peak, "branch_fractions": mix,
             "backward": backward,
             "note": "whole batched call timed (prep, pair kernel, multi-chunk finish, small-|Q| pass)",

@@ -70,7 +70,9 @@ typedef enum {
  *  precision        pft_precision.
  *  q_per_thread     Q points each thread keeps in registers (0 = default; FP32: 1, 2,
  *                   4 or 8; FP64: 1 or 2).
- *  block_threads    threads per block of the main kernel (0 = default; 128 or 256).
+ *  block_threads    threads per block of the main kernel (0 = default; 128 or 256; the
+ *                   batched FP32 calls also take 512 with q_per_thread 4, one block per SM,
+ *                   and take it by default on a shared Q set of 4 x 512 points or more).
  *  k_splits         number of segment/face chunks summed in the FP64 second pass
  *                   (0 = chosen from the problem size and the GPU).  For a fixed
  *                   value and launch shape the result is bitwise reproducible;
@@ -261,7 +263,7 @@ int pft3d_pair_faces(const int32_t* faces_host, int64_t n_faces, int32_t* faces_
  * by a stable radix sort, and each run of 32 q_per_thread sorted points fills one
  * group's slots; the last, partial block keeps the sorted order.
  *  q          [n_q][dim] float64, device.      perm  [n_q] int32, device, written.
- *  dim        2 or 3; q_per_thread 1, 2, 4 or 8; block_threads 128 or 256.
+ *  dim        2 or 3; q_per_thread 1, 2, 4 or 8; block_threads 128, 256 or 512.
  * Workspace: pft_q_order_workspace_size(n_q) bytes, 256-byte aligned.
  * Returns PFT_OK, PFT_ERR_INVALID_ARG, PFT_ERR_UNSUPPORTED (n_q > INT32_MAX or
  * another shape), PFT_ERR_WORKSPACE, PFT_ERR_CUDA.  Asynchronous on `stream`.

@@ -17,6 +17,8 @@ import threading
 
 CANDIDATES_FP32 = [(1, 128), (2, 128), (4, 128), (8, 128), (1, 256), (2, 256), (4, 256), (8, 256)]
 CANDIDATES_FP64 = [(1, 128), (2, 128), (1, 256), (2, 256)]
+# the batched calls also run one block of 512 threads per SM (4 Q points per thread)
+CANDIDATES_BATCHED_FP32 = CANDIDATES_FP32 + [(4, 512)]
 
 _lock = threading.Lock()
 
@@ -129,7 +131,7 @@ def tune_mesh3d(verts, faces, q, precision: str = "fp32", sample: int = 65536, *
 def tune_batched2d(verts, poly_off, q, q_off=None, precision: str = "fp32", **kw):
     """Best launch shape for pft2d_polygons_batched (each candidate with its own prepared schedule)."""
     import paper_2104_08309_gb300 as pft
-    cands = CANDIDATES_FP64 if precision == "fp64" else CANDIDATES_FP32
+    cands = CANDIDATES_FP64 if precision == "fp64" else CANDIDATES_BATCHED_FP32
     n_polys = len(poly_off) - 1
     key = make_key(_device_name(verts), "batched2d", precision, n_polys, verts.shape[0], q.shape[0])
 

@@ -328,7 +328,7 @@ int pft_q_order(const double* q, int64_t n_q, int dim, int q_per_thread, int blo
   if (n_q < 0 || (dim != 2 && dim != 3)) return PFT_ERR_INVALID_ARG;
   if (n_q > INT32_MAX) return PFT_ERR_UNSUPPORTED;
   const int r = q_per_thread, nt = block_threads;
-  if (!(r == 1 || r == 2 || r == 4 || r == 8) || (nt != 128 && nt != 256)) return PFT_ERR_UNSUPPORTED;
+  if (!(r == 1 || r == 2 || r == 4 || r == 8) || (nt != 128 && nt != 256 && nt != 512)) return PFT_ERR_UNSUPPORTED;
   if (n_q == 0) return PFT_OK;
   if (q == nullptr || perm == nullptr) return PFT_ERR_INVALID_ARG;
   if (bad_ws(ws, ws_bytes, qorder_layout(n_q).total)) return PFT_ERR_WORKSPACE;

@@ -100,14 +100,22 @@ struct HostPlan {
 
 bool batched_config(int dim, bool fp64, int r, int nt);
 
-int resolve_batched(int dim, const pft_options* o, bool& fp64, int& r, int& nt, float& tau, int& q_order) {
+// Default launch shape: one block of 512 threads per SM on a shared Q set that fills its Q tiles
+// (r x 512 points or more), else blocks of 128.  Two or more resident blocks of the persistent
+// kernel do not share an SM evenly (the warps of the block that started first keep the issue
+// priority), so with a static schedule the later blocks ran up to a third longer than the first
+// ones while the SM sat half empty; the warps of one block walk the same tile ring and finish
+// together.
+int resolve_batched(int dim, const pft_options* o, bool shared_q, int64_t n_q, bool& fp64, int& r, int& nt,
+                    float& tau, int& q_order) {
   pft_options z;
   std::memset(&z, 0, sizeof(z));
   const pft_options& p = o ? *o : z;
   if (p.precision != PFT_FP32_COMPENSATED && p.precision != PFT_FP64) return PFT_ERR_INVALID_ARG;
   fp64 = p.precision == PFT_FP64;
   r = p.q_per_thread ? p.q_per_thread : (fp64 ? 1 : 4);
-  nt = p.block_threads ? p.block_threads : 128;
+  nt = p.block_threads ? p.block_threads
+                       : (shared_q && n_q >= (int64_t)r * 512 && batched_config(dim, fp64, r, 512) ? 512 : 128);
   if (!batched_config(dim, fp64, r, nt) || p.tile_items != 0 || p.k_splits != 0) return PFT_ERR_UNSUPPORTED;
   tau = p.face_series_tau == 0.f ? 6.0f : p.face_series_tau;
   if (!(tau > 0.f && tau <= 6.0f)) return PFT_ERR_INVALID_ARG;
@@ -124,7 +132,7 @@ int build_plan(int dim, const int64_t* poly_off, int64_t n_polys, const int64_t*
   bool fp64;
   int r, nt, q_order;
   float tau;
-  if (int e = resolve_batched(dim, opts, fp64, r, nt, tau, q_order)) return e;
+  if (int e = resolve_batched(dim, opts, q_off == nullptr, n_q, fp64, r, nt, tau, q_order)) return e;
   if (n_polys < 0 || n_q < 0 || (n_polys > 0 && poly_off == nullptr)) return PFT_ERR_INVALID_ARG;
   if (n_polys > 0 && poly_off[0] != 0) return PFT_ERR_OFFSETS;
   for (int64_t i = 0; i < n_polys; ++i)
@@ -429,14 +437,90 @@ __device__ __forceinline__ void finish_out(const double* Q, double re, double im
   out[2 * row + 1] = k * (re * sp + im * cp);
 }
 
+// The centre as float pairs c = hi + lo (to ~2^-48 of |c|), taken once per item.
+struct CenterF {
+  float hi[3], lo[3];
+};
+__device__ __forceinline__ CenterF center_f(const PolyInfo& pi) {
+  const double c[3] = {pi.cx, pi.cy, pi.cz};
+  CenterF f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    f.hi[d] = __double2float_rn(c[d]);
+    f.lo[d] = __double2float_rn(c[d] - (double)f.hi[d]);
+  }
+  return f;
+}
+
+constexpr float kTwoPiHi = 6.28318548202514648438f;       // 2 pi rounded to FP32
+constexpr float kTwoPiLo = -1.7484555314695172e-07f;        // 2 pi - kTwoPiHi, rounded to FP32
+
+// The same finish for the FP32 policies' single-chunk outputs, without FP64 arithmetic: GB300 runs
+// FP64 at a small fraction of its FP32 rate, and all warps of a block reach this together at the end
+// of every item.  Q.c is carried as s + t (the products with hi exact through their FMA residuals,
+// the lo products and the residuals in t), k = rint(s / 2 pi), and s - k 2pi_hi is exact in FP32 (both
+// are multiples of 2^-21 and the difference is below 4 in magnitude), so the reduced phase carries one
+// rounding, as the FP64 reduction cast to FP32 does; sincosf of it, the factor s/|Q|^2 and the
+// rotation of hi + lo in FP32: about 3e-7 of |F| against ~1e-7 for the sums themselves.  Phases
+// beyond 2^20 rad take the FP64 finish.
+template <int D>
+__device__ __forceinline__ void finish_out_f32(const float* Q, const CAcc& re, const CAcc& im, const PolyInfo& pi,
+                                               const CenterF& cf, int64_t row, double* out, uint32_t* small,
+                                               WsHeader* h) {
+  bool zero = true;
+  float q2 = 0.f;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    zero = zero && Q[d] == 0.f;
+    q2 = fmaf(Q[d], Q[d], q2);
+  }
+  if (zero) {
+    out[2 * row] = pi.measure;
+    out[2 * row + 1] = 0.0;
+    return;
+  }
+  if (q2 * (pi.rmax * pi.rmax) < (float)(kTauSmallQ * kTauSmallQ)) {   // |Q| r_max < tau_small
+    small[atomicAdd(&h->small_q_count, 1u)] = (uint32_t)row;
+    return;
+  }
+  float s = Q[0] * cf.hi[0];
+  float t = fmaf(Q[0], cf.hi[0], -s);
+#pragma unroll
+  for (int d = 1; d < D; ++d) {
+    const float p = Q[d] * cf.hi[d];
+    const float e = fmaf(Q[d], cf.hi[d], -p);
+    float s2, e2;
+    two_sum(s, p, s2, e2);
+    s = s2;
+    t += e2 + e;
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) t = fmaf(Q[d], cf.lo[d], t);
+  if (!(fabsf(s) < 1048576.f)) {
+    const double Qd[3] = {(double)Q[0], (double)Q[1], D == 3 ? (double)Q[2] : 0.0};
+    finish_out<D, true>(Qd, (double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo, pi, row, out, small, h);
+    return;
+  }
+  const float k = rintf(s * kInvTwoPi);
+  const float ph = fmaf(-k, kTwoPiHi, s) + fmaf(-k, kTwoPiLo, t);
+  float sp, cp;
+  sincosf(ph, &sp, &cp);
+  const float f = (D == 2 ? 2.0f : 1.0f) / q2;
+  const float a = re.hi + re.lo, b = im.hi + im.lo;
+  out[2 * row] = (double)(f * fmaf(a, cp, -b * sp));
+  out[2 * row + 1] = (double)(f * fmaf(a, sp, b * cp));
+}
+
 // Persistent kernel: block b runs items [cta_off[b], cta_off[b+1]) in order.  The
 // segment tiles of consecutive items form one stream through the ring; the last
 // warp to finish a slot issues the tile kStages further on (as in k_fwd).
 // Register budget: as the single-shape kernel, except that the 3D FP32 shapes with 128 threads
 // keep one block per SM fewer here (4 at 4 Q points, 5 at 2), where the item loop and the
-// in-place finish would otherwise spill.
+// in-place finish would otherwise spill, and that 512 threads are one block per SM (up to 128
+// registers: 16 warps, as 2 x 256 or 4 x 128).
 template <class Pol, int R, int NT>
-constexpr int kBatchedMinBlocks = (Pol::kDim == 3 && R == 4 && NT == 128) ? 4
+constexpr int kBatchedMinBlocks = NT >= 512 ? 1
+                                  : (Pol::kDim == 3 && R == 4 && NT == 128) ? 4
                                   : (Pol::kDim == 3 && R == 2 && NT == 128 && sizeof(typename Pol::QT) == 4)
                                       ? 5
                                       : kMinBlocks<Pol, R, NT>;
@@ -561,17 +645,24 @@ __global__ void __launch_bounds__(NT, kBatchedMinBlocks<Pol, R, NT>) k_batched(
     }
     if (!ok) break;
     const PolyInfo pi = info[it.poly];
+    constexpr bool kF32 = sizeof(QT) == 4;
+    CenterF cf{};
+    if constexpr (kF32) {
+      if (pp.n_chunks == 1) cf = center_f(pi);
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int64_t iq = q0 + (int64_t)r * NT + threadIdx.x;
       if (iq >= qend) continue;
-      const double2 f = acc.get(r);
       const int64_t local = (qperm ? (int64_t)qperm[iq] : iq) - pp.q_begin;
       if (pp.n_chunks > 1) {
-        partial[pp.part_base + (int64_t)it.chunk * pp.n_q + local] = f;
+        partial[pp.part_base + (int64_t)it.chunk * pp.n_q + local] = acc.get(r);
+      } else if constexpr (kF32) {
+        finish_out_f32<D>(qr[r], acc.re[r], acc.im[r], pi, cf, pp.out_base + local, out, small, h);
       } else {
+        const double2 f = acc.get(r);
         const double Qd[3] = {(double)qr[r][0], (double)qr[r][1], (double)qr[r][2]};
-        finish_out<D, sizeof(QT) == 4>(Qd, f.x, f.y, pi, pp.out_base + local, out, small, h);
+        finish_out<D, false>(Qd, f.x, f.y, pi, pp.out_base + local, out, small, h);
       }
     }
   }
@@ -758,7 +849,8 @@ cudaError_t launch_batched_one(int grid, const BPlanHeader* ph, const int32_t* c
 #define PFT_BATCHED_CASES(X)                                                                          \
   X(Pol2F32, 1, 128) X(Pol2F32, 2, 128) X(Pol2F32, 4, 128) X(Pol2F32, 8, 128) X(Pol2F32, 1, 256)      \
   X(Pol2F32, 2, 256) X(Pol2F32, 4, 256) X(Pol2F32, 8, 256) X(Pol2F64, 1, 128) X(Pol2F64, 2, 128)      \
-  X(Pol2F64, 1, 256) X(Pol2F64, 2, 256) X(Pol3F32, 2, 128) X(Pol3F32, 4, 128) X(Pol3F64, 1, 128)
+  X(Pol2F64, 1, 256) X(Pol2F64, 2, 256) X(Pol3F32, 2, 128) X(Pol3F32, 4, 128) X(Pol3F64, 1, 128)      \
+  X(Pol2F32, 4, 512) X(Pol3F32, 4, 512)
 
 #define PFT_BATCHED_MATCH(P, RR, NN) \
   (P::kDim == dim && (sizeof(P::QT) == 8) == fp64 && r == RR && nt == NN)

@@ -42,7 +42,8 @@ def _areas(v, off):
 
 # the FP64 path keeps at most 2 Q points per thread (larger shapes are refused synchronously)
 @pytest.mark.parametrize("prec,r,nt", [(p, r, nt) for p in ("fp32", "fp64")
-                                       for r, nt in ((4, 128), (1, 256), (2, 128)) if p == "fp32" or r <= 2])
+                                       for r, nt in ((4, 128), (1, 256), (2, 128), (4, 512))
+                                       if p == "fp32" or (r <= 2 and nt < 512)])
 def test_shared_grid_vs_oracle(torch_dev, prec, r, nt):
     torch, dev = torch_dev
     import paper_2104_08309_gb300 as pft
@@ -130,7 +131,7 @@ def test_c3_full_batch_fp32_vs_fp64_gpu(torch_dev):
     ref = _c(pft.pft2d_polygons_batched(vd, offd, qd, prepared=prep, check_status=True))
     q0 = int(np.flatnonzero(np.all(w.q == 0, axis=1))[0])
     area = np.abs(ref[:, q0])
-    for r, nt in autotune.CANDIDATES_FP32:
+    for r, nt in autotune.CANDIDATES_BATCHED_FP32:
         prep = pft.pft2d_batched_prepare(w.poly_off, w.q.shape[0], options={"q_per_thread": r, "block_threads": nt},
                                          device=dev)
         got = _c(pft.pft2d_polygons_batched(vd, offd, qd, prepared=prep, check_status=True))
@@ -153,3 +154,28 @@ def test_plan_mismatch_is_rejected(torch_dev):
     with pytest.raises(pft.PFTError, match="offsets"):
         pft.pft2d_polygons_batched(torch.from_numpy(v).to(dev), torch.from_numpy(off2).to(dev), q, prepared=prep,
                                    check_status=True)
+
+
+def test_default_shape_on_a_large_shared_grid_is_bitwise_the_same(torch_dev):
+    """On a shared Q set of 4 x 512 points or more the default launch shape is one block of 512
+    threads per SM; every Q point's sum runs over the same segments in the same order in any
+    launch shape, so the result equals the 4 x 128 and 4 x 256 shapes bit for bit (and the oracle
+    on sampled polygons)."""
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    v, off = synth.batched_star_polygons(96, seed=8)
+    q = synth.q_grid_2d(48, 40.0)                   # 2,304 points, one ragged 2,048-point tile
+    vd, qd, offd = torch.from_numpy(v).to(dev), torch.from_numpy(q).to(dev), torch.from_numpy(off).to(dev)
+    outs = {}
+    for name, opts in (("default", None), ("4x128", {"q_per_thread": 4, "block_threads": 128}),
+                       ("4x256", {"q_per_thread": 4, "block_threads": 256}),
+                       ("4x512", {"q_per_thread": 4, "block_threads": 512})):
+        prep = pft.pft2d_batched_prepare(off, q.shape[0], options=opts, device=dev)
+        outs[name] = pft.pft2d_polygons_batched(vd, offd, qd, prepared=prep, check_status=True).clone()
+    for name in ("4x128", "4x256", "4x512"):
+        assert torch.equal(outs["default"], outs[name]), name
+    got = _c(outs["default"])
+    for i in (0, 17, 95):
+        vi = v[off[i]:off[i + 1]]
+        ref = oracle.ft2d(vi, q)
+        assert np.max(np.abs(got[i] - ref)) / abs(ref[np.flatnonzero(np.all(q == 0, axis=1))[0]]) < TOL["fp32"], i

@@ -154,3 +154,32 @@ def test_empty_mesh_in_batch(torch_dev, rng):
         vi, fi = _mesh(v, f, off, i)
         ref = oracle.ft3d(vi, fi, q)
         assert np.max(np.abs(got[k] - ref)) / abs(ref[0]) < TOL["fp32"]
+
+
+def test_default_shape_on_a_large_shared_grid_is_bitwise_the_same(torch_dev):
+    """On a shared Q set of 4 x 512 points or more the default launch shape is one block of 512
+    threads per SM (the same result bit for bit as asking for it).  The series form of a face is
+    chosen per warp from the largest P over the warp's Q points, and without the library's Q order
+    (too few pairs here) a warp of another block size holds other Q points: the 4 x 128 shape then
+    agrees to rounding, and both agree with the oracle on sampled meshes."""
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    v, f, off = synth.mesh_batch(24, seed=6, levels=(1, 2, 3))
+    q = synth.q_grid_3d(14, 20.0)                   # 2,744 points, one ragged 2,048-point tile
+    vd, fd, qd = (torch.from_numpy(a).to(dev) for a in (v, f, q))
+    outs = {}
+    for name, opts in (("default", None), ("4x128", {"q_per_thread": 4, "block_threads": 128}),
+                       ("4x512", {"q_per_thread": 4, "block_threads": 512})):
+        prep = pft.pft3d_batched_prepare(off, q.shape[0], options=opts, device=dev)
+        outs[name] = pft.pft3d_meshes_batched(vd, fd, torch.from_numpy(off).to(dev), qd, prepared=prep,
+                                              check_status=True).clone()
+    assert torch.equal(outs["default"], outs["4x512"])
+    got, alt = _c(outs["default"]), _c(outs["4x128"])
+    for i in range(off.size - 1):
+        vol = abs(got[i][np.flatnonzero(np.all(q == 0, axis=1))[0]])
+        assert np.max(np.abs(got[i] - alt[i])) / vol < 1e-6, i
+    for i in (0, 11, 23):
+        vi, fi = _mesh(v, f, off, i)
+        ref = oracle.ft3d(vi, fi, q)
+        vol = abs(oracle.ft3d(vi, fi, [[0.0, 0.0, 0.0]])[0])
+        assert np.max(np.abs(got[i] - ref)) / vol < TOL["fp32"], i

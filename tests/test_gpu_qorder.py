@@ -72,7 +72,7 @@ def test_q_order_matches_its_definition(torch_dev, rng, d):
     q[3, 0] = np.nan
     q[11] = 0.0
     for r in (1, 2, 4, 8):
-        for nt in (128, 256):
+        for nt in (128, 256, 512):
             got = _perm(torch_dev, q, r, nt)
             assert np.array_equal(np.sort(got), np.arange(q.shape[0])), (r, nt)
             assert np.array_equal(got, mirror_perm(q, r, nt)), (r, nt)

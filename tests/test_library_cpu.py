@@ -109,6 +109,32 @@ def test_q_order_option_and_workspace(lib):
     assert lib.pft_q_order(fake, 0, 3, 4, 128, None, None, 0, None) == 0                     # nothing to do
 
 
+def test_batched_default_launch_shape(lib):
+    """Batched FP32 calls default to one block of 512 threads (4 Q points each) on a shared Q set of
+    4 x 512 points or more, else to 4 x 128; FP64 keeps 1 x 128.  Seen here through the plan's item
+    count (polygons x Q tiles of R x NT points) in the workspace size."""
+    npol = 1000
+    off = (ctypes.c_int64 * (npol + 1))(*[16 * i for i in range(npol + 1)])
+    nv = 16 * npol
+
+    def size(n_q, q_off=None, **kw):
+        o = _capi.Options(**kw)
+        return lib.pft2d_batched_workspace_size(nv, off, npol, q_off, n_q, ctypes.byref(o))
+
+    assert size(4096) == size(4096, q_per_thread=4, block_threads=512)
+    assert size(4096) < size(4096, q_per_thread=4, block_threads=128)
+    assert size(2047) == size(2047, q_per_thread=4, block_threads=128)       # below 4 x 512 points
+    qo = (ctypes.c_int64 * (npol + 1))(*[5 * i for i in range(npol + 1)])
+    assert size(5 * npol, qo) == size(5 * npol, qo, q_per_thread=4, block_threads=128)   # per-polygon lists
+    assert size(4096, precision=1) == size(4096, precision=1, q_per_thread=1, block_threads=128)
+    assert size(4096, q_per_thread=2, block_threads=512) == 0               # 512 threads: 4 Q points only
+    assert size(4096, precision=1, q_per_thread=1, block_threads=512) == 0
+    mo = (ctypes.c_int64 * (npol + 1))(*[20 * i for i in range(npol + 1)])
+    o, o512 = _capi.Options(), _capi.Options(q_per_thread=4, block_threads=512)
+    assert (lib.pft3d_batched_workspace_size(20 * npol, mo, npol, None, 4096, ctypes.byref(o))
+            == lib.pft3d_batched_workspace_size(20 * npol, mo, npol, None, 4096, ctypes.byref(o512)))
+
+
 def test_argument_errors_are_synchronous(lib):
     """Rejected before any device work: negative sizes, bad options, short or misaligned workspace."""
     fake = ctypes.c_void_p(256)     # never dereferenced: every call below fails its host checks
