@@ -292,15 +292,59 @@ __global__ void __launch_bounds__(kBThreads) k_bprep(const float* __restrict__ v
   }
   double area = 0.0;
   float rm = 0.f;
-  for (int64_t j = threadIdx.x; j < n; j += kBThreads) {
-    const int64_t a = pp.seg_begin + j, b = pp.seg_begin + (j + 1 < n ? j + 1 : 0);
-    const double x0 = (double)v[2 * a] - c[0], y0 = (double)v[2 * a + 1] - c[1];
-    const double x1 = (double)v[2 * b] - c[0], y1 = (double)v[2 * b + 1] - c[1];
-    const double mxd = 0.5 * (x0 + x1), myd = 0.5 * (y0 + y1), hx = 0.5 * (x1 - x0), hy = 0.5 * (y1 - y0);
-    area += 0.5 * (x0 * y1 - x1 * y0);
-    rm = fmaxf(rm, __double2float_ru(sqrt(x0 * x0 + y0 * y0)));
-    if (FP64) reinterpret_cast<Seg64*>(segs)[a] = Seg64{mxd, myd, hx, hy};
-    else reinterpret_cast<Seg32*>(segs)[a] = Seg32{(float)mxd, (float)myd, (float)hx, (float)hy};
+  if constexpr (FP64) {
+    for (int64_t j = threadIdx.x; j < n; j += kBThreads) {
+      const int64_t a = pp.seg_begin + j, b = pp.seg_begin + (j + 1 < n ? j + 1 : 0);
+      const double x0 = (double)v[2 * a] - c[0], y0 = (double)v[2 * a + 1] - c[1];
+      const double x1 = (double)v[2 * b] - c[0], y1 = (double)v[2 * b + 1] - c[1];
+      area += 0.5 * (x0 * y1 - x1 * y0);
+      rm = fmaxf(rm, __double2float_ru(sqrt(x0 * x0 + y0 * y0)));
+      reinterpret_cast<Seg64*>(segs)[a] = Seg64{0.5 * (x0 + x1), 0.5 * (y0 + y1), 0.5 * (x1 - x0), 0.5 * (y1 - y0)};
+    }
+  } else {
+    // FP32 records without FP64 arithmetic (GB300's FP64 pipe is a small fraction of its FP32
+    // rate): with the centre c = c_hi + c_lo as floats, v - c_hi = s + e exactly (TwoSum), so a
+    // centred coordinate is the float pair s + (e - c_lo); m and h are each rounded once from the
+    // float-pair sum or difference of two such pairs.  The area is the record polygon's own
+    // (p0 x p1 / 2 = mx hy - my hx for p0,1 = m -/+ h), each product split exactly by its FMA and
+    // summed with compensation: within ~1e-7 of the vertex polygon's, as the records are.  The
+    // radius bound comes from the centred vertex in FP32, raised by a relative 1e-6 to stay above
+    // the exact value.
+    float chi[2], clo[2];
+    for (int d = 0; d < 2; ++d) {
+      chi[d] = __double2float_rn(c[d]);
+      clo[d] = __double2float_rn(c[d] - (double)chi[d]);
+    }
+    auto centred = [&](float x, int d, float& s, float& t) {
+      float e;
+      two_sum(x, -chi[d], s, e);
+      t = e - clo[d];
+    };
+    auto half_sum = [](float s0, float t0, float s1, float t1) {   // (s0 + t0 + s1 + t1) / 2
+      float s, e;
+      two_sum(s0, s1, s, e);
+      return 0.5f * (s + (e + (t0 + t1)));
+    };
+    CAcc ar;
+    ar.init();
+    for (int64_t j = threadIdx.x; j < n; j += kBThreads) {
+      const int64_t a = pp.seg_begin + j, b = pp.seg_begin + (j + 1 < n ? j + 1 : 0);
+      float s0x, t0x, s0y, t0y, s1x, t1x, s1y, t1y;
+      centred(v[2 * a], 0, s0x, t0x);
+      centred(v[2 * a + 1], 1, s0y, t0y);
+      centred(v[2 * b], 0, s1x, t1x);
+      centred(v[2 * b + 1], 1, s1y, t1y);
+      const float mx = half_sum(s0x, t0x, s1x, t1x), my = half_sum(s0y, t0y, s1y, t1y);
+      const float hx = half_sum(s1x, t1x, -s0x, -t0x), hy = half_sum(s1y, t1y, -s0y, -t0y);
+      reinterpret_cast<Seg32*>(segs)[a] = Seg32{mx, my, hx, hy};
+      const float p = mx * hy, pe = fmaf(mx, hy, -p), q = my * hx, qe = fmaf(my, hx, -q);
+      float d, de;
+      two_sum(p, -q, d, de);
+      ar.add(d);
+      ar.add(de + (pe - qe));
+      rm = fmaxf(rm, sqrtf(fmaf(s0x, s0x, s0y * s0y)) * 1.000001f);
+    }
+    area = (double)ar.hi + (double)ar.lo;
   }
   area = bsum(area, shd);
   rm = bminmax(rm, true, shf);
@@ -656,7 +700,12 @@ __global__ void __launch_bounds__(NT, kBatchedMinBlocks<Pol, R, NT>) k_batched(
       if (iq >= qend) continue;
       const int64_t local = (qperm ? (int64_t)qperm[iq] : iq) - pp.q_begin;
       if (pp.n_chunks > 1) {
-        partial[pp.part_base + (int64_t)it.chunk * pp.n_q + local] = acc.get(r);
+        const int64_t at_ = pp.part_base + (int64_t)it.chunk * pp.n_q + local;
+        if constexpr (kF32)   // the compensated sums as they are: (re hi, re lo, im hi, im lo)
+          reinterpret_cast<float4*>(partial)[at_] =
+              make_float4(acc.re[r].hi, acc.re[r].lo, acc.im[r].hi, acc.im[r].lo);
+        else
+          partial[at_] = acc.get(r);
       } else if constexpr (kF32) {
         finish_out_f32<D>(qr[r], acc.re[r], acc.im[r], pi, cf, pp.out_base + local, out, small, h);
       } else {
@@ -675,7 +724,9 @@ __global__ void __launch_bounds__(NT, kBatchedMinBlocks<Pol, R, NT>) k_batched(
   }
 }
 
-// Multi-chunk shapes: fixed-order FP64 sum of their chunk partials, then the finish.
+// Multi-chunk shapes: fixed-order sum of their chunk partials, then the finish.  The FP32
+// policies' partials are compensated float pairs, added in the same compensated accumulator and
+// finished in FP32 (as the single-chunk outputs are); the FP64 policies' are doubles.
 __global__ void __launch_bounds__(kBThreads) k_bfinal(const BPlanHeader* ph, const int32_t* __restrict__ mc,
                                                       const PolyPlan* __restrict__ pplan,
                                                       const PolyInfo* __restrict__ info, const double* __restrict__ q,
@@ -686,6 +737,28 @@ __global__ void __launch_bounds__(kBThreads) k_bfinal(const BPlanHeader* ph, con
   const PolyInfo pi = info[i];
   const bool fp64 = ph->fp64 != 0;
   const int D = ph->dim;
+  if (!fp64) {
+    const CenterF cf = center_f(pi);
+    const float4* pf = reinterpret_cast<const float4*>(partial);
+    for (int64_t l = threadIdx.x; l < pp.n_q; l += kBThreads) {
+      CAcc re, im;
+      re.init();
+      im.init();
+      for (int c = 0; c < pp.n_chunks; ++c) {
+        const float4 p = pf[pp.part_base + (int64_t)c * pp.n_q + l];
+        re.add(p.x);
+        re.add(p.y);
+        im.add(p.z);
+        im.add(p.w);
+      }
+      const int64_t iq = pp.q_begin + l;
+      float Q[3] = {0.f, 0.f, 0.f};
+      for (int d = 0; d < D; ++d) Q[d] = (float)q[D * iq + d];
+      if (D == 2) finish_out_f32<2>(Q, re, im, pi, cf, pp.out_base + l, out, small, h);
+      else finish_out_f32<3>(Q, re, im, pi, cf, pp.out_base + l, out, small, h);
+    }
+    return;
+  }
   for (int64_t l = threadIdx.x; l < pp.n_q; l += kBThreads) {
     double re = 0.0, im = 0.0;
     for (int c = 0; c < pp.n_chunks; ++c) {
@@ -695,14 +768,9 @@ __global__ void __launch_bounds__(kBThreads) k_bfinal(const BPlanHeader* ph, con
     }
     const int64_t iq = pp.q_begin + l;
     double Q[3] = {0.0, 0.0, 0.0};
-    for (int d = 0; d < D; ++d) Q[d] = fp64 ? q[D * iq + d] : (double)(float)q[D * iq + d];
-    if (fp64) {
-      if (D == 2) finish_out<2, false>(Q, re, im, pi, pp.out_base + l, out, small, h);
-      else finish_out<3, false>(Q, re, im, pi, pp.out_base + l, out, small, h);
-    } else {
-      if (D == 2) finish_out<2, true>(Q, re, im, pi, pp.out_base + l, out, small, h);
-      else finish_out<3, true>(Q, re, im, pi, pp.out_base + l, out, small, h);
-    }
+    for (int d = 0; d < D; ++d) Q[d] = q[D * iq + d];
+    if (D == 2) finish_out<2, false>(Q, re, im, pi, pp.out_base + l, out, small, h);
+    else finish_out<3, false>(Q, re, im, pi, pp.out_base + l, out, small, h);
   }
 }
 
