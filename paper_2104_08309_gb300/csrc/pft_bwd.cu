@@ -1592,13 +1592,32 @@ int sm_count() {
   return std::max(1, sms);
 }
 
-// Q chunks so that the grid (item blocks x chunks) covers the GPU in whole waves.
+// Q chunks so that the grid (item blocks x chunks) is 16 waves of 8 blocks per SM (about 25 waves at
+// the pair kernels' 5 resident blocks): blocks do not finish in waves (the resident blocks of an SM
+// share it unevenly), and the last ones to start leave SMs partly idle for about a third of a
+// block's run.  The 3D adjoint on 81,920 faces x 32,768 Q: 9.29 ms at 4 waves of 8, 9.07 ms at 16.
 int q_splits(int64_t n_items, int64_t n_q) {
   const int64_t item_blocks = std::max<int64_t>(1, (n_items + kBwdNT - 1) / kBwdNT);
-  const int64_t slots = (int64_t)sm_count() * 8;   // ~8 resident blocks of 128 threads per SM
+  const int64_t slots = (int64_t)sm_count() * 8;
   const int64_t q_tiles = std::max<int64_t>(1, (n_q + kQTile - 1) / kQTile);
-  int64_t k = std::max<int64_t>(1, (4 * slots + item_blocks - 1) / item_blocks);
+  int64_t k = std::max<int64_t>(1, (16 * slots + item_blocks - 1) / item_blocks);
   return (int)std::min<int64_t>({k, q_tiles, 256});
+}
+
+// Chunks of a Q-gradient launch: k (the fewest that fill whole waves, the last >= 97 % full) raised,
+// for a launch of fewer than 40 waves, as far as chunks of at least 16 tiles and 64 chunks allow,
+// the last wave still >= 97 % full (the tail of the last blocks, as above).  The 3D Q-gradient on
+// 81,920 faces x 32,768 Q: 7 chunks (2 waves) 9.91 ms, 64 chunks 9.22 ms.
+int more_chunks(int k, int64_t q_blocks, int64_t slots, int64_t tiles) {
+  const int kw_max = (int)std::min<int64_t>(64, tiles / 16);
+  if ((double)(q_blocks * k) / (double)slots >= 40.0) return k;
+  for (int c = k + 1; c <= kw_max; ++c) {
+    const double waves = (double)(q_blocks * c) / (double)slots;
+    if (waves / std::ceil(waves) < 0.97) continue;
+    k = c;
+    if (waves >= 40.0) break;
+  }
+  return k;
 }
 
 struct BwdLayout {
@@ -1668,6 +1687,7 @@ QgLayout qg_layout(int64_t n_faces, int64_t n_q, bool tiled) {
     if (eff > best_eff + 1e-9) { best_eff = eff; best_k = c; }
   }
   if (k == 0) k = best_k;
+  k = more_chunks(k, q_blocks, slots, face_tiles);
   const int64_t tiles_per = (face_tiles + k - 1) / k;
   y.per_split = tiles_per * kFTile;
   y.ks = (int)((face_tiles + tiles_per - 1) / tiles_per);
@@ -1704,6 +1724,7 @@ QgLayout qg2_layout(int64_t n_segs, int64_t n_prep, int64_t n_q, bool tiled) {
     if (eff > best_eff + 1e-9) { best_eff = eff; best_k = c; }
   }
   if (k == 0) k = best_k;
+  k = more_chunks(k, q_blocks, slots, seg_tiles);
   const int64_t tiles_per = (seg_tiles + k - 1) / k;
   y.per_split = tiles_per * kSTile;
   y.ks = (int)((seg_tiles + tiles_per - 1) / tiles_per);
@@ -1735,7 +1756,9 @@ BbLayout bb_layout(int64_t nv, int64_t np, int64_t n_q, bool per_poly_q) {
   y.grid = std::max<int64_t>(1, np + (nv + kBbSegs - 1) / kBbSegs);   // at least the pair blocks needed
   const int64_t slots = (int64_t)sm_count() * 8;
   const int64_t q_tiles = std::max<int64_t>(1, (n_q + kQTile - 1) / kQTile);
-  const int64_t k = std::min<int64_t>({std::max<int64_t>(1, (4 * slots + y.grid - 1) / y.grid), q_tiles, 256});
+  // Q chunks for 16 waves of 8 blocks per SM, as q_splits (the tail of the last blocks to start):
+  // 4,096 polygons x 64^2 Q 17.32 -> 17.04 ms, 1,024 meshes x 32^3 Q 218.5 -> 212.6 ms against 4 waves
+  const int64_t k = std::min<int64_t>({std::max<int64_t>(1, (16 * slots + y.grid - 1) / y.grid), q_tiles, 256});
   y.per_split = ((q_tiles + k - 1) / k) * kQTile;
   y.ks = (int)std::max<int64_t>(1, (n_q + y.per_split - 1) / y.per_split);
   const int64_t rows = std::max<int64_t>(per_poly_q ? n_q : np * n_q, 1);
@@ -1767,7 +1790,9 @@ Bb3Layout bb3_layout(int64_t nv, int64_t nf, int64_t nm, int64_t n_q, bool per_m
   y.grid = std::max<int64_t>(1, nm + (nf + kBwdNT - 1) / kBwdNT);   // at least the pair blocks needed
   const int64_t slots = (int64_t)sm_count() * 8;
   const int64_t q_tiles = std::max<int64_t>(1, (n_q + kQTile - 1) / kQTile);
-  const int64_t k = std::min<int64_t>({std::max<int64_t>(1, (4 * slots + y.grid - 1) / y.grid), q_tiles, 256});
+  // Q chunks for 16 waves of 8 blocks per SM, as q_splits (the tail of the last blocks to start):
+  // 4,096 polygons x 64^2 Q 17.32 -> 17.04 ms, 1,024 meshes x 32^3 Q 218.5 -> 212.6 ms against 4 waves
+  const int64_t k = std::min<int64_t>({std::max<int64_t>(1, (16 * slots + y.grid - 1) / y.grid), q_tiles, 256});
   y.per_split = ((q_tiles + k - 1) / k) * kQTile;
   y.ks = (int)std::max<int64_t>(1, (n_q + y.per_split - 1) / y.per_split);
   const int64_t rows = std::max<int64_t>(per_mesh_q ? n_q : nm * n_q, 1);
