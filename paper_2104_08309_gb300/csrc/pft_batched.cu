@@ -395,44 +395,108 @@ __global__ void __launch_bounds__(kBThreads) k_bprep3(const float* __restrict__ 
   }
   double vol = 0.0;
   float rm = 0.f;
-  for (int64_t j = threadIdx.x; j < n; j += kBThreads) {
-    const int64_t m = pp.seg_begin + j;
-    double g[3] = {0, 0, 0}, q0[3] = {0, 0, 0}, q1[3] = {0, 0, 0}, N[3] = {0, 0, 0};
-    if (corner_ok(m)) {
-      double P[3][3];
-      bool fin = true;
-      for (int k = 0; k < 3; ++k)
-        for (int d = 0; d < 3; ++d) {
-          P[k][d] = (double)v[3 * (int64_t)f[3 * m + k] + d] - c[d];
-          fin = fin && isfinite(P[k][d]);
+  if constexpr (FP64) {
+    for (int64_t j = threadIdx.x; j < n; j += kBThreads) {
+      const int64_t m = pp.seg_begin + j;
+      double g[3] = {0, 0, 0}, q0[3] = {0, 0, 0}, q1[3] = {0, 0, 0}, N[3] = {0, 0, 0};
+      if (corner_ok(m)) {
+        double P[3][3];
+        bool fin = true;
+        for (int k = 0; k < 3; ++k)
+          for (int d = 0; d < 3; ++d) {
+            P[k][d] = (double)v[3 * (int64_t)f[3 * m + k] + d] - c[d];
+            fin = fin && isfinite(P[k][d]);
+          }
+        if (fin) {
+          for (int d = 0; d < 3; ++d) {
+            g[d] = (P[0][d] + P[1][d] + P[2][d]) / 3.0;
+            q0[d] = P[0][d] - g[d];
+            q1[d] = P[1][d] - g[d];
+          }
+          const double e1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+          const double e2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+          N[0] = e1[1] * e2[2] - e1[2] * e2[1];
+          N[1] = e1[2] * e2[0] - e1[0] * e2[2];
+          N[2] = e1[0] * e2[1] - e1[1] * e2[0];
+          vol += (P[0][0] * (P[1][1] * P[2][2] - P[1][2] * P[2][1]) +
+                  P[0][1] * (P[1][2] * P[2][0] - P[1][0] * P[2][2]) +
+                  P[0][2] * (P[1][0] * P[2][1] - P[1][1] * P[2][0])) / 6.0;
+          double r2 = 0.0;
+          for (int k = 0; k < 3; ++k) r2 = fmax(r2, P[k][0] * P[k][0] + P[k][1] * P[k][1] + P[k][2] * P[k][2]);
+          rm = fmaxf(rm, __double2float_ru(sqrt(r2)));
         }
-      if (fin) {
-        for (int d = 0; d < 3; ++d) {
-          g[d] = (P[0][d] + P[1][d] + P[2][d]) / 3.0;
-          q0[d] = P[0][d] - g[d];
-          q1[d] = P[1][d] - g[d];
-        }
-        const double e1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
-        const double e2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
-        N[0] = e1[1] * e2[2] - e1[2] * e2[1];
-        N[1] = e1[2] * e2[0] - e1[0] * e2[2];
-        N[2] = e1[0] * e2[1] - e1[1] * e2[0];
-        vol += (P[0][0] * (P[1][1] * P[2][2] - P[1][2] * P[2][1]) +
-                P[0][1] * (P[1][2] * P[2][0] - P[1][0] * P[2][2]) +
-                P[0][2] * (P[1][0] * P[2][1] - P[1][1] * P[2][0])) / 6.0;
-        double r2 = 0.0;
-        for (int k = 0; k < 3; ++k) r2 = fmax(r2, P[k][0] * P[k][0] + P[k][1] * P[k][1] + P[k][2] * P[k][2]);
-        rm = fmaxf(rm, __double2float_ru(sqrt(r2)));
       }
-    }
-    if (FP64) {
       reinterpret_cast<Face64*>(recs)[m] = Face64{g[0], g[1], g[2], q0[0], q0[1], q0[2], q1[0], q1[1], q1[2],
                                                   N[0], N[1], N[2]};
-    } else {
-      reinterpret_cast<Face32*>(recs)[m] =
-          Face32{(float)g[0], (float)g[1], (float)g[2], (float)q0[0], (float)q0[1], (float)q0[2],
-                 (float)q1[0], (float)q1[1], (float)q1[2], (float)N[0], (float)N[1], (float)N[2]};
     }
+  } else {
+    // FP32 records without FP64 arithmetic, as k_bprep: each centred corner is a float pair
+    // s + t (TwoSum of the vertex and the centre's high part, less its low part); the centroid is
+    // rounded once from the pair sum over 3 (the remainder of the rounded quotient is exact through
+    // its FMA), q0, q1 and the edges from TwoSum differences, N = e1 x e2 with Kahan's FMA form of
+    // each 2 x 2 determinant.  The volume is the records' own: det(P0, P1, P2) = g . N for the
+    // centroid g and N = (P1 - P0) x (P2 - P0), so it is the compensated sum of g . N over 6, each
+    // product split exactly by its FMA.  Radius bound as in 2D.
+    float chi[3], clo[3];
+    for (int d = 0; d < 3; ++d) {
+      chi[d] = __double2float_rn(c[d]);
+      clo[d] = __double2float_rn(c[d] - (double)chi[d]);
+    }
+    auto det2 = [](float a, float b, float cc, float dd) {   // a b - cc dd
+      const float w = cc * dd;
+      return fmaf(a, b, -w) + fmaf(-cc, dd, w);
+    };
+    CAcc va;
+    va.init();
+    for (int64_t j = threadIdx.x; j < n; j += kBThreads) {
+      const int64_t m = pp.seg_begin + j;
+      float G[3] = {0.f, 0.f, 0.f}, Q0[3] = {0.f, 0.f, 0.f}, Q1[3] = {0.f, 0.f, 0.f}, Nn[3] = {0.f, 0.f, 0.f};
+      if (corner_ok(m)) {
+        float sp[3][3], tp[3][3];
+        bool fin = true;
+        for (int k = 0; k < 3; ++k)
+          for (int d = 0; d < 3; ++d) {
+            const float x = v[3 * (int64_t)f[3 * m + k] + d];
+            fin = fin && isfinite(x);
+            float e;
+            two_sum(x, -chi[d], sp[k][d], e);
+            tp[k][d] = e - clo[d];
+          }
+        if (fin) {
+          float e1[3], e2[3];
+          for (int d = 0; d < 3; ++d) {
+            float a, ea, b, eb;
+            two_sum(sp[0][d], sp[1][d], a, ea);
+            two_sum(a, sp[2][d], b, eb);
+            const float lo = (ea + eb) + (tp[0][d] + tp[1][d] + tp[2][d]);
+            const float gh = b / 3.0f;
+            G[d] = gh + (fmaf(-gh, 3.0f, b) + lo) / 3.0f;
+            float x, ex;
+            two_sum(sp[0][d], -G[d], x, ex);
+            Q0[d] = x + (ex + tp[0][d]);
+            two_sum(sp[1][d], -G[d], x, ex);
+            Q1[d] = x + (ex + tp[1][d]);
+            two_sum(sp[1][d], -sp[0][d], x, ex);
+            e1[d] = x + (ex + (tp[1][d] - tp[0][d]));
+            two_sum(sp[2][d], -sp[0][d], x, ex);
+            e2[d] = x + (ex + (tp[2][d] - tp[0][d]));
+          }
+          Nn[0] = det2(e1[1], e2[2], e1[2], e2[1]);
+          Nn[1] = det2(e1[2], e2[0], e1[0], e2[2]);
+          Nn[2] = det2(e1[0], e2[1], e1[1], e2[0]);
+          for (int d = 0; d < 3; ++d) {
+            const float pr = G[d] * Nn[d];
+            va.add(pr);
+            va.add(fmaf(G[d], Nn[d], -pr));
+          }
+          for (int k = 0; k < 3; ++k)
+            rm = fmaxf(rm, sqrtf(fmaf(sp[k][0], sp[k][0], fmaf(sp[k][1], sp[k][1], sp[k][2] * sp[k][2]))) * 1.000001f);
+        }
+      }
+      reinterpret_cast<Face32*>(recs)[m] = Face32{G[0], G[1], G[2], Q0[0], Q0[1], Q0[2], Q1[0], Q1[1], Q1[2],
+                                                  Nn[0], Nn[1], Nn[2]};
+    }
+    vol = ((double)va.hi + (double)va.lo) / 6.0;
   }
   vol = bsum(vol, shd);
   rm = bminmax(rm, true, shf);
