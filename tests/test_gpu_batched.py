@@ -179,3 +179,27 @@ def test_default_shape_on_a_large_shared_grid_is_bitwise_the_same(torch_dev):
         vi = v[off[i]:off[i + 1]]
         ref = oracle.ft2d(vi, q)
         assert np.max(np.abs(got[i] - ref)) / abs(ref[np.flatnonzero(np.all(q == 0, axis=1))[0]]) < TOL["fp32"], i
+
+
+@pytest.mark.parametrize("shape", [None, (4, 128)])
+def test_far_from_the_origin_phase_reduction(torch_dev, shape):
+    """Polygons centred about 3e3 and 1e5 from the origin: the translation phase Q.c reaches about
+    1.7e5 rad, which the FP32 finish reduces from a float-float Q.c in two parts, and about 6e6 rad,
+    beyond 2^20 rad, where it takes the FP64 finish; one polygon of 5,000 vertices (two chunks) goes
+    through the multi-chunk finish.  Every polygon against the oracle within 1e-5 of its area."""
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    specs = [(64, (2500.0, -1800.0)), (5000, (-3100.0, 2000.0)), (300, (90000.0, -60000.0)), (17, (1.5, 0.5))]
+    parts = [synth.star_polygon(n, seed=40 + k, center=c) for k, (n, c) in enumerate(specs)]
+    off = np.zeros(len(parts) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([p.shape[0] for p in parts])
+    v = np.concatenate(parts).astype(np.float32)
+    rng = np.random.default_rng(41)
+    q = np.concatenate([[[0.0, 0.0], [0.3, -0.2]], rng.uniform(-40, 40, (600, 2))])
+    opts = None if shape is None else {"q_per_thread": shape[0], "block_threads": shape[1]}
+    got = _c(pft.pft2d_polygons_batched(torch.from_numpy(v).to(dev), torch.from_numpy(off),
+                                        torch.from_numpy(q).to(dev), options=opts, check_status=True))
+    areas = _areas(v, off)
+    for i in range(len(parts)):
+        ref = oracle.ft2d(v[off[i]:off[i + 1]], q)
+        assert np.max(np.abs(got[i] - ref)) / areas[i] < TOL["fp32"], i

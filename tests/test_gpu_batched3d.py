@@ -183,3 +183,31 @@ def test_default_shape_on_a_large_shared_grid_is_bitwise_the_same(torch_dev):
         ref = oracle.ft3d(vi, fi, q)
         vol = abs(oracle.ft3d(vi, fi, [[0.0, 0.0, 0.0]])[0])
         assert np.max(np.abs(got[i] - ref)) / vol < TOL["fp32"], i
+
+
+def test_far_from_the_origin_phase_reduction(torch_dev, rng):
+    """Meshes centred about 2e3 and 6e4 from the origin: Q.c reaches about 1e5 rad (the FP32 finish's
+    float-float reduction) and about 3e6 rad (beyond 2^20 rad: the FP64 finish); a 20,480-face mesh
+    (5 chunks) goes through the multi-chunk finish.  Each mesh against the oracle within 1e-5 of its
+    volume."""
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    shifts = [((1500.0, -2200.0, 800.0), 2), ((-1200.0, 900.0, 1700.0), 5), ((40000.0, 30000.0, -50000.0), 1)]
+    vs, fs, off = [], [], [0]
+    base = 0
+    for k, (sh, level) in enumerate(shifts):
+        vk, fk = synth.perturbed_icosphere(level, seed=50 + k, amp=0.03)
+        vs.append((vk.astype(np.float64) + np.array(sh)).astype(np.float32))
+        fs.append(fk + base)
+        base += vk.shape[0]
+        off.append(off[-1] + fk.shape[0])
+    v = np.concatenate(vs).astype(np.float32)
+    f = np.concatenate(fs).astype(np.int32)
+    off = np.array(off, dtype=np.int64)
+    q = _q_mix(rng, 400, 25.0)
+    got = _c(pft.pft3d_meshes_batched(torch.from_numpy(v).to(dev), torch.from_numpy(f).to(dev), off,
+                                      torch.from_numpy(q).to(dev), check_status=True))
+    for i in range(off.size - 1):
+        vi, fi = _mesh(v, f, off, i)
+        ref = oracle.ft3d(vi, fi, q)
+        assert np.max(np.abs(got[i] - ref)) / abs(ref[0]) < TOL["fp32"], i
