@@ -467,7 +467,8 @@ def bench_batched(dev, warmup, steps):
     rl = roofline2d(pairs, ms / 1e3, sfu_sinc_fraction(w.verts, w.poly_off, w.q),
                     torch.cuda.get_device_properties(dev).multi_processor_count, float(pk.get("sm_max_mhz", 2070.0)),
                     paired=tuned["q_per_thread"] % 2 == 0)
-    rl["note"] = ("whole 4-launch call timed; the finish of the 16.8M outputs (2/|Q|^2, e^{iQ.c}) "
+    rl["note"] = (f"whole {int(launches)}-launch call timed; the finish of the 16.8M outputs (2/|Q|^2, "
+                  "e^{iQ.c}) "
                   "is outside the per-pair count")
     # the plain FP64 GPU path on the same batch (one call), and the FP32 result's deviation from it
     p64 = pft.pft2d_batched_prepare(w.poly_off, w.q.shape[0], options={"precision": "fp64"}, device=dev)

@@ -57,10 +57,12 @@ struct PolyInfo {       // written by k_bprep / k_bprep3: centre, area or volume
 };
 
 struct BLayout {
-  size_t plan_hdr, cta_off, items, pplan, mc, info, segs, partial, small, qperm, qscratch, total;
+  size_t plan_hdr, cta_off, items, pplan, mc, info, segs, partial, small, qperm, qscratch, qlo, total;
 };
 
 inline size_t al(size_t x) { return (x + 255) / 256 * 256; }
+// q - (float)q per Q coordinate (FP32 policies): the FP32 finish's phase Q.c takes the caller's Q
+inline size_t qlo_bytes(int64_t dim, int64_t n_q) { return sizeof(float) * (size_t)dim * (size_t)std::max<int64_t>(n_q, 1); }
 
 BLayout layout(int dim, int64_t n_polys, int64_t n_verts, int64_t n_items, int64_t n_cta, int64_t n_mc,
                int64_t part_rows, int64_t n_out, bool fp64, int64_t n_q, bool q_tiled) {
@@ -79,6 +81,9 @@ BLayout layout(int dim, int64_t n_polys, int64_t n_verts, int64_t n_items, int64
   if (q_tiled) {
     y.qperm = o;    o = al(o + sizeof(int32_t) * (size_t)n_q);
     y.qscratch = o; o = al(o + qorder_layout(n_q).total);
+  }
+  if (!fp64) {   // the last region, so that its offset follows from the total: the low parts of Q
+    y.qlo = o;  o = al(o + qlo_bytes(dim, n_q));
   }
   y.total = o;
   return y;
@@ -565,14 +570,17 @@ constexpr float kTwoPiLo = -1.7484555314695172e-07f;        // 2 pi - kTwoPiHi, 
 
 // The same finish for the FP32 policies' single-chunk outputs, without FP64 arithmetic: GB300 runs
 // FP64 at a small fraction of its FP32 rate, and all warps of a block reach this together at the end
-// of every item.  Q.c is carried as s + t (the products with hi exact through their FMA residuals,
-// the lo products and the residuals in t), k = rint(s / 2 pi), and s - k 2pi_hi is exact in FP32 (both
+// of every item.  The phase takes the caller's Q, Q + Qlo (Q rounded to float, as the pair sums used
+// it, and the low part q - (float)q from k_bqlo): a shape far from the origin would otherwise see
+// its phase moved by |c| times the rounding of Q.  Q.c is carried as s + t (the products Q c_hi exact
+// through their FMA residuals; Q c_lo, Qlo c_hi and the residuals in t), k = rint(s / 2 pi), and s - k 2pi_hi is exact in FP32 (both
 // are multiples of 2^-21 and the difference is below 4 in magnitude), so the reduced phase carries one
 // rounding, as the FP64 reduction cast to FP32 does; sincosf of it, the factor s/|Q|^2 and the
 // rotation of hi + lo in FP32: about 3e-7 of |F| against ~1e-7 for the sums themselves.  Phases
 // beyond 2^20 rad take the FP64 finish.
 template <int D>
-__device__ __forceinline__ void finish_out_f32(const float* Q, const CAcc& re, const CAcc& im, const PolyInfo& pi,
+__device__ __forceinline__ void finish_out_f32(const float* Q, const float* Qlo, const CAcc& re, const CAcc& im,
+                                               const PolyInfo& pi,
                                                const CenterF& cf, int64_t row, double* out, uint32_t* small,
                                                WsHeader* h) {
   bool zero = true;
@@ -603,9 +611,10 @@ __device__ __forceinline__ void finish_out_f32(const float* Q, const CAcc& re, c
     t += e2 + e;
   }
 #pragma unroll
-  for (int d = 0; d < D; ++d) t = fmaf(Q[d], cf.lo[d], t);
+  for (int d = 0; d < D; ++d) t = fmaf(Qlo[d], cf.hi[d], fmaf(Q[d], cf.lo[d], t));
   if (!(fabsf(s) < 1048576.f)) {
-    const double Qd[3] = {(double)Q[0], (double)Q[1], D == 3 ? (double)Q[2] : 0.0};
+    const double Qd[3] = {(double)Q[0] + (double)Qlo[0], (double)Q[1] + (double)Qlo[1],
+                          D == 3 ? (double)Q[2] + (double)Qlo[2] : 0.0};
     finish_out<D, true>(Qd, (double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo, pi, row, out, small, h);
     return;
   }
@@ -638,7 +647,7 @@ __global__ void __launch_bounds__(NT, kBatchedMinBlocks<Pol, R, NT>) k_batched(
     const BPlanHeader* __restrict__ ph, const int32_t* __restrict__ cta_off, const BItem* __restrict__ items,
     const PolyPlan* __restrict__ pplan, const PolyInfo* __restrict__ info, const typename Pol::Item* __restrict__ segs,
     const double* __restrict__ q, double2* __restrict__ partial, double* __restrict__ out, uint32_t* small,
-    WsHeader* h, Thr th, const int32_t* __restrict__ qperm) {
+    WsHeader* h, Thr th, const int32_t* __restrict__ qperm, const float* __restrict__ qlo) {
   using Item = typename Pol::Item;
   using QT = typename Pol::QT;
   constexpr int TILE = Pol::kTile;
@@ -771,7 +780,10 @@ __global__ void __launch_bounds__(NT, kBatchedMinBlocks<Pol, R, NT>) k_batched(
         else
           partial[at_] = acc.get(r);
       } else if constexpr (kF32) {
-        finish_out_f32<D>(qr[r], acc.re[r], acc.im[r], pi, cf, pp.out_base + local, out, small, h);
+        float ql[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int d = 0; d < D; ++d) ql[d] = qlo[D * (pp.q_begin + local) + d];
+        finish_out_f32<D>(qr[r], ql, acc.re[r], acc.im[r], pi, cf, pp.out_base + local, out, small, h);
       } else {
         const double2 f = acc.get(r);
         const double Qd[3] = {(double)qr[r][0], (double)qr[r][1], (double)qr[r][2]};
@@ -788,6 +800,12 @@ __global__ void __launch_bounds__(NT, kBatchedMinBlocks<Pol, R, NT>) k_batched(
   }
 }
 
+// The low parts q - (float)q of the caller's Q coordinates (FP32 policies), for the finish's phase.
+__global__ void __launch_bounds__(kBThreads) k_bqlo(const double* __restrict__ q, int64_t n, float* __restrict__ qlo) {
+  const int64_t i = blockIdx.x * (int64_t)kBThreads + threadIdx.x;
+  if (i < n) qlo[i] = __double2float_rn(q[i] - (double)__double2float_rn(q[i]));
+}
+
 // Multi-chunk shapes: fixed-order sum of their chunk partials, then the finish.  The FP32
 // policies' partials are compensated float pairs, added in the same compensated accumulator and
 // finished in FP32 (as the single-chunk outputs are); the FP64 policies' are doubles.
@@ -795,7 +813,7 @@ __global__ void __launch_bounds__(kBThreads) k_bfinal(const BPlanHeader* ph, con
                                                       const PolyPlan* __restrict__ pplan,
                                                       const PolyInfo* __restrict__ info, const double* __restrict__ q,
                                                       const double2* __restrict__ partial, double* out,
-                                                      uint32_t* small, WsHeader* h) {
+                                                      uint32_t* small, WsHeader* h, const float* __restrict__ qlo) {
   const int i = mc[blockIdx.x];
   const PolyPlan pp = pplan[i];
   const PolyInfo pi = info[i];
@@ -816,10 +834,14 @@ __global__ void __launch_bounds__(kBThreads) k_bfinal(const BPlanHeader* ph, con
         im.add(p.w);
       }
       const int64_t iq = pp.q_begin + l;
-      float Q[3] = {0.f, 0.f, 0.f};
-      for (int d = 0; d < D; ++d) Q[d] = (float)q[D * iq + d];
-      if (D == 2) finish_out_f32<2>(Q, re, im, pi, cf, pp.out_base + l, out, small, h);
-      else finish_out_f32<3>(Q, re, im, pi, cf, pp.out_base + l, out, small, h);
+      float Q[3], ql[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        Q[d] = d < D ? (float)q[D * iq + d] : 0.f;
+        ql[d] = d < D ? qlo[D * iq + d] : 0.f;
+      }
+      if (D == 2) finish_out_f32<2>(Q, ql, re, im, pi, cf, pp.out_base + l, out, small, h);
+      else finish_out_f32<3>(Q, ql, re, im, pi, cf, pp.out_base + l, out, small, h);
     }
     return;
   }
@@ -864,8 +886,7 @@ __global__ void __launch_bounds__(kBThreads) k_bsmall(const float* __restrict__ 
     }
     const PolyPlan pp = pplan[i];
     const PolyInfo pi = info[i];
-    const double qx = ph->fp64 ? q[2 * iq] : (double)(float)q[2 * iq];
-    const double qy = ph->fp64 ? q[2 * iq + 1] : (double)(float)q[2 * iq + 1];
+    const double qx = q[2 * iq], qy = q[2 * iq + 1];   // the caller's Q (FP64 series, either precision)
     double re = 0.0, im = 0.0;
     for (int64_t j = threadIdx.x; j < pp.n_seg; j += kBThreads) {
       const int64_t a = pp.seg_begin + j, b = pp.seg_begin + (j + 1 < pp.n_seg ? j + 1 : 0);
@@ -929,7 +950,7 @@ __global__ void __launch_bounds__(kBThreads) k_bsmall3(const float* __restrict__
     const PolyInfo pi = info[i];
     const double c[3] = {pi.cx, pi.cy, pi.cz};
     double Q[3];
-    for (int d = 0; d < 3; ++d) Q[d] = ph->fp64 ? q[3 * iq + d] : (double)(float)q[3 * iq + d];
+    for (int d = 0; d < 3; ++d) Q[d] = q[3 * iq + d];   // the caller's Q (FP64 series, either precision)
     double re = 0.0, im = 0.0;
     for (int64_t j = threadIdx.x; j < pp.n_seg; j += kBThreads) {
       const int64_t m = pp.seg_begin + j;
@@ -970,10 +991,10 @@ template <class Pol, int R, int NT>
 cudaError_t launch_batched_one(int grid, const BPlanHeader* ph, const int32_t* cta_off, const BItem* items,
                                const PolyPlan* pplan, const PolyInfo* info, const void* segs, const double* q,
                                double2* partial, double* out, uint32_t* small, WsHeader* h, Thr th, cudaStream_t st,
-                               const int32_t* qperm) {
+                               const int32_t* qperm, const float* qlo) {
   k_batched<Pol, R, NT><<<grid, NT, 0, st>>>(ph, cta_off, items, pplan, info,
                                              static_cast<const typename Pol::Item*>(segs), q, partial, out, small, h,
-                                             th, qperm);
+                                             th, qperm, qlo);
   return cudaGetLastError();
 }
 
@@ -1006,11 +1027,11 @@ int batched_blocks_per_sm(int dim, bool fp64, int r, int nt) {
 cudaError_t launch_batched(int dim, bool fp64, int r, int nt, int grid, const BPlanHeader* ph, const int32_t* cta_off,
                            const BItem* items, const PolyPlan* pplan, const PolyInfo* info, const void* segs,
                            const double* q, double2* partial, double* out, uint32_t* small, WsHeader* h, Thr th,
-                           cudaStream_t st, const int32_t* qperm) {
+                           cudaStream_t st, const int32_t* qperm, const float* qlo) {
 #define X(P, RR, NN)                                                                                      \
   if (PFT_BATCHED_MATCH(P, RR, NN))                                                                      \
     return launch_batched_one<P, RR, NN>(grid, ph, cta_off, items, pplan, info, segs, q, partial, out, small, h, \
-                                         th, st, qperm);
+                                         th, st, qperm, qlo);
   PFT_BATCHED_CASES(X)
 #undef X
   return cudaErrorInvalidConfiguration;
@@ -1112,14 +1133,25 @@ int run_rest(const PlanHandle& p, void* ws, const double* q, double* out, WsHead
                       &g_batched_launches) != cudaSuccess)
       return PFT_ERR_CUDA;
   }
+  float* qlo = nullptr;
+  if (p.fp64 == 0) {   // the last region of the workspace
+    qlo = at<float>(ws, (size_t)p.total - qlo_bytes(p.dim, p.n_q));
+    const int64_t n = p.dim * p.n_q;
+    if (n > 0) {
+      k_bqlo<<<(unsigned)((n + kBThreads - 1) / kBThreads), kBThreads, 0, st>>>(q, n, qlo);
+      if (cudaGetLastError() != cudaSuccess) return PFT_ERR_CUDA;
+      ++g_batched_launches;
+    }
+  }
   if (launch_batched((int)p.dim, p.fp64 != 0, (int)p.r, (int)p.nt, (int)p.grid, phd,
                      at<int32_t>(ws, (size_t)p.cta_off), at<BItem>(ws, (size_t)p.items), pplan, info,
-                     at<void>(ws, (size_t)p.segs), q, partial, out, small, h, plan_thr(p), st, qperm) != cudaSuccess)
+                     at<void>(ws, (size_t)p.segs), q, partial, out, small, h, plan_thr(p), st, qperm,
+                     qlo) != cudaSuccess)
     return PFT_ERR_CUDA;
   ++g_batched_launches;
   if (p.n_mc > 0) {
     k_bfinal<<<(unsigned)p.n_mc, kBThreads, 0, st>>>(phd, at<int32_t>(ws, (size_t)p.mc), pplan, info, q, partial,
-                                                      out, small, h);
+                                                      out, small, h, qlo);
     if (cudaGetLastError() != cudaSuccess) return PFT_ERR_CUDA;
     ++g_batched_launches;
   }

@@ -468,9 +468,14 @@ __global__ void k_bq(const double* __restrict__ q, const double* __restrict__ g,
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // record slot
   if (s >= n_q) return;
   const int64_t i = perm ? (int64_t)perm[s] : s;                      // its Q point (caller's index)
+  // the record holds Q rounded to float (the pair kernels' Q); the weight's phase and 1/|Q|^2 take
+  // the caller's Q, as the forward's finish does
   float qf[3] = {0.f, 0.f, 0.f};
-  for (int d = 0; d < D; ++d) qf[d] = (float)q[D * i + d];
-  const double Q[3] = {qf[0], qf[1], qf[2]};
+  double Q[3] = {0.0, 0.0, 0.0};
+  for (int d = 0; d < D; ++d) {
+    Q[d] = q[D * i + d];
+    qf[d] = (float)Q[d];
+  }
   const double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
   QRec r{qf[0], qf[1], qf[2], 0.f, 0.f, 0.f, 0.f, 0.f};
   const double rmax = (double)__uint_as_float(h->rmax_bits);
@@ -555,7 +560,7 @@ __global__ void k_qfinal(const double* __restrict__ q, const double* __restrict_
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n_q) return;
   double Q[3];
-  for (int d = 0; d < 3; ++d) Q[d] = (double)(float)q[3 * i + d];   // the Q the FP32 pairs used
+  for (int d = 0; d < 3; ++d) Q[d] = q[3 * i + d];   // the caller's Q (factors and phase in FP64)
   const double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
   const double rmax = (double)__uint_as_float(h->rmax_bits);
   if (q2 == 0.0 || sqrt(q2) * rmax < kTauSmallQ) return;   // k_qsmall's (same test as k_bq)
@@ -615,7 +620,7 @@ __global__ void __launch_bounds__(kAux) k_qsmall_part(const float* __restrict__ 
     const int64_t e = u / nch, ch = u % nch;
     const int64_t i = list[e];
     double Q[3];
-    for (int d = 0; d < 3; ++d) Q[d] = (double)(float)q[3 * i + d];
+    for (int d = 0; d < 3; ++d) Q[d] = q[3 * i + d];
     double acc[kQsF] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int64_t m1 = min(nf, (ch + 1) * per);
     for (int64_t m = ch * per + threadIdx.x; m < m1; m += kAux) {
@@ -662,7 +667,7 @@ __global__ void k_qsmall_fin(int64_t nf, const double* __restrict__ q, const dou
     for (int64_t ch = 0; ch < nch; ++ch)
       for (int k = 0; k < kQsF; ++k) acc[k] += part[(e * nch + ch) * kQsF + k];
     double Q[3];
-    for (int d = 0; d < 3; ++d) Q[d] = (double)(float)q[3 * i + d];
+    for (int d = 0; d < 3; ++d) Q[d] = q[3 * i + d];
     double sp, cp;
     sincos(Q[0] * c[0] + Q[1] * c[1] + Q[2] * c[2], &sp, &cp);
     const double gr = g[2 * i], gi = g[2 * i + 1];
@@ -752,7 +757,7 @@ __global__ void k_qfinal2d(const double* __restrict__ q, const double* __restric
                            const double* __restrict__ partial, int ks, const WsHeader* h, double* __restrict__ out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n_q) return;
-  const double Q[2] = {(double)(float)q[2 * i], (double)(float)q[2 * i + 1]};   // as the FP32 pairs used it
+  const double Q[2] = {q[2 * i], q[2 * i + 1]};   // the caller's Q (factors and phase in FP64)
   const double q2 = Q[0] * Q[0] + Q[1] * Q[1];
   const double rmax = (double)__uint_as_float(h->rmax_bits);
   if (q2 == 0.0 || sqrt(q2) * rmax < kTauSmallQ) return;   // k_qsmall2d's (same test as k_bq)
@@ -788,7 +793,7 @@ __global__ void __launch_bounds__(kAux) k_qsmall2d_part(const float* __restrict_
   for (int64_t u = blockIdx.x; u < (int64_t)count * nch; u += gridDim.x) {
     const int64_t e = u / nch, ch = u % nch;
     const int64_t i = list[e];
-    const double Q[2] = {(double)(float)q[2 * i], (double)(float)q[2 * i + 1]};
+    const double Q[2] = {q[2 * i], q[2 * i + 1]};
     double acc[kQsF2] = {0, 0, 0, 0, 0, 0};
     const int64_t j1 = min(nv, (ch + 1) * per);
     for (int64_t j = ch * per + threadIdx.x; j < j1; j += kAux) {
@@ -835,7 +840,7 @@ __global__ void k_qsmall2d_fin(int64_t nv, const double* __restrict__ q, const d
     double acc[kQsF2] = {0, 0, 0, 0, 0, 0};
     for (int64_t ch = 0; ch < nch; ++ch)
       for (int k = 0; k < kQsF2; ++k) acc[k] += part[(e * nch + ch) * kQsF2 + k];
-    const double Q[2] = {(double)(float)q[2 * i], (double)(float)q[2 * i + 1]};
+    const double Q[2] = {q[2 * i], q[2 * i + 1]};
     double sp, cp;
     sincos(Q[0] * c[0] + Q[1] * c[1], &sp, &cp);
     const double gr = g[2 * i], gi = g[2 * i + 1];
@@ -963,7 +968,7 @@ __global__ void k_bvert2d(const float* __restrict__ v, int64_t nv, const int64_t
     const double pp[2] = {(double)v[2 * jp] - c[0], (double)v[2 * jp + 1] - c[1]};
     for (uint32_t e = 0; e < ns; ++e) {   // fixed order is not needed for a plain sum of a few terms, but kept
       const int64_t iq = small[e];
-      const double qx = (double)(float)q[2 * iq], qy = (double)(float)q[2 * iq + 1];
+      const double qx = q[2 * iq], qy = q[2 * iq + 1];
       const double phc = qx * c[0] + qy * c[1];
       double d0[2] = {0, 0}, d1[2] = {0, 0}, e0[2] = {0, 0}, e1[2] = {0, 0};
       seg_small(pj, pn, qx, qy, g[2 * iq], g[2 * iq + 1], phc, d0, d1);   // j is the start
@@ -1086,9 +1091,10 @@ __global__ void __launch_bounds__(kAux) k_bbq(const double* __restrict__ q, cons
     const int64_t l = l0 + threadIdx.x;
     bool is_small = false;
     if (l < nqi) {
-      const float qx = (float)q[D * (qb + l)], qy = (float)q[D * (qb + l) + 1];
-      const float qz = D == 3 ? (float)q[D * (qb + l) + D - 1] : 0.f;
-      const double Qx = qx, Qy = qy, Qz = qz, q2 = Qx * Qx + Qy * Qy + Qz * Qz;
+      // the record holds Q rounded to float; the weight's phase and factor take the caller's Q
+      const double Qx = q[D * (qb + l)], Qy = q[D * (qb + l) + 1], Qz = D == 3 ? q[D * (qb + l) + D - 1] : 0.0;
+      const float qx = (float)Qx, qy = (float)Qy, qz = (float)Qz;
+      const double q2 = Qx * Qx + Qy * Qy + Qz * Qz;
       QRec r{qx, qy, qz, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (q2 == 0.0 || q2 * ((double)P.rmax * (double)P.rmax) < kTauSmallQ * kTauSmallQ) {
         is_small = true;
@@ -1240,7 +1246,7 @@ __global__ void k_bbvert(const float* __restrict__ v, int64_t nv, const int64_t*
     const double pp[2] = {(double)v[2 * jp] - c[0], (double)v[2 * jp + 1] - c[1]};
     for (int32_t e = 0; e < ns; ++e) {
       const int64_t l = small[gb + e];
-      const double qx = (double)(float)q[2 * (qb + l)], qy = (double)(float)q[2 * (qb + l) + 1];
+      const double qx = q[2 * (qb + l)], qy = q[2 * (qb + l) + 1];
       const double phc = qx * c[0] + qy * c[1];
       const double gr = g[2 * (gb + l)], gi = g[2 * (gb + l) + 1];
       double d0[2] = {0, 0}, d1[2] = {0, 0}, e0[2] = {0, 0}, e1[2] = {0, 0};
@@ -1460,7 +1466,7 @@ __device__ void corner_adj(int64_t m, const float* __restrict__ v, int64_t nv, c
     const double N[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
     for (uint32_t e = 0; e < ns; ++e) {
       const int64_t iq = q_base + small[e], ig = g_base + small[e];
-      const double Q[3] = {(double)(float)q[3 * iq], (double)(float)q[3 * iq + 1], (double)(float)q[3 * iq + 2]};
+      const double Q[3] = {q[3 * iq], q[3 * iq + 1], q[3 * iq + 2]};
       const double al[3] = {Q[0] * P[0][0] + Q[1] * P[0][1] + Q[2] * P[0][2],
                             Q[0] * P[1][0] + Q[1] * P[1][1] + Q[2] * P[1][2],
                             Q[0] * P[2][0] + Q[1] * P[2][1] + Q[2] * P[2][2]};

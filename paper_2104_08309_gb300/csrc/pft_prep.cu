@@ -259,7 +259,10 @@ __global__ void k_finalize(int dim, const double* __restrict__ q, int64_t n_q, c
   double Q[3] = {0, 0, 0};
   for (int d = 0; d < dim; ++d) {
     double x = q[dim * i + d];
-    Q[d] = fp64 ? x : (double)(float)x;   // the FP32 path evaluated the sum at Q rounded to float
+    // the caller's Q: the FP32 pair sums ran at Q rounded to float in coordinates centred on the
+    // bounding box, where that moves them by ~1e-7 of |S|; in the phase Q.c the same rounding would
+    // move the result by |c| times it, which for a shape far from the origin is not small
+    Q[d] = x;
   }
   const double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
   if (q2 == 0.0) {
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_smallq3d(const float* __restr
   for (uint32_t e = blockIdx.x; e < count; e += gridDim.x) {
     const int64_t i = list[e];
     double Q[3];
-    for (int d = 0; d < 3; ++d) Q[d] = fp64 ? q[3 * i + d] : (double)(float)q[3 * i + d];
+    for (int d = 0; d < 3; ++d) Q[d] = q[3 * i + d];   // the caller's Q (FP64 series)
     double re = 0.0, im = 0.0;
     for (int64_t m = threadIdx.x; m < nf; m += kSmallThreads) {
       const int32_t id[3] = {f[3 * m], f[3 * m + 1], f[3 * m + 2]};
@@ -347,7 +350,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_smallq2d(const float* __restr
   for (uint32_t e = blockIdx.x; e < count; e += gridDim.x) {
     const int64_t i = list[e];
     double Q[2];
-    for (int d = 0; d < 2; ++d) Q[d] = fp64 ? q[2 * i + d] : (double)(float)q[2 * i + d];
+    for (int d = 0; d < 2; ++d) Q[d] = q[2 * i + d];   // the caller's Q (FP64 series)
     double re = 0.0, im = 0.0;
     for (int64_t j = threadIdx.x; j < nv; j += kSmallThreads) {
       int64_t lo = 0, hi = nl;

@@ -135,3 +135,26 @@ def test_c4_full_size_sampled_vertices(torch_dev):
     again = pft.pft3d_mesh_backward(torch.from_numpy(w.verts).to(dev), torch.from_numpy(w.faces).to(dev),
                                     torch.from_numpy(w.q).to(dev), torch.from_numpy(_g_pairs(g)).to(dev)).cpu().numpy()
     assert np.array_equal(got, again)
+
+
+def test_far_from_the_origin(torch_dev, rng):
+    """The adjoints of shapes thousands of units from the origin, at Q that float32 cannot represent:
+    the Q records' weights g e^{-iQ.c}/|Q|^2 take the caller's Q, as the forward's finish does."""
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    v = synth.star_polygon(200, seed=4, center=(2500.0, -1800.0)).astype(np.float32)
+    q = np.concatenate([[[1e-5, 2e-5], [0.3, -0.2]], rng.uniform(-30, 30, (1500, 2))])
+    g = rng.normal(size=q.shape[0]) + 1j * rng.normal(size=q.shape[0])
+    ref = oracle.grad2d(v, q, g)
+    got = pft.pft2d_polygons_backward(torch.from_numpy(v).to(dev), torch.from_numpy(q).to(dev),
+                                      torch.from_numpy(_g_pairs(g)).to(dev), check_status=True).cpu().numpy()
+    assert _rel(got, ref) < GTOL
+    v, f = synth.perturbed_icosphere(2, seed=12, amp=0.08)
+    v = (v.astype(np.float64) + np.array([1500.0, -2200.0, 800.0])).astype(np.float32)
+    q = np.concatenate([[[1e-5, 0, 2e-5], [0.3, -0.2, 0.1]], rng.uniform(-25, 25, (1200, 3))])
+    g = rng.normal(size=q.shape[0]) + 1j * rng.normal(size=q.shape[0])
+    ref = oracle.grad3d(v, f, q, g)
+    got = pft.pft3d_mesh_backward(torch.from_numpy(v).to(dev), torch.from_numpy(f).to(dev),
+                                  torch.from_numpy(q).to(dev), torch.from_numpy(_g_pairs(g)).to(dev),
+                                  check_status=True).cpu().numpy()
+    assert _rel(got, ref) < GTOL

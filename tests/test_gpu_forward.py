@@ -271,3 +271,20 @@ def test_degenerate_faces_and_segments(torch_dev, prec, rng):
     ref2 = oracle.ft2d(p, q2)
     got2 = run2d(torch_dev, p2, q2, precision=prec)
     assert rel_err(got2, ref2, ref2[0]) < TOL[prec]
+
+
+def test_far_from_the_origin(torch_dev, rng):
+    """Shapes thousands of units from the origin, at Q that float32 cannot represent: the FP32 pair sums
+    run at Q rounded to float in coordinates centred on the shape, and the translation phase e^{iQ.c},
+    1/|Q|^2 and the small-|Q| FP64 series take the caller's Q (Q rounded to float would move the phase
+    by |c| times the rounding, 3e-5 rad here).  Against the oracle within 1e-5 of F(0)."""
+    q2 = np.concatenate([[[0.0, 0.0], [1e-5, -2e-5], [0.3, -0.2]], rng.uniform(-40, 40, (800, 2))])
+    for c in ((2500.0, -1800.0), (90000.0, -60000.0)):
+        v = synth.star_polygon(200, seed=8, center=c).astype(np.float32)
+        ref = oracle.ft2d(v, q2)
+        assert rel_err(run2d(torch_dev, v, q2), ref, ref[0]) < TOL["fp32"], c
+    v, f = synth.perturbed_icosphere(3, seed=9, amp=0.05)
+    v = (v.astype(np.float64) + np.array([1500.0, -2200.0, 800.0])).astype(np.float32)
+    q3 = np.concatenate([[[0.0, 0.0, 0.0], [1e-5, 0.0, 2e-5], [0.3, -0.2, 0.1]], rng.uniform(-25, 25, (600, 3))])
+    ref = oracle.ft3d(v, f, q3)
+    assert rel_err(run3d(torch_dev, v, f, q3), ref, ref[0]) < TOL["fp32"]

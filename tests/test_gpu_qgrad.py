@@ -105,3 +105,15 @@ def test_tiny_q_beside_large_q(torch_dev, rng):
     ref = oracle.qgrad3d(v, f, q, g)
     assert np.max(np.abs(got - ref)) < 1e-5 * _scale(v, f, g)
     assert np.max(np.abs(got[::32] - ref[::32])) < 1e-9 * _scale(v, f, g)
+
+
+def test_far_from_the_origin(torch_dev, rng):
+    """dL/dQ of a mesh about 2,800 units from the origin at Q that float32 cannot represent: the
+    factors and the phase take the caller's Q."""
+    v, f = synth.perturbed_icosphere(2, seed=14, amp=0.08)
+    v = (v.astype(np.float64) + np.array([1500.0, -2200.0, 800.0])).astype(np.float32)
+    q = np.concatenate([[[1e-5, 0, 2e-5], [0.3, -0.2, 0.1]], rng.uniform(-25, 25, (800, 3))])
+    g = rng.normal(size=q.shape[0]) + 1j * rng.normal(size=q.shape[0])
+    got = _qgrad(torch_dev, v, f, q, g)
+    ref = oracle.qgrad3d(v, f, q, g)
+    assert np.max(np.abs(got - ref)) < 1e-5 * _scale(v, f, g)
