@@ -51,6 +51,9 @@ OPS = {
     # skips the shared edge's u^2, Chebyshev sinc and range test (8), so each face costs 88 on average
     "edge_sum_shared": {"fp32": 88, "sfu": 7},
 }
+# An edge of the edge sum with |Q.d/2| > pi: sin(u)/u on the SFU (sinc_large: the turn reduction 4, the
+# SFU argument scaling 1, the product with 1/u 1; sin and 1/u on the SFU) on top of the polynomial.
+OPS_EDGE_SFU_SINC = {"fp32": 6, "sfu": 2}
 SERIES_BOUNDS = [("series_k7", 0.25), ("series_k9", 1.0), ("series_k11", 2.25),
                  ("series_k13", 4.0)]         # P bounds of the forms below k = 17 (kP* in pft_pairs.cuh)
 # 2D segment term (Pol2F32::tile): projections 6, u^2 1, Chebyshev sinc 6, range test 1, the
@@ -175,18 +178,9 @@ def peaks():
         return {"sm_max_mhz": 2070.0}, "fallback"
 
 
-def branch_mix(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0, n_pairs=0):
-    """Fractions of (Q, face) pairs the kernel evaluates with each branch.
-
-    Mirrors the kernel's rule on a seeded sample: for one face, a warp holds the
-    Q indices base + k*nt + 32*w + lane (k < r, lane < 32); if every one has
-    P < p_hi = tau^2/4 they all take the first series form whose bound b has
-    p_hi <= b or every P < b (k = 17 when none has); otherwise the edge sum (the
-    few pairs below tau_lo^2/4 that the edge branch redoes with the series are
-    counted as edge).  Thresholds are compared in float32, as the kernel does.  With n_pairs > 0
-    (faces 2k, 2k+1 paired, k < n_pairs) a paired face whose partner takes the edge sum in the same
-    warp as well is counted as edge_sum_shared.
-    """
+def _warp_sample(v, f, q, r, nt, n_warps, seed):
+    """A seeded sample of (face, warp) pairs as the kernel forms them: for one face, a warp holds the
+    Q indices base + k*nt + 32*w + lane (k < r, lane < 32).  Returns the faces and the Q of each warp."""
     rng = np.random.default_rng(seed)
     fi = rng.integers(0, f.shape[0], n_warps)
     per_block = r * nt
@@ -195,13 +189,20 @@ def branch_mix(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0, n_pairs=0):
     idx = (base[:, None, None] + np.arange(r)[None, :, None] * nt + 32 * w[:, None, None]
            + np.arange(32)[None, None, :]).reshape(n_warps, -1)
     idx = np.minimum(idx, q.shape[0] - 1)
-    qq = q[idx]                                          # [w, r*32, 3]
+    return fi, q[idx]                                    # [w], [w, r*32, 3]
+
+
+def _corner_phases(v, f, faces, qq):
+    p = v.astype(np.float64)[f[faces]]                   # [w, 3, 3]
+    g = p.mean(axis=1)
+    return np.einsum("wlj,wj->wl", qq, p[:, 0] - g), np.einsum("wlj,wj->wl", qq, p[:, 1] - g)
+
+
+def _edge_rule(v, f, q, tau, r, nt, n_warps, seed, n_pairs):
+    fi, qq = _warp_sample(v, f, q, r, nt, n_warps, seed)
 
     def warp_pmax(faces):
-        p = v.astype(np.float64)[f[faces]]               # [w, 3, 3]
-        g = p.mean(axis=1)
-        a0 = np.einsum("wlj,wj->wl", qq, p[:, 0] - g)
-        a1 = np.einsum("wlj,wj->wl", qq, p[:, 1] - g)
+        a0, a1 = _corner_phases(v, f, faces, qq)
         return (a0 * a0 + a0 * a1 + a1 * a1).max(axis=1).astype(np.float32)
 
     pmax = warp_pmax(fi)
@@ -211,6 +212,21 @@ def branch_mix(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0, n_pairs=0):
     if n_pairs > 0:
         partner = np.where(fi < 2 * n_pairs, fi ^ 1, fi)
         shared = (fi < 2 * n_pairs) & ~left & (warp_pmax(partner) >= p_hi)
+    return fi, qq, pmax, p_hi, left, shared
+
+
+def branch_mix(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0, n_pairs=0):
+    """Fractions of (Q, face) pairs the kernel evaluates with each branch.
+
+    Mirrors the kernel's rule on a seeded sample (`_warp_sample`): if every Q of a warp has
+    P < p_hi = tau^2/4 they all take the first series form whose bound b has
+    p_hi <= b or every P < b (k = 17 when none has); otherwise the edge sum (the
+    few pairs below tau_lo^2/4 that the edge branch redoes with the series are
+    counted as edge).  Thresholds are compared in float32, as the kernel does.  With n_pairs > 0
+    (faces 2k, 2k+1 paired, k < n_pairs) a paired face whose partner takes the edge sum in the same
+    warp as well is counted as edge_sum_shared.
+    """
+    _, _, pmax, p_hi, left, shared = _edge_rule(v, f, q, tau, r, nt, n_warps, seed, n_pairs)
     out = {"edge_sum": float(np.mean(~left & ~shared)), "edge_sum_shared": float(np.mean(shared))}
     for name, b in SERIES_BOUNDS:
         take = left & ((p_hi <= np.float32(b)) | (pmax < np.float32(b)))
@@ -218,6 +234,19 @@ def branch_mix(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0, n_pairs=0):
         left &= ~take
     out["series_k17"] = float(np.mean(left))
     return {k: out[k] for k in OPS}
+
+
+def edge_sfu_sinc(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0, n_pairs=0):
+    """Edges per pair (over all pairs) whose sinc the edge sum takes on the SFU: in a warp on the edge
+    sum, edge l of a pair with u_l^2 > pi^2 in float32, u = ((a1 - a0)/2, (-a0 - 2 a1)/2, (2 a0 + a1)/2)
+    (face_edge; the shared edge of a paired face is evaluated by its partner).  Each costs
+    OPS_EDGE_SFU_SINC on top of the polynomial sinc every edge pays."""
+    fi, qq, _, _, left, shared = _edge_rule(v, f, q, tau, r, nt, n_warps, seed, n_pairs)
+    a0, a1 = _corner_phases(v, f, fi, qq)
+    u = np.stack([(a1 - a0) / 2, (-a0 - 2 * a1) / 2, (2 * a0 + a1) / 2], axis=-1).astype(np.float32)
+    big = (u * u) > np.float32(np.pi ** 2)                # [w, r*32, 3]
+    per_pair = np.where(shared[:, None], big[:, :, 1:].sum(axis=-1), big.sum(axis=-1))
+    return float(np.mean(np.where((~left)[:, None], per_pair, 0)))
 
 
 def kernel_order(pft, q, qd, r, nt, n_items):
@@ -311,9 +340,10 @@ def roofline2d(pairs, t_s, f_sfu, n_sm, clk_mhz, table=None, paired=True):
             "peak_basis": "128 FP32 lanes" if paired else "128 FP32/SFU issue slots"}
 
 
-def roofline(pairs, t_main_s, mix, n_sm, clk_mhz, paired=True):
-    """3D face term: (ops per pair, binding ops per pair, achieved and peak binding ops/s)."""
-    ops = {k: sum(mix[b] * OPS[b][k] for b in OPS) for k in ("fp32", "sfu")}
+def roofline(pairs, t_main_s, mix, n_sm, clk_mhz, paired=True, sfu_edges=0.0):
+    """3D face term: (ops per pair, binding ops per pair, achieved and peak binding ops/s).
+    sfu_edges: edges per pair whose sinc the edge sum takes on the SFU (`edge_sfu_sinc`)."""
+    ops = {k: sum(mix[b] * OPS[b][k] for b in OPS) + sfu_edges * OPS_EDGE_SFU_SINC[k] for k in ("fp32", "sfu")}
     cyc, lanes = bound_cycles(ops, paired)                       # SM cycles per pair at the limit
     peak_ops = n_sm * clk_mhz * 1e6 * lanes / cyc                # binding ops/s at the limit
     achieved = lanes * pairs / t_main_s
@@ -566,9 +596,11 @@ def bench_batched3d(dev, warmup, steps):
     ms = float(np.mean(ts))
     pairs = float(f.shape[0]) * float(q.shape[0])
     pk, _ = peaks()
-    mix = branch_mix(v, f, kernel_order(pft, q, qd, r, nt, f.shape[0]), tau=6.0, r=r, nt=nt)
+    qk = kernel_order(pft, q, qd, r, nt, f.shape[0])
+    mix = branch_mix(v, f, qk, tau=6.0, r=r, nt=nt)
+    sfu_e = edge_sfu_sinc(v, f, qk, tau=6.0, r=r, nt=nt)
     _, _, ach, peak = roofline(pairs, ms / 1e3, mix, torch.cuda.get_device_properties(dev).multi_processor_count,
-                               float(pk.get("sm_max_mhz", 2070.0)))
+                               float(pk.get("sm_max_mhz", 2070.0)), sfu_edges=sfu_e)
     status = int(pft.pft_status(prep.ws))
     del g                                    # the CUDA graph
     # the batched adjoint: vertex gradients of every mesh for seeded weights on the same grid
@@ -593,6 +625,7 @@ def bench_batched3d(dev, warmup, steps):
             "q_points": int(q.shape[0]), "launch_shape": [r, nt], "launches_per_step": int(launches),
             "cuda_graph": True,
             "device_status": status, "roofline_frac": ach / peak, "branch_fractions": mix,
+            "edge_sfu_sinc_per_pair": sfu_e,
             "backward": backward,
             "note": "whole batched call timed (prep, pair kernel, multi-chunk finish, small-|Q| pass)",
             "l2": "flushed between steps"}
@@ -673,12 +706,15 @@ def bench_polymesh(dev, warmup, steps):
     ref = (f2[:, 0] + 1j * f2[:, 1]) * h * np.sinc(x / np.pi) * np.exp(1j * x)
     vol = abs(got[int(np.flatnonzero(np.all(q == 0, axis=1))[0])])
     pk, _ = peaks()
-    mix = branch_mix(v, halving_triangles(idx, off), kernel_order(pft, q, qd, 4, 128, n_tris), tau=6.0, r=4, nt=128)
+    tris, qk = halving_triangles(idx, off), kernel_order(pft, q, qd, 4, 128, n_tris)
+    mix = branch_mix(v, tris, qk, tau=6.0, r=4, nt=128)
+    sfu_e = edge_sfu_sinc(v, tris, qk, tau=6.0, r=4, nt=128)
     _, _, ach, peak = roofline(pairs, ms / 1e3, mix, torch.cuda.get_device_properties(dev).multi_processor_count,
-                               float(pk.get("sm_max_mhz", 2070.0)))
+                               float(pk.get("sm_max_mhz", 2070.0)), sfu_edges=sfu_e)
     return {"value": pairs / (ms / 1e3) / 1e9, "unit": UNIT + " (Q, triangle)", "ms_per_call": ms,
             "faces": int(off.size - 1), "triangles": n_tris, "q_points": int(q.shape[0]), "pairs_per_call": pairs,
             "launches_per_call": launches, "roofline_frac": ach / peak, "branch_fractions": mix,
+            "edge_sfu_sinc_per_pair": sfu_e,
             "vs_2d_path_times_extrusion_max_abs_over_volume": float(np.max(np.abs(got - ref)) / vol),
             "l2": "flushed between calls"}
 
@@ -1004,16 +1040,23 @@ def main():
         clk_max = float(pk.get("sm_max_mhz", 2070.0))
         qk = kernel_order(pft, q, qd, args.q_per_thread, args.block_threads, f.shape[0])
         mix = branch_mix(v, f, qk, tau=args.tau or 6.0, r=args.q_per_thread, nt=args.block_threads)
+        sfu_e = edge_sfu_sinc(v, f, qk, tau=args.tau or 6.0, r=args.q_per_thread, nt=args.block_threads)
         paired = args.q_per_thread % 2 == 0        # even R: Q points in paired FP32 registers
-        ops, lanes, achieved, peak_ops = roofline(pairs, ms_main / 1e3, mix, n_sm, clk_max, paired)
+        ops, lanes, achieved, peak_ops = roofline(pairs, ms_main / 1e3, mix, n_sm, clk_max, paired, sfu_e)
         for variant in variants:
             if "face_pairs" in variant:
-                vmix = branch_mix(v, f_pairs, qk, tau=variant["face_series_tau"], r=args.q_per_thread,
-                                  nt=args.block_threads, n_pairs=n_pairs)
+                vkw = dict(tau=variant["face_series_tau"], r=args.q_per_thread, nt=args.block_threads,
+                           n_pairs=n_pairs)
+                vf = f_pairs
             else:
-                vmix = branch_mix(v, f, qk, tau=variant["face_series_tau"], r=args.q_per_thread, nt=args.block_threads)
-            _, _, v_ach, v_peak = roofline(pairs, variant["main_kernel_ms"] / 1e3, vmix, n_sm, clk_max, paired)
+                vkw = dict(tau=variant["face_series_tau"], r=args.q_per_thread, nt=args.block_threads)
+                vf = f
+            vmix = branch_mix(v, vf, qk, **vkw)
+            v_sfu = edge_sfu_sinc(v, vf, qk, **vkw)
+            _, _, v_ach, v_peak = roofline(pairs, variant["main_kernel_ms"] / 1e3, vmix, n_sm, clk_max, paired,
+                                           v_sfu)
             variant["branch_fractions"] = vmix
+            variant["edge_sfu_sinc_per_pair"] = v_sfu
             variant["roofline_frac"] = v_ach / v_peak
         value = whole_job_rate(world, pairs, ms_step)
         line = {
@@ -1038,7 +1081,7 @@ def main():
                                         f"{n_sm} SMs x 128 FP32/SFU issue slots x {clk_max:.0f} MHz "
                                         f"({pk_kind} max SM clock)"),
                          "ops_per_pair": {"fp32": ops["fp32"], "sfu": ops["sfu"]},
-                         "branch_fractions": mix},
+                         "branch_fractions": mix, "edge_sfu_sinc_per_pair": sfu_e},
             "clocks": clk,
             "gpu_launches": launches,
             "e2e": {"value": whole_job_rate(world, pairs, e2e_t), "unit": UNIT,

@@ -291,3 +291,22 @@ def test_branch_mix_with_pairs_splits_the_edge_sums(mesh):
     for k in plain:
         if not k.startswith("edge"):
             assert paired[k] == plain[k]
+
+
+def test_edge_sfu_sinc_count():
+    """bench.edge_sfu_sinc counts the edges whose sinc the edge sum takes on the SFU.  A triangle
+    (0,0,0), (L,0,0), (0,e,0) at Q = (k,0,0) has edge phases u = kL/2, -kL/2, 0 and P = (kL)^2/3:
+    kL = 6.5 puts it on the edge sum (P > 9) with two edges past pi; kL = 4 takes a series form
+    (P < 9, nothing counted), and at tau = 1 the edge sum with both |u| = 2 < pi."""
+    L, e = 1.0, 1e-3
+    v = np.array([[0, 0, 0], [L, 0, 0], [0, e, 0]], dtype=np.float32)
+    f = np.array([[0, 1, 2]], dtype=np.int32)
+    count = lambda kl, tau: bench.edge_sfu_sinc(v, f, np.tile([[kl / L, 0.0, 0.0]], (256, 1)), tau=tau, r=2,
+                                                nt=128, n_warps=16)
+    assert count(6.5, 6.0) == 2.0
+    assert count(4.0, 6.0) == 0.0
+    assert count(4.0, 1.0) == 0.0
+    assert count(6.5, 1.0) == 2.0
+    # the per-edge price is the 2D SFU sinc's extra over the polynomial one (the same sinc_large code)
+    assert bench.OPS_EDGE_SFU_SINC == {k: bench.OPS2D["sfu_sinc"][k] - bench.OPS2D["poly_sinc"][k]
+                                       for k in ("fp32", "sfu")}
