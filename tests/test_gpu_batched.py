@@ -203,3 +203,29 @@ def test_far_from_the_origin_phase_reduction(torch_dev, shape):
     for i in range(len(parts)):
         ref = oracle.ft2d(v[off[i]:off[i + 1]], q)
         assert np.max(np.abs(got[i] - ref)) / areas[i] < TOL["fp32"], i
+
+
+def test_per_polygon_q_sets_one_block_per_sm(torch_dev):
+    """Per-polygon Q lists (short ones among them: 2,048-point Q tiles mostly empty) with one block of
+    512 threads per SM asked for: bit for bit the default launch shape's result (2D sums do not depend
+    on the launch shape), and the oracle."""
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    v, off = _mixed_batch()
+    rng = np.random.default_rng(6)
+    counts = np.array([5, 0, 700, 3, 1, 64, 2100, 2, 0, 40, 1000, 6])
+    q_off = np.zeros(counts.size + 1, dtype=np.int64)
+    q_off[1:] = np.cumsum(counts)
+    q = rng.uniform(-25, 25, (q_off[-1], 2))
+    args = (torch.from_numpy(v).to(dev), torch.from_numpy(off), torch.from_numpy(q).to(dev))
+    a = pft.pft2d_polygons_batched(*args, q_off=torch.from_numpy(q_off), check_status=True)
+    b = pft.pft2d_polygons_batched(*args, q_off=torch.from_numpy(q_off), options={"q_per_thread": 4,
+                                   "block_threads": 512}, check_status=True)
+    assert torch.equal(a, b)
+    got = _c(b)
+    areas = _areas(v, off)
+    ref = oracle.ft2d_batched(v, off, q, q_off=q_off)
+    for i in range(counts.size):
+        sl = slice(q_off[i], q_off[i + 1])
+        if counts[i]:
+            assert np.max(np.abs(got[sl] - ref[sl])) / areas[i] < TOL["fp32"], i

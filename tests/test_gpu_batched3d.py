@@ -211,3 +211,23 @@ def test_far_from_the_origin_phase_reduction(torch_dev, rng):
         vi, fi = _mesh(v, f, off, i)
         ref = oracle.ft3d(vi, fi, q)
         assert np.max(np.abs(got[i] - ref)) / abs(ref[0]) < TOL["fp32"], i
+
+
+def test_per_mesh_q_sets_one_block_per_sm(torch_dev, rng):
+    """Per-mesh Q lists with one block of 512 threads per SM asked for (the 2,048-point Q tiles of the
+    short lists mostly empty), against the oracle."""
+    torch, dev = torch_dev
+    import paper_2104_08309_gb300 as pft
+    v, f, off = synth.mesh_batch(9, seed=7)
+    counts = rng.integers(1, 2500, off.size - 1)
+    q_off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    q = rng.uniform(-20, 20, (int(q_off[-1]), 3))
+    q[q_off[:-1]] = 0.0
+    got = _c(pft.pft3d_meshes_batched(torch.from_numpy(v).to(dev), torch.from_numpy(f).to(dev), off,
+                                      torch.from_numpy(q).to(dev), q_off,
+                                      options={"q_per_thread": 4, "block_threads": 512}, check_status=True))
+    for i in range(off.size - 1):
+        vi, fi = _mesh(v, f, off, i)
+        sl = slice(q_off[i], q_off[i + 1])
+        ref = oracle.ft3d(vi, fi, q[sl])
+        assert np.max(np.abs(got[sl] - ref)) / abs(ref[0]) < TOL["fp32"], i
