@@ -7,6 +7,7 @@ float32 steps, which bounds the FMA form from above).
 import math
 import os
 import re
+from fractions import Fraction
 
 import numpy as np
 
@@ -271,3 +272,63 @@ def test_p_bits_order_as_unsigned():
     bits = x.view(np.uint32)
     assert np.all(np.diff(bits.astype(np.int64)) >= 0)
     assert np.uint32(0x7F800000) > bits.max() and np.float32(np.nan).view(np.uint32) > np.uint32(0x7F800000)
+
+
+def _fmaf(a, b, c):
+    """fmaf for float32 inputs: the product is exact in float64; the sum is rounded to float64 and then
+    to float32, which differs from the fused single rounding only in rare ties (immaterial to the
+    bound below; the one exactness claim is checked with rationals)."""
+    return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def _two_sum(a, b):
+    s = np.float32(a + b)
+    bb = np.float32(s - a)
+    return s, np.float32(np.float32(a - np.float32(s - bb)) + np.float32(b - bb))
+
+
+def test_fp32_finish_phase_reduction():
+    """The batched FP32 finish reduces the translation phase Q.c without FP64 arithmetic: Q.c as
+    s + t (products with the centre's float high part split exactly by FMA, the low parts of Q and
+    c in t), k = rint(s / 2 pi), ph = fma(-k, 2pi_hi, s) + fma(-k, 2pi_lo, t).  The constants are
+    the float32 rounding of 2 pi and its residual; s - k 2pi_hi is exact in float32; and the phase
+    matches Q.c mod 2 pi (50-digit reference) within 3e-7 rad for |Q.c| below 2^20."""
+    mpmath = __import__("pytest").importorskip("mpmath")
+    text = open(os.path.join(CSRC, "pft_batched.cu")).read()
+    hi = np.float32(float(re.search(r"kTwoPiHi = ([-+0-9.e]+)f", text).group(1)))
+    lo = np.float32(float(re.search(r"kTwoPiLo = ([-+0-9.e]+)f", text).group(1)))
+    inv = np.float32(float(re.search(r"kInvTwoPi = ([-+0-9.e]+)f", open(os.path.join(CSRC, "pft_common.cuh")).read()).group(1)))
+    assert hi == np.float32(2 * math.pi) and lo == np.float32(2 * math.pi - float(hi))
+    mpmath.mp.dps = 50
+    two_pi = 2 * mpmath.pi
+    rng = np.random.default_rng(7)
+    worst, n_checked = 0.0, 0
+    for _ in range(400):
+        q = rng.uniform(-60, 60, 3)                                     # the caller's FP64 Q
+        c = rng.uniform(-1e4, 1e4, 3) * rng.choice([1e-4, 1e-2, 1.0])   # the FP64 centre
+        qh = q.astype(np.float32)
+        ql = (q - qh.astype(np.float64)).astype(np.float32)
+        ch = c.astype(np.float32)
+        cl = (c - ch.astype(np.float64)).astype(np.float32)
+        s = np.float32(qh[0] * ch[0])
+        t = _fmaf(qh[0], ch[0], -s)
+        for d in (1, 2):
+            p = np.float32(qh[d] * ch[d])
+            e = _fmaf(qh[d], ch[d], -p)
+            s, e2 = _two_sum(s, p)
+            t = np.float32(t + np.float32(e2 + e))
+        for d in range(3):
+            t = _fmaf(ql[d], ch[d], _fmaf(qh[d], cl[d], t))
+        if not abs(s) < 2.0 ** 20:       # the kernel takes its FP64 finish there
+            continue
+        n_checked += 1
+        k = np.float32(np.rint(np.float32(s * inv)))
+        exact = Fraction(float(s)) - Fraction(float(k)) * Fraction(float(hi))
+        r = np.float32(float(exact))
+        assert Fraction(float(r)) == exact                                       # s - k 2pi_hi fits a float32
+        ph = np.float32(r + _fmaf(-k, lo, t))
+        ref = mpmath.fsum(mpmath.mpf(float(qd)) * mpmath.mpf(float(cd)) for qd, cd in zip(q, c))
+        ref = ref - two_pi * mpmath.nint(ref / two_pi)
+        err = abs(float(ph) - float(ref))
+        worst = max(worst, min(err, abs(err - 2 * math.pi)))
+    assert n_checked > 300 and worst < 3e-7, (n_checked, worst)
