@@ -635,6 +635,13 @@ __device__ __forceinline__ void finish_out_f32(const float* Q, const float* Qlo,
 // keep one block per SM fewer here (4 at 4 Q points, 5 at 2), where the item loop and the
 // in-place finish would otherwise spill, and that 512 threads are one block per SM (up to 128
 // registers: 16 warps, as 2 x 256 or 4 x 128).
+// Records per tile of the batched kernel's ring.  With one block of 16 warps per SM walking it (the
+// 512-thread shapes), tiles twice the single-shape kernel's ran faster: 4,096 polygons, 256 segments
+// 7.63 against 7.70 ms at 128; 1,024 meshes, 128 faces 67.2 against 68.2 ms at 64 (a 16 KB or 24 KB
+// ring).  The other launch shapes keep the policy's tile.
+template <class Pol, int NT>
+constexpr int kBTile = NT >= 512 ? 2 * Pol::kTile : Pol::kTile;
+
 template <class Pol, int R, int NT>
 constexpr int kBatchedMinBlocks = NT >= 512 ? 1
                                   : (Pol::kDim == 3 && R == 4 && NT == 128) ? 4
@@ -650,7 +657,7 @@ __global__ void __launch_bounds__(NT, kBatchedMinBlocks<Pol, R, NT>) k_batched(
     WsHeader* h, Thr th, const int32_t* __restrict__ qperm, const float* __restrict__ qlo) {
   using Item = typename Pol::Item;
   using QT = typename Pol::QT;
-  constexpr int TILE = Pol::kTile;
+  constexpr int TILE = kBTile<Pol, NT>;
   constexpr int D = Pol::kDim;
   constexpr int NW = NT / 32;
   __shared__ __align__(128) Item ring[kStages * TILE];

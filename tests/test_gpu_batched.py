@@ -156,11 +156,13 @@ def test_plan_mismatch_is_rejected(torch_dev):
                                    check_status=True)
 
 
-def test_default_shape_on_a_large_shared_grid_is_bitwise_the_same(torch_dev):
+def test_default_shape_on_a_large_shared_grid(torch_dev):
     """On a shared Q set of 4 x 512 points or more the default launch shape is one block of 512
-    threads per SM; every Q point's sum runs over the same segments in the same order in any
-    launch shape, so the result equals the 4 x 128 and 4 x 256 shapes bit for bit (and the oracle
-    on sampled polygons)."""
+    threads per SM (bit for bit the same as asking for it).  Every Q point's sum runs over the same
+    segments in the same order in any launch shape, but the 512-thread shapes sum over tiles of 256
+    segments rather than 128 (the FP32 sums are compensated across tiles): the 4 x 128 and 4 x 256
+    shapes agree with each other bit for bit and with the default to rounding, and all with the
+    oracle on sampled polygons."""
     torch, dev = torch_dev
     import paper_2104_08309_gb300 as pft
     v, off = synth.batched_star_polygons(96, seed=8)
@@ -172,9 +174,11 @@ def test_default_shape_on_a_large_shared_grid_is_bitwise_the_same(torch_dev):
                        ("4x512", {"q_per_thread": 4, "block_threads": 512})):
         prep = pft.pft2d_batched_prepare(off, q.shape[0], options=opts, device=dev)
         outs[name] = pft.pft2d_polygons_batched(vd, offd, qd, prepared=prep, check_status=True).clone()
-    for name in ("4x128", "4x256", "4x512"):
-        assert torch.equal(outs["default"], outs[name]), name
-    got = _c(outs["default"])
+    assert torch.equal(outs["default"], outs["4x512"])
+    assert torch.equal(outs["4x128"], outs["4x256"])
+    got, alt = _c(outs["default"]), _c(outs["4x128"])
+    area = np.abs(got[:, np.flatnonzero(np.all(q == 0, axis=1))[0]])
+    assert np.max(np.abs(got - alt).max(axis=1) / area) < 1e-6
     for i in (0, 17, 95):
         vi = v[off[i]:off[i + 1]]
         ref = oracle.ft2d(vi, q)
@@ -207,8 +211,8 @@ def test_far_from_the_origin_phase_reduction(torch_dev, shape):
 
 def test_per_polygon_q_sets_one_block_per_sm(torch_dev):
     """Per-polygon Q lists (short ones among them: 2,048-point Q tiles mostly empty) with one block of
-    512 threads per SM asked for: bit for bit the default launch shape's result (2D sums do not depend
-    on the launch shape), and the oracle."""
+    512 threads per SM asked for: the default launch shape's result to rounding (the 512-thread shapes
+    sum over tiles of 256 segments, the others 128), and the oracle."""
     torch, dev = torch_dev
     import paper_2104_08309_gb300 as pft
     v, off = _mixed_batch()
@@ -221,9 +225,13 @@ def test_per_polygon_q_sets_one_block_per_sm(torch_dev):
     a = pft.pft2d_polygons_batched(*args, q_off=torch.from_numpy(q_off), check_status=True)
     b = pft.pft2d_polygons_batched(*args, q_off=torch.from_numpy(q_off), options={"q_per_thread": 4,
                                    "block_threads": 512}, check_status=True)
-    assert torch.equal(a, b)
-    got = _c(b)
     areas = _areas(v, off)
+    ca, cb = _c(a), _c(b)
+    for i in range(counts.size):
+        sl = slice(q_off[i], q_off[i + 1])
+        if counts[i]:
+            assert np.max(np.abs(ca[sl] - cb[sl])) / areas[i] < 1e-6, i
+    got = cb
     ref = oracle.ft2d_batched(v, off, q, q_off=q_off)
     for i in range(counts.size):
         sl = slice(q_off[i], q_off[i + 1])

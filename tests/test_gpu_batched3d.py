@@ -156,7 +156,7 @@ def test_empty_mesh_in_batch(torch_dev, rng):
         assert np.max(np.abs(got[k] - ref)) / abs(ref[0]) < TOL["fp32"]
 
 
-def test_default_shape_on_a_large_shared_grid_is_bitwise_the_same(torch_dev):
+def test_default_shape_on_a_large_shared_grid(torch_dev):
     """On a shared Q set of 4 x 512 points or more the default launch shape is one block of 512
     threads per SM (the same result bit for bit as asking for it).  The series form of a face is
     chosen per warp from the largest P over the warp's Q points, and without the library's Q order
