@@ -636,11 +636,11 @@ __device__ __forceinline__ void finish_out_f32(const float* Q, const float* Qlo,
 // in-place finish would otherwise spill, and that 512 threads are one block per SM (up to 128
 // registers: 16 warps, as 2 x 256 or 4 x 128).
 // Records per tile of the batched kernel's ring.  With one block of 16 warps per SM walking it (the
-// 512-thread shapes), tiles twice the single-shape kernel's ran faster: 4,096 polygons, 256 segments
-// 7.63 against 7.70 ms at 128; 1,024 meshes, 128 faces 67.2 against 68.2 ms at 64 (a 16 KB or 24 KB
-// ring).  The other launch shapes keep the policy's tile.
+// 512-thread shapes), 256 segments ran faster than 128 (4,096 polygons: 7.63 against 7.70 ms) and
+// 128 faces faster than 64 (1,024 meshes: 67.2 against 68.2 ms): a 16 KB or 24 KB ring.  The other
+// launch shapes take the policy's tile.
 template <class Pol, int NT>
-constexpr int kBTile = NT >= 512 ? 2 * Pol::kTile : Pol::kTile;
+constexpr int kBTile = NT >= 512 ? (Pol::kDim == 2 ? 256 : 128) : Pol::kTile;
 
 template <class Pol, int R, int NT>
 constexpr int kBatchedMinBlocks = NT >= 512 ? 1
