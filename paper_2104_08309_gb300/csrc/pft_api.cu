@@ -85,11 +85,12 @@ FwdLaunch plan_fwd(int dim, const Opts& o, int64_t n_items, int64_t n_q) {
       if (eff > best_eff + 1e-9) { best_eff = eff; best_k = c; }
     }
     if (k == 0) k = best_k;
-    // Long launches: more chunks, up to about 40 waves (chunks of at least 64 tiles, the last wave
-    // still >= 97 % full).  Blocks do not finish in waves: the resident blocks of an SM share it
-    // unevenly, and the last blocks to start leave SMs partly idle for about a third of a block's
-    // run (a 1.3M-face mesh on 2M Q points: 10.8 waves lost 2 % of the launch against 43).
-    const int kw_max = (int)std::min<int64_t>(64, item_tiles / 64);
+    // Long launches: more chunks, up to about 40 waves (chunks of at least 4,096 faces or 8,192
+    // segments, the last wave still >= 97 % full).  Blocks do not finish in waves: the resident
+    // blocks of an SM share it unevenly, and the last blocks to start leave SMs partly idle for about
+    // a third of a block's run (a 1.3M-face mesh on 2M Q points: 10.8 waves lost 2 % of the launch
+    // against 43).
+    const int kw_max = (int)std::min<int64_t>(64, n_items / (dim == 3 ? 4096 : 8192));
     if ((double)(L.q_tiles * k) / (double)slots < 40.0) {
       for (int c = k + 1; c <= kw_max; ++c) {
         const double waves = (double)(L.q_tiles * c) / (double)slots;
