@@ -239,13 +239,14 @@ def branch_mix(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0, n_pairs=0):
 def edge_sfu_sinc(v, f, q, tau=6.0, r=2, nt=128, n_warps=4096, seed=0, n_pairs=0):
     """Edges per pair (over all pairs) whose sinc the edge sum takes on the SFU: in a warp on the edge
     sum, edge l of a pair with u_l^2 > pi^2 in float32, u = ((a1 - a0)/2, (-a0 - 2 a1)/2, (2 a0 + a1)/2)
-    (face_edge; the shared edge of a paired face is evaluated by its partner).  Each costs
-    OPS_EDGE_SFU_SINC on top of the polynomial sinc every edge pays."""
+    (face_edge).  The shared first edge of a pair whose faces both take the edge sum is evaluated once,
+    by the first face, for both: half an edge per face, as edge_sum_shared averages its saving.  Each
+    costs OPS_EDGE_SFU_SINC on top of the polynomial sinc every edge pays."""
     fi, qq, _, _, left, shared = _edge_rule(v, f, q, tau, r, nt, n_warps, seed, n_pairs)
     a0, a1 = _corner_phases(v, f, fi, qq)
     u = np.stack([(a1 - a0) / 2, (-a0 - 2 * a1) / 2, (2 * a0 + a1) / 2], axis=-1).astype(np.float32)
     big = (u * u) > np.float32(np.pi ** 2)                # [w, r*32, 3]
-    per_pair = np.where(shared[:, None], big[:, :, 1:].sum(axis=-1), big.sum(axis=-1))
+    per_pair = np.where(shared[:, None], big[:, :, 1:].sum(axis=-1) + 0.5 * big[:, :, 0], big.sum(axis=-1))
     return float(np.mean(np.where((~left)[:, None], per_pair, 0)))
 
 

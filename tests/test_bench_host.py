@@ -307,6 +307,12 @@ def test_edge_sfu_sinc_count():
     assert count(4.0, 6.0) == 0.0
     assert count(4.0, 1.0) == 0.0
     assert count(6.5, 1.0) == 2.0
+    # a pair sharing its first edge (faces 0 and 1, both on the edge sum): that edge counts half per face
+    v2 = np.array([[0, 0, 0], [L, 0, 0], [0, e, 0], [0, -e, 0]], dtype=np.float32)
+    f2 = np.array([[0, 1, 2], [1, 0, 3]], dtype=np.int32)
+    q2 = np.tile([[6.5 / L, 0.0, 0.0]], (256, 1))
+    assert bench.edge_sfu_sinc(v2, f2, q2, tau=6.0, r=2, nt=128, n_warps=64, n_pairs=1) == 1.5
+    assert bench.edge_sfu_sinc(v2, f2, q2, tau=6.0, r=2, nt=128, n_warps=64) == 2.0
     # the per-edge price is the 2D SFU sinc's extra over the polynomial one (the same sinc_large code)
     assert bench.OPS_EDGE_SFU_SINC == {k: bench.OPS2D["sfu_sinc"][k] - bench.OPS2D["poly_sinc"][k]
                                        for k in ("fp32", "sfu")}
