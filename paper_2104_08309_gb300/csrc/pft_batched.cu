@@ -780,12 +780,12 @@ __global__ void __launch_bounds__(NT, kBatchedMinBlocks<Pol, R, NT>) k_batched(
       if (iq >= qend) continue;
       const int64_t local = (qperm ? (int64_t)qperm[iq] : iq) - pp.q_begin;
       if (pp.n_chunks > 1) {
-        const int64_t at_ = pp.part_base + (int64_t)it.chunk * pp.n_q + local;
+        const int64_t pidx = pp.part_base + (int64_t)it.chunk * pp.n_q + local;
         if constexpr (kF32)   // the compensated sums as they are: (re hi, re lo, im hi, im lo)
-          reinterpret_cast<float4*>(partial)[at_] =
+          reinterpret_cast<float4*>(partial)[pidx] =
               make_float4(acc.re[r].hi, acc.re[r].lo, acc.im[r].hi, acc.im[r].lo);
         else
-          partial[at_] = acc.get(r);
+          partial[pidx] = acc.get(r);
       } else if constexpr (kF32) {
         float ql[3] = {0.f, 0.f, 0.f};
 #pragma unroll
